@@ -1,0 +1,103 @@
+/*
+ * GeoFlood FP64 CPU oracle -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, single-threaded double-precision restatement of the
+ * per-patch wave-propagation step of GeoFlood (Kyanjo, Calhoun & George,
+ * "GeoFlood (v1.0.0): Computational model for overland flooding",
+ * arXiv 2403.15435).  It exists to check the CUDA library against the
+ * method.  Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline
+ * and reference legs may load it; the product path never links, imports or
+ * calls anything here, and nothing here includes a product header.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no fused multiply-add, IEEE
+ * sqrt and division), so every operation rounds exactly as written.
+ */
+#ifndef GEOFLOOD_ORACLE_H
+#define GEOFLOOD_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORACLE_BC_WALL 0
+#define ORACLE_BC_EXTRAP 1
+
+/* Patch flags produced by the tagger (Sec. 4.1 criteria 1, 3, 4). */
+#define ORACLE_TAG_KEEP 0
+#define ORACLE_TAG_REFINE 1
+#define ORACLE_TAG_COARSEN 2
+
+typedef struct {
+  int mi, mj;        /* blocks (trees) of the level-0 arrangement, Sec. 4 */
+  int mx;            /* patch cells per side (square patches mx x mx) */
+  int minlevel, maxlevel;
+  int bc[4];         /* left, right, bottom, top: ORACLE_BC_* */
+  double xlower, xupper, ylower, yupper;
+  double g, drytol, manning_n;
+  double cfl_desired, cfl_max, dt_initial, dt_max;
+  double tag_depth, tag_speed, tag_deta, eta0;
+  double src_box[4]; /* x0, x1, y0, y1 of the flood-source region */
+  int src_level;     /* refine the source region up to this level */
+} oracle_config;
+
+typedef struct oracle_forest oracle_forest;
+
+/* One augmented Riemann solve at an edge in the normal frame (Sec. 3.3).
+ * Inputs per side: depth h, normal momentum n, transverse momentum t, bed b.
+ * Outputs: Z[3][3] f-waves (wave p, component k = mass, normal momentum,
+ * transverse momentum) and s[3] wave speeds. */
+void oracle_riemann(double hL, double nL, double tL, double bL, double hR,
+                    double nR, double tR, double bR, double g, double drytol,
+                    double* Z, double* s);
+
+/* One unsplit second-order step on a single grid of nx*ny interior cells
+ * with 2 filled ghost layers; arrays are [ny+4][nx+4] row-major.  Writes the
+ * interior of hn/hun/hvn (ghost entries are copied from the input), returns
+ * in *cmax the largest |s|/dx or |s|/dy over the edges that update interior
+ * cells, in *nclip the number of negative depths reset to zero and in
+ * *clipdepth the sum of the depths so added. */
+void oracle_step_grid(int nx, int ny, const double* h, const double* hu,
+                      const double* hv, const double* b, double dx, double dy,
+                      double dt, double g, double drytol, double manning_n,
+                      double* hn, double* hun, double* hvn, double* cmax,
+                      long* nclip, double* clipdepth);
+
+/* Cell average of the bilinear interpolant of a DEM over a rectangle. */
+double oracle_dem_average(const double* z, int nx, int ny, double x0,
+                          double y0, double dx, double dy, double xa,
+                          double xb, double ya, double yb);
+
+oracle_forest* oracle_forest_new(const oracle_config* cfg);
+void oracle_forest_free(oracle_forest* f);
+int oracle_forest_set_topo(oracle_forest* f, const double* z, int nx, int ny,
+                           double x0, double y0, double dx, double dy);
+int oracle_forest_npatch(const oracle_forest* f);
+void oracle_forest_patch_info(const oracle_forest* f, int* level, int* px,
+                              int* py);
+/* Interior arrays [npatch][mx][mx] (row index j, column index i). */
+int oracle_forest_write(oracle_forest* f, const double* h, const double* hu,
+                        const double* hv);
+void oracle_forest_read(const oracle_forest* f, double* h, double* hu,
+                        double* hv, double* b);
+/* Whole tiles [npatch][4][mx+4][mx+4] (h, hu, hv, b), ghosts included. */
+void oracle_forest_read_tiles(const oracle_forest* f, double* out);
+void oracle_forest_set_time(oracle_forest* f, double t, double dt_next);
+void oracle_forest_get_time(const oracle_forest* f, double* t,
+                            double* dt_next, long* steps, long* rejects,
+                            long* nclip, double* clipvol);
+int oracle_forest_step(oracle_forest* f, double t_target, int max_steps,
+                       double* t_out, int* steps_out);
+void oracle_forest_tags(const oracle_forest* f, uint8_t* flags);
+int oracle_forest_regrid(oracle_forest* f);
+double oracle_forest_mass(const oracle_forest* f);
+int oracle_forest_set_gauges(oracle_forest* f, const double* xy, int n);
+void oracle_forest_gauges(const oracle_forest* f, double* out,
+                          double* arrival);
+void oracle_forest_ghost_fill(oracle_forest* f);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

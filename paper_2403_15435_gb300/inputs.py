@@ -1,0 +1,255 @@
+"""Seeded synthetic workloads (problem set-up only, no solver arithmetic).
+
+Shared by the tests, the benchmark and the oracle harness: every function here
+builds a problem description -- a configuration, a DEM grid, an initial
+condition and gauge points -- from a 64-bit seed.  Nothing here evaluates the
+wave-propagation method; both the CUDA library and the CPU oracle receive the
+same arrays.
+
+The workloads stand in for the paper's test cases (Sec. 5, Sec. 6), whose
+datasets (UK Environment Agency benchmarks, the CADAM Malpasset DEM) are not
+available: the shapes, sizes, depths, Manning coefficients and CFL numbers
+follow the paper and the benchmark configuration list; the terrain is synthetic.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Callable, Optional, Sequence, Tuple
+
+import numpy as np
+
+BC_WALL = 0
+BC_EXTRAP = 1
+
+SEED_BASE = 20240322
+
+
+@dataclasses.dataclass
+class Config:
+    """Forest, physics and control parameters (Sec. 4, Sec. 5.1, Sec. 6.6)."""
+
+    mi: int = 1
+    mj: int = 1
+    mx: int = 32
+    minlevel: int = 0
+    maxlevel: int = 0
+    bc: Tuple[int, int, int, int] = (BC_WALL, BC_WALL, BC_WALL, BC_WALL)
+    xlower: float = 0.0
+    xupper: float = 1.0
+    ylower: float = 0.0
+    yupper: float = 1.0
+    g: float = 9.81
+    drytol: float = 1e-3
+    manning_n: float = 0.0
+    cfl_desired: float = 0.9
+    cfl_max: float = 1.0
+    dt_initial: float = 1e-2
+    dt_max: float = math.inf
+    tag_depth: float = 1e-3
+    tag_speed: float = 0.01
+    tag_deta: float = 0.05
+    eta0: float = 0.0
+    src_box: Tuple[float, float, float, float] = (0.0, -1.0, 0.0, -1.0)
+    src_level: int = 0
+    regrid_interval: int = 0
+    precision: int = 0  # 0 = FP64, 1 = FP32 surface-deviation form
+
+
+@dataclasses.dataclass
+class Dem:
+    z: np.ndarray  # [ny][nx] nodal elevations
+    x0: float
+    y0: float
+    dx: float
+    dy: float
+
+
+# An initial condition maps cell centres and cell-averaged beds to h, hu, hv.
+InitialCondition = Callable[[np.ndarray, np.ndarray, np.ndarray],
+                            Tuple[np.ndarray, np.ndarray, np.ndarray]]
+
+
+@dataclasses.dataclass
+class Problem:
+    name: str
+    cfg: Config
+    dem: Optional[Dem]
+    ic: InitialCondition
+    t_end: float
+    gauges: Optional[np.ndarray] = None  # [n][2]
+
+
+# --------------------------------------------------------------------------
+# terrain generators
+# --------------------------------------------------------------------------
+
+def flat_dem(cfg: Config, value: float = 0.0) -> Dem:
+    z = np.full((2, 2), value, dtype=np.float64)
+    return Dem(z, cfg.xlower, cfg.ylower, cfg.xupper - cfg.xlower,
+               cfg.yupper - cfg.ylower)
+
+
+def node_grid(cfg: Config, spacing: float):
+    nx = int(round((cfg.xupper - cfg.xlower) / spacing)) + 1
+    ny = int(round((cfg.yupper - cfg.ylower) / spacing)) + 1
+    x = cfg.xlower + spacing * np.arange(nx)
+    y = cfg.ylower + spacing * np.arange(ny)
+    return np.meshgrid(x, y)
+
+
+def gaussian_sum_dem(cfg: Config, n: int, seed: int, spacing: float,
+                     amp=(0.0, 3.0), width=(20.0, 200.0)) -> Dem:
+    """Sum of n Gaussian mounds, amplitudes U[amp], widths U[width], centres
+    uniform over the domain."""
+    rng = np.random.default_rng(seed)
+    A = rng.uniform(amp[0], amp[1], n)
+    W = rng.uniform(width[0], width[1], n)
+    cx = rng.uniform(cfg.xlower, cfg.xupper, n)
+    cy = rng.uniform(cfg.ylower, cfg.yupper, n)
+    X, Y = node_grid(cfg, spacing)
+    z = np.zeros_like(X)
+    for k in range(n):
+        z += A[k] * np.exp(-((X - cx[k]) ** 2 + (Y - cy[k]) ** 2) / (2 * W[k] ** 2))
+    return Dem(z, cfg.xlower, cfg.ylower, spacing, spacing)
+
+
+def value_noise(X: np.ndarray, Y: np.ndarray, seed: int, octaves: int,
+                base_wavelength: float) -> np.ndarray:
+    """Fractal value noise: octaves of bilinearly interpolated seeded lattice
+    values, halving the wavelength and the amplitude each octave; normalised to
+    unit peak amplitude."""
+    rng = np.random.default_rng(seed)
+    out = np.zeros_like(X)
+    amp = 1.0
+    wl = base_wavelength
+    x0, y0 = X.min(), Y.min()
+    for _ in range(octaves):
+        gx = int(math.ceil((X.max() - x0) / wl)) + 2
+        gy = int(math.ceil((Y.max() - y0) / wl)) + 2
+        lat = rng.uniform(-1.0, 1.0, (gy, gx))
+        fx = (X - x0) / wl
+        fy = (Y - y0) / wl
+        i = np.floor(fx).astype(int)
+        j = np.floor(fy).astype(int)
+        ax = fx - i
+        ay = fy - j
+        v = ((1 - ay) * ((1 - ax) * lat[j, i] + ax * lat[j, i + 1]) +
+             ay * ((1 - ax) * lat[j + 1, i] + ax * lat[j + 1, i + 1]))
+        out += amp * v
+        amp *= 0.5
+        wl *= 0.5
+    peak = np.abs(out).max()
+    return out / peak if peak > 0 else out
+
+
+# --------------------------------------------------------------------------
+# workloads
+# --------------------------------------------------------------------------
+
+def stoker(nx: int = 128, patch: Optional[int] = None) -> Problem:
+    """1D-in-2D wet-wet dam break on a flat bed (Stoker closed form):
+    128x128 at dx = 5 m, h = 2 m for x < 320 m and 0.5 m elsewhere, walls,
+    CFL 0.9, t = 20 s, n = 0.  With patch=None one patch spans the grid."""
+    dx = 640.0 / nx
+    m = patch or nx
+    cfg = Config(mi=nx // m, mj=nx // m, mx=m, xupper=640.0, yupper=640.0,
+                 drytol=1e-3, manning_n=0.0, dt_initial=0.5 * dx / 5.0)
+
+    def ic(x, y, b):
+        h = np.where(x < 320.0, 2.0, 0.5)
+        return h, np.zeros_like(h), np.zeros_like(h)
+
+    return Problem("stoker", cfg, flat_dem(cfg), ic, 20.0)
+
+
+def lake_at_rest(nx: int = 128, patch: Optional[int] = None, eta: float = 1.0,
+                 amp: float = 0.5, sigma: float = 50.0) -> Problem:
+    """Still water at surface eta over a Gaussian bump of amplitude amp and
+    width sigma centred in the 640 m square; eta = 0.3 emerges the bump."""
+    m = patch or nx
+    cfg = Config(mi=nx // m, mj=nx // m, mx=m, xupper=640.0, yupper=640.0,
+                 drytol=1e-3, manning_n=0.0, dt_initial=0.5)
+    X, Y = node_grid(cfg, 640.0 / nx / 2)
+    z = amp * np.exp(-((X - 320.0) ** 2 + (Y - 320.0) ** 2) / (2 * sigma ** 2))
+    dem = Dem(z, 0.0, 0.0, 640.0 / nx / 2, 640.0 / nx / 2)
+
+    def ic(x, y, b):
+        h = np.maximum(eta - b, 0.0)
+        return h, np.zeros_like(h), np.zeros_like(h)
+
+    return Problem("lake_at_rest", cfg, dem, ic, 0.0)
+
+
+def radial_dambreak(n: int = 1024, patch: int = 32, dx: float = 2.0,
+                    radius: float = 200.0, depth: float = 5.0,
+                    flat: bool = False, seed: int = SEED_BASE + 1,
+                    manning_n: float = 0.033, drytol: float = 1e-3) -> Problem:
+    """Radial dam break onto a dry bed over seeded smooth terrain: n x n cells
+    of dx metres in patch x patch patches, 40 Gaussians (amplitudes U[0,3] m,
+    widths U[20,200] m), cylinder of the given radius at the given depth,
+    drytol 1e-3 m, Manning 0.033, t = 60 s."""
+    L = n * dx
+    cfg = Config(mi=n // patch, mj=n // patch, mx=patch, xupper=L, yupper=L,
+                 drytol=drytol, manning_n=manning_n, dt_initial=0.1,
+                 tag_depth=drytol)
+    dem = flat_dem(cfg) if flat else gaussian_sum_dem(cfg, 40, seed, dx)
+    c = 0.5 * L
+
+    def ic(x, y, b):
+        r2 = (x - c) ** 2 + (y - c) ** 2
+        h = np.where(r2 < radius * radius, depth, 0.0)
+        return h, np.zeros_like(h), np.zeros_like(h)
+
+    return Problem("radial_dambreak", cfg, dem, ic, 60.0)
+
+
+def v_valley(mi: int = 16, mj: int = 8, patch: int = 32, minlevel: int = 2,
+             maxlevel: int = 4, seed: int = SEED_BASE + 2,
+             dem_spacing: float = 2.0, depth: float = 20.0,
+             breach_x: float = 500.0, manning_n: float = 0.033,
+             n_gauges: int = 16, Lx: float = 4000.0, Ly: float = 2000.0
+             ) -> Problem:
+    """Synthetic V-valley (4 km x 2 km): side slope 0.05, down-valley slope
+    0.005, seeded fractal noise of 0.5 m amplitude; reservoir upstream of
+    x = breach_x filled to `depth` above the thalweg at the breach, dry
+    downstream, instantaneous full breach; n = 0.033; 16 seeded gauges along
+    the thalweg and banks; regrid every 4 steps."""
+    cfg = Config(mi=mi, mj=mj, mx=patch, minlevel=minlevel, maxlevel=maxlevel,
+                 xupper=Lx, yupper=Ly, drytol=1e-4, manning_n=manning_n,
+                 dt_initial=0.05, tag_depth=1e-4, tag_speed=0.01,
+                 tag_deta=0.05, regrid_interval=4,
+                 src_box=(0.0, breach_x, 0.0, Ly), src_level=maxlevel)
+    X, Y = node_grid(cfg, dem_spacing)
+    noise = value_noise(X, Y, seed, 6, 800.0)
+    z = 0.05 * np.abs(Y - 0.5 * Ly) + 0.005 * (Lx - X) + 0.5 * noise
+    dem = Dem(z, 0.0, 0.0, dem_spacing, dem_spacing)
+    surface = 0.005 * (Lx - breach_x) + depth
+    cfg.eta0 = surface
+
+    def ic(x, y, b):
+        h = np.where(x < breach_x, np.maximum(surface - b, 0.0), 0.0)
+        return h, np.zeros_like(h), np.zeros_like(h)
+
+    rng = np.random.default_rng(seed + 1000)
+    gx = rng.uniform(breach_x + 100.0, Lx - 100.0, n_gauges)
+    off = rng.choice([-1.0, 0.0, 1.0], n_gauges) * rng.uniform(0.0, 150.0, n_gauges)
+    gauges = np.stack([gx, 0.5 * Ly + off], axis=1)
+    return Problem("v_valley", cfg, dem, ic, 600.0, gauges)
+
+
+def cell_centres(cfg: Config, levels: Sequence[int], pxs: Sequence[int],
+                 pys: Sequence[int]):
+    """Cell centres [npatch][mx][mx] of a patch list (row index j, column i)."""
+    m = cfg.mx
+    xs = np.empty((len(levels), m, m))
+    ys = np.empty((len(levels), m, m))
+    idx = np.arange(m)
+    for k, (L, px, py) in enumerate(zip(levels, pxs, pys)):
+        dx = (cfg.xupper - cfg.xlower) / (cfg.mi * m * (1 << L))
+        dy = (cfg.yupper - cfg.ylower) / (cfg.mj * m * (1 << L))
+        xc = cfg.xlower + (px * m + idx + 0.5) * dx
+        yc = cfg.ylower + (py * m + idx + 0.5) * dy
+        xs[k] = xc[None, :]
+        ys[k] = yc[:, None]
+    return xs, ys
