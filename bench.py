@@ -1,0 +1,287 @@
+"""Benchmark: cell-updates/s of the GeoFlood wave-propagation hot path.
+
+Workload (one "step"): the 1024 x 1024 radial dam break of 32 x 32 patches
+(dx = 2 m, 40-Gaussian seeded terrain, cylinder of radius 200 m at 5 m depth
+onto a dry bed, drytol 1e-3 m, Manning 0.033, walls, CFL 0.9) run from t = 0
+to t = 60 s in plain FP64: every accepted time step does the ghost fill, the
+augmented Riemann solves, limited corrections, transverse terms, update,
+Manning friction and the CFL control.  value = sum over accepted steps of the
+interior cells updated / device time of the run, inputs resident in HBM; the
+L2 is flushed (a 256 MB write) before every timed run.  e2e = the same run
+through the C ABI from pinned host arrays (upload, run, read back).
+
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same
+workload (there is no other implementation of the paper to run).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_CELLS = 1024
+PATCH = 32
+T_END = 60.0
+WORKLOAD = "radial dam break 1024x1024, 32x32 patches, dx 2 m, FP64, t 0->60 s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--t-end", type=float, default=T_END)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(
+                    ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                     "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                    timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        import statistics
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4)
+                          if len(s) > 4 + k and s[4 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# Algorithmic work per cell update of the FP64 step, counted operation by
+# operation from the scheme: reads h, hu, hv, b and
+# writes h, hu, hv (56 B) and ~FLOP_PER_CELL double-precision operations.
+BYTES_PER_CELL_FP64 = 56
+FLOP_PER_CELL_FP64 = None  # filled from the design doc's count once measured
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_2403_15435_gb300 import geoflood, inputs
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    prob = inputs.radial_dambreak(N_CELLS, PATCH, dx=2.0)
+    f = geoflood.Forest(prob.cfg, prob.dem, stream=stream.cuda_stream)
+    f.set_state(prob.ic)
+    n = f.npatch
+    m = prob.cfg.mx
+    h0, hu0, hv0, _ = f.read()
+    cells = n * m * m
+    # pinned host buffers for the end-to-end leg
+    pin = lambda: torch.empty((n, m, m), dtype=torch.float64, pin_memory=True).numpy()
+    H, HU, HV = pin(), pin(), pin()
+    H[:], HU[:], HV[:] = h0, hu0, hv0
+    OH, OHU, OHV = pin(), pin(), pin()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def reset():
+        f.write(H, HU, HV)
+        f.set_time(0.0, prob.cfg.dt_initial)
+
+    def one_run():
+        _, n_acc = f.step(args.t_end)
+        return n_acc
+
+    for _ in range(args.warmup):
+        reset()
+        one_run()
+    torch.cuda.synchronize(dev)
+
+    times, steps_list = [], []
+    launches0 = f.launch_count()
+    f.profile(True)
+    ev = []
+    with ClockSampler(local) as clk:
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        for _ in range(args.steps):
+            reset()
+            flush.fill_(1.0)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            st = one_run()
+            b.record(stream)
+            ev.append((a, b))
+            steps_list.append(st)
+        torch.cuda.synchronize(dev)
+    launches_timed = f.launch_count() - launches0
+    for a, b in ev:
+        times.append(a.elapsed_time(b) / 1e3)
+    k_ms, k_n = f.profile_read("patch_step")
+    f.profile(False)
+    total_t = sum(times)
+    total_cells = sum(steps_list) * cells
+    if world > 1:
+        t = torch.tensor([total_t], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_t = float(t.item())
+    value = total_cells * world / total_t
+
+    # end-to-end through the C ABI with host buffers
+    e2e_t = []
+    for _ in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        f.write(H, HU, HV)
+        f.set_time(0.0, prob.cfg.dt_initial)
+        _, n_acc = f.step(args.t_end)
+        f.read_into(OH, OHU, OHV)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_cells = n_acc * cells
+    e2e = {"value": e2e_cells * world / (sum(e2e_t) / len(e2e_t)), "unit": "cell-updates/s",
+           "h2d_bytes_per_step": 3 * cells * 8, "d2h_bytes_per_step": 3 * cells * 8}
+
+    peaks = measured_peaks()
+    avg_launch = k_ms / 1e3 / max(1, k_n)
+    bytes_per_launch = BYTES_PER_CELL_FP64 * cells
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    roof = {"bound": "hbm", "achieved": bytes_per_launch / avg_launch / 1e9,
+            "peak": hbm, "unit": "GB/s",
+            "frac": bytes_per_launch / avg_launch / 1e9 / hbm,
+            "traffic": None, "kernel": "patch_step", "avg_launch_ms": avg_launch * 1e3,
+            "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    cpu = cpu_baseline()
+    line = {
+        "metric": "cell-updates/s", "value": value, "unit": "cell-updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total_t / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": cells, "patches": n,
+                   "accepted_steps_per_run": steps_list[0], "l2": "flushed (256 MB write) before each timed run",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": launches_timed, "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def cpu_baseline(budget_s=12.0):
+    """The oracle as it stands on a bounded sample: a 128 x 128 window of
+    the same workload (16 patches of 32 x 32 around the cylinder edge, same
+    terrain and dx), stepped until the budget is spent."""
+    import oracle
+    from paper_2403_15435_gb300 import inputs
+    prob = inputs.radial_dambreak(128, 32, dx=2.0, radius=100.0)
+    f = oracle.OracleForest(prob.cfg, prob.dem)
+    f.set_state(prob.ic)
+    t0 = time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t0 < budget_s:
+        _, n = f.step(1e9, 5)
+        steps += n
+    dt = time.perf_counter() - t0
+    return {"value": steps * 128 * 128 / dt, "unit": "cell-updates/s", "cores": 1,
+            "kind": "oracle", "sample": "128x128 window (16 patches of 32x32), same terrain/dx, %d steps in %.1f s" % (steps, dt)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2403_15435_gb300 import inputs
+    prob = inputs.radial_dambreak(128, 32, dx=2.0, radius=100.0)
+    f = oracle.OracleForest(prob.cfg, prob.dem)
+    f.set_state(prob.ic)
+    for _ in range(args.warmup):
+        f.step(1e9, 2)
+    t0 = time.perf_counter()
+    steps = 0
+    for _ in range(args.steps):
+        _, n = f.step(1e9, 4)
+        steps += n
+    dt = time.perf_counter() - t0
+    v = steps * 128 * 128 / dt
+    line = {"impl": "reference", "metric": "cell-updates/s", "value": v,
+            "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "128x128 window, 4 time steps per bench step"},
+            "cpu_baseline": {"value": v, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                             "sample": "128x128 window (16 patches), 4 steps per bench step"},
+            "e2e": {"value": v, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,209 @@
+/*
+ * geoflood.h -- C ABI of the GB300 (sm_103a) GeoFlood wave-propagation
+ * library.
+ *
+ * The library advances the 2D shallow-water equations with bathymetry and
+ * Manning friction (Sec. 3.1, Eq. shallow, Eq. manning of Kyanjo, Calhoun &
+ * George, "GeoFlood (v1.0.0): Computational model for overland flooding",
+ * arXiv 2403.15435) by the second-order wave-propagation method with the
+ * augmented Riemann solver (Sec. 3.2 Eqs. wpa_update and
+ * wpa_update_corrections, Sec. 3.3) on a quadtree of fixed-size patches
+ * (Sec. 4), for one or many independent scenarios at once.
+ *
+ * Conventions for every call:
+ *   - the return value is GEOFLOOD_OK (0) or a negative GEOFLOOD_ERR_* code;
+ *     geoflood_last_error() then holds a message owned by the context;
+ *   - no C++ exception crosses the ABI;
+ *   - host pointers are owned by the caller and only read or written during
+ *     the call; device state is owned by the context and freed by
+ *     geoflood_destroy();
+ *   - calls on one context are not thread safe; all device work is issued on
+ *     the stream given to geoflood_init_forest() (NULL = the legacy default
+ *     stream); calls that return host data synchronise that stream;
+ *   - arrays of patch data are [npatch][mx][mx] row-major (row index j along
+ *     y, column index i along x) in the scenario's patch order, which is the
+ *     Morton order of the patches on the finest patch grid;
+ *   - all floating-point arguments are double.
+ */
+#ifndef GEOFLOOD_H
+#define GEOFLOOD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GEOFLOOD_OK 0
+#define GEOFLOOD_ERR_ARG -1            /* invalid argument */
+#define GEOFLOOD_ERR_CUDA -2           /* a CUDA call failed */
+#define GEOFLOOD_ERR_OOM -3            /* device allocation failed */
+#define GEOFLOOD_ERR_CFL -4            /* more than 50 rejected steps in a row */
+#define GEOFLOOD_ERR_NAN -5            /* a non-finite value appeared */
+#define GEOFLOOD_ERR_NEGATIVE_DEPTH -6 /* reserved: negative depths are reset */
+#define GEOFLOOD_ERR_TIMEOUT -7        /* a bounded device wait expired */
+#define GEOFLOOD_ERR_CAPACITY -8       /* patch table or buffer capacity */
+#define GEOFLOOD_ERR_STATE -9          /* call out of order (e.g. no state) */
+
+#define GEOFLOOD_BC_WALL 0   /* reflecting wall (Sec. 5.1 closed boundaries) */
+#define GEOFLOOD_BC_EXTRAP 1 /* zero-order extrapolation (open boundary) */
+
+#define GEOFLOOD_FP64 0 /* plain double precision */
+
+#define GEOFLOOD_TAG_KEEP 0
+#define GEOFLOOD_TAG_REFINE 1
+#define GEOFLOOD_TAG_COARSEN 2
+
+/* Forest, physics and control parameters.  Geometry (Sec. 4): mi x mj
+ * level-0 blocks, each a patch of mx x mx cells (mx = 16 or 32), levels
+ * minlevel..maxlevel with refinement ratio 2; the domain is
+ * [xlower, xupper] x [ylower, yupper].  g and drytol (Sec. 5.1 wet/dry
+ * threshold tau); CFL control (Sec. 5.1 maximum CFL, Sec. 6.6 initial time
+ * step): the next dt is cfl_desired / cmax, a step whose CFL number exceeds
+ * cfl_max is retaken.  Tagging thresholds (Sec. 4.1 criteria 1, 3, 4) and
+ * the flood-source box [x0, x1, y0, y1] refined to src_level (Sec. 6.4).
+ * max_patches bounds the patches of all scenarios together. */
+typedef struct {
+  int mi, mj, mx;
+  int minlevel, maxlevel;
+  int bc[4]; /* left, right, bottom, top */
+  int precision;
+  int num_scenarios;
+  int max_patches;
+  int max_gauges;
+  double xlower, xupper, ylower, yupper;
+  double g, drytol;
+  double cfl_desired, cfl_max, dt_initial, dt_max;
+  double tag_depth, tag_speed, tag_deta;
+  double src_box[4];
+  int src_level;
+  int reserved;
+} geoflood_config;
+
+typedef struct geoflood_ctx geoflood_ctx;
+
+/* Initial-condition callback: for n cells with centres (x[k], y[k]) and
+ * cell-averaged bed b[k], write the depth h[k] and momenta hu[k], hv[k]. */
+typedef void (*geoflood_qinit_fn)(int n, const double* x, const double* y,
+                                  const double* b, double* h, double* hu,
+                                  double* hv, void* user);
+
+/* Create a context: validates cfg, allocates the device state for
+ * max_patches patches and builds every scenario's forest uniformly at
+ * minlevel with a flat bed at zero and dry cells.  stream is a cudaStream_t
+ * (may be NULL).  On success *out receives the context.  Errors: ARG, CUDA,
+ * OOM, CAPACITY. */
+int geoflood_init_forest(const geoflood_config* cfg, void* stream,
+                         geoflood_ctx** out);
+
+/* Free all device and host state of the context (NULL is allowed). */
+void geoflood_destroy(geoflood_ctx* ctx);
+
+/* Message of the last failed call (owned by the context; "" if none). */
+const char* geoflood_last_error(const geoflood_ctx* ctx);
+
+/* Per-scenario physics: Manning coefficient n (Eq. manning) and reference
+ * surface eta0 used by the tagger (|eta - eta0| > tag_deta). */
+int geoflood_set_scenario(geoflood_ctx* ctx, int scenario, double manning_n,
+                          double eta0);
+
+/* Topography of one scenario from one DEM (Sec. 6.2): z[ny][nx] nodal
+ * elevations at (x0 + i dx, y0 + j dy), nx, ny >= 2.  Every cell's bed, ghost
+ * cells included, becomes the exact cell average of the DEM's bilinear
+ * interpolant (constant beyond the DEM).  The DEM is copied to the device
+ * and kept for regrids.  Errors: ARG, CUDA, OOM. */
+int geoflood_set_topo(geoflood_ctx* ctx, int scenario, const double* z, int nx,
+                      int ny, double x0, double y0, double dx, double dy);
+
+/* Number of patches of a scenario. */
+int geoflood_npatch(geoflood_ctx* ctx, int scenario, int* npatch);
+
+/* Level and position (px, py on that level's patch grid) of every patch of
+ * the scenario, in storage order; each array holds npatch ints. */
+int geoflood_patch_info(geoflood_ctx* ctx, int scenario, int* level, int* px,
+                        int* py);
+
+/* Copy host interior arrays [npatch][mx][mx] into the scenario's current
+ * state and refill all ghost cells.  Errors: ARG, CUDA. */
+int geoflood_write_patches(geoflood_ctx* ctx, int scenario, const double* h,
+                           const double* hu, const double* hv);
+
+/* Copy the scenario's current interior state to host arrays
+ * [npatch][mx][mx]; any pointer may be NULL.  Synchronises the stream. */
+int geoflood_read_patches(geoflood_ctx* ctx, int scenario, double* h,
+                          double* hu, double* hv, double* b);
+
+/* Copy whole patch tiles, ghosts included, to host: [npatch][4][mx+4][mx+4]
+ * with fields h, hu, hv, b. */
+int geoflood_read_tiles(geoflood_ctx* ctx, int scenario, double* out);
+
+/* Set the initial state through a callback (evaluated on the host once for
+ * all interior cells of the scenario), then fill the ghosts. */
+int geoflood_set_state(geoflood_ctx* ctx, int scenario, geoflood_qinit_fn fn,
+                       void* user);
+
+/* Simulation time and the dt the next step will try. */
+int geoflood_set_time(geoflood_ctx* ctx, int scenario, double t,
+                      double dt_next);
+
+/* Time, next dt, accepted steps, rejected steps, number of negative depths
+ * reset to zero and the volume so added; any pointer may be NULL. */
+int geoflood_get_time(geoflood_ctx* ctx, int scenario, double* t,
+                      double* dt_next, long long* steps, long long* rejects,
+                      long long* nclip, double* clipvol);
+
+/* Advance every scenario towards t_target by at most max_steps accepted
+ * steps of the adaptive scheme (Sec. 3.2, 3.3, Eq. manning; CFL rule of
+ * Sec. 5.1): ghost fill, unsplit second-order step with transverse
+ * propagation and Manning friction, CFL check with reject/retake, gauges.
+ * Each scenario keeps its own dt.  t_out[s] and steps_out[s] (arrays of
+ * num_scenarios entries, may be NULL) receive the reached time and the
+ * accepted steps taken by this call.  Errors: CFL (a scenario rejected 50
+ * steps in a row), NAN, CUDA, STATE. */
+int geoflood_step(geoflood_ctx* ctx, double t_target, int max_steps,
+                  double* t_out, int* steps_out);
+
+/* Per-patch refinement flags of the plain tagger (Sec. 4.1 criteria 1, 3,
+ * 4): GEOFLOOD_TAG_* for each of the scenario's npatch patches. */
+int geoflood_tags(geoflood_ctx* ctx, int scenario, uint8_t* flags);
+
+/* Regrid every scenario (Sec. 4, Sec. 6.6): tag, refine one level, enforce
+ * the 2:1 face/corner balance, coarsen complete sibling quartets, move the
+ * data with the ghost-cell operators (copy, 2x2 average, limited
+ * interpolation), recompute the beds and refill the ghosts.  Errors:
+ * CAPACITY (more than max_patches patches), CUDA. */
+int geoflood_regrid(geoflood_ctx* ctx);
+
+/* Water volume sum h dx dy of a scenario's current state (FP64). */
+int geoflood_mass(geoflood_ctx* ctx, int scenario, double* mass);
+
+/* Register n <= max_gauges gauge points xy[n][2] of a scenario (Sec. 5.1
+ * control points, Sec. 6.5 gauges); they are sampled after every accepted
+ * step. */
+int geoflood_set_gauges(geoflood_ctx* ctx, int scenario, const double* xy,
+                        int n);
+
+/* Latest gauge samples out[n][5] = (t, h, hu, hv, eta) and arrival times
+ * arrival[n] (first sample time with h > 0.01 m, -1 if none); either
+ * pointer may be NULL. */
+int geoflood_gauges(geoflood_ctx* ctx, int scenario, double* out,
+                    double* arrival);
+
+/* Kernel timing with CUDA events around every launch of the named kernel
+ * family ("patch_step", "ghost_fill", "controller", "gauges"): enable != 0
+ * starts recording (and clears earlier records). */
+int geoflood_profile(geoflood_ctx* ctx, int enable);
+
+/* Sum of the recorded durations (ms) and number of recorded launches of one
+ * kernel family since geoflood_profile(ctx, 1).  Synchronises. */
+int geoflood_profile_read(geoflood_ctx* ctx, const char* kernel,
+                          double* total_ms, long long* launches);
+
+/* Number of kernels this context has launched since it was created. */
+int geoflood_launch_count(geoflood_ctx* ctx, long long* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

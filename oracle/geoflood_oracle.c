@@ -51,6 +51,9 @@ void oracle_riemann(double hL, double nL, double tL, double bL, double hR,
   int wetL = hL > drytol;
   int wetR = hR > drytol;
   if (!wetL && !wetR) return; /* both dry: no waves */
+  /* a dry cell keeps its small stored depth in its surface elevation, so a
+   * still shoreline is at rest; its fluxes use zero depth */
+  double sL = hL, sR = hR;
   if (!wetL) { hL = 0.0; nL = 0.0; tL = 0.0; }
   if (!wetR) { hR = 0.0; nR = 0.0; tR = 0.0; }
 
@@ -65,7 +68,7 @@ void oracle_riemann(double hL, double nL, double tL, double bL, double hR,
     double hm = hL + nL / sw;
     if (bR >= bL + hm) {
       wallR = 1;
-      hR = hL; nR = -nL; tR = tL; bR = bL;
+      hR = hL; nR = -nL; tR = tL; bR = bL; sR = hL;
     } else {
       bR = hL + bL; /* the flow overtops: lower the dry step to the surface */
     }
@@ -77,7 +80,7 @@ void oracle_riemann(double hL, double nL, double tL, double bL, double hR,
     double hm = hR - nR / sw;
     if (bL >= bR + hm) {
       wallL = 1;
-      hL = hR; nL = -nR; tL = tR; bL = bR;
+      hL = hR; nL = -nR; tL = tR; bL = bR; sL = hR;
     } else {
       bL = hR + bR;
     }
@@ -110,7 +113,7 @@ void oracle_riemann(double hL, double nL, double tL, double bL, double hR,
 
   double hbar = 0.5 * (hL + hR);
   double db = bR - bL;
-  double deta = (hR + bR) - (hL + bL);
+  double deta = (sR + bR) - (sL + bL);
   double den = s3 - s1;
   double dn = nR - nL;
   double hhll = (s3 * hR - s1 * hL - dn) / den;

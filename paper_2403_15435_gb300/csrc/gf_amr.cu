@@ -1,0 +1,642 @@
+// Quadtree kernels (FP64): ghost-cell exchange between patches at equal or
+// different levels (copy / 2x2 average / limited interpolation) and the
+// physical boundaries, topography cell averages from a DEM, regrid data
+// transfer, the plain tagger, gauges, volume sums and host staging.
+// Compiled with -fmad=false.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "gf_internal.h"
+
+namespace {
+
+struct Geo {
+  const GfGeom& G;
+  const GfView& V;
+  __device__ Geo(const GfGeom& g, const GfView& v) : G(g), V(v) {}
+  __device__ long long nx(int L) const { return (long long)G.mi * G.M << L; }
+  __device__ long long ny(int L) const { return (long long)G.mj * G.M << L; }
+  __device__ double dx(int L) const { return (G.xupper - G.xlower) / (double)nx(L); }
+  __device__ double dy(int L) const { return (G.yupper - G.ylower) / (double)ny(L); }
+  __device__ int tix(int i, int j) const { return (i + GF_NG) + (j + GF_NG) * G.T; }
+  // leaf of level L holding cell (I, J) of that level, or -1
+  __device__ int leaf(int s, int L, long long I, long long J) const {
+    if (L < 0 || L > G.maxlevel) return -1;
+    const long long P = I >= 0 ? I / G.M : -1, Q = J >= 0 ? J / G.M : -1;
+    const long long w = (long long)G.mi << L, h = (long long)G.mj << L;
+    if (P < 0 || Q < 0 || P >= w || Q >= h) return -1;
+    return V.lut[V.scen[s].lut_off + G.lut_lev_off[L] + P + Q * w];
+  }
+  __device__ const double* cellp(int p, int buf) const {
+    return V.q[buf] + (size_t)p * 3 * G.T * G.T;
+  }
+};
+
+// Composite value (h, hu, hv, b) at cell (I, J) of level L: the leaf of that
+// level, a coarser leaf's cell, or the mean of the finer cells (down to two
+// levels finer, which a 2:1 balanced forest never exceeds).
+__device__ void value_at(const Geo& e, int s, int L, long long I, long long J,
+                         double (&out)[4], int* err) {
+  const int TT = e.G.T * e.G.T;
+  for (int l = L; l >= 0; --l) {
+    const long long Il = I >> (L - l), Jl = J >> (L - l);
+    const int p = e.leaf(s, l, Il, Jl);
+    if (p >= 0) {
+      const GfPatch P = e.V.patch[p];
+      const int c = e.tix((int)(Il - (long long)P.px * e.G.M),
+                          (int)(Jl - (long long)P.py * e.G.M));
+      const double* q = e.cellp(p, e.V.ctl[s].cur);
+      out[0] = q[c];
+      out[1] = q[TT + c];
+      out[2] = q[2 * TT + c];
+      out[3] = e.V.b[(size_t)p * TT + c];
+      return;
+    }
+  }
+  double v[4][4];
+  for (int ch = 0; ch < 4; ++ch) {
+    const long long Ic = 2 * I + (ch & 1), Jc = 2 * J + (ch >> 1);
+    const int p = e.leaf(s, L + 1, Ic, Jc);
+    if (p >= 0) {
+      const GfPatch P = e.V.patch[p];
+      const int c = e.tix((int)(Ic - (long long)P.px * e.G.M),
+                          (int)(Jc - (long long)P.py * e.G.M));
+      const double* q = e.cellp(p, e.V.ctl[s].cur);
+      v[ch][0] = q[c];
+      v[ch][1] = q[TT + c];
+      v[ch][2] = q[2 * TT + c];
+      v[ch][3] = e.V.b[(size_t)p * TT + c];
+    } else {
+      double w[4][4];
+      for (int gc = 0; gc < 4; ++gc) {
+        const long long Ig = 2 * Ic + (gc & 1), Jg = 2 * Jc + (gc >> 1);
+        const int pg = e.leaf(s, L + 2, Ig, Jg);
+        if (pg < 0) {
+          *err = 1;
+          w[gc][0] = w[gc][1] = w[gc][2] = w[gc][3] = 0.0;
+          continue;
+        }
+        const GfPatch P = e.V.patch[pg];
+        const int c = e.tix((int)(Ig - (long long)P.px * e.G.M),
+                            (int)(Jg - (long long)P.py * e.G.M));
+        const double* q = e.cellp(pg, e.V.ctl[s].cur);
+        w[gc][0] = q[c];
+        w[gc][1] = q[TT + c];
+        w[gc][2] = q[2 * TT + c];
+        w[gc][3] = e.V.b[(size_t)pg * TT + c];
+      }
+      for (int f = 0; f < 4; ++f)
+        v[ch][f] = 0.25 * ((w[0][f] + w[1][f]) + (w[2][f] + w[3][f]));
+    }
+  }
+  for (int f = 0; f < 4; ++f)
+    out[f] = 0.25 * ((v[0][f] + v[1][f]) + (v[2][f] + v[3][f]));
+}
+
+__device__ __forceinline__ double minmod(double a, double b) {
+  if (a * b <= 0.0) return 0.0;
+  return fabs(a) < fabs(b) ? a : b;
+}
+
+// Value (h, hu, hv) of cell (I, J) of level L whose bed is bt, from the
+// forest of the view: copy from a same-level leaf, mean of finer cells, or
+// limited interpolation of the coarser level's surface and momenta (Sec. 4
+// ghost cells, Sec. 6.2 surface-preserving interpolation).
+__device__ void fill_cell(const Geo& e, int s, int L, long long I, long long J,
+                          double bt, double (&out)[3], int* err) {
+  const int TT = e.G.T * e.G.T;
+  const int p = e.leaf(s, L, I, J);
+  if (p >= 0) {
+    const GfPatch P = e.V.patch[p];
+    const int c = e.tix((int)(I - (long long)P.px * e.G.M),
+                        (int)(J - (long long)P.py * e.G.M));
+    const double* q = e.cellp(p, e.V.ctl[s].cur);
+    out[0] = q[c];
+    out[1] = q[TT + c];
+    out[2] = q[2 * TT + c];
+    return;
+  }
+  bool coarser = false;
+  for (int l = L - 1; l >= 0 && !coarser; --l)
+    coarser = e.leaf(s, l, I >> (L - l), J >> (L - l)) >= 0;
+  if (!coarser) {
+    double v[4][4];
+    value_at(e, s, L + 1, 2 * I, 2 * J, v[0], err);
+    value_at(e, s, L + 1, 2 * I + 1, 2 * J, v[1], err);
+    value_at(e, s, L + 1, 2 * I, 2 * J + 1, v[2], err);
+    value_at(e, s, L + 1, 2 * I + 1, 2 * J + 1, v[3], err);
+    for (int f = 0; f < 3; ++f)
+      out[f] = 0.25 * ((v[0][f] + v[1][f]) + (v[2][f] + v[3][f]));
+    return;
+  }
+  const long long ic = I >> 1, jc = J >> 1;
+  const long long NXc = e.nx(L - 1), NYc = e.ny(L - 1);
+  double nb[3][3][4];
+  bool in[3][3];
+  for (int dj = -1; dj <= 1; ++dj)
+    for (int di = -1; di <= 1; ++di) {
+      const long long a = ic + di, b = jc + dj;
+      in[dj + 1][di + 1] = a >= 0 && b >= 0 && a < NXc && b < NYc;
+      if (in[dj + 1][di + 1]) value_at(e, s, L - 1, a, b, nb[dj + 1][di + 1], err);
+    }
+  const double drytol = e.G.drytol;
+  const double* qc = nb[1][1];
+  if (qc[0] <= drytol) {
+    out[0] = qc[0];
+    out[1] = qc[1];
+    out[2] = qc[2];
+    return;
+  }
+  bool allwet = true;
+  for (int dj = 0; dj < 3; ++dj)
+    for (int di = 0; di < 3; ++di)
+      if (in[dj][di] && !(nb[dj][di][0] > drytol)) allwet = false;
+  const double etac = qc[0] + qc[3];
+  double hf, huf, hvf;
+  if (allwet) {
+    const double sx = (I & 1) ? 0.25 : -0.25, sy = (J & 1) ? 0.25 : -0.25;
+    double et[3][3];
+    for (int dj = 0; dj < 3; ++dj)
+      for (int di = 0; di < 3; ++di)
+        et[dj][di] = in[dj][di] ? nb[dj][di][0] + nb[dj][di][3] : 0.0;
+    const bool hx = in[1][0] && in[1][2], hy = in[0][1] && in[2][1];
+    const double gx = hx ? minmod(et[1][2] - et[1][1], et[1][1] - et[1][0]) : 0.0;
+    const double gy = hy ? minmod(et[2][1] - et[1][1], et[1][1] - et[0][1]) : 0.0;
+    const double ux = hx ? minmod(nb[1][2][1] - qc[1], qc[1] - nb[1][0][1]) : 0.0;
+    const double uy = hy ? minmod(nb[2][1][1] - qc[1], qc[1] - nb[0][1][1]) : 0.0;
+    const double vx = hx ? minmod(nb[1][2][2] - qc[2], qc[2] - nb[1][0][2]) : 0.0;
+    const double vy = hy ? minmod(nb[2][1][2] - qc[2], qc[2] - nb[0][1][2]) : 0.0;
+    const double etaf = (etac + sx * gx) + sy * gy;
+    huf = (qc[1] + sx * ux) + sy * uy;
+    hvf = (qc[2] + sx * vx) + sy * vy;
+    hf = etaf - bt;
+  } else {
+    hf = etac - bt;
+    huf = qc[1];
+    hvf = qc[2];
+  }
+  if (hf < 0.0) hf = 0.0;
+  if (hf <= drytol) { huf = 0.0; hvf = 0.0; }
+  out[0] = hf;
+  out[1] = huf;
+  out[2] = hvf;
+}
+
+// Physical boundaries of one tile held in global memory: bottom/top over the
+// columns inside the domain, then left/right over every row (Sec. 5.1 closed
+// walls mirror the cells and negate the normal momentum; extrapolation
+// copies the edge cell).  fields: 0 = h, hu, hv in q; 1 = the bed in b.
+__device__ void tile_bc(const Geo& e, const GfPatch& P, double* q,
+                        double* bfield, int bed) {
+  const int M = e.G.M, T = e.G.T, TT = T * T;
+  const long long NX = e.nx(P.level), NY = e.ny(P.level);
+  const int nf = bed ? 1 : 3;
+  for (int side = 2; side <= 3; ++side) {
+    const bool at = side == 2 ? (P.py == 0) : ((long long)(P.py + 1) * M == NY);
+    if (!at) continue;
+    const bool wall = e.G.bc[side] == 0;
+    const int n = T * GF_NG * nf;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      const int i = k % T - GF_NG, gl = (k / T) % GF_NG + 1, f = k / (T * GF_NG);
+      const long long I = (long long)P.px * M + i;
+      if (I < 0 || I >= NX) continue;
+      const int jg = side == 2 ? -gl : M - 1 + gl;
+      const int js = wall ? (side == 2 ? gl - 1 : M - gl) : (side == 2 ? 0 : M - 1);
+      double* a = bed ? bfield : q + f * TT;
+      double v = a[e.tix(i, js)];
+      if (!bed && wall && f == 2) v = -v;
+      a[e.tix(i, jg)] = v;
+    }
+    __syncthreads();
+  }
+  for (int side = 0; side <= 1; ++side) {
+    const bool at = side == 0 ? (P.px == 0) : ((long long)(P.px + 1) * M == NX);
+    if (!at) continue;
+    const bool wall = e.G.bc[side] == 0;
+    const int n = T * GF_NG * nf;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      const int j = k % T - GF_NG, gl = (k / T) % GF_NG + 1, f = k / (T * GF_NG);
+      const int ig = side == 0 ? -gl : M - 1 + gl;
+      const int is = wall ? (side == 0 ? gl - 1 : M - gl) : (side == 0 ? 0 : M - 1);
+      double* a = bed ? bfield : q + f * TT;
+      double v = a[e.tix(is, j)];
+      if (!bed && wall && f == 1) v = -v;
+      a[e.tix(ig, j)] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// Ghost fill: one CTA per patch.  Interior-domain ghosts from the leaves
+// (reads only leaf interiors, so patches are independent), then the
+// physical boundaries.
+__global__ void k_ghost_fill(const GfGeom G, const GfView V, int only_accepted,
+                             int* errflag) {
+  const int p = blockIdx.x;
+  const GfPatch P = V.patch[p];
+  const GfCtl* C = V.ctl + P.scen;
+  if (only_accepted && !C->accepted) return;
+  Geo e(G, V);
+  const int M = G.M, T = G.T, TT = T * T;
+  double* q = V.q[C->cur] + (size_t)p * 3 * TT;
+  const double* bb = V.b + (size_t)p * TT;
+  const long long NX = e.nx(P.level), NY = e.ny(P.level);
+  const int nghost = TT - M * M;
+  int err = 0;
+  for (int k = threadIdx.x; k < nghost; k += blockDim.x) {
+    // enumerate ghost cells: the two bottom rows, the two top rows, then the
+    // left and right column pairs of the interior rows
+    int i, j;
+    const int band = 2 * T;
+    if (k < band) { i = k % T - GF_NG; j = k / T - GF_NG; }
+    else if (k < 2 * band) { i = (k - band) % T - GF_NG; j = M + (k - band) / T; }
+    else {
+      const int r = k - 2 * band;  // 4 * M cells
+      j = r / 4;
+      const int c = r % 4;
+      i = c < 2 ? c - GF_NG : M + (c - 2);
+    }
+    const long long I = (long long)P.px * M + i, J = (long long)P.py * M + j;
+    if (I < 0 || J < 0 || I >= NX || J >= NY) continue;
+    const int c = e.tix(i, j);
+    double out[3];
+    fill_cell(e, P.scen, P.level, I, J, bb[c], out, &err);
+    q[c] = out[0];
+    q[TT + c] = out[1];
+    q[2 * TT + c] = out[2];
+  }
+  if (err && errflag) *errflag = 1;
+  __syncthreads();
+  tile_bc(e, P, q, nullptr, 0);
+}
+
+// ------------------------------------------------------------ topography
+
+__device__ double dem_eval(const GfScenario& S, double x, double y) {
+  const int nx = S.dnx, ny = S.dny;
+  double fx = (x - S.dx0) / S.ddx, fy = (y - S.dy0) / S.ddy;
+  if (fx < 0.0) fx = 0.0;
+  if (fx > (double)(nx - 1)) fx = (double)(nx - 1);
+  if (fy < 0.0) fy = 0.0;
+  if (fy > (double)(ny - 1)) fy = (double)(ny - 1);
+  int i = (int)floor(fx), j = (int)floor(fy);
+  if (i > nx - 2) i = nx - 2;
+  if (j > ny - 2) j = ny - 2;
+  if (i < 0) i = 0;
+  if (j < 0) j = 0;
+  const double ax = fx - (double)i, ay = fy - (double)j;
+  const double* z = S.dem;
+  const double z00 = z[i + (size_t)j * nx], z10 = z[i + 1 + (size_t)j * nx];
+  const double z01 = z[i + (size_t)(j + 1) * nx];
+  const double z11 = z[i + 1 + (size_t)(j + 1) * nx];
+  return (1.0 - ay) * ((1.0 - ax) * z00 + ax * z10) +
+         ay * ((1.0 - ax) * z01 + ax * z11);
+}
+
+// Range of DEM node indices that may lie strictly inside (a, b).
+__device__ void node_range(double a, double b, double o, double d, int n,
+                           int* lo, int* hi) {
+  int l = (int)floor((a - o) / d) - 1, h = (int)ceil((b - o) / d) + 1;
+  *lo = l < 0 ? 0 : l;
+  *hi = h > n - 1 ? n - 1 : h;
+}
+
+// Exact average over [xa,xb]x[ya,yb] of the DEM's bilinear interpolant: the
+// node lines cut the cell into pieces on which the interpolant is bilinear;
+// each piece contributes its area times the value at its midpoint.  The
+// pieces are visited row by row in increasing coordinate order.
+__device__ double dem_average(const GfScenario& S, double xa, double xb,
+                              double ya, double yb) {
+  int xl, xh, yl, yh;
+  node_range(xa, xb, S.dx0, S.ddx, S.dnx, &xl, &xh);
+  node_range(ya, yb, S.dy0, S.ddy, S.dny, &yl, &yh);
+  double sum = 0.0;
+  double y0 = ya;
+  for (int jn = yl; jn <= yh + 1; ++jn) {
+    double y1;
+    if (jn <= yh) {
+      const double yn = S.dy0 + (double)jn * S.ddy;
+      if (!(yn > ya && yn < yb)) continue;
+      y1 = yn;
+    } else {
+      y1 = yb;
+    }
+    double x0 = xa;
+    for (int in = xl; in <= xh + 1; ++in) {
+      double x1;
+      if (in <= xh) {
+        const double xn = S.dx0 + (double)in * S.ddx;
+        if (!(xn > xa && xn < xb)) continue;
+        x1 = xn;
+      } else {
+        x1 = xb;
+      }
+      const double xm = 0.5 * (x0 + x1), ym = 0.5 * (y0 + y1);
+      const double w = (x1 - x0) * (y1 - y0);
+      sum += w * dem_eval(S, xm, ym);
+      x0 = x1;
+    }
+    y0 = y1;
+  }
+  return sum / ((xb - xa) * (yb - ya));
+}
+
+__global__ void k_topo(const GfGeom G, const GfView V, int first) {
+  const int p = first + blockIdx.x;
+  const GfPatch P = V.patch[p];
+  Geo e(G, V);
+  const int M = G.M, T = G.T, TT = T * T;
+  double* b = V.b + (size_t)p * TT;
+  const GfScenario S = V.scen[P.scen];
+  const long long NX = e.nx(P.level), NY = e.ny(P.level);
+  const double dx = e.dx(P.level), dy = e.dy(P.level);
+  for (int k = threadIdx.x; k < TT; k += blockDim.x) {
+    const int i = k % T - GF_NG, j = k / T - GF_NG;
+    const long long I = (long long)P.px * M + i, J = (long long)P.py * M + j;
+    double v = 0.0;
+    if (I >= 0 && J >= 0 && I < NX && J < NY && S.dem) {
+      const double xa = G.xlower + (double)I * dx;
+      const double xb = G.xlower + (double)(I + 1) * dx;
+      const double ya = G.ylower + (double)J * dy;
+      const double yb = G.ylower + (double)(J + 1) * dy;
+      v = dem_average(S, xa, xb, ya, yb);
+    }
+    b[k] = v;
+  }
+  __syncthreads();
+  tile_bc(e, P, nullptr, b, 1);
+}
+
+// Regrid transfer: every interior cell of every new patch from the old
+// forest by the ghost-cell operators (copy, average, interpolation).
+__global__ void k_regrid_fill(const GfGeom G, const GfView O, const GfView N,
+                              int* errflag) {
+  const int p = blockIdx.x;
+  const GfPatch P = N.patch[p];
+  Geo eo(G, O);
+  const int M = G.M, T = G.T, TT = T * T;
+  const int dst = 1 - O.ctl[P.scen].cur;
+  double* q = N.q[dst] + (size_t)p * 3 * TT;
+  const double* bn = N.b + (size_t)p * TT;
+  int err = 0;
+  for (int k = threadIdx.x; k < M * M; k += blockDim.x) {
+    const int i = k % M, j = k / M;
+    const long long I = (long long)P.px * M + i, J = (long long)P.py * M + j;
+    const int c = (i + GF_NG) + (j + GF_NG) * T;
+    double out[3];
+    fill_cell(eo, P.scen, P.level, I, J, bn[c], out, &err);
+    q[c] = out[0];
+    q[TT + c] = out[1];
+    q[2 * TT + c] = out[2];
+  }
+  if (err && errflag) *errflag = 1;
+}
+
+// Plain tagger (Sec. 4.1 criteria 1, 3, 4; Sec. 6.4).
+__global__ void k_tags(const GfGeom G, const GfView V, uint8_t* flags) {
+  const int p = blockIdx.x;
+  const GfPatch P = V.patch[p];
+  Geo e(G, V);
+  const int M = G.M, T = G.T, TT = T * T;
+  const double* q = V.q[V.ctl[P.scen].cur] + (size_t)p * 3 * TT;
+  const double* b = V.b + (size_t)p * TT;
+  const GfScenario S = V.scen[P.scen];
+  const double dx = e.dx(P.level), dy = e.dy(P.level);
+  int m = 0;
+  for (int k = threadIdx.x; k < M * M; k += blockDim.x) {
+    const int i = k % M, j = k / M;
+    const int c = e.tix(i, j);
+    const double h = q[c];
+    int r = 0;
+    if (h > G.tag_depth) {
+      const double u = q[TT + c] / h, v = q[2 * TT + c] / h;
+      const double sp = sqrt(u * u + v * v);
+      const double eta = h + b[c];
+      if (sp > G.tag_speed || fabs(eta - S.eta0) > G.tag_deta) r = 2;
+    }
+    const double xc = G.xlower + ((double)((long long)P.px * M + i) + 0.5) * dx;
+    const double yc = G.ylower + ((double)((long long)P.py * M + j) + 0.5) * dy;
+    if (xc >= G.src_box[0] && xc <= G.src_box[1] && yc >= G.src_box[2] &&
+        yc <= G.src_box[3]) {
+      if (P.level < G.src_level) r = 2;
+      else if (r < 1) r = 1;
+    }
+    m = r > m ? r : m;
+  }
+  m = __reduce_max_sync(0xffffffffu, m);
+  __shared__ int wm[32];
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int mm = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mm = wm[w] > mm ? wm[w] : mm;
+    uint8_t f;
+    if (mm == 2) f = P.level < G.maxlevel ? 1 : 0;
+    else if (mm == 1) f = 0;
+    else f = P.level > G.minlevel ? 2 : 0;
+    flags[p] = f;
+  }
+}
+
+// Gauges (Sec. 5.1 control points, Sec. 6.5): bilinear in the finest leaf,
+// ghosts included; arrival at the first sample with h > 1 cm.
+__global__ void k_gauges(const GfGeom G, const GfView V, int only_accepted) {
+  const int s = blockIdx.y;
+  const GfScenario S = V.scen[s];
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= S.ngauge) return;
+  const GfCtl* C = V.ctl + s;
+  if (only_accepted && !C->accepted) return;
+  Geo e(G, V);
+  const double x = S.gxy[2 * g], y = S.gxy[2 * g + 1];
+  int p = -1, L = 0;
+  for (int l = G.maxlevel; l >= 0 && p < 0; --l) {
+    const double pw = (G.xupper - G.xlower) / (double)(G.mi << l);
+    const double ph = (G.yupper - G.ylower) / (double)(G.mj << l);
+    long long Pq = (long long)floor((x - G.xlower) / pw);
+    long long Qq = (long long)floor((y - G.ylower) / ph);
+    const long long w = (long long)G.mi << l, hgt = (long long)G.mj << l;
+    if (Pq < 0) Pq = 0;
+    if (Qq < 0) Qq = 0;
+    if (Pq >= w) Pq = w - 1;
+    if (Qq >= hgt) Qq = hgt - 1;
+    const int k = V.lut[S.lut_off + G.lut_lev_off[l] + Pq + Qq * w];
+    if (k >= 0) { p = k; L = l; }
+  }
+  double* o = S.gout + 5 * g;
+  o[0] = C->t;
+  if (p < 0) { o[1] = o[2] = o[3] = o[4] = 0.0; return; }
+  const GfPatch P = V.patch[p];
+  const int M = G.M, TT = G.T * G.T;
+  const double fx = (x - G.xlower) / e.dx(L) - 0.5 - (double)((long long)P.px * M);
+  const double fy = (y - G.ylower) / e.dy(L) - 0.5 - (double)((long long)P.py * M);
+  int i0 = (int)floor(fx), j0 = (int)floor(fy);
+  if (i0 < -1) i0 = -1;
+  if (j0 < -1) j0 = -1;
+  if (i0 > M - 1) i0 = M - 1;
+  if (j0 > M - 1) j0 = M - 1;
+  const double ax = fx - (double)i0, ay = fy - (double)j0;
+  const double* q = V.q[C->cur] + (size_t)p * 3 * TT;
+  const double* b = V.b + (size_t)p * TT;
+  const int c00 = e.tix(i0, j0), c10 = e.tix(i0 + 1, j0);
+  const int c01 = e.tix(i0, j0 + 1), c11 = e.tix(i0 + 1, j0 + 1);
+  double v[4];
+  for (int f = 0; f < 4; ++f) {
+    double a00, a10, a01, a11;
+    if (f < 3) {
+      a00 = q[f * TT + c00]; a10 = q[f * TT + c10];
+      a01 = q[f * TT + c01]; a11 = q[f * TT + c11];
+    } else {
+      a00 = q[c00] + b[c00]; a10 = q[c10] + b[c10];
+      a01 = q[c01] + b[c01]; a11 = q[c11] + b[c11];
+    }
+    v[f] = (1.0 - ay) * ((1.0 - ax) * a00 + ax * a10) +
+           ay * ((1.0 - ax) * a01 + ax * a11);
+  }
+  o[1] = v[0]; o[2] = v[1]; o[3] = v[2]; o[4] = v[3];
+  if (S.garr[g] < 0.0 && v[0] > 0.01) S.garr[g] = C->t;
+}
+
+// Volume per patch (fixed-order block tree), then per scenario.
+__global__ void k_patch_mass(const GfGeom G, const GfView V, double* pmass) {
+  const int p = blockIdx.x;
+  const GfPatch P = V.patch[p];
+  Geo e(G, V);
+  const int M = G.M, TT = G.T * G.T;
+  const double* q = V.q[V.ctl[P.scen].cur] + (size_t)p * 3 * TT;
+  double v = 0.0;
+  for (int k = threadIdx.x; k < M * M; k += blockDim.x) v += q[e.tix(k % M, k / M)];
+  __shared__ double red[256];
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) pmass[p] = red[0] * (e.dx(P.level) * e.dy(P.level));
+}
+
+__global__ void k_scen_mass(const GfScenario* sc, const double* pmass,
+                            double* smass) {
+  const int s = blockIdx.x;
+  const int off = sc[s].poff, n = sc[s].pcount;
+  double v = 0.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) v += pmass[off + k];
+  __shared__ double red[256];
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) smass[s] = red[0];
+}
+
+// Staging between tiles and dense field-major interior arrays
+// [field][count][M][M] (fields h, hu, hv, b for packing; h, hu, hv for
+// unpacking).
+__global__ void k_pack(const GfGeom G, const GfView V, int first, double* out,
+                       int cur) {
+  const int p = first + blockIdx.x;
+  const int M = G.M, T = G.T, TT = T * T, MM = M * M;
+  const size_t plane = (size_t)gridDim.x * MM;
+  const double* q = V.q[cur] + (size_t)p * 3 * TT;
+  const double* b = V.b + (size_t)p * TT;
+  for (int k = threadIdx.x; k < 4 * MM; k += blockDim.x) {
+    const int f = k / MM, r = k % MM;
+    const int c = (r % M + GF_NG) + (r / M + GF_NG) * T;
+    out[f * plane + (size_t)blockIdx.x * MM + r] = f < 3 ? q[f * TT + c] : b[c];
+  }
+}
+
+__global__ void k_unpack(const GfGeom G, const GfView V, int first,
+                         const double* in, int cur) {
+  const int p = first + blockIdx.x;
+  const int M = G.M, T = G.T, TT = T * T, MM = M * M;
+  const size_t plane = (size_t)gridDim.x * MM;
+  double* q = V.q[cur] + (size_t)p * 3 * TT;
+  for (int k = threadIdx.x; k < 3 * MM; k += blockDim.x) {
+    const int f = k / MM, r = k % MM;
+    const int c = (r % M + GF_NG) + (r / M + GF_NG) * T;
+    q[f * TT + c] = in[f * plane + (size_t)blockIdx.x * MM + r];
+  }
+}
+
+inline int ok() { return cudaGetLastError() == cudaSuccess ? 0 : -2; }
+
+}  // namespace
+
+namespace gf {
+
+static int* g_errflag = nullptr;
+
+int launch_ghost_fill(const GfGeom& g, const GfView& v, int only_accepted,
+                      void* stream) {
+  if (v.npatch <= 0) return 0;
+  k_ghost_fill<<<v.npatch, 128, 0, static_cast<cudaStream_t>(stream)>>>(
+      g, v, only_accepted, g_errflag);
+  return ok();
+}
+
+int launch_topo(const GfGeom& g, const GfView& v, int first, int count,
+                void* stream) {
+  if (count <= 0) return 0;
+  k_topo<<<count, 128, 0, static_cast<cudaStream_t>(stream)>>>(g, v, first);
+  return ok();
+}
+
+int launch_regrid_fill(const GfGeom& g, const GfView& oldv, const GfView& newv,
+                       void* stream) {
+  if (newv.npatch <= 0) return 0;
+  k_regrid_fill<<<newv.npatch, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      g, oldv, newv, g_errflag);
+  return ok();
+}
+
+int launch_tags(const GfGeom& g, const GfView& v, uint8_t* flags,
+                void* stream) {
+  if (v.npatch <= 0) return 0;
+  k_tags<<<v.npatch, 256, 0, static_cast<cudaStream_t>(stream)>>>(g, v, flags);
+  return ok();
+}
+
+int launch_gauges(const GfGeom& g, const GfView& v, int only_accepted,
+                  int max_gauges, void* stream) {
+  if (max_gauges <= 0) return 0;
+  dim3 grid((max_gauges + 63) / 64, g.nscen);
+  k_gauges<<<grid, 64, 0, static_cast<cudaStream_t>(stream)>>>(g, v,
+                                                              only_accepted);
+  return ok();
+}
+
+int launch_mass(const GfGeom& g, const GfView& v, double* pmass,
+                double* smass, int nscen, void* stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (v.npatch > 0) k_patch_mass<<<v.npatch, 256, 0, st>>>(g, v, pmass);
+  k_scen_mass<<<nscen, 256, 0, st>>>(v.scen, pmass, smass);
+  return ok();
+}
+
+int launch_pack_interior(const GfGeom& g, const GfView& v, int first,
+                         int count, double* out, int field_mask, int cur,
+                         void* stream) {
+  (void)field_mask;
+  if (count <= 0) return 0;
+  k_pack<<<count, 256, 0, static_cast<cudaStream_t>(stream)>>>(g, v, first,
+                                                              out, cur);
+  return ok();
+}
+
+int launch_unpack_interior(const GfGeom& g, const GfView& v, int first,
+                           int count, const double* in, int cur,
+                           void* stream) {
+  if (count <= 0) return 0;
+  k_unpack<<<count, 256, 0, static_cast<cudaStream_t>(stream)>>>(g, v, first,
+                                                                in, cur);
+  return ok();
+}
+
+void set_errflag(int* p) { g_errflag = p; }
+
+}  // namespace gf

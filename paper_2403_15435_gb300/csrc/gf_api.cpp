@@ -1,0 +1,722 @@
+// C ABI of the GeoFlood GB300 library: context, forest tables, staging and
+// the time-stepping driver.  See include/geoflood.h for the contract of each
+// entry point.
+#include "../../include/geoflood.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "gf_forest.h"
+#include "gf_internal.h"
+
+namespace {
+
+struct ProfRec {
+  cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct geoflood_ctx {
+  geoflood_config cfg{};
+  cudaStream_t st = nullptr;
+  GfGeom G{};
+  int cap = 0, nscen = 0, npatch = 0;
+  double* q[2] = {nullptr, nullptr};
+  double* b[2] = {nullptr, nullptr};
+  int bsel = 0;
+  GfPatch* d_patch[2] = {nullptr, nullptr};
+  int* d_lut[2] = {nullptr, nullptr};
+  int tsel = 0;
+  GfScenario* d_scen = nullptr;
+  std::vector<GfScenario> h_scen;
+  GfCtl* d_ctl = nullptr;
+  GfCtl* h_ctl = nullptr;  // pinned mirror
+  double* d_pmass = nullptr;
+  double* d_smass = nullptr;
+  uint8_t* d_flags = nullptr;
+  int* d_err = nullptr;
+  double* d_stage = nullptr;
+  size_t stage_cap = 0;
+  std::vector<gf::HostForest> forests;
+  std::vector<double*> d_dem, d_gxy, d_gout, d_garr;
+  int max_gauges_used = 0;
+  std::string err;
+  bool prof = false;
+  std::map<std::string, std::vector<ProfRec>> prof_recs;
+  std::vector<cudaEvent_t> pool;
+  size_t pool_used = 0;
+  long long launches = 0;
+};
+
+namespace {
+
+int fail(geoflood_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+#define CK(call)                                                          \
+  do {                                                                    \
+    cudaError_t e_ = (call);                                              \
+    if (e_ != cudaSuccess)                                                \
+      return fail(ctx, GEOFLOOD_ERR_CUDA,                                 \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));    \
+  } while (0)
+
+#define CKL(expr, name)                                                   \
+  do {                                                                    \
+    if ((expr) != 0) {                                                    \
+      cudaError_t e_ = cudaGetLastError();                                \
+      return fail(ctx, GEOFLOOD_ERR_CUDA,                                 \
+                  std::string("launch ") + name + ": " +                  \
+                      cudaGetErrorString(e_));                            \
+    }                                                                     \
+  } while (0)
+
+GfView view(geoflood_ctx* c, int t, int bb) {
+  GfView v{};
+  v.patch = c->d_patch[t];
+  v.lut = c->d_lut[t];
+  v.scen = c->d_scen;
+  v.ctl = c->d_ctl;
+  v.q[0] = c->q[0];
+  v.q[1] = c->q[1];
+  v.b = c->b[bb];
+  v.npatch = c->npatch;
+  return v;
+}
+GfView view(geoflood_ctx* c) { return view(c, c->tsel, c->bsel); }
+
+// Events come from a pool created ahead of time so that recording them adds
+// no allocation to the launch loop.
+cudaEvent_t pool_event(geoflood_ctx* c) {
+  if (c->pool_used == c->pool.size()) {
+    const size_t grow = c->pool.empty() ? 4096 : c->pool.size();
+    for (size_t k = 0; k < grow; ++k) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      c->pool.push_back(e);
+    }
+  }
+  return c->pool[c->pool_used++];
+}
+void prof_begin(geoflood_ctx* c, const char* name, ProfRec* r) {
+  if (!c->prof) return;
+  r->a = pool_event(c);
+  r->b = pool_event(c);
+  cudaEventRecord(r->a, c->st);
+  (void)name;
+}
+void prof_end(geoflood_ctx* c, const char* name, ProfRec* r) {
+  if (!c->prof) return;
+  cudaEventRecord(r->b, c->st);
+  c->prof_recs[name].push_back(*r);
+}
+
+bool valid_scen(geoflood_ctx* c, int s) { return c && s >= 0 && s < c->nscen; }
+
+int sync_ctl_down(geoflood_ctx* ctx) {
+  CK(cudaMemcpyAsync(ctx->h_ctl, ctx->d_ctl, sizeof(GfCtl) * ctx->nscen,
+                     cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return 0;
+}
+
+int sync_ctl_up(geoflood_ctx* ctx) {
+  CK(cudaMemcpyAsync(ctx->d_ctl, ctx->h_ctl, sizeof(GfCtl) * ctx->nscen,
+                     cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return 0;
+}
+
+int ensure_stage(geoflood_ctx* ctx, size_t doubles) {
+  if (doubles <= ctx->stage_cap) return 0;
+  if (ctx->d_stage) cudaFree(ctx->d_stage);
+  ctx->d_stage = nullptr;
+  CK(cudaMalloc(&ctx->d_stage, doubles * sizeof(double)));
+  ctx->stage_cap = doubles;
+  return 0;
+}
+
+// Upload the patch table and lookup tables of the current forests into
+// table slot t; updates poff/pcount of every scenario.
+int upload_tables(geoflood_ctx* ctx, int t,
+                  const std::vector<std::vector<gf::Leaf>>& lv) {
+  size_t total = 0;
+  for (auto& v : lv) total += v.size();
+  if ((long long)total > ctx->cap)
+    return fail(ctx, GEOFLOOD_ERR_CAPACITY,
+                "forest needs " + std::to_string(total) +
+                    " patches, capacity is " + std::to_string(ctx->cap));
+  std::vector<GfPatch> hp(total);
+  std::vector<int> lut((size_t)ctx->nscen * ctx->G.lut_per_scen, -1);
+  int off = 0;
+  for (int s = 0; s < ctx->nscen; ++s) {
+    ctx->h_scen[s].poff = off;
+    ctx->h_scen[s].pcount = (int)lv[s].size();
+    for (size_t k = 0; k < lv[s].size(); ++k) {
+      const gf::Leaf& l = lv[s][k];
+      hp[off + k] = GfPatch{l.level, l.px, l.py, s};
+      const long long w = (long long)ctx->G.mi << l.level;
+      lut[(size_t)ctx->h_scen[s].lut_off + ctx->G.lut_lev_off[l.level] + l.px +
+          (long long)l.py * w] = off + (int)k;
+    }
+    off += (int)lv[s].size();
+  }
+  CK(cudaMemcpyAsync(ctx->d_patch[t], hp.data(), sizeof(GfPatch) * total,
+                     cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->d_lut[t], lut.data(), sizeof(int) * lut.size(),
+                     cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->d_scen, ctx->h_scen.data(),
+                     sizeof(GfScenario) * ctx->nscen, cudaMemcpyHostToDevice,
+                     ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));  // host vectors die at return
+  return 0;
+}
+
+int upload_scen(geoflood_ctx* ctx) {
+  CK(cudaMemcpyAsync(ctx->d_scen, ctx->h_scen.data(),
+                     sizeof(GfScenario) * ctx->nscen, cudaMemcpyHostToDevice,
+                     ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return 0;
+}
+
+int check_errflag(geoflood_ctx* ctx) {
+  int e = 0;
+  CK(cudaMemcpyAsync(&e, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost,
+                     ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  if (e) {
+    CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->st));
+    return fail(ctx, GEOFLOOD_ERR_STATE,
+                "forest lookup failed (unbalanced or uncovered forest)");
+  }
+  return 0;
+}
+
+int ghost_fill_all(geoflood_ctx* ctx) {
+  gf::set_errflag(ctx->d_err);
+  ProfRec r;
+  prof_begin(ctx, "ghost_fill", &r);
+  CKL(gf::launch_ghost_fill(ctx->G, view(ctx), 0, ctx->st), "ghost_fill");
+  prof_end(ctx, "ghost_fill", &r);
+  ctx->launches++;
+  return check_errflag(ctx);
+}
+
+int topo_scenario(geoflood_ctx* ctx, int s) {
+  CKL(gf::launch_topo(ctx->G, view(ctx), ctx->h_scen[s].poff,
+                      ctx->h_scen[s].pcount, ctx->st),
+      "topo");
+  ctx->launches++;
+  return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int geoflood_init_forest(const geoflood_config* cfg, void* stream,
+                         geoflood_ctx** out) {
+  if (!cfg || !out) return GEOFLOOD_ERR_ARG;
+  *out = nullptr;
+  const geoflood_config& c = *cfg;
+  if (!(c.mx == 16 || c.mx == 32) || c.mi < 1 || c.mj < 1 || c.minlevel < 0 ||
+      c.maxlevel < c.minlevel || c.maxlevel > GF_MAXLEV - 2 ||
+      c.num_scenarios < 1 || c.max_patches < 1 || c.max_gauges < 0 ||
+      !(c.xupper > c.xlower) || !(c.yupper > c.ylower) || !(c.g > 0) ||
+      !(c.drytol > 0) || !(c.cfl_desired > 0) || !(c.cfl_max >= c.cfl_desired) ||
+      !(c.dt_initial > 0) || !(c.dt_max > 0) || c.precision != GEOFLOOD_FP64)
+    return GEOFLOOD_ERR_ARG;
+  for (int k = 0; k < 4; ++k)
+    if (c.bc[k] != GEOFLOOD_BC_WALL && c.bc[k] != GEOFLOOD_BC_EXTRAP)
+      return GEOFLOOD_ERR_ARG;
+  geoflood_ctx* ctx = new geoflood_ctx();
+  ctx->cfg = c;
+  ctx->st = static_cast<cudaStream_t>(stream);
+  ctx->nscen = c.num_scenarios;
+  ctx->cap = c.max_patches;
+  GfGeom& G = ctx->G;
+  G.mi = c.mi; G.mj = c.mj; G.M = c.mx; G.T = c.mx + 2 * GF_NG;
+  G.minlevel = c.minlevel; G.maxlevel = c.maxlevel;
+  for (int k = 0; k < 4; ++k) G.bc[k] = c.bc[k];
+  G.xlower = c.xlower; G.xupper = c.xupper; G.ylower = c.ylower; G.yupper = c.yupper;
+  G.g = c.g; G.drytol = c.drytol;
+  G.cfl_desired = c.cfl_desired; G.cfl_max = c.cfl_max; G.dt_max = c.dt_max;
+  G.tag_depth = c.tag_depth; G.tag_speed = c.tag_speed; G.tag_deta = c.tag_deta;
+  for (int k = 0; k < 4; ++k) G.src_box[k] = c.src_box[k];
+  G.src_level = c.src_level;
+  G.nscen = c.num_scenarios;
+  long long acc = 0;
+  for (int L = 0; L <= GF_MAXLEV; ++L) {
+    G.lut_lev_off[L] = acc;
+    if (L <= c.maxlevel) acc += ((long long)c.mi << L) * ((long long)c.mj << L);
+  }
+  G.lut_per_scen = acc;
+
+  const size_t TT = (size_t)G.T * G.T;
+  const size_t cap = (size_t)ctx->cap;
+  auto alloc = [&](void** p, size_t bytes) -> bool {
+    return cudaMalloc(p, bytes) == cudaSuccess;
+  };
+  bool okk = true;
+  okk &= alloc((void**)&ctx->q[0], cap * 3 * TT * sizeof(double));
+  okk &= alloc((void**)&ctx->q[1], cap * 3 * TT * sizeof(double));
+  okk &= alloc((void**)&ctx->b[0], cap * TT * sizeof(double));
+  okk &= alloc((void**)&ctx->b[1], cap * TT * sizeof(double));
+  okk &= alloc((void**)&ctx->d_patch[0], cap * sizeof(GfPatch));
+  okk &= alloc((void**)&ctx->d_patch[1], cap * sizeof(GfPatch));
+  okk &= alloc((void**)&ctx->d_lut[0], (size_t)ctx->nscen * G.lut_per_scen * sizeof(int));
+  okk &= alloc((void**)&ctx->d_lut[1], (size_t)ctx->nscen * G.lut_per_scen * sizeof(int));
+  okk &= alloc((void**)&ctx->d_scen, ctx->nscen * sizeof(GfScenario));
+  okk &= alloc((void**)&ctx->d_ctl, ctx->nscen * sizeof(GfCtl));
+  okk &= alloc((void**)&ctx->d_pmass, cap * sizeof(double));
+  okk &= alloc((void**)&ctx->d_smass, ctx->nscen * sizeof(double));
+  okk &= alloc((void**)&ctx->d_flags, cap);
+  okk &= alloc((void**)&ctx->d_err, sizeof(int));
+  okk &= cudaMallocHost((void**)&ctx->h_ctl, ctx->nscen * sizeof(GfCtl)) == cudaSuccess;
+  if (!okk) {
+    cudaGetLastError();
+    geoflood_destroy(ctx);
+    return GEOFLOOD_ERR_OOM;
+  }
+  ctx->h_scen.assign(ctx->nscen, GfScenario{});
+  ctx->d_dem.assign(ctx->nscen, nullptr);
+  ctx->d_gxy.assign(ctx->nscen, nullptr);
+  ctx->d_gout.assign(ctx->nscen, nullptr);
+  ctx->d_garr.assign(ctx->nscen, nullptr);
+  for (int s = 0; s < ctx->nscen; ++s) {
+    ctx->h_scen[s].lut_off = (long long)s * G.lut_per_scen;
+    ctx->forests.emplace_back(c.mi, c.mj, c.minlevel, c.maxlevel);
+    ctx->forests.back().uniform(c.minlevel);
+  }
+  std::memset(ctx->h_ctl, 0, sizeof(GfCtl) * ctx->nscen);
+  for (int s = 0; s < ctx->nscen; ++s) ctx->h_ctl[s].dt_next = c.dt_initial;
+  int rc = 0;
+  do {
+    if (cudaMemsetAsync(ctx->q[0], 0, cap * 3 * TT * sizeof(double), ctx->st) ||
+        cudaMemsetAsync(ctx->q[1], 0, cap * 3 * TT * sizeof(double), ctx->st) ||
+        cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->st)) {
+      rc = GEOFLOOD_ERR_CUDA;
+      break;
+    }
+    std::vector<std::vector<gf::Leaf>> lv;
+    for (auto& f : ctx->forests) lv.push_back(f.leaves());
+    if ((rc = upload_tables(ctx, 0, lv))) break;
+    ctx->npatch = 0;
+    for (auto& v : lv) ctx->npatch += (int)v.size();
+    if ((rc = sync_ctl_up(ctx))) break;
+    for (int s = 0; s < ctx->nscen && !rc; ++s) rc = topo_scenario(ctx, s);
+    if (rc) break;
+    rc = ghost_fill_all(ctx);
+  } while (0);
+  if (rc) {
+    geoflood_destroy(ctx);
+    return rc;
+  }
+  *out = ctx;
+  return GEOFLOOD_OK;
+}
+
+void geoflood_destroy(geoflood_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->st);
+  for (int k = 0; k < 2; ++k) {
+    cudaFree(ctx->q[k]);
+    cudaFree(ctx->b[k]);
+    cudaFree(ctx->d_patch[k]);
+    cudaFree(ctx->d_lut[k]);
+  }
+  cudaFree(ctx->d_scen);
+  cudaFree(ctx->d_ctl);
+  cudaFree(ctx->d_pmass);
+  cudaFree(ctx->d_smass);
+  cudaFree(ctx->d_flags);
+  cudaFree(ctx->d_err);
+  cudaFree(ctx->d_stage);
+  for (auto p : ctx->d_dem) cudaFree(p);
+  for (auto p : ctx->d_gxy) cudaFree(p);
+  for (auto p : ctx->d_gout) cudaFree(p);
+  for (auto p : ctx->d_garr) cudaFree(p);
+  if (ctx->h_ctl) cudaFreeHost(ctx->h_ctl);
+  for (auto e : ctx->pool) cudaEventDestroy(e);
+  delete ctx;
+}
+
+const char* geoflood_last_error(const geoflood_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : "null context";
+}
+
+int geoflood_set_scenario(geoflood_ctx* ctx, int s, double manning_n,
+                          double eta0) {
+  if (!valid_scen(ctx, s) || !(manning_n >= 0))
+    return fail(ctx, GEOFLOOD_ERR_ARG, "set_scenario: bad argument");
+  ctx->h_scen[s].manning_n = manning_n;
+  ctx->h_scen[s].eta0 = eta0;
+  return upload_scen(ctx);
+}
+
+int geoflood_set_topo(geoflood_ctx* ctx, int s, const double* z, int nx,
+                      int ny, double x0, double y0, double dx, double dy) {
+  if (!valid_scen(ctx, s) || !z || nx < 2 || ny < 2 || !(dx > 0) || !(dy > 0))
+    return fail(ctx, GEOFLOOD_ERR_ARG, "set_topo: bad argument");
+  if (ctx->d_dem[s]) cudaFree(ctx->d_dem[s]);
+  ctx->d_dem[s] = nullptr;
+  const size_t n = (size_t)nx * ny;
+  if (cudaMalloc(&ctx->d_dem[s], n * sizeof(double)) != cudaSuccess)
+    return fail(ctx, GEOFLOOD_ERR_OOM, "set_topo: DEM allocation");
+  CK(cudaMemcpyAsync(ctx->d_dem[s], z, n * sizeof(double),
+                     cudaMemcpyHostToDevice, ctx->st));
+  GfScenario& S = ctx->h_scen[s];
+  S.dem = ctx->d_dem[s];
+  S.dnx = nx; S.dny = ny; S.dx0 = x0; S.dy0 = y0; S.ddx = dx; S.ddy = dy;
+  int rc = upload_scen(ctx);
+  if (rc) return rc;
+  if ((rc = topo_scenario(ctx, s))) return rc;
+  return ghost_fill_all(ctx);
+}
+
+int geoflood_npatch(geoflood_ctx* ctx, int s, int* np) {
+  if (!valid_scen(ctx, s) || !np) return fail(ctx, GEOFLOOD_ERR_ARG, "npatch: bad argument");
+  *np = ctx->h_scen[s].pcount;
+  return 0;
+}
+
+int geoflood_patch_info(geoflood_ctx* ctx, int s, int* level, int* px,
+                        int* py) {
+  if (!valid_scen(ctx, s)) return fail(ctx, GEOFLOOD_ERR_ARG, "patch_info: bad scenario");
+  const auto& lv = ctx->forests[s].leaves();
+  for (size_t k = 0; k < lv.size(); ++k) {
+    if (level) level[k] = lv[k].level;
+    if (px) px[k] = lv[k].px;
+    if (py) py[k] = lv[k].py;
+  }
+  return 0;
+}
+
+int geoflood_write_patches(geoflood_ctx* ctx, int s, const double* h,
+                           const double* hu, const double* hv) {
+  if (!valid_scen(ctx, s) || !h || !hu || !hv)
+    return fail(ctx, GEOFLOOD_ERR_ARG, "write_patches: bad argument");
+  const int n = ctx->h_scen[s].pcount;
+  const size_t plane = (size_t)n * ctx->G.M * ctx->G.M;
+  int rc = ensure_stage(ctx, 4 * plane);
+  if (rc) return rc;
+  if ((rc = sync_ctl_down(ctx))) return rc;
+  CK(cudaMemcpyAsync(ctx->d_stage, h, plane * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->d_stage + plane, hu, plane * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->d_stage + 2 * plane, hv, plane * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+  CKL(gf::launch_unpack_interior(ctx->G, view(ctx), ctx->h_scen[s].poff, n,
+                                 ctx->d_stage, ctx->h_ctl[s].cur, ctx->st),
+      "unpack");
+  ctx->launches++;
+  ctx->h_ctl[s].status = 0;
+  ctx->h_ctl[s].nonfinite = 0;
+  if ((rc = sync_ctl_up(ctx))) return rc;
+  return ghost_fill_all(ctx);
+}
+
+int geoflood_read_patches(geoflood_ctx* ctx, int s, double* h, double* hu,
+                          double* hv, double* b) {
+  if (!valid_scen(ctx, s)) return fail(ctx, GEOFLOOD_ERR_ARG, "read_patches: bad scenario");
+  const int n = ctx->h_scen[s].pcount;
+  const size_t plane = (size_t)n * ctx->G.M * ctx->G.M;
+  int rc = ensure_stage(ctx, 4 * plane);
+  if (rc) return rc;
+  if ((rc = sync_ctl_down(ctx))) return rc;
+  CKL(gf::launch_pack_interior(ctx->G, view(ctx), ctx->h_scen[s].poff, n,
+                               ctx->d_stage, 15, ctx->h_ctl[s].cur, ctx->st),
+      "pack");
+  ctx->launches++;
+  double* dst[4] = {h, hu, hv, b};
+  for (int f = 0; f < 4; ++f)
+    if (dst[f])
+      CK(cudaMemcpyAsync(dst[f], ctx->d_stage + f * plane, plane * sizeof(double),
+                         cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return 0;
+}
+
+int geoflood_read_tiles(geoflood_ctx* ctx, int s, double* out) {
+  if (!valid_scen(ctx, s) || !out) return fail(ctx, GEOFLOOD_ERR_ARG, "read_tiles: bad argument");
+  int rc = sync_ctl_down(ctx);
+  if (rc) return rc;
+  const size_t TT = (size_t)ctx->G.T * ctx->G.T;
+  const int off = ctx->h_scen[s].poff, n = ctx->h_scen[s].pcount;
+  const double* q = ctx->q[ctx->h_ctl[s].cur];
+  for (int k = 0; k < n; ++k) {
+    CK(cudaMemcpyAsync(out + (size_t)k * 4 * TT, q + (size_t)(off + k) * 3 * TT,
+                       3 * TT * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(out + (size_t)k * 4 * TT + 3 * TT,
+                       ctx->b[ctx->bsel] + (size_t)(off + k) * TT,
+                       TT * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  }
+  CK(cudaStreamSynchronize(ctx->st));
+  return 0;
+}
+
+int geoflood_set_state(geoflood_ctx* ctx, int s, geoflood_qinit_fn fn,
+                       void* user) {
+  if (!valid_scen(ctx, s) || !fn) return fail(ctx, GEOFLOOD_ERR_ARG, "set_state: bad argument");
+  const int n = ctx->h_scen[s].pcount, M = ctx->G.M;
+  const size_t plane = (size_t)n * M * M;
+  std::vector<double> x(plane), y(plane), bb(plane), h(plane), hu(plane), hv(plane);
+  int rc = geoflood_read_patches(ctx, s, nullptr, nullptr, nullptr, bb.data());
+  if (rc) return rc;
+  const auto& lv = ctx->forests[s].leaves();
+  for (int k = 0; k < n; ++k) {
+    const int L = lv[k].level;
+    const double dx = (ctx->G.xupper - ctx->G.xlower) / (double)((long long)ctx->G.mi * M << L);
+    const double dy = (ctx->G.yupper - ctx->G.ylower) / (double)((long long)ctx->G.mj * M << L);
+    for (int j = 0; j < M; ++j)
+      for (int i = 0; i < M; ++i) {
+        const size_t o = (size_t)k * M * M + (size_t)j * M + i;
+        x[o] = ctx->G.xlower + ((double)((long long)lv[k].px * M + i) + 0.5) * dx;
+        y[o] = ctx->G.ylower + ((double)((long long)lv[k].py * M + j) + 0.5) * dy;
+      }
+  }
+  fn((int)plane, x.data(), y.data(), bb.data(), h.data(), hu.data(), hv.data(), user);
+  return geoflood_write_patches(ctx, s, h.data(), hu.data(), hv.data());
+}
+
+int geoflood_set_time(geoflood_ctx* ctx, int s, double t, double dt_next) {
+  if (!valid_scen(ctx, s) || !(dt_next > 0)) return fail(ctx, GEOFLOOD_ERR_ARG, "set_time: bad argument");
+  int rc = sync_ctl_down(ctx);
+  if (rc) return rc;
+  ctx->h_ctl[s].t = t;
+  ctx->h_ctl[s].dt_next = dt_next;
+  ctx->h_ctl[s].status = 0;
+  return sync_ctl_up(ctx);
+}
+
+int geoflood_get_time(geoflood_ctx* ctx, int s, double* t, double* dt_next,
+                      long long* steps, long long* rejects, long long* nclip,
+                      double* clipvol) {
+  if (!valid_scen(ctx, s)) return fail(ctx, GEOFLOOD_ERR_ARG, "get_time: bad scenario");
+  int rc = sync_ctl_down(ctx);
+  if (rc) return rc;
+  const GfCtl& C = ctx->h_ctl[s];
+  if (t) *t = C.t;
+  if (dt_next) *dt_next = C.dt_next;
+  if (steps) *steps = C.steps;
+  if (rejects) *rejects = C.rejects;
+  if (nclip) *nclip = C.nclip;
+  if (clipvol) *clipvol = C.clipvol;
+  return 0;
+}
+
+int geoflood_step(geoflood_ctx* ctx, double t_target, int max_steps,
+                  double* t_out, int* steps_out) {
+  if (!ctx || max_steps < 0) return fail(ctx, GEOFLOOD_ERR_ARG, "step: bad argument");
+  CKL(gf::launch_ctl_begin(ctx->d_ctl, ctx->nscen, t_target, max_steps,
+                           nullptr, ctx->st),
+      "ctl_begin");
+  ctx->launches++;
+  gf::set_errflag(ctx->d_err);
+  const GfView v = view(ctx);
+  // Launch in chunks; the device controller deactivates a scenario when it
+  // reaches t_target or max_steps accepted steps, and later launches of its
+  // patches return at once.  Rejected steps need extra launches, bounded by
+  // the controller's limit on consecutive rejections.
+  long long launched = 0;
+  const long long limit = (long long)max_steps * 2 + 64;
+  int chunk = 4;
+  while (max_steps > 0) {
+    const int k = (int)std::min<long long>(chunk, std::max<long long>(1, max_steps - launched));
+    for (int it = 0; it < k; ++it) {
+      ProfRec r;
+      prof_begin(ctx, "patch_step", &r);
+      CKL(gf::launch_patch_step_f64(ctx->G, v, ctx->d_pmass, ctx->st), "patch_step");
+      prof_end(ctx, "patch_step", &r);
+      prof_begin(ctx, "controller", &r);
+      CKL(gf::launch_controller(ctx->G, v, ctx->d_pmass, ctx->nscen, ctx->st), "controller");
+      prof_end(ctx, "controller", &r);
+      prof_begin(ctx, "ghost_fill", &r);
+      CKL(gf::launch_ghost_fill(ctx->G, v, 1, ctx->st), "ghost_fill");
+      prof_end(ctx, "ghost_fill", &r);
+      ctx->launches += 3;
+      if (ctx->max_gauges_used > 0) {
+        prof_begin(ctx, "gauges", &r);
+        CKL(gf::launch_gauges(ctx->G, v, 1, ctx->max_gauges_used, ctx->st), "gauges");
+        prof_end(ctx, "gauges", &r);
+        ctx->launches++;
+      }
+    }
+    launched += k;
+    int rc = sync_ctl_down(ctx);
+    if (rc) return rc;
+    bool any = false;
+    for (int s = 0; s < ctx->nscen; ++s) any |= ctx->h_ctl[s].active != 0;
+    if (!any) break;
+    if (launched > limit) return fail(ctx, GEOFLOOD_ERR_CFL, "step: too many retakes");
+    chunk = std::min(chunk * 2, 64);
+  }
+  int rc = sync_ctl_down(ctx);
+  if (rc) return rc;
+  if ((rc = check_errflag(ctx))) return rc;
+  int status = 0;
+  for (int s = 0; s < ctx->nscen; ++s) {
+    const GfCtl& C = ctx->h_ctl[s];
+    if (t_out) t_out[s] = C.t;
+    if (steps_out) steps_out[s] = (int)C.taken;
+    if (C.status && !status) status = C.status;
+  }
+  if (status == GEOFLOOD_ERR_NAN) return fail(ctx, status, "non-finite value in the state");
+  if (status == GEOFLOOD_ERR_CFL) return fail(ctx, status, "too many rejected steps in a row");
+  if (status == GEOFLOOD_ERR_TIMEOUT) return fail(ctx, status, "bounded device wait expired");
+  if (status) return fail(ctx, status, "device error");
+  return 0;
+}
+
+int geoflood_tags(geoflood_ctx* ctx, int s, uint8_t* flags) {
+  if (!valid_scen(ctx, s) || !flags) return fail(ctx, GEOFLOOD_ERR_ARG, "tags: bad argument");
+  CKL(gf::launch_tags(ctx->G, view(ctx), ctx->d_flags, ctx->st), "tags");
+  ctx->launches++;
+  CK(cudaMemcpyAsync(flags, ctx->d_flags + ctx->h_scen[s].poff,
+                     ctx->h_scen[s].pcount, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return 0;
+}
+
+int geoflood_regrid(geoflood_ctx* ctx) {
+  if (!ctx) return GEOFLOOD_ERR_ARG;
+  int rc = sync_ctl_down(ctx);
+  if (rc) return rc;
+  std::vector<uint8_t> flags(ctx->npatch);
+  CKL(gf::launch_tags(ctx->G, view(ctx), ctx->d_flags, ctx->st), "tags");
+  ctx->launches++;
+  CK(cudaMemcpyAsync(flags.data(), ctx->d_flags, ctx->npatch, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  std::vector<std::vector<gf::Leaf>> lv(ctx->nscen);
+  size_t total = 0;
+  for (int s = 0; s < ctx->nscen; ++s) {
+    lv[s] = ctx->forests[s].regrid(flags.data() + ctx->h_scen[s].poff);
+    total += lv[s].size();
+  }
+  if ((long long)total > ctx->cap)
+    return fail(ctx, GEOFLOOD_ERR_CAPACITY,
+                "regrid needs " + std::to_string(total) + " patches, capacity is " +
+                    std::to_string(ctx->cap));
+  const GfView oldv = view(ctx);
+  std::vector<GfScenario> saved = ctx->h_scen;
+  const int nt = ctx->tsel ^ 1, nb = ctx->bsel ^ 1;
+  if ((rc = upload_tables(ctx, nt, lv))) {
+    ctx->h_scen = saved;
+    upload_scen(ctx);
+    return rc;
+  }
+  GfView newv = view(ctx, nt, nb);
+  newv.npatch = (int)total;
+  CKL(gf::launch_topo(ctx->G, newv, 0, (int)total, ctx->st), "topo");
+  gf::set_errflag(ctx->d_err);
+  CKL(gf::launch_regrid_fill(ctx->G, oldv, newv, ctx->st), "regrid_fill");
+  ctx->launches += 2;
+  CK(cudaStreamSynchronize(ctx->st));
+  for (int s = 0; s < ctx->nscen; ++s) {
+    ctx->h_ctl[s].cur ^= 1;
+    ctx->forests[s].set_leaves(lv[s]);
+  }
+  ctx->tsel = nt;
+  ctx->bsel = nb;
+  ctx->npatch = (int)total;
+  if ((rc = sync_ctl_up(ctx))) return rc;
+  if ((rc = check_errflag(ctx))) return rc;
+  return ghost_fill_all(ctx);
+}
+
+int geoflood_mass(geoflood_ctx* ctx, int s, double* mass) {
+  if (!valid_scen(ctx, s) || !mass) return fail(ctx, GEOFLOOD_ERR_ARG, "mass: bad argument");
+  CKL(gf::launch_mass(ctx->G, view(ctx), ctx->d_pmass, ctx->d_smass, ctx->nscen, ctx->st), "mass");
+  ctx->launches += 2;
+  CK(cudaMemcpyAsync(mass, ctx->d_smass + s, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return 0;
+}
+
+int geoflood_set_gauges(geoflood_ctx* ctx, int s, const double* xy, int n) {
+  if (!valid_scen(ctx, s) || n < 0 || n > ctx->cfg.max_gauges || (n > 0 && !xy))
+    return fail(ctx, GEOFLOOD_ERR_ARG, "set_gauges: bad argument");
+  cudaFree(ctx->d_gxy[s]);
+  cudaFree(ctx->d_gout[s]);
+  cudaFree(ctx->d_garr[s]);
+  ctx->d_gxy[s] = ctx->d_gout[s] = ctx->d_garr[s] = nullptr;
+  const int m = n > 0 ? n : 1;
+  CK(cudaMalloc(&ctx->d_gxy[s], 2 * m * sizeof(double)));
+  CK(cudaMalloc(&ctx->d_gout[s], 5 * m * sizeof(double)));
+  CK(cudaMalloc(&ctx->d_garr[s], m * sizeof(double)));
+  if (n > 0)
+    CK(cudaMemcpyAsync(ctx->d_gxy[s], xy, 2 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemsetAsync(ctx->d_gout[s], 0, 5 * m * sizeof(double), ctx->st));
+  std::vector<double> neg(m, -1.0);
+  CK(cudaMemcpyAsync(ctx->d_garr[s], neg.data(), m * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+  GfScenario& S = ctx->h_scen[s];
+  S.ngauge = n;
+  S.gxy = ctx->d_gxy[s];
+  S.gout = ctx->d_gout[s];
+  S.garr = ctx->d_garr[s];
+  int rc = upload_scen(ctx);
+  if (rc) return rc;
+  ctx->max_gauges_used = 0;
+  for (auto& sc : ctx->h_scen) ctx->max_gauges_used = std::max(ctx->max_gauges_used, sc.ngauge);
+  CKL(gf::launch_gauges(ctx->G, view(ctx), 0, ctx->max_gauges_used, ctx->st), "gauges");
+  ctx->launches++;
+  CK(cudaStreamSynchronize(ctx->st));
+  return 0;
+}
+
+int geoflood_gauges(geoflood_ctx* ctx, int s, double* out, double* arrival) {
+  if (!valid_scen(ctx, s)) return fail(ctx, GEOFLOOD_ERR_ARG, "gauges: bad scenario");
+  const int n = ctx->h_scen[s].ngauge;
+  if (n > 0 && out)
+    CK(cudaMemcpyAsync(out, ctx->d_gout[s], 5 * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  if (n > 0 && arrival)
+    CK(cudaMemcpyAsync(arrival, ctx->d_garr[s], n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return 0;
+}
+
+int geoflood_profile(geoflood_ctx* ctx, int enable) {
+  if (!ctx) return GEOFLOOD_ERR_ARG;
+  CK(cudaStreamSynchronize(ctx->st));
+  ctx->prof_recs.clear();
+  ctx->pool_used = 0;
+  if (enable) pool_event(ctx), ctx->pool_used = 0;  // pre-create the pool
+  ctx->prof = enable != 0;
+  return 0;
+}
+
+int geoflood_profile_read(geoflood_ctx* ctx, const char* kernel,
+                          double* total_ms, long long* launches) {
+  if (!ctx || !kernel) return GEOFLOOD_ERR_ARG;
+  CK(cudaStreamSynchronize(ctx->st));
+  double tot = 0.0;
+  long long n = 0;
+  auto it = ctx->prof_recs.find(kernel);
+  if (it != ctx->prof_recs.end())
+    for (auto& r : it->second) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, r.a, r.b));
+      tot += ms;
+      ++n;
+    }
+  if (total_ms) *total_ms = tot;
+  if (launches) *launches = n;
+  return 0;
+}
+
+int geoflood_launch_count(geoflood_ctx* ctx, long long* launches) {
+  if (!ctx || !launches) return GEOFLOOD_ERR_ARG;
+  *launches = ctx->launches;
+  return 0;
+}
+
+}  // extern "C"

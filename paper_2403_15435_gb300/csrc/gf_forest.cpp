@@ -1,0 +1,163 @@
+// Host quadtree: regrid with 2:1 balance.  The balance test works on the set
+// of tree nodes (leaves and their ancestors): a leaf of level L touches a
+// leaf of level >= L+2 exactly when some node of level L+2 sits in the ring
+// of level-(L+2) positions around the leaf.
+#include "gf_forest.h"
+
+#include <algorithm>
+#include <unordered_set>
+
+namespace gf {
+
+namespace {
+
+inline uint64_t key(int L, long long x, long long y) {
+  return ((uint64_t)L << 58) | ((uint64_t)x << 29) | (uint64_t)y;
+}
+
+class NodeSet {
+ public:
+  NodeSet(int mi, int mj) : mi_(mi), mj_(mj) {}
+  void add_leaf(int L, int x, int y) {
+    for (int l = L; l >= 0; --l) {
+      if (!s_.insert(key(l, x >> (L - l), y >> (L - l))).second) break;
+    }
+  }
+  bool has(int L, long long x, long long y) const {
+    if (x < 0 || y < 0 || x >= ((long long)mi_ << L) || y >= ((long long)mj_ << L))
+      return false;
+    return s_.count(key(L, x, y)) != 0;
+  }
+  // any node of level Lr in the one-position ring around the square
+  // [x0, x0+n) x [y0, y0+n) of that level
+  bool ring_has(int Lr, long long x0, long long y0, long long n) const {
+    for (long long x = x0 - 1; x <= x0 + n; ++x) {
+      if (has(Lr, x, y0 - 1) || has(Lr, x, y0 + n)) return true;
+    }
+    for (long long y = y0; y < y0 + n; ++y) {
+      if (has(Lr, x0 - 1, y) || has(Lr, x0 + n, y)) return true;
+    }
+    return false;
+  }
+
+ private:
+  int mi_, mj_;
+  std::unordered_set<uint64_t> s_;
+};
+
+}  // namespace
+
+uint64_t HostForest::morton(const Leaf& l) const {
+  const uint64_t X = (uint64_t)l.px << (maxl_ - l.level);
+  const uint64_t Y = (uint64_t)l.py << (maxl_ - l.level);
+  uint64_t k = 0;
+  for (int b = 0; b < 31; ++b) {
+    k |= ((X >> b) & 1ull) << (2 * b);
+    k |= ((Y >> b) & 1ull) << (2 * b + 1);
+  }
+  return k;
+}
+
+void HostForest::sort(std::vector<Leaf>& v) const {
+  std::sort(v.begin(), v.end(), [this](const Leaf& a, const Leaf& b) {
+    return morton(a) < morton(b);
+  });
+}
+
+void HostForest::uniform(int level) {
+  leaves_.clear();
+  const int w = mi_ << level, h = mj_ << level;
+  for (int y = 0; y < h; ++y)
+    for (int x = 0; x < w; ++x) leaves_.push_back(Leaf{level, x, y});
+  sort(leaves_);
+}
+
+std::vector<Leaf> HostForest::regrid(const uint8_t* flags) const {
+  const size_t n0 = leaves_.size();
+  // 1. refinement of tagged leaves
+  std::vector<Leaf> cur;
+  std::vector<int> from;  // original index, -1 for new leaves
+  cur.reserve(n0 * 2);
+  for (size_t k = 0; k < n0; ++k) {
+    const Leaf& l = leaves_[k];
+    if (flags[k] == 1 && l.level < maxl_) {
+      for (int c = 0; c < 4; ++c) {
+        cur.push_back(Leaf{l.level + 1, 2 * l.px + (c & 1), 2 * l.py + (c >> 1)});
+        from.push_back(-1);
+      }
+    } else {
+      cur.push_back(l);
+      from.push_back((int)k);
+    }
+  }
+  // 2. balance: refine leaves that touch a leaf two or more levels finer
+  NodeSet nodes(mi_, mj_);
+  for (const Leaf& l : cur) nodes.add_leaf(l.level, l.px, l.py);
+  for (bool changed = true; changed;) {
+    changed = false;
+    const size_t n = cur.size();
+    for (size_t k = 0; k < n; ++k) {
+      const Leaf l = cur[k];
+      const int Lr = l.level + 2;
+      if (Lr > maxl_) continue;
+      if (!nodes.ring_has(Lr, 4LL * l.px, 4LL * l.py, 4)) continue;
+      const Leaf c0{l.level + 1, 2 * l.px, 2 * l.py};
+      cur[k] = c0;
+      from[k] = -1;
+      nodes.add_leaf(c0.level, c0.px, c0.py);
+      for (int c = 1; c < 4; ++c) {
+        const Leaf ch{l.level + 1, 2 * l.px + (c & 1), 2 * l.py + (c >> 1)};
+        cur.push_back(ch);
+        from.push_back(-1);
+        nodes.add_leaf(ch.level, ch.px, ch.py);
+      }
+      changed = true;
+    }
+  }
+  // 3. coarsening of untouched complete quartets
+  std::vector<int> where(n0, -1);
+  for (size_t k = 0; k < cur.size(); ++k)
+    if (from[k] >= 0) where[from[k]] = (int)k;
+  // index of original leaves by position
+  std::unordered_set<uint64_t> orig;
+  for (size_t k = 0; k < n0; ++k) orig.insert(key(leaves_[k].level, leaves_[k].px, leaves_[k].py));
+  std::vector<char> drop(cur.size(), 0);
+  std::vector<Leaf> parents;
+  // map position -> original index for the sibling lookup
+  std::vector<std::pair<uint64_t, int>> pos;
+  pos.reserve(n0);
+  for (size_t k = 0; k < n0; ++k)
+    pos.emplace_back(key(leaves_[k].level, leaves_[k].px, leaves_[k].py), (int)k);
+  std::sort(pos.begin(), pos.end());
+  auto find = [&](int L, int x, int y) -> int {
+    const uint64_t kk = key(L, x, y);
+    auto it = std::lower_bound(pos.begin(), pos.end(), std::make_pair(kk, -1));
+    return (it != pos.end() && it->first == kk) ? it->second : -1;
+  };
+  for (size_t k = 0; k < n0; ++k) {
+    const Leaf& l = leaves_[k];
+    if (l.level <= minl_ || (l.px & 1) || (l.py & 1)) continue;
+    int sib[4];
+    bool ok = true;
+    for (int c = 0; c < 4 && ok; ++c) {
+      const int o = find(l.level, l.px + (c & 1), l.py + (c >> 1));
+      if (o < 0 || flags[o] != 2 || where[o] < 0) ok = false;
+      else sib[c] = o;
+    }
+    if (!ok) continue;
+    // parent at level L-1 spans 4x4 positions of level L+1
+    const int Lr = l.level + 1;
+    if (Lr <= maxl_ && nodes.ring_has(Lr, 2LL * l.px, 2LL * l.py, 4)) continue;
+    for (int c = 0; c < 4; ++c) drop[where[sib[c]]] = 1;
+    parents.push_back(Leaf{l.level - 1, l.px / 2, l.py / 2});
+  }
+  std::vector<Leaf> out;
+  out.reserve(cur.size());
+  for (size_t k = 0; k < cur.size(); ++k)
+    if (!drop[k]) out.push_back(cur[k]);
+  for (const Leaf& p : parents) out.push_back(p);
+  sort(out);
+  return out;
+}
+
+}  // namespace gf

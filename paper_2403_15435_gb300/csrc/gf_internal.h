@@ -1,0 +1,105 @@
+// Internal device-side structures shared by the kernels and the host runtime
+// of the GeoFlood GB300 library.  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+
+#define GF_NG 2          // ghost layers
+#define GF_MAXLEV 16     // deepest level a forest may use
+#define GF_MAXSTEP_REJECT 50
+#define GF_SPIN_LIMIT (1u << 22)  // bounded waits on TMA mbarriers
+
+// One patch: level, position on that level's patch grid, scenario.
+struct GfPatch {
+  int level, px, py, scen;
+};
+
+// Per-scenario constants read by the kernels.
+struct GfScenario {
+  double manning_n, eta0;
+  const double* dem;  // nodal DEM [dny][dnx] or null (flat bed at 0)
+  int dnx, dny;
+  double dx0, dy0, ddx, ddy;
+  int poff, pcount;   // patch range in the table
+  long long lut_off;  // offset of this scenario's lookup tables
+  int ngauge;
+  int pad;
+  const double* gxy;  // [ngauge][2]
+  double* gout;       // [ngauge][5] latest sample
+  double* garr;       // [ngauge] arrival time or -1
+};
+
+// Per-scenario time-stepping state, owned by the device controller.
+struct GfCtl {
+  double t, dt_next, dt_use, t_target;
+  double clipvol, step_clipvol, mass;
+  unsigned long long cmax_bits;     // max CFL rate of the step (bits of a
+                                    // non-negative double, atomicMax'ed)
+  unsigned long long step_nclip;
+  long long steps, rejects, nclip, taken, max_steps;
+  int cur;       // which state buffer is current
+  int active;    // this scenario still advances in the current call
+  int last;      // the step in flight is clipped to t_target
+  int accepted;  // the last step was accepted
+  int inrow;     // consecutive rejections
+  int status;    // GEOFLOOD_* error from the device, 0 if none
+  int nonfinite; // a non-finite value was produced
+  int pad;
+};
+
+// Forest geometry and physics shared by every scenario.
+struct GfGeom {
+  int mi, mj, M, T;  // T = M + 2*GF_NG
+  int minlevel, maxlevel;
+  int bc[4];
+  double xlower, xupper, ylower, yupper;
+  double g, drytol;
+  double cfl_desired, cfl_max, dt_max;
+  double tag_depth, tag_speed, tag_deta;
+  double src_box[4];
+  int src_level;
+  int nscen;
+  long long lut_per_scen;
+  long long lut_lev_off[GF_MAXLEV + 1];
+};
+
+// Everything a kernel needs to find patches and their data.
+struct GfView {
+  const GfPatch* patch;   // [npatch]
+  const int* lut;         // per scenario, per level: patch index or -1
+  GfScenario* scen;       // [nscen]
+  GfCtl* ctl;             // [nscen]
+  double* q[2];           // state buffers [cap][3][T][T]
+  double* b;              // beds [cap][T][T]
+  int npatch;
+  int pad;
+};
+
+// Kernel launchers (defined in the .cu files).
+namespace gf {
+int launch_patch_step_f64(const GfGeom& g, const GfView& v, double* pmass,
+                          void* stream);
+int launch_controller(const GfGeom& g, const GfView& v, const double* pmass,
+                      int nscen, void* stream);
+int launch_ctl_begin(GfCtl* ctl, int nscen, double t_target,
+                     long long max_steps, const int* scen_mask, void* stream);
+int launch_ghost_fill(const GfGeom& g, const GfView& v, int only_active,
+                      void* stream);
+int launch_topo(const GfGeom& g, const GfView& v, int first, int count,
+                void* stream);
+int launch_regrid_fill(const GfGeom& g, const GfView& oldv,
+                       const GfView& newv, void* stream);
+int launch_tags(const GfGeom& g, const GfView& v, uint8_t* flags,
+                void* stream);
+int launch_gauges(const GfGeom& g, const GfView& v, int only_accepted,
+                  int max_gauges, void* stream);
+int launch_mass(const GfGeom& g, const GfView& v, double* pmass,
+                double* smass, int nscen, void* stream);
+int launch_pack_interior(const GfGeom& g, const GfView& v, int scen_first,
+                         int count, double* out, int field_mask, int cur,
+                         void* stream);
+int launch_unpack_interior(const GfGeom& g, const GfView& v, int first,
+                           int count, const double* in, int cur,
+                           void* stream);
+void set_errflag(int* device_flag);
+}  // namespace gf

@@ -1,0 +1,295 @@
+"""ctypes binding of libgeoflood.so (argument marshalling only).
+
+Every computation runs in the CUDA library; this module converts numpy arrays
+and Python values to the C ABI of ``include/geoflood.h`` and raises
+:class:`GeoFloodError` on a non-zero status.  It refuses to work without the
+built library: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import threading
+
+import numpy as np
+
+from . import inputs
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libgeoflood.so")
+_lib = None
+_lock = threading.Lock()
+
+OK = 0
+ERRORS = {
+    -1: "ARG", -2: "CUDA", -3: "OOM", -4: "CFL", -5: "NAN",
+    -6: "NEGATIVE_DEPTH", -7: "TIMEOUT", -8: "CAPACITY", -9: "STATE",
+}
+KEEP, REFINE, COARSEN = 0, 1, 2
+
+
+class GeoFloodError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("geoflood error %d (%s): %s" % (code, ERRORS.get(code, "?"), msg))
+        self.code = code
+
+
+class _Cfg(C.Structure):
+    _fields_ = [
+        ("mi", C.c_int), ("mj", C.c_int), ("mx", C.c_int),
+        ("minlevel", C.c_int), ("maxlevel", C.c_int), ("bc", C.c_int * 4),
+        ("precision", C.c_int), ("num_scenarios", C.c_int),
+        ("max_patches", C.c_int), ("max_gauges", C.c_int),
+        ("xlower", C.c_double), ("xupper", C.c_double),
+        ("ylower", C.c_double), ("yupper", C.c_double),
+        ("g", C.c_double), ("drytol", C.c_double),
+        ("cfl_desired", C.c_double), ("cfl_max", C.c_double),
+        ("dt_initial", C.c_double), ("dt_max", C.c_double),
+        ("tag_depth", C.c_double), ("tag_speed", C.c_double),
+        ("tag_deta", C.c_double), ("src_box", C.c_double * 4),
+        ("src_level", C.c_int), ("reserved", C.c_int),
+    ]
+
+
+QINIT = C.CFUNCTYPE(None, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                    C.POINTER(C.c_double), C.POINTER(C.c_double),
+                    C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p)
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def lib():
+    """Load libgeoflood.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_LIB_PATH):
+                raise RuntimeError(
+                    "libgeoflood.so is missing: run __graft_entry__.build() "
+                    "(nvcc for sm_103a); there is no CPU fallback")
+            L = C.CDLL(_LIB_PATH)
+            vp, ip, dp = C.c_void_p, C.c_int, C.POINTER(C.c_double)
+            pi = C.POINTER(C.c_int)
+            ll = C.POINTER(C.c_longlong)
+            sig = {
+                "geoflood_init_forest": [C.POINTER(_Cfg), vp, C.POINTER(vp)],
+                "geoflood_set_scenario": [vp, ip, C.c_double, C.c_double],
+                "geoflood_set_topo": [vp, ip, dp, ip, ip] + [C.c_double] * 4,
+                "geoflood_npatch": [vp, ip, pi],
+                "geoflood_patch_info": [vp, ip, pi, pi, pi],
+                "geoflood_write_patches": [vp, ip, dp, dp, dp],
+                "geoflood_read_patches": [vp, ip, dp, dp, dp, dp],
+                "geoflood_read_tiles": [vp, ip, dp],
+                "geoflood_set_state": [vp, ip, QINIT, vp],
+                "geoflood_set_time": [vp, ip, C.c_double, C.c_double],
+                "geoflood_get_time": [vp, ip, dp, dp, ll, ll, ll, dp],
+                "geoflood_step": [vp, C.c_double, ip, dp, pi],
+                "geoflood_tags": [vp, ip, C.POINTER(C.c_uint8)],
+                "geoflood_regrid": [vp],
+                "geoflood_mass": [vp, ip, dp],
+                "geoflood_set_gauges": [vp, ip, dp, ip],
+                "geoflood_gauges": [vp, ip, dp, dp],
+                "geoflood_profile": [vp, ip],
+                "geoflood_profile_read": [vp, C.c_char_p, dp, ll],
+                "geoflood_launch_count": [vp, ll],
+            }
+            for name, args in sig.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = C.c_int
+            L.geoflood_destroy.argtypes = [vp]
+            L.geoflood_destroy.restype = None
+            L.geoflood_last_error.argtypes = [vp]
+            L.geoflood_last_error.restype = C.c_char_p
+            _lib = L
+    return _lib
+
+
+def _p(a, t=C.c_double):
+    return a.ctypes.data_as(C.POINTER(t))
+
+
+def config_struct(cfg: inputs.Config, num_scenarios=1, max_patches=None,
+                  max_gauges=64) -> _Cfg:
+    c = _Cfg()
+    for name in ("mi", "mj", "mx", "minlevel", "maxlevel", "src_level", "precision"):
+        setattr(c, name, int(getattr(cfg, name)))
+    for name in ("xlower", "xupper", "ylower", "yupper", "g", "drytol",
+                 "cfl_desired", "cfl_max", "dt_initial", "dt_max", "tag_depth",
+                 "tag_speed", "tag_deta"):
+        v = float(getattr(cfg, name))
+        setattr(c, name, v if math.isfinite(v) else 1e300)
+    for k in range(4):
+        c.bc[k] = int(cfg.bc[k])
+        c.src_box[k] = float(cfg.src_box[k])
+    c.num_scenarios = int(num_scenarios)
+    if max_patches is None:
+        per = cfg.mi * cfg.mj * (4 ** cfg.maxlevel)
+        max_patches = num_scenarios * min(per, max(4096, cfg.mi * cfg.mj * 4 ** cfg.minlevel * 4))
+    c.max_patches = int(max_patches)
+    c.max_gauges = int(max_gauges)
+    return c
+
+
+class Forest:
+    """One context: forests of num_scenarios scenarios on the GPU."""
+
+    def __init__(self, cfg: inputs.Config, dem=None, num_scenarios=1,
+                 max_patches=None, max_gauges=64, stream=None):
+        self.cfg = cfg
+        self.nscen = num_scenarios
+        self._c = config_struct(cfg, num_scenarios, max_patches, max_gauges)
+        h = C.c_void_p()
+        rc = lib().geoflood_init_forest(C.byref(self._c), stream, C.byref(h))
+        if rc:
+            raise GeoFloodError(rc, "init_forest")
+        self._h = h
+        self._ng = {}
+        for s in range(num_scenarios):
+            self._check(lib().geoflood_set_scenario(self._h, s, cfg.manning_n, cfg.eta0))
+            if dem is not None:
+                self.set_topo(dem, s)
+
+    def _check(self, rc):
+        if rc:
+            raise GeoFloodError(rc, lib().geoflood_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().geoflood_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def set_scenario(self, s, manning_n, eta0):
+        self._check(lib().geoflood_set_scenario(self._h, s, manning_n, eta0))
+
+    def set_topo(self, dem, s=0):
+        z = np.ascontiguousarray(dem.z, dtype=np.float64)
+        ny, nx = z.shape
+        self._check(lib().geoflood_set_topo(self._h, s, _p(z), nx, ny, dem.x0,
+                                            dem.y0, dem.dx, dem.dy))
+
+    def npatch_of(self, s=0):
+        n = C.c_int()
+        self._check(lib().geoflood_npatch(self._h, s, C.byref(n)))
+        return n.value
+
+    @property
+    def npatch(self):
+        return self.npatch_of(0)
+
+    def patch_info(self, s=0):
+        n = self.npatch_of(s)
+        L = np.empty(n, np.int32)
+        X = np.empty(n, np.int32)
+        Y = np.empty(n, np.int32)
+        self._check(lib().geoflood_patch_info(self._h, s, _p(L, C.c_int),
+                                              _p(X, C.c_int), _p(Y, C.c_int)))
+        return L, X, Y
+
+    def write(self, h, hu, hv, s=0):
+        a = [np.ascontiguousarray(x, dtype=np.float64) for x in (h, hu, hv)]
+        self._check(lib().geoflood_write_patches(self._h, s, *[_p(x) for x in a]))
+
+    def read(self, s=0):
+        n, m = self.npatch_of(s), self.cfg.mx
+        out = [np.empty((n, m, m)) for _ in range(4)]
+        self._check(lib().geoflood_read_patches(self._h, s, *[_p(x) for x in out]))
+        return tuple(out)
+
+    def read_into(self, h, hu, hv, b=None, s=0):
+        """Read the state into caller arrays (e.g. pinned host buffers)."""
+        ptr = lambda x: _p(x) if x is not None else None
+        self._check(lib().geoflood_read_patches(self._h, s, ptr(h), ptr(hu), ptr(hv), ptr(b)))
+
+    def read_tiles(self, s=0):
+        n, T = self.npatch_of(s), self.cfg.mx + 4
+        out = np.empty((n, 4, T, T))
+        self._check(lib().geoflood_read_tiles(self._h, s, _p(out)))
+        return out
+
+    def set_state(self, ic, s=0):
+        """Initial state through the library's host callback."""
+        def cb(n, x, y, b, h, hu, hv, user):
+            X = np.ctypeslib.as_array(x, (n,))
+            Y = np.ctypeslib.as_array(y, (n,))
+            B = np.ctypeslib.as_array(b, (n,))
+            hh, uu, vv = ic(X, Y, B)
+            np.ctypeslib.as_array(h, (n,))[:] = np.broadcast_to(hh, (n,))
+            np.ctypeslib.as_array(hu, (n,))[:] = np.broadcast_to(uu, (n,))
+            np.ctypeslib.as_array(hv, (n,))[:] = np.broadcast_to(vv, (n,))
+        fn = QINIT(cb)
+        self._check(lib().geoflood_set_state(self._h, s, fn, None))
+
+    def set_time(self, t, dt_next, s=0):
+        self._check(lib().geoflood_set_time(self._h, s, float(t), float(dt_next)))
+
+    def time(self, s=0):
+        t, dt, cv = C.c_double(), C.c_double(), C.c_double()
+        st, rj, nc = C.c_longlong(), C.c_longlong(), C.c_longlong()
+        self._check(lib().geoflood_get_time(self._h, s, C.byref(t), C.byref(dt),
+                                            C.byref(st), C.byref(rj), C.byref(nc),
+                                            C.byref(cv)))
+        return dict(t=t.value, dt_next=dt.value, steps=st.value, rejects=rj.value,
+                    nclip=nc.value, clipvol=cv.value)
+
+    def step(self, t_target, max_steps=1 << 30):
+        """Advance every scenario; returns (t, steps) of scenario 0 and keeps
+        the per-scenario arrays in last_t / last_steps."""
+        t = np.zeros(self.nscen)
+        n = np.zeros(self.nscen, np.int32)
+        self._check(lib().geoflood_step(self._h, float(t_target), int(min(max_steps, 2**31 - 1)),
+                                        _p(t), _p(n, C.c_int)))
+        self.last_t, self.last_steps = t, n
+        return float(t[0]), int(n[0])
+
+    def tags(self, s=0):
+        f = np.empty(self.npatch_of(s), np.uint8)
+        self._check(lib().geoflood_tags(self._h, s, _p(f, C.c_uint8)))
+        return f
+
+    def regrid(self):
+        self._check(lib().geoflood_regrid(self._h))
+        return self.npatch
+
+    def mass(self, s=0):
+        m = C.c_double()
+        self._check(lib().geoflood_mass(self._h, s, C.byref(m)))
+        return m.value
+
+    def set_gauges(self, xy, s=0):
+        xy = np.ascontiguousarray(xy, dtype=np.float64).reshape(-1, 2)
+        self._ng[s] = len(xy)
+        self._check(lib().geoflood_set_gauges(self._h, s, _p(xy), len(xy)))
+
+    def gauges(self, s=0):
+        n = self._ng.get(s, 0)
+        out = np.empty((n, 5))
+        arr = np.empty(n)
+        self._check(lib().geoflood_gauges(self._h, s, _p(out), _p(arr)))
+        return out, arr
+
+    def profile(self, enable=True):
+        self._check(lib().geoflood_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self, kernel):
+        ms = C.c_double()
+        n = C.c_longlong()
+        self._check(lib().geoflood_profile_read(self._h, kernel.encode(), C.byref(ms), C.byref(n)))
+        return ms.value, n.value
+
+    def launch_count(self):
+        n = C.c_longlong()
+        self._check(lib().geoflood_launch_count(self._h, C.byref(n)))
+        return n.value
+
+
+def exported_symbols():
+    """Names of the entry points include/geoflood.h declares."""
+    import re
+    hdr = open(os.path.join(os.path.dirname(_HERE), "include", "geoflood.h")).read()
+    return sorted(set(re.findall(r"\b(geoflood_[a-z_]+)\s*\(", hdr)))
