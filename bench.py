@@ -26,6 +26,10 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# DRAM bytes (read + write) of one patch_step launch on this workload, from
+# the ncu capture summarised in profiles/ (None when the kernel has changed
+# since the capture).
+TRAFFIC_PER_LAUNCH = None
 N_CELLS = 1024
 PATCH = 32
 T_END = 60.0
@@ -39,7 +43,23 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--t-end", type=float, default=T_END)
+    ap.add_argument("--profile-case", type=int, default=0,
+                    help="run N x N cells of the workload for --profile-steps "
+                         "steps and exit (for ncu captures; prints no JSON)")
+    ap.add_argument("--profile-steps", type=int, default=20)
     return ap.parse_args()
+
+
+def run_profile_case(args):
+    """Fixed-length run of the same workload at another size (no timing)."""
+    import torch
+    from paper_2403_15435_gb300 import geoflood, inputs
+    n = args.profile_case
+    prob = inputs.radial_dambreak(n, PATCH, dx=2.0, radius=200.0 * n / N_CELLS)
+    f = geoflood.Forest(prob.cfg, prob.dem, max_patches=(n // PATCH) ** 2)
+    f.set_state(prob.ic)
+    _, steps = f.step(1e9, args.profile_steps)
+    print("profile case %d x %d: %d steps, t = %.3f s" % (n, n, steps, f.time()["t"]))
 
 
 def dist_env():
@@ -105,11 +125,24 @@ def measured_peaks():
         return {}
 
 
-# Algorithmic work per cell update of the FP64 step, counted operation by
-# operation from the scheme: reads h, hu, hv, b and
-# writes h, hu, hv (56 B) and ~FLOP_PER_CELL double-precision operations.
+# Algorithmic work of the FP64 patch step, counted operation by operation
+# from the scheme: a wet cell update takes two edge solves (74 operations
+# each), two limited edge fluxes (81), two increments (9), two transverse
+# splits (38), two transverse fluxes (9), the update (30) and Manning
+# friction (16): 468 FP64 operations (add, sub, mul, div, sqrt, cbrt each
+# counted once); a dry cell needs none.  Traffic: read h, hu, hv, b and write
+# h, hu, hv = 56 B per cell update.
 BYTES_PER_CELL_FP64 = 56
-FLOP_PER_CELL_FP64 = None  # filled from the design doc's count once measured
+OPS_PER_WET_CELL_FP64 = 468
+FP64_LANES_PER_SM = 2  # measured: DFMA throughput 1.20 TFLOP/s on 152 SMs
+N_SM = 152
+
+
+def fp64_peak_gops(peaks):
+    """FP64 operation peak: 152 SMs x 2 FP64 lanes x the maximum SM clock
+    (one add, mul or FMA per lane per clock)."""
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    return N_SM * FP64_LANES_PER_SM * mhz / 1e3
 
 
 def run_ours(args):
@@ -154,6 +187,7 @@ def run_ours(args):
 
     times, steps_list = [], []
     launches0 = f.launch_count()
+    cu0, wet0 = f.counters()
     f.profile(True)
     ev = []
     with ClockSampler(local) as clk:
@@ -172,6 +206,7 @@ def run_ours(args):
             steps_list.append(st)
         torch.cuda.synchronize(dev)
     launches_timed = f.launch_count() - launches0
+    cu1, wet1 = f.counters()
     for a, b in ev:
         times.append(a.elapsed_time(b) / 1e3)
     k_ms, k_n = f.profile_read("patch_step")
@@ -200,13 +235,15 @@ def run_ours(args):
 
     peaks = measured_peaks()
     avg_launch = k_ms / 1e3 / max(1, k_n)
-    bytes_per_launch = BYTES_PER_CELL_FP64 * cells
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    roof = {"bound": "hbm", "achieved": bytes_per_launch / avg_launch / 1e9,
-            "peak": hbm, "unit": "GB/s",
-            "frac": bytes_per_launch / avg_launch / 1e9 / hbm,
-            "traffic": None, "kernel": "patch_step", "avg_launch_ms": avg_launch * 1e3,
-            "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    ops_per_launch = OPS_PER_WET_CELL_FP64 * (wet1 - wet0) / max(1, k_n)
+    peak = fp64_peak_gops(peaks)
+    achieved = ops_per_launch / avg_launch / 1e9
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GOP/s",
+            "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH,
+            "kernel": "patch_step (FP64)", "avg_launch_ms": avg_launch * 1e3,
+            "ops_per_launch": ops_per_launch, "wet_fraction": (wet1 - wet0) / max(1, cu1 - cu0),
+            "peak_source": "derived: 152 SMs x 2 FP64 lanes x %.0f MHz (measured DFMA probe 1.20 TFLOP/s)" % float(peaks.get("sm_max_mhz", 2070.0)),
+            "hbm_frac_of_measured": BYTES_PER_CELL_FP64 * cells / avg_launch / 1e9 / peaks.get("hbm_gbs", 6785.2)}
     cpu = cpu_baseline()
     line = {
         "metric": "cell-updates/s", "value": value, "unit": "cell-updates/s",
@@ -277,7 +314,9 @@ def run_reference(args):
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.profile_case:
+        run_profile_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

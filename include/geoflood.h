@@ -200,6 +200,12 @@ int geoflood_profile(geoflood_ctx* ctx, int enable);
 int geoflood_profile_read(geoflood_ctx* ctx, const char* kernel,
                           double* total_ms, long long* launches);
 
+/* Work counters of a scenario since the context was created: interior cell
+ * updates computed by the patch step (rejected steps included) and how many
+ * of them were wet (h > drytol) at the start of the step. */
+int geoflood_counters(geoflood_ctx* ctx, int scenario, long long* cell_updates,
+                      long long* wet_cell_updates);
+
 /* Number of kernels this context has launched since it was created. */
 int geoflood_launch_count(geoflood_ctx* ctx, long long* launches);
 

@@ -713,6 +713,16 @@ int geoflood_profile_read(geoflood_ctx* ctx, const char* kernel,
   return 0;
 }
 
+int geoflood_counters(geoflood_ctx* ctx, int s, long long* cell_updates,
+                      long long* wet_cell_updates) {
+  if (!valid_scen(ctx, s)) return fail(ctx, GEOFLOOD_ERR_ARG, "counters: bad scenario");
+  int rc = sync_ctl_down(ctx);
+  if (rc) return rc;
+  if (cell_updates) *cell_updates = (long long)ctx->h_ctl[s].cell_updates;
+  if (wet_cell_updates) *wet_cell_updates = (long long)ctx->h_ctl[s].wet_updates;
+  return 0;
+}
+
 int geoflood_launch_count(geoflood_ctx* ctx, long long* launches) {
   if (!ctx || !launches) return GEOFLOOD_ERR_ARG;
   *launches = ctx->launches;

@@ -36,6 +36,8 @@ struct GfCtl {
   unsigned long long cmax_bits;     // max CFL rate of the step (bits of a
                                     // non-negative double, atomicMax'ed)
   unsigned long long step_nclip;
+  unsigned long long cell_updates;  // interior cells stepped (all launches)
+  unsigned long long wet_updates;   // of which wet (h > drytol) before the step
   long long steps, rejects, nclip, taken, max_steps;
   int cur;       // which state buffer is current
   int active;    // this scenario still advances in the current call

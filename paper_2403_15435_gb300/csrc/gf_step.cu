@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(NT, 1)
   // ------------------------------------------------ update, friction, out
   const double mn = V.scen[P.scen].manning_n;
   double vol = 0.0, clipd = 0.0;
-  unsigned nclip = 0;
+  unsigned nclip = 0, nwet = 0;
   bool bad = false;
 #pragma unroll
   for (int r = 0; r < RC; ++r) {
@@ -318,6 +318,7 @@ __global__ void __launch_bounds__(NT, 1)
       const int i = k % M, j = k / M;
       const int c = tix<M>(i, j);
       const double q[3] = {sh[c], shu[c], shv[c]};
+      nwet += q[0] > drytol ? 1u : 0u;
       double o[3];
 #pragma unroll
       for (int f = 0; f < 3; ++f) {
@@ -351,6 +352,8 @@ __global__ void __launch_bounds__(NT, 1)
   smx = warp_max(smx);
   smy = warp_max(smy);
   vol = warp_sum_tree(vol);
+  nwet = __reduce_add_sync(0xffffffffu, nwet);
+  if (lane == 0 && nwet) atomicAdd(&C->wet_updates, (unsigned long long)nwet);
   if (lane == 0) {
     red[wid] = smx;
     red[NW + wid] = smy;
@@ -367,6 +370,7 @@ __global__ void __launch_bounds__(NT, 1)
     const double cx = mx / dx, cy = my / dy;
     const double cm = cx > cy ? cx : cy;
     atomicMax(&C->cmax_bits, (unsigned long long)__double_as_longlong(cm));
+    atomicAdd(&C->cell_updates, (unsigned long long)(M * M));
     pmass[p] = vs * (dx * dy);
   }
   if (nclip) {

@@ -95,6 +95,7 @@ def lib():
                 "geoflood_profile": [vp, ip],
                 "geoflood_profile_read": [vp, C.c_char_p, dp, ll],
                 "geoflood_launch_count": [vp, ll],
+                "geoflood_counters": [vp, ip, ll, ll],
             }
             for name, args in sig.items():
                 f = getattr(L, name)
@@ -281,6 +282,11 @@ class Forest:
         n = C.c_longlong()
         self._check(lib().geoflood_profile_read(self._h, kernel.encode(), C.byref(ms), C.byref(n)))
         return ms.value, n.value
+
+    def counters(self, s=0):
+        a, b = C.c_longlong(), C.c_longlong()
+        self._check(lib().geoflood_counters(self._h, s, C.byref(a), C.byref(b)))
+        return a.value, b.value
 
     def launch_count(self):
         n = C.c_longlong()
