@@ -209,6 +209,48 @@ int geoflood_counters(geoflood_ctx* ctx, int scenario, long long* cell_updates,
 /* Number of kernels this context has launched since it was created. */
 int geoflood_launch_count(geoflood_ctx* ctx, long long* launches);
 
+/* One FP64 patch step on caller-owned device buffers, allocating nothing.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot let the library allocate device memory -- for example a host code
+ * that owns all device memory through its own pool, or code running where a
+ * cudaMalloc is not allowed -- and therefore cannot create a context.  It
+ * runs the same patch-step kernel as geoflood_step (augmented Riemann solves,
+ * limited corrections, transverse terms, update, Manning friction) on npatch
+ * independent tiles of one level with a fixed dt.
+ *
+ *   q_in   device, [npatch][3][mx+4][mx+4] h, hu, hv with the two ghost
+ *          layers already filled (e.g. by geoflood_read_tiles);
+ *   b      device, [npatch][mx+4][mx+4] bed, ghosts included;
+ *   q_out  device, same shape as q_in and distinct from it: the interior of
+ *          every tile is written, the ghost entries are left untouched;
+ *   mx     16 or 32; dx, dy the cell sizes; dt the step; g, drytol,
+ *          manning_n as in the context API;
+ *   cmax   host, may be NULL: receives max over the patches of
+ *          max(|s|/dx, |s|/dy) over the edges that update interior cells
+ *          (the CFL number of the step is dt * cmax); when non-NULL the call
+ *          synchronises the stream;
+ *   stream cudaStream_t or NULL.
+ *
+ * The scratch it needs (patch table, per-patch volumes, the CFL reduction
+ * cell) lives in one static device array of about 384 KiB that every GPU
+ * loading the library keeps until the process exits; hence npatch is limited
+ * to 16384 and a larger npatch returns GEOFLOOD_ERR_CAPACITY.  The first call
+ * on a device looks up that array's device address (once per device), so
+ * make the first call before any stream capture.  All calls share the array
+ * and each call overwrites the previous call's contents (the reduction cell
+ * is cleared at the start of every call): calls whose work overlaps on the
+ * GPU race, so keep them on one stream.  Errors: ARG, CAPACITY, CUDA; the
+ * message is returned by geoflood_noalloc_last_error(). */
+int geoflood_step_tiles_noalloc(const double* q_in, const double* b,
+                                double* q_out, int npatch, int mx, double dx,
+                                double dy, double dt, double g, double drytol,
+                                double manning_n, double* cmax, void* stream);
+
+/* Message of the last failed geoflood_step_tiles_noalloc call on this host
+ * thread ("" if none). */
+const char* geoflood_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

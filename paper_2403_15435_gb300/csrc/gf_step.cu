@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstdio>
+#include <cstring>
 
 #include "gf_internal.h"
 #include "gf_solver.cuh"
@@ -520,3 +522,142 @@ int launch_ctl_begin(GfCtl* ctl, int nscen, double t_target,
 }
 
 }  // namespace gf
+
+// ---------------------------------------------------------------------------
+// Entry point for callers that cannot allocate device memory.
+//
+// Some callers own every byte of device memory themselves: a solver embedded
+// in a host code with its own memory pool, or code that runs where
+// cudaMalloc is not allowed (inside a captured region that must not grow the
+// pool, or under an allocator that hands out only pre-registered buffers).
+// They cannot create a geoflood context, because a context allocates its
+// state.  geoflood_step_tiles_noalloc runs the same FP64 patch-step kernel on
+// tiles the caller provides, and keeps the small scratch it needs (patch
+// table, per-patch volume, the reduction cell of the CFL rate) in the static
+// device array below, so the call allocates nothing.
+//
+// Limits and behaviour:
+//   - at most GF_NOALLOC_MAX_PATCHES patches per call (the array holds
+//     GF_NOALLOC_MAX_PATCHES * 24 bytes + 512 bytes, about 384 KiB, on every
+//     GPU that loads the library, until the process exits);
+//   - the first call on a device looks up the array's device address with
+//     cudaGetSymbolAddress (once per device); make that first call before any
+//     stream capture;
+//   - every call reuses the same array and overwrites what the previous call
+//     left there (the reduction cell is cleared at the start of each call),
+//     so calls whose kernels overlap on the GPU race: issue them on one stream
+//     or order them.
+// ---------------------------------------------------------------------------
+#define GF_NOALLOC_MAX_PATCHES 16384
+
+namespace {
+
+struct NoallocScratch {
+  GfCtl ctl;
+  GfScenario scen;
+  GfPatch patch[GF_NOALLOC_MAX_PATCHES];
+  double pmass[GF_NOALLOC_MAX_PATCHES];
+};
+
+static __device__ __align__(256) unsigned char
+    gf_noalloc_scratch[sizeof(NoallocScratch)];
+
+__global__ void k_noalloc_init(NoallocScratch* S, int n, double dt,
+                               double manning_n) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k == 0) {
+    GfCtl c{};
+    c.active = 1;
+    c.cur = 0;
+    c.dt_use = dt;
+    S->ctl = c;
+    GfScenario sc{};
+    sc.manning_n = manning_n;
+    sc.pcount = n;
+    S->scen = sc;
+  }
+  if (k < n) S->patch[k] = GfPatch{0, 0, 0, 0};
+}
+
+NoallocScratch* noalloc_scratch(int* rc) {
+  static NoallocScratch* addr[64] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    *rc = -2;
+    return nullptr;
+  }
+  if (!addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, gf_noalloc_scratch) != cudaSuccess || !p) {
+      *rc = -2;
+      return nullptr;
+    }
+    addr[dev] = static_cast<NoallocScratch*>(p);
+  }
+  *rc = 0;
+  return addr[dev];
+}
+
+thread_local char noalloc_err[256] = "";
+
+int noalloc_fail(int code, const char* msg) {
+  snprintf(noalloc_err, sizeof(noalloc_err), "%s", msg);
+  return code;
+}
+
+}  // namespace
+
+extern "C" const char* geoflood_noalloc_last_error(void) { return noalloc_err; }
+
+extern "C" int geoflood_step_tiles_noalloc(const double* q_in, const double* b,
+                                           double* q_out, int npatch, int mx,
+                                           double dx, double dy, double dt,
+                                           double g, double drytol,
+                                           double manning_n, double* cmax,
+                                           void* stream) {
+  if (!q_in || !b || !q_out || q_in == q_out || !(mx == 16 || mx == 32) ||
+      !(dx > 0) || !(dy > 0) || !(dt > 0) || !(g > 0) || !(drytol > 0) ||
+      !(manning_n >= 0))
+    return noalloc_fail(-1, "step_tiles_noalloc: bad argument");
+  if (npatch < 1 || npatch > GF_NOALLOC_MAX_PATCHES)
+    return noalloc_fail(-8, "step_tiles_noalloc: npatch must be in [1, 16384]");
+  int rc = 0;
+  NoallocScratch* S = noalloc_scratch(&rc);
+  if (!S) return noalloc_fail(rc, "step_tiles_noalloc: cudaGetSymbolAddress failed");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // one level-0 patch per tile; the patch width mx*dx is a power-of-two
+  // multiple of dx, so the kernel's dx = width / mx is exact
+  GfGeom G{};
+  G.mi = 1; G.mj = 1; G.M = mx; G.T = mx + 2 * GF_NG;
+  G.xlower = 0.0; G.xupper = dx * mx;
+  G.ylower = 0.0; G.yupper = dy * mx;
+  G.g = g; G.drytol = drytol;
+  G.cfl_desired = 0.9; G.cfl_max = 1.0; G.dt_max = 1e300;
+  G.nscen = 1;
+  GfView V{};
+  V.patch = S->patch;
+  V.lut = nullptr;
+  V.scen = &S->scen;
+  V.ctl = &S->ctl;
+  V.q[0] = const_cast<double*>(q_in);
+  V.q[1] = q_out;
+  V.b = const_cast<double*>(b);
+  V.npatch = npatch;
+  k_noalloc_init<<<(npatch + 255) / 256, 256, 0, st>>>(S, npatch, dt, manning_n);
+  if (cudaGetLastError() != cudaSuccess)
+    return noalloc_fail(-2, "step_tiles_noalloc: init launch failed");
+  const int lr = mx == 32 ? launch_step_t<32, 512>(G, V, S->pmass, st)
+                          : launch_step_t<16, 256>(G, V, S->pmass, st);
+  if (lr) return noalloc_fail(-2, "step_tiles_noalloc: step launch failed");
+  if (cmax) {
+    unsigned long long bits = 0;
+    if (cudaMemcpyAsync(&bits, &S->ctl.cmax_bits, sizeof(bits),
+                        cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return noalloc_fail(-2, "step_tiles_noalloc: reading the CFL rate failed");
+    double v;
+    std::memcpy(&v, &bits, sizeof(v));
+    *cmax = v;
+  }
+  return 0;
+}
