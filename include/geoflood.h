@@ -50,6 +50,10 @@ extern "C" {
 #define GEOFLOOD_BC_EXTRAP 1 /* zero-order extrapolation (open boundary) */
 
 #define GEOFLOOD_FP64 0 /* plain double precision */
+/* FP32 surface-deviation form: state w = h + b - eta0, hu, hv in FP32 with
+ * FP32 compensation terms for the update; wet/dry tests exact (FP64 where
+ * FP32 cannot decide); volumes and time stepping in FP64. */
+#define GEOFLOOD_FP32_DEV 1
 
 #define GEOFLOOD_TAG_KEEP 0
 #define GEOFLOOD_TAG_REFINE 1

@@ -20,11 +20,12 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # (source, extra flags)
 SOURCES = [
     ("gf_step.cu", ["-fmad=false"]),
+    ("gf_step32.cu", []),
     ("gf_amr.cu", ["-fmad=false"]),
     ("gf_forest.cpp", []),
     ("gf_api.cpp", []),
 ]
-HEADERS = ["gf_internal.h", "gf_solver.cuh", "gf_forest.h"]
+HEADERS = ["gf_internal.h", "gf_solver.cuh", "gf_forest.h", "gf_step_kernel.cuh"]
 
 
 def nvcc() -> str:

@@ -11,7 +11,9 @@
 
 namespace {
 
+template <typename T>
 struct Geo {
+  static constexpr bool DEV = sizeof(T) == 4;  // FP32 surface-deviation form
   const GfGeom& G;
   const GfView& V;
   __device__ Geo(const GfGeom& g, const GfView& v) : G(g), V(v) {}
@@ -28,17 +30,46 @@ struct Geo {
     if (P < 0 || Q < 0 || P >= w || Q >= h) return -1;
     return V.lut[V.scen[s].lut_off + G.lut_lev_off[L] + P + Q * w];
   }
-  __device__ const double* cellp(int p, int buf) const {
-    return V.q[buf] + (size_t)p * 3 * G.T * G.T;
+  __device__ T* qp(int p, int buf) const {
+    T* base;
+    if constexpr (DEV) base = V.qf[buf];
+    else base = V.q[buf];
+    return base + (size_t)p * 3 * G.T * G.T;
+  }
+  __device__ T* bp(int p) const {
+    T* base;
+    if constexpr (DEV) base = V.bf;
+    else base = V.b;
+    return base + (size_t)p * G.T * G.T;
+  }
+  // (h, hu, hv, b) of cell c of patch p in buffer buf, in FP64; in the
+  // deviation form h = w - b exactly and b is the bed minus eta0
+  __device__ void load(int p, int buf, int c, double (&o)[4]) const {
+    const int TT = G.T * G.T;
+    const T* q = qp(p, buf);
+    const double b = (double)bp(p)[c];
+    o[0] = DEV ? (double)q[c] - b : (double)q[c];
+    o[1] = (double)q[TT + c];
+    o[2] = (double)q[2 * TT + c];
+    o[3] = b;
+  }
+  // store (h, hu, hv) into cell c of patch p, buffer buf, whose bed is b
+  __device__ void store(T* q, int c, double h, double hu, double hv,
+                        double b) const {
+    const int TT = G.T * G.T;
+    q[c] = DEV ? (T)(h + b) : (T)h;
+    q[TT + c] = (T)hu;
+    q[2 * TT + c] = (T)hv;
   }
 };
 
 // Composite value (h, hu, hv, b) at cell (I, J) of level L: the leaf of that
 // level, a coarser leaf's cell, or the mean of the finer cells (down to two
 // levels finer, which a 2:1 balanced forest never exceeds).
-__device__ void value_at(const Geo& e, int s, int L, long long I, long long J,
-                         double (&out)[4], int* err) {
-  const int TT = e.G.T * e.G.T;
+template <typename T>
+__device__ void value_at(const Geo<T>& e, int s, int L, long long I,
+                         long long J, double (&out)[4], int* err) {
+  const int cur = e.V.ctl[s].cur;
   for (int l = L; l >= 0; --l) {
     const long long Il = I >> (L - l), Jl = J >> (L - l);
     const int p = e.leaf(s, l, Il, Jl);
@@ -46,11 +77,7 @@ __device__ void value_at(const Geo& e, int s, int L, long long I, long long J,
       const GfPatch P = e.V.patch[p];
       const int c = e.tix((int)(Il - (long long)P.px * e.G.M),
                           (int)(Jl - (long long)P.py * e.G.M));
-      const double* q = e.cellp(p, e.V.ctl[s].cur);
-      out[0] = q[c];
-      out[1] = q[TT + c];
-      out[2] = q[2 * TT + c];
-      out[3] = e.V.b[(size_t)p * TT + c];
+      e.load(p, cur, c, out);
       return;
     }
   }
@@ -62,11 +89,7 @@ __device__ void value_at(const Geo& e, int s, int L, long long I, long long J,
       const GfPatch P = e.V.patch[p];
       const int c = e.tix((int)(Ic - (long long)P.px * e.G.M),
                           (int)(Jc - (long long)P.py * e.G.M));
-      const double* q = e.cellp(p, e.V.ctl[s].cur);
-      v[ch][0] = q[c];
-      v[ch][1] = q[TT + c];
-      v[ch][2] = q[2 * TT + c];
-      v[ch][3] = e.V.b[(size_t)p * TT + c];
+      e.load(p, cur, c, v[ch]);
     } else {
       double w[4][4];
       for (int gc = 0; gc < 4; ++gc) {
@@ -80,11 +103,7 @@ __device__ void value_at(const Geo& e, int s, int L, long long I, long long J,
         const GfPatch P = e.V.patch[pg];
         const int c = e.tix((int)(Ig - (long long)P.px * e.G.M),
                             (int)(Jg - (long long)P.py * e.G.M));
-        const double* q = e.cellp(pg, e.V.ctl[s].cur);
-        w[gc][0] = q[c];
-        w[gc][1] = q[TT + c];
-        w[gc][2] = q[2 * TT + c];
-        w[gc][3] = e.V.b[(size_t)pg * TT + c];
+        e.load(pg, cur, c, w[gc]);
       }
       for (int f = 0; f < 4; ++f)
         v[ch][f] = 0.25 * ((w[0][f] + w[1][f]) + (w[2][f] + w[3][f]));
@@ -103,18 +122,19 @@ __device__ __forceinline__ double minmod(double a, double b) {
 // forest of the view: copy from a same-level leaf, mean of finer cells, or
 // limited interpolation of the coarser level's surface and momenta (Sec. 4
 // ghost cells, Sec. 6.2 surface-preserving interpolation).
-__device__ void fill_cell(const Geo& e, int s, int L, long long I, long long J,
-                          double bt, double (&out)[3], int* err) {
-  const int TT = e.G.T * e.G.T;
+template <typename T>
+__device__ void fill_cell(const Geo<T>& e, int s, int L, long long I,
+                          long long J, double bt, double (&out)[3], int* err) {
   const int p = e.leaf(s, L, I, J);
   if (p >= 0) {
     const GfPatch P = e.V.patch[p];
     const int c = e.tix((int)(I - (long long)P.px * e.G.M),
                         (int)(J - (long long)P.py * e.G.M));
-    const double* q = e.cellp(p, e.V.ctl[s].cur);
-    out[0] = q[c];
-    out[1] = q[TT + c];
-    out[2] = q[2 * TT + c];
+    double o4[4];
+    e.load(p, e.V.ctl[s].cur, c, o4);
+    out[0] = o4[0];
+    out[1] = o4[1];
+    out[2] = o4[2];
     return;
   }
   bool coarser = false;
@@ -187,24 +207,25 @@ __device__ void fill_cell(const Geo& e, int s, int L, long long I, long long J,
 // columns inside the domain, then left/right over every row (Sec. 5.1 closed
 // walls mirror the cells and negate the normal momentum; extrapolation
 // copies the edge cell).  fields: 0 = h, hu, hv in q; 1 = the bed in b.
-__device__ void tile_bc(const Geo& e, const GfPatch& P, double* q,
-                        double* bfield, int bed) {
-  const int M = e.G.M, T = e.G.T, TT = T * T;
+template <typename T, typename G2>
+__device__ void tile_bc(const G2& e, const GfPatch& P, T* q, T* bfield,
+                        int bed) {
+  const int M = e.G.M, T_ = e.G.T, TT = T_ * T_;
   const long long NX = e.nx(P.level), NY = e.ny(P.level);
   const int nf = bed ? 1 : 3;
   for (int side = 2; side <= 3; ++side) {
     const bool at = side == 2 ? (P.py == 0) : ((long long)(P.py + 1) * M == NY);
     if (!at) continue;
     const bool wall = e.G.bc[side] == 0;
-    const int n = T * GF_NG * nf;
+    const int n = T_ * GF_NG * nf;
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
-      const int i = k % T - GF_NG, gl = (k / T) % GF_NG + 1, f = k / (T * GF_NG);
+      const int i = k % T_ - GF_NG, gl = (k / T_) % GF_NG + 1, f = k / (T_ * GF_NG);
       const long long I = (long long)P.px * M + i;
       if (I < 0 || I >= NX) continue;
       const int jg = side == 2 ? -gl : M - 1 + gl;
       const int js = wall ? (side == 2 ? gl - 1 : M - gl) : (side == 2 ? 0 : M - 1);
-      double* a = bed ? bfield : q + f * TT;
-      double v = a[e.tix(i, js)];
+      T* a = bed ? bfield : q + f * TT;
+      T v = a[e.tix(i, js)];
       if (!bed && wall && f == 2) v = -v;
       a[e.tix(i, jg)] = v;
     }
@@ -214,13 +235,13 @@ __device__ void tile_bc(const Geo& e, const GfPatch& P, double* q,
     const bool at = side == 0 ? (P.px == 0) : ((long long)(P.px + 1) * M == NX);
     if (!at) continue;
     const bool wall = e.G.bc[side] == 0;
-    const int n = T * GF_NG * nf;
+    const int n = T_ * GF_NG * nf;
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
-      const int j = k % T - GF_NG, gl = (k / T) % GF_NG + 1, f = k / (T * GF_NG);
+      const int j = k % T_ - GF_NG, gl = (k / T_) % GF_NG + 1, f = k / (T_ * GF_NG);
       const int ig = side == 0 ? -gl : M - 1 + gl;
       const int is = wall ? (side == 0 ? gl - 1 : M - gl) : (side == 0 ? 0 : M - 1);
-      double* a = bed ? bfield : q + f * TT;
-      double v = a[e.tix(is, j)];
+      T* a = bed ? bfield : q + f * TT;
+      T v = a[e.tix(is, j)];
       if (!bed && wall && f == 1) v = -v;
       a[e.tix(ig, j)] = v;
     }
@@ -231,16 +252,17 @@ __device__ void tile_bc(const Geo& e, const GfPatch& P, double* q,
 // Ghost fill: one CTA per patch.  Interior-domain ghosts from the leaves
 // (reads only leaf interiors, so patches are independent), then the
 // physical boundaries.
+template <typename T>
 __global__ void k_ghost_fill(const GfGeom G, const GfView V, int only_accepted,
                              int* errflag) {
   const int p = blockIdx.x;
   const GfPatch P = V.patch[p];
   const GfCtl* C = V.ctl + P.scen;
   if (only_accepted && !C->accepted) return;
-  Geo e(G, V);
-  const int M = G.M, T = G.T, TT = T * T;
-  double* q = V.q[C->cur] + (size_t)p * 3 * TT;
-  const double* bb = V.b + (size_t)p * TT;
+  Geo<T> e(G, V);
+  const int M = G.M, T_ = G.T, TT = T_ * T_;
+  T* q = e.qp(p, C->cur);
+  const T* bb = e.bp(p);
   const long long NX = e.nx(P.level), NY = e.ny(P.level);
   const int nghost = TT - M * M;
   int err = 0;
@@ -248,9 +270,9 @@ __global__ void k_ghost_fill(const GfGeom G, const GfView V, int only_accepted,
     // enumerate ghost cells: the two bottom rows, the two top rows, then the
     // left and right column pairs of the interior rows
     int i, j;
-    const int band = 2 * T;
-    if (k < band) { i = k % T - GF_NG; j = k / T - GF_NG; }
-    else if (k < 2 * band) { i = (k - band) % T - GF_NG; j = M + (k - band) / T; }
+    const int band = 2 * T_;
+    if (k < band) { i = k % T_ - GF_NG; j = k / T_ - GF_NG; }
+    else if (k < 2 * band) { i = (k - band) % T_ - GF_NG; j = M + (k - band) / T_; }
     else {
       const int r = k - 2 * band;  // 4 * M cells
       j = r / 4;
@@ -260,15 +282,14 @@ __global__ void k_ghost_fill(const GfGeom G, const GfView V, int only_accepted,
     const long long I = (long long)P.px * M + i, J = (long long)P.py * M + j;
     if (I < 0 || J < 0 || I >= NX || J >= NY) continue;
     const int c = e.tix(i, j);
+    const double bt = (double)bb[c];
     double out[3];
-    fill_cell(e, P.scen, P.level, I, J, bb[c], out, &err);
-    q[c] = out[0];
-    q[TT + c] = out[1];
-    q[2 * TT + c] = out[2];
+    fill_cell(e, P.scen, P.level, I, J, bt, out, &err);
+    e.store(q, c, out[0], out[1], out[2], bt);
   }
   if (err && errflag) *errflag = 1;
   __syncthreads();
-  tile_bc(e, P, q, nullptr, 0);
+  tile_bc<T>(e, P, q, nullptr, 0);
 }
 
 // ------------------------------------------------------------ topography
@@ -342,17 +363,18 @@ __device__ double dem_average(const GfScenario& S, double xa, double xb,
   return sum / ((xb - xa) * (yb - ya));
 }
 
+template <typename T>
 __global__ void k_topo(const GfGeom G, const GfView V, int first) {
   const int p = first + blockIdx.x;
   const GfPatch P = V.patch[p];
-  Geo e(G, V);
-  const int M = G.M, T = G.T, TT = T * T;
-  double* b = V.b + (size_t)p * TT;
+  Geo<T> e(G, V);
+  const int M = G.M, T_ = G.T, TT = T_ * T_;
+  T* b = e.bp(p);
   const GfScenario S = V.scen[P.scen];
   const long long NX = e.nx(P.level), NY = e.ny(P.level);
   const double dx = e.dx(P.level), dy = e.dy(P.level);
   for (int k = threadIdx.x; k < TT; k += blockDim.x) {
-    const int i = k % T - GF_NG, j = k / T - GF_NG;
+    const int i = k % T_ - GF_NG, j = k / T_ - GF_NG;
     const long long I = (long long)P.px * M + i, J = (long long)P.py * M + j;
     double v = 0.0;
     if (I >= 0 && J >= 0 && I < NX && J < NY && S.dem) {
@@ -362,58 +384,70 @@ __global__ void k_topo(const GfGeom G, const GfView V, int first) {
       const double yb = G.ylower + (double)(J + 1) * dy;
       v = dem_average(S, xa, xb, ya, yb);
     }
-    b[k] = v;
+    // the deviation form keeps the bed relative to the reference surface
+    b[k] = Geo<T>::DEV ? (T)(v - S.eta0) : (T)v;
   }
   __syncthreads();
-  tile_bc(e, P, nullptr, b, 1);
+  tile_bc<T>(e, P, nullptr, b, 1);
 }
 
 // Regrid transfer: every interior cell of every new patch from the old
-// forest by the ghost-cell operators (copy, average, interpolation).
+// forest by the ghost-cell operators (copy, average, interpolation).  The
+// FP32 compensation terms of new cells start at zero.
+template <typename T>
 __global__ void k_regrid_fill(const GfGeom G, const GfView O, const GfView N,
                               int* errflag) {
   const int p = blockIdx.x;
   const GfPatch P = N.patch[p];
-  Geo eo(G, O);
-  const int M = G.M, T = G.T, TT = T * T;
+  Geo<T> eo(G, O), en(G, N);
+  const int M = G.M, T_ = G.T;
   const int dst = 1 - O.ctl[P.scen].cur;
-  double* q = N.q[dst] + (size_t)p * 3 * TT;
-  const double* bn = N.b + (size_t)p * TT;
+  T* q = en.qp(p, dst);
+  const T* bn = en.bp(p);
   int err = 0;
   for (int k = threadIdx.x; k < M * M; k += blockDim.x) {
     const int i = k % M, j = k / M;
     const long long I = (long long)P.px * M + i, J = (long long)P.py * M + j;
-    const int c = (i + GF_NG) + (j + GF_NG) * T;
+    const int c = (i + GF_NG) + (j + GF_NG) * T_;
+    const double bt = (double)bn[c];
     double out[3];
-    fill_cell(eo, P.scen, P.level, I, J, bn[c], out, &err);
-    q[c] = out[0];
-    q[TT + c] = out[1];
-    q[2 * TT + c] = out[2];
+    fill_cell(eo, P.scen, P.level, I, J, bt, out, &err);
+    en.store(q, c, out[0], out[1], out[2], bt);
+    if constexpr (Geo<T>::DEV) {
+      float* lo = N.lof[dst] + (size_t)p * 3 * M * M;
+      lo[k] = 0.0f;
+      lo[M * M + k] = 0.0f;
+      lo[2 * M * M + k] = 0.0f;
+    }
   }
   if (err && errflag) *errflag = 1;
 }
 
 // Plain tagger (Sec. 4.1 criteria 1, 3, 4; Sec. 6.4).
+template <typename T>
 __global__ void k_tags(const GfGeom G, const GfView V, uint8_t* flags) {
   const int p = blockIdx.x;
   const GfPatch P = V.patch[p];
-  Geo e(G, V);
-  const int M = G.M, T = G.T, TT = T * T;
-  const double* q = V.q[V.ctl[P.scen].cur] + (size_t)p * 3 * TT;
-  const double* b = V.b + (size_t)p * TT;
+  Geo<T> e(G, V);
+  const int M = G.M;
+  const int cur = V.ctl[P.scen].cur;
   const GfScenario S = V.scen[P.scen];
   const double dx = e.dx(P.level), dy = e.dy(P.level);
+  // surfaces are compared with eta0; the deviation form stores them relative
+  const double eref = Geo<T>::DEV ? 0.0 : S.eta0;
   int m = 0;
   for (int k = threadIdx.x; k < M * M; k += blockDim.x) {
     const int i = k % M, j = k / M;
     const int c = e.tix(i, j);
-    const double h = q[c];
+    double v4[4];
+    e.load(p, cur, c, v4);
+    const double h = v4[0];
     int r = 0;
     if (h > G.tag_depth) {
-      const double u = q[TT + c] / h, v = q[2 * TT + c] / h;
+      const double u = v4[1] / h, v = v4[2] / h;
       const double sp = sqrt(u * u + v * v);
-      const double eta = h + b[c];
-      if (sp > G.tag_speed || fabs(eta - S.eta0) > G.tag_deta) r = 2;
+      const double eta = h + v4[3];
+      if (sp > G.tag_speed || fabs(eta - eref) > G.tag_deta) r = 2;
     }
     const double xc = G.xlower + ((double)((long long)P.px * M + i) + 0.5) * dx;
     const double yc = G.ylower + ((double)((long long)P.py * M + j) + 0.5) * dy;
@@ -441,6 +475,7 @@ __global__ void k_tags(const GfGeom G, const GfView V, uint8_t* flags) {
 
 // Gauges (Sec. 5.1 control points, Sec. 6.5): bilinear in the finest leaf,
 // ghosts included; arrival at the first sample with h > 1 cm.
+template <typename T>
 __global__ void k_gauges(const GfGeom G, const GfView V, int only_accepted) {
   const int s = blockIdx.y;
   const GfScenario S = V.scen[s];
@@ -448,7 +483,7 @@ __global__ void k_gauges(const GfGeom G, const GfView V, int only_accepted) {
   if (g >= S.ngauge) return;
   const GfCtl* C = V.ctl + s;
   if (only_accepted && !C->accepted) return;
-  Geo e(G, V);
+  Geo<T> e(G, V);
   const double x = S.gxy[2 * g], y = S.gxy[2 * g + 1];
   int p = -1, L = 0;
   for (int l = G.maxlevel; l >= 0 && p < 0; --l) {
@@ -468,7 +503,7 @@ __global__ void k_gauges(const GfGeom G, const GfView V, int only_accepted) {
   o[0] = C->t;
   if (p < 0) { o[1] = o[2] = o[3] = o[4] = 0.0; return; }
   const GfPatch P = V.patch[p];
-  const int M = G.M, TT = G.T * G.T;
+  const int M = G.M;
   const double fx = (x - G.xlower) / e.dx(L) - 0.5 - (double)((long long)P.px * M);
   const double fy = (y - G.ylower) / e.dy(L) - 0.5 - (double)((long long)P.py * M);
   int i0 = (int)floor(fx), j0 = (int)floor(fy);
@@ -477,36 +512,42 @@ __global__ void k_gauges(const GfGeom G, const GfView V, int only_accepted) {
   if (i0 > M - 1) i0 = M - 1;
   if (j0 > M - 1) j0 = M - 1;
   const double ax = fx - (double)i0, ay = fy - (double)j0;
-  const double* q = V.q[C->cur] + (size_t)p * 3 * TT;
-  const double* b = V.b + (size_t)p * TT;
-  const int c00 = e.tix(i0, j0), c10 = e.tix(i0 + 1, j0);
-  const int c01 = e.tix(i0, j0 + 1), c11 = e.tix(i0 + 1, j0 + 1);
+  double c4[4][4];
+  e.load(p, C->cur, e.tix(i0, j0), c4[0]);
+  e.load(p, C->cur, e.tix(i0 + 1, j0), c4[1]);
+  e.load(p, C->cur, e.tix(i0, j0 + 1), c4[2]);
+  e.load(p, C->cur, e.tix(i0 + 1, j0 + 1), c4[3]);
+  const double eoff = Geo<T>::DEV ? S.eta0 : 0.0;
   double v[4];
   for (int f = 0; f < 4; ++f) {
     double a00, a10, a01, a11;
     if (f < 3) {
-      a00 = q[f * TT + c00]; a10 = q[f * TT + c10];
-      a01 = q[f * TT + c01]; a11 = q[f * TT + c11];
+      a00 = c4[0][f]; a10 = c4[1][f]; a01 = c4[2][f]; a11 = c4[3][f];
     } else {
-      a00 = q[c00] + b[c00]; a10 = q[c10] + b[c10];
-      a01 = q[c01] + b[c01]; a11 = q[c11] + b[c11];
+      a00 = c4[0][0] + c4[0][3]; a10 = c4[1][0] + c4[1][3];
+      a01 = c4[2][0] + c4[2][3]; a11 = c4[3][0] + c4[3][3];
     }
     v[f] = (1.0 - ay) * ((1.0 - ax) * a00 + ax * a10) +
            ay * ((1.0 - ax) * a01 + ax * a11);
   }
-  o[1] = v[0]; o[2] = v[1]; o[3] = v[2]; o[4] = v[3];
+  o[1] = v[0]; o[2] = v[1]; o[3] = v[2]; o[4] = v[3] + eoff;
   if (S.garr[g] < 0.0 && v[0] > 0.01) S.garr[g] = C->t;
 }
 
 // Volume per patch (fixed-order block tree), then per scenario.
+template <typename T>
 __global__ void k_patch_mass(const GfGeom G, const GfView V, double* pmass) {
   const int p = blockIdx.x;
   const GfPatch P = V.patch[p];
-  Geo e(G, V);
-  const int M = G.M, TT = G.T * G.T;
-  const double* q = V.q[V.ctl[P.scen].cur] + (size_t)p * 3 * TT;
+  Geo<T> e(G, V);
+  const int M = G.M;
+  const int cur = V.ctl[P.scen].cur;
   double v = 0.0;
-  for (int k = threadIdx.x; k < M * M; k += blockDim.x) v += q[e.tix(k % M, k / M)];
+  for (int k = threadIdx.x; k < M * M; k += blockDim.x) {
+    double c4[4];
+    e.load(p, cur, e.tix(k % M, k / M), c4);
+    v += c4[0];
+  }
   __shared__ double red[256];
   red[threadIdx.x] = v;
   __syncthreads();
@@ -534,32 +575,48 @@ __global__ void k_scen_mass(const GfScenario* sc, const double* pmass,
 }
 
 // Staging between tiles and dense field-major interior arrays
-// [field][count][M][M] (fields h, hu, hv, b for packing; h, hu, hv for
-// unpacking).
+// [field][count][M][M] in FP64: fields h, hu, hv, b for packing; h, hu, hv
+// for unpacking (the deviation form converts w = h + b - eta0 and clears the
+// compensation terms).
+template <typename T>
 __global__ void k_pack(const GfGeom G, const GfView V, int first, double* out,
                        int cur) {
   const int p = first + blockIdx.x;
-  const int M = G.M, T = G.T, TT = T * T, MM = M * M;
+  Geo<T> e(G, V);
+  const int M = G.M, MM = M * M;
   const size_t plane = (size_t)gridDim.x * MM;
-  const double* q = V.q[cur] + (size_t)p * 3 * TT;
-  const double* b = V.b + (size_t)p * TT;
-  for (int k = threadIdx.x; k < 4 * MM; k += blockDim.x) {
-    const int f = k / MM, r = k % MM;
-    const int c = (r % M + GF_NG) + (r / M + GF_NG) * T;
-    out[f * plane + (size_t)blockIdx.x * MM + r] = f < 3 ? q[f * TT + c] : b[c];
+  const double eoff = Geo<T>::DEV ? V.scen[V.patch[p].scen].eta0 : 0.0;
+  for (int k = threadIdx.x; k < MM; k += blockDim.x) {
+    const int c = (k % M + GF_NG) + (k / M + GF_NG) * G.T;
+    double c4[4];
+    e.load(p, cur, c, c4);
+    const size_t o = (size_t)blockIdx.x * MM + k;
+    out[o] = c4[0];
+    out[plane + o] = c4[1];
+    out[2 * plane + o] = c4[2];
+    out[3 * plane + o] = c4[3] + eoff;
   }
 }
 
+template <typename T>
 __global__ void k_unpack(const GfGeom G, const GfView V, int first,
                          const double* in, int cur) {
   const int p = first + blockIdx.x;
-  const int M = G.M, T = G.T, TT = T * T, MM = M * M;
+  Geo<T> e(G, V);
+  const int M = G.M, MM = M * M;
   const size_t plane = (size_t)gridDim.x * MM;
-  double* q = V.q[cur] + (size_t)p * 3 * TT;
-  for (int k = threadIdx.x; k < 3 * MM; k += blockDim.x) {
-    const int f = k / MM, r = k % MM;
-    const int c = (r % M + GF_NG) + (r / M + GF_NG) * T;
-    q[f * TT + c] = in[f * plane + (size_t)blockIdx.x * MM + r];
+  T* q = e.qp(p, cur);
+  const T* b = e.bp(p);
+  for (int k = threadIdx.x; k < MM; k += blockDim.x) {
+    const int c = (k % M + GF_NG) + (k / M + GF_NG) * G.T;
+    const size_t o = (size_t)blockIdx.x * MM + k;
+    e.store(q, c, in[o], in[plane + o], in[2 * plane + o], (double)b[c]);
+    if constexpr (Geo<T>::DEV) {
+      float* lo = V.lof[cur] + (size_t)p * 3 * MM;
+      lo[k] = 0.0f;
+      lo[MM + k] = 0.0f;
+      lo[2 * MM + k] = 0.0f;
+    }
   }
 }
 
@@ -574,30 +631,36 @@ static int* g_errflag = nullptr;
 int launch_ghost_fill(const GfGeom& g, const GfView& v, int only_accepted,
                       void* stream) {
   if (v.npatch <= 0) return 0;
-  k_ghost_fill<<<v.npatch, 128, 0, static_cast<cudaStream_t>(stream)>>>(
-      g, v, only_accepted, g_errflag);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (v.prec) k_ghost_fill<float><<<v.npatch, 128, 0, st>>>(g, v, only_accepted, g_errflag);
+  else k_ghost_fill<double><<<v.npatch, 128, 0, st>>>(g, v, only_accepted, g_errflag);
   return ok();
 }
 
 int launch_topo(const GfGeom& g, const GfView& v, int first, int count,
                 void* stream) {
   if (count <= 0) return 0;
-  k_topo<<<count, 128, 0, static_cast<cudaStream_t>(stream)>>>(g, v, first);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (v.prec) k_topo<float><<<count, 128, 0, st>>>(g, v, first);
+  else k_topo<double><<<count, 128, 0, st>>>(g, v, first);
   return ok();
 }
 
 int launch_regrid_fill(const GfGeom& g, const GfView& oldv, const GfView& newv,
                        void* stream) {
   if (newv.npatch <= 0) return 0;
-  k_regrid_fill<<<newv.npatch, 256, 0, static_cast<cudaStream_t>(stream)>>>(
-      g, oldv, newv, g_errflag);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (newv.prec) k_regrid_fill<float><<<newv.npatch, 256, 0, st>>>(g, oldv, newv, g_errflag);
+  else k_regrid_fill<double><<<newv.npatch, 256, 0, st>>>(g, oldv, newv, g_errflag);
   return ok();
 }
 
 int launch_tags(const GfGeom& g, const GfView& v, uint8_t* flags,
                 void* stream) {
   if (v.npatch <= 0) return 0;
-  k_tags<<<v.npatch, 256, 0, static_cast<cudaStream_t>(stream)>>>(g, v, flags);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (v.prec) k_tags<float><<<v.npatch, 256, 0, st>>>(g, v, flags);
+  else k_tags<double><<<v.npatch, 256, 0, st>>>(g, v, flags);
   return ok();
 }
 
@@ -605,15 +668,19 @@ int launch_gauges(const GfGeom& g, const GfView& v, int only_accepted,
                   int max_gauges, void* stream) {
   if (max_gauges <= 0) return 0;
   dim3 grid((max_gauges + 63) / 64, g.nscen);
-  k_gauges<<<grid, 64, 0, static_cast<cudaStream_t>(stream)>>>(g, v,
-                                                              only_accepted);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (v.prec) k_gauges<float><<<grid, 64, 0, st>>>(g, v, only_accepted);
+  else k_gauges<double><<<grid, 64, 0, st>>>(g, v, only_accepted);
   return ok();
 }
 
 int launch_mass(const GfGeom& g, const GfView& v, double* pmass,
                 double* smass, int nscen, void* stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (v.npatch > 0) k_patch_mass<<<v.npatch, 256, 0, st>>>(g, v, pmass);
+  if (v.npatch > 0) {
+    if (v.prec) k_patch_mass<float><<<v.npatch, 256, 0, st>>>(g, v, pmass);
+    else k_patch_mass<double><<<v.npatch, 256, 0, st>>>(g, v, pmass);
+  }
   k_scen_mass<<<nscen, 256, 0, st>>>(v.scen, pmass, smass);
   return ok();
 }
@@ -623,8 +690,9 @@ int launch_pack_interior(const GfGeom& g, const GfView& v, int first,
                          void* stream) {
   (void)field_mask;
   if (count <= 0) return 0;
-  k_pack<<<count, 256, 0, static_cast<cudaStream_t>(stream)>>>(g, v, first,
-                                                              out, cur);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (v.prec) k_pack<float><<<count, 256, 0, st>>>(g, v, first, out, cur);
+  else k_pack<double><<<count, 256, 0, st>>>(g, v, first, out, cur);
   return ok();
 }
 
@@ -632,8 +700,9 @@ int launch_unpack_interior(const GfGeom& g, const GfView& v, int first,
                            int count, const double* in, int cur,
                            void* stream) {
   if (count <= 0) return 0;
-  k_unpack<<<count, 256, 0, static_cast<cudaStream_t>(stream)>>>(g, v, first,
-                                                                in, cur);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (v.prec) k_unpack<float><<<count, 256, 0, st>>>(g, v, first, in, cur);
+  else k_unpack<double><<<count, 256, 0, st>>>(g, v, first, in, cur);
   return ok();
 }
 

@@ -31,6 +31,10 @@ struct geoflood_ctx {
   int cap = 0, nscen = 0, npatch = 0;
   double* q[2] = {nullptr, nullptr};
   double* b[2] = {nullptr, nullptr};
+  float* qf[2] = {nullptr, nullptr};  // FP32 surface-deviation state
+  float* bf[2] = {nullptr, nullptr};
+  float* lof[2] = {nullptr, nullptr};
+  int prec = 0;
   int bsel = 0;
   GfPatch* d_patch[2] = {nullptr, nullptr};
   int* d_lut[2] = {nullptr, nullptr};
@@ -90,7 +94,13 @@ GfView view(geoflood_ctx* c, int t, int bb) {
   v.q[0] = c->q[0];
   v.q[1] = c->q[1];
   v.b = c->b[bb];
+  v.qf[0] = c->qf[0];
+  v.qf[1] = c->qf[1];
+  v.bf = c->bf[bb];
+  v.lof[0] = c->lof[0];
+  v.lof[1] = c->lof[1];
   v.npatch = c->npatch;
+  v.prec = c->prec;
   return v;
 }
 GfView view(geoflood_ctx* c) { return view(c, c->tsel, c->bsel); }
@@ -235,7 +245,8 @@ int geoflood_init_forest(const geoflood_config* cfg, void* stream,
       c.num_scenarios < 1 || c.max_patches < 1 || c.max_gauges < 0 ||
       !(c.xupper > c.xlower) || !(c.yupper > c.ylower) || !(c.g > 0) ||
       !(c.drytol > 0) || !(c.cfl_desired > 0) || !(c.cfl_max >= c.cfl_desired) ||
-      !(c.dt_initial > 0) || !(c.dt_max > 0) || c.precision != GEOFLOOD_FP64)
+      !(c.dt_initial > 0) || !(c.dt_max > 0) ||
+      (c.precision != GEOFLOOD_FP64 && c.precision != GEOFLOOD_FP32_DEV))
     return GEOFLOOD_ERR_ARG;
   for (int k = 0; k < 4; ++k)
     if (c.bc[k] != GEOFLOOD_BC_WALL && c.bc[k] != GEOFLOOD_BC_EXTRAP)
@@ -269,10 +280,21 @@ int geoflood_init_forest(const geoflood_config* cfg, void* stream,
     return cudaMalloc(p, bytes) == cudaSuccess;
   };
   bool okk = true;
-  okk &= alloc((void**)&ctx->q[0], cap * 3 * TT * sizeof(double));
-  okk &= alloc((void**)&ctx->q[1], cap * 3 * TT * sizeof(double));
-  okk &= alloc((void**)&ctx->b[0], cap * TT * sizeof(double));
-  okk &= alloc((void**)&ctx->b[1], cap * TT * sizeof(double));
+  ctx->prec = c.precision == GEOFLOOD_FP32_DEV ? 1 : 0;
+  const size_t MM = (size_t)G.M * G.M;
+  if (ctx->prec) {
+    okk &= alloc((void**)&ctx->qf[0], cap * 3 * TT * sizeof(float));
+    okk &= alloc((void**)&ctx->qf[1], cap * 3 * TT * sizeof(float));
+    okk &= alloc((void**)&ctx->bf[0], cap * TT * sizeof(float));
+    okk &= alloc((void**)&ctx->bf[1], cap * TT * sizeof(float));
+    okk &= alloc((void**)&ctx->lof[0], cap * 3 * MM * sizeof(float));
+    okk &= alloc((void**)&ctx->lof[1], cap * 3 * MM * sizeof(float));
+  } else {
+    okk &= alloc((void**)&ctx->q[0], cap * 3 * TT * sizeof(double));
+    okk &= alloc((void**)&ctx->q[1], cap * 3 * TT * sizeof(double));
+    okk &= alloc((void**)&ctx->b[0], cap * TT * sizeof(double));
+    okk &= alloc((void**)&ctx->b[1], cap * TT * sizeof(double));
+  }
   okk &= alloc((void**)&ctx->d_patch[0], cap * sizeof(GfPatch));
   okk &= alloc((void**)&ctx->d_patch[1], cap * sizeof(GfPatch));
   okk &= alloc((void**)&ctx->d_lut[0], (size_t)ctx->nscen * G.lut_per_scen * sizeof(int));
@@ -303,8 +325,13 @@ int geoflood_init_forest(const geoflood_config* cfg, void* stream,
   for (int s = 0; s < ctx->nscen; ++s) ctx->h_ctl[s].dt_next = c.dt_initial;
   int rc = 0;
   do {
-    if (cudaMemsetAsync(ctx->q[0], 0, cap * 3 * TT * sizeof(double), ctx->st) ||
-        cudaMemsetAsync(ctx->q[1], 0, cap * 3 * TT * sizeof(double), ctx->st) ||
+    const size_t qbytes = cap * 3 * TT * (ctx->prec ? sizeof(float) : sizeof(double));
+    void* q0 = ctx->prec ? (void*)ctx->qf[0] : (void*)ctx->q[0];
+    void* q1 = ctx->prec ? (void*)ctx->qf[1] : (void*)ctx->q[1];
+    if (cudaMemsetAsync(q0, 0, qbytes, ctx->st) ||
+        cudaMemsetAsync(q1, 0, qbytes, ctx->st) ||
+        (ctx->prec && (cudaMemsetAsync(ctx->lof[0], 0, cap * 3 * MM * sizeof(float), ctx->st) ||
+                       cudaMemsetAsync(ctx->lof[1], 0, cap * 3 * MM * sizeof(float), ctx->st))) ||
         cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->st)) {
       rc = GEOFLOOD_ERR_CUDA;
       break;
@@ -333,6 +360,9 @@ void geoflood_destroy(geoflood_ctx* ctx) {
   for (int k = 0; k < 2; ++k) {
     cudaFree(ctx->q[k]);
     cudaFree(ctx->b[k]);
+    cudaFree(ctx->qf[k]);
+    cudaFree(ctx->bf[k]);
+    cudaFree(ctx->lof[k]);
     cudaFree(ctx->d_patch[k]);
     cudaFree(ctx->d_lut[k]);
   }
@@ -356,19 +386,41 @@ const char* geoflood_last_error(const geoflood_ctx* ctx) {
   return ctx ? ctx->err.c_str() : "null context";
 }
 
+// In the deviation form the stored surface w = h + b - eta0 depends on the
+// bed and eta0: changing either keeps the depths by reading them out before
+// and writing them back after.
+static int keep_depths(geoflood_ctx* ctx, int s, std::vector<double>& h,
+                       std::vector<double>& hu, std::vector<double>& hv) {
+  const size_t plane = (size_t)ctx->h_scen[s].pcount * ctx->G.M * ctx->G.M;
+  h.resize(plane);
+  hu.resize(plane);
+  hv.resize(plane);
+  return geoflood_read_patches(ctx, s, h.data(), hu.data(), hv.data(), nullptr);
+}
+
 int geoflood_set_scenario(geoflood_ctx* ctx, int s, double manning_n,
                           double eta0) {
   if (!valid_scen(ctx, s) || !(manning_n >= 0))
     return fail(ctx, GEOFLOOD_ERR_ARG, "set_scenario: bad argument");
+  std::vector<double> h, hu, hv;
+  int rc = 0;
+  const bool moved = ctx->prec && eta0 != ctx->h_scen[s].eta0;
+  if (moved && (rc = keep_depths(ctx, s, h, hu, hv))) return rc;
   ctx->h_scen[s].manning_n = manning_n;
   ctx->h_scen[s].eta0 = eta0;
-  return upload_scen(ctx);
+  if ((rc = upload_scen(ctx))) return rc;
+  if (!moved) return 0;
+  if ((rc = topo_scenario(ctx, s))) return rc;
+  return geoflood_write_patches(ctx, s, h.data(), hu.data(), hv.data());
 }
 
 int geoflood_set_topo(geoflood_ctx* ctx, int s, const double* z, int nx,
                       int ny, double x0, double y0, double dx, double dy) {
   if (!valid_scen(ctx, s) || !z || nx < 2 || ny < 2 || !(dx > 0) || !(dy > 0))
     return fail(ctx, GEOFLOOD_ERR_ARG, "set_topo: bad argument");
+  std::vector<double> h, hu, hv;
+  int rc = 0;
+  if (ctx->prec && (rc = keep_depths(ctx, s, h, hu, hv))) return rc;
   if (ctx->d_dem[s]) cudaFree(ctx->d_dem[s]);
   ctx->d_dem[s] = nullptr;
   const size_t n = (size_t)nx * ny;
@@ -379,9 +431,10 @@ int geoflood_set_topo(geoflood_ctx* ctx, int s, const double* z, int nx,
   GfScenario& S = ctx->h_scen[s];
   S.dem = ctx->d_dem[s];
   S.dnx = nx; S.dny = ny; S.dx0 = x0; S.dy0 = y0; S.ddx = dx; S.ddy = dy;
-  int rc = upload_scen(ctx);
+  rc = upload_scen(ctx);
   if (rc) return rc;
   if ((rc = topo_scenario(ctx, s))) return rc;
+  if (ctx->prec) return geoflood_write_patches(ctx, s, h.data(), hu.data(), hv.data());
   return ghost_fill_all(ctx);
 }
 
@@ -452,15 +505,35 @@ int geoflood_read_tiles(geoflood_ctx* ctx, int s, double* out) {
   if (rc) return rc;
   const size_t TT = (size_t)ctx->G.T * ctx->G.T;
   const int off = ctx->h_scen[s].poff, n = ctx->h_scen[s].pcount;
-  const double* q = ctx->q[ctx->h_ctl[s].cur];
-  for (int k = 0; k < n; ++k) {
-    CK(cudaMemcpyAsync(out + (size_t)k * 4 * TT, q + (size_t)(off + k) * 3 * TT,
-                       3 * TT * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
-    CK(cudaMemcpyAsync(out + (size_t)k * 4 * TT + 3 * TT,
-                       ctx->b[ctx->bsel] + (size_t)(off + k) * TT,
-                       TT * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  const int cur = ctx->h_ctl[s].cur;
+  if (!ctx->prec) {
+    for (int k = 0; k < n; ++k) {
+      CK(cudaMemcpyAsync(out + (size_t)k * 4 * TT, ctx->q[cur] + (size_t)(off + k) * 3 * TT,
+                         3 * TT * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+      CK(cudaMemcpyAsync(out + (size_t)k * 4 * TT + 3 * TT,
+                         ctx->b[ctx->bsel] + (size_t)(off + k) * TT,
+                         TT * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    }
+    CK(cudaStreamSynchronize(ctx->st));
+    return 0;
   }
+  // deviation form: h = w - b exactly, b = (b - eta0) + eta0
+  std::vector<float> qh((size_t)n * 3 * TT), bh((size_t)n * TT);
+  CK(cudaMemcpyAsync(qh.data(), ctx->qf[cur] + (size_t)off * 3 * TT,
+                     qh.size() * sizeof(float), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(bh.data(), ctx->bf[ctx->bsel] + (size_t)off * TT,
+                     bh.size() * sizeof(float), cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
+  const double e0 = ctx->h_scen[s].eta0;
+  for (int k = 0; k < n; ++k)
+    for (size_t c = 0; c < TT; ++c) {
+      const double b = (double)bh[(size_t)k * TT + c];
+      double* o = out + (size_t)k * 4 * TT;
+      o[c] = (double)qh[(size_t)k * 3 * TT + c] - b;
+      o[TT + c] = (double)qh[(size_t)k * 3 * TT + TT + c];
+      o[2 * TT + c] = (double)qh[(size_t)k * 3 * TT + 2 * TT + c];
+      o[3 * TT + c] = b + e0;
+    }
   return 0;
 }
 
@@ -535,7 +608,9 @@ int geoflood_step(geoflood_ctx* ctx, double t_target, int max_steps,
     for (int it = 0; it < k; ++it) {
       ProfRec r;
       prof_begin(ctx, "patch_step", &r);
-      CKL(gf::launch_patch_step_f64(ctx->G, v, ctx->d_pmass, ctx->st), "patch_step");
+      CKL(ctx->prec ? gf::launch_patch_step_f32(ctx->G, v, ctx->d_pmass, ctx->st)
+                    : gf::launch_patch_step_f64(ctx->G, v, ctx->d_pmass, ctx->st),
+          "patch_step");
       prof_end(ctx, "patch_step", &r);
       prof_begin(ctx, "controller", &r);
       CKL(gf::launch_controller(ctx->G, v, ctx->d_pmass, ctx->nscen, ctx->st), "controller");

@@ -71,15 +71,20 @@ struct GfView {
   const int* lut;         // per scenario, per level: patch index or -1
   GfScenario* scen;       // [nscen]
   GfCtl* ctl;             // [nscen]
-  double* q[2];           // state buffers [cap][3][T][T]
-  double* b;              // beds [cap][T][T]
+  double* q[2];           // FP64 state buffers [cap][3][T][T]: h, hu, hv
+  double* b;              // FP64 beds [cap][T][T]
+  float* qf[2];           // FP32 state [cap][3][T][T]: w = h + b - eta0, hu, hv
+  float* bf;              // FP32 beds minus eta0 [cap][T][T]
+  float* lof[2];          // FP32 compensation terms [cap][3][M][M]
   int npatch;
-  int pad;
+  int prec;               // 0 = FP64, 1 = FP32 surface deviation
 };
 
 // Kernel launchers (defined in the .cu files).
 namespace gf {
 int launch_patch_step_f64(const GfGeom& g, const GfView& v, double* pmass,
+                          void* stream);
+int launch_patch_step_f32(const GfGeom& g, const GfView& v, double* pmass,
                           void* stream);
 int launch_controller(const GfGeom& g, const GfView& v, const double* pmass,
                       int nscen, void* stream);

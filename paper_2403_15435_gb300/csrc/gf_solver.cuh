@@ -12,6 +12,8 @@ namespace gfk {
 template <typename R>
 struct Side {
   R h, n, t, b;  // depth, normal momentum, transverse momentum, bed
+  R w;           // surface-deviation form only: stored surface h + b - eta0
+  bool wet;      // surface-deviation form only: exact wet test of the cell
 };
 
 template <typename R>
@@ -26,14 +28,21 @@ __device__ __forceinline__ R rmax(R a, R b) { return a > b ? a : b; }
 // fan is negative.  Acoustic speeds: Einfeldt (HLLE) with Roe averages, or
 // the dam-break front speeds at a wet/dry edge.  A dry cell whose bed is
 // above the wet surface is tested with the mirrored (reflecting) problem.
-template <typename R>
+//
+// DEV = false: plain form, the state is (h, n, t) and the bed b; the wet test
+// is h > drytol and the surface jump is formed from depths and beds.
+// DEV = true: surface-deviation form, each side also carries its stored
+// surface w = h + b - eta0 (b is then the bed minus eta0) and a wet flag
+// decided exactly from the stored values; the surface jump is the difference
+// of the stored surfaces, so a lake at rest gives exactly zero waves.
+template <typename R, bool DEV = false>
 __device__ __forceinline__ void riemann(Side<R> l, Side<R> r, R g, R drytol,
                                         R (&Z)[9], R (&s)[3]) {
 #pragma unroll
   for (int k = 0; k < 9; ++k) Z[k] = R(0);
   s[0] = s[1] = s[2] = R(0);
-  const bool wetl = l.h > drytol;
-  const bool wetr = r.h > drytol;
+  const bool wetl = DEV ? l.wet : (l.h > drytol);
+  const bool wetr = DEV ? r.wet : (r.h > drytol);
   if (!wetl && !wetr) return;
   // surface depths: a dry cell keeps its stored depth in its surface so a
   // still shoreline stays at rest; fluxes and speeds see zero depth
@@ -42,25 +51,31 @@ __device__ __forceinline__ void riemann(Side<R> l, Side<R> r, R g, R drytol,
   if (!wetr) { r.h = R(0); r.n = R(0); r.t = R(0); }
 
   int wall = 0;  // +1: right side is a wall, -1: left side is a wall
-  if (!wetr && r.b > l.h + l.b) {
+  if (!wetr && (DEV ? r.b > l.w : r.b > l.h + l.b)) {
     const R u = l.n / l.h;
     const R c = sqrt(g * l.h);
     const R sw = rmax(c - u, c);       // fastest wave of the mirrored problem
     const R hm = l.h + l.n / sw;       // its HLL middle depth
     if (r.b >= l.b + hm) {
       wall = 1;
-      r.h = l.h; r.n = -l.n; r.t = l.t; r.b = l.b; er = l.h;
+      r.h = l.h; r.n = -l.n; r.t = l.t; r.b = l.b; er = l.h; r.w = l.w;
+    } else if (DEV) {
+      r.w = l.w + er;                  // overtopped: step lowered to surface
+      r.b = l.w;
     } else {
-      r.b = l.h + l.b;                 // overtopped: step lowered to surface
+      r.b = l.h + l.b;
     }
-  } else if (!wetl && l.b > r.h + r.b) {
+  } else if (!wetl && (DEV ? l.b > r.w : l.b > r.h + r.b)) {
     const R u = r.n / r.h;
     const R c = sqrt(g * r.h);
     const R sw = rmax(u + c, c);
     const R hm = r.h - r.n / sw;
     if (l.b >= r.b + hm) {
       wall = -1;
-      l.h = r.h; l.n = -r.n; l.t = r.t; l.b = r.b; el = r.h;
+      l.h = r.h; l.n = -r.n; l.t = r.t; l.b = r.b; el = r.h; l.w = r.w;
+    } else if (DEV) {
+      l.w = r.w + el;
+      l.b = r.w;
     } else {
       l.b = r.h + r.b;
     }
@@ -90,7 +105,7 @@ __device__ __forceinline__ void riemann(Side<R> l, Side<R> r, R g, R drytol,
 
   const R hbar = R(0.5) * (l.h + r.h);
   const R db = r.b - l.b;
-  const R deta = (er + r.b) - (el + l.b);
+  const R deta = DEV ? r.w - l.w : (er + r.b) - (el + l.b);
   const R den = s3 - s1;
   const R dn = r.n - l.n;
   const R hhll = (s3 * r.h - s1 * l.h - dn) / den;
@@ -200,17 +215,20 @@ __device__ __forceinline__ void edge_fluxes(const R* Z, const R* S,
 
 // Transverse split of an increment d = (mass, momentum along the split
 // direction, other momentum) in a cell with depth h, momenta ma (along) and
-// mo (other), bed b: eigenvectors of the split direction's Jacobian with
-// speeds w - c, w, w + c.  plus/minus are returned in the same frame.  A part
-// entering a dry neighbour (depth hn <= drytol) whose bed is above the cell's
-// surface is dropped; a dry cell splits nothing.
+// mo (other): eigenvectors of the split direction's Jacobian with speeds
+// w - c, w, w + c.  plus/minus are returned in the same frame.  A part
+// entering a dry neighbour whose bed is above the cell's surface is dropped;
+// a dry cell splits nothing.  Wet tests and the surface come from the caller:
+// wet, wetm, wetp for the cell and its neighbours at -1 and +1, eta the
+// cell's surface, bm, bp the neighbours' beds (same datum as eta).
 template <typename R>
-__device__ __forceinline__ void tsplit(R h, R ma, R mo, R b, R hm, R bm, R hp,
-                                       R bp, const R (&d)[3], R g, R drytol,
-                                       R (&plus)[3], R (&minus)[3]) {
+__device__ __forceinline__ void tsplit(R h, R ma, R mo, R eta, bool wet,
+                                       bool wetm, R bm, bool wetp, R bp,
+                                       const R (&d)[3], R g, R (&plus)[3],
+                                       R (&minus)[3]) {
   plus[0] = plus[1] = plus[2] = R(0);
   minus[0] = minus[1] = minus[2] = R(0);
-  if (!(h > drytol)) return;
+  if (!wet) return;
   const R w = ma / h;
   const R z = mo / h;
   const R c = sqrt(g * h);
@@ -222,9 +240,8 @@ __device__ __forceinline__ void tsplit(R h, R ma, R mo, R b, R hm, R bm, R hp,
   const R W1[3] = {c1, c1 * l1, c1 * z};
   const R W3[3] = {c3, c3 * l3, c3 * z};
   const R W2[3] = {R(0), R(0), c2};
-  const R eta = h + b;
-  const bool openp = !((hp <= drytol) && (bp > eta));
-  const bool openm = !((hm <= drytol) && (bm > eta));
+  const bool openp = !(!wetp && (bp > eta));
+  const bool openm = !(!wetm && (bm > eta));
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const R p1 = l1 > R(0) ? W1[k] : R(0), q1 = l1 < R(0) ? W1[k] : R(0);
@@ -233,6 +250,18 @@ __device__ __forceinline__ void tsplit(R h, R ma, R mo, R b, R hm, R bm, R hp,
     if (openp) plus[k] = (p1 + p3) + p2;
     if (openm) minus[k] = (q1 + q3) + q2;
   }
+}
+
+// Exact wet test of a stored surface-deviation cell: depth = w - b (both
+// FP32) compared with drytol as the FP64 value (w - b is exact in double).
+// FP32 decides when the rounded difference is clear of drytol by more than
+// its rounding bound; otherwise the test is redone in FP64.
+__device__ __forceinline__ bool wet_dev(float w, float b, double drytol,
+                                        float dtf, float margin) {
+  const float h = w - b;
+  if (h > dtf + margin) return true;
+  if (h < dtf - margin) return false;
+  return ((double)w - (double)b) > drytol;
 }
 
 }  // namespace gfk

@@ -1,0 +1,20 @@
+// FP32 surface-deviation patch step (instantiation of gf_step_kernel.cuh).
+// Compiled with fused multiply-add allowed: this path is checked against the
+// FP64 oracle with absolute depth and momentum tolerances, not bit for bit.
+#include <cuda_runtime.h>
+
+#include "gf_internal.h"
+#include "gf_step_kernel.cuh"
+
+namespace gf {
+
+int launch_patch_step_f32(const GfGeom& g, const GfView& v, double* pmass,
+                          void* stream) {
+  if (v.npatch <= 0) return 0;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (g.M == 32) return gfs::launch_step<gfs::PrecF32, 32, 512, 2>(g, v, pmass, st);
+  if (g.M == 16) return gfs::launch_step<gfs::PrecF32, 16, 256, 4>(g, v, pmass, st);
+  return -1;
+}
+
+}  // namespace gf

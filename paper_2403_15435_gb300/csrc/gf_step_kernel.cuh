@@ -1,0 +1,521 @@
+// The patch-step kernel, templated on the precision policy:
+//   PrecF64 -- plain FP64 state (h, hu, hv) and bed b;
+//   PrecF32 -- FP32 surface-deviation state (w = h + b - eta0, hu, hv) with
+//              FP32 compensation terms for the update, bed b - eta0, exact
+//              wet tests (FP32 with an FP64 tie-break) and FP64 volume sums.
+//
+// One CTA per patch.  The (M+4)^2 tile of the state and bed is staged in
+// shared memory by 1D TMA bulk copies; then, in barrier-separated phases:
+// every x-edge's augmented Riemann solve (Sec. 3.3), the MC-limited f-wave
+// corrections (Sec. 3.2, Eq. wpa_update_corrections), the per-cell x
+// increments and their transverse split along y (2D extension, leveque2002
+// cited in Sec. 3.2), the same for y, the unsplit update, Manning friction
+// (Eq. manning), and the per-patch CFL rate (warp-shuffle max) and volume.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "gf_internal.h"
+#include "gf_solver.cuh"
+
+namespace gfs {
+
+struct PrecF64 {
+  using R = double;
+  static constexpr bool DEV = false;
+};
+struct PrecF32 {
+  using R = float;
+  static constexpr bool DEV = true;
+};
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(count)
+               : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile(
+      "mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+          smem_addr(bar)),
+      "r"(bytes)
+      : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src,
+                                         unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes "
+      "[%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Bounded wait on phase 0 of the barrier; returns false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned limit) {
+  for (unsigned it = 0; it < limit; ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], "
+        "%2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(0u)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+template <typename R>
+__device__ __forceinline__ R warp_max(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const R w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = v > w ? v : w;
+  }
+  return v;
+}
+
+__device__ __forceinline__ double warp_sum_tree(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+template <class P, int M>
+struct Layout {
+  using R = typename P::R;
+  static constexpr int T = M + 2 * GF_NG;
+  static constexpr int TT = T * T;
+  static constexpr int NR = M + 2;  // lines swept: one ghost line each side
+  static constexpr int NE = M + 3;  // edges per line, a in [-1, M+1]
+  static constexpr int NEDGE = NR * NE;
+  static constexpr int NLIM = NR * (M + 1);   // edges a in [0, M] per line
+  static constexpr int NCELL = M * (M + 2);   // cells of the increments
+  static constexpr int NF = P::DEV ? 5 : 4;   // tile fields (+ depth)
+  // byte offsets in dynamic shared memory
+  static constexpr size_t OFF_W = sizeof(R) * NF * TT;
+  static constexpr size_t OFF_F = OFF_W + sizeof(R) * 12 * NEDGE;
+  static constexpr size_t OFF_G = OFF_F + sizeof(R) * 3 * M * (M + 1);
+  static constexpr size_t OFF_RED = align16(OFF_G + sizeof(R) * 3 * M * (M + 1));
+  static constexpr size_t OFF_WET = OFF_RED + sizeof(double) * 64;
+  static constexpr size_t OFF_BAR = align16(OFF_WET + (P::DEV ? TT : 0));
+  static constexpr size_t BYTES = OFF_BAR + 16;
+};
+
+template <int M>
+__device__ __forceinline__ int tix(int i, int j) {
+  return (i + GF_NG) + (j + GF_NG) * (M + 2 * GF_NG);
+}
+
+// Increment cell of item k in a sweep: items below M*M are interior cells in
+// the fixed order (i = k % M, j = k / M) used by the final update, so each
+// thread owns the same cells in both sweeps; then the ghost line before and
+// the one after.  a is the position along the sweep, line the one across.
+template <int M>
+__device__ __forceinline__ void cell_item(int k, int dir, int& a, int& line) {
+  if (k < M * M) {
+    const int i = k % M, j = k / M;
+    a = dir == 0 ? i : j;
+    line = dir == 0 ? j : i;
+  } else if (k < M * M + M) {
+    a = k - M * M;
+    line = -1;
+  } else {
+    a = k - M * M - M;
+    line = M;
+  }
+}
+
+template <class P, int M, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
+    k_patch_step(const GfGeom G, const GfView V, double* __restrict__ pmass) {
+  using R = typename P::R;
+  constexpr bool DEV = P::DEV;
+  using Lo = Layout<P, M>;
+  constexpr int TT = Lo::TT, NE = Lo::NE;
+  constexpr int RL = (Lo::NLIM + NT - 1) / NT;    // limiter items per thread
+  constexpr int RC = (M * M + NT - 1) / NT;       // interior cells per thread
+  constexpr int RX = (Lo::NCELL + NT - 1) / NT;   // increment cells per thread
+
+  const int p = blockIdx.x;
+  const GfPatch Pt = V.patch[p];
+  GfCtl* C = V.ctl + Pt.scen;
+  if (!C->active) return;
+
+  extern __shared__ __align__(16) unsigned char smraw[];
+  R* s0 = reinterpret_cast<R*>(smraw);  // h (FP64) or w (deviation form)
+  R* shu = s0 + TT;
+  R* shv = s0 + 2 * TT;
+  R* sb = s0 + 3 * TT;
+  R* sdep = DEV ? s0 + 4 * TT : s0;     // depth
+  R* W = reinterpret_cast<R*>(smraw + Lo::OFF_W);
+  R* Ftr = reinterpret_cast<R*>(smraw + Lo::OFF_F);  // [row j][edge 0..M][3]
+  R* Gtr = reinterpret_cast<R*>(smraw + Lo::OFF_G);  // [column i][edge][3]
+  double* red = reinterpret_cast<double*>(smraw + Lo::OFF_RED);
+  unsigned char* swet = smraw + Lo::OFF_WET;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smraw + Lo::OFF_BAR);
+
+  const int tid = threadIdx.x;
+  const int cur = C->cur;
+  const R* qs;
+  R* qd;
+  const R* bs;
+  if constexpr (DEV) {
+    qs = V.qf[cur] + (size_t)p * 3 * TT;
+    qd = V.qf[cur ^ 1] + (size_t)p * 3 * TT;
+    bs = V.bf + (size_t)p * TT;
+  } else {
+    qs = V.q[cur] + (size_t)p * 3 * TT;
+    qd = V.q[cur ^ 1] + (size_t)p * 3 * TT;
+    bs = V.b + (size_t)p * TT;
+  }
+
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_expect_tx(bar, 4u * TT * sizeof(R));
+    bulk_g2s(s0, qs, TT * sizeof(R), bar);
+    bulk_g2s(shu, qs + TT, TT * sizeof(R), bar);
+    bulk_g2s(shv, qs + 2 * TT, TT * sizeof(R), bar);
+    bulk_g2s(sb, bs, TT * sizeof(R), bar);
+  }
+  __syncthreads();
+  if (!mbar_wait(bar, GF_SPIN_LIMIT)) {
+    if (tid == 0) C->status = -7;  // GEOFLOOD_ERR_TIMEOUT
+    mbar_wait(bar, GF_SPIN_LIMIT);
+    return;
+  }
+
+  const double drytol = G.drytol;
+  const R g = (R)G.g;
+  const R rdry = (R)drytol;
+  const float dtf = (float)drytol;
+  const float margin = (float)(drytol * 0x1p-20);
+  const double dt = C->dt_use;
+  const long long NXL = (long long)G.mi * M << Pt.level;
+  const long long NYL = (long long)G.mj * M << Pt.level;
+  const double dx = (G.xupper - G.xlower) / (double)NXL;
+  const double dy = (G.yupper - G.ylower) / (double)NYL;
+  const R nux = (R)(dt / dx), nuy = (R)(dt / dy);
+  R smx = R(0), smy = R(0);
+
+  // Per-cell depth and exact wet flag (deviation form), and whether the
+  // tile holds any wet cell at all.
+  int anywet = 0;
+  for (int k = tid; k < TT; k += NT) {
+    if constexpr (DEV) {
+      const float w = s0[k], b = sb[k];
+      sdep[k] = w - b;
+      const bool wt = gfk::wet_dev(w, b, drytol, dtf, margin);
+      swet[k] = wt ? 1 : 0;
+      anywet |= wt ? 1 : 0;
+    } else {
+      anywet |= s0[k] > rdry ? 1 : 0;
+    }
+  }
+  anywet = __syncthreads_or(anywet);
+  auto wetc = [&](int c) -> bool {
+    if constexpr (DEV) return swet[c] != 0;
+    else return s0[c] > rdry;
+  };
+  auto surf = [&](int c) -> R {
+    if constexpr (DEV) return s0[c];
+    else return s0[c] + sb[c];
+  };
+
+  R X[RC][3];   // nu_x * dQx of owned interior cells
+  R Y[RC][3];   // nu_y * dQy
+
+  // A tile without a wet cell (ghosts included) has only dry-dry edges: every
+  // wave, correction and transverse term is zero and the update reduces to
+  // zeroing the momenta of the (dry) cells, which the dry branch below does
+  // without the sweeps; the results are identical.
+#pragma unroll 1
+  for (int dir = 0; dir < (anywet ? 2 : 0); ++dir) {
+    const R* sn = dir == 0 ? shu : shv;  // normal momentum
+    const R* st = dir == 0 ? shv : shu;  // transverse momentum
+    const R nu = dir == 0 ? nux : nuy;
+    // phase 1: Riemann solves on lines -1..M, edges -1..M+1
+    for (int k = tid; k < Lo::NEDGE; k += NT) {
+      const int line = k / NE - 1, a = k % NE - 1;
+      const int cl = dir == 0 ? tix<M>(a - 1, line) : tix<M>(line, a - 1);
+      const int cr = dir == 0 ? tix<M>(a, line) : tix<M>(line, a);
+      R Z[9], S[3];
+      gfk::riemann<R, DEV>(
+          gfk::Side<R>{sdep[cl], sn[cl], st[cl], sb[cl], s0[cl], wetc(cl)},
+          gfk::Side<R>{sdep[cr], sn[cr], st[cr], sb[cr], s0[cr], wetc(cr)}, g,
+          rdry, Z, S);
+      R* w = W + 12 * k;
+#pragma unroll
+      for (int q = 0; q < 9; ++q) w[q] = Z[q];
+      w[9] = S[0];
+      w[10] = S[1];
+      w[11] = S[2];
+    }
+    __syncthreads();
+    // phase 2: fluctuations and limited corrections on edges 0..M
+    R AMr[RL][3], APr[RL][3], FFr[RL][3];
+#pragma unroll
+    for (int r = 0; r < RL; ++r) {
+      const int k = tid + r * NT;
+      if (k < Lo::NLIM) {
+        const int line = k / (M + 1) - 1, a = k % (M + 1);
+        const int e = (line + 1) * NE + a + 1;
+        const R* w = W + 12 * e;
+        const int cl = dir == 0 ? tix<M>(a - 1, line) : tix<M>(line, a - 1);
+        const int cr = dir == 0 ? tix<M>(a, line) : tix<M>(line, a);
+        const bool wet = wetc(cl) && wetc(cr);
+        gfk::edge_fluxes<R>(w, w + 9, w - 12, w + 12, nu, wet, AMr[r], APr[r],
+                            FFr[r]);
+        if (line >= 0 && line < M) {
+          R m = R(0);
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            const R as = w[9 + q] > R(0) ? w[9 + q] : -w[9 + q];
+            m = as > m ? as : m;
+          }
+          if (dir == 0) smx = m > smx ? m : smx;
+          else smy = m > smy ? m : smy;
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RL; ++r) {
+      const int k = tid + r * NT;
+      if (k < Lo::NLIM) {
+        const int line = k / (M + 1) - 1, a = k % (M + 1);
+        R* w = W + 12 * ((line + 1) * NE + a + 1);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          w[q] = AMr[r][q];
+          w[3 + q] = APr[r][q];
+          w[6 + q] = FFr[r][q];
+        }
+      }
+    }
+    __syncthreads();
+    // phase 3: per-cell increments and their transverse split
+    R* Tr = dir == 0 ? Gtr : Ftr;
+    R MIr[RX][3];
+#pragma unroll
+    for (int r = 0; r < RX; ++r) {
+      const int k = tid + r * NT;
+      if (k < Lo::NCELL) {
+        int a, line;  // a: position along the sweep, line: across
+        cell_item<M>(k, dir, a, line);
+        const R* wl = W + 12 * ((line + 1) * NE + a + 1);  // edge a
+        const R* wr = wl + 12;                              // edge a+1
+        R d[3];  // frame: mass, normal (sweep) momentum, transverse
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+          d[q] = (wl[3 + q] + wr[q]) + (wr[6 + q] - wl[6 + q]);
+        if (r < RC && k < M * M) {
+          // store nu * dQ in (h, hu, hv) order
+          if (dir == 0) {
+            X[r][0] = nu * d[0]; X[r][1] = nu * d[1]; X[r][2] = nu * d[2];
+          } else {
+            Y[r][0] = nu * d[0]; Y[r][1] = nu * d[2]; Y[r][2] = nu * d[1];
+          }
+        }
+        // split along the other direction: in that frame the "along"
+        // momentum is this sweep's transverse momentum
+        const int ci = dir == 0 ? tix<M>(a, line) : tix<M>(line, a);
+        const int cm = dir == 0 ? tix<M>(a, line - 1) : tix<M>(line - 1, a);
+        const int cp = dir == 0 ? tix<M>(a, line + 1) : tix<M>(line + 1, a);
+        const R dd[3] = {d[0], d[2], d[1]};
+        R pl[3], mi[3];
+        gfk::tsplit<R>(sdep[ci], st[ci], sn[ci], surf(ci), wetc(ci), wetc(cm),
+                       sb[cm], wetc(cp), sb[cp], dd, g, pl, mi);
+        // back to (h, hu, hv): frame (mass, along = st, other = sn)
+        const R plh[3] = {pl[0], dir == 0 ? pl[2] : pl[1],
+                          dir == 0 ? pl[1] : pl[2]};
+        MIr[r][0] = mi[0];
+        MIr[r][1] = dir == 0 ? mi[2] : mi[1];
+        MIr[r][2] = dir == 0 ? mi[1] : mi[2];
+        if (line + 1 <= M) {
+          R* o = Tr + 3 * (a * (M + 1) + line + 1);
+          o[0] = plh[0]; o[1] = plh[1]; o[2] = plh[2];
+        }
+      }
+    }
+    __syncthreads();
+    const R nut = dir == 0 ? nux : nuy;
+#pragma unroll
+    for (int r = 0; r < RX; ++r) {
+      const int k = tid + r * NT;
+      if (k < Lo::NCELL) {
+        int a, line;
+        cell_item<M>(k, dir, a, line);
+        if (line >= 0) {
+          R* o = Tr + 3 * (a * (M + 1) + line);
+#pragma unroll
+          for (int q = 0; q < 3; ++q) o[q] = R(-0.5) * nut * (o[q] + MIr[r][q]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  // ------------------------------------------------ update, friction, out
+  const R mn = (R)V.scen[Pt.scen].manning_n;
+  double vol = 0.0, clipd = 0.0;
+  R volr = R(0);
+  unsigned nclip = 0, nwet = 0;
+  bool bad = false;
+  const float* los = nullptr;
+  float* lod = nullptr;
+  if constexpr (DEV) {
+    los = V.lof[cur] + (size_t)p * 3 * M * M;
+    lod = V.lof[cur ^ 1] + (size_t)p * 3 * M * M;
+  }
+#pragma unroll
+  for (int r = 0; r < RC; ++r) {
+    const int k = tid + r * NT;
+    if (k >= M * M) continue;
+    const int i = k % M, j = k / M;
+    const int c = tix<M>(i, j);
+    if (!anywet) {
+      qd[c] = s0[c];
+      qd[TT + c] = R(0);
+      qd[2 * TT + c] = R(0);
+      if constexpr (DEV) {
+        lod[k] = los[k];
+        lod[M * M + k] = 0.0f;
+        lod[2 * M * M + k] = 0.0f;
+        volr += sdep[c];
+      } else {
+        vol += s0[c];
+      }
+      continue;
+    }
+    const R q[3] = {s0[c], shu[c], shv[c]};
+    nwet += wetc(c) ? 1u : 0u;
+    R o[3];
+    if constexpr (!DEV) {
+#pragma unroll
+      for (int f = 0; f < 3; ++f) {
+        const R fl = X[r][f] + Y[r][f];
+        const R* fa = Ftr + 3 * (j * (M + 1) + i);
+        const R* ga = Gtr + 3 * (i * (M + 1) + j);
+        const R tf = nux * (fa[3 + f] - fa[f]) + nuy * (ga[3 + f] - ga[f]);
+        o[f] = (q[f] - fl) - tf;
+      }
+      if (o[0] < R(0)) { clipd -= o[0]; o[0] = R(0); ++nclip; }
+      if (mn > R(0) && o[0] > rdry) {
+        const R u = o[1] / o[0], v = o[2] / o[0];
+        const R sp = sqrt(u * u + v * v);
+        const R D = g * mn * mn * sp / (o[0] * cbrt(o[0]));
+        const R den = R(1) + (R)dt * D;
+        o[1] = o[1] / den;
+        o[2] = o[2] / den;
+      }
+      if (o[0] <= rdry) { o[1] = R(0); o[2] = R(0); }
+      vol += o[0];
+    } else {
+      // compensated update: (hi + lo) - fl - tf, hi rounded, lo the error
+      float lo[3];
+#pragma unroll
+      for (int f = 0; f < 3; ++f) {
+        const float fl = X[r][f] + Y[r][f];
+        const float* fa = Ftr + 3 * (j * (M + 1) + i);
+        const float* ga = Gtr + 3 * (i * (M + 1) + j);
+        const float tf = nux * (fa[3 + f] - fa[f]) + nuy * (ga[3 + f] - ga[f]);
+        const float x = (los[f * M * M + k] - fl) - tf;
+        const float s = q[f] + x;
+        const float bb = s - q[f];
+        lo[f] = (q[f] - (s - bb)) + (x - bb);
+        o[f] = s;
+      }
+      const float bc = sb[c];
+      if (o[0] < bc) {  // negative depth: reset to a dry bed
+        clipd += (double)bc - (double)o[0];
+        o[0] = bc;
+        lo[0] = 0.0f;
+        ++nclip;
+      }
+      const bool wnew = gfk::wet_dev(o[0], bc, drytol, dtf, margin);
+      if (mn > 0.0f && wnew) {
+        const float h = o[0] - bc;
+        const float u = o[1] / h, v = o[2] / h;
+        const float sp = sqrtf(u * u + v * v);
+        const float D = g * mn * mn * sp / (h * cbrtf(h));
+        const float den = 1.0f + (float)dt * D;
+        o[1] = o[1] / den;
+        o[2] = o[2] / den;
+        lo[1] = lo[1] / den;
+        lo[2] = lo[2] / den;
+      }
+      if (!wnew) { o[1] = 0.0f; o[2] = 0.0f; lo[1] = 0.0f; lo[2] = 0.0f; }
+#pragma unroll
+      for (int f = 0; f < 3; ++f) lod[f * M * M + k] = lo[f];
+      volr += o[0] - bc;
+    }
+    bad |= !(isfinite(o[0]) && isfinite(o[1]) && isfinite(o[2]));
+    qd[c] = o[0];
+    qd[TT + c] = o[1];
+    qd[2 * TT + c] = o[2];
+  }
+  if constexpr (DEV) vol = (double)volr;
+
+  // block reductions: CFL rate (max), volume (FP64, fixed-order tree)
+  const int lane = tid & 31, wid = tid >> 5;
+  constexpr int NW = NT / 32;
+  smx = warp_max(smx);
+  smy = warp_max(smy);
+  vol = warp_sum_tree(vol);
+  nwet = __reduce_add_sync(0xffffffffu, nwet);
+  if (lane == 0 && nwet) atomicAdd(&C->wet_updates, (unsigned long long)nwet);
+  if (lane == 0) {
+    red[wid] = (double)smx;
+    red[NW + wid] = (double)smy;
+    red[2 * NW + wid] = vol;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double mx = 0.0, my = 0.0, vs = 0.0;
+    for (int w = 0; w < NW; ++w) {
+      mx = red[w] > mx ? red[w] : mx;
+      my = red[NW + w] > my ? red[NW + w] : my;
+      vs += red[2 * NW + w];
+    }
+    const double cx = mx / dx, cy = my / dy;
+    const double cm = cx > cy ? cx : cy;
+    atomicMax(&C->cmax_bits, (unsigned long long)__double_as_longlong(cm));
+    atomicAdd(&C->cell_updates, (unsigned long long)(M * M));
+    pmass[p] = vs * (dx * dy);
+  }
+  if (nclip) {
+    atomicAdd(&C->step_nclip, (unsigned long long)nclip);
+    atomicAdd(&C->step_clipvol, clipd * (dx * dy));
+  }
+  if (bad) C->nonfinite = 1;
+}
+
+template <class P, int M, int NT, int MINB>
+int launch_step(const GfGeom& g, const GfView& v, double* pmass,
+                cudaStream_t st) {
+  constexpr size_t bytes = Layout<P, M>::BYTES;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k_patch_step<P, M, NT, MINB>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bytes) != cudaSuccess)
+      return -2;
+    attr = true;
+  }
+  k_patch_step<P, M, NT, MINB><<<v.npatch, NT, bytes, st>>>(g, v, pmass);
+  return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+}  // namespace gfs
