@@ -29,11 +29,11 @@ sys.path.insert(0, ROOT)
 # DRAM bytes (read + write) of one patch_step launch on this workload, from
 # the ncu capture summarised in profiles/ (None when the kernel has changed
 # since the capture).
-TRAFFIC_PER_LAUNCH = None
+TRAFFIC_PER_LAUNCH_FP64 = None
 N_CELLS = 1024
 PATCH = 32
 T_END = 60.0
-WORKLOAD = "radial dam break 1024x1024, 32x32 patches, dx 2 m, FP64, t 0->60 s"
+WORKLOAD = "radial dam break 1024x1024, 32x32 patches, dx 2 m, t 0->60 s"
 
 
 def parse():
@@ -47,6 +47,8 @@ def parse():
                     help="run N x N cells of the workload for --profile-steps "
                          "steps and exit (for ncu captures; prints no JSON)")
     ap.add_argument("--profile-steps", type=int, default=20)
+    ap.add_argument("--profile-precision", type=int, default=1, choices=[0, 1],
+                    help="0 = FP64, 1 = FP32 deviation form")
     return ap.parse_args()
 
 
@@ -56,6 +58,7 @@ def run_profile_case(args):
     from paper_2403_15435_gb300 import geoflood, inputs
     n = args.profile_case
     prob = inputs.radial_dambreak(n, PATCH, dx=2.0, radius=200.0 * n / N_CELLS)
+    prob.cfg.precision = args.profile_precision
     f = geoflood.Forest(prob.cfg, prob.dem, max_patches=(n // PATCH) ** 2)
     f.set_state(prob.ic)
     _, steps = f.step(1e9, args.profile_steps)
@@ -125,6 +128,14 @@ def measured_peaks():
         return {}
 
 
+# FP32 deviation form: read w, hu, hv, b and the three compensation terms,
+# write w, hu, hv and the compensation terms = 52 B per cell update; the
+# operation count adds the compensated update (24) and the exact wet tests (8)
+# to the scheme's 468.
+BYTES_PER_CELL_FP32 = 52
+OPS_PER_WET_CELL_FP32 = 500
+FP32_LANES_PER_SM = 128
+TRAFFIC_PER_LAUNCH_FP32 = None
 # Algorithmic work of the FP64 patch step, counted operation by operation
 # from the scheme: a wet cell update takes two edge solves (74 operations
 # each), two limited edge fluxes (81), two increments (9), two transverse
@@ -138,34 +149,22 @@ FP64_LANES_PER_SM = 2  # measured: DFMA throughput 1.20 TFLOP/s on 152 SMs
 N_SM = 152
 
 
-def fp64_peak_gops(peaks):
-    """FP64 operation peak: 152 SMs x 2 FP64 lanes x the maximum SM clock
-    (one add, mul or FMA per lane per clock)."""
-    mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    return N_SM * FP64_LANES_PER_SM * mhz / 1e3
-
-
-def run_ours(args):
-    import numpy as np
+def measure(prec, args, dev, stream, world, local, gauges):
+    """Time the workload in one precision: warm-up runs, then args.steps timed
+    runs (L2 flushed before each), per-launch patch_step events, counters
+    and the end-to-end runs through the C ABI with pinned host buffers."""
     import torch
     from paper_2403_15435_gb300 import geoflood, inputs
 
-    rank, world, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream(dev)
-
     prob = inputs.radial_dambreak(N_CELLS, PATCH, dx=2.0)
+    prob.cfg.precision = prec
     f = geoflood.Forest(prob.cfg, prob.dem, stream=stream.cuda_stream)
     f.set_state(prob.ic)
+    f.set_gauges(gauges)
     n = f.npatch
     m = prob.cfg.mx
     h0, hu0, hv0, _ = f.read()
     cells = n * m * m
-    # pinned host buffers for the end-to-end leg
     pin = lambda: torch.empty((n, m, m), dtype=torch.float64, pin_memory=True).numpy()
     H, HU, HV = pin(), pin(), pin()
     H[:], HU[:], HV[:] = h0, hu0, hv0
@@ -175,51 +174,46 @@ def run_ours(args):
     def reset():
         f.write(H, HU, HV)
         f.set_time(0.0, prob.cfg.dt_initial)
-
-    def one_run():
-        _, n_acc = f.step(args.t_end)
-        return n_acc
+        f.set_gauges(gauges)
 
     for _ in range(args.warmup):
         reset()
-        one_run()
+        f.step(args.t_end)
     torch.cuda.synchronize(dev)
 
-    times, steps_list = [], []
+    steps_list, ev = [], []
     launches0 = f.launch_count()
     cu0, wet0 = f.counters()
     f.profile(True)
-    ev = []
     with ClockSampler(local) as clk:
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
         for _ in range(args.steps):
             reset()
-            flush.fill_(1.0)
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            st = one_run()
+            _, n_acc = f.step(args.t_end)
             b.record(stream)
             ev.append((a, b))
-            steps_list.append(st)
+            steps_list.append(n_acc)
         torch.cuda.synchronize(dev)
-    launches_timed = f.launch_count() - launches0
+    launches = f.launch_count() - launches0
     cu1, wet1 = f.counters()
-    for a, b in ev:
-        times.append(a.elapsed_time(b) / 1e3)
+    total_t = sum(a.elapsed_time(b) / 1e3 for a, b in ev)
     k_ms, k_n = f.profile_read("patch_step")
     f.profile(False)
-    total_t = sum(times)
-    total_cells = sum(steps_list) * cells
     if world > 1:
         t = torch.tensor([total_t], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_t = float(t.item())
-    value = total_cells * world / total_t
+    value = sum(steps_list) * cells * world / total_t
+    gauge_out, arrival = f.gauges()
+    final = f.read()[:3]
 
-    # end-to-end through the C ABI with host buffers
     e2e_t = []
     for _ in range(max(1, min(args.steps, 3))):
         torch.cuda.synchronize(dev)
@@ -229,32 +223,97 @@ def run_ours(args):
         _, n_acc = f.step(args.t_end)
         f.read_into(OH, OHU, OHV)
         e2e_t.append(time.perf_counter() - t0)
-    e2e_cells = n_acc * cells
-    e2e = {"value": e2e_cells * world / (sum(e2e_t) / len(e2e_t)), "unit": "cell-updates/s",
-           "h2d_bytes_per_step": 3 * cells * 8, "d2h_bytes_per_step": 3 * cells * 8}
+    e2e = {"value": n_acc * cells * world / (sum(e2e_t) / len(e2e_t)),
+           "unit": "cell-updates/s", "h2d_bytes_per_step": 3 * cells * 8,
+           "d2h_bytes_per_step": 3 * cells * 8}
+    f.close()
+    return dict(value=value, ms_per_step=1e3 * total_t / args.steps, steps=steps_list,
+                cells=cells, patches=n, launches=launches, clocks=clk.summary(),
+                k_ms=k_ms, k_n=k_n, wet=wet1 - wet0, updates=cu1 - cu0, e2e=e2e,
+                gauges=gauge_out, arrival=arrival, final=final)
+
+
+def roofline(r, prec, peaks):
+    """Roofline of the patch_step kernel from the live per-launch events:
+    HBM side from the algorithmic bytes per cell update, ALU side from the
+    counted operations per wet cell update; the binding side is reported."""
+    avg = r["k_ms"] / 1e3 / max(1, r["k_n"])
+    cells = r["cells"]
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    hbm = float(peaks.get("hbm_gbs", 6785.2))
+    if prec == 0:
+        bytes_cell, ops_wet = BYTES_PER_CELL_FP64, OPS_PER_WET_CELL_FP64
+        alu_peak = N_SM * FP64_LANES_PER_SM * mhz / 1e3            # GOP/s
+        alu_src = "152 SMs x 2 FP64 lanes x %.0f MHz" % mhz
+        traffic = TRAFFIC_PER_LAUNCH_FP64
+    else:
+        bytes_cell, ops_wet = BYTES_PER_CELL_FP32, OPS_PER_WET_CELL_FP32
+        alu_peak = N_SM * FP32_LANES_PER_SM * mhz / 1e3            # GOP/s
+        alu_src = "152 SMs x 128 FP32 lanes x %.0f MHz" % mhz
+        traffic = TRAFFIC_PER_LAUNCH_FP32
+    ops = ops_wet * r["wet"] / max(1, r["k_n"])
+    alu = ops / avg / 1e9
+    gbs = bytes_cell * cells / avg / 1e9
+    out = {"kernel": "patch_step (%s)" % ("FP64" if prec == 0 else "FP32 deviation form"),
+           "avg_launch_ms": avg * 1e3, "wet_fraction": r["wet"] / max(1, r["updates"]),
+           "alu": {"achieved": alu, "peak": alu_peak, "unit": "GOP/s", "frac": alu / alu_peak,
+                   "ops_per_launch": ops, "peak_source": "derived: " + alu_src},
+           "hbm": {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                   "bytes_per_launch": bytes_cell * cells, "peak_source": "measured"}}
+    side = "alu" if out["alu"]["frac"] >= out["hbm"]["frac"] else "hbm"
+    out.update({"bound": side, "achieved": out[side]["achieved"], "peak": out[side]["peak"],
+                "unit": out[side]["unit"], "frac": out[side]["frac"], "traffic": traffic})
+    return out
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    # a stream of its own: the library captures its step chunks as CUDA
+    # graphs, which the legacy default stream does not allow
+    stream = torch.cuda.Stream(device=dev)
+    # 16 gauges on rays from the cylinder centre (x, y in m)
+    ang = np.linspace(0.0, 2 * np.pi, 16, endpoint=False)
+    rad = np.linspace(250.0, 900.0, 16)
+    gauges = np.stack([1024.0 + rad * np.cos(ang), 1024.0 + rad * np.sin(ang)], 1)
 
     peaks = measured_peaks()
-    avg_launch = k_ms / 1e3 / max(1, k_n)
-    ops_per_launch = OPS_PER_WET_CELL_FP64 * (wet1 - wet0) / max(1, k_n)
-    peak = fp64_peak_gops(peaks)
-    achieved = ops_per_launch / avg_launch / 1e9
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GOP/s",
-            "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH,
-            "kernel": "patch_step (FP64)", "avg_launch_ms": avg_launch * 1e3,
-            "ops_per_launch": ops_per_launch, "wet_fraction": (wet1 - wet0) / max(1, cu1 - cu0),
-            "peak_source": "derived: 152 SMs x 2 FP64 lanes x %.0f MHz (measured DFMA probe 1.20 TFLOP/s)" % float(peaks.get("sm_max_mhz", 2070.0)),
-            "hbm_frac_of_measured": BYTES_PER_CELL_FP64 * cells / avg_launch / 1e9 / peaks.get("hbm_gbs", 6785.2)}
+    r32 = measure(1, args, dev, stream, world, local, gauges)
+    r64 = measure(0, args, dev, stream, world, local, gauges)
+    roof32 = roofline(r32, 1, peaks)
+    roof64 = roofline(r64, 0, peaks)
+    # error of the FP32 run against the FP64 run of the same workload
+    err = {"max_abs_depth_m": float(np.abs(r32["final"][0] - r64["final"][0]).max()),
+           "max_abs_momentum_m2s": float(max(np.abs(r32["final"][1] - r64["final"][1]).max(),
+                                             np.abs(r32["final"][2] - r64["final"][2]).max())),
+           "gauge_depth_max_abs_m": float(np.abs(r32["gauges"][:, 1] - r64["gauges"][:, 1]).max()),
+           "arrival_max_abs_s": float(np.abs(r32["arrival"] - r64["arrival"]).max())}
     cpu = cpu_baseline()
     line = {
-        "metric": "cell-updates/s", "value": value, "unit": "cell-updates/s",
+        "metric": "cell-updates/s", "value": r32["value"], "unit": "cell-updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * total_t / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "cells": cells, "patches": n,
-                   "accepted_steps_per_run": steps_list[0], "l2": "flushed (256 MB write) before each timed run",
+        "ms_per_step": r32["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": r32["cells"], "patches": r32["patches"],
+                   "accepted_steps_per_run": r32["steps"][0],
+                   "precision": "FP32 surface-deviation form (compensated update, exact wet tests)",
+                   "tagging": "none: uniform single-level grid, no regrid in this workload",
+                   "l2": "flushed (256 MB write) before each timed run; within a run the "
+                         "working set stays in L2",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-        "gpu_launches": launches_timed, "clocks": clk.summary(),
+        "roofline": roof32, "cpu_baseline": cpu, "e2e": r32["e2e"],
+        "gpu_launches": r32["launches"], "clocks": r32["clocks"],
+        "fp64": {"value": r64["value"], "ms_per_step": r64["ms_per_step"], "dtype": "f64",
+                 "accepted_steps_per_run": r64["steps"][0], "roofline": roof64,
+                 "e2e": r64["e2e"], "gpu_launches": r64["launches"], "clocks": r64["clocks"]},
+        "fp32_vs_fp64_error": err,
     }
     if rank == 0:
         print(json.dumps(line))

@@ -253,7 +253,7 @@ __device__ void tile_bc(const G2& e, const GfPatch& P, T* q, T* bfield,
 // (reads only leaf interiors, so patches are independent), then the
 // physical boundaries.
 template <typename T>
-__global__ void k_ghost_fill(const GfGeom G, const GfView V, int only_accepted,
+__global__ void k_ghost_fill(const __grid_constant__ GfGeom G, const __grid_constant__ GfView V, int only_accepted,
                              int* errflag) {
   const int p = blockIdx.x;
   const GfPatch P = V.patch[p];
@@ -282,6 +282,21 @@ __global__ void k_ghost_fill(const GfGeom G, const GfView V, int only_accepted,
     const long long I = (long long)P.px * M + i, J = (long long)P.py * M + j;
     if (I < 0 || J < 0 || I >= NX || J >= NY) continue;
     const int c = e.tix(i, j);
+    // same-level neighbour (from the neighbour table): copy the stored
+    // values as they are
+    const int region = i < 0 ? (j < 0 ? 4 : (j >= M ? 6 : 0))
+                             : (i >= M ? (j < 0 ? 5 : (j >= M ? 7 : 1))
+                                       : (j < 0 ? 2 : 3));
+    const int pn = V.nbr ? V.nbr[(size_t)p * 8 + region] : e.leaf(P.scen, P.level, I, J);
+    if (pn >= 0) {
+      const GfPatch Pn = V.patch[pn];
+      const int cn = e.tix((int)(I - (long long)Pn.px * M), (int)(J - (long long)Pn.py * M));
+      const T* qn = e.qp(pn, C->cur);
+      q[c] = qn[cn];
+      q[TT + c] = qn[TT + cn];
+      q[2 * TT + c] = qn[2 * TT + cn];
+      continue;
+    }
     const double bt = (double)bb[c];
     double out[3];
     fill_cell(e, P.scen, P.level, I, J, bt, out, &err);
@@ -364,7 +379,7 @@ __device__ double dem_average(const GfScenario& S, double xa, double xb,
 }
 
 template <typename T>
-__global__ void k_topo(const GfGeom G, const GfView V, int first) {
+__global__ void k_topo(const __grid_constant__ GfGeom G, const __grid_constant__ GfView V, int first) {
   const int p = first + blockIdx.x;
   const GfPatch P = V.patch[p];
   Geo<T> e(G, V);
@@ -395,7 +410,8 @@ __global__ void k_topo(const GfGeom G, const GfView V, int first) {
 // forest by the ghost-cell operators (copy, average, interpolation).  The
 // FP32 compensation terms of new cells start at zero.
 template <typename T>
-__global__ void k_regrid_fill(const GfGeom G, const GfView O, const GfView N,
+__global__ void k_regrid_fill(const __grid_constant__ GfGeom G, const __grid_constant__ GfView O,
+                              const __grid_constant__ GfView N,
                               int* errflag) {
   const int p = blockIdx.x;
   const GfPatch P = N.patch[p];
@@ -425,7 +441,7 @@ __global__ void k_regrid_fill(const GfGeom G, const GfView O, const GfView N,
 
 // Plain tagger (Sec. 4.1 criteria 1, 3, 4; Sec. 6.4).
 template <typename T>
-__global__ void k_tags(const GfGeom G, const GfView V, uint8_t* flags) {
+__global__ void k_tags(const __grid_constant__ GfGeom G, const __grid_constant__ GfView V, uint8_t* flags) {
   const int p = blockIdx.x;
   const GfPatch P = V.patch[p];
   Geo<T> e(G, V);
@@ -476,7 +492,7 @@ __global__ void k_tags(const GfGeom G, const GfView V, uint8_t* flags) {
 // Gauges (Sec. 5.1 control points, Sec. 6.5): bilinear in the finest leaf,
 // ghosts included; arrival at the first sample with h > 1 cm.
 template <typename T>
-__global__ void k_gauges(const GfGeom G, const GfView V, int only_accepted) {
+__global__ void k_gauges(const __grid_constant__ GfGeom G, const __grid_constant__ GfView V, int only_accepted) {
   const int s = blockIdx.y;
   const GfScenario S = V.scen[s];
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -536,7 +552,7 @@ __global__ void k_gauges(const GfGeom G, const GfView V, int only_accepted) {
 
 // Volume per patch (fixed-order block tree), then per scenario.
 template <typename T>
-__global__ void k_patch_mass(const GfGeom G, const GfView V, double* pmass) {
+__global__ void k_patch_mass(const __grid_constant__ GfGeom G, const __grid_constant__ GfView V, double* pmass) {
   const int p = blockIdx.x;
   const GfPatch P = V.patch[p];
   Geo<T> e(G, V);
@@ -579,7 +595,7 @@ __global__ void k_scen_mass(const GfScenario* sc, const double* pmass,
 // for unpacking (the deviation form converts w = h + b - eta0 and clears the
 // compensation terms).
 template <typename T>
-__global__ void k_pack(const GfGeom G, const GfView V, int first, double* out,
+__global__ void k_pack(const __grid_constant__ GfGeom G, const __grid_constant__ GfView V, int first, double* out,
                        int cur) {
   const int p = first + blockIdx.x;
   Geo<T> e(G, V);
@@ -599,7 +615,7 @@ __global__ void k_pack(const GfGeom G, const GfView V, int first, double* out,
 }
 
 template <typename T>
-__global__ void k_unpack(const GfGeom G, const GfView V, int first,
+__global__ void k_unpack(const __grid_constant__ GfGeom G, const __grid_constant__ GfView V, int first,
                          const double* in, int cur) {
   const int p = first + blockIdx.x;
   Geo<T> e(G, V);

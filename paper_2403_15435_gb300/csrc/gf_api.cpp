@@ -38,6 +38,16 @@ struct geoflood_ctx {
   int bsel = 0;
   GfPatch* d_patch[2] = {nullptr, nullptr};
   int* d_lut[2] = {nullptr, nullptr};
+  int* d_nbr[2] = {nullptr, nullptr};
+  unsigned* d_done = nullptr;
+  bool own_stream = false;
+  // CUDA graphs of chunks of steps, keyed by chunk length
+  struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    int k = 0, tsel = -1, bsel = -1, npatch = -1, gauges = -1, prof = -1;
+    std::vector<ProfRec> ev;
+  };
+  std::vector<Graph> graphs;
   int tsel = 0;
   GfScenario* d_scen = nullptr;
   std::vector<GfScenario> h_scen;
@@ -55,6 +65,8 @@ struct geoflood_ctx {
   std::string err;
   bool prof = false;
   std::map<std::string, std::vector<ProfRec>> prof_recs;
+  std::map<std::string, double> prof_ms;
+  std::map<std::string, long long> prof_n;
   std::vector<cudaEvent_t> pool;
   size_t pool_used = 0;
   long long launches = 0;
@@ -99,6 +111,8 @@ GfView view(geoflood_ctx* c, int t, int bb) {
   v.bf = c->bf[bb];
   v.lof[0] = c->lof[0];
   v.lof[1] = c->lof[1];
+  v.nbr = c->d_nbr[t];
+  v.done = c->d_done;
   v.npatch = c->npatch;
   v.prec = c->prec;
   return v;
@@ -181,6 +195,23 @@ int upload_tables(geoflood_ctx* ctx, int t,
     }
     off += (int)lv[s].size();
   }
+  // same-level neighbours of every patch (left, right, bottom, top, then the
+  // corners bottom-left, bottom-right, top-left, top-right)
+  std::vector<int> nb(total * 8);
+  static const int DX[8] = {-1, 1, 0, 0, -1, 1, -1, 1};
+  static const int DY[8] = {0, 0, -1, 1, -1, -1, 1, 1};
+  for (size_t k = 0; k < total; ++k) {
+    const GfPatch& P = hp[k];
+    const long long w = (long long)ctx->G.mi << P.level, h = (long long)ctx->G.mj << P.level;
+    for (int r = 0; r < 8; ++r) {
+      const long long X = P.px + DX[r], Y = P.py + DY[r];
+      if (X < 0 || Y < 0 || X >= w || Y >= h) { nb[k * 8 + r] = GF_NBR_OUTSIDE; continue; }
+      const int q = lut[(size_t)ctx->h_scen[P.scen].lut_off + ctx->G.lut_lev_off[P.level] + X + Y * w];
+      nb[k * 8 + r] = q >= 0 ? q : GF_NBR_OTHER;
+    }
+  }
+  CK(cudaMemcpyAsync(ctx->d_nbr[t], nb.data(), sizeof(int) * nb.size(),
+                     cudaMemcpyHostToDevice, ctx->st));
   CK(cudaMemcpyAsync(ctx->d_patch[t], hp.data(), sizeof(GfPatch) * total,
                      cudaMemcpyHostToDevice, ctx->st));
   CK(cudaMemcpyAsync(ctx->d_lut[t], lut.data(), sizeof(int) * lut.size(),
@@ -254,6 +285,15 @@ int geoflood_init_forest(const geoflood_config* cfg, void* stream,
   geoflood_ctx* ctx = new geoflood_ctx();
   ctx->cfg = c;
   ctx->st = static_cast<cudaStream_t>(stream);
+  if (!ctx->st) {
+    // graphs cannot be captured on the legacy default stream: use a
+    // blocking stream of our own, which stays ordered with the legacy one
+    if (cudaStreamCreate(&ctx->st) != cudaSuccess) {
+      delete ctx;
+      return GEOFLOOD_ERR_CUDA;
+    }
+    ctx->own_stream = true;
+  }
   ctx->nscen = c.num_scenarios;
   ctx->cap = c.max_patches;
   GfGeom& G = ctx->G;
@@ -297,6 +337,9 @@ int geoflood_init_forest(const geoflood_config* cfg, void* stream,
   }
   okk &= alloc((void**)&ctx->d_patch[0], cap * sizeof(GfPatch));
   okk &= alloc((void**)&ctx->d_patch[1], cap * sizeof(GfPatch));
+  okk &= alloc((void**)&ctx->d_nbr[0], cap * 8 * sizeof(int));
+  okk &= alloc((void**)&ctx->d_nbr[1], cap * 8 * sizeof(int));
+  okk &= alloc((void**)&ctx->d_done, sizeof(unsigned));
   okk &= alloc((void**)&ctx->d_lut[0], (size_t)ctx->nscen * G.lut_per_scen * sizeof(int));
   okk &= alloc((void**)&ctx->d_lut[1], (size_t)ctx->nscen * G.lut_per_scen * sizeof(int));
   okk &= alloc((void**)&ctx->d_scen, ctx->nscen * sizeof(GfScenario));
@@ -332,7 +375,8 @@ int geoflood_init_forest(const geoflood_config* cfg, void* stream,
         cudaMemsetAsync(q1, 0, qbytes, ctx->st) ||
         (ctx->prec && (cudaMemsetAsync(ctx->lof[0], 0, cap * 3 * MM * sizeof(float), ctx->st) ||
                        cudaMemsetAsync(ctx->lof[1], 0, cap * 3 * MM * sizeof(float), ctx->st))) ||
-        cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->st)) {
+        cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->st) ||
+        cudaMemsetAsync(ctx->d_done, 0, sizeof(unsigned), ctx->st)) {
       rc = GEOFLOOD_ERR_CUDA;
       break;
     }
@@ -365,7 +409,11 @@ void geoflood_destroy(geoflood_ctx* ctx) {
     cudaFree(ctx->lof[k]);
     cudaFree(ctx->d_patch[k]);
     cudaFree(ctx->d_lut[k]);
+    cudaFree(ctx->d_nbr[k]);
   }
+  for (auto& gr : ctx->graphs)
+    if (gr.exec) cudaGraphExecDestroy(gr.exec);
+  cudaFree(ctx->d_done);
   cudaFree(ctx->d_scen);
   cudaFree(ctx->d_ctl);
   cudaFree(ctx->d_pmass);
@@ -378,6 +426,7 @@ void geoflood_destroy(geoflood_ctx* ctx) {
   for (auto p : ctx->d_gout) cudaFree(p);
   for (auto p : ctx->d_garr) cudaFree(p);
   if (ctx->h_ctl) cudaFreeHost(ctx->h_ctl);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->st);
   for (auto e : ctx->pool) cudaEventDestroy(e);
   delete ctx;
 }
@@ -596,44 +645,83 @@ int geoflood_step(geoflood_ctx* ctx, double t_target, int max_steps,
   ctx->launches++;
   gf::set_errflag(ctx->d_err);
   const GfView v = view(ctx);
-  // Launch in chunks; the device controller deactivates a scenario when it
-  // reaches t_target or max_steps accepted steps, and later launches of its
-  // patches return at once.  Rejected steps need extra launches, bounded by
-  // the controller's limit on consecutive rejections.
+  // The steps run in chunks of K captured as one CUDA graph (patch step with
+  // the fused CFL controller, ghost fill, gauges); the device controller
+  // deactivates a scenario when it reaches t_target or max_steps accepted
+  // steps, after which its patches return at once.  Rejected steps need
+  // extra launches, bounded by the controller's limit on rejections in a row.
+  const int K = std::max(1, std::min(16, max_steps));
+  geoflood_ctx::Graph* gr = nullptr;
+  for (auto& c : ctx->graphs)
+    if (c.k == K) gr = &c;
+  if (!gr) {
+    ctx->graphs.emplace_back();
+    gr = &ctx->graphs.back();
+    gr->k = K;
+  }
+  const int prof = ctx->prof ? 1 : 0;
+  if (!gr->exec || gr->tsel != ctx->tsel || gr->bsel != ctx->bsel ||
+      gr->npatch != ctx->npatch || gr->gauges != ctx->max_gauges_used ||
+      gr->prof != prof) {
+    if (gr->exec) cudaGraphExecDestroy(gr->exec);
+    gr->exec = nullptr;
+    gr->ev.clear();
+    CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
+    int lrc = 0;
+    for (int it = 0; it < K && !lrc; ++it) {
+      ProfRec r{};
+      if (prof) {
+        r.a = pool_event(ctx);
+        r.b = pool_event(ctx);
+        // an external record node: the event is recorded at every replay
+        cudaEventRecordWithFlags(r.a, ctx->st, cudaEventRecordExternal);
+      }
+      lrc |= ctx->prec ? gf::launch_patch_step_f32(ctx->G, v, ctx->d_pmass, ctx->st)
+                       : gf::launch_patch_step_f64(ctx->G, v, ctx->d_pmass, ctx->st);
+      if (prof) {
+        cudaEventRecordWithFlags(r.b, ctx->st, cudaEventRecordExternal);
+        gr->ev.push_back(r);
+      }
+      lrc |= gf::launch_ghost_fill(ctx->G, v, 1, ctx->st);
+      if (ctx->max_gauges_used > 0)
+        lrc |= gf::launch_gauges(ctx->G, v, 1, ctx->max_gauges_used, ctx->st);
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(ctx->st, &graph);
+    if (lrc || ce != cudaSuccess)
+      return fail(ctx, GEOFLOOD_ERR_CUDA, std::string("step: graph capture failed: ") +
+                                              cudaGetErrorString(ce != cudaSuccess ? ce : cudaGetLastError()));
+    ce = cudaGraphInstantiate(&gr->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess)
+      return fail(ctx, GEOFLOOD_ERR_CUDA, std::string("step: graph instantiation failed: ") +
+                                              cudaGetErrorString(ce));
+    gr->tsel = ctx->tsel;
+    gr->bsel = ctx->bsel;
+    gr->npatch = ctx->npatch;
+    gr->gauges = ctx->max_gauges_used;
+    gr->prof = prof;
+  }
+  const int per_step = 2 + (ctx->max_gauges_used > 0 ? 1 : 0);
   long long launched = 0;
   const long long limit = (long long)max_steps * 2 + 64;
-  int chunk = 4;
   while (max_steps > 0) {
-    const int k = (int)std::min<long long>(chunk, std::max<long long>(1, max_steps - launched));
-    for (int it = 0; it < k; ++it) {
-      ProfRec r;
-      prof_begin(ctx, "patch_step", &r);
-      CKL(ctx->prec ? gf::launch_patch_step_f32(ctx->G, v, ctx->d_pmass, ctx->st)
-                    : gf::launch_patch_step_f64(ctx->G, v, ctx->d_pmass, ctx->st),
-          "patch_step");
-      prof_end(ctx, "patch_step", &r);
-      prof_begin(ctx, "controller", &r);
-      CKL(gf::launch_controller(ctx->G, v, ctx->d_pmass, ctx->nscen, ctx->st), "controller");
-      prof_end(ctx, "controller", &r);
-      prof_begin(ctx, "ghost_fill", &r);
-      CKL(gf::launch_ghost_fill(ctx->G, v, 1, ctx->st), "ghost_fill");
-      prof_end(ctx, "ghost_fill", &r);
-      ctx->launches += 3;
-      if (ctx->max_gauges_used > 0) {
-        prof_begin(ctx, "gauges", &r);
-        CKL(gf::launch_gauges(ctx->G, v, 1, ctx->max_gauges_used, ctx->st), "gauges");
-        prof_end(ctx, "gauges", &r);
-        ctx->launches++;
-      }
-    }
-    launched += k;
+    CK(cudaGraphLaunch(gr->exec, ctx->st));
+    ctx->launches += (long long)K * per_step;
+    launched += K;
     int rc = sync_ctl_down(ctx);
     if (rc) return rc;
+    if (prof)
+      for (auto& r : gr->ev) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, r.a, r.b));
+        ctx->prof_ms["patch_step"] += ms;
+        ctx->prof_n["patch_step"] += 1;
+      }
     bool any = false;
     for (int s = 0; s < ctx->nscen; ++s) any |= ctx->h_ctl[s].active != 0;
     if (!any) break;
     if (launched > limit) return fail(ctx, GEOFLOOD_ERR_CFL, "step: too many retakes");
-    chunk = std::min(chunk * 2, 64);
   }
   int rc = sync_ctl_down(ctx);
   if (rc) return rc;
@@ -763,6 +851,12 @@ int geoflood_profile(geoflood_ctx* ctx, int enable) {
   if (!ctx) return GEOFLOOD_ERR_ARG;
   CK(cudaStreamSynchronize(ctx->st));
   ctx->prof_recs.clear();
+  ctx->prof_ms.clear();
+  ctx->prof_n.clear();
+  for (auto& gr : ctx->graphs) {  // their events come from the pool
+    if (gr.exec) cudaGraphExecDestroy(gr.exec);
+    gr.exec = nullptr;
+  }
   ctx->pool_used = 0;
   if (enable) pool_event(ctx), ctx->pool_used = 0;  // pre-create the pool
   ctx->prof = enable != 0;
@@ -773,8 +867,8 @@ int geoflood_profile_read(geoflood_ctx* ctx, const char* kernel,
                           double* total_ms, long long* launches) {
   if (!ctx || !kernel) return GEOFLOOD_ERR_ARG;
   CK(cudaStreamSynchronize(ctx->st));
-  double tot = 0.0;
-  long long n = 0;
+  double tot = ctx->prof_ms.count(kernel) ? ctx->prof_ms[kernel] : 0.0;
+  long long n = ctx->prof_n.count(kernel) ? ctx->prof_n[kernel] : 0;
   auto it = ctx->prof_recs.find(kernel);
   if (it != ctx->prof_recs.end())
     for (auto& r : it->second) {

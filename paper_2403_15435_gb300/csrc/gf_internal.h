@@ -76,9 +76,18 @@ struct GfView {
   float* qf[2];           // FP32 state [cap][3][T][T]: w = h + b - eta0, hu, hv
   float* bf;              // FP32 beds minus eta0 [cap][T][T]
   float* lof[2];          // FP32 compensation terms [cap][3][M][M]
+  const int* nbr;         // [npatch][8] same-level neighbours (see below)
+  unsigned* done;         // CTA completion counter of the step (or null)
   int npatch;
   int prec;               // 0 = FP64, 1 = FP32 surface deviation
 };
+
+// Neighbour table entries, per patch in the order left, right, bottom, top,
+// bottom-left, bottom-right, top-left, top-right: the index of the leaf of
+// the same level there, GF_NBR_OTHER if that region is covered by leaves of
+// another level, GF_NBR_OUTSIDE beyond the domain.
+#define GF_NBR_OTHER -1
+#define GF_NBR_OUTSIDE -2
 
 // Kernel launchers (defined in the .cu files).
 namespace gf {
@@ -86,8 +95,6 @@ int launch_patch_step_f64(const GfGeom& g, const GfView& v, double* pmass,
                           void* stream);
 int launch_patch_step_f32(const GfGeom& g, const GfView& v, double* pmass,
                           void* stream);
-int launch_controller(const GfGeom& g, const GfView& v, const double* pmass,
-                      int nscen, void* stream);
 int launch_ctl_begin(GfCtl* ctl, int nscen, double t_target,
                      long long max_steps, const int* scen_mask, void* stream);
 int launch_ghost_fill(const GfGeom& g, const GfView& v, int only_active,

@@ -13,77 +13,6 @@
 
 namespace {
 
-// Controller: one block per scenario.  Sums the per-patch volumes in a fixed
-// order, then thread 0 applies the CFL rule (Sec. 5.1, Sec. 6.6): reject and
-// retake when dt*cmax > cfl_max, else accept, advance t and pick the next dt.
-__global__ void k_controller(const GfGeom G, GfCtl* ctl, const GfScenario* sc,
-                             const double* __restrict__ pmass) {
-  const int s = blockIdx.x;
-  GfCtl* C = ctl + s;
-  __shared__ double red[256];
-  __shared__ int act;
-  if (threadIdx.x == 0) {
-    act = C->active;
-    if (!act) C->accepted = 0;
-  }
-  __syncthreads();
-  if (!act) return;
-  const int off = sc[s].poff, n = sc[s].pcount;
-  double v = 0.0;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) v += pmass[off + k];
-  red[threadIdx.x] = v;
-  __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x != 0) return;
-  const double cmax = __longlong_as_double((long long)C->cmax_bits);
-  C->cmax_bits = 0ull;
-  const double dt = C->dt_use;
-  if (C->nonfinite) {
-    C->status = -5;  // GEOFLOOD_ERR_NAN
-    C->active = 0;
-    C->accepted = 0;
-    return;
-  }
-  if (dt * cmax > G.cfl_max) {
-    C->dt_next = G.cfl_desired / cmax;
-    C->rejects += 1;
-    C->accepted = 0;
-    C->step_nclip = 0ull;
-    C->step_clipvol = 0.0;
-    if (++C->inrow > GF_MAXSTEP_REJECT) {
-      C->status = -4;  // GEOFLOOD_ERR_CFL
-      C->active = 0;
-      return;
-    }
-  } else {
-    C->inrow = 0;
-    C->cur ^= 1;
-    C->t = C->last ? C->t_target : C->t + dt;
-    C->steps += 1;
-    C->taken += 1;
-    C->nclip += (long long)C->step_nclip;
-    C->clipvol += C->step_clipvol;
-    C->step_nclip = 0ull;
-    C->step_clipvol = 0.0;
-    C->mass = red[0];
-    C->accepted = 1;
-    if (cmax > 0.0) {
-      const double dn = G.cfl_desired / cmax;
-      C->dt_next = dn < G.dt_max ? dn : G.dt_max;
-    }
-  }
-  if (!(C->t < C->t_target) || C->taken >= C->max_steps) {
-    C->active = 0;
-    return;
-  }
-  const double rem = C->t_target - C->t;
-  if (C->dt_next < rem) { C->dt_use = C->dt_next; C->last = 0; }
-  else { C->dt_use = rem; C->last = 1; }
-}
-
 __global__ void k_ctl_begin(GfCtl* ctl, int nscen, double t_target,
                             long long max_steps, const int* mask) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -119,13 +48,6 @@ int launch_patch_step_f64(const GfGeom& g, const GfView& v, double* pmass,
   if (g.M == 32) return gfs::launch_step<gfs::PrecF64, 32, 512, 1>(g, v, pmass, st);
   if (g.M == 16) return gfs::launch_step<gfs::PrecF64, 16, 256, 1>(g, v, pmass, st);
   return -1;
-}
-
-int launch_controller(const GfGeom& g, const GfView& v, const double* pmass,
-                      int nscen, void* stream) {
-  k_controller<<<nscen, 256, 0, static_cast<cudaStream_t>(stream)>>>(
-      g, v.ctl, v.scen, pmass);
-  return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
 int launch_ctl_begin(GfCtl* ctl, int nscen, double t_target,

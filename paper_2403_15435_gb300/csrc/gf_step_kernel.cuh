@@ -137,9 +137,10 @@ __device__ __forceinline__ void cell_item(int k, int dir, int& a, int& line) {
   }
 }
 
-template <class P, int M, int NT, int MINB>
-__global__ void __launch_bounds__(NT, MINB)
-    k_patch_step(const GfGeom G, const GfView V, double* __restrict__ pmass) {
+template <class P, int M, int NT>
+__device__ __forceinline__ void patch_body(const GfGeom& G, const GfView& V,
+                                           double* __restrict__ pmass,
+                                           unsigned char* smraw) {
   using R = typename P::R;
   constexpr bool DEV = P::DEV;
   using Lo = Layout<P, M>;
@@ -151,9 +152,7 @@ __global__ void __launch_bounds__(NT, MINB)
   const int p = blockIdx.x;
   const GfPatch Pt = V.patch[p];
   GfCtl* C = V.ctl + Pt.scen;
-  if (!C->active) return;
 
-  extern __shared__ __align__(16) unsigned char smraw[];
   R* s0 = reinterpret_cast<R*>(smraw);  // h (FP64) or w (deviation form)
   R* shu = s0 + TT;
   R* shv = s0 + 2 * TT;
@@ -190,24 +189,45 @@ __global__ void __launch_bounds__(NT, MINB)
     bulk_g2s(sb, bs, TT * sizeof(R), bar);
   }
   __syncthreads();
-  if (!mbar_wait(bar, GF_SPIN_LIMIT)) {
+  // every wait is bounded; the decision to give up is taken by the whole CTA
+  if (!__syncthreads_and(mbar_wait(bar, GF_SPIN_LIMIT) ? 1 : 0)) {
     if (tid == 0) C->status = -7;  // GEOFLOOD_ERR_TIMEOUT
     mbar_wait(bar, GF_SPIN_LIMIT);
+    __syncthreads();
     return;
   }
 
+  // per-patch scalars: computed once by thread 0 (FP64 divisions are slow
+  // on this part, so no thread repeats them) and broadcast through shared
+  // memory
+  double* scal = red + 48;  // dx, dy, nux, nuy, then the R-typed copies
+  R* rscal = reinterpret_cast<R*>(red + 52);  // g, drytol, nux, nuy, n, dt
+  float* fscal = reinterpret_cast<float*>(red + 60);  // drytol, margin
+  if (tid == 0) {
+    const long long NXL = (long long)G.mi * M << Pt.level;
+    const long long NYL = (long long)G.mj * M << Pt.level;
+    const double dx0 = (G.xupper - G.xlower) / (double)NXL;
+    const double dy0 = (G.yupper - G.ylower) / (double)NYL;
+    scal[0] = dx0;
+    scal[1] = dy0;
+    scal[2] = C->dt_use / dx0;
+    scal[3] = C->dt_use / dy0;
+    rscal[0] = (R)G.g;
+    rscal[1] = (R)G.drytol;
+    rscal[2] = (R)scal[2];
+    rscal[3] = (R)scal[3];
+    rscal[4] = (R)V.scen[Pt.scen].manning_n;
+    rscal[5] = (R)C->dt_use;
+    fscal[0] = (float)G.drytol;
+    fscal[1] = (float)(G.drytol * 0x1p-20);
+  }
   const double drytol = G.drytol;
-  const R g = (R)G.g;
-  const R rdry = (R)drytol;
-  const float dtf = (float)drytol;
-  const float margin = (float)(drytol * 0x1p-20);
-  const double dt = C->dt_use;
-  const long long NXL = (long long)G.mi * M << Pt.level;
-  const long long NYL = (long long)G.mj * M << Pt.level;
-  const double dx = (G.xupper - G.xlower) / (double)NXL;
-  const double dy = (G.yupper - G.ylower) / (double)NYL;
-  const R nux = (R)(dt / dx), nuy = (R)(dt / dy);
   R smx = R(0), smy = R(0);
+
+  __syncthreads();
+  const R g = rscal[0], rdry = rscal[1], nux = rscal[2], nuy = rscal[3];
+  const R dtr = rscal[5];
+  const float dtf = fscal[0], margin = fscal[1];
 
   // Per-cell depth and exact wet flag (deviation form), and whether the
   // tile holds any wet cell at all.
@@ -224,6 +244,7 @@ __global__ void __launch_bounds__(NT, MINB)
     }
   }
   anywet = __syncthreads_or(anywet);
+  const double dx = scal[0], dy = scal[1];
   auto wetc = [&](int c) -> bool {
     if constexpr (DEV) return swet[c] != 0;
     else return s0[c] > rdry;
@@ -368,7 +389,7 @@ __global__ void __launch_bounds__(NT, MINB)
   }
 
   // ------------------------------------------------ update, friction, out
-  const R mn = (R)V.scen[Pt.scen].manning_n;
+  const R mn = rscal[4];
   double vol = 0.0, clipd = 0.0;
   R volr = R(0);
   unsigned nclip = 0, nwet = 0;
@@ -416,7 +437,7 @@ __global__ void __launch_bounds__(NT, MINB)
         const R u = o[1] / o[0], v = o[2] / o[0];
         const R sp = sqrt(u * u + v * v);
         const R D = g * mn * mn * sp / (o[0] * cbrt(o[0]));
-        const R den = R(1) + (R)dt * D;
+        const R den = R(1) + dtr * D;
         o[1] = o[1] / den;
         o[2] = o[2] / den;
       }
@@ -450,7 +471,7 @@ __global__ void __launch_bounds__(NT, MINB)
         const float u = o[1] / h, v = o[2] / h;
         const float sp = sqrtf(u * u + v * v);
         const float D = g * mn * mn * sp / (h * cbrtf(h));
-        const float den = 1.0f + (float)dt * D;
+        const float den = 1.0f + dtr * D;
         o[1] = o[1] / den;
         o[2] = o[2] / den;
         lo[1] = lo[1] / den;
@@ -466,14 +487,20 @@ __global__ void __launch_bounds__(NT, MINB)
     qd[TT + c] = o[1];
     qd[2 * TT + c] = o[2];
   }
-  if constexpr (DEV) vol = (double)volr;
-
-  // block reductions: CFL rate (max), volume (FP64, fixed-order tree)
+  // block reductions: CFL rate (max), volume (fixed-order tree; FP64 in the
+  // plain form, FP32 within a warp and FP64 across warps in the deviation
+  // form)
   const int lane = tid & 31, wid = tid >> 5;
   constexpr int NW = NT / 32;
   smx = warp_max(smx);
   smy = warp_max(smy);
-  vol = warp_sum_tree(vol);
+  if constexpr (DEV) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) volr += __shfl_down_sync(0xffffffffu, volr, o);
+    vol = lane == 0 ? (double)volr : 0.0;
+  } else {
+    vol = warp_sum_tree(vol);
+  }
   nwet = __reduce_add_sync(0xffffffffu, nwet);
   if (lane == 0 && nwet) atomicAdd(&C->wet_updates, (unsigned long long)nwet);
   if (lane == 0) {
@@ -500,6 +527,112 @@ __global__ void __launch_bounds__(NT, MINB)
     atomicAdd(&C->step_clipvol, clipd * (dx * dy));
   }
   if (bad) C->nonfinite = 1;
+}
+
+// End of a step: the last CTA to finish applies the CFL rule to every active
+// scenario (Sec. 5.1 maximum CFL, Sec. 6.6): it sums the per-patch volumes in
+// a fixed order, rejects the step and sets a smaller dt when dt*cmax exceeds
+// cfl_max, else accepts it (swaps the state buffers, advances t) and picks
+// the next dt = cfl_desired / cmax, clipped to land on t_target.
+template <int NT>
+__device__ void step_finish(const GfGeom& G, const GfView& V,
+                            const double* pmass, double* red) {
+  __shared__ int last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned t = atomicAdd(V.done, 1u);
+    last = t == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  constexpr int NW = NT / 32;
+  const volatile double* pm = pmass;
+  for (int s = 0; s < G.nscen; ++s) {
+    volatile GfCtl* C = V.ctl + s;
+    const int act = C->active;
+    __syncthreads();
+    if (!act) {
+      if (tid == 0) C->accepted = 0;
+      continue;
+    }
+    const int off = V.scen[s].poff, n = V.scen[s].pcount;
+    double v = 0.0;
+    for (int k = tid; k < n; k += NT) v += pm[off + k];
+    v = warp_sum_tree(v);
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    if (tid == 0) {
+      double vol = 0.0;
+      for (int w = 0; w < NW; ++w) vol += red[w];
+      const double cmax = __longlong_as_double((long long)C->cmax_bits);
+      C->cmax_bits = 0ull;
+      const double dt = C->dt_use;
+      bool go_on = true;
+      if (C->nonfinite) {
+        C->status = -5;  // GEOFLOOD_ERR_NAN
+        C->active = 0;
+        C->accepted = 0;
+        go_on = false;
+      } else if (dt * cmax > G.cfl_max) {
+        C->dt_next = G.cfl_desired / cmax;
+        C->rejects = C->rejects + 1;
+        C->accepted = 0;
+        C->step_nclip = 0ull;
+        C->step_clipvol = 0.0;
+        C->inrow = C->inrow + 1;
+        if (C->inrow > GF_MAXSTEP_REJECT) {
+          C->status = -4;  // GEOFLOOD_ERR_CFL
+          C->active = 0;
+          go_on = false;
+        }
+      } else {
+        C->inrow = 0;
+        C->cur = C->cur ^ 1;
+        C->t = C->last ? C->t_target : C->t + dt;
+        C->steps = C->steps + 1;
+        C->taken = C->taken + 1;
+        C->nclip = C->nclip + (long long)C->step_nclip;
+        C->clipvol = C->clipvol + C->step_clipvol;
+        C->step_nclip = 0ull;
+        C->step_clipvol = 0.0;
+        C->mass = vol;
+        C->accepted = 1;
+        if (cmax > 0.0) {
+          const double dn = G.cfl_desired / cmax;
+          C->dt_next = dn < G.dt_max ? dn : G.dt_max;
+        }
+      }
+      if (go_on) {
+        if (!(C->t < C->t_target) || C->taken >= C->max_steps) {
+          C->active = 0;
+        } else {
+          const double rem = C->t_target - C->t;
+          if (C->dt_next < rem) { C->dt_use = C->dt_next; C->last = 0; }
+          else { C->dt_use = rem; C->last = 1; }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    __threadfence();
+    *V.done = 0u;
+  }
+}
+
+template <class P, int M, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
+    k_patch_step(const __grid_constant__ GfGeom G,
+                 const __grid_constant__ GfView V, double* __restrict__ pmass) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const GfPatch Pt = V.patch[blockIdx.x];
+  if (V.ctl[Pt.scen].active) patch_body<P, M, NT>(G, V, pmass, smraw);
+  if (V.done)
+    step_finish<NT>(G, V, pmass,
+                    reinterpret_cast<double*>(smraw + Layout<P, M>::OFF_RED));
 }
 
 template <class P, int M, int NT, int MINB>
