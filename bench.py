@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--profile-steps", type=int, default=20)
     ap.add_argument("--profile-precision", type=int, default=1, choices=[0, 1],
                     help="0 = FP64, 1 = FP32 deviation form")
+    ap.add_argument("--profile-variant", type=int, default=0,
+                    help="patch-step kernel variant (see geoflood_autotune)")
     return ap.parse_args()
 
 
@@ -61,6 +63,7 @@ def run_profile_case(args):
     prob.cfg.precision = args.profile_precision
     f = geoflood.Forest(prob.cfg, prob.dem, max_patches=(n // PATCH) ** 2)
     f.set_state(prob.ic)
+    f.set_variant(args.profile_variant)
     _, steps = f.step(1e9, args.profile_steps)
     print("profile case %d x %d: %d steps, t = %.3f s" % (n, n, steps, f.time()["t"]))
 
@@ -180,6 +183,8 @@ def measure(prec, args, dev, stream, world, local, gauges):
         reset()
         f.step(args.t_end)
     torch.cuda.synchronize(dev)
+    # autotune the kernel shape on the end state of the warm-up run
+    variant, variant_ms = f.autotune(5)
 
     steps_list, ev = [], []
     launches0 = f.launch_count()
@@ -228,6 +233,7 @@ def measure(prec, args, dev, stream, world, local, gauges):
            "d2h_bytes_per_step": 3 * cells * 8}
     f.close()
     return dict(value=value, ms_per_step=1e3 * total_t / args.steps, steps=steps_list,
+                variant=variant, variant_ms=[float(x) for x in variant_ms[:2]],
                 cells=cells, patches=n, launches=launches, clocks=clk.summary(),
                 k_ms=k_ms, k_n=k_n, wet=wet1 - wet0, updates=cu1 - cu0, e2e=e2e,
                 gauges=gauge_out, arrival=arrival, final=final)
@@ -304,6 +310,9 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "cells": r32["cells"], "patches": r32["patches"],
                    "accepted_steps_per_run": r32["steps"][0],
                    "precision": "FP32 surface-deviation form (compensated update, exact wet tests)",
+                   "kernel_variant": {"chosen": r32["variant"], "ms_per_launch": r32["variant_ms"],
+                                      "variants": ["32x32 tile per 512-thread CTA, TMA bulk staging",
+                                                   "16x16 sub-tiles, 4 x 352-thread CTAs per patch"]},
                    "tagging": "none: uniform single-level grid, no regrid in this workload",
                    "l2": "flushed (256 MB write) before each timed run; within a run the "
                          "working set stays in L2",
@@ -311,6 +320,7 @@ def run_ours(args):
         "roofline": roof32, "cpu_baseline": cpu, "e2e": r32["e2e"],
         "gpu_launches": r32["launches"], "clocks": r32["clocks"],
         "fp64": {"value": r64["value"], "ms_per_step": r64["ms_per_step"], "dtype": "f64",
+                 "kernel_variant": {"chosen": r64["variant"], "ms_per_launch": r64["variant_ms"]},
                  "accepted_steps_per_run": r64["steps"][0], "roofline": roof64,
                  "e2e": r64["e2e"], "gpu_launches": r64["launches"], "clocks": r64["clocks"]},
         "fp32_vs_fp64_error": err,

@@ -210,6 +210,21 @@ int geoflood_profile_read(geoflood_ctx* ctx, const char* kernel,
 int geoflood_counters(geoflood_ctx* ctx, int scenario, long long* cell_updates,
                       long long* wet_cell_updates);
 
+/* Autotuner of the patch-step kernel shape (patch size, threads per CTA,
+ * halo staging): times every available variant reps times on the current
+ * state (without advancing it), selects the fastest for this context and
+ * returns its number in *variant and the times (ms per launch) in
+ * ms_per_variant (two entries for 32 x 32 patches, one for 16 x 16; either
+ * pointer may be NULL).  Variants of 32 x 32 patches: 0 = one 512-thread CTA
+ * per patch staging the whole tile by TMA bulk copies, 1 = four CTAs per
+ * patch, each staging a 16 x 16 sub-tile with its two-cell halo.  Results
+ * do not depend on the variant. */
+int geoflood_autotune(geoflood_ctx* ctx, int reps, int* variant,
+                      double* ms_per_variant);
+
+/* Select a patch-step variant by number (see geoflood_autotune). */
+int geoflood_set_variant(geoflood_ctx* ctx, int variant);
+
 /* Number of kernels this context has launched since it was created. */
 int geoflood_launch_count(geoflood_ctx* ctx, long long* launches);
 

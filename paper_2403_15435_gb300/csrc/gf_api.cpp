@@ -44,7 +44,7 @@ struct geoflood_ctx {
   // CUDA graphs of chunks of steps, keyed by chunk length
   struct Graph {
     cudaGraphExec_t exec = nullptr;
-    int k = 0, tsel = -1, bsel = -1, npatch = -1, gauges = -1, prof = -1;
+    int k = 0, tsel = -1, bsel = -1, npatch = -1, gauges = -1, prof = -1, variant = -1;
     std::vector<ProfRec> ev;
   };
   std::vector<Graph> graphs;
@@ -62,6 +62,7 @@ struct geoflood_ctx {
   std::vector<gf::HostForest> forests;
   std::vector<double*> d_dem, d_gxy, d_gout, d_garr;
   int max_gauges_used = 0;
+  int variant = 0;  // patch-step kernel variant (see geoflood_autotune)
   std::string err;
   bool prof = false;
   std::map<std::string, std::vector<ProfRec>> prof_recs;
@@ -344,7 +345,7 @@ int geoflood_init_forest(const geoflood_config* cfg, void* stream,
   okk &= alloc((void**)&ctx->d_lut[1], (size_t)ctx->nscen * G.lut_per_scen * sizeof(int));
   okk &= alloc((void**)&ctx->d_scen, ctx->nscen * sizeof(GfScenario));
   okk &= alloc((void**)&ctx->d_ctl, ctx->nscen * sizeof(GfCtl));
-  okk &= alloc((void**)&ctx->d_pmass, cap * sizeof(double));
+  okk &= alloc((void**)&ctx->d_pmass, cap * 4 * sizeof(double));  // per sub-tile
   okk &= alloc((void**)&ctx->d_smass, ctx->nscen * sizeof(double));
   okk &= alloc((void**)&ctx->d_flags, cap);
   okk &= alloc((void**)&ctx->d_err, sizeof(int));
@@ -662,7 +663,7 @@ int geoflood_step(geoflood_ctx* ctx, double t_target, int max_steps,
   const int prof = ctx->prof ? 1 : 0;
   if (!gr->exec || gr->tsel != ctx->tsel || gr->bsel != ctx->bsel ||
       gr->npatch != ctx->npatch || gr->gauges != ctx->max_gauges_used ||
-      gr->prof != prof) {
+      gr->prof != prof || gr->variant != ctx->variant) {
     if (gr->exec) cudaGraphExecDestroy(gr->exec);
     gr->exec = nullptr;
     gr->ev.clear();
@@ -676,8 +677,8 @@ int geoflood_step(geoflood_ctx* ctx, double t_target, int max_steps,
         // an external record node: the event is recorded at every replay
         cudaEventRecordWithFlags(r.a, ctx->st, cudaEventRecordExternal);
       }
-      lrc |= ctx->prec ? gf::launch_patch_step_f32(ctx->G, v, ctx->d_pmass, ctx->st)
-                       : gf::launch_patch_step_f64(ctx->G, v, ctx->d_pmass, ctx->st);
+      lrc |= ctx->prec ? gf::launch_patch_step_f32(ctx->G, v, ctx->d_pmass, ctx->variant, ctx->st)
+                       : gf::launch_patch_step_f64(ctx->G, v, ctx->d_pmass, ctx->variant, ctx->st);
       if (prof) {
         cudaEventRecordWithFlags(r.b, ctx->st, cudaEventRecordExternal);
         gr->ev.push_back(r);
@@ -701,6 +702,7 @@ int geoflood_step(geoflood_ctx* ctx, double t_target, int max_steps,
     gr->npatch = ctx->npatch;
     gr->gauges = ctx->max_gauges_used;
     gr->prof = prof;
+    gr->variant = ctx->variant;
   }
   const int per_step = 2 + (ctx->max_gauges_used > 0 ? 1 : 0);
   long long launched = 0;
@@ -889,6 +891,58 @@ int geoflood_counters(geoflood_ctx* ctx, int s, long long* cell_updates,
   if (rc) return rc;
   if (cell_updates) *cell_updates = (long long)ctx->h_ctl[s].cell_updates;
   if (wet_cell_updates) *wet_cell_updates = (long long)ctx->h_ctl[s].wet_updates;
+  return 0;
+}
+
+int geoflood_autotune(geoflood_ctx* ctx, int reps, int* variant,
+                      double* ms_per_variant) {
+  if (!ctx || reps < 1) return GEOFLOOD_ERR_ARG;
+  int rc = sync_ctl_down(ctx);
+  if (rc) return rc;
+  // time every variant on the current state: the launches write only the
+  // next-state buffer and the step counters, which are restored afterwards
+  std::vector<GfCtl> saved(ctx->h_ctl, ctx->h_ctl + ctx->nscen);
+  for (int s = 0; s < ctx->nscen; ++s) {
+    ctx->h_ctl[s].active = 1;
+    if (!(ctx->h_ctl[s].dt_use > 0)) ctx->h_ctl[s].dt_use = ctx->h_ctl[s].dt_next;
+  }
+  if ((rc = sync_ctl_up(ctx))) return rc;
+  GfView v = view(ctx);
+  v.done = nullptr;  // no controller: the state does not advance
+  const int nv = gf::patch_step_variants(ctx->G.M);
+  cudaEvent_t a = pool_event(ctx), b = pool_event(ctx);
+  int best = 0;
+  double best_ms = 1e300;
+  for (int k = 0; k < nv; ++k) {
+    for (int w = 0; w < 2; ++w)  // warm-up
+      CKL(ctx->prec ? gf::launch_patch_step_f32(ctx->G, v, ctx->d_pmass, k, ctx->st)
+                    : gf::launch_patch_step_f64(ctx->G, v, ctx->d_pmass, k, ctx->st),
+          "autotune");
+    CK(cudaEventRecord(a, ctx->st));
+    for (int r = 0; r < reps; ++r)
+      CKL(ctx->prec ? gf::launch_patch_step_f32(ctx->G, v, ctx->d_pmass, k, ctx->st)
+                    : gf::launch_patch_step_f64(ctx->G, v, ctx->d_pmass, k, ctx->st),
+          "autotune");
+    CK(cudaEventRecord(b, ctx->st));
+    CK(cudaEventSynchronize(b));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, a, b));
+    const double per = ms / reps;
+    if (ms_per_variant) ms_per_variant[k] = per;
+    if (per < best_ms) { best_ms = per; best = k; }
+    ctx->launches += reps + 2;
+  }
+  std::copy(saved.begin(), saved.end(), ctx->h_ctl);
+  if ((rc = sync_ctl_up(ctx))) return rc;
+  ctx->variant = best;
+  if (variant) *variant = best;
+  return 0;
+}
+
+int geoflood_set_variant(geoflood_ctx* ctx, int variant) {
+  if (!ctx || variant < 0 || variant >= gf::patch_step_variants(ctx->G.M))
+    return fail(ctx, GEOFLOOD_ERR_ARG, "set_variant: no such variant");
+  ctx->variant = variant;
   return 0;
 }
 

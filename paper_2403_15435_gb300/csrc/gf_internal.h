@@ -91,10 +91,11 @@ struct GfView {
 
 // Kernel launchers (defined in the .cu files).
 namespace gf {
+int patch_step_variants(int mx);
 int launch_patch_step_f64(const GfGeom& g, const GfView& v, double* pmass,
-                          void* stream);
+                          int variant, void* stream);
 int launch_patch_step_f32(const GfGeom& g, const GfView& v, double* pmass,
-                          void* stream);
+                          int variant, void* stream);
 int launch_ctl_begin(GfCtl* ctl, int nscen, double t_target,
                      long long max_steps, const int* scen_mask, void* stream);
 int launch_ghost_fill(const GfGeom& g, const GfView& v, int only_active,

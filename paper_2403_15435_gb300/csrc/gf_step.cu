@@ -41,12 +41,20 @@ __global__ void k_ctl_begin(GfCtl* ctl, int nscen, double t_target,
 
 namespace gf {
 
+// Kernel variants (the autotuner picks one per context): for 32 x 32
+// patches, 0 = one 512-thread CTA per patch (TMA bulk staging of the whole
+// tile), 1 = four 256-thread CTAs of 16 x 16 sub-tiles; 16 x 16 patches have
+// the single variant 0.
+int patch_step_variants(int mx) { return mx == 32 ? 2 : 1; }
+
 int launch_patch_step_f64(const GfGeom& g, const GfView& v, double* pmass,
-                          void* stream) {
+                          int variant, void* stream) {
   if (v.npatch <= 0) return 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (g.M == 32) return gfs::launch_step<gfs::PrecF64, 32, 512, 1>(g, v, pmass, st);
-  if (g.M == 16) return gfs::launch_step<gfs::PrecF64, 16, 256, 1>(g, v, pmass, st);
+  if (g.M == 32 && variant == 1)
+    return gfs::launch_step<gfs::PrecF64, 32, 16, 256, 2>(g, v, pmass, st);
+  if (g.M == 32) return gfs::launch_step<gfs::PrecF64, 32, 32, 512, 1>(g, v, pmass, st);
+  if (g.M == 16) return gfs::launch_step<gfs::PrecF64, 16, 16, 256, 1>(g, v, pmass, st);
   return -1;
 }
 
@@ -184,8 +192,8 @@ extern "C" int geoflood_step_tiles_noalloc(const double* q_in, const double* b,
   if (cudaGetLastError() != cudaSuccess)
     return noalloc_fail(-2, "step_tiles_noalloc: init launch failed");
   const int lr = mx == 32
-                     ? gfs::launch_step<gfs::PrecF64, 32, 512, 1>(G, V, S->pmass, st)
-                     : gfs::launch_step<gfs::PrecF64, 16, 256, 1>(G, V, S->pmass, st);
+                     ? gfs::launch_step<gfs::PrecF64, 32, 32, 512, 1>(G, V, S->pmass, st)
+                     : gfs::launch_step<gfs::PrecF64, 16, 16, 256, 1>(G, V, S->pmass, st);
   if (lr) return noalloc_fail(-2, "step_tiles_noalloc: step launch failed");
   if (cmax) {
     unsigned long long bits = 0;

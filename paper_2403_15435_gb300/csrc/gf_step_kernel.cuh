@@ -137,7 +137,13 @@ __device__ __forceinline__ void cell_item(int k, int dir, int& a, int& line) {
   }
 }
 
-template <class P, int M, int NT>
+// M is the side of the sub-tile this CTA updates, MP the side of the patch:
+// a patch of MP x MP cells is covered by (MP/M)^2 CTAs, each staging its
+// (M+4)^2 window (interior + two ghost layers, taken from the patch tile,
+// whose ghosts are filled) and writing its M x M cells.  Every cell's update
+// depends only on its two-cell neighbourhood, so the result does not depend
+// on M.
+template <class P, int MP, int M, int NT>
 __device__ __forceinline__ void patch_body(const GfGeom& G, const GfView& V,
                                            double* __restrict__ pmass,
                                            unsigned char* smraw) {
@@ -145,13 +151,19 @@ __device__ __forceinline__ void patch_body(const GfGeom& G, const GfView& V,
   constexpr bool DEV = P::DEV;
   using Lo = Layout<P, M>;
   constexpr int TT = Lo::TT, NE = Lo::NE;
+  constexpr int TGW = MP + 2 * GF_NG, TG = TGW * TGW;  // patch tile
+  constexpr int NS1 = MP / M, NSUB = NS1 * NS1;
   constexpr int RL = (Lo::NLIM + NT - 1) / NT;    // limiter items per thread
   constexpr int RC = (M * M + NT - 1) / NT;       // interior cells per thread
   constexpr int RX = (Lo::NCELL + NT - 1) / NT;   // increment cells per thread
 
-  const int p = blockIdx.x;
+  const int p = blockIdx.x / NSUB, sub = blockIdx.x % NSUB;
+  const int ox = (sub % NS1) * M, oy = (sub / NS1) * M;
   const GfPatch Pt = V.patch[p];
   GfCtl* C = V.ctl + Pt.scen;
+  // global tile index of local cell (i, j), and interior index in the patch
+  auto gix = [&](int i, int j) { return (ox + i + GF_NG) + (oy + j + GF_NG) * TGW; };
+  auto pix = [&](int i, int j) { return (ox + i) + (oy + j) * MP; };
 
   R* s0 = reinterpret_cast<R*>(smraw);  // h (FP64) or w (deviation form)
   R* shu = s0 + TT;
@@ -171,30 +183,44 @@ __device__ __forceinline__ void patch_body(const GfGeom& G, const GfView& V,
   R* qd;
   const R* bs;
   if constexpr (DEV) {
-    qs = V.qf[cur] + (size_t)p * 3 * TT;
-    qd = V.qf[cur ^ 1] + (size_t)p * 3 * TT;
-    bs = V.bf + (size_t)p * TT;
+    qs = V.qf[cur] + (size_t)p * 3 * TG;
+    qd = V.qf[cur ^ 1] + (size_t)p * 3 * TG;
+    bs = V.bf + (size_t)p * TG;
   } else {
-    qs = V.q[cur] + (size_t)p * 3 * TT;
-    qd = V.q[cur ^ 1] + (size_t)p * 3 * TT;
-    bs = V.b + (size_t)p * TT;
+    qs = V.q[cur] + (size_t)p * 3 * TG;
+    qd = V.q[cur ^ 1] + (size_t)p * 3 * TG;
+    bs = V.b + (size_t)p * TG;
   }
 
-  if (tid == 0) {
-    mbar_init(bar, 1);
-    mbar_expect_tx(bar, 4u * TT * sizeof(R));
-    bulk_g2s(s0, qs, TT * sizeof(R), bar);
-    bulk_g2s(shu, qs + TT, TT * sizeof(R), bar);
-    bulk_g2s(shv, qs + 2 * TT, TT * sizeof(R), bar);
-    bulk_g2s(sb, bs, TT * sizeof(R), bar);
-  }
-  __syncthreads();
-  // every wait is bounded; the decision to give up is taken by the whole CTA
-  if (!__syncthreads_and(mbar_wait(bar, GF_SPIN_LIMIT) ? 1 : 0)) {
-    if (tid == 0) C->status = -7;  // GEOFLOOD_ERR_TIMEOUT
-    mbar_wait(bar, GF_SPIN_LIMIT);
+  if constexpr (M == MP) {
+    // whole patch: its four contiguous fields arrive by 1D TMA bulk copies
+    if (tid == 0) {
+      mbar_init(bar, 1);
+      mbar_expect_tx(bar, 4u * TT * sizeof(R));
+      bulk_g2s(s0, qs, TT * sizeof(R), bar);
+      bulk_g2s(shu, qs + TT, TT * sizeof(R), bar);
+      bulk_g2s(shv, qs + 2 * TT, TT * sizeof(R), bar);
+      bulk_g2s(sb, bs, TT * sizeof(R), bar);
+    }
     __syncthreads();
-    return;
+    // every wait is bounded; the decision to give up is taken by the whole CTA
+    if (!__syncthreads_and(mbar_wait(bar, GF_SPIN_LIMIT) ? 1 : 0)) {
+      if (tid == 0) C->status = -7;  // GEOFLOOD_ERR_TIMEOUT
+      mbar_wait(bar, GF_SPIN_LIMIT);
+      __syncthreads();
+      return;
+    }
+  } else {
+    // sub-tile: the (M+4)^2 window of each field, row segments read with
+    // consecutive threads on consecutive addresses
+    for (int k = tid; k < TT; k += NT) {
+      const int li = k % Lo::T, lj = k / Lo::T;
+      const int g = (ox + li) + (oy + lj) * TGW;
+      s0[k] = qs[g];
+      shu[k] = qs[TG + g];
+      shv[k] = qs[2 * TG + g];
+      sb[k] = bs[g];
+    }
   }
 
   // per-patch scalars: computed once by thread 0 (FP64 divisions are slow
@@ -204,8 +230,8 @@ __device__ __forceinline__ void patch_body(const GfGeom& G, const GfView& V,
   R* rscal = reinterpret_cast<R*>(red + 52);  // g, drytol, nux, nuy, n, dt
   float* fscal = reinterpret_cast<float*>(red + 60);  // drytol, margin
   if (tid == 0) {
-    const long long NXL = (long long)G.mi * M << Pt.level;
-    const long long NYL = (long long)G.mj * M << Pt.level;
+    const long long NXL = (long long)G.mi * MP << Pt.level;
+    const long long NYL = (long long)G.mj * MP << Pt.level;
     const double dx0 = (G.xupper - G.xlower) / (double)NXL;
     const double dy0 = (G.yupper - G.ylower) / (double)NYL;
     scal[0] = dx0;
@@ -397,8 +423,8 @@ __device__ __forceinline__ void patch_body(const GfGeom& G, const GfView& V,
   const float* los = nullptr;
   float* lod = nullptr;
   if constexpr (DEV) {
-    los = V.lof[cur] + (size_t)p * 3 * M * M;
-    lod = V.lof[cur ^ 1] + (size_t)p * 3 * M * M;
+    los = V.lof[cur] + (size_t)p * 3 * MP * MP;
+    lod = V.lof[cur ^ 1] + (size_t)p * 3 * MP * MP;
   }
 #pragma unroll
   for (int r = 0; r < RC; ++r) {
@@ -406,14 +432,15 @@ __device__ __forceinline__ void patch_body(const GfGeom& G, const GfView& V,
     if (k >= M * M) continue;
     const int i = k % M, j = k / M;
     const int c = tix<M>(i, j);
+    const int cg = gix(i, j), kp = pix(i, j);
     if (!anywet) {
-      qd[c] = s0[c];
-      qd[TT + c] = R(0);
-      qd[2 * TT + c] = R(0);
+      qd[cg] = s0[c];
+      qd[TG + cg] = R(0);
+      qd[2 * TG + cg] = R(0);
       if constexpr (DEV) {
-        lod[k] = los[k];
-        lod[M * M + k] = 0.0f;
-        lod[2 * M * M + k] = 0.0f;
+        lod[kp] = los[kp];
+        lod[MP * MP + kp] = 0.0f;
+        lod[2 * MP * MP + kp] = 0.0f;
         volr += sdep[c];
       } else {
         vol += s0[c];
@@ -452,7 +479,7 @@ __device__ __forceinline__ void patch_body(const GfGeom& G, const GfView& V,
         const float* fa = Ftr + 3 * (j * (M + 1) + i);
         const float* ga = Gtr + 3 * (i * (M + 1) + j);
         const float tf = nux * (fa[3 + f] - fa[f]) + nuy * (ga[3 + f] - ga[f]);
-        const float x = (los[f * M * M + k] - fl) - tf;
+        const float x = (los[f * MP * MP + kp] - fl) - tf;
         const float s = q[f] + x;
         const float bb = s - q[f];
         lo[f] = (q[f] - (s - bb)) + (x - bb);
@@ -479,13 +506,13 @@ __device__ __forceinline__ void patch_body(const GfGeom& G, const GfView& V,
       }
       if (!wnew) { o[1] = 0.0f; o[2] = 0.0f; lo[1] = 0.0f; lo[2] = 0.0f; }
 #pragma unroll
-      for (int f = 0; f < 3; ++f) lod[f * M * M + k] = lo[f];
+      for (int f = 0; f < 3; ++f) lod[f * MP * MP + kp] = lo[f];
       volr += o[0] - bc;
     }
     bad |= !(isfinite(o[0]) && isfinite(o[1]) && isfinite(o[2]));
-    qd[c] = o[0];
-    qd[TT + c] = o[1];
-    qd[2 * TT + c] = o[2];
+    qd[cg] = o[0];
+    qd[TG + cg] = o[1];
+    qd[2 * TG + cg] = o[2];
   }
   // block reductions: CFL rate (max), volume (fixed-order tree; FP64 in the
   // plain form, FP32 within a warp and FP64 across warps in the deviation
@@ -520,7 +547,7 @@ __device__ __forceinline__ void patch_body(const GfGeom& G, const GfView& V,
     const double cm = cx > cy ? cx : cy;
     atomicMax(&C->cmax_bits, (unsigned long long)__double_as_longlong(cm));
     atomicAdd(&C->cell_updates, (unsigned long long)(M * M));
-    pmass[p] = vs * (dx * dy);
+    pmass[blockIdx.x] = vs * (dx * dy);
   }
   if (nclip) {
     atomicAdd(&C->step_nclip, (unsigned long long)nclip);
@@ -536,7 +563,7 @@ __device__ __forceinline__ void patch_body(const GfGeom& G, const GfView& V,
 // the next dt = cfl_desired / cmax, clipped to land on t_target.
 template <int NT>
 __device__ void step_finish(const GfGeom& G, const GfView& V,
-                            const double* pmass, double* red) {
+                            const double* pmass, double* red, int nsub) {
   __shared__ int last;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -558,7 +585,7 @@ __device__ void step_finish(const GfGeom& G, const GfView& V,
       if (tid == 0) C->accepted = 0;
       continue;
     }
-    const int off = V.scen[s].poff, n = V.scen[s].pcount;
+    const int off = V.scen[s].poff * nsub, n = V.scen[s].pcount * nsub;
     double v = 0.0;
     for (int k = tid; k < n; k += NT) v += pm[off + k];
     v = warp_sum_tree(v);
@@ -623,31 +650,37 @@ __device__ void step_finish(const GfGeom& G, const GfView& V,
   }
 }
 
-template <class P, int M, int NT, int MINB>
+template <class P, int MP, int M, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
     k_patch_step(const __grid_constant__ GfGeom G,
                  const __grid_constant__ GfView V, double* __restrict__ pmass) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const GfPatch Pt = V.patch[blockIdx.x];
-  if (V.ctl[Pt.scen].active) patch_body<P, M, NT>(G, V, pmass, smraw);
+  constexpr int NSUB = (MP / M) * (MP / M);
+  const GfPatch Pt = V.patch[blockIdx.x / NSUB];
+  if (V.ctl[Pt.scen].active) patch_body<P, MP, M, NT>(G, V, pmass, smraw);
   if (V.done)
     step_finish<NT>(G, V, pmass,
-                    reinterpret_cast<double*>(smraw + Layout<P, M>::OFF_RED));
+                    reinterpret_cast<double*>(smraw + Layout<P, M>::OFF_RED),
+                    NSUB);
 }
 
-template <class P, int M, int NT, int MINB>
+// Launch the patch step on every patch: MP x MP patches, M x M sub-tiles
+// per CTA of NT threads (MINB CTAs per SM).  pmass holds (MP/M)^2 entries
+// per patch.
+template <class P, int MP, int M, int NT, int MINB>
 int launch_step(const GfGeom& g, const GfView& v, double* pmass,
                 cudaStream_t st) {
   constexpr size_t bytes = Layout<P, M>::BYTES;
   static bool attr = false;
   if (!attr) {
-    if (cudaFuncSetAttribute(k_patch_step<P, M, NT, MINB>,
+    if (cudaFuncSetAttribute(k_patch_step<P, MP, M, NT, MINB>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)bytes) != cudaSuccess)
       return -2;
     attr = true;
   }
-  k_patch_step<P, M, NT, MINB><<<v.npatch, NT, bytes, st>>>(g, v, pmass);
+  constexpr int NSUB = (MP / M) * (MP / M);
+  k_patch_step<P, MP, M, NT, MINB><<<v.npatch * NSUB, NT, bytes, st>>>(g, v, pmass);
   return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 

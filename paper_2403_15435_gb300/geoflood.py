@@ -96,6 +96,8 @@ def lib():
                 "geoflood_profile_read": [vp, C.c_char_p, dp, ll],
                 "geoflood_launch_count": [vp, ll],
                 "geoflood_counters": [vp, ip, ll, ll],
+                "geoflood_autotune": [vp, ip, pi, dp],
+                "geoflood_set_variant": [vp, ip],
             }
             for name, args in sig.items():
                 f = getattr(L, name)
@@ -287,6 +289,15 @@ class Forest:
         a, b = C.c_longlong(), C.c_longlong()
         self._check(lib().geoflood_counters(self._h, s, C.byref(a), C.byref(b)))
         return a.value, b.value
+
+    def autotune(self, reps=5):
+        v = C.c_int()
+        ms = np.zeros(4)
+        self._check(lib().geoflood_autotune(self._h, int(reps), C.byref(v), _p(ms)))
+        return v.value, ms
+
+    def set_variant(self, variant):
+        self._check(lib().geoflood_set_variant(self._h, int(variant)))
 
     def launch_count(self):
         n = C.c_longlong()
