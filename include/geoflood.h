@@ -214,11 +214,12 @@ int geoflood_counters(geoflood_ctx* ctx, int scenario, long long* cell_updates,
  * halo staging): times every available variant reps times on the current
  * state (without advancing it), selects the fastest for this context and
  * returns its number in *variant and the times (ms per launch) in
- * ms_per_variant (two entries for 32 x 32 patches, one for 16 x 16; either
+ * ms_per_variant (three entries for 32 x 32 patches, one for 16 x 16; either
  * pointer may be NULL).  Variants of 32 x 32 patches: 0 = one 512-thread CTA
  * per patch staging the whole tile by TMA bulk copies, 1 = four CTAs per
- * patch, each staging a 16 x 16 sub-tile with its two-cell halo.  Results
- * do not depend on the variant. */
+ * patch, each staging a 16 x 16 sub-tile with its two-cell halo, 2 = the
+ * same shapes with the register budget of one CTA per SM.  Results do not
+ * depend on the variant. */
 int geoflood_autotune(geoflood_ctx* ctx, int reps, int* variant,
                       double* ms_per_variant);
 

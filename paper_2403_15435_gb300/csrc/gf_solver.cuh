@@ -256,12 +256,19 @@ __device__ __forceinline__ void tsplit(R h, R ma, R mo, R eta, bool wet,
 // FP32) compared with drytol as the FP64 value (w - b is exact in double).
 // FP32 decides when the rounded difference is clear of drytol by more than
 // its rounding bound; otherwise the test is redone in FP64.
+// The FP64 tie-break is a separate, non-inlined function so that the
+// compiler cannot evaluate it speculatively on every call (FP64 is slow on
+// this part).
+static __device__ __noinline__ bool wet_dev_tie(float w, float b, double drytol) {
+  return ((double)w - (double)b) > drytol;
+}
+
 __device__ __forceinline__ bool wet_dev(float w, float b, double drytol,
                                         float dtf, float margin) {
   const float h = w - b;
   if (h > dtf + margin) return true;
   if (h < dtf - margin) return false;
-  return ((double)w - (double)b) > drytol;
+  return wet_dev_tie(w, b, drytol);
 }
 
 }  // namespace gfk

@@ -43,9 +43,10 @@ namespace gf {
 
 // Kernel variants (the autotuner picks one per context): for 32 x 32
 // patches, 0 = one 512-thread CTA per patch (TMA bulk staging of the whole
-// tile), 1 = four 256-thread CTAs of 16 x 16 sub-tiles; 16 x 16 patches have
-// the single variant 0.
-int patch_step_variants(int mx) { return mx == 32 ? 2 : 1; }
+// tile), 1 = four CTAs of 16 x 16 sub-tiles per patch, 2 = as 0 (FP32) or 1
+// (FP64) with the register limit for one CTA per SM; 16 x 16 patches have the
+// single variant 0.
+int patch_step_variants(int mx) { return mx == 32 ? 3 : 1; }
 
 int launch_patch_step_f64(const GfGeom& g, const GfView& v, double* pmass,
                           int variant, void* stream) {
@@ -53,6 +54,8 @@ int launch_patch_step_f64(const GfGeom& g, const GfView& v, double* pmass,
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (g.M == 32 && variant == 1)
     return gfs::launch_step<gfs::PrecF64, 32, 16, 256, 2>(g, v, pmass, st);
+  if (g.M == 32 && variant == 2)
+    return gfs::launch_step<gfs::PrecF64, 32, 16, 256, 1>(g, v, pmass, st);
   if (g.M == 32) return gfs::launch_step<gfs::PrecF64, 32, 32, 512, 1>(g, v, pmass, st);
   if (g.M == 16) return gfs::launch_step<gfs::PrecF64, 16, 16, 256, 1>(g, v, pmass, st);
   return -1;

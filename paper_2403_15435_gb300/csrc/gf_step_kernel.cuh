@@ -418,6 +418,7 @@ __device__ __forceinline__ void patch_body(const GfGeom& G, const GfView& V,
   const R mn = rscal[4];
   double vol = 0.0, clipd = 0.0;
   R volr = R(0);
+  float clipf = 0.0f;  // deviation form: clipped depth, FP32 per thread
   unsigned nclip = 0, nwet = 0;
   bool bad = false;
   const float* los = nullptr;
@@ -487,7 +488,7 @@ __device__ __forceinline__ void patch_body(const GfGeom& G, const GfView& V,
       }
       const float bc = sb[c];
       if (o[0] < bc) {  // negative depth: reset to a dry bed
-        clipd += (double)bc - (double)o[0];
+        clipf += bc - o[0];
         o[0] = bc;
         lo[0] = 0.0f;
         ++nclip;
@@ -550,6 +551,7 @@ __device__ __forceinline__ void patch_body(const GfGeom& G, const GfView& V,
     pmass[blockIdx.x] = vs * (dx * dy);
   }
   if (nclip) {
+    if constexpr (DEV) clipd = (double)clipf;
     atomicAdd(&C->step_nclip, (unsigned long long)nclip);
     atomicAdd(&C->step_clipvol, clipd * (dx * dy));
   }

@@ -245,6 +245,6 @@ def test_kernel_variants_agree_bitwise(prec):
         states.append(g.read())
         if variant == 1:
             best, ms = g.autotune(3)
-            assert best in (0, 1) and ms[0] > 0 and ms[1] > 0
+            assert best in (0, 1, 2) and ms[0] > 0 and ms[1] > 0 and ms[2] > 0
     for a, b in zip(states[0], states[1]):
         assert np.array_equal(a, b)
