@@ -59,6 +59,10 @@ extern "C" {
 #define GEOFLOOD_TAG_REFINE 1
 #define GEOFLOOD_TAG_COARSEN 2
 
+/* taggers (geoflood_set_tagger) */
+#define GEOFLOOD_TAGGER_PLAIN 0
+#define GEOFLOOD_TAGGER_LEARNED 1
+
 /* Forest, physics and control parameters.  Geometry (Sec. 4): mi x mj
  * level-0 blocks, each a patch of mx x mx cells (mx = 16 or 32), levels
  * minlevel..maxlevel with refinement ratio 2; the domain is
@@ -270,6 +274,122 @@ int geoflood_step_tiles_noalloc(const double* q_in, const double* b,
 /* Message of the last failed geoflood_step_tiles_noalloc call on this host
  * thread ("" if none). */
 const char* geoflood_noalloc_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Learned refinement predictor.
+ *
+ * The paper refines where the plain criteria of Sec. 4.1 (depth, speed,
+ * surface elevation, flood-source region) fire, re-evaluated at every
+ * regrid.  This extension predicts those flags several steps ahead so that
+ * regridding can run less often: a 3-layer convolutional network (3 x 3
+ * kernels, 16 channels, ReLU, mean pool, linear head, logistic output) over
+ * an 18 x 18 pixel view of each patch: the 16 x 16 grid of (M/16)^2 cell
+ * means of the interior plus a ring whose pixels average the band of
+ * same-level cells (composite over the forest, M/2 deep) beyond the edge
+ * beside them, leaving out cells outside the domain.
+ * Input channels: h, hu, hv, bed minus the interior mean bed (each divided
+ * by its scale), level / 4, and zeros.  BF16 operands on the tensor cores,
+ * FP32 accumulation and FP32 master parameters.
+ *
+ * Parameters (FP32, geoflood_cnn_nparam() of them, in this order): for layers
+ * l = 1, 2, 3, W_l[16 co][144] with column tap * 16 + ci, tap = (dy + 1) * 3
+ * + (dx + 1) (dy the row offset), then b_l[16]; then the head wh[16], bh[1].
+ *
+ * The plain criterion always judges: with the learned tagger selected,
+ * geoflood_tags and geoflood_regrid refine where either the criterion or the
+ * network (probability above the threshold) asks for it, and
+ * geoflood_check_tags counts what the criterion wants refined that the mesh
+ * does not yet resolve, so that a caller can regrid at once on a miss. */
+
+/* Number of network parameters (6977). */
+int geoflood_cnn_nparam(void);
+
+/* Load the parameters (host, n floats); resets the Adam moments.  The
+ * random initialisation is the caller's.  Errors: ARG (wrong n), OOM. */
+int geoflood_cnn_set_params(geoflood_ctx* ctx, const float* prm, int n);
+
+/* Copy the current parameters to host memory (n floats).  STATE if none. */
+int geoflood_cnn_get_params(geoflood_ctx* ctx, float* prm, int n);
+
+/* Scales that divide h, hu, hv and the relative bed (4 floats > 0; default
+ * 10 m, 10 m^2/s, 10 m^2/s, 10 m). */
+int geoflood_cnn_set_scale(geoflood_ctx* ctx, const float* scale);
+
+/* Input features of scenario s: host [npatch][324][16] BF16 bit patterns,
+ * pixel = Y * 18 + X over the 18 x 18 view. */
+int geoflood_cnn_features(geoflood_ctx* ctx, int s, uint16_t* out);
+
+/* Logits of the network for the patches of scenario s (host, npatch). */
+int geoflood_cnn_predict(geoflood_ctx* ctx, int s, float* logit);
+
+/* Forward and backward pass on n host samples x ([n][324][16] BF16 bits)
+ * with labels in {0, 1}: the logits, the gradient of the mean weighted
+ * cross-entropy (weight pos_weight on positive samples) with respect to
+ * every parameter, and that loss.  Any output may be NULL. */
+int geoflood_cnn_grad(geoflood_ctx* ctx, const uint16_t* x, const float* label,
+                      int n, float pos_weight, float* logit, float* grad,
+                      float* loss);
+
+/* Allocate (or clear) a device dataset of up to capacity samples. */
+int geoflood_cnn_dataset(geoflood_ctx* ctx, int capacity);
+
+/* Record the features of every current patch as pending samples with
+ * labels 0. */
+int geoflood_cnn_snapshot(geoflood_ctx* ctx);
+
+/* Evaluate the plain criterion on every patch: *misses = number of patches
+ * it wants refined that are below the finest level.  With observe != 0 the
+ * patches it flags for refinement get label 1 in the pending samples, which
+ * must come from a snapshot of the same patches (STATE otherwise). */
+int geoflood_check_tags(geoflood_ctx* ctx, int observe, int* misses);
+
+/* Append the pending samples to the dataset (up to its capacity); returns
+ * the dataset size and, if positives is non-NULL, its number of label-1
+ * samples. */
+int geoflood_cnn_commit(geoflood_ctx* ctx, int* total, int* positives);
+
+/* Copy samples [first, first + n) of the dataset to the host (x or y may be
+ * NULL). */
+int geoflood_cnn_dataset_read(geoflood_ctx* ctx, int first, int n, uint16_t* x,
+                              float* y);
+
+/* Train on the dataset: epochs passes over seeded shuffles (splitmix64 from
+ * seed) in minibatches of batch samples, Adam (beta 0.9 / 0.999, eps 1e-8)
+ * at learning rate lr on the weighted cross-entropy.  epoch_loss (host,
+ * epochs floats, may be NULL) receives the mean minibatch loss of each
+ * epoch. */
+int geoflood_cnn_train(geoflood_ctx* ctx, int epochs, int batch, float lr,
+                       float pos_weight, unsigned long long seed,
+                       float* epoch_loss);
+
+/* Time stepping with periodic regridding (Sec. 3.3 regrids every few
+ * steps; Sec. 6.4 every 4).  Advances every scenario to t_target in chunks
+ * of check_interval steps; after each chunk the plain criterion is
+ * evaluated (geoflood_check_tags) and the forest regrids when
+ * regrid_interval steps have passed since the last regrid or, with
+ * GEOFLOOD_ADVANCE_REGRID_ON_MISS, as soon as the criterion reports a
+ * miss.  With GEOFLOOD_ADVANCE_COLLECT it records training samples instead
+ * (features at each regrid, labels OR'ed over the checks up to the next one;
+ * no regrid on misses): call geoflood_cnn_dataset first.  Needs
+ * 1 <= check_interval <= regrid_interval. */
+#define GEOFLOOD_ADVANCE_COLLECT 1
+#define GEOFLOOD_ADVANCE_REGRID_ON_MISS 2
+typedef struct {
+  long long steps;        /* accepted steps (maximum over scenarios) */
+  long long patch_steps;  /* sum over steps of the number of patches */
+  long long checks;       /* evaluations of the plain criterion */
+  long long misses;       /* sum over checks of the patches it wanted refined */
+  long long regrids;      /* regrids done */
+  long long miss_regrids; /* of which triggered by a miss */
+  long long samples;      /* dataset size after the run (COLLECT) */
+} geoflood_advance_stats;
+int geoflood_advance(geoflood_ctx* ctx, double t_target, int regrid_interval,
+                     int check_interval, int mode, geoflood_advance_stats* out);
+
+/* Select the tagger used by geoflood_tags and geoflood_regrid; threshold is
+ * the probability above which the network's flag counts (0 < threshold < 1).
+ * LEARNED needs parameters (STATE otherwise). */
+int geoflood_set_tagger(geoflood_ctx* ctx, int tagger, float threshold);
 
 #ifdef __cplusplus
 }

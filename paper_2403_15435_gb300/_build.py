@@ -22,6 +22,7 @@ SOURCES = [
     ("gf_step.cu", ["-fmad=false"]),
     ("gf_step32.cu", []),
     ("gf_amr.cu", ["-fmad=false"]),
+    ("gf_cnn.cu", []),
     ("gf_forest.cpp", []),
     ("gf_api.cpp", []),
 ]

@@ -3,6 +3,7 @@
 // physical boundaries, topography cell averages from a DEM, regrid data
 // transfer, the plain tagger, gauges, volume sums and host staging.
 // Compiled with -fmad=false.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -441,7 +442,8 @@ __global__ void k_regrid_fill(const __grid_constant__ GfGeom G, const __grid_con
 
 // Plain tagger (Sec. 4.1 criteria 1, 3, 4; Sec. 6.4).
 template <typename T>
-__global__ void k_tags(const __grid_constant__ GfGeom G, const __grid_constant__ GfView V, uint8_t* flags) {
+__global__ void k_tags(const __grid_constant__ GfGeom G, const __grid_constant__ GfView V,
+                       const GfTagOut O) {
   const int p = blockIdx.x;
   const GfPatch P = V.patch[p];
   Geo<T> e(G, V);
@@ -481,11 +483,18 @@ __global__ void k_tags(const __grid_constant__ GfGeom G, const __grid_constant__
   if (threadIdx.x == 0) {
     int mm = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mm = wm[w] > mm ? wm[w] : mm;
+    // the plain criterion's own verdict: recorded, turned into training
+    // labels, or counted as a miss where the patch could still be refined
+    if (O.raw) O.raw[p] = (uint8_t)mm;
+    if (O.label && mm == 2) O.label[p] = 1.0f;
+    if (O.misses && mm == 2 && P.level < G.maxlevel) atomicAdd(O.misses, 1u);
+    // learned tags add refinement (or keep a fine patch) on top of it
+    if (O.logit && O.logit[p] > O.logit_thr) mm = 2;
     uint8_t f;
     if (mm == 2) f = P.level < G.maxlevel ? 1 : 0;
     else if (mm == 1) f = 0;
     else f = P.level > G.minlevel ? 2 : 0;
-    flags[p] = f;
+    if (O.flags) O.flags[p] = f;
   }
 }
 
@@ -636,6 +645,90 @@ __global__ void k_unpack(const __grid_constant__ GfGeom G, const __grid_constant
   }
 }
 
+// Input features of the learned refinement predictor on an 18 x 18 pixel
+// grid.  The 16 x 16 inner pixels are means over f x f blocks of the patch
+// interior (f = M / 16); each ring pixel is the mean over the band of cells
+// of the same level that lies beyond the patch edge next to it, M / 2 cells
+// deep (f cells wide along the edge, M / 2 x M / 2 at the corners), read from
+// whichever leaves cover it; cells outside the domain are left out.  This
+// lets the network see water up to half a patch away.  Channels: h, hu, hv,
+// bed minus the mean interior bed, each divided by its scale, then level /
+// 4; channels 5..15 are zero.  Output [count][324][16] BF16, pixel = Y * 18
+// + X.
+struct FeatScale {
+  float s[4];
+};
+
+template <typename T>
+__global__ void k_cnn_features(const __grid_constant__ GfGeom G,
+                               const __grid_constant__ GfView V, int first,
+                               FeatScale sc, __nv_bfloat16* out) {
+  const int p = first + blockIdx.x;
+  const GfPatch P = V.patch[p];
+  Geo<T> e(G, V);
+  const int M = G.M, f = M / 16, W = M / 2;
+  const int cur = V.ctl[P.scen].cur;
+  __shared__ double part[256];
+  __shared__ double bmean;
+  double bs = 0.0;
+  for (int k = threadIdx.x; k < M * M; k += blockDim.x) {
+    double c4[4];
+    e.load(p, cur, e.tix(k % M, k / M), c4);
+    bs += c4[3];
+  }
+  part[threadIdx.x] = bs;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) bmean = part[0] / (double)(M * M);
+  __syncthreads();
+  __nv_bfloat16* o = out + (size_t)blockIdx.x * 324 * 16;
+  const long long NX = e.nx(P.level), NY = e.ny(P.level);
+  const long long I0 = (long long)P.px * M, J0 = (long long)P.py * M;
+  int err = 0;
+  for (int px = threadIdx.x; px < 324; px += blockDim.x) {
+    const int Y = px / 18, X = px % 18;
+    // cell range [i0, i1) x [j0, j1) of the pixel, patch-relative
+    const int i0 = X == 0 ? -W : X == 17 ? M : (X - 1) * f;
+    const int i1 = X == 0 ? 0 : X == 17 ? M + W : X * f;
+    const int j0 = Y == 0 ? -W : Y == 17 ? M : (Y - 1) * f;
+    const int j1 = Y == 0 ? 0 : Y == 17 ? M + W : Y * f;
+    const bool inner = X >= 1 && X <= 16 && Y >= 1 && Y <= 16;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    int cnt = 0;
+    for (int j = j0; j < j1; ++j)
+      for (int i = i0; i < i1; ++i) {
+        double c4[4];
+        if (inner) {
+          e.load(p, cur, e.tix(i, j), c4);
+        } else {
+          const long long I = I0 + i, J = J0 + j;
+          if (I < 0 || J < 0 || I >= NX || J >= NY) continue;
+          value_at(e, P.scen, P.level, I, J, c4, &err);
+        }
+        acc[0] += c4[0];
+        acc[1] += c4[1];
+        acc[2] += c4[2];
+        acc[3] += c4[3];
+        ++cnt;
+      }
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    if (cnt > 0) {
+      const double inv = 1.0 / (double)cnt;
+      v[0] = (float)(acc[0] * inv / (double)sc.s[0]);
+      v[1] = (float)(acc[1] * inv / (double)sc.s[1]);
+      v[2] = (float)(acc[2] * inv / (double)sc.s[2]);
+      v[3] = (float)((acc[3] * inv - bmean) / (double)sc.s[3]);
+    }
+    __nv_bfloat16* op = o + px * 16;
+    for (int c = 0; c < 4; ++c) op[c] = __float2bfloat16_rn(v[c]);
+    op[4] = __float2bfloat16_rn(0.25f * (float)P.level);
+    for (int c = 5; c < 16; ++c) op[c] = __float2bfloat16_rn(0.f);
+  }
+}
+
 inline int ok() { return cudaGetLastError() == cudaSuccess ? 0 : -2; }
 
 }  // namespace
@@ -673,10 +766,29 @@ int launch_regrid_fill(const GfGeom& g, const GfView& oldv, const GfView& newv,
 
 int launch_tags(const GfGeom& g, const GfView& v, uint8_t* flags,
                 void* stream) {
+  GfTagOut o{};
+  o.flags = flags;
+  return launch_tags_ex(g, v, o, stream);
+}
+
+int launch_tags_ex(const GfGeom& g, const GfView& v, const GfTagOut& o,
+                   void* stream) {
   if (v.npatch <= 0) return 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (v.prec) k_tags<float><<<v.npatch, 256, 0, st>>>(g, v, flags);
-  else k_tags<double><<<v.npatch, 256, 0, st>>>(g, v, flags);
+  if (v.prec) k_tags<float><<<v.npatch, 256, 0, st>>>(g, v, o);
+  else k_tags<double><<<v.npatch, 256, 0, st>>>(g, v, o);
+  return ok();
+}
+
+int launch_cnn_features(const GfGeom& g, const GfView& v, int first, int count,
+                        const float* scale, void* out, void* stream) {
+  if (count <= 0) return 0;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  FeatScale sc{{scale[0], scale[1], scale[2], scale[3]}};
+  if (v.prec)
+    k_cnn_features<float><<<count, 256, 0, st>>>(g, v, first, sc, static_cast<__nv_bfloat16*>(out));
+  else
+    k_cnn_features<double><<<count, 256, 0, st>>>(g, v, first, sc, static_cast<__nv_bfloat16*>(out));
   return ok();
 }
 

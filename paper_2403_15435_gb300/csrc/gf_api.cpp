@@ -22,6 +22,46 @@ struct ProfRec {
   cudaEvent_t a, b;
 };
 
+// Device state of the learned refinement predictor.
+struct CnnState {
+  float* prm = nullptr;  // FP32 master parameters
+  void* wb = nullptr;    // BF16 conv weights [3][16][144]
+  void* wf = nullptr;    // and their flipped transposes
+  float* grad = nullptr;
+  float* am = nullptr;   // Adam moments
+  float* av = nullptr;
+  int adam_t = 0;
+  bool ready = false;
+  float scale[4] = {10.f, 10.f, 10.f, 10.f};
+  // inference over the current patches (sized to the patch capacity)
+  void* x = nullptr;
+  void* a[3] = {nullptr, nullptr, nullptr};
+  float* pool = nullptr;
+  float* logit = nullptr;
+  // pending samples: features at a snapshot, labels OR'ed over checks
+  void* px = nullptr;
+  float* py = nullptr;
+  int pend_n = -1;
+  long long pend_gen = -1;
+  // dataset
+  void* dx = nullptr;
+  float* dy = nullptr;
+  int ds_cap = 0, ds_n = 0;
+  // training minibatch
+  void* xb = nullptr;
+  float* yb = nullptr;
+  int* idx = nullptr;
+  void* ta[3] = {nullptr, nullptr, nullptr};
+  void* td[3] = {nullptr, nullptr, nullptr};
+  float* tv = nullptr;
+  float* tlogit = nullptr;
+  float* loss = nullptr;
+  int bcap = 0, idx_cap = 0;
+  int tagger = GEOFLOOD_TAGGER_PLAIN;
+  float logit_thr = 0.f;
+  unsigned* misses = nullptr;
+};
+
 }  // namespace
 
 struct geoflood_ctx {
@@ -71,6 +111,8 @@ struct geoflood_ctx {
   std::vector<cudaEvent_t> pool;
   size_t pool_used = 0;
   long long launches = 0;
+  long long generation = 0;  // bumped by every regrid
+  CnnState cnn;
 };
 
 namespace {
@@ -263,6 +305,111 @@ int topo_scenario(geoflood_ctx* ctx, int s) {
   return 0;
 }
 
+int cnn_alloc(geoflood_ctx* ctx, void** p, size_t bytes) {
+  if (*p) return 0;
+  if (cudaMalloc(p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(ctx, GEOFLOOD_ERR_OOM, "learned tagger: out of device memory");
+  }
+  return 0;
+}
+
+const size_t CNN_X_BYTES = (size_t)gf::CNN_IN_PIX * gf::CNN_CH * 2;
+const size_t CNN_A_BYTES = (size_t)gf::CNN_PIX * gf::CNN_CH * 2;
+
+int cnn_params_alloc(geoflood_ctx* ctx) {
+  CnnState& n = ctx->cnn;
+  const size_t np = (size_t)gf::cnn_nparam();
+  int rc = 0;
+  rc |= cnn_alloc(ctx, (void**)&n.prm, np * 4);
+  rc |= cnn_alloc(ctx, (void**)&n.grad, np * 4);
+  rc |= cnn_alloc(ctx, (void**)&n.am, np * 4);
+  rc |= cnn_alloc(ctx, (void**)&n.av, np * 4);
+  rc |= cnn_alloc(ctx, &n.wb, 3 * 16 * 144 * 2);
+  rc |= cnn_alloc(ctx, &n.wf, 3 * 16 * 144 * 2);
+  rc |= cnn_alloc(ctx, (void**)&n.loss, 4 * 1024);
+  return rc ? GEOFLOOD_ERR_OOM : 0;
+}
+
+int cnn_infer_alloc(geoflood_ctx* ctx) {
+  CnnState& n = ctx->cnn;
+  const size_t cap = (size_t)ctx->cap;
+  int rc = 0;
+  rc |= cnn_alloc(ctx, &n.x, cap * CNN_X_BYTES);
+  for (int l = 0; l < 3; ++l) rc |= cnn_alloc(ctx, &n.a[l], cap * CNN_A_BYTES);
+  rc |= cnn_alloc(ctx, (void**)&n.pool, cap * 16 * 4);
+  rc |= cnn_alloc(ctx, (void**)&n.logit, cap * 4);
+  return rc ? GEOFLOOD_ERR_OOM : 0;
+}
+
+int cnn_batch_alloc(geoflood_ctx* ctx, int b) {
+  CnnState& n = ctx->cnn;
+  if (b <= n.bcap) return 0;
+  for (void* p : {n.xb, (void*)n.yb, n.ta[0], n.ta[1], n.ta[2], n.td[0], n.td[1], n.td[2],
+                  (void*)n.tv, (void*)n.tlogit})
+    cudaFree(p);
+  n.xb = nullptr; n.yb = nullptr; n.tv = nullptr; n.tlogit = nullptr;
+  for (int l = 0; l < 3; ++l) n.ta[l] = n.td[l] = nullptr;
+  n.bcap = 0;
+  int rc = 0;
+  rc |= cnn_alloc(ctx, &n.xb, (size_t)b * CNN_X_BYTES);
+  rc |= cnn_alloc(ctx, (void**)&n.yb, (size_t)b * 4);
+  for (int l = 0; l < 3; ++l) {
+    rc |= cnn_alloc(ctx, &n.ta[l], (size_t)b * CNN_A_BYTES);
+    rc |= cnn_alloc(ctx, &n.td[l], (size_t)b * CNN_A_BYTES);
+  }
+  rc |= cnn_alloc(ctx, (void**)&n.tv, (size_t)b * 16 * 4);
+  rc |= cnn_alloc(ctx, (void**)&n.tlogit, (size_t)b * 4);
+  if (rc) return GEOFLOOD_ERR_OOM;
+  n.bcap = b;
+  return 0;
+}
+
+// Features and logits of the current patches [first, first + count).
+int cnn_infer(geoflood_ctx* ctx, int first, int count) {
+  CnnState& n = ctx->cnn;
+  int rc = cnn_infer_alloc(ctx);
+  if (rc) return rc;
+  CKL(gf::launch_cnn_features(ctx->G, view(ctx), first, count, n.scale, n.x, ctx->st),
+      "cnn_features");
+  CKL(gf::cnn_forward(n.x, n.wb, n.prm, n.a[0], n.a[1], n.a[2], n.pool, n.logit, count,
+                      ctx->st),
+      "cnn_forward");
+  ctx->launches += 5;
+  return 0;
+}
+
+// One tagging pass over every patch into ctx->d_flags; with learned tags the
+// network's predictions are added to the plain criterion.  misses (device
+// counter) and pending labels are filled when asked for.
+int tag_pass(geoflood_ctx* ctx, bool learned, unsigned* misses, float* label = nullptr) {
+  GfTagOut o{};
+  o.flags = ctx->d_flags;
+  o.misses = misses;
+  o.label = label;
+  if (learned) {
+    if (!ctx->cnn.ready)
+      return fail(ctx, GEOFLOOD_ERR_STATE, "learned tagging without network parameters");
+    int rc = cnn_infer(ctx, 0, ctx->npatch);
+    if (rc) return rc;
+    o.logit = ctx->cnn.logit;
+    o.logit_thr = ctx->cnn.logit_thr;
+  }
+  CKL(gf::launch_tags_ex(ctx->G, view(ctx), o, ctx->st), "tags");
+  ctx->launches++;
+  return 0;
+}
+
+// splitmix64 (Steele, Lea and Flood 2014): the stream behind the minibatch
+// shuffles.
+uint64_t splitmix64(uint64_t& x) {
+  uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
 }  // namespace
 
 extern "C" {
@@ -429,6 +576,13 @@ void geoflood_destroy(geoflood_ctx* ctx) {
   if (ctx->h_ctl) cudaFreeHost(ctx->h_ctl);
   if (ctx->own_stream) cudaStreamDestroy(ctx->st);
   for (auto e : ctx->pool) cudaEventDestroy(e);
+  CnnState& n = ctx->cnn;
+  for (void* p : {(void*)n.prm, n.wb, n.wf, (void*)n.grad, (void*)n.am, (void*)n.av, n.x,
+                  n.a[0], n.a[1], n.a[2], (void*)n.pool, (void*)n.logit, n.px, (void*)n.py,
+                  n.dx, (void*)n.dy, n.xb, (void*)n.yb, (void*)n.idx, n.ta[0], n.ta[1],
+                  n.ta[2], n.td[0], n.td[1], n.td[2], (void*)n.tv, (void*)n.tlogit,
+                  (void*)n.loss, (void*)n.misses})
+    cudaFree(p);
   delete ctx;
 }
 
@@ -744,8 +898,8 @@ int geoflood_step(geoflood_ctx* ctx, double t_target, int max_steps,
 
 int geoflood_tags(geoflood_ctx* ctx, int s, uint8_t* flags) {
   if (!valid_scen(ctx, s) || !flags) return fail(ctx, GEOFLOOD_ERR_ARG, "tags: bad argument");
-  CKL(gf::launch_tags(ctx->G, view(ctx), ctx->d_flags, ctx->st), "tags");
-  ctx->launches++;
+  int rc = tag_pass(ctx, ctx->cnn.tagger == GEOFLOOD_TAGGER_LEARNED, nullptr);
+  if (rc) return rc;
   CK(cudaMemcpyAsync(flags, ctx->d_flags + ctx->h_scen[s].poff,
                      ctx->h_scen[s].pcount, cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
@@ -757,8 +911,7 @@ int geoflood_regrid(geoflood_ctx* ctx) {
   int rc = sync_ctl_down(ctx);
   if (rc) return rc;
   std::vector<uint8_t> flags(ctx->npatch);
-  CKL(gf::launch_tags(ctx->G, view(ctx), ctx->d_flags, ctx->st), "tags");
-  ctx->launches++;
+  if ((rc = tag_pass(ctx, ctx->cnn.tagger == GEOFLOOD_TAGGER_LEARNED, nullptr))) return rc;
   CK(cudaMemcpyAsync(flags.data(), ctx->d_flags, ctx->npatch, cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
   std::vector<std::vector<gf::Leaf>> lv(ctx->nscen);
@@ -793,6 +946,7 @@ int geoflood_regrid(geoflood_ctx* ctx) {
   ctx->tsel = nt;
   ctx->bsel = nb;
   ctx->npatch = (int)total;
+  ctx->generation++;
   if ((rc = sync_ctl_up(ctx))) return rc;
   if ((rc = check_errflag(ctx))) return rc;
   return ghost_fill_all(ctx);
@@ -949,6 +1103,308 @@ int geoflood_set_variant(geoflood_ctx* ctx, int variant) {
 int geoflood_launch_count(geoflood_ctx* ctx, long long* launches) {
   if (!ctx || !launches) return GEOFLOOD_ERR_ARG;
   *launches = ctx->launches;
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Learned refinement predictor
+
+int geoflood_cnn_nparam(void) { return gf::cnn_nparam(); }
+
+int geoflood_cnn_set_params(geoflood_ctx* ctx, const float* prm, int n) {
+  if (!ctx || !prm || n != gf::cnn_nparam())
+    return fail(ctx, GEOFLOOD_ERR_ARG, "cnn_set_params: expected " +
+                                           std::to_string(gf::cnn_nparam()) + " parameters");
+  int rc = cnn_params_alloc(ctx);
+  if (rc) return rc;
+  CnnState& c = ctx->cnn;
+  CK(cudaMemcpyAsync(c.prm, prm, (size_t)n * 4, cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemsetAsync(c.am, 0, (size_t)n * 4, ctx->st));
+  CK(cudaMemsetAsync(c.av, 0, (size_t)n * 4, ctx->st));
+  CKL(gf::cnn_cast(c.prm, c.wb, c.wf, ctx->st), "cnn_cast");
+  ctx->launches++;
+  CK(cudaStreamSynchronize(ctx->st));
+  c.adam_t = 0;
+  c.ready = true;
+  return 0;
+}
+
+int geoflood_cnn_get_params(geoflood_ctx* ctx, float* prm, int n) {
+  if (!ctx || !prm || n != gf::cnn_nparam() || !ctx->cnn.ready)
+    return fail(ctx, GEOFLOOD_ERR_ARG, "cnn_get_params: no parameters or bad size");
+  CK(cudaMemcpyAsync(prm, ctx->cnn.prm, (size_t)n * 4, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return 0;
+}
+
+int geoflood_cnn_set_scale(geoflood_ctx* ctx, const float* scale) {
+  if (!ctx || !scale) return GEOFLOOD_ERR_ARG;
+  for (int k = 0; k < 4; ++k)
+    if (!(scale[k] > 0.f)) return fail(ctx, GEOFLOOD_ERR_ARG, "cnn_set_scale: scales must be > 0");
+  std::copy(scale, scale + 4, ctx->cnn.scale);
+  return 0;
+}
+
+int geoflood_cnn_features(geoflood_ctx* ctx, int s, uint16_t* out) {
+  if (!valid_scen(ctx, s) || !out) return fail(ctx, GEOFLOOD_ERR_ARG, "cnn_features: bad argument");
+  CnnState& n = ctx->cnn;
+  int rc = cnn_infer_alloc(ctx);
+  if (rc) return rc;
+  const int first = ctx->h_scen[s].poff, count = ctx->h_scen[s].pcount;
+  CKL(gf::launch_cnn_features(ctx->G, view(ctx), first, count, n.scale, n.x, ctx->st),
+      "cnn_features");
+  ctx->launches++;
+  CK(cudaMemcpyAsync(out, n.x, (size_t)count * CNN_X_BYTES, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return 0;
+}
+
+int geoflood_cnn_predict(geoflood_ctx* ctx, int s, float* logit) {
+  if (!valid_scen(ctx, s) || !logit) return fail(ctx, GEOFLOOD_ERR_ARG, "cnn_predict: bad argument");
+  if (!ctx->cnn.ready) return fail(ctx, GEOFLOOD_ERR_STATE, "cnn_predict: no parameters");
+  const int first = ctx->h_scen[s].poff, count = ctx->h_scen[s].pcount;
+  int rc = cnn_infer(ctx, first, count);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(logit, ctx->cnn.logit, (size_t)count * 4, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return 0;
+}
+
+int geoflood_cnn_grad(geoflood_ctx* ctx, const uint16_t* x, const float* label, int n,
+                      float pos_weight, float* logit, float* grad, float* loss) {
+  if (!ctx || !x || !label || n < 1 || !(pos_weight > 0.f))
+    return fail(ctx, GEOFLOOD_ERR_ARG, "cnn_grad: bad argument");
+  CnnState& c = ctx->cnn;
+  if (!c.ready) return fail(ctx, GEOFLOOD_ERR_STATE, "cnn_grad: no parameters");
+  int rc = cnn_batch_alloc(ctx, n);
+  if (rc) return rc;
+  const int np = gf::cnn_nparam();
+  CK(cudaMemcpyAsync(c.xb, x, (size_t)n * CNN_X_BYTES, cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(c.yb, label, (size_t)n * 4, cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemsetAsync(c.grad, 0, (size_t)np * 4, ctx->st));
+  CK(cudaMemsetAsync(c.loss, 0, 4, ctx->st));
+  CKL(gf::cnn_forward(c.xb, c.wb, c.prm, c.ta[0], c.ta[1], c.ta[2], c.tv, c.tlogit, n, ctx->st),
+      "cnn_forward");
+  CKL(gf::cnn_backward(c.xb, c.wf, c.prm, c.ta[0], c.ta[1], c.ta[2], c.tv, c.tlogit, c.yb,
+                       pos_weight, c.grad, c.loss, c.td[0], c.td[1], c.td[2], n, ctx->st),
+      "cnn_backward");
+  ctx->launches += 11;
+  if (logit) CK(cudaMemcpyAsync(logit, c.tlogit, (size_t)n * 4, cudaMemcpyDeviceToHost, ctx->st));
+  if (grad) CK(cudaMemcpyAsync(grad, c.grad, (size_t)np * 4, cudaMemcpyDeviceToHost, ctx->st));
+  if (loss) CK(cudaMemcpyAsync(loss, c.loss, 4, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return 0;
+}
+
+int geoflood_cnn_dataset(geoflood_ctx* ctx, int capacity) {
+  if (!ctx || capacity < 0) return GEOFLOOD_ERR_ARG;
+  CnnState& c = ctx->cnn;
+  if (capacity != c.ds_cap) {
+    cudaFree(c.dx);
+    cudaFree(c.dy);
+    c.dx = nullptr;
+    c.dy = nullptr;
+    c.ds_cap = 0;
+    if (capacity > 0) {
+      int rc = cnn_alloc(ctx, &c.dx, (size_t)capacity * CNN_X_BYTES);
+      rc |= cnn_alloc(ctx, (void**)&c.dy, (size_t)capacity * 4);
+      if (rc) return GEOFLOOD_ERR_OOM;
+    }
+    c.ds_cap = capacity;
+  }
+  c.ds_n = 0;
+  c.pend_n = -1;
+  return 0;
+}
+
+int geoflood_cnn_snapshot(geoflood_ctx* ctx) {
+  if (!ctx) return GEOFLOOD_ERR_ARG;
+  CnnState& c = ctx->cnn;
+  const size_t cap = (size_t)ctx->cap;
+  int rc = cnn_alloc(ctx, &c.px, cap * CNN_X_BYTES);
+  rc |= cnn_alloc(ctx, (void**)&c.py, cap * 4);
+  if (rc) return GEOFLOOD_ERR_OOM;
+  CKL(gf::launch_cnn_features(ctx->G, view(ctx), 0, ctx->npatch, c.scale, c.px, ctx->st),
+      "cnn_features");
+  ctx->launches++;
+  CK(cudaMemsetAsync(c.py, 0, (size_t)ctx->npatch * 4, ctx->st));
+  c.pend_n = ctx->npatch;
+  c.pend_gen = ctx->generation;
+  return 0;
+}
+
+int geoflood_check_tags(geoflood_ctx* ctx, int observe, int* misses) {
+  if (!ctx) return GEOFLOOD_ERR_ARG;
+  CnnState& c = ctx->cnn;
+  if (observe && (c.pend_n != ctx->npatch || c.pend_gen != ctx->generation))
+    return fail(ctx, GEOFLOOD_ERR_STATE, "check_tags: no snapshot of the current patches");
+  int rc = cnn_alloc(ctx, (void**)&c.misses, sizeof(unsigned));
+  if (rc) return rc;
+  CK(cudaMemsetAsync(c.misses, 0, sizeof(unsigned), ctx->st));
+  if ((rc = tag_pass(ctx, false, c.misses, observe ? c.py : nullptr))) return rc;
+  unsigned m = 0;
+  CK(cudaMemcpyAsync(&m, c.misses, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  if (misses) *misses = (int)m;
+  return 0;
+}
+
+int geoflood_cnn_commit(geoflood_ctx* ctx, int* total, int* positives) {
+  if (!ctx) return GEOFLOOD_ERR_ARG;
+  CnnState& c = ctx->cnn;
+  if (c.pend_n < 0 || c.pend_gen != ctx->generation)
+    return fail(ctx, GEOFLOOD_ERR_STATE, "cnn_commit: no snapshot of the current patches");
+  const int add = std::min(c.pend_n, c.ds_cap - c.ds_n);
+  if (add > 0) {
+    CK(cudaMemcpyAsync((char*)c.dx + (size_t)c.ds_n * CNN_X_BYTES, c.px, (size_t)add * CNN_X_BYTES,
+                       cudaMemcpyDeviceToDevice, ctx->st));
+    CK(cudaMemcpyAsync(c.dy + c.ds_n, c.py, (size_t)add * 4, cudaMemcpyDeviceToDevice, ctx->st));
+    c.ds_n += add;
+  }
+  c.pend_n = -1;
+  if (positives) {
+    std::vector<float> y(c.ds_n);
+    if (c.ds_n)
+      CK(cudaMemcpyAsync(y.data(), c.dy, (size_t)c.ds_n * 4, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    int npos = 0;
+    for (float v : y) npos += v > 0.5f;
+    *positives = npos;
+  }
+  if (total) *total = c.ds_n;
+  return 0;
+}
+
+int geoflood_cnn_dataset_read(geoflood_ctx* ctx, int first, int n, uint16_t* x, float* y) {
+  if (!ctx || first < 0 || n < 0 || first + n > ctx->cnn.ds_n)
+    return fail(ctx, GEOFLOOD_ERR_ARG, "cnn_dataset_read: range outside the dataset");
+  CnnState& c = ctx->cnn;
+  if (n == 0) return 0;
+  if (x) CK(cudaMemcpyAsync(x, (char*)c.dx + (size_t)first * CNN_X_BYTES, (size_t)n * CNN_X_BYTES,
+                            cudaMemcpyDeviceToHost, ctx->st));
+  if (y) CK(cudaMemcpyAsync(y, c.dy + first, (size_t)n * 4, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return 0;
+}
+
+int geoflood_cnn_train(geoflood_ctx* ctx, int epochs, int batch, float lr, float pos_weight,
+                       unsigned long long seed, float* epoch_loss) {
+  if (!ctx || epochs < 0 || epochs > 1024 || batch < 1 || !(lr > 0.f) || !(pos_weight > 0.f))
+    return fail(ctx, GEOFLOOD_ERR_ARG, "cnn_train: bad argument");
+  CnnState& c = ctx->cnn;
+  if (!c.ready) return fail(ctx, GEOFLOOD_ERR_STATE, "cnn_train: no parameters");
+  const int N = c.ds_n;
+  if (N < 1) return fail(ctx, GEOFLOOD_ERR_STATE, "cnn_train: empty dataset");
+  batch = std::min(batch, N);
+  int rc = cnn_batch_alloc(ctx, batch);
+  if (rc) return rc;
+  if (N > c.idx_cap) {
+    cudaFree(c.idx);
+    c.idx = nullptr;
+    c.idx_cap = 0;
+    if ((rc = cnn_alloc(ctx, (void**)&c.idx, (size_t)N * 4))) return rc;
+    c.idx_cap = N;
+  }
+  const int np = gf::cnn_nparam();
+  std::vector<int> perm(N);
+  uint64_t st = seed;
+  CK(cudaMemsetAsync(c.loss, 0, 4 * 1024, ctx->st));
+  const int nb = N / batch;  // full batches only
+  for (int e = 0; e < epochs; ++e) {
+    for (int k = 0; k < N; ++k) perm[k] = k;
+    for (int k = N - 1; k > 0; --k) {  // Fisher-Yates
+      const int j = (int)(splitmix64(st) % (uint64_t)(k + 1));
+      std::swap(perm[k], perm[j]);
+    }
+    CK(cudaMemcpyAsync(c.idx, perm.data(), (size_t)N * 4, cudaMemcpyHostToDevice, ctx->st));
+    for (int b = 0; b < nb; ++b) {
+      CKL(gf::cnn_gather(c.dx, c.dy, c.idx + (size_t)b * batch, batch, c.xb, c.yb, ctx->st),
+          "cnn_gather");
+      CK(cudaMemsetAsync(c.grad, 0, (size_t)np * 4, ctx->st));
+      CKL(gf::cnn_forward(c.xb, c.wb, c.prm, c.ta[0], c.ta[1], c.ta[2], c.tv, c.tlogit, batch,
+                          ctx->st),
+          "cnn_forward");
+      CKL(gf::cnn_backward(c.xb, c.wf, c.prm, c.ta[0], c.ta[1], c.ta[2], c.tv, c.tlogit, c.yb,
+                           pos_weight, c.grad, c.loss + e, c.td[0], c.td[1], c.td[2], batch,
+                           ctx->st),
+          "cnn_backward");
+      CKL(gf::cnn_adam(c.prm, c.grad, c.am, c.av, lr, ++c.adam_t, ctx->st), "cnn_adam");
+      CKL(gf::cnn_cast(c.prm, c.wb, c.wf, ctx->st), "cnn_cast");
+      ctx->launches += 14;
+    }
+    // the host vector is rewritten next epoch: wait for its copy
+    CK(cudaStreamSynchronize(ctx->st));
+  }
+  if (epoch_loss && epochs > 0) {
+    std::vector<float> l(epochs);
+    CK(cudaMemcpyAsync(l.data(), c.loss, (size_t)epochs * 4, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    for (int e = 0; e < epochs; ++e) epoch_loss[e] = l[e] / (float)nb;
+  }
+  CK(cudaStreamSynchronize(ctx->st));
+  return 0;
+}
+
+int geoflood_advance(geoflood_ctx* ctx, double t_target, int regrid_interval,
+                     int check_interval, int mode, geoflood_advance_stats* out) {
+  if (!ctx || regrid_interval < 1 || check_interval < 1 || check_interval > regrid_interval ||
+      (mode & ~(GEOFLOOD_ADVANCE_COLLECT | GEOFLOOD_ADVANCE_REGRID_ON_MISS)))
+    return fail(ctx, GEOFLOOD_ERR_ARG, "advance: bad argument");
+  const bool collect = mode & GEOFLOOD_ADVANCE_COLLECT;
+  const bool on_miss = (mode & GEOFLOOD_ADVANCE_REGRID_ON_MISS) && !collect;
+  geoflood_advance_stats st{};
+  int rc = 0;
+  if (collect && (rc = geoflood_cnn_snapshot(ctx))) return rc;
+  std::vector<double> t(ctx->nscen);
+  std::vector<int> n(ctx->nscen);
+  int since = 0;
+  for (;;) {
+    const int want = std::min(check_interval, regrid_interval - since);
+    const int np = ctx->npatch;
+    if ((rc = geoflood_step(ctx, t_target, want, t.data(), n.data()))) return rc;
+    int taken = 0;
+    bool done = true;
+    for (int s = 0; s < ctx->nscen; ++s) {
+      taken = std::max(taken, n[s]);
+      done &= !(t[s] < t_target);
+    }
+    st.steps += taken;
+    st.patch_steps += (long long)taken * np;
+    since += taken;
+    if (done) break;
+    if (taken == 0) return fail(ctx, GEOFLOOD_ERR_STATE, "advance: no progress");
+    // the plain criterion judges at every check
+    int misses = 0;
+    if ((rc = geoflood_check_tags(ctx, collect ? 1 : 0, &misses))) return rc;
+    st.checks++;
+    st.misses += misses;
+    const bool due = since >= regrid_interval;
+    if (due || (on_miss && misses > 0)) {
+      if (collect) {
+        int total = 0;
+        if ((rc = geoflood_cnn_commit(ctx, &total, nullptr))) return rc;
+        st.samples = total;
+      }
+      if ((rc = geoflood_regrid(ctx))) return rc;
+      st.regrids++;
+      if (!due) st.miss_regrids++;
+      since = 0;
+      if (collect && (rc = geoflood_cnn_snapshot(ctx))) return rc;
+    }
+  }
+  if (collect) ctx->cnn.pend_n = -1;
+  if (out) *out = st;
+  return 0;
+}
+
+int geoflood_set_tagger(geoflood_ctx* ctx, int tagger, float threshold) {
+  if (!ctx || (tagger != GEOFLOOD_TAGGER_PLAIN && tagger != GEOFLOOD_TAGGER_LEARNED) ||
+      !(threshold > 0.f && threshold < 1.f))
+    return fail(ctx, GEOFLOOD_ERR_ARG, "set_tagger: bad argument");
+  if (tagger == GEOFLOOD_TAGGER_LEARNED && !ctx->cnn.ready)
+    return fail(ctx, GEOFLOOD_ERR_STATE, "set_tagger: no network parameters");
+  ctx->cnn.tagger = tagger;
+  ctx->cnn.logit_thr = std::log(threshold / (1.f - threshold));
   return 0;
 }
 

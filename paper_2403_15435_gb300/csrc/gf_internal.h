@@ -90,6 +90,20 @@ struct GfView {
 #define GF_NBR_OUTSIDE -2
 
 // Kernel launchers (defined in the .cu files).
+// Outputs of the tagging pass (every pointer may be null).  raw: the plain
+// criterion per patch (0 coarsen, 1 keep, 2 refine); label: set to 1 where it
+// says refine; misses: count of patches it wants refined below the finest
+// level; logit/logit_thr: learned predictions that add refinement before
+// flags (0 keep, 1 refine, 2 coarsen) are formed.
+struct GfTagOut {
+  uint8_t* flags;
+  uint8_t* raw;
+  float* label;
+  unsigned* misses;
+  const float* logit;
+  float logit_thr;
+};
+
 namespace gf {
 int patch_step_variants(int mx);
 int launch_patch_step_f64(const GfGeom& g, const GfView& v, double* pmass,
@@ -117,4 +131,27 @@ int launch_unpack_interior(const GfGeom& g, const GfView& v, int first,
                            int count, const double* in, int cur,
                            void* stream);
 void set_errflag(int* device_flag);
+int launch_tags_ex(const GfGeom& g, const GfView& v, const GfTagOut& o,
+                   void* stream);
+int launch_cnn_features(const GfGeom& g, const GfView& v, int first, int count,
+                        const float* scale, void* out, void* stream);
+// learned refinement predictor (gf_cnn.cu)
+int cnn_nparam();
+int cnn_forward(const void* x0, const void* wb, const float* prm, void* a1,
+                void* a2, void* a3, float* v, float* logit, int npatch,
+                void* stream);
+int cnn_backward(const void* x0, const void* wf, const float* prm,
+                 const void* a1, const void* a2, const void* a3, const float* v,
+                 const float* logit, const float* label, float pos_weight,
+                 float* grad, float* loss, void* d1, void* d2, void* d3,
+                 int npatch, void* stream);
+int cnn_adam(float* prm, const float* grad, float* m, float* v, float lr,
+             int t, void* stream);
+int cnn_cast(const float* prm, void* wb, void* wf, void* stream);
+int cnn_to_bf16(const float* x, void* y, size_t n, void* stream);
+int cnn_gather(const void* x, const float* y, const int* idx, int n, void* xb,
+               float* yb, void* stream);
+constexpr int CNN_IN_PIX = 324;  // 18 x 18 input pixels per patch
+constexpr int CNN_PIX = 256;     // 16 x 16 activation pixels per patch
+constexpr int CNN_CH = 16;
 }  // namespace gf

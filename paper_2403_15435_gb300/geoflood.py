@@ -27,6 +27,8 @@ ERRORS = {
     -6: "NEGATIVE_DEPTH", -7: "TIMEOUT", -8: "CAPACITY", -9: "STATE",
 }
 KEEP, REFINE, COARSEN = 0, 1, 2
+TAGGER_PLAIN, TAGGER_LEARNED = 0, 1
+CNN_IN_PIX, CNN_CH = 324, 16
 
 
 class GeoFloodError(RuntimeError):
@@ -52,6 +54,14 @@ class _Cfg(C.Structure):
     ]
 
 
+class AdvanceStats(C.Structure):
+    _fields_ = [(n, C.c_longlong) for n in ("steps", "patch_steps", "checks", "misses",
+                                             "regrids", "miss_regrids", "samples")]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
 QINIT = C.CFUNCTYPE(None, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                     C.POINTER(C.c_double), C.POINTER(C.c_double),
                     C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p)
@@ -74,6 +84,8 @@ def lib():
             vp, ip, dp = C.c_void_p, C.c_int, C.POINTER(C.c_double)
             pi = C.POINTER(C.c_int)
             ll = C.POINTER(C.c_longlong)
+            fp = C.POINTER(C.c_float)
+            u16p = C.POINTER(C.c_uint16)
             sig = {
                 "geoflood_init_forest": [C.POINTER(_Cfg), vp, C.POINTER(vp)],
                 "geoflood_set_scenario": [vp, ip, C.c_double, C.c_double],
@@ -98,6 +110,20 @@ def lib():
                 "geoflood_counters": [vp, ip, ll, ll],
                 "geoflood_autotune": [vp, ip, pi, dp],
                 "geoflood_set_variant": [vp, ip],
+                "geoflood_cnn_set_params": [vp, fp, ip],
+                "geoflood_cnn_get_params": [vp, fp, ip],
+                "geoflood_cnn_set_scale": [vp, fp],
+                "geoflood_cnn_features": [vp, ip, u16p],
+                "geoflood_cnn_predict": [vp, ip, fp],
+                "geoflood_cnn_grad": [vp, u16p, fp, ip, C.c_float, fp, fp, fp],
+                "geoflood_cnn_dataset": [vp, ip],
+                "geoflood_cnn_snapshot": [vp],
+                "geoflood_check_tags": [vp, ip, pi],
+                "geoflood_cnn_commit": [vp, pi, pi],
+                "geoflood_cnn_dataset_read": [vp, ip, ip, u16p, fp],
+                "geoflood_cnn_train": [vp, ip, ip, C.c_float, C.c_float, C.c_ulonglong, fp],
+                "geoflood_set_tagger": [vp, ip, C.c_float],
+                "geoflood_advance": [vp, C.c_double, ip, ip, ip, C.POINTER(AdvanceStats)],
             }
             for name, args in sig.items():
                 f = getattr(L, name)
@@ -107,6 +133,8 @@ def lib():
             L.geoflood_destroy.restype = None
             L.geoflood_last_error.argtypes = [vp]
             L.geoflood_last_error.restype = C.c_char_p
+            L.geoflood_cnn_nparam.argtypes = []
+            L.geoflood_cnn_nparam.restype = C.c_int
             _lib = L
     return _lib
 
@@ -303,6 +331,94 @@ class Forest:
         n = C.c_longlong()
         self._check(lib().geoflood_launch_count(self._h, C.byref(n)))
         return n.value
+
+    # learned refinement predictor -------------------------------------------
+
+    def cnn_set_params(self, prm):
+        prm = np.ascontiguousarray(prm, dtype=np.float32)
+        self._check(lib().geoflood_cnn_set_params(self._h, _p(prm, C.c_float), len(prm)))
+
+    def cnn_get_params(self):
+        prm = np.empty(cnn_nparam(), np.float32)
+        self._check(lib().geoflood_cnn_get_params(self._h, _p(prm, C.c_float), len(prm)))
+        return prm
+
+    def cnn_set_scale(self, scale):
+        sc = np.ascontiguousarray(scale, dtype=np.float32).reshape(4)
+        self._check(lib().geoflood_cnn_set_scale(self._h, _p(sc, C.c_float)))
+
+    def cnn_features(self, s=0):
+        """BF16 bit patterns [npatch][324][16] (view with bf16_to_float)."""
+        out = np.empty((self.npatch_of(s), CNN_IN_PIX, CNN_CH), np.uint16)
+        self._check(lib().geoflood_cnn_features(self._h, s, _p(out, C.c_uint16)))
+        return out
+
+    def cnn_predict(self, s=0):
+        out = np.empty(self.npatch_of(s), np.float32)
+        self._check(lib().geoflood_cnn_predict(self._h, s, _p(out, C.c_float)))
+        return out
+
+    def cnn_grad(self, x, label, pos_weight=1.0):
+        x = np.ascontiguousarray(x, dtype=np.uint16)
+        y = np.ascontiguousarray(label, dtype=np.float32)
+        n = len(y)
+        logit = np.empty(n, np.float32)
+        grad = np.empty(cnn_nparam(), np.float32)
+        loss = np.empty(1, np.float32)
+        self._check(lib().geoflood_cnn_grad(self._h, _p(x, C.c_uint16), _p(y, C.c_float), n,
+                                            float(pos_weight), _p(logit, C.c_float),
+                                            _p(grad, C.c_float), _p(loss, C.c_float)))
+        return logit, grad, float(loss[0])
+
+    def cnn_dataset(self, capacity):
+        self._check(lib().geoflood_cnn_dataset(self._h, int(capacity)))
+
+    def cnn_snapshot(self):
+        self._check(lib().geoflood_cnn_snapshot(self._h))
+
+    def check_tags(self, observe=False):
+        m = C.c_int()
+        self._check(lib().geoflood_check_tags(self._h, 1 if observe else 0, C.byref(m)))
+        return m.value
+
+    def cnn_commit(self):
+        n, npos = C.c_int(), C.c_int()
+        self._check(lib().geoflood_cnn_commit(self._h, C.byref(n), C.byref(npos)))
+        return n.value, npos.value
+
+    def cnn_dataset_read(self, first, n):
+        x = np.empty((n, CNN_IN_PIX, CNN_CH), np.uint16)
+        y = np.empty(n, np.float32)
+        self._check(lib().geoflood_cnn_dataset_read(self._h, int(first), int(n),
+                                                    _p(x, C.c_uint16), _p(y, C.c_float)))
+        return x, y
+
+    def cnn_train(self, epochs, batch, lr=1e-3, pos_weight=1.0, seed=0):
+        loss = np.zeros(max(1, epochs), np.float32)
+        self._check(lib().geoflood_cnn_train(self._h, int(epochs), int(batch), float(lr),
+                                             float(pos_weight), int(seed) & (2**64 - 1),
+                                             _p(loss, C.c_float)))
+        return loss[:epochs]
+
+    def advance(self, t_target, regrid_interval=4, check_interval=4, collect=False,
+                regrid_on_miss=False):
+        st = AdvanceStats()
+        mode = (1 if collect else 0) | (2 if regrid_on_miss else 0)
+        self._check(lib().geoflood_advance(self._h, float(t_target), int(regrid_interval),
+                                           int(check_interval), mode, C.byref(st)))
+        return st.as_dict()
+
+    def set_tagger(self, tagger, threshold=0.5):
+        self._check(lib().geoflood_set_tagger(self._h, int(tagger), float(threshold)))
+
+
+def cnn_nparam():
+    return lib().geoflood_cnn_nparam()
+
+
+def bf16_to_float(bits):
+    """Widen BF16 bit patterns to float32 (exact)."""
+    return (np.asarray(bits, np.uint16).astype(np.uint32) << 16).view(np.float32)
 
 
 def exported_symbols():
