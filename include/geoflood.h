@@ -198,9 +198,11 @@ int geoflood_set_gauges(geoflood_ctx* ctx, int scenario, const double* xy,
 int geoflood_gauges(geoflood_ctx* ctx, int scenario, double* out,
                     double* arrival);
 
-/* Kernel timing with CUDA events around every launch of the named kernel
- * family ("patch_step", "ghost_fill", "controller", "gauges"): enable != 0
- * starts recording (and clears earlier records). */
+/* Kernel timing with CUDA events around launches of the named kernel
+ * family ("patch_step", "ghost_fill"): enable = n > 0 starts recording (and
+ * clears earlier records), timing every n-th step of each captured chunk of
+ * steps (n = 1: every launch; a larger n keeps the cost of the event nodes
+ * off the other steps); 0 stops. */
 int geoflood_profile(geoflood_ctx* ctx, int enable);
 
 /* Sum of the recorded durations (ms) and number of recorded launches of one
@@ -218,11 +220,13 @@ int geoflood_counters(geoflood_ctx* ctx, int scenario, long long* cell_updates,
  * halo staging): times every available variant reps times on the current
  * state (without advancing it), selects the fastest for this context and
  * returns its number in *variant and the times (ms per launch) in
- * ms_per_variant (three entries for 32 x 32 patches, one for 16 x 16; either
+ * ms_per_variant (one entry per variant, at most 8: for 32 x 32 patches
+ * three in FP64 and four in the FP32 deviation form, one for 16 x 16; either
  * pointer may be NULL).  Variants of 32 x 32 patches: 0 = one 512-thread CTA
  * per patch staging the whole tile by TMA bulk copies, 1 = four CTAs per
  * patch, each staging a 16 x 16 sub-tile with its two-cell halo, 2 = the
- * same shapes with the register budget of one CTA per SM.  Results do not
+ * FP32 shape of 0 or the FP64 shape of 1 with the register budget of one
+ * CTA per SM, 3 (FP32 only) = one 1024-thread CTA per patch.  Results do not
  * depend on the variant. */
 int geoflood_autotune(geoflood_ctx* ctx, int reps, int* variant,
                       double* ms_per_variant);

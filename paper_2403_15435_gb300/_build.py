@@ -20,7 +20,10 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # (source, extra flags)
 SOURCES = [
     ("gf_step.cu", ["-fmad=false"]),
-    ("gf_step32.cu", []),
+    # FP32 kernels: approximate single-precision division and square root
+    # (a few ulp; the FP32 path is held to absolute tolerances, and a lake at
+    # rest still gives exactly zero waves)
+    ("gf_step32.cu", ["-prec-div=false", "-prec-sqrt=false"]),
     ("gf_amr.cu", ["-fmad=false"]),
     ("gf_cnn.cu", []),
     ("gf_forest.cpp", []),

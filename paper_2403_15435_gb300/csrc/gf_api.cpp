@@ -80,12 +80,16 @@ struct geoflood_ctx {
   int* d_lut[2] = {nullptr, nullptr};
   int* d_nbr[2] = {nullptr, nullptr};
   unsigned* d_done = nullptr;
+  unsigned* d_sched = nullptr;        // launch-order parity and counters
+  int* d_ord[2] = {nullptr, nullptr}; // launch orders of the patch step
+  unsigned char* d_same = nullptr;    // per work unit: buffers agree
   bool own_stream = false;
   // CUDA graphs of chunks of steps, keyed by chunk length
   struct Graph {
     cudaGraphExec_t exec = nullptr;
     int k = 0, tsel = -1, bsel = -1, npatch = -1, gauges = -1, prof = -1, variant = -1;
-    std::vector<ProfRec> ev;
+    std::vector<ProfRec> ev;   // sampled patch-step launches
+    std::vector<ProfRec> evg;  // sampled ghost fills
   };
   std::vector<Graph> graphs;
   int tsel = 0;
@@ -105,6 +109,7 @@ struct geoflood_ctx {
   int variant = 0;  // patch-step kernel variant (see geoflood_autotune)
   std::string err;
   bool prof = false;
+  int prof_every = 1;  // time every n-th patch step of a graph chunk
   std::map<std::string, std::vector<ProfRec>> prof_recs;
   std::map<std::string, double> prof_ms;
   std::map<std::string, long long> prof_n;
@@ -156,6 +161,10 @@ GfView view(geoflood_ctx* c, int t, int bb) {
   v.lof[1] = c->lof[1];
   v.nbr = c->d_nbr[t];
   v.done = c->d_done;
+  v.sched = c->d_sched;
+  v.ord0 = c->d_ord[0];
+  v.ord1 = c->d_ord[1];
+  v.same = c->d_same;
   v.npatch = c->npatch;
   v.prec = c->prec;
   return v;
@@ -255,6 +264,16 @@ int upload_tables(geoflood_ctx* ctx, int t,
   }
   CK(cudaMemcpyAsync(ctx->d_nbr[t], nb.data(), sizeof(int) * nb.size(),
                      cudaMemcpyHostToDevice, ctx->st));
+  // a new patch list: launch order back to patch order, no tile known to
+  // agree between the buffers
+  std::vector<int> iota(total);
+  for (size_t k = 0; k < total; ++k) iota[k] = (int)k;
+  CK(cudaMemcpyAsync(ctx->d_ord[0], iota.data(), sizeof(int) * total,
+                     cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->d_ord[1], iota.data(), sizeof(int) * total,
+                     cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemsetAsync(ctx->d_sched, 0, 4 * sizeof(unsigned), ctx->st));
+  CK(cudaMemsetAsync(ctx->d_same, 0, (size_t)ctx->cap * 4, ctx->st));
   CK(cudaMemcpyAsync(ctx->d_patch[t], hp.data(), sizeof(GfPatch) * total,
                      cudaMemcpyHostToDevice, ctx->st));
   CK(cudaMemcpyAsync(ctx->d_lut[t], lut.data(), sizeof(int) * lut.size(),
@@ -297,7 +316,16 @@ int ghost_fill_all(geoflood_ctx* ctx) {
   return check_errflag(ctx);
 }
 
+// After the host writes state or beds, no tile is known to agree between
+// the two state buffers.
+int forget_same(geoflood_ctx* ctx) {
+  CK(cudaMemsetAsync(ctx->d_same, 0, (size_t)ctx->cap * 4, ctx->st));
+  return 0;
+}
+
 int topo_scenario(geoflood_ctx* ctx, int s) {
+  int rc = forget_same(ctx);
+  if (rc) return rc;
   CKL(gf::launch_topo(ctx->G, view(ctx), ctx->h_scen[s].poff,
                       ctx->h_scen[s].pcount, ctx->st),
       "topo");
@@ -461,6 +489,18 @@ int geoflood_init_forest(const geoflood_config* cfg, void* stream,
     if (L <= c.maxlevel) acc += ((long long)c.mi << L) * ((long long)c.mj << L);
   }
   G.lut_per_scen = acc;
+  for (int L = 0; L <= GF_MAXLEV; ++L) {
+    const double nx = (double)((long long)c.mi * c.mx << L);
+    const double ny = (double)((long long)c.mj * c.mx << L);
+    G.dxl[L] = (c.xupper - c.xlower) / nx;
+    G.dyl[L] = (c.yupper - c.ylower) / ny;
+    G.areal[L] = G.dxl[L] * G.dyl[L];
+    G.inv_dxf[L] = (float)(1.0 / G.dxl[L]);
+    G.inv_dyf[L] = (float)(1.0 / G.dyl[L]);
+  }
+  G.gf = (float)c.g;
+  G.drytolf = (float)c.drytol;
+  G.marginf = (float)(c.drytol * 0x1p-20);
 
   const size_t TT = (size_t)G.T * G.T;
   const size_t cap = (size_t)ctx->cap;
@@ -488,6 +528,10 @@ int geoflood_init_forest(const geoflood_config* cfg, void* stream,
   okk &= alloc((void**)&ctx->d_nbr[0], cap * 8 * sizeof(int));
   okk &= alloc((void**)&ctx->d_nbr[1], cap * 8 * sizeof(int));
   okk &= alloc((void**)&ctx->d_done, sizeof(unsigned));
+  okk &= alloc((void**)&ctx->d_sched, 4 * sizeof(unsigned));
+  okk &= alloc((void**)&ctx->d_ord[0], cap * sizeof(int));
+  okk &= alloc((void**)&ctx->d_ord[1], cap * sizeof(int));
+  okk &= alloc((void**)&ctx->d_same, cap * 4);
   okk &= alloc((void**)&ctx->d_lut[0], (size_t)ctx->nscen * G.lut_per_scen * sizeof(int));
   okk &= alloc((void**)&ctx->d_lut[1], (size_t)ctx->nscen * G.lut_per_scen * sizeof(int));
   okk &= alloc((void**)&ctx->d_scen, ctx->nscen * sizeof(GfScenario));
@@ -562,6 +606,10 @@ void geoflood_destroy(geoflood_ctx* ctx) {
   for (auto& gr : ctx->graphs)
     if (gr.exec) cudaGraphExecDestroy(gr.exec);
   cudaFree(ctx->d_done);
+  cudaFree(ctx->d_sched);
+  cudaFree(ctx->d_ord[0]);
+  cudaFree(ctx->d_ord[1]);
+  cudaFree(ctx->d_same);
   cudaFree(ctx->d_scen);
   cudaFree(ctx->d_ctl);
   cudaFree(ctx->d_pmass);
@@ -611,6 +659,7 @@ int geoflood_set_scenario(geoflood_ctx* ctx, int s, double manning_n,
   const bool moved = ctx->prec && eta0 != ctx->h_scen[s].eta0;
   if (moved && (rc = keep_depths(ctx, s, h, hu, hv))) return rc;
   ctx->h_scen[s].manning_n = manning_n;
+  ctx->h_scen[s].manning_f = (float)manning_n;
   ctx->h_scen[s].eta0 = eta0;
   if ((rc = upload_scen(ctx))) return rc;
   if (!moved) return 0;
@@ -672,6 +721,7 @@ int geoflood_write_patches(geoflood_ctx* ctx, int s, const double* h,
   CK(cudaMemcpyAsync(ctx->d_stage, h, plane * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
   CK(cudaMemcpyAsync(ctx->d_stage + plane, hu, plane * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
   CK(cudaMemcpyAsync(ctx->d_stage + 2 * plane, hv, plane * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+  if ((rc = forget_same(ctx))) return rc;
   CKL(gf::launch_unpack_interior(ctx->G, view(ctx), ctx->h_scen[s].poff, n,
                                  ctx->d_stage, ctx->h_ctl[s].cur, ctx->st),
       "unpack");
@@ -814,30 +864,40 @@ int geoflood_step(geoflood_ctx* ctx, double t_target, int max_steps,
     gr = &ctx->graphs.back();
     gr->k = K;
   }
-  const int prof = ctx->prof ? 1 : 0;
+  const int prof = ctx->prof ? ctx->prof_every : 0;
   if (!gr->exec || gr->tsel != ctx->tsel || gr->bsel != ctx->bsel ||
       gr->npatch != ctx->npatch || gr->gauges != ctx->max_gauges_used ||
       gr->prof != prof || gr->variant != ctx->variant) {
     if (gr->exec) cudaGraphExecDestroy(gr->exec);
     gr->exec = nullptr;
     gr->ev.clear();
+    gr->evg.clear();
     CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
     int lrc = 0;
     for (int it = 0; it < K && !lrc; ++it) {
-      ProfRec r{};
-      if (prof) {
+      // sampled launches are bracketed by external event-record nodes (the
+      // events are recorded at every replay)
+      const bool sample = prof && it % prof == 0;
+      ProfRec r{}, rg{};
+      if (sample) {
         r.a = pool_event(ctx);
         r.b = pool_event(ctx);
-        // an external record node: the event is recorded at every replay
+        rg.a = pool_event(ctx);
+        rg.b = pool_event(ctx);
         cudaEventRecordWithFlags(r.a, ctx->st, cudaEventRecordExternal);
       }
       lrc |= ctx->prec ? gf::launch_patch_step_f32(ctx->G, v, ctx->d_pmass, ctx->variant, ctx->st)
                        : gf::launch_patch_step_f64(ctx->G, v, ctx->d_pmass, ctx->variant, ctx->st);
-      if (prof) {
+      if (sample) {
         cudaEventRecordWithFlags(r.b, ctx->st, cudaEventRecordExternal);
         gr->ev.push_back(r);
+        cudaEventRecordWithFlags(rg.a, ctx->st, cudaEventRecordExternal);
       }
       lrc |= gf::launch_ghost_fill(ctx->G, v, 1, ctx->st);
+      if (sample) {
+        cudaEventRecordWithFlags(rg.b, ctx->st, cudaEventRecordExternal);
+        gr->evg.push_back(rg);
+      }
       if (ctx->max_gauges_used > 0)
         lrc |= gf::launch_gauges(ctx->G, v, 1, ctx->max_gauges_used, ctx->st);
     }
@@ -867,13 +927,20 @@ int geoflood_step(geoflood_ctx* ctx, double t_target, int max_steps,
     launched += K;
     int rc = sync_ctl_down(ctx);
     if (rc) return rc;
-    if (prof)
+    if (prof) {
       for (auto& r : gr->ev) {
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, r.a, r.b));
         ctx->prof_ms["patch_step"] += ms;
         ctx->prof_n["patch_step"] += 1;
       }
+      for (auto& r : gr->evg) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, r.a, r.b));
+        ctx->prof_ms["ghost_fill"] += ms;
+        ctx->prof_n["ghost_fill"] += 1;
+      }
+    }
     bool any = false;
     for (int s = 0; s < ctx->nscen; ++s) any |= ctx->h_ctl[s].active != 0;
     if (!any) break;
@@ -1014,8 +1081,10 @@ int geoflood_profile(geoflood_ctx* ctx, int enable) {
     gr.exec = nullptr;
   }
   ctx->pool_used = 0;
+  if (enable < 0) return fail(ctx, GEOFLOOD_ERR_ARG, "profile: enable must be >= 0");
   if (enable) pool_event(ctx), ctx->pool_used = 0;  // pre-create the pool
   ctx->prof = enable != 0;
+  ctx->prof_every = enable > 0 ? enable : 1;
   return 0;
 }
 
@@ -1063,7 +1132,7 @@ int geoflood_autotune(geoflood_ctx* ctx, int reps, int* variant,
   if ((rc = sync_ctl_up(ctx))) return rc;
   GfView v = view(ctx);
   v.done = nullptr;  // no controller: the state does not advance
-  const int nv = gf::patch_step_variants(ctx->G.M);
+  const int nv = gf::patch_step_variants(ctx->G.M, ctx->prec);
   cudaEvent_t a = pool_event(ctx), b = pool_event(ctx);
   int best = 0;
   double best_ms = 1e300;
@@ -1094,7 +1163,7 @@ int geoflood_autotune(geoflood_ctx* ctx, int reps, int* variant,
 }
 
 int geoflood_set_variant(geoflood_ctx* ctx, int variant) {
-  if (!ctx || variant < 0 || variant >= gf::patch_step_variants(ctx->G.M))
+  if (!ctx || variant < 0 || variant >= gf::patch_step_variants(ctx->G.M, ctx->prec))
     return fail(ctx, GEOFLOOD_ERR_ARG, "set_variant: no such variant");
   ctx->variant = variant;
   return 0;

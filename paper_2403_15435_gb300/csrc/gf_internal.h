@@ -17,6 +17,8 @@ struct GfPatch {
 // Per-scenario constants read by the kernels.
 struct GfScenario {
   double manning_n, eta0;
+  float manning_f;    // FP32 copy of manning_n
+  int pad0;
   const double* dem;  // nodal DEM [dny][dnx] or null (flat bed at 0)
   int dnx, dny;
   double dx0, dy0, ddx, ddy;
@@ -63,6 +65,11 @@ struct GfGeom {
   int nscen;
   long long lut_per_scen;
   long long lut_lev_off[GF_MAXLEV + 1];
+  // per-level cell sizes and FP32 copies of the constants, computed on the
+  // host so that the FP32 kernels need no FP64 arithmetic per patch
+  double dxl[GF_MAXLEV + 1], dyl[GF_MAXLEV + 1], areal[GF_MAXLEV + 1];
+  float inv_dxf[GF_MAXLEV + 1], inv_dyf[GF_MAXLEV + 1];
+  float gf, drytolf, marginf;
 };
 
 // Everything a kernel needs to find patches and their data.
@@ -78,6 +85,18 @@ struct GfView {
   float* lof[2];          // FP32 compensation terms [cap][3][M][M]
   const int* nbr;         // [npatch][8] same-level neighbours (see below)
   unsigned* done;         // CTA completion counter of the step (or null)
+  // Launch order of the patch step (or null: patch order).  sched[0] selects
+  // which of ord0/ord1 this launch reads; the launch writes the other one
+  // with the patches whose tile held water first (sched[1], sched[2] count
+  // the wet and dry entries) and its last CTA flips sched[0].  Only with a
+  // controller (done != null).
+  unsigned* sched;
+  int* ord0;
+  int* ord1;
+  // Per CTA work unit (patch * sub-tiles + sub-tile): 1 when both state
+  // buffers hold the same interior (a dry tile was copied), so a dry tile
+  // can skip its writes (or null).
+  unsigned char* same;
   int npatch;
   int prec;               // 0 = FP64, 1 = FP32 surface deviation
 };
@@ -105,7 +124,7 @@ struct GfTagOut {
 };
 
 namespace gf {
-int patch_step_variants(int mx);
+int patch_step_variants(int mx, int prec);
 int launch_patch_step_f64(const GfGeom& g, const GfView& v, double* pmass,
                           int variant, void* stream);
 int launch_patch_step_f32(const GfGeom& g, const GfView& v, double* pmass,

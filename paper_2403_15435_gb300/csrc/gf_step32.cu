@@ -16,6 +16,8 @@ int launch_patch_step_f32(const GfGeom& g, const GfView& v, double* pmass,
     return gfs::launch_step<gfs::PrecF32, 32, 16, 352, 2>(g, v, pmass, st);
   if (g.M == 32 && variant == 2)
     return gfs::launch_step<gfs::PrecF32, 32, 32, 512, 1>(g, v, pmass, st);
+  if (g.M == 32 && variant == 3)
+    return gfs::launch_step<gfs::PrecF32, 32, 32, 1024, 1>(g, v, pmass, st);
   if (g.M == 32) return gfs::launch_step<gfs::PrecF32, 32, 32, 512, 2>(g, v, pmass, st);
   if (g.M == 16) return gfs::launch_step<gfs::PrecF32, 16, 16, 352, 2>(g, v, pmass, st);
   return -1;

@@ -144,9 +144,10 @@ __device__ __forceinline__ void cell_item(int k, int dir, int& a, int& line) {
 // depends only on its two-cell neighbourhood, so the result does not depend
 // on M.
 template <class P, int MP, int M, int NT>
-__device__ __forceinline__ void patch_body(const GfGeom& G, const GfView& V,
-                                           double* __restrict__ pmass,
-                                           unsigned char* smraw) {
+__device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
+                                          double* __restrict__ pmass,
+                                          unsigned char* smraw, const int p,
+                                          const int sub) {
   using R = typename P::R;
   constexpr bool DEV = P::DEV;
   using Lo = Layout<P, M>;
@@ -157,7 +158,7 @@ __device__ __forceinline__ void patch_body(const GfGeom& G, const GfView& V,
   constexpr int RC = (M * M + NT - 1) / NT;       // interior cells per thread
   constexpr int RX = (Lo::NCELL + NT - 1) / NT;   // increment cells per thread
 
-  const int p = blockIdx.x / NSUB, sub = blockIdx.x % NSUB;
+  const int unit = p * NSUB + sub;  // CTA work unit: volume slot, same[] flag
   const int ox = (sub % NS1) * M, oy = (sub / NS1) * M;
   const GfPatch Pt = V.patch[p];
   GfCtl* C = V.ctl + Pt.scen;
@@ -192,23 +193,35 @@ __device__ __forceinline__ void patch_body(const GfGeom& G, const GfView& V,
     bs = V.b + (size_t)p * TG;
   }
 
+  // A tile whose interior is the same in both buffers (it was dry and copied)
+  // needs only its surface and bed to find out whether it is still dry; its
+  // momenta are fetched only if water has arrived.
+  const bool same_in = V.same != nullptr && V.same[unit] != 0;
+  bool mom_issued = false;
   if constexpr (M == MP) {
-    // whole patch: its four contiguous fields arrive by 1D TMA bulk copies
+    // whole patch: its four contiguous fields arrive by 1D TMA bulk copies,
+    // surface and bed on bar[0], the momenta on bar[1]
     if (tid == 0) {
       mbar_init(bar, 1);
-      mbar_expect_tx(bar, 4u * TT * sizeof(R));
+      mbar_init(bar + 1, 1);
+      mbar_expect_tx(bar, 2u * TT * sizeof(R));
       bulk_g2s(s0, qs, TT * sizeof(R), bar);
-      bulk_g2s(shu, qs + TT, TT * sizeof(R), bar);
-      bulk_g2s(shv, qs + 2 * TT, TT * sizeof(R), bar);
       bulk_g2s(sb, bs, TT * sizeof(R), bar);
+      if (!same_in) {
+        mbar_expect_tx(bar + 1, 2u * TT * sizeof(R));
+        bulk_g2s(shu, qs + TT, TT * sizeof(R), bar + 1);
+        bulk_g2s(shv, qs + 2 * TT, TT * sizeof(R), bar + 1);
+      }
     }
+    mom_issued = !same_in;
     __syncthreads();
     // every wait is bounded; the decision to give up is taken by the whole CTA
     if (!__syncthreads_and(mbar_wait(bar, GF_SPIN_LIMIT) ? 1 : 0)) {
       if (tid == 0) C->status = -7;  // GEOFLOOD_ERR_TIMEOUT
       mbar_wait(bar, GF_SPIN_LIMIT);
+      if (mom_issued) mbar_wait(bar + 1, GF_SPIN_LIMIT);
       __syncthreads();
-      return;
+      return 0;
     }
   } else {
     // sub-tile: the (M+4)^2 window of each field, row segments read with
@@ -230,22 +243,33 @@ __device__ __forceinline__ void patch_body(const GfGeom& G, const GfView& V,
   R* rscal = reinterpret_cast<R*>(red + 52);  // g, drytol, nux, nuy, n, dt
   float* fscal = reinterpret_cast<float*>(red + 60);  // drytol, margin
   if (tid == 0) {
-    const long long NXL = (long long)G.mi * MP << Pt.level;
-    const long long NYL = (long long)G.mj * MP << Pt.level;
-    const double dx0 = (G.xupper - G.xlower) / (double)NXL;
-    const double dy0 = (G.yupper - G.ylower) / (double)NYL;
-    scal[0] = dx0;
-    scal[1] = dy0;
-    scal[2] = C->dt_use / dx0;
-    scal[3] = C->dt_use / dy0;
-    rscal[0] = (R)G.g;
-    rscal[1] = (R)G.drytol;
-    rscal[2] = (R)scal[2];
-    rscal[3] = (R)scal[3];
-    rscal[4] = (R)V.scen[Pt.scen].manning_n;
-    rscal[5] = (R)C->dt_use;
-    fscal[0] = (float)G.drytol;
-    fscal[1] = (float)(G.drytol * 0x1p-20);
+    if constexpr (DEV) {
+      // FP32 from the host's per-level tables: one conversion per patch
+      const float dtf32 = (float)C->dt_use;
+      rscal[0] = G.gf;
+      rscal[1] = G.drytolf;
+      rscal[2] = dtf32 * G.inv_dxf[Pt.level];
+      rscal[3] = dtf32 * G.inv_dyf[Pt.level];
+      rscal[4] = V.scen[Pt.scen].manning_f;
+      rscal[5] = dtf32;
+      fscal[0] = G.drytolf;
+      fscal[1] = G.marginf;
+    } else {
+      const long long NXL = (long long)G.mi * MP << Pt.level;
+      const long long NYL = (long long)G.mj * MP << Pt.level;
+      const double dx0 = (G.xupper - G.xlower) / (double)NXL;
+      const double dy0 = (G.yupper - G.ylower) / (double)NYL;
+      scal[0] = dx0;
+      scal[1] = dy0;
+      scal[2] = C->dt_use / dx0;
+      scal[3] = C->dt_use / dy0;
+      rscal[0] = (R)G.g;
+      rscal[1] = (R)G.drytol;
+      rscal[2] = (R)scal[2];
+      rscal[3] = (R)scal[3];
+      rscal[4] = (R)V.scen[Pt.scen].manning_n;
+      rscal[5] = (R)C->dt_use;
+    }
   }
   const double drytol = G.drytol;
   R smx = R(0), smy = R(0);
@@ -270,7 +294,28 @@ __device__ __forceinline__ void patch_body(const GfGeom& G, const GfView& V,
     }
   }
   anywet = __syncthreads_or(anywet);
-  const double dx = scal[0], dy = scal[1];
+  if constexpr (M == MP) {
+    // the momenta: requested now if water arrived at a copied dry tile, and
+    // waited for whenever they were requested
+    if (anywet && !mom_issued) {
+      if (tid == 0) {
+        mbar_expect_tx(bar + 1, 2u * TT * sizeof(R));
+        bulk_g2s(shu, qs + TT, TT * sizeof(R), bar + 1);
+        bulk_g2s(shv, qs + 2 * TT, TT * sizeof(R), bar + 1);
+      }
+      mom_issued = true;
+    }
+    if (mom_issued && !__syncthreads_and(mbar_wait(bar + 1, GF_SPIN_LIMIT) ? 1 : 0)) {
+      if (tid == 0) C->status = -7;  // GEOFLOOD_ERR_TIMEOUT
+      mbar_wait(bar + 1, GF_SPIN_LIMIT);
+      __syncthreads();
+      return 0;
+    }
+  }
+  // a dry tile whose interior is already the same in both buffers writes
+  // nothing (its update is the identity on the surface, zero momenta)
+  const bool skip_writes = same_in && !anywet;
+  if (V.same != nullptr && tid == 0) V.same[unit] = anywet ? 0 : 1;
   auto wetc = [&](int c) -> bool {
     if constexpr (DEV) return swet[c] != 0;
     else return s0[c] > rdry;
@@ -435,17 +480,18 @@ __device__ __forceinline__ void patch_body(const GfGeom& G, const GfView& V,
     const int c = tix<M>(i, j);
     const int cg = gix(i, j), kp = pix(i, j);
     if (!anywet) {
-      qd[cg] = s0[c];
-      qd[TG + cg] = R(0);
-      qd[2 * TG + cg] = R(0);
-      if constexpr (DEV) {
-        lod[kp] = los[kp];
-        lod[MP * MP + kp] = 0.0f;
-        lod[2 * MP * MP + kp] = 0.0f;
-        volr += sdep[c];
-      } else {
-        vol += s0[c];
+      if (!skip_writes) {
+        qd[cg] = s0[c];
+        qd[TG + cg] = R(0);
+        qd[2 * TG + cg] = R(0);
+        if constexpr (DEV) {
+          lod[kp] = los[kp];
+          lod[MP * MP + kp] = 0.0f;
+          lod[2 * MP * MP + kp] = 0.0f;
+        }
       }
+      if constexpr (DEV) volr += sdep[c];
+      else vol += s0[c];
       continue;
     }
     const R q[3] = {s0[c], shu[c], shv[c]};
@@ -520,42 +566,73 @@ __device__ __forceinline__ void patch_body(const GfGeom& G, const GfView& V,
   // form)
   const int lane = tid & 31, wid = tid >> 5;
   constexpr int NW = NT / 32;
+  static_assert(NW <= 32, "one warp reduces the per-warp partials");
+  // the partials fit below the broadcast scalars at red + 48
+  static_assert(DEV ? 3 * NW <= 96 : 3 * NW <= 48, "reduction area");
   smx = warp_max(smx);
   smy = warp_max(smy);
-  if constexpr (DEV) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) volr += __shfl_down_sync(0xffffffffu, volr, o);
-    vol = lane == 0 ? (double)volr : 0.0;
-  } else {
-    vol = warp_sum_tree(vol);
-  }
   nwet = __reduce_add_sync(0xffffffffu, nwet);
   if (lane == 0 && nwet) atomicAdd(&C->wet_updates, (unsigned long long)nwet);
-  if (lane == 0) {
-    red[wid] = (double)smx;
-    red[NW + wid] = (double)smy;
-    red[2 * NW + wid] = vol;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    double mx = 0.0, my = 0.0, vs = 0.0;
-    for (int w = 0; w < NW; ++w) {
-      mx = red[w] > mx ? red[w] : mx;
-      my = red[NW + w] > my ? red[NW + w] : my;
-      vs += red[2 * NW + w];
+  if constexpr (DEV) {
+    // deviation form: FP32 partials; warp 0 converts the NW warp volumes to
+    // FP64 in one instruction and sums them with a shuffle tree
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) volr += __shfl_down_sync(0xffffffffu, volr, o);
+    float* redf = reinterpret_cast<float*>(red);
+    if (lane == 0) {
+      redf[wid] = smx;
+      redf[NW + wid] = smy;
+      redf[2 * NW + wid] = volr;
     }
-    const double cx = mx / dx, cy = my / dy;
-    const double cm = cx > cy ? cx : cy;
-    atomicMax(&C->cmax_bits, (unsigned long long)__double_as_longlong(cm));
-    atomicAdd(&C->cell_updates, (unsigned long long)(M * M));
-    pmass[blockIdx.x] = vs * (dx * dy);
-  }
-  if (nclip) {
-    if constexpr (DEV) clipd = (double)clipf;
-    atomicAdd(&C->step_nclip, (unsigned long long)nclip);
-    atomicAdd(&C->step_clipvol, clipd * (dx * dy));
+    __syncthreads();
+    if (wid == 0) {
+      float mx = lane < NW ? redf[lane] : 0.0f;
+      float my = lane < NW ? redf[NW + lane] : 0.0f;
+      mx = warp_max(mx);
+      my = warp_max(my);
+      double vs = lane < NW ? (double)redf[2 * NW + lane] : 0.0;
+      vs = warp_sum_tree(vs);
+      if (lane == 0) {
+        const float cx = mx * G.inv_dxf[Pt.level], cy = my * G.inv_dyf[Pt.level];
+        const double cm = (double)(cx > cy ? cx : cy);
+        atomicMax(&C->cmax_bits, (unsigned long long)__double_as_longlong(cm));
+        atomicAdd(&C->cell_updates, (unsigned long long)(M * M));
+        pmass[unit] = vs * G.areal[Pt.level];
+      }
+    }
+    if (nclip) {
+      atomicAdd(&C->step_nclip, (unsigned long long)nclip);
+      atomicAdd(&C->step_clipvol, (double)clipf * G.areal[Pt.level]);
+    }
+  } else {
+    const double dx = scal[0], dy = scal[1];
+    vol = warp_sum_tree(vol);
+    if (lane == 0) {
+      red[wid] = (double)smx;
+      red[NW + wid] = (double)smy;
+      red[2 * NW + wid] = vol;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double mx = 0.0, my = 0.0, vs = 0.0;
+      for (int w = 0; w < NW; ++w) {
+        mx = red[w] > mx ? red[w] : mx;
+        my = red[NW + w] > my ? red[NW + w] : my;
+        vs += red[2 * NW + w];
+      }
+      const double cx = mx / dx, cy = my / dy;
+      const double cm = cx > cy ? cx : cy;
+      atomicMax(&C->cmax_bits, (unsigned long long)__double_as_longlong(cm));
+      atomicAdd(&C->cell_updates, (unsigned long long)(M * M));
+      pmass[unit] = vs * (dx * dy);
+    }
+    if (nclip) {
+      atomicAdd(&C->step_nclip, (unsigned long long)nclip);
+      atomicAdd(&C->step_clipvol, clipd * (dx * dy));
+    }
   }
   if (bad) C->nonfinite = 1;
+  return anywet;
 }
 
 // End of a step: the last CTA to finish applies the CFL rule to every active
@@ -647,6 +724,11 @@ __device__ void step_finish(const GfGeom& G, const GfView& V,
     __syncthreads();
   }
   if (tid == 0) {
+    if (V.sched) {
+      V.sched[0] ^= 1u;
+      V.sched[1] = 0u;
+      V.sched[2] = 0u;
+    }
     __threadfence();
     *V.done = 0u;
   }
@@ -658,8 +740,20 @@ __global__ void __launch_bounds__(NT, MINB)
                  const __grid_constant__ GfView V, double* __restrict__ pmass) {
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int NSUB = (MP / M) * (MP / M);
-  const GfPatch Pt = V.patch[blockIdx.x / NSUB];
-  if (V.ctl[Pt.scen].active) patch_body<P, MP, M, NT>(G, V, pmass, smraw);
+  const int slot = blockIdx.x / NSUB, sub = blockIdx.x % NSUB;
+  // launch order: tiles that held water in the previous launch first, so the
+  // long wet CTAs start at once and the short dry ones fill in around them
+  const bool sched = V.sched != nullptr && V.done != nullptr;
+  const unsigned par = sched ? V.sched[0] : 0u;
+  const int p = sched ? (par ? V.ord1 : V.ord0)[slot] : slot;
+  const GfPatch Pt = V.patch[p];
+  int wet = 0;
+  if (V.ctl[Pt.scen].active) wet = patch_body<P, MP, M, NT>(G, V, pmass, smraw, p, sub);
+  if (sched && sub == 0 && threadIdx.x == 0) {
+    int* nxt = par ? V.ord0 : V.ord1;
+    if (wet) nxt[atomicAdd(V.sched + 1, 1u)] = p;
+    else nxt[V.npatch - 1 - (int)atomicAdd(V.sched + 2, 1u)] = p;
+  }
   if (V.done)
     step_finish<NT>(G, V, pmass,
                     reinterpret_cast<double*>(smraw + Layout<P, M>::OFF_RED),

@@ -304,8 +304,8 @@ class Forest:
         self._check(lib().geoflood_gauges(self._h, s, _p(out), _p(arr)))
         return out, arr
 
-    def profile(self, enable=True):
-        self._check(lib().geoflood_profile(self._h, 1 if enable else 0))
+    def profile(self, enable=True, every=1):
+        self._check(lib().geoflood_profile(self._h, int(every) if enable else 0))
 
     def profile_read(self, kernel):
         ms = C.c_double()
@@ -320,7 +320,7 @@ class Forest:
 
     def autotune(self, reps=5):
         v = C.c_int()
-        ms = np.zeros(4)
+        ms = np.full(8, np.nan)
         self._check(lib().geoflood_autotune(self._h, int(reps), C.byref(v), _p(ms)))
         return v.value, ms
 
