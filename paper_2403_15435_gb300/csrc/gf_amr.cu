@@ -250,22 +250,32 @@ __device__ void tile_bc(const G2& e, const GfPatch& P, T* q, T* bfield,
   }
 }
 
-// Ghost fill: one CTA per patch.  Interior-domain ghosts from the leaves
-// (reads only leaf interiors, so patches are independent), then the
-// physical boundaries.
+// Ghost fill: one CTA per patch, one thread per ghost cell.  Interior-domain
+// ghosts from the leaves (reads only leaf interiors, so patches are
+// independent), then the physical boundaries.  A ghost cell in a region
+// whose same-level neighbour exists is a plain copy of that neighbour's
+// stored values; its position in the neighbour follows from the region's
+// offset, so only the neighbour's index is looked up (in shared memory).
 template <typename T>
 __global__ void k_ghost_fill(const __grid_constant__ GfGeom G, const __grid_constant__ GfView V, int only_accepted,
-                             int* errflag) {
-  const int p = blockIdx.x;
+                             int* errflag, const int* list) {
+  // with a list: only the listed patches, and only the regions without a
+  // same-level neighbour (the patch step pushed those)
+  const int p = list ? list[blockIdx.x] : blockIdx.x;
+  __shared__ int snb[8];
+  if (threadIdx.x < 8)
+    snb[threadIdx.x] = V.nbr ? V.nbr[(size_t)p * 8 + threadIdx.x] : GF_NBR_OTHER;
   const GfPatch P = V.patch[p];
   const GfCtl* C = V.ctl + P.scen;
   if (only_accepted && !C->accepted) return;
   Geo<T> e(G, V);
   const int M = G.M, T_ = G.T, TT = T_ * T_;
-  T* q = e.qp(p, C->cur);
+  const int cur = C->cur;
+  T* q = e.qp(p, cur);
   const T* bb = e.bp(p);
   const long long NX = e.nx(P.level), NY = e.ny(P.level);
   const int nghost = TT - M * M;
+  __syncthreads();
   int err = 0;
   for (int k = threadIdx.x; k < nghost; k += blockDim.x) {
     // enumerate ghost cells: the two bottom rows, the two top rows, then the
@@ -283,19 +293,22 @@ __global__ void k_ghost_fill(const __grid_constant__ GfGeom G, const __grid_cons
     const long long I = (long long)P.px * M + i, J = (long long)P.py * M + j;
     if (I < 0 || J < 0 || I >= NX || J >= NY) continue;
     const int c = e.tix(i, j);
-    // same-level neighbour (from the neighbour table): copy the stored
-    // values as they are
-    const int region = i < 0 ? (j < 0 ? 4 : (j >= M ? 6 : 0))
-                             : (i >= M ? (j < 0 ? 5 : (j >= M ? 7 : 1))
-                                       : (j < 0 ? 2 : 3));
-    const int pn = V.nbr ? V.nbr[(size_t)p * 8 + region] : e.leaf(P.scen, P.level, I, J);
+    // regions: left, right, bottom, top, then the corners bottom-left,
+    // bottom-right, top-left, top-right
+    const int dxr = i < 0 ? -1 : (i >= M ? 1 : 0);
+    const int dyr = j < 0 ? -1 : (j >= M ? 1 : 0);
+    const int region = dxr == 0 ? (dyr < 0 ? 2 : 3)
+                                : (dyr == 0 ? (dxr < 0 ? 0 : 1)
+                                            : 4 + (dxr > 0 ? 1 : 0) + (dyr > 0 ? 2 : 0));
+    const int pn = V.nbr ? snb[region] : e.leaf(P.scen, P.level, I, J);
+    if (pn >= 0 && list) continue;
     if (pn >= 0) {
-      const GfPatch Pn = V.patch[pn];
-      const int cn = e.tix((int)(I - (long long)Pn.px * M), (int)(J - (long long)Pn.py * M));
-      const T* qn = e.qp(pn, C->cur);
-      q[c] = qn[cn];
-      q[TT + c] = qn[TT + cn];
-      q[2 * TT + c] = qn[2 * TT + cn];
+      const int cn = e.tix(i - dxr * M, j - dyr * M);
+      const T* qn = e.qp(pn, cur);
+      const T a0 = qn[cn], a1 = qn[TT + cn], a2 = qn[2 * TT + cn];
+      q[c] = a0;
+      q[TT + c] = a1;
+      q[2 * TT + c] = a2;
       continue;
     }
     const double bt = (double)bb[c];
@@ -304,8 +317,67 @@ __global__ void k_ghost_fill(const __grid_constant__ GfGeom G, const __grid_cons
     e.store(q, c, out[0], out[1], out[2], bt);
   }
   if (err && errflag) *errflag = 1;
+  if (list) return;  // the physical boundaries follow in k_ghost_bc
   __syncthreads();
   tile_bc<T>(e, P, q, nullptr, 0);
+}
+
+// Physical boundaries after the step (one thread per ghost cell of the
+// listed boundary patches): a ghost cell outside the domain takes the cell
+// mirrored (wall) or clamped (extrapolation) across every boundary it lies
+// beyond, with the normal momentum of each wall negated.  This equals the
+// y-sides-then-x-sides order of tile_bc, because the source cell is inside
+// the domain (interior or a ghost already filled) and never written here.
+template <typename T>
+__global__ void k_ghost_bc(const __grid_constant__ GfGeom G, const __grid_constant__ GfView V,
+                           const int* list, int n) {
+  const int M = G.M, T_ = G.T, TT = T_ * T_;
+  const int nghost = TT - M * M;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)n * nghost) return;
+  const int p = list[idx / nghost];
+  const int k = (int)(idx % nghost);
+  const GfPatch P = V.patch[p];
+  const GfCtl* C = V.ctl + P.scen;
+  if (!C->accepted) return;
+  Geo<T> e(G, V);
+  int i, j;
+  const int band = 2 * T_;
+  if (k < band) { i = k % T_ - GF_NG; j = k / T_ - GF_NG; }
+  else if (k < 2 * band) { i = (k - band) % T_ - GF_NG; j = M + (k - band) / T_; }
+  else {
+    const int r = k - 2 * band;
+    j = r / 4;
+    const int c = r % 4;
+    i = c < 2 ? c - GF_NG : M + (c - 2);
+  }
+  const long long NX = e.nx(P.level), NY = e.ny(P.level);
+  const long long I = (long long)P.px * M + i, J = (long long)P.py * M + j;
+  const bool outx = I < 0 || I >= NX, outy = J < 0 || J >= NY;
+  if (!outx && !outy) return;
+  int is = i, js = j;
+  T sgn_u = T(1), sgn_v = T(1);
+  if (outx) {
+    const int side = I < 0 ? 0 : 1;
+    const bool wall = G.bc[side] == 0;
+    const int gl = I < 0 ? (int)(-I) : (int)(I - NX + 1);  // 1 or 2 cells out
+    const int edge = I < 0 ? 0 : M - 1;                    // patch-local edge
+    is = wall ? (I < 0 ? gl - 1 : M - gl) : edge;
+    if (wall) sgn_u = T(-1);
+  }
+  if (outy) {
+    const int side = J < 0 ? 2 : 3;
+    const bool wall = G.bc[side] == 0;
+    const int gl = J < 0 ? (int)(-J) : (int)(J - NY + 1);
+    const int edge = J < 0 ? 0 : M - 1;
+    js = wall ? (J < 0 ? gl - 1 : M - gl) : edge;
+    if (wall) sgn_v = T(-1);
+  }
+  T* q = e.qp(p, C->cur);
+  const int c = e.tix(i, j), cs = e.tix(is, js);
+  q[c] = q[cs];
+  q[TT + c] = sgn_u * q[TT + cs];
+  q[2 * TT + c] = sgn_v * q[2 * TT + cs];
 }
 
 // ------------------------------------------------------------ topography
@@ -741,8 +813,33 @@ int launch_ghost_fill(const GfGeom& g, const GfView& v, int only_accepted,
                       void* stream) {
   if (v.npatch <= 0) return 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (v.prec) k_ghost_fill<float><<<v.npatch, 128, 0, st>>>(g, v, only_accepted, g_errflag);
-  else k_ghost_fill<double><<<v.npatch, 128, 0, st>>>(g, v, only_accepted, g_errflag);
+  const int nghost = g.T * g.T - g.M * g.M;  // 272 (M = 32) or 144 (M = 16)
+  const int nt = (nghost + 31) / 32 * 32;
+  if (v.prec) k_ghost_fill<float><<<v.npatch, nt, 0, st>>>(g, v, only_accepted, g_errflag, nullptr);
+  else k_ghost_fill<double><<<v.npatch, nt, 0, st>>>(g, v, only_accepted, g_errflag, nullptr);
+  return ok();
+}
+
+int launch_ghost_rest(const GfGeom& g, const GfView& v, const int* list, int n,
+                      void* stream) {
+  if (n <= 0) return 0;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int nghost = g.T * g.T - g.M * g.M;
+  const int nt = (nghost + 31) / 32 * 32;
+  if (v.prec) k_ghost_fill<float><<<n, nt, 0, st>>>(g, v, 1, g_errflag, list);
+  else k_ghost_fill<double><<<n, nt, 0, st>>>(g, v, 1, g_errflag, list);
+  return ok();
+}
+
+int launch_ghost_bc(const GfGeom& g, const GfView& v, const int* list, int n,
+                    void* stream) {
+  if (n <= 0) return 0;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int nghost = g.T * g.T - g.M * g.M;
+  const long long total = (long long)n * nghost;
+  const int blocks = (int)((total + 255) / 256);
+  if (v.prec) k_ghost_bc<float><<<blocks, 256, 0, st>>>(g, v, list, n);
+  else k_ghost_bc<double><<<blocks, 256, 0, st>>>(g, v, list, n);
   return ok();
 }
 

@@ -83,6 +83,12 @@ struct geoflood_ctx {
   unsigned* d_sched = nullptr;        // launch-order parity and counters
   int* d_ord[2] = {nullptr, nullptr}; // launch orders of the patch step
   unsigned char* d_same = nullptr;    // per work unit: buffers agree
+  unsigned* d_pwet = nullptr;         // adaptive variant: per-patch flags
+  unsigned* d_pcnt = nullptr;
+  int* d_glist[2] = {nullptr, nullptr};  // patches with a coarser/finer neighbour
+  int nglist[2] = {0, 0};
+  int* d_blist[2] = {nullptr, nullptr};  // patches on the domain boundary
+  int nblist[2] = {0, 0};
   bool own_stream = false;
   // CUDA graphs of chunks of steps, keyed by chunk length
   struct Graph {
@@ -165,6 +171,9 @@ GfView view(geoflood_ctx* c, int t, int bb) {
   v.ord0 = c->d_ord[0];
   v.ord1 = c->d_ord[1];
   v.same = c->d_same;
+  v.push = 1;
+  v.pwet = c->d_pwet;
+  v.pcnt = c->d_pcnt;
   v.npatch = c->npatch;
   v.prec = c->prec;
   return v;
@@ -264,6 +273,26 @@ int upload_tables(geoflood_ctx* ctx, int t,
   }
   CK(cudaMemcpyAsync(ctx->d_nbr[t], nb.data(), sizeof(int) * nb.size(),
                      cudaMemcpyHostToDevice, ctx->st));
+  // patches with a ghost region that no same-level neighbour pushes into:
+  // a finer or coarser neighbour (gl), or the domain boundary (bl)
+  std::vector<int> gl, bl;
+  for (size_t k = 0; k < total; ++k) {
+    bool other = false, outside = false;
+    for (int r = 0; r < 8; ++r) {
+      other |= nb[k * 8 + r] == GF_NBR_OTHER;
+      outside |= nb[k * 8 + r] == GF_NBR_OUTSIDE;
+    }
+    if (other) gl.push_back((int)k);
+    if (outside) bl.push_back((int)k);
+  }
+  ctx->nglist[t] = (int)gl.size();
+  ctx->nblist[t] = (int)bl.size();
+  if (!gl.empty())
+    CK(cudaMemcpyAsync(ctx->d_glist[t], gl.data(), sizeof(int) * gl.size(),
+                       cudaMemcpyHostToDevice, ctx->st));
+  if (!bl.empty())
+    CK(cudaMemcpyAsync(ctx->d_blist[t], bl.data(), sizeof(int) * bl.size(),
+                       cudaMemcpyHostToDevice, ctx->st));
   // a new patch list: launch order back to patch order, no tile known to
   // agree between the buffers
   std::vector<int> iota(total);
@@ -274,6 +303,8 @@ int upload_tables(geoflood_ctx* ctx, int t,
                      cudaMemcpyHostToDevice, ctx->st));
   CK(cudaMemsetAsync(ctx->d_sched, 0, 4 * sizeof(unsigned), ctx->st));
   CK(cudaMemsetAsync(ctx->d_same, 0, (size_t)ctx->cap * 4, ctx->st));
+  CK(cudaMemsetAsync(ctx->d_pwet, 0, (size_t)ctx->cap * sizeof(unsigned), ctx->st));
+  CK(cudaMemsetAsync(ctx->d_pcnt, 0, (size_t)ctx->cap * sizeof(unsigned), ctx->st));
   CK(cudaMemcpyAsync(ctx->d_patch[t], hp.data(), sizeof(GfPatch) * total,
                      cudaMemcpyHostToDevice, ctx->st));
   CK(cudaMemcpyAsync(ctx->d_lut[t], lut.data(), sizeof(int) * lut.size(),
@@ -532,6 +563,12 @@ int geoflood_init_forest(const geoflood_config* cfg, void* stream,
   okk &= alloc((void**)&ctx->d_ord[0], cap * sizeof(int));
   okk &= alloc((void**)&ctx->d_ord[1], cap * sizeof(int));
   okk &= alloc((void**)&ctx->d_same, cap * 4);
+  okk &= alloc((void**)&ctx->d_pwet, cap * sizeof(unsigned));
+  okk &= alloc((void**)&ctx->d_pcnt, cap * sizeof(unsigned));
+  okk &= alloc((void**)&ctx->d_glist[0], cap * sizeof(int));
+  okk &= alloc((void**)&ctx->d_glist[1], cap * sizeof(int));
+  okk &= alloc((void**)&ctx->d_blist[0], cap * sizeof(int));
+  okk &= alloc((void**)&ctx->d_blist[1], cap * sizeof(int));
   okk &= alloc((void**)&ctx->d_lut[0], (size_t)ctx->nscen * G.lut_per_scen * sizeof(int));
   okk &= alloc((void**)&ctx->d_lut[1], (size_t)ctx->nscen * G.lut_per_scen * sizeof(int));
   okk &= alloc((void**)&ctx->d_scen, ctx->nscen * sizeof(GfScenario));
@@ -610,6 +647,12 @@ void geoflood_destroy(geoflood_ctx* ctx) {
   cudaFree(ctx->d_ord[0]);
   cudaFree(ctx->d_ord[1]);
   cudaFree(ctx->d_same);
+  cudaFree(ctx->d_pwet);
+  cudaFree(ctx->d_pcnt);
+  cudaFree(ctx->d_glist[0]);
+  cudaFree(ctx->d_glist[1]);
+  cudaFree(ctx->d_blist[0]);
+  cudaFree(ctx->d_blist[1]);
   cudaFree(ctx->d_scen);
   cudaFree(ctx->d_ctl);
   cudaFree(ctx->d_pmass);
@@ -893,7 +936,10 @@ int geoflood_step(geoflood_ctx* ctx, double t_target, int max_steps,
         gr->ev.push_back(r);
         cudaEventRecordWithFlags(rg.a, ctx->st, cudaEventRecordExternal);
       }
-      lrc |= gf::launch_ghost_fill(ctx->G, v, 1, ctx->st);
+      lrc |= gf::launch_ghost_rest(ctx->G, v, ctx->d_glist[ctx->tsel], ctx->nglist[ctx->tsel],
+                                   ctx->st);
+      lrc |= gf::launch_ghost_bc(ctx->G, v, ctx->d_blist[ctx->tsel], ctx->nblist[ctx->tsel],
+                                 ctx->st);
       if (sample) {
         cudaEventRecordWithFlags(rg.b, ctx->st, cudaEventRecordExternal);
         gr->evg.push_back(rg);
@@ -918,7 +964,8 @@ int geoflood_step(geoflood_ctx* ctx, double t_target, int max_steps,
     gr->prof = prof;
     gr->variant = ctx->variant;
   }
-  const int per_step = 2 + (ctx->max_gauges_used > 0 ? 1 : 0);
+  const int per_step = 1 + (ctx->nglist[ctx->tsel] > 0 ? 1 : 0) +
+                       (ctx->nblist[ctx->tsel] > 0 ? 1 : 0) + (ctx->max_gauges_used > 0 ? 1 : 0);
   long long launched = 0;
   const long long limit = (long long)max_steps * 2 + 64;
   while (max_steps > 0) {

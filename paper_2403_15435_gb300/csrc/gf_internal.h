@@ -97,6 +97,14 @@ struct GfView {
   // buffers hold the same interior (a dry tile was copied), so a dry tile
   // can skip its writes (or null).
   unsigned char* same;
+  // 1: the patch step also writes the two edge rows and columns of its new
+  // interior into the ghost cells of its same-level neighbours in the next
+  // buffer (so the separate ghost fill skips those regions); needs nbr.
+  int push;
+  // adaptive variant: per patch, whether a sub-tile held water and how many
+  // of its CTAs have finished (both back to 0 after the patch is reported)
+  unsigned* pwet;
+  unsigned* pcnt;
   int npatch;
   int prec;               // 0 = FP64, 1 = FP32 surface deviation
 };
@@ -133,6 +141,14 @@ int launch_ctl_begin(GfCtl* ctl, int nscen, double t_target,
                      long long max_steps, const int* scen_mask, void* stream);
 int launch_ghost_fill(const GfGeom& g, const GfView& v, int only_active,
                       void* stream);
+// Ghost cells in regions without a same-level neighbour (which the patch
+// step's push leaves out) for the patches of list[0..n).
+int launch_ghost_rest(const GfGeom& g, const GfView& v, const int* list, int n,
+                      void* stream);
+// Physical-boundary ghost cells of the patches of list[0..n) (after
+// launch_ghost_rest).
+int launch_ghost_bc(const GfGeom& g, const GfView& v, const int* list, int n,
+                    void* stream);
 int launch_topo(const GfGeom& g, const GfView& v, int first, int count,
                 void* stream);
 int launch_regrid_fill(const GfGeom& g, const GfView& oldv,

@@ -172,36 +172,41 @@ __device__ __forceinline__ R dot3(const R* a, const R* b) {
 
 // Fluctuations A-dQ, A+dQ and the limited correction flux of one edge from
 // its waves (Z, S) and the waves of its two neighbouring edges (Zm at the
-// edge before, Zp at the edge after).  nodry = false switches the correction
-// off (an edge touching a dry cell).
-template <typename R>
+// edge before, Zp at the edge after).  Component c of a wave array is at
+// [c * ST] (ST = 1: packed; larger: one plane per component).  nodry = false
+// switches the correction off (an edge touching a dry cell).
+template <typename R, int ST = 1>
 __device__ __forceinline__ void edge_fluxes(const R* Z, const R* S,
                                             const R* Zm, const R* Zp, R nu,
                                             bool nodry, R (&am)[3],
                                             R (&ap)[3], R (&ff)[3]) {
   R cm[3][3], cp[3][3], cf[3][3];
+  R z[9];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) z[c] = Z[c * ST];
 #pragma unroll
   for (int p = 0; p < 3; ++p) {
-    const R sp = S[p];
+    const R sp = S[p * ST];
     const R wm = sp < R(0) ? R(1) : (sp == R(0) ? R(0.5) : R(0));
     const R wp = sp > R(0) ? R(1) : (sp == R(0) ? R(0.5) : R(0));
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      cm[p][k] = Z[3 * p + k] * wm;
-      cp[p][k] = Z[3 * p + k] * wp;
+      cm[p][k] = z[3 * p + k] * wm;
+      cp[p][k] = z[3 * p + k] * wp;
       cf[p][k] = R(0);
     }
     if (sp != R(0) && nodry) {
-      const R zz = dot3(Z + 3 * p, Z + 3 * p);
+      const R zz = dot3(z + 3 * p, z + 3 * p);
       if (zz != R(0)) {
         const R* up = sp > R(0) ? Zm : Zp;
-        const R th = dot3(up + 3 * p, Z + 3 * p) / zz;
+        const R u3[3] = {up[(3 * p) * ST], up[(3 * p + 1) * ST], up[(3 * p + 2) * ST]};
+        const R th = dot3(u3, z + 3 * p) / zz;
         const R phi = mc(th);
         const R sg = sp > R(0) ? R(1) : R(-1);
         const R as = sp > R(0) ? sp : -sp;
         const R coef = R(0.5) * sg * (R(1) - nu * as) * phi;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) cf[p][k] = coef * Z[3 * p + k];
+        for (int k = 0; k < 3; ++k) cf[p][k] = coef * z[3 * p + k];
       }
     }
   }

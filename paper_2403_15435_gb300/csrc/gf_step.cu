@@ -46,7 +46,7 @@ namespace gf {
 // tile), 1 = four CTAs of 16 x 16 sub-tiles per patch, 2 = as 0 (FP32) or 1
 // (FP64) with the register limit for one CTA per SM; 16 x 16 patches have the
 // single variant 0.
-int patch_step_variants(int mx, int prec) { return mx == 32 ? (prec ? 4 : 3) : 1; }
+int patch_step_variants(int mx, int prec) { return mx == 32 ? 4 : 1; }
 
 int launch_patch_step_f64(const GfGeom& g, const GfView& v, double* pmass,
                           int variant, void* stream) {
@@ -56,6 +56,8 @@ int launch_patch_step_f64(const GfGeom& g, const GfView& v, double* pmass,
     return gfs::launch_step<gfs::PrecF64, 32, 16, 256, 2>(g, v, pmass, st);
   if (g.M == 32 && variant == 2)
     return gfs::launch_step<gfs::PrecF64, 32, 16, 256, 1>(g, v, pmass, st);
+  if (g.M == 32 && variant == 3)
+    return gfs::launch_step_adaptive<gfs::PrecF64, 32, 16, 352, 1>(g, v, pmass, st);
   if (g.M == 32) return gfs::launch_step<gfs::PrecF64, 32, 32, 512, 1>(g, v, pmass, st);
   if (g.M == 16) return gfs::launch_step<gfs::PrecF64, 16, 16, 256, 1>(g, v, pmass, st);
   return -1;

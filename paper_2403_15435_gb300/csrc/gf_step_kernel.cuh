@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "gf_internal.h"
 #include "gf_solver.cuh"
@@ -108,7 +109,8 @@ struct Layout {
   static constexpr size_t OFF_F = OFF_W + sizeof(R) * 12 * NEDGE;
   static constexpr size_t OFF_G = OFF_F + sizeof(R) * 3 * M * (M + 1);
   static constexpr size_t OFF_RED = align16(OFF_G + sizeof(R) * 3 * M * (M + 1));
-  static constexpr size_t OFF_WET = OFF_RED + sizeof(double) * 64;
+  static constexpr size_t OFF_NB = OFF_RED + sizeof(double) * 64;  // 8 ints
+  static constexpr size_t OFF_WET = OFF_NB + 32;
   static constexpr size_t OFF_BAR = align16(OFF_WET + (P::DEV ? TT : 0));
   static constexpr size_t BYTES = OFF_BAR + 16;
 };
@@ -151,7 +153,7 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
   using R = typename P::R;
   constexpr bool DEV = P::DEV;
   using Lo = Layout<P, M>;
-  constexpr int TT = Lo::TT, NE = Lo::NE;
+  constexpr int TT = Lo::TT, NE = Lo::NE, NEDGE = Lo::NEDGE;
   constexpr int TGW = MP + 2 * GF_NG, TG = TGW * TGW;  // patch tile
   constexpr int NS1 = MP / M, NSUB = NS1 * NS1;
   constexpr int RL = (Lo::NLIM + NT - 1) / NT;    // limiter items per thread
@@ -176,6 +178,7 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
   R* Gtr = reinterpret_cast<R*>(smraw + Lo::OFF_G);  // [column i][edge][3]
   double* red = reinterpret_cast<double*>(smraw + Lo::OFF_RED);
   unsigned char* swet = smraw + Lo::OFF_WET;
+  int* snb = reinterpret_cast<int*>(smraw + Lo::OFF_NB);  // same-level neighbours
   uint64_t* bar = reinterpret_cast<uint64_t*>(smraw + Lo::OFF_BAR);
 
   const int tid = threadIdx.x;
@@ -271,6 +274,8 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
       rscal[5] = (R)C->dt_use;
     }
   }
+  const bool push = V.push != 0 && V.nbr != nullptr;
+  if (push && tid < 8) snb[tid] = V.nbr[(size_t)p * 8 + tid];
   const double drytol = G.drytol;
   R smx = R(0), smy = R(0);
 
@@ -332,8 +337,10 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
   // wave, correction and transverse term is zero and the update reduces to
   // zeroing the momenta of the (dry) cells, which the dry branch below does
   // without the sweeps; the results are identical.
-#pragma unroll 1
-  for (int dir = 0; dir < (anywet ? 2 : 0); ++dir) {
+  // one sweep; the direction is a compile-time constant so that the index
+  // arithmetic of the two sweeps is resolved statically
+  auto sweep = [&](auto dirc) {
+    constexpr int dir = decltype(dirc)::value;
     const R* sn = dir == 0 ? shu : shv;  // normal momentum
     const R* st = dir == 0 ? shv : shu;  // transverse momentum
     const R nu = dir == 0 ? nux : nuy;
@@ -347,12 +354,13 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
           gfk::Side<R>{sdep[cl], sn[cl], st[cl], sb[cl], s0[cl], wetc(cl)},
           gfk::Side<R>{sdep[cr], sn[cr], st[cr], sb[cr], s0[cr], wetc(cr)}, g,
           rdry, Z, S);
-      R* w = W + 12 * k;
+      // waves in planes: component q of edge k at W[q * NEDGE + k]
+      R* w = W + k;
 #pragma unroll
-      for (int q = 0; q < 9; ++q) w[q] = Z[q];
-      w[9] = S[0];
-      w[10] = S[1];
-      w[11] = S[2];
+      for (int q = 0; q < 9; ++q) w[q * NEDGE] = Z[q];
+      w[9 * NEDGE] = S[0];
+      w[10 * NEDGE] = S[1];
+      w[11 * NEDGE] = S[2];
     }
     __syncthreads();
     // phase 2: fluctuations and limited corrections on edges 0..M
@@ -363,17 +371,18 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
       if (k < Lo::NLIM) {
         const int line = k / (M + 1) - 1, a = k % (M + 1);
         const int e = (line + 1) * NE + a + 1;
-        const R* w = W + 12 * e;
+        const R* w = W + e;
         const int cl = dir == 0 ? tix<M>(a - 1, line) : tix<M>(line, a - 1);
         const int cr = dir == 0 ? tix<M>(a, line) : tix<M>(line, a);
         const bool wet = wetc(cl) && wetc(cr);
-        gfk::edge_fluxes<R>(w, w + 9, w - 12, w + 12, nu, wet, AMr[r], APr[r],
-                            FFr[r]);
+        gfk::edge_fluxes<R, NEDGE>(w, w + 9 * NEDGE, w - 1, w + 1, nu, wet, AMr[r],
+                                   APr[r], FFr[r]);
         if (line >= 0 && line < M) {
           R m = R(0);
 #pragma unroll
           for (int q = 0; q < 3; ++q) {
-            const R as = w[9 + q] > R(0) ? w[9 + q] : -w[9 + q];
+            const R sq = w[(9 + q) * NEDGE];
+            const R as = sq > R(0) ? sq : -sq;
             m = as > m ? as : m;
           }
           if (dir == 0) smx = m > smx ? m : smx;
@@ -387,12 +396,12 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
       const int k = tid + r * NT;
       if (k < Lo::NLIM) {
         const int line = k / (M + 1) - 1, a = k % (M + 1);
-        R* w = W + 12 * ((line + 1) * NE + a + 1);
+        R* w = W + ((line + 1) * NE + a + 1);
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-          w[q] = AMr[r][q];
-          w[3 + q] = APr[r][q];
-          w[6 + q] = FFr[r][q];
+          w[q * NEDGE] = AMr[r][q];
+          w[(3 + q) * NEDGE] = APr[r][q];
+          w[(6 + q) * NEDGE] = FFr[r][q];
         }
       }
     }
@@ -406,12 +415,13 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
       if (k < Lo::NCELL) {
         int a, line;  // a: position along the sweep, line: across
         cell_item<M>(k, dir, a, line);
-        const R* wl = W + 12 * ((line + 1) * NE + a + 1);  // edge a
-        const R* wr = wl + 12;                              // edge a+1
+        const R* wl = W + ((line + 1) * NE + a + 1);  // edge a
+        const R* wr = wl + 1;                          // edge a+1
         R d[3];  // frame: mass, normal (sweep) momentum, transverse
 #pragma unroll
         for (int q = 0; q < 3; ++q)
-          d[q] = (wl[3 + q] + wr[q]) + (wr[6 + q] - wl[6 + q]);
+          d[q] = (wl[(3 + q) * NEDGE] + wr[q * NEDGE]) +
+                 (wr[(6 + q) * NEDGE] - wl[(6 + q) * NEDGE]);
         if (r < RC && k < M * M) {
           // store nu * dQ in (h, hu, hv) order
           if (dir == 0) {
@@ -457,7 +467,35 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
       }
     }
     __syncthreads();
+  };
+  if (anywet) {
+    sweep(std::integral_constant<int, 0>{});
+    sweep(std::integral_constant<int, 1>{});
   }
+
+  // New values of a cell near the patch edge also go to the ghost cells of
+  // the same-level neighbours in the next buffer (each such ghost cell has
+  // exactly this one writer; the neighbours read only the current buffer).
+  R* qnext;
+  if constexpr (DEV) qnext = V.qf[cur ^ 1];
+  else qnext = V.q[cur ^ 1];
+  auto push_edge = [&](int gi, int gj, R v0, R v1, R v2) {
+    const int dxs = gi < GF_NG ? -1 : (gi >= MP - GF_NG ? 1 : 0);
+    const int dys = gj < GF_NG ? -1 : (gj >= MP - GF_NG ? 1 : 0);
+    if (!push || (dxs == 0 && dys == 0)) return;
+    auto put = [&](int r, int x, int y) {
+      const int pn = snb[r];
+      if (pn < 0) return;
+      R* d = qnext + (size_t)pn * 3 * TG + (x + GF_NG) + (y + GF_NG) * TGW;
+      d[0] = v0;
+      d[TG] = v1;
+      d[2 * TG] = v2;
+    };
+    if (dxs != 0) put(dxs < 0 ? 0 : 1, gi - dxs * MP, gj);
+    if (dys != 0) put(dys < 0 ? 2 : 3, gi, gj - dys * MP);
+    if (dxs != 0 && dys != 0)
+      put(4 + (dxs > 0 ? 1 : 0) + (dys > 0 ? 2 : 0), gi - dxs * MP, gj - dys * MP);
+  };
 
   // ------------------------------------------------ update, friction, out
   const R mn = rscal[4];
@@ -484,6 +522,7 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
         qd[cg] = s0[c];
         qd[TG + cg] = R(0);
         qd[2 * TG + cg] = R(0);
+        push_edge(ox + i, oy + j, s0[c], R(0), R(0));
         if constexpr (DEV) {
           lod[kp] = los[kp];
           lod[MP * MP + kp] = 0.0f;
@@ -560,6 +599,7 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
     qd[cg] = o[0];
     qd[TG + cg] = o[1];
     qd[2 * TG + cg] = o[2];
+    push_edge(ox + i, oy + j, o[0], o[1], o[2]);
   }
   // block reductions: CFL rate (max), volume (fixed-order tree; FP64 in the
   // plain form, FP32 within a warp and FP64 across warps in the deviation
@@ -633,6 +673,142 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
   }
   if (bad) C->nonfinite = 1;
   return anywet;
+}
+
+// Whole-patch pass of the adaptive variant for a patch expected to be dry:
+// one CTA stages the surface and bed of the MP x MP tile (two TMA bulk
+// copies), decides whether any cell of the tile holds water and, if none
+// does, applies the dry update (copy the surface, zero the momenta) to the
+// whole patch.  Returns 1 if the tile held water (the caller then runs the
+// M x M sub-tiles one after the other; the result does not depend on the
+// split).
+template <class P, int MP, int M, int NT>
+__device__ __forceinline__ int whole_tile(const GfGeom& G, const GfView& V,
+                                          double* __restrict__ pmass,
+                                          unsigned char* smraw, const int p) {
+  using R = typename P::R;
+  constexpr bool DEV = P::DEV;
+  using Lo = Layout<P, M>;
+  constexpr int TGW = MP + 2 * GF_NG, TG = TGW * TGW;
+  constexpr int NS1 = MP / M, NSUB = NS1 * NS1;
+  constexpr int NW = NT / 32;
+  static_assert(2 * TG * sizeof(R) <= Lo::OFF_RED, "tile staging fits the sub-tile layout");
+  static_assert(NSUB * NW <= 96, "per-quadrant partials fit the reduction area");
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const GfPatch Pt = V.patch[p];
+  GfCtl* C = V.ctl + Pt.scen;
+  const int cur = C->cur;
+  R* s0 = reinterpret_cast<R*>(smraw);
+  R* sb = s0 + TG;
+  double* red = reinterpret_cast<double*>(smraw + Lo::OFF_RED);
+  int* snb = reinterpret_cast<int*>(smraw + Lo::OFF_NB);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smraw + Lo::OFF_BAR);
+  const R* qs;
+  R* qd;
+  R* qnext;
+  const R* bs;
+  if constexpr (DEV) {
+    qs = V.qf[cur] + (size_t)p * 3 * TG;
+    qnext = V.qf[cur ^ 1];
+    bs = V.bf + (size_t)p * TG;
+  } else {
+    qs = V.q[cur] + (size_t)p * 3 * TG;
+    qnext = V.q[cur ^ 1];
+    bs = V.b + (size_t)p * TG;
+  }
+  qd = qnext + (size_t)p * 3 * TG;
+  bool same_in = V.same != nullptr;
+  if (same_in)
+    for (int u = 0; u < NSUB; ++u) same_in = same_in && V.same[p * NSUB + u] != 0;
+  const bool push = V.push != 0 && V.nbr != nullptr;
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_expect_tx(bar, 2u * TG * sizeof(R));
+    bulk_g2s(s0, qs, TG * sizeof(R), bar);
+    bulk_g2s(sb, bs, TG * sizeof(R), bar);
+  }
+  if (push && tid < 8) snb[tid] = V.nbr[(size_t)p * 8 + tid];
+  __syncthreads();
+  if (!__syncthreads_and(mbar_wait(bar, GF_SPIN_LIMIT) ? 1 : 0)) {
+    if (tid == 0) C->status = -7;  // GEOFLOOD_ERR_TIMEOUT
+    mbar_wait(bar, GF_SPIN_LIMIT);
+    __syncthreads();
+    return 0;
+  }
+  const double drytol = G.drytol;
+  int anywet = 0;
+  for (int k = tid; k < TG; k += NT) {
+    if constexpr (DEV) anywet |= gfk::wet_dev(s0[k], sb[k], drytol, G.drytolf, G.marginf) ? 1 : 0;
+    else anywet |= s0[k] > drytol ? 1 : 0;
+  }
+  anywet = __syncthreads_or(anywet);
+  if (anywet) return 1;  // the caller runs the sub-tiles
+  // dry update of the whole patch (skipped when both buffers already agree)
+  const float* los = nullptr;
+  float* lod = nullptr;
+  if constexpr (DEV) {
+    los = V.lof[cur] + (size_t)p * 3 * MP * MP;
+    lod = V.lof[cur ^ 1] + (size_t)p * 3 * MP * MP;
+  }
+  R vq[NSUB];
+#pragma unroll
+  for (int u = 0; u < NSUB; ++u) vq[u] = R(0);
+  for (int k = tid; k < MP * MP; k += NT) {
+    const int i = k % MP, j = k / MP;
+    const int c = (i + GF_NG) + (j + GF_NG) * TGW;
+    const R w = s0[c];
+    const R h = DEV ? w - sb[c] : w;
+    const int u = (i / M) + NS1 * (j / M);
+#pragma unroll
+    for (int q = 0; q < NSUB; ++q)
+      if (q == u) vq[q] += h;
+    if (!same_in) {
+      qd[c] = w;
+      qd[TG + c] = R(0);
+      qd[2 * TG + c] = R(0);
+      if constexpr (DEV) {
+        lod[k] = los[k];
+        lod[MP * MP + k] = 0.0f;
+        lod[2 * MP * MP + k] = 0.0f;
+      }
+      if (push) {
+        const int dxs = i < GF_NG ? -1 : (i >= MP - GF_NG ? 1 : 0);
+        const int dys = j < GF_NG ? -1 : (j >= MP - GF_NG ? 1 : 0);
+        auto put = [&](int r, int x, int y) {
+          const int pn = snb[r];
+          if (pn < 0) return;
+          R* d = qnext + (size_t)pn * 3 * TG + (x + GF_NG) + (y + GF_NG) * TGW;
+          d[0] = w;
+          d[TG] = R(0);
+          d[2 * TG] = R(0);
+        };
+        if (dxs != 0) put(dxs < 0 ? 0 : 1, i - dxs * MP, j);
+        if (dys != 0) put(dys < 0 ? 2 : 3, i, j - dys * MP);
+        if (dxs != 0 && dys != 0)
+          put(4 + (dxs > 0 ? 1 : 0) + (dys > 0 ? 2 : 0), i - dxs * MP, j - dys * MP);
+      }
+    }
+  }
+  // per-quadrant volumes: FP32 (deviation form) or FP64 partials per warp,
+  // summed in FP64 in a fixed order
+#pragma unroll
+  for (int q = 0; q < NSUB; ++q) {
+    R v = vq[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    vq[q] = v;
+  }
+  if (lane == 0)
+    for (int q = 0; q < NSUB; ++q) red[q * NW + wid] = (double)vq[q];
+  __syncthreads();
+  if (tid < NSUB) {
+    double vs = 0.0;
+    for (int w = 0; w < NW; ++w) vs += red[tid * NW + w];
+    pmass[p * NSUB + tid] = vs * G.areal[Pt.level];
+    if (V.same != nullptr) V.same[p * NSUB + tid] = 1;
+  }
+  if (tid == 0) atomicAdd(&C->cell_updates, (unsigned long long)(MP * MP));
+  return 0;
 }
 
 // End of a step: the last CTA to finish applies the CFL rule to every active
@@ -726,12 +902,77 @@ __device__ void step_finish(const GfGeom& G, const GfView& V,
   if (tid == 0) {
     if (V.sched) {
       V.sched[0] ^= 1u;
+      V.sched[3] = V.sched[1];  // wet patches at the head of the next order
       V.sched[1] = 0u;
       V.sched[2] = 0u;
     }
     __threadfence();
     *V.done = 0u;
   }
+}
+
+// Adaptive variant: the previous launch's wet patches (the head of its
+// launch order, sched[3] of them) get NSUB CTAs each, one per M x M
+// sub-tile; every other patch gets one CTA that checks the whole tile and
+// takes the dry update, or the sub-tiles in turn if water has arrived.  The
+// grid has NSUB CTAs per patch; those beyond the work exit at once.
+template <class P, int MP, int M, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
+    k_patch_step_adaptive(const __grid_constant__ GfGeom G,
+                          const __grid_constant__ GfView V,
+                          double* __restrict__ pmass) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int NSUB = (MP / M) * (MP / M);
+  const bool sched = V.sched != nullptr && V.done != nullptr;
+  const unsigned par = sched ? V.sched[0] : 0u;
+  const int nw = sched ? (int)V.sched[3] : 0;
+  const int* ord = sched ? (par ? V.ord1 : V.ord0) : nullptr;
+  const int b = blockIdx.x;
+  int p = -1, wet = 0;
+  int s_lo = 0, s_hi = 0;  // sub-tiles this CTA computes
+  bool whole = false, active = false;
+  if (b < nw * NSUB) {
+    p = ord[b / NSUB];
+    s_lo = b % NSUB;
+    s_hi = s_lo + 1;
+  } else if (b < nw * NSUB + (V.npatch - nw)) {
+    p = sched ? ord[nw + (b - nw * NSUB)] : b;
+    whole = true;
+  }
+  if (p >= 0) active = V.ctl[V.patch[p].scen].active != 0;
+  if (whole && active && whole_tile<P, MP, M, NT>(G, V, pmass, smraw, p)) {
+    wet = 1;
+    s_lo = 0;
+    s_hi = NSUB;
+  }
+  if (!active) s_hi = s_lo;
+  // one call site of the sub-tile body
+  for (int sub = s_lo; sub < s_hi; ++sub) {
+    wet |= patch_body<P, MP, M, NT>(G, V, pmass, smraw, p, sub);
+    __syncthreads();
+  }
+  bool report = whole && threadIdx.x == 0;
+  if (!whole && p >= 0 && threadIdx.x == 0) {
+    // the last of the patch's CTAs reports whether any sub-tile held water
+    if (wet) V.pwet[p] = 1u;
+    __threadfence();
+    const unsigned c = atomicAdd(V.pcnt + p, 1u);
+    if (c == NSUB - 1) {
+      __threadfence();
+      wet = *(volatile unsigned*)(V.pwet + p) != 0u;
+      V.pwet[p] = 0u;
+      V.pcnt[p] = 0u;
+      report = true;
+    }
+  }
+  if (sched && report) {
+    int* nxt = par ? V.ord0 : V.ord1;
+    if (wet) nxt[atomicAdd(V.sched + 1, 1u)] = p;
+    else nxt[V.npatch - 1 - (int)atomicAdd(V.sched + 2, 1u)] = p;
+  }
+  if (V.done)
+    step_finish<NT>(G, V, pmass,
+                    reinterpret_cast<double*>(smraw + Layout<P, M>::OFF_RED), NSUB);
 }
 
 template <class P, int MP, int M, int NT, int MINB>
@@ -777,6 +1018,25 @@ int launch_step(const GfGeom& g, const GfView& v, double* pmass,
   }
   constexpr int NSUB = (MP / M) * (MP / M);
   k_patch_step<P, MP, M, NT, MINB><<<v.npatch * NSUB, NT, bytes, st>>>(g, v, pmass);
+  return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+// Launch the adaptive variant (NSUB CTAs per patch, see
+// k_patch_step_adaptive); pmass holds (MP/M)^2 entries per patch.
+template <class P, int MP, int M, int NT, int MINB>
+int launch_step_adaptive(const GfGeom& g, const GfView& v, double* pmass,
+                         cudaStream_t st) {
+  constexpr size_t bytes = Layout<P, M>::BYTES;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k_patch_step_adaptive<P, MP, M, NT, MINB>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bytes) != cudaSuccess)
+      return -2;
+    attr = true;
+  }
+  constexpr int NSUB = (MP / M) * (MP / M);
+  k_patch_step_adaptive<P, MP, M, NT, MINB><<<v.npatch * NSUB, NT, bytes, st>>>(g, v, pmass);
   return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 

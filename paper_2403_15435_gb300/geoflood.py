@@ -320,7 +320,7 @@ class Forest:
 
     def autotune(self, reps=5):
         v = C.c_int()
-        ms = np.full(8, np.nan)
+        ms = np.full(16, np.nan)
         self._check(lib().geoflood_autotune(self._h, int(reps), C.byref(v), _p(ms)))
         return v.value, ms
 
