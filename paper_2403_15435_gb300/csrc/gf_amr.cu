@@ -317,67 +317,9 @@ __global__ void k_ghost_fill(const __grid_constant__ GfGeom G, const __grid_cons
     e.store(q, c, out[0], out[1], out[2], bt);
   }
   if (err && errflag) *errflag = 1;
-  if (list) return;  // the physical boundaries follow in k_ghost_bc
+  // physical boundaries last (they mirror the cells filled above)
   __syncthreads();
   tile_bc<T>(e, P, q, nullptr, 0);
-}
-
-// Physical boundaries after the step (one thread per ghost cell of the
-// listed boundary patches): a ghost cell outside the domain takes the cell
-// mirrored (wall) or clamped (extrapolation) across every boundary it lies
-// beyond, with the normal momentum of each wall negated.  This equals the
-// y-sides-then-x-sides order of tile_bc, because the source cell is inside
-// the domain (interior or a ghost already filled) and never written here.
-template <typename T>
-__global__ void k_ghost_bc(const __grid_constant__ GfGeom G, const __grid_constant__ GfView V,
-                           const int* list, int n) {
-  const int M = G.M, T_ = G.T, TT = T_ * T_;
-  const int nghost = TT - M * M;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long long)n * nghost) return;
-  const int p = list[idx / nghost];
-  const int k = (int)(idx % nghost);
-  const GfPatch P = V.patch[p];
-  const GfCtl* C = V.ctl + P.scen;
-  if (!C->accepted) return;
-  Geo<T> e(G, V);
-  int i, j;
-  const int band = 2 * T_;
-  if (k < band) { i = k % T_ - GF_NG; j = k / T_ - GF_NG; }
-  else if (k < 2 * band) { i = (k - band) % T_ - GF_NG; j = M + (k - band) / T_; }
-  else {
-    const int r = k - 2 * band;
-    j = r / 4;
-    const int c = r % 4;
-    i = c < 2 ? c - GF_NG : M + (c - 2);
-  }
-  const long long NX = e.nx(P.level), NY = e.ny(P.level);
-  const long long I = (long long)P.px * M + i, J = (long long)P.py * M + j;
-  const bool outx = I < 0 || I >= NX, outy = J < 0 || J >= NY;
-  if (!outx && !outy) return;
-  int is = i, js = j;
-  T sgn_u = T(1), sgn_v = T(1);
-  if (outx) {
-    const int side = I < 0 ? 0 : 1;
-    const bool wall = G.bc[side] == 0;
-    const int gl = I < 0 ? (int)(-I) : (int)(I - NX + 1);  // 1 or 2 cells out
-    const int edge = I < 0 ? 0 : M - 1;                    // patch-local edge
-    is = wall ? (I < 0 ? gl - 1 : M - gl) : edge;
-    if (wall) sgn_u = T(-1);
-  }
-  if (outy) {
-    const int side = J < 0 ? 2 : 3;
-    const bool wall = G.bc[side] == 0;
-    const int gl = J < 0 ? (int)(-J) : (int)(J - NY + 1);
-    const int edge = J < 0 ? 0 : M - 1;
-    js = wall ? (J < 0 ? gl - 1 : M - gl) : edge;
-    if (wall) sgn_v = T(-1);
-  }
-  T* q = e.qp(p, C->cur);
-  const int c = e.tix(i, j), cs = e.tix(is, js);
-  q[c] = q[cs];
-  q[TT + c] = sgn_u * q[TT + cs];
-  q[2 * TT + c] = sgn_v * q[2 * TT + cs];
 }
 
 // ------------------------------------------------------------ topography
@@ -572,15 +514,12 @@ __global__ void k_tags(const __grid_constant__ GfGeom G, const __grid_constant__
 
 // Gauges (Sec. 5.1 control points, Sec. 6.5): bilinear in the finest leaf,
 // ghosts included; arrival at the first sample with h > 1 cm.
+// Stencil of gauge g of scenario S: the finest leaf holding the point, and
+// the lower-left cell (i0, j0 in [-1, M-1], ghosts included) and weights of
+// the bilinear interpolation between cell centres.
 template <typename T>
-__global__ void k_gauges(const __grid_constant__ GfGeom G, const __grid_constant__ GfView V, int only_accepted) {
-  const int s = blockIdx.y;
-  const GfScenario S = V.scen[s];
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= S.ngauge) return;
-  const GfCtl* C = V.ctl + s;
-  if (only_accepted && !C->accepted) return;
-  Geo<T> e(G, V);
+__device__ GfGaugeRef gauge_locate(const Geo<T>& e, const GfGeom& G, const GfView& V,
+                                   const GfScenario& S, int g) {
   const double x = S.gxy[2 * g], y = S.gxy[2 * g + 1];
   int p = -1, L = 0;
   for (int l = G.maxlevel; l >= 0 && p < 0; --l) {
@@ -596,9 +535,8 @@ __global__ void k_gauges(const __grid_constant__ GfGeom G, const __grid_constant
     const int k = V.lut[S.lut_off + G.lut_lev_off[l] + Pq + Qq * w];
     if (k >= 0) { p = k; L = l; }
   }
-  double* o = S.gout + 5 * g;
-  o[0] = C->t;
-  if (p < 0) { o[1] = o[2] = o[3] = o[4] = 0.0; return; }
+  GfGaugeRef r{-1, 0, 0.0, 0.0};
+  if (p < 0) return r;
   const GfPatch P = V.patch[p];
   const int M = G.M;
   const double fx = (x - G.xlower) / e.dx(L) - 0.5 - (double)((long long)P.px * M);
@@ -608,24 +546,56 @@ __global__ void k_gauges(const __grid_constant__ GfGeom G, const __grid_constant
   if (j0 < -1) j0 = -1;
   if (i0 > M - 1) i0 = M - 1;
   if (j0 > M - 1) j0 = M - 1;
-  const double ax = fx - (double)i0, ay = fy - (double)j0;
+  r.p = p;
+  r.c = e.tix(i0, j0);
+  r.ax = fx - (double)i0;
+  r.ay = fy - (double)j0;
+  return r;
+}
+
+template <typename T>
+__global__ void k_gauge_refs(const __grid_constant__ GfGeom G, const __grid_constant__ GfView V) {
+  const int s = blockIdx.y;
+  const GfScenario S = V.scen[s];
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= S.ngauge) return;
+  Geo<T> e(G, V);
+  const GfGaugeRef r = gauge_locate(e, G, V, S, g);
+  S.gref[g] = r;
+  if (r.p >= 0 && V.gflag != nullptr) V.gflag[r.p] = 1;
+}
+
+// Gauges (Sec. 5.1 control points, Sec. 6.5): bilinear in the finest leaf,
+// ghosts included; arrival at the first sample with h > 1 cm.  During a
+// run the patch step samples each gauge from its staged tile; this kernel
+// takes the samples outside the step (registration, end of a run).
+template <typename T>
+__global__ void k_gauges(const __grid_constant__ GfGeom G, const __grid_constant__ GfView V, int only_accepted) {
+  const int s = blockIdx.y;
+  const GfScenario S = V.scen[s];
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= S.ngauge) return;
+  const GfCtl* C = V.ctl + s;
+  if (only_accepted && !C->accepted) return;
+  Geo<T> e(G, V);
+  const GfGaugeRef r = gauge_locate(e, G, V, S, g);
+  double* o = S.gout + 5 * g;
+  o[0] = C->t;
+  if (r.p < 0) { o[1] = o[2] = o[3] = o[4] = 0.0; return; }
+  const int p = r.p, T_ = G.T;
   double c4[4][4];
-  e.load(p, C->cur, e.tix(i0, j0), c4[0]);
-  e.load(p, C->cur, e.tix(i0 + 1, j0), c4[1]);
-  e.load(p, C->cur, e.tix(i0, j0 + 1), c4[2]);
-  e.load(p, C->cur, e.tix(i0 + 1, j0 + 1), c4[3]);
+  e.load(p, C->cur, r.c, c4[0]);
+  e.load(p, C->cur, r.c + 1, c4[1]);
+  e.load(p, C->cur, r.c + T_, c4[2]);
+  e.load(p, C->cur, r.c + T_ + 1, c4[3]);
   const double eoff = Geo<T>::DEV ? S.eta0 : 0.0;
   double v[4];
   for (int f = 0; f < 4; ++f) {
-    double a00, a10, a01, a11;
-    if (f < 3) {
-      a00 = c4[0][f]; a10 = c4[1][f]; a01 = c4[2][f]; a11 = c4[3][f];
-    } else {
-      a00 = c4[0][0] + c4[0][3]; a10 = c4[1][0] + c4[1][3];
-      a01 = c4[2][0] + c4[2][3]; a11 = c4[3][0] + c4[3][3];
-    }
-    v[f] = (1.0 - ay) * ((1.0 - ax) * a00 + ax * a10) +
-           ay * ((1.0 - ax) * a01 + ax * a11);
+    if (f < 3)
+      v[f] = gf_bilinear(c4[0][f], c4[1][f], c4[2][f], c4[3][f], r.ax, r.ay);
+    else
+      v[f] = gf_bilinear(c4[0][0] + c4[0][3], c4[1][0] + c4[1][3], c4[2][0] + c4[2][3],
+                         c4[3][0] + c4[3][3], r.ax, r.ay);
   }
   o[1] = v[0]; o[2] = v[1]; o[3] = v[2]; o[4] = v[3] + eoff;
   if (S.garr[g] < 0.0 && v[0] > 0.01) S.garr[g] = C->t;
@@ -831,17 +801,6 @@ int launch_ghost_rest(const GfGeom& g, const GfView& v, const int* list, int n,
   return ok();
 }
 
-int launch_ghost_bc(const GfGeom& g, const GfView& v, const int* list, int n,
-                    void* stream) {
-  if (n <= 0) return 0;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const int nghost = g.T * g.T - g.M * g.M;
-  const long long total = (long long)n * nghost;
-  const int blocks = (int)((total + 255) / 256);
-  if (v.prec) k_ghost_bc<float><<<blocks, 256, 0, st>>>(g, v, list, n);
-  else k_ghost_bc<double><<<blocks, 256, 0, st>>>(g, v, list, n);
-  return ok();
-}
 
 int launch_topo(const GfGeom& g, const GfView& v, int first, int count,
                 void* stream) {
@@ -886,6 +845,16 @@ int launch_cnn_features(const GfGeom& g, const GfView& v, int first, int count,
     k_cnn_features<float><<<count, 256, 0, st>>>(g, v, first, sc, static_cast<__nv_bfloat16*>(out));
   else
     k_cnn_features<double><<<count, 256, 0, st>>>(g, v, first, sc, static_cast<__nv_bfloat16*>(out));
+  return ok();
+}
+
+int launch_gauge_refs(const GfGeom& g, const GfView& v, int max_gauges,
+                      void* stream) {
+  if (max_gauges <= 0) return 0;
+  dim3 grid((max_gauges + 63) / 64, g.nscen);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (v.prec) k_gauge_refs<float><<<grid, 64, 0, st>>>(g, v);
+  else k_gauge_refs<double><<<grid, 64, 0, st>>>(g, v);
   return ok();
 }
 

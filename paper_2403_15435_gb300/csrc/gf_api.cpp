@@ -83,12 +83,11 @@ struct geoflood_ctx {
   unsigned* d_sched = nullptr;        // launch-order parity and counters
   int* d_ord[2] = {nullptr, nullptr}; // launch orders of the patch step
   unsigned char* d_same = nullptr;    // per work unit: buffers agree
+  unsigned char* d_gflag = nullptr;   // per patch: holds a gauge
   unsigned* d_pwet = nullptr;         // adaptive variant: per-patch flags
   unsigned* d_pcnt = nullptr;
   int* d_glist[2] = {nullptr, nullptr};  // patches with a coarser/finer neighbour
   int nglist[2] = {0, 0};
-  int* d_blist[2] = {nullptr, nullptr};  // patches on the domain boundary
-  int nblist[2] = {0, 0};
   bool own_stream = false;
   // CUDA graphs of chunks of steps, keyed by chunk length
   struct Graph {
@@ -111,6 +110,7 @@ struct geoflood_ctx {
   size_t stage_cap = 0;
   std::vector<gf::HostForest> forests;
   std::vector<double*> d_dem, d_gxy, d_gout, d_garr;
+  std::vector<GfGaugeRef*> d_gref;
   int max_gauges_used = 0;
   int variant = 0;  // patch-step kernel variant (see geoflood_autotune)
   std::string err;
@@ -173,6 +173,7 @@ GfView view(geoflood_ctx* c, int t, int bb) {
   v.same = c->d_same;
   v.push = 1;
   v.pwet = c->d_pwet;
+  v.gflag = c->d_gflag;
   v.pcnt = c->d_pcnt;
   v.npatch = c->npatch;
   v.prec = c->prec;
@@ -273,25 +274,17 @@ int upload_tables(geoflood_ctx* ctx, int t,
   }
   CK(cudaMemcpyAsync(ctx->d_nbr[t], nb.data(), sizeof(int) * nb.size(),
                      cudaMemcpyHostToDevice, ctx->st));
-  // patches with a ghost region that no same-level neighbour pushes into:
-  // a finer or coarser neighbour (gl), or the domain boundary (bl)
-  std::vector<int> gl, bl;
+  // patches with a ghost region that no same-level neighbour pushes into (a
+  // finer or coarser neighbour): their ghost fill runs after each step
+  std::vector<int> gl;
   for (size_t k = 0; k < total; ++k) {
-    bool other = false, outside = false;
-    for (int r = 0; r < 8; ++r) {
-      other |= nb[k * 8 + r] == GF_NBR_OTHER;
-      outside |= nb[k * 8 + r] == GF_NBR_OUTSIDE;
-    }
+    bool other = false;
+    for (int r = 0; r < 8; ++r) other |= nb[k * 8 + r] == GF_NBR_OTHER;
     if (other) gl.push_back((int)k);
-    if (outside) bl.push_back((int)k);
   }
   ctx->nglist[t] = (int)gl.size();
-  ctx->nblist[t] = (int)bl.size();
   if (!gl.empty())
     CK(cudaMemcpyAsync(ctx->d_glist[t], gl.data(), sizeof(int) * gl.size(),
-                       cudaMemcpyHostToDevice, ctx->st));
-  if (!bl.empty())
-    CK(cudaMemcpyAsync(ctx->d_blist[t], bl.data(), sizeof(int) * bl.size(),
                        cudaMemcpyHostToDevice, ctx->st));
   // a new patch list: launch order back to patch order, no tile known to
   // agree between the buffers
@@ -301,9 +294,10 @@ int upload_tables(geoflood_ctx* ctx, int t,
                      cudaMemcpyHostToDevice, ctx->st));
   CK(cudaMemcpyAsync(ctx->d_ord[1], iota.data(), sizeof(int) * total,
                      cudaMemcpyHostToDevice, ctx->st));
-  CK(cudaMemsetAsync(ctx->d_sched, 0, 4 * sizeof(unsigned), ctx->st));
+  CK(cudaMemsetAsync(ctx->d_sched, 0, 8 * sizeof(unsigned), ctx->st));
   CK(cudaMemsetAsync(ctx->d_same, 0, (size_t)ctx->cap * 4, ctx->st));
   CK(cudaMemsetAsync(ctx->d_pwet, 0, (size_t)ctx->cap * sizeof(unsigned), ctx->st));
+  CK(cudaMemsetAsync(ctx->d_gflag, 0, (size_t)ctx->cap, ctx->st));
   CK(cudaMemsetAsync(ctx->d_pcnt, 0, (size_t)ctx->cap * sizeof(unsigned), ctx->st));
   CK(cudaMemcpyAsync(ctx->d_patch[t], hp.data(), sizeof(GfPatch) * total,
                      cudaMemcpyHostToDevice, ctx->st));
@@ -559,16 +553,15 @@ int geoflood_init_forest(const geoflood_config* cfg, void* stream,
   okk &= alloc((void**)&ctx->d_nbr[0], cap * 8 * sizeof(int));
   okk &= alloc((void**)&ctx->d_nbr[1], cap * 8 * sizeof(int));
   okk &= alloc((void**)&ctx->d_done, sizeof(unsigned));
-  okk &= alloc((void**)&ctx->d_sched, 4 * sizeof(unsigned));
+  okk &= alloc((void**)&ctx->d_sched, 8 * sizeof(unsigned));
   okk &= alloc((void**)&ctx->d_ord[0], cap * sizeof(int));
   okk &= alloc((void**)&ctx->d_ord[1], cap * sizeof(int));
   okk &= alloc((void**)&ctx->d_same, cap * 4);
   okk &= alloc((void**)&ctx->d_pwet, cap * sizeof(unsigned));
+  okk &= alloc((void**)&ctx->d_gflag, cap);
   okk &= alloc((void**)&ctx->d_pcnt, cap * sizeof(unsigned));
   okk &= alloc((void**)&ctx->d_glist[0], cap * sizeof(int));
   okk &= alloc((void**)&ctx->d_glist[1], cap * sizeof(int));
-  okk &= alloc((void**)&ctx->d_blist[0], cap * sizeof(int));
-  okk &= alloc((void**)&ctx->d_blist[1], cap * sizeof(int));
   okk &= alloc((void**)&ctx->d_lut[0], (size_t)ctx->nscen * G.lut_per_scen * sizeof(int));
   okk &= alloc((void**)&ctx->d_lut[1], (size_t)ctx->nscen * G.lut_per_scen * sizeof(int));
   okk &= alloc((void**)&ctx->d_scen, ctx->nscen * sizeof(GfScenario));
@@ -588,6 +581,7 @@ int geoflood_init_forest(const geoflood_config* cfg, void* stream,
   ctx->d_gxy.assign(ctx->nscen, nullptr);
   ctx->d_gout.assign(ctx->nscen, nullptr);
   ctx->d_garr.assign(ctx->nscen, nullptr);
+  ctx->d_gref.assign(ctx->nscen, nullptr);
   for (int s = 0; s < ctx->nscen; ++s) {
     ctx->h_scen[s].lut_off = (long long)s * G.lut_per_scen;
     ctx->forests.emplace_back(c.mi, c.mj, c.minlevel, c.maxlevel);
@@ -648,11 +642,10 @@ void geoflood_destroy(geoflood_ctx* ctx) {
   cudaFree(ctx->d_ord[1]);
   cudaFree(ctx->d_same);
   cudaFree(ctx->d_pwet);
+  cudaFree(ctx->d_gflag);
   cudaFree(ctx->d_pcnt);
   cudaFree(ctx->d_glist[0]);
   cudaFree(ctx->d_glist[1]);
-  cudaFree(ctx->d_blist[0]);
-  cudaFree(ctx->d_blist[1]);
   cudaFree(ctx->d_scen);
   cudaFree(ctx->d_ctl);
   cudaFree(ctx->d_pmass);
@@ -664,6 +657,7 @@ void geoflood_destroy(geoflood_ctx* ctx) {
   for (auto p : ctx->d_gxy) cudaFree(p);
   for (auto p : ctx->d_gout) cudaFree(p);
   for (auto p : ctx->d_garr) cudaFree(p);
+  for (auto p : ctx->d_gref) cudaFree(p);
   if (ctx->h_ctl) cudaFreeHost(ctx->h_ctl);
   if (ctx->own_stream) cudaStreamDestroy(ctx->st);
   for (auto e : ctx->pool) cudaEventDestroy(e);
@@ -771,6 +765,7 @@ int geoflood_write_patches(geoflood_ctx* ctx, int s, const double* h,
   ctx->launches++;
   ctx->h_ctl[s].status = 0;
   ctx->h_ctl[s].nonfinite = 0;
+  ctx->h_ctl[s].accepted = 0;  // the state is not a step result
   if ((rc = sync_ctl_up(ctx))) return rc;
   return ghost_fill_all(ctx);
 }
@@ -865,6 +860,7 @@ int geoflood_set_time(geoflood_ctx* ctx, int s, double t, double dt_next) {
   ctx->h_ctl[s].t = t;
   ctx->h_ctl[s].dt_next = dt_next;
   ctx->h_ctl[s].status = 0;
+  ctx->h_ctl[s].accepted = 0;  // no step result for the next step to sample
   return sync_ctl_up(ctx);
 }
 
@@ -938,14 +934,10 @@ int geoflood_step(geoflood_ctx* ctx, double t_target, int max_steps,
       }
       lrc |= gf::launch_ghost_rest(ctx->G, v, ctx->d_glist[ctx->tsel], ctx->nglist[ctx->tsel],
                                    ctx->st);
-      lrc |= gf::launch_ghost_bc(ctx->G, v, ctx->d_blist[ctx->tsel], ctx->nblist[ctx->tsel],
-                                 ctx->st);
       if (sample) {
         cudaEventRecordWithFlags(rg.b, ctx->st, cudaEventRecordExternal);
         gr->evg.push_back(rg);
       }
-      if (ctx->max_gauges_used > 0)
-        lrc |= gf::launch_gauges(ctx->G, v, 1, ctx->max_gauges_used, ctx->st);
     }
     cudaGraph_t graph = nullptr;
     cudaError_t ce = cudaStreamEndCapture(ctx->st, &graph);
@@ -964,8 +956,7 @@ int geoflood_step(geoflood_ctx* ctx, double t_target, int max_steps,
     gr->prof = prof;
     gr->variant = ctx->variant;
   }
-  const int per_step = 1 + (ctx->nglist[ctx->tsel] > 0 ? 1 : 0) +
-                       (ctx->nblist[ctx->tsel] > 0 ? 1 : 0) + (ctx->max_gauges_used > 0 ? 1 : 0);
+  const int per_step = 1 + (ctx->nglist[ctx->tsel] > 0 ? 1 : 0);
   long long launched = 0;
   const long long limit = (long long)max_steps * 2 + 64;
   while (max_steps > 0) {
@@ -992,6 +983,12 @@ int geoflood_step(geoflood_ctx* ctx, double t_target, int max_steps,
     for (int s = 0; s < ctx->nscen; ++s) any |= ctx->h_ctl[s].active != 0;
     if (!any) break;
     if (launched > limit) return fail(ctx, GEOFLOOD_ERR_CFL, "step: too many retakes");
+  }
+  // the steps sample the gauges at the start of the next step; sample the
+  // final state here
+  if (ctx->max_gauges_used > 0) {
+    CKL(gf::launch_gauges(ctx->G, v, 0, ctx->max_gauges_used, ctx->st), "gauges");
+    ctx->launches++;
   }
   int rc = sync_ctl_down(ctx);
   if (rc) return rc;
@@ -1055,12 +1052,17 @@ int geoflood_regrid(geoflood_ctx* ctx) {
   CK(cudaStreamSynchronize(ctx->st));
   for (int s = 0; s < ctx->nscen; ++s) {
     ctx->h_ctl[s].cur ^= 1;
+    ctx->h_ctl[s].accepted = 0;  // gauges sample step results only
     ctx->forests[s].set_leaves(lv[s]);
   }
   ctx->tsel = nt;
   ctx->bsel = nb;
   ctx->npatch = (int)total;
   ctx->generation++;
+  if (ctx->max_gauges_used > 0) {
+    CKL(gf::launch_gauge_refs(ctx->G, view(ctx), ctx->max_gauges_used, ctx->st), "gauge_refs");
+    ctx->launches++;
+  }
   if ((rc = sync_ctl_up(ctx))) return rc;
   if ((rc = check_errflag(ctx))) return rc;
   return ghost_fill_all(ctx);
@@ -1081,11 +1083,14 @@ int geoflood_set_gauges(geoflood_ctx* ctx, int s, const double* xy, int n) {
   cudaFree(ctx->d_gxy[s]);
   cudaFree(ctx->d_gout[s]);
   cudaFree(ctx->d_garr[s]);
+  cudaFree(ctx->d_gref[s]);
   ctx->d_gxy[s] = ctx->d_gout[s] = ctx->d_garr[s] = nullptr;
+  ctx->d_gref[s] = nullptr;
   const int m = n > 0 ? n : 1;
   CK(cudaMalloc(&ctx->d_gxy[s], 2 * m * sizeof(double)));
   CK(cudaMalloc(&ctx->d_gout[s], 5 * m * sizeof(double)));
   CK(cudaMalloc(&ctx->d_garr[s], m * sizeof(double)));
+  CK(cudaMalloc(&ctx->d_gref[s], m * sizeof(GfGaugeRef)));
   if (n > 0)
     CK(cudaMemcpyAsync(ctx->d_gxy[s], xy, 2 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
   CK(cudaMemsetAsync(ctx->d_gout[s], 0, 5 * m * sizeof(double), ctx->st));
@@ -1096,10 +1101,13 @@ int geoflood_set_gauges(geoflood_ctx* ctx, int s, const double* xy, int n) {
   S.gxy = ctx->d_gxy[s];
   S.gout = ctx->d_gout[s];
   S.garr = ctx->d_garr[s];
+  S.gref = ctx->d_gref[s];
   int rc = upload_scen(ctx);
   if (rc) return rc;
   ctx->max_gauges_used = 0;
   for (auto& sc : ctx->h_scen) ctx->max_gauges_used = std::max(ctx->max_gauges_used, sc.ngauge);
+  CK(cudaMemsetAsync(ctx->d_gflag, 0, (size_t)ctx->cap, ctx->st));
+  CKL(gf::launch_gauge_refs(ctx->G, view(ctx), ctx->max_gauges_used, ctx->st), "gauge_refs");
   CKL(gf::launch_gauges(ctx->G, view(ctx), 0, ctx->max_gauges_used, ctx->st), "gauges");
   ctx->launches++;
   CK(cudaStreamSynchronize(ctx->st));
@@ -1204,6 +1212,7 @@ int geoflood_autotune(geoflood_ctx* ctx, int reps, int* variant,
   }
   std::copy(saved.begin(), saved.end(), ctx->h_ctl);
   if ((rc = sync_ctl_up(ctx))) return rc;
+  if ((rc = forget_same(ctx))) return rc;
   ctx->variant = best;
   if (variant) *variant = best;
   return 0;
@@ -1213,7 +1222,8 @@ int geoflood_set_variant(geoflood_ctx* ctx, int variant) {
   if (!ctx || variant < 0 || variant >= gf::patch_step_variants(ctx->G.M, ctx->prec))
     return fail(ctx, GEOFLOOD_ERR_ARG, "set_variant: no such variant");
   ctx->variant = variant;
-  return 0;
+  // the per-unit volumes of another variant's layout are not reusable
+  return forget_same(ctx);
 }
 
 int geoflood_launch_count(geoflood_ctx* ctx, long long* launches) {

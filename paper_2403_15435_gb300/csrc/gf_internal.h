@@ -15,6 +15,14 @@ struct GfPatch {
 };
 
 // Per-scenario constants read by the kernels.
+// Where a gauge samples: the finest leaf p holding the point, the tile
+// index c of the lower-left cell of its 2 x 2 bilinear stencil and the
+// weights (ax, ay) of the upper/right cells.  Refreshed after every regrid.
+struct GfGaugeRef {
+  int p, c;
+  double ax, ay;
+};
+
 struct GfScenario {
   double manning_n, eta0;
   float manning_f;    // FP32 copy of manning_n
@@ -27,6 +35,7 @@ struct GfScenario {
   int ngauge;
   int pad;
   const double* gxy;  // [ngauge][2]
+  GfGaugeRef* gref;   // [ngauge]
   double* gout;       // [ngauge][5] latest sample
   double* garr;       // [ngauge] arrival time or -1
 };
@@ -105,6 +114,8 @@ struct GfView {
   // of its CTAs have finished (both back to 0 after the patch is reported)
   unsigned* pwet;
   unsigned* pcnt;
+  // per patch: 1 if a gauge samples in it (or null)
+  unsigned char* gflag;
   int npatch;
   int prec;               // 0 = FP64, 1 = FP32 surface deviation
 };
@@ -131,6 +142,14 @@ struct GfTagOut {
   float logit_thr;
 };
 
+#ifdef __CUDACC__
+// Bilinear weights of the gauges, one form shared by every kernel that samples.
+__device__ __forceinline__ double gf_bilinear(double a00, double a10, double a01,
+                                              double a11, double ax, double ay) {
+  return (1.0 - ay) * ((1.0 - ax) * a00 + ax * a10) + ay * ((1.0 - ax) * a01 + ax * a11);
+}
+#endif
+
 namespace gf {
 int patch_step_variants(int mx, int prec);
 int launch_patch_step_f64(const GfGeom& g, const GfView& v, double* pmass,
@@ -142,19 +161,19 @@ int launch_ctl_begin(GfCtl* ctl, int nscen, double t_target,
 int launch_ghost_fill(const GfGeom& g, const GfView& v, int only_active,
                       void* stream);
 // Ghost cells in regions without a same-level neighbour (which the patch
-// step's push leaves out) for the patches of list[0..n).
+// step's push leaves out), then the physical boundaries of the tile, for the
+// patches of list[0..n).
 int launch_ghost_rest(const GfGeom& g, const GfView& v, const int* list, int n,
                       void* stream);
-// Physical-boundary ghost cells of the patches of list[0..n) (after
-// launch_ghost_rest).
-int launch_ghost_bc(const GfGeom& g, const GfView& v, const int* list, int n,
-                    void* stream);
 int launch_topo(const GfGeom& g, const GfView& v, int first, int count,
                 void* stream);
 int launch_regrid_fill(const GfGeom& g, const GfView& oldv,
                        const GfView& newv, void* stream);
 int launch_tags(const GfGeom& g, const GfView& v, uint8_t* flags,
                 void* stream);
+// Recompute every scenario's gauge stencils (after a regrid or new gauges).
+int launch_gauge_refs(const GfGeom& g, const GfView& v, int max_gauges,
+                      void* stream);
 int launch_gauges(const GfGeom& g, const GfView& v, int only_accepted,
                   int max_gauges, void* stream);
 int launch_mass(const GfGeom& g, const GfView& v, double* pmass,

@@ -60,20 +60,29 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src,
       : "memory");
 }
 
-// Bounded wait on phase 0 of the barrier; returns false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned limit) {
+// Bounded wait for the completion of the barrier's phase with the given
+// parity; returns false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned limit,
+                                          unsigned parity = 0u) {
   for (unsigned it = 0; it < limit; ++it) {
     unsigned done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], "
         "%2;\n selp.u32 %0, 1, 0, p;\n}"
         : "=r"(done)
-        : "r"(smem_addr(bar)), "r"(0u)
+        : "r"(smem_addr(bar)), "r"(parity)
         : "memory");
     if (done) return true;
   }
   return false;
 }
+
+// Phases of the two staging barriers of a CTA that stages one tile after
+// another (persistent variant): the parity each barrier completes next.
+struct TmaPhase {
+  unsigned b0, b1;
+  bool init;
+};
 
 template <typename R>
 __device__ __forceinline__ R warp_max(R v) {
@@ -92,6 +101,109 @@ __device__ __forceinline__ double warp_sum_tree(double v) {
 }
 
 constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+// Writes that follow a new value (v0, v1, v2) of cell (gi, gj) of patch p
+// (patch position (px, py); nxp x nyp patches on its level), other than the
+// cell itself, into the next buffer: the ghost cells of the same-level
+// neighbours (snb, one writer per ghost cell) that copy it, and the
+// physical-boundary ghost cells of p or of those neighbours that mirror it
+// (wall: reflected across the edge with the normal momentum negated;
+// extrapolation: the edge cell copied into both ghost layers).  A boundary
+// ghost whose mirror source is a neighbour's cell is written by that
+// neighbour, so no ghost depends on another CTA's writes in the same launch.
+template <typename R, int MP>
+__device__ __forceinline__ void emit_edge(R* qnext, int p, int px, int py,
+                                          int nxp, int nyp, const int* snb,
+                                          const int* bc, bool push, int gi,
+                                          int gj, R v0, R v1, R v2) {
+  constexpr int TGW = MP + 2 * GF_NG, TG = TGW * TGW;
+  if (gi >= GF_NG && gi < MP - GF_NG && gj >= GF_NG && gj < MP - GF_NG) return;
+  auto target = [&](int q, int qx, int qy, int x, int y, bool self) {
+    R* base = qnext + (size_t)q * 3 * TG;
+    auto put = [&](int a, int b, R su, R sv) {
+      R* d = base + (a + GF_NG) + (b + GF_NG) * TGW;
+      d[0] = v0;
+      d[TG] = su * v1;
+      d[2 * TG] = sv * v2;
+    };
+    int xm[2], ym[2], nx = 0, ny = 0;
+    R fx = R(1), fy = R(1);
+    if (qx == 0 && (x == 0 || x == 1)) {
+      if (bc[0] == 0) { xm[nx++] = -1 - x; fx = R(-1); }
+      else if (x == 0) { xm[nx++] = -1; xm[nx++] = -2; }
+    } else if (qx == nxp - 1 && (x == MP - 1 || x == MP - 2)) {
+      if (bc[1] == 0) { xm[nx++] = 2 * MP - 1 - x; fx = R(-1); }
+      else if (x == MP - 1) { xm[nx++] = MP; xm[nx++] = MP + 1; }
+    }
+    if (qy == 0 && (y == 0 || y == 1)) {
+      if (bc[2] == 0) { ym[ny++] = -1 - y; fy = R(-1); }
+      else if (y == 0) { ym[ny++] = -1; ym[ny++] = -2; }
+    } else if (qy == nyp - 1 && (y == MP - 1 || y == MP - 2)) {
+      if (bc[3] == 0) { ym[ny++] = 2 * MP - 1 - y; fy = R(-1); }
+      else if (y == MP - 1) { ym[ny++] = MP; ym[ny++] = MP + 1; }
+    }
+    if (!self) put(x, y, R(1), R(1));
+    for (int a = 0; a < nx; ++a) put(xm[a], y, fx, R(1));
+    for (int b = 0; b < ny; ++b) put(x, ym[b], R(1), fy);
+    for (int a = 0; a < nx; ++a)
+      for (int b = 0; b < ny; ++b) put(xm[a], ym[b], fx, fy);
+  };
+  target(p, px, py, gi, gj, true);
+  if (!push) return;
+  const int dxs = gi < GF_NG ? -1 : (gi >= MP - GF_NG ? 1 : 0);
+  const int dys = gj < GF_NG ? -1 : (gj >= MP - GF_NG ? 1 : 0);
+  auto nb = [&](int r, int dx, int dy) {
+    const int pn = snb[r];
+    if (pn >= 0) target(pn, px + dx, py + dy, gi - dx * MP, gj - dy * MP, false);
+  };
+  if (dxs != 0) nb(dxs < 0 ? 0 : 1, dxs, 0);
+  if (dys != 0) nb(dys < 0 ? 2 : 3, 0, dys);
+  if (dxs != 0 && dys != 0) nb(4 + (dxs > 0 ? 1 : 0) + (dys > 0 ? 2 : 0), dxs, dys);
+}
+
+// Gauge samples of the state this launch starts from (the previous launch's
+// accepted result, at time C->t), taken from the CTA's staged window: the
+// window covers patch cells [ox - 2, ox + WM + 1]^2; a gauge whose stencil
+// starts in sub-tile (ox, oy) is taken by that window's CTA.  mom = false:
+// the momenta were not staged (a dry tile, where they are zero).
+template <typename R, bool DEV, int MP, int WM>
+__device__ __forceinline__ void sample_gauges(const GfView& V, int scen, const GfCtl* C,
+                                              int p, int ox, int oy, const R* s0,
+                                              const R* shu, const R* shv, const R* sb,
+                                              bool mom) {
+  constexpr int TGW = MP + 2 * GF_NG, WW = WM + 2 * GF_NG;
+  const GfScenario& S = V.scen[scen];
+  for (int g = threadIdx.x; g < S.ngauge; g += blockDim.x) {
+    const GfGaugeRef r = S.gref[g];
+    if (r.p != p) continue;
+    const int i0 = r.c % TGW - GF_NG, j0 = r.c / TGW - GF_NG;
+    const int ic = i0 < 0 ? 0 : i0, jc = j0 < 0 ? 0 : j0;
+    if ((ic / WM) * WM != ox || (jc / WM) * WM != oy) continue;
+    const int c = (i0 - ox + GF_NG) + (j0 - oy + GF_NG) * WW;
+    const int cs[4] = {c, c + 1, c + WW, c + WW + 1};
+    double a[4][4];  // h, hu, hv, h + b per stencil cell
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const double b = (double)sb[cs[k]];
+      const double h = DEV ? (double)s0[cs[k]] - b : (double)s0[cs[k]];
+      a[k][0] = h;
+      a[k][1] = mom ? (double)shu[cs[k]] : 0.0;
+      a[k][2] = mom ? (double)shv[cs[k]] : 0.0;
+      a[k][3] = h + b;
+    }
+    double v[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) v[f] = gf_bilinear(a[0][f], a[1][f], a[2][f], a[3][f], r.ax, r.ay);
+    double* o = S.gout + 5 * g;
+    const double t = C->t;
+    o[0] = t;
+    o[1] = v[0];
+    o[2] = v[1];
+    o[3] = v[2];
+    o[4] = v[3] + (DEV ? S.eta0 : 0.0);
+    if (S.garr[g] < 0.0 && v[0] > 0.01) S.garr[g] = t;
+  }
+}
 
 template <class P, int M>
 struct Layout {
@@ -149,7 +261,8 @@ template <class P, int MP, int M, int NT>
 __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
                                           double* __restrict__ pmass,
                                           unsigned char* smraw, const int p,
-                                          const int sub) {
+                                          const int sub, TmaPhase* tp = nullptr,
+                                          bool* wrote = nullptr) {
   using R = typename P::R;
   constexpr bool DEV = P::DEV;
   using Lo = Layout<P, M>;
@@ -161,6 +274,7 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
   constexpr int RX = (Lo::NCELL + NT - 1) / NT;   // increment cells per thread
 
   const int unit = p * NSUB + sub;  // CTA work unit: volume slot, same[] flag
+  const bool has_gauge = V.gflag != nullptr && V.gflag[p] != 0;
   const int ox = (sub % NS1) * M, oy = (sub / NS1) * M;
   const GfPatch Pt = V.patch[p];
   GfCtl* C = V.ctl + Pt.scen;
@@ -201,12 +315,17 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
   // momenta are fetched only if water has arrived.
   const bool same_in = V.same != nullptr && V.same[unit] != 0;
   bool mom_issued = false;
+  // staging barrier phases (a CTA that stages several tiles keeps them in tp)
+  const bool fresh = tp == nullptr || !tp->init;
+  const unsigned ph0 = tp ? tp->b0 : 0u, ph1 = tp ? tp->b1 : 0u;
   if constexpr (M == MP) {
     // whole patch: its four contiguous fields arrive by 1D TMA bulk copies,
     // surface and bed on bar[0], the momenta on bar[1]
     if (tid == 0) {
-      mbar_init(bar, 1);
-      mbar_init(bar + 1, 1);
+      if (fresh) {
+        mbar_init(bar, 1);
+        mbar_init(bar + 1, 1);
+      }
       mbar_expect_tx(bar, 2u * TT * sizeof(R));
       bulk_g2s(s0, qs, TT * sizeof(R), bar);
       bulk_g2s(sb, bs, TT * sizeof(R), bar);
@@ -217,15 +336,17 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
       }
     }
     mom_issued = !same_in;
+    if (tp) tp->init = true;
     __syncthreads();
     // every wait is bounded; the decision to give up is taken by the whole CTA
-    if (!__syncthreads_and(mbar_wait(bar, GF_SPIN_LIMIT) ? 1 : 0)) {
+    if (!__syncthreads_and(mbar_wait(bar, GF_SPIN_LIMIT, ph0) ? 1 : 0)) {
       if (tid == 0) C->status = -7;  // GEOFLOOD_ERR_TIMEOUT
-      mbar_wait(bar, GF_SPIN_LIMIT);
-      if (mom_issued) mbar_wait(bar + 1, GF_SPIN_LIMIT);
+      mbar_wait(bar, GF_SPIN_LIMIT, ph0);
+      if (mom_issued) mbar_wait(bar + 1, GF_SPIN_LIMIT, ph1);
       __syncthreads();
-      return 0;
+      return -1;
     }
+    if (tp) tp->b0 ^= 1u;
   } else {
     // sub-tile: the (M+4)^2 window of each field, row segments read with
     // consecutive threads on consecutive addresses
@@ -285,20 +406,39 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
   const float dtf = fscal[0], margin = fscal[1];
 
   // Per-cell depth and exact wet flag (deviation form), and whether the
-  // tile holds any wet cell at all.
-  int anywet = 0;
-  for (int k = tid; k < TT; k += NT) {
+  // tile holds any wet cell at all.  A tile whose interior is unchanged and
+  // was dry (same_in) can only have taken water into its ghost cells, so the
+  // interior is examined only if they hold some.
+  constexpr int NRING = TT - M * M;
+  auto ring_cell = [&](int k) {  // k-th ghost cell of the window
+    const int band = 2 * Lo::T;
+    if (k < band) return k;                                 // two bottom rows
+    if (k < 2 * band) return (M + GF_NG) * Lo::T + (k - band);  // two top rows
+    const int r = k - 2 * band, j = r / 4, c = r % 4;
+    return (j + GF_NG) * Lo::T + (c < 2 ? c : M + c);       // side columns
+  };
+  auto examine = [&](int k) -> int {
     if constexpr (DEV) {
       const float w = s0[k], b = sb[k];
       sdep[k] = w - b;
       const bool wt = gfk::wet_dev(w, b, drytol, dtf, margin);
       swet[k] = wt ? 1 : 0;
-      anywet |= wt ? 1 : 0;
+      return wt ? 1 : 0;
     } else {
-      anywet |= s0[k] > rdry ? 1 : 0;
+      return s0[k] > rdry ? 1 : 0;
     }
+  };
+  int anywet = 0;
+  if (same_in) {
+    for (int k = tid; k < NRING; k += NT) anywet |= examine(ring_cell(k));
+    anywet = __syncthreads_or(anywet);
+    if (anywet)
+      for (int k = tid; k < M * M; k += NT)
+        examine((k % M + GF_NG) + (k / M + GF_NG) * Lo::T);
+  } else {
+    for (int k = tid; k < TT; k += NT) anywet |= examine(k);
+    anywet = __syncthreads_or(anywet);
   }
-  anywet = __syncthreads_or(anywet);
   if constexpr (M == MP) {
     // the momenta: requested now if water arrived at a copied dry tile, and
     // waited for whenever they were requested
@@ -310,17 +450,27 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
       }
       mom_issued = true;
     }
-    if (mom_issued && !__syncthreads_and(mbar_wait(bar + 1, GF_SPIN_LIMIT) ? 1 : 0)) {
+    if (mom_issued && !__syncthreads_and(mbar_wait(bar + 1, GF_SPIN_LIMIT, ph1) ? 1 : 0)) {
       if (tid == 0) C->status = -7;  // GEOFLOOD_ERR_TIMEOUT
-      mbar_wait(bar + 1, GF_SPIN_LIMIT);
+      mbar_wait(bar + 1, GF_SPIN_LIMIT, ph1);
       __syncthreads();
-      return 0;
+      return -1;
     }
+    if (mom_issued && tp) tp->b1 ^= 1u;
   }
   // a dry tile whose interior is already the same in both buffers writes
   // nothing (its update is the identity on the surface, zero momenta)
   const bool skip_writes = same_in && !anywet;
   if (V.same != nullptr && tid == 0) V.same[unit] = anywet ? 0 : 1;
+  if (has_gauge && C->accepted)
+    sample_gauges<R, DEV, MP, M>(V, Pt.scen, C, p, ox, oy, s0, shu, shv, sb,
+                                 M != MP || mom_issued);
+  if (skip_writes) {
+    // nothing changes: no writes, no waves, and the tile's volume from the
+    // previous step (pmass[unit]) still holds
+    if (wrote) *wrote = false;
+    return 0;
+  }
   auto wetc = [&](int c) -> bool {
     if constexpr (DEV) return swet[c] != 0;
     else return s0[c] > rdry;
@@ -473,28 +623,14 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
     sweep(std::integral_constant<int, 1>{});
   }
 
-  // New values of a cell near the patch edge also go to the ghost cells of
-  // the same-level neighbours in the next buffer (each such ghost cell has
-  // exactly this one writer; the neighbours read only the current buffer).
+  // New values of a cell near the patch edge also go to the ghost cells that
+  // copy or mirror it (same-level neighbours, physical boundaries).
   R* qnext;
   if constexpr (DEV) qnext = V.qf[cur ^ 1];
   else qnext = V.q[cur ^ 1];
+  const int nxp = G.mi << Pt.level, nyp = G.mj << Pt.level;
   auto push_edge = [&](int gi, int gj, R v0, R v1, R v2) {
-    const int dxs = gi < GF_NG ? -1 : (gi >= MP - GF_NG ? 1 : 0);
-    const int dys = gj < GF_NG ? -1 : (gj >= MP - GF_NG ? 1 : 0);
-    if (!push || (dxs == 0 && dys == 0)) return;
-    auto put = [&](int r, int x, int y) {
-      const int pn = snb[r];
-      if (pn < 0) return;
-      R* d = qnext + (size_t)pn * 3 * TG + (x + GF_NG) + (y + GF_NG) * TGW;
-      d[0] = v0;
-      d[TG] = v1;
-      d[2 * TG] = v2;
-    };
-    if (dxs != 0) put(dxs < 0 ? 0 : 1, gi - dxs * MP, gj);
-    if (dys != 0) put(dys < 0 ? 2 : 3, gi, gj - dys * MP);
-    if (dxs != 0 && dys != 0)
-      put(4 + (dxs > 0 ? 1 : 0) + (dys > 0 ? 2 : 0), gi - dxs * MP, gj - dys * MP);
+    emit_edge<R, MP>(qnext, p, Pt.px, Pt.py, nxp, nyp, snb, G.bc, push, gi, gj, v0, v1, v2);
   };
 
   // ------------------------------------------------ update, friction, out
@@ -636,7 +772,6 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
         const float cx = mx * G.inv_dxf[Pt.level], cy = my * G.inv_dyf[Pt.level];
         const double cm = (double)(cx > cy ? cx : cy);
         atomicMax(&C->cmax_bits, (unsigned long long)__double_as_longlong(cm));
-        atomicAdd(&C->cell_updates, (unsigned long long)(M * M));
         pmass[unit] = vs * G.areal[Pt.level];
       }
     }
@@ -663,7 +798,6 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
       const double cx = mx / dx, cy = my / dy;
       const double cm = cx > cy ? cx : cy;
       atomicMax(&C->cmax_bits, (unsigned long long)__double_as_longlong(cm));
-      atomicAdd(&C->cell_updates, (unsigned long long)(M * M));
       pmass[unit] = vs * (dx * dy);
     }
     if (nclip) {
@@ -743,6 +877,8 @@ __device__ __forceinline__ int whole_tile(const GfGeom& G, const GfView& V,
   }
   anywet = __syncthreads_or(anywet);
   if (anywet) return 1;  // the caller runs the sub-tiles
+  if (V.gflag != nullptr && V.gflag[p] != 0 && C->accepted)
+    sample_gauges<R, DEV, MP, MP>(V, Pt.scen, C, p, 0, 0, s0, s0, s0, sb, false);
   // dry update of the whole patch (skipped when both buffers already agree)
   const float* los = nullptr;
   float* lod = nullptr;
@@ -771,22 +907,8 @@ __device__ __forceinline__ int whole_tile(const GfGeom& G, const GfView& V,
         lod[MP * MP + k] = 0.0f;
         lod[2 * MP * MP + k] = 0.0f;
       }
-      if (push) {
-        const int dxs = i < GF_NG ? -1 : (i >= MP - GF_NG ? 1 : 0);
-        const int dys = j < GF_NG ? -1 : (j >= MP - GF_NG ? 1 : 0);
-        auto put = [&](int r, int x, int y) {
-          const int pn = snb[r];
-          if (pn < 0) return;
-          R* d = qnext + (size_t)pn * 3 * TG + (x + GF_NG) + (y + GF_NG) * TGW;
-          d[0] = w;
-          d[TG] = R(0);
-          d[2 * TG] = R(0);
-        };
-        if (dxs != 0) put(dxs < 0 ? 0 : 1, i - dxs * MP, j);
-        if (dys != 0) put(dys < 0 ? 2 : 3, i, j - dys * MP);
-        if (dxs != 0 && dys != 0)
-          put(4 + (dxs > 0 ? 1 : 0) + (dys > 0 ? 2 : 0), i - dxs * MP, j - dys * MP);
-      }
+      emit_edge<R, MP>(qnext, p, Pt.px, Pt.py, G.mi << Pt.level, G.mj << Pt.level, snb, G.bc,
+                       push, i, j, w, R(0), R(0));
     }
   }
   // per-quadrant volumes: FP32 (deviation form) or FP64 partials per warp,
@@ -807,7 +929,6 @@ __device__ __forceinline__ int whole_tile(const GfGeom& G, const GfView& V,
     pmass[p * NSUB + tid] = vs * G.areal[Pt.level];
     if (V.same != nullptr) V.same[p * NSUB + tid] = 1;
   }
-  if (tid == 0) atomicAdd(&C->cell_updates, (unsigned long long)(MP * MP));
   return 0;
 }
 
@@ -818,11 +939,14 @@ __device__ __forceinline__ int whole_tile(const GfGeom& G, const GfView& V,
 // the next dt = cfl_desired / cmax, clipped to land on t_target.
 template <int NT>
 __device__ void step_finish(const GfGeom& G, const GfView& V,
-                            const double* pmass, double* red, int nsub) {
+                            const double* pmass, double* red, int nsub,
+                            int cells_per_patch, bool wrote = true) {
   __shared__ int last;
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
+    // a CTA that wrote volumes makes them visible before it counts itself
+    // done; one that wrote nothing the controller reads needs no fence
+    if (wrote) __threadfence();
     const unsigned t = atomicAdd(V.done, 1u);
     last = t == gridDim.x - 1;
   }
@@ -841,6 +965,9 @@ __device__ void step_finish(const GfGeom& G, const GfView& V,
       continue;
     }
     const int off = V.scen[s].poff * nsub, n = V.scen[s].pcount * nsub;
+    if (tid == 0)
+      C->cell_updates = C->cell_updates +
+                        (unsigned long long)V.scen[s].pcount * (unsigned long long)cells_per_patch;
     double v = 0.0;
     for (int k = tid; k < n; k += NT) v += pm[off + k];
     v = warp_sum_tree(v);
@@ -972,7 +1099,7 @@ __global__ void __launch_bounds__(NT, MINB)
   }
   if (V.done)
     step_finish<NT>(G, V, pmass,
-                    reinterpret_cast<double*>(smraw + Layout<P, M>::OFF_RED), NSUB);
+                    reinterpret_cast<double*>(smraw + Layout<P, M>::OFF_RED), NSUB, MP * MP);
 }
 
 template <class P, int MP, int M, int NT, int MINB>
@@ -989,7 +1116,9 @@ __global__ void __launch_bounds__(NT, MINB)
   const int p = sched ? (par ? V.ord1 : V.ord0)[slot] : slot;
   const GfPatch Pt = V.patch[p];
   int wet = 0;
-  if (V.ctl[Pt.scen].active) wet = patch_body<P, MP, M, NT>(G, V, pmass, smraw, p, sub);
+  bool wrote = true;
+  if (V.ctl[Pt.scen].active) wet = patch_body<P, MP, M, NT>(G, V, pmass, smraw, p, sub, nullptr, &wrote);
+  else wrote = false;
   if (sched && sub == 0 && threadIdx.x == 0) {
     int* nxt = par ? V.ord0 : V.ord1;
     if (wet) nxt[atomicAdd(V.sched + 1, 1u)] = p;
@@ -998,7 +1127,7 @@ __global__ void __launch_bounds__(NT, MINB)
   if (V.done)
     step_finish<NT>(G, V, pmass,
                     reinterpret_cast<double*>(smraw + Layout<P, M>::OFF_RED),
-                    NSUB);
+                    NSUB, MP * MP, wrote);
 }
 
 // Launch the patch step on every patch: MP x MP patches, M x M sub-tiles
