@@ -432,9 +432,11 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
   if (same_in) {
     for (int k = tid; k < NRING; k += NT) anywet |= examine(ring_cell(k));
     anywet = __syncthreads_or(anywet);
-    if (anywet)
+    if (anywet) {
       for (int k = tid; k < M * M; k += NT)
         examine((k % M + GF_NG) + (k / M + GF_NG) * Lo::T);
+      __syncthreads();  // the sweeps read every thread's depths and flags
+    }
   } else {
     for (int k = tid; k < TT; k += NT) anywet |= examine(k);
     anywet = __syncthreads_or(anywet);
