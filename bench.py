@@ -27,9 +27,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 # DRAM bytes (read + write) of one patch_step launch on this workload, from
-# the ncu capture summarised in profiles/ (None when the kernel has changed
-# since the capture).
-TRAFFIC_PER_LAUNCH_FP64 = None
+# the ncu captures summarised in profiles/ (launch 401 of the run, the second
+# warm-up run; ncu flushes the caches before each pass, so these are
+# cold-cache figures).  None when the kernel has changed since the capture.
+TRAFFIC_PER_LAUNCH_FP64 = 23416576
 N_CELLS = 1024
 PATCH = 32
 T_END = 60.0
@@ -138,7 +139,7 @@ def measured_peaks():
 BYTES_PER_CELL_FP32 = 52
 OPS_PER_WET_CELL_FP32 = 500
 FP32_LANES_PER_SM = 128
-TRAFFIC_PER_LAUNCH_FP32 = None
+TRAFFIC_PER_LAUNCH_FP32 = 12843264
 # Algorithmic work of the FP64 patch step, counted operation by operation
 # from the scheme: a wet cell update takes two edge solves (74 operations
 # each), two limited edge fluxes (81), two increments (9), two transverse
@@ -246,6 +247,84 @@ def measure(prec, args, dev, stream, world, local, gauges):
                 gauges=gauge_out, arrival=arrival, final=final)
 
 
+AMR_T_END = 90.0
+AMR_WORKLOAD = ("V-valley 2 km x 1 km, 4x2 blocks of 32x32 patches, levels 0-3 (finest dx 1.95 m), "
+                "12 m reservoir, full breach at x = 350 m, n = 0.033, t 0->90 s, 8 gauges")
+CNN_SCALE = (4.0, 8.0, 8.0, 4.0)
+
+
+def measure_amr(stream):
+    """The method with quadtree refinement: plain FP64 with the paper's
+    regrid interval of 4 steps against the FP32 deviation form with learned
+    tags and a regrid interval of 16 steps (the plain criterion checked every
+    4 steps, regridding at once on a miss).  The network is trained first, on
+    the plain criterion's flags from another valley.  Times are wall clock of
+    the whole driver loop (steps, checks, regrids, host quadtree)."""
+    import numpy as np
+    import torch
+    from paper_2403_15435_gb300 import geoflood, inputs
+
+    t0 = time.perf_counter()
+    tr = inputs.valley_2km(seed=inputs.SEED_BASE + 40, depth=10.0, breach_x=300.0,
+                           precision=1)
+    f = geoflood.Forest(tr.cfg, tr.dem, stream=stream.cuda_stream)
+    f.set_state(tr.ic)
+    f.cnn_set_scale(CNN_SCALE)
+    f.cnn_dataset(60000)
+    st = f.advance(60.0, regrid_interval=16, check_interval=4, collect=True)
+    _, y = f.cnn_dataset_read(0, st["samples"])
+    npos = int(y.sum())
+    pw = float(np.clip((len(y) - npos) / max(npos, 1), 1.0, 20.0))
+    f.cnn_set_params(inputs.cnn_init(3))
+    loss = f.cnn_train(40, 64, lr=2e-3, pos_weight=pw, seed=7)
+    prm = f.cnn_get_params()
+    f.close()
+    train = {"samples": int(len(y)), "positives": npos, "epochs": 40,
+             "loss_first": float(loss[0]), "loss_last": float(loss[-1]),
+             "seconds": time.perf_counter() - t0}
+
+    def run(prec, learned, regrid):
+        prob = inputs.valley_2km(precision=prec)
+        res = None
+        for rep in range(2):  # the first run instantiates graphs and warms up
+            g = geoflood.Forest(prob.cfg, prob.dem, stream=stream.cuda_stream)
+            g.set_state(prob.ic)
+            g.cnn_set_scale(CNN_SCALE)
+            if learned:
+                g.cnn_set_params(prm)
+                g.set_tagger(geoflood.TAGGER_LEARNED, 0.5)
+            g.set_gauges(prob.gauges)
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            s = g.advance(AMR_T_END, regrid_interval=regrid, check_interval=4,
+                          regrid_on_miss=learned)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - a
+            out, arr = g.gauges()
+            cells = s["patch_steps"] * prob.cfg.mx * prob.cfg.mx
+            res = {"value": cells / wall, "unit": "cell-updates/s", "wall_s": wall,
+                   "steps": s["steps"], "regrids": s["regrids"],
+                   "regrids_on_miss": s["miss_regrids"], "criterion_misses": s["misses"],
+                   "cell_updates": cells, "gauge_h": out[:, 1].copy(), "arrival": arr.copy()}
+            g.close()
+        return res
+
+    plain = run(0, False, 4)
+    learned = run(1, True, 16)
+    both = (plain["arrival"] >= 0) & (learned["arrival"] >= 0)
+    err = {"gauge_depth_max_abs_m": float(np.abs(learned["gauge_h"] - plain["gauge_h"]).max()),
+           "arrival_max_abs_s": float(np.abs(learned["arrival"] - plain["arrival"])[both].max())
+           if both.any() else None,
+           "gauges_reached": [int((plain["arrival"] >= 0).sum()), int((learned["arrival"] >= 0).sum())]}
+    for r in (plain, learned):
+        r.pop("gauge_h")
+        r.pop("arrival")
+    return {"workload": AMR_WORKLOAD, "plain_fp64_regrid4": plain,
+            "fp32_learned_regrid16": learned, "speedup": learned["value"] / plain["value"],
+            "error_vs_plain_fp64": err, "training": train,
+            "timing": "wall clock around the whole driver loop, second of two runs"}
+
+
 def roofline(r, prec, peaks):
     """Roofline of the patch_step kernel from the live per-launch events:
     HBM side from the algorithmic bytes per cell update, ALU side from the
@@ -312,6 +391,7 @@ def run_ours(args):
                                              np.abs(r32["final"][2] - r64["final"][2]).max())),
            "gauge_depth_max_abs_m": float(np.abs(r32["gauges"][:, 1] - r64["gauges"][:, 1]).max()),
            "arrival_max_abs_s": float(np.abs(r32["arrival"] - r64["arrival"]).max())}
+    amr = measure_amr(stream)
     cpu = cpu_baseline()
     line = {
         "metric": "cell-updates/s", "value": r32["value"], "unit": "cell-updates/s",
@@ -337,6 +417,7 @@ def run_ours(args):
                  "accepted_steps_per_run": r64["steps"][0], "roofline": roof64,
                  "e2e": r64["e2e"], "gpu_launches": r64["launches"], "clocks": r64["clocks"]},
         "fp32_vs_fp64_error": err,
+        "amr_valley": amr,
     }
     if rank == 0:
         print(json.dumps(line))

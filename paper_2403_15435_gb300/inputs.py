@@ -238,6 +238,35 @@ def v_valley(mi: int = 16, mj: int = 8, patch: int = 32, minlevel: int = 2,
     return Problem("v_valley", cfg, dem, ic, 600.0, gauges)
 
 
+def valley_2km(seed: int = SEED_BASE + 41, depth: float = 12.0,
+               breach_x: float = 350.0, patch: int = 32,
+               precision: int = 0) -> Problem:
+    """A 2 km x 1 km V-valley (the 4 km x 2 km valley at half the size):
+    4 x 2 blocks of 32 x 32 patches (8 x 4 of 16 x 16) on levels 0..3, so the
+    finest cells are 1.95 m; reservoir at `depth` above the thalweg upstream
+    of `breach_x`, refined to level 1 there; 8 gauges."""
+    scale = 32 // patch
+    prob = v_valley(mi=4 * scale, mj=2 * scale, patch=patch, minlevel=0, maxlevel=3,
+                    seed=seed, dem_spacing=8.0, depth=depth, breach_x=breach_x,
+                    n_gauges=8, Lx=2000.0, Ly=1000.0)
+    prob.cfg.src_level = 1
+    prob.cfg.precision = precision
+    return prob
+
+
+def cnn_init(seed: int, nch: int = 16, taps: int = 9) -> np.ndarray:
+    """Seeded initial parameters of the refinement predictor in its layout
+    (three layers of W[nch][taps * nch] then b[nch], then wh[nch], bh):
+    He-normal weights, zero biases, a small normal head."""
+    rng = np.random.default_rng(seed)
+    k = taps * nch
+    parts = []
+    for _ in range(3):
+        parts += [rng.normal(0.0, math.sqrt(2.0 / k), nch * k), rng.normal(0.0, 0.05, nch)]
+    parts += [rng.normal(0.0, 0.25, nch), np.array([-0.5])]
+    return np.concatenate(parts).astype(np.float32)
+
+
 def cell_centres(cfg: Config, levels: Sequence[int], pxs: Sequence[int],
                  pys: Sequence[int]):
     """Cell centres [npatch][mx][mx] of a patch list (row index j, column i)."""
