@@ -394,8 +394,9 @@ __device__ double dem_average(const GfScenario& S, double xa, double xb,
 }
 
 template <typename T>
-__global__ void k_topo(const __grid_constant__ GfGeom G, const __grid_constant__ GfView V, int first) {
-  const int p = first + blockIdx.x;
+__global__ void k_topo(const __grid_constant__ GfGeom G, const __grid_constant__ GfView V, int first,
+                       const int* list) {
+  const int p = list ? list[blockIdx.x] : first + blockIdx.x;
   const GfPatch P = V.patch[p];
   Geo<T> e(G, V);
   const int M = G.M, T_ = G.T, TT = T_ * T_;
@@ -427,8 +428,8 @@ __global__ void k_topo(const __grid_constant__ GfGeom G, const __grid_constant__
 template <typename T>
 __global__ void k_regrid_fill(const __grid_constant__ GfGeom G, const __grid_constant__ GfView O,
                               const __grid_constant__ GfView N,
-                              int* errflag) {
-  const int p = blockIdx.x;
+                              int* errflag, const int* list) {
+  const int p = list ? list[blockIdx.x] : blockIdx.x;
   const GfPatch P = N.patch[p];
   Geo<T> eo(G, O), en(G, N);
   const int M = G.M, T_ = G.T;
@@ -452,6 +453,35 @@ __global__ void k_regrid_fill(const __grid_constant__ GfGeom G, const __grid_con
     }
   }
   if (err && errflag) *errflag = 1;
+}
+
+// Regrid transfer of a patch that is a leaf of both forests: its bed, state
+// (ghosts included) and compensation terms are copied from its old slot;
+// pairs[k] = (new index, old index).
+template <typename T>
+__global__ void k_regrid_keep(const __grid_constant__ GfGeom G, const __grid_constant__ GfView O,
+                              const __grid_constant__ GfView N, const int2* pairs) {
+  const int2 pr = pairs[blockIdx.x];
+  const int pn = pr.x, po = pr.y;
+  const GfPatch P = N.patch[pn];
+  Geo<T> eo(G, O), en(G, N);
+  const int M = G.M, TT = G.T * G.T;
+  const int src = O.ctl[P.scen].cur, dst = 1 - src;
+  const T* qo = eo.qp(po, src);
+  T* qn = en.qp(pn, dst);
+  const T* bo = eo.bp(po);
+  T* bn = en.bp(pn);
+  for (int k = threadIdx.x; k < TT; k += blockDim.x) {
+    bn[k] = bo[k];
+    qn[k] = qo[k];
+    qn[TT + k] = qo[TT + k];
+    qn[2 * TT + k] = qo[2 * TT + k];
+  }
+  if constexpr (Geo<T>::DEV) {
+    const float* lo = O.lof[src] + (size_t)po * 3 * M * M;
+    float* ln = N.lof[dst] + (size_t)pn * 3 * M * M;
+    for (int k = threadIdx.x; k < 3 * M * M; k += blockDim.x) ln[k] = lo[k];
+  }
 }
 
 // Plain tagger (Sec. 4.1 criteria 1, 3, 4; Sec. 6.4).
@@ -803,20 +833,31 @@ int launch_ghost_rest(const GfGeom& g, const GfView& v, const int* list, int n,
 
 
 int launch_topo(const GfGeom& g, const GfView& v, int first, int count,
-                void* stream) {
+                void* stream, const int* list) {
   if (count <= 0) return 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (v.prec) k_topo<float><<<count, 128, 0, st>>>(g, v, first);
-  else k_topo<double><<<count, 128, 0, st>>>(g, v, first);
+  if (v.prec) k_topo<float><<<count, 128, 0, st>>>(g, v, first, list);
+  else k_topo<double><<<count, 128, 0, st>>>(g, v, first, list);
   return ok();
 }
 
 int launch_regrid_fill(const GfGeom& g, const GfView& oldv, const GfView& newv,
-                       void* stream) {
-  if (newv.npatch <= 0) return 0;
+                       void* stream, const int* list, int count) {
+  const int n = list ? count : newv.npatch;
+  if (n <= 0) return 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (newv.prec) k_regrid_fill<float><<<newv.npatch, 256, 0, st>>>(g, oldv, newv, g_errflag);
-  else k_regrid_fill<double><<<newv.npatch, 256, 0, st>>>(g, oldv, newv, g_errflag);
+  if (newv.prec) k_regrid_fill<float><<<n, 256, 0, st>>>(g, oldv, newv, g_errflag, list);
+  else k_regrid_fill<double><<<n, 256, 0, st>>>(g, oldv, newv, g_errflag, list);
+  return ok();
+}
+
+int launch_regrid_keep(const GfGeom& g, const GfView& oldv, const GfView& newv,
+                       const void* pairs, int count, void* stream) {
+  if (count <= 0) return 0;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int2* pr = static_cast<const int2*>(pairs);
+  if (newv.prec) k_regrid_keep<float><<<count, 256, 0, st>>>(g, oldv, newv, pr);
+  else k_regrid_keep<double><<<count, 256, 0, st>>>(g, oldv, newv, pr);
   return ok();
 }
 

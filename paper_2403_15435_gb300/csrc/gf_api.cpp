@@ -11,6 +11,7 @@
 #include <cstring>
 #include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "gf_forest.h"
@@ -86,6 +87,8 @@ struct geoflood_ctx {
   unsigned char* d_gflag = nullptr;   // per patch: holds a gauge
   unsigned* d_pwet = nullptr;         // adaptive variant: per-patch flags
   unsigned* d_pcnt = nullptr;
+  int* d_rlist = nullptr;   // regrid: new slots to compute
+  int* d_rpairs = nullptr;  // regrid: (new, old) slots to copy
   int* d_glist[2] = {nullptr, nullptr};  // patches with a coarser/finer neighbour
   int nglist[2] = {0, 0};
   bool own_stream = false;
@@ -560,6 +563,8 @@ int geoflood_init_forest(const geoflood_config* cfg, void* stream,
   okk &= alloc((void**)&ctx->d_pwet, cap * sizeof(unsigned));
   okk &= alloc((void**)&ctx->d_gflag, cap);
   okk &= alloc((void**)&ctx->d_pcnt, cap * sizeof(unsigned));
+  okk &= alloc((void**)&ctx->d_rlist, cap * sizeof(int));
+  okk &= alloc((void**)&ctx->d_rpairs, cap * 2 * sizeof(int));
   okk &= alloc((void**)&ctx->d_glist[0], cap * sizeof(int));
   okk &= alloc((void**)&ctx->d_glist[1], cap * sizeof(int));
   okk &= alloc((void**)&ctx->d_lut[0], (size_t)ctx->nscen * G.lut_per_scen * sizeof(int));
@@ -644,6 +649,8 @@ void geoflood_destroy(geoflood_ctx* ctx) {
   cudaFree(ctx->d_pwet);
   cudaFree(ctx->d_gflag);
   cudaFree(ctx->d_pcnt);
+  cudaFree(ctx->d_rlist);
+  cudaFree(ctx->d_rpairs);
   cudaFree(ctx->d_glist[0]);
   cudaFree(ctx->d_glist[1]);
   cudaFree(ctx->d_scen);
@@ -1027,9 +1034,32 @@ int geoflood_regrid(geoflood_ctx* ctx) {
   CK(cudaStreamSynchronize(ctx->st));
   std::vector<std::vector<gf::Leaf>> lv(ctx->nscen);
   size_t total = 0;
+  // leaves present in both forests keep their data (copied from the old slot)
+  std::map<std::tuple<int, int, int, int>, int> old_index;
   for (int s = 0; s < ctx->nscen; ++s) {
+    const std::vector<gf::Leaf> old = ctx->forests[s].leaves();
+    for (size_t k = 0; k < old.size(); ++k)
+      old_index[std::make_tuple(s, old[k].level, old[k].px, old[k].py)] =
+          ctx->h_scen[s].poff + (int)k;
     lv[s] = ctx->forests[s].regrid(flags.data() + ctx->h_scen[s].poff);
     total += lv[s].size();
+  }
+  std::vector<int> fresh;         // new slots computed from the old forest
+  std::vector<int> keep;          // (new, old) slot pairs
+  {
+    int off = 0;
+    for (int s = 0; s < ctx->nscen; ++s) {
+      for (size_t k = 0; k < lv[s].size(); ++k) {
+        auto it = old_index.find(std::make_tuple(s, lv[s][k].level, lv[s][k].px, lv[s][k].py));
+        if (it == old_index.end()) {
+          fresh.push_back(off + (int)k);
+        } else {
+          keep.push_back(off + (int)k);
+          keep.push_back(it->second);
+        }
+      }
+      off += (int)lv[s].size();
+    }
   }
   if ((long long)total > ctx->cap)
     return fail(ctx, GEOFLOOD_ERR_CAPACITY,
@@ -1045,10 +1075,18 @@ int geoflood_regrid(geoflood_ctx* ctx) {
   }
   GfView newv = view(ctx, nt, nb);
   newv.npatch = (int)total;
-  CKL(gf::launch_topo(ctx->G, newv, 0, (int)total, ctx->st), "topo");
+  const int nfresh = (int)fresh.size(), nkeep = (int)keep.size() / 2;
+  if (nfresh)
+    CK(cudaMemcpyAsync(ctx->d_rlist, fresh.data(), sizeof(int) * fresh.size(),
+                       cudaMemcpyHostToDevice, ctx->st));
+  if (nkeep)
+    CK(cudaMemcpyAsync(ctx->d_rpairs, keep.data(), sizeof(int) * keep.size(),
+                       cudaMemcpyHostToDevice, ctx->st));
+  CKL(gf::launch_topo(ctx->G, newv, 0, nfresh, ctx->st, ctx->d_rlist), "topo");
   gf::set_errflag(ctx->d_err);
-  CKL(gf::launch_regrid_fill(ctx->G, oldv, newv, ctx->st), "regrid_fill");
-  ctx->launches += 2;
+  CKL(gf::launch_regrid_fill(ctx->G, oldv, newv, ctx->st, ctx->d_rlist, nfresh), "regrid_fill");
+  CKL(gf::launch_regrid_keep(ctx->G, oldv, newv, ctx->d_rpairs, nkeep, ctx->st), "regrid_keep");
+  ctx->launches += 3;
   CK(cudaStreamSynchronize(ctx->st));
   for (int s = 0; s < ctx->nscen; ++s) {
     ctx->h_ctl[s].cur ^= 1;

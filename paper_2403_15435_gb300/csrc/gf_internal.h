@@ -165,10 +165,15 @@ int launch_ghost_fill(const GfGeom& g, const GfView& v, int only_active,
 // patches of list[0..n).
 int launch_ghost_rest(const GfGeom& g, const GfView& v, const int* list, int n,
                       void* stream);
+// Beds of patches [first, first + count), or of list[0..count) if list.
 int launch_topo(const GfGeom& g, const GfView& v, int first, int count,
-                void* stream);
-int launch_regrid_fill(const GfGeom& g, const GfView& oldv,
-                       const GfView& newv, void* stream);
+                void* stream, const int* list = nullptr);
+// Regrid transfer into the new forest: every patch, or list[0..count).
+int launch_regrid_fill(const GfGeom& g, const GfView& oldv, const GfView& newv,
+                       void* stream, const int* list = nullptr, int count = 0);
+// Copy of the patches present in both forests: pairs (int2: new, old).
+int launch_regrid_keep(const GfGeom& g, const GfView& oldv, const GfView& newv,
+                       const void* pairs, int count, void* stream);
 int launch_tags(const GfGeom& g, const GfView& v, uint8_t* flags,
                 void* stream);
 // Recompute every scenario's gauge stencils (after a regrid or new gauges).

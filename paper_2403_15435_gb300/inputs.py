@@ -208,13 +208,15 @@ def v_valley(mi: int = 16, mj: int = 8, patch: int = 32, minlevel: int = 2,
              maxlevel: int = 4, seed: int = SEED_BASE + 2,
              dem_spacing: float = 2.0, depth: float = 20.0,
              breach_x: float = 500.0, manning_n: float = 0.033,
-             n_gauges: int = 16, Lx: float = 4000.0, Ly: float = 2000.0
-             ) -> Problem:
+             n_gauges: int = 16, Lx: float = 4000.0, Ly: float = 2000.0,
+             breach_width: Optional[float] = None) -> Problem:
     """Synthetic V-valley (4 km x 2 km): side slope 0.05, down-valley slope
     0.005, seeded fractal noise of 0.5 m amplitude; reservoir upstream of
     x = breach_x filled to `depth` above the thalweg at the breach, dry
-    downstream, instantaneous full breach; n = 0.033; 16 seeded gauges along
-    the thalweg and banks; regrid every 4 steps."""
+    downstream, instantaneous full breach (or, with breach_width, a dam 5 m
+    above the reservoir surface along x = breach_x with a breach of that
+    width centred on the thalweg); n = 0.033; 16 seeded gauges along the
+    thalweg and banks; regrid every 4 steps."""
     cfg = Config(mi=mi, mj=mj, mx=patch, minlevel=minlevel, maxlevel=maxlevel,
                  xupper=Lx, yupper=Ly, drytol=1e-4, manning_n=manning_n,
                  dt_initial=0.05, tag_depth=1e-4, tag_speed=0.01,
@@ -223,8 +225,12 @@ def v_valley(mi: int = 16, mj: int = 8, patch: int = 32, minlevel: int = 2,
     X, Y = node_grid(cfg, dem_spacing)
     noise = value_noise(X, Y, seed, 6, 800.0)
     z = 0.05 * np.abs(Y - 0.5 * Ly) + 0.005 * (Lx - X) + 0.5 * noise
-    dem = Dem(z, 0.0, 0.0, dem_spacing, dem_spacing)
     surface = 0.005 * (Lx - breach_x) + depth
+    if breach_width is not None:
+        dam = (X >= breach_x) & (X < breach_x + 4 * dem_spacing) & \
+            (np.abs(Y - 0.5 * Ly) >= 0.5 * breach_width)
+        z = np.where(dam, np.maximum(z, surface + 5.0), z)
+    dem = Dem(z, 0.0, 0.0, dem_spacing, dem_spacing)
     cfg.eta0 = surface
 
     def ic(x, y, b):
@@ -252,6 +258,26 @@ def valley_2km(seed: int = SEED_BASE + 41, depth: float = 12.0,
     prob.cfg.src_level = 1
     prob.cfg.precision = precision
     return prob
+
+
+def valley_ensemble(n: int, seed: int = SEED_BASE + 4, precision: int = 1):
+    """n scenarios of the 2 km x 1 km valley for one batched context:
+    breach width U[50, 400] m, reservoir depth U[10, 30] m, Manning n
+    U[0.02, 0.05], terrain noise seeded per scenario; one forest
+    configuration (from the first scenario).  Returns the problems."""
+    rng = np.random.default_rng(seed)
+    probs = []
+    for k in range(n):
+        prob = v_valley(mi=4, mj=2, patch=32, minlevel=0, maxlevel=3,
+                        seed=seed + 100 + k, dem_spacing=8.0,
+                        depth=float(rng.uniform(10.0, 30.0)), breach_x=350.0,
+                        manning_n=float(rng.uniform(0.02, 0.05)), n_gauges=8,
+                        Lx=2000.0, Ly=1000.0,
+                        breach_width=float(rng.uniform(50.0, 400.0)))
+        prob.cfg.src_level = 1
+        prob.cfg.precision = precision
+        probs.append(prob)
+    return probs
 
 
 def cnn_init(seed: int, nch: int = 16, taps: int = 9) -> np.ndarray:
