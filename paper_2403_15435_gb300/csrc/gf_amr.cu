@@ -497,28 +497,64 @@ __global__ void k_tags(const __grid_constant__ GfGeom G, const __grid_constant__
   const double dx = e.dx(P.level), dy = e.dy(P.level);
   // surfaces are compared with eta0; the deviation form stores them relative
   const double eref = Geo<T>::DEV ? 0.0 : S.eta0;
-  int m = 0;
-  for (int k = threadIdx.x; k < M * M; k += blockDim.x) {
-    const int i = k % M, j = k / M;
-    const int c = e.tix(i, j);
-    double v4[4];
-    e.load(p, cur, c, v4);
-    const double h = v4[0];
-    int r = 0;
-    if (h > G.tag_depth) {
-      const double u = v4[1] / h, v = v4[2] / h;
-      const double sp = sqrt(u * u + v * v);
-      const double eta = h + v4[3];
-      if (sp > G.tag_speed || fabs(eta - eref) > G.tag_deta) r = 2;
+  // the source box against the patch's first and last cell centres (the
+  // centres grow with the index, so the per-cell test is needed only for a
+  // patch that the box edge crosses)
+  auto xcen = [&](int i) { return G.xlower + ((double)((long long)P.px * M + i) + 0.5) * dx; };
+  auto ycen = [&](int j) { return G.ylower + ((double)((long long)P.py * M + j) + 0.5) * dy; };
+  const double x0 = xcen(0), x1 = xcen(M - 1), y0 = ycen(0), y1 = ycen(M - 1);
+  const bool box_none = x1 < G.src_box[0] || x0 > G.src_box[1] || y1 < G.src_box[2] ||
+                        y0 > G.src_box[3];
+  const bool box_all = x0 >= G.src_box[0] && x1 <= G.src_box[1] && y0 >= G.src_box[2] &&
+                       y1 <= G.src_box[3];
+  const int rbox = P.level < G.src_level ? 2 : 1;  // a cell in the box asks this
+  int m = box_all ? rbox : 0;
+  if (m < 2) {
+    // cells in rounds of blockDim; stop once any cell asks for refinement
+    for (int k0 = 0; k0 < M * M; k0 += blockDim.x) {
+      const int k = k0 + threadIdx.x;
+      if (k < M * M) {
+        const int i = k % M, j = k / M;
+        const int c = e.tix(i, j);
+        int r = 0;
+        if constexpr (Geo<T>::DEV) {
+          // deviation form in FP32: depth w - b, speed test without a
+          // division, surface deviation |w| (one mismatch with the FP64
+          // criterion is possible at a threshold tie; counted in the tests)
+          const float* q = e.qp(p, cur);
+          const int TT = G.T * G.T;
+          const float w = q[c], b = e.bp(p)[c];
+          const float h = w - b;
+          if (h > G.tag_depthf) {
+            const float hu = q[TT + c], hv = q[2 * TT + c], st = G.tag_speedf * h;
+            if (hu * hu + hv * hv > st * st || fabsf(w) > G.tag_detaf) r = 2;
+          }
+        } else {
+          double v4[4];
+          e.load(p, cur, c, v4);
+          const double h = v4[0];
+          if (h > G.tag_depth) {
+            const double u = v4[1] / h, v = v4[2] / h;
+            const double sp = sqrt(u * u + v * v);
+            const double eta = h + v4[3];
+            if (sp > G.tag_speed || fabs(eta - eref) > G.tag_deta) r = 2;
+          }
+        }
+        if (!box_none && !box_all) {
+          const double xc = xcen(i), yc = ycen(j);
+          if (xc >= G.src_box[0] && xc <= G.src_box[1] && yc >= G.src_box[2] &&
+              yc <= G.src_box[3]) {
+            if (rbox == 2) r = 2;
+            else if (r < 1) r = 1;
+          }
+        }
+        m = r > m ? r : m;
+      }
+      if (__syncthreads_or(m == 2)) {
+        m = 2;
+        break;
+      }
     }
-    const double xc = G.xlower + ((double)((long long)P.px * M + i) + 0.5) * dx;
-    const double yc = G.ylower + ((double)((long long)P.py * M + j) + 0.5) * dy;
-    if (xc >= G.src_box[0] && xc <= G.src_box[1] && yc >= G.src_box[2] &&
-        yc <= G.src_box[3]) {
-      if (P.level < G.src_level) r = 2;
-      else if (r < 1) r = 1;
-    }
-    m = r > m ? r : m;
   }
   m = __reduce_max_sync(0xffffffffu, m);
   __shared__ int wm[32];

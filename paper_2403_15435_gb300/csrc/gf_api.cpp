@@ -529,6 +529,9 @@ int geoflood_init_forest(const geoflood_config* cfg, void* stream,
   G.gf = (float)c.g;
   G.drytolf = (float)c.drytol;
   G.marginf = (float)(c.drytol * 0x1p-20);
+  G.tag_depthf = (float)c.tag_depth;
+  G.tag_speedf = (float)c.tag_speed;
+  G.tag_detaf = (float)c.tag_deta;
 
   const size_t TT = (size_t)G.T * G.T;
   const size_t cap = (size_t)ctx->cap;

@@ -79,6 +79,7 @@ struct GfGeom {
   double dxl[GF_MAXLEV + 1], dyl[GF_MAXLEV + 1], areal[GF_MAXLEV + 1];
   float inv_dxf[GF_MAXLEV + 1], inv_dyf[GF_MAXLEV + 1];
   float gf, drytolf, marginf;
+  float tag_depthf, tag_speedf, tag_detaf;
 };
 
 // Everything a kernel needs to find patches and their data.
