@@ -322,6 +322,80 @@ __global__ void k_ghost_fill(const __grid_constant__ GfGeom G, const __grid_cons
   tile_bc<T>(e, P, q, nullptr, 0);
 }
 
+// Ghost cells of one patch region without a same-level neighbour (a finer
+// or coarser leaf covers it), one thread per cell: regs[k] = patch * 8 +
+// region (left, right, bottom, top: 2 x M cells; corners: 2 x 2), filled
+// from the leaves by the ghost operators, then copied to the physical-boundary
+// ghost cells that mirror it.  Runs after each accepted step; the same-level
+// regions and the other boundary ghosts are written by the patch step.
+template <typename T>
+__global__ void k_ghost_other(const __grid_constant__ GfGeom G, const __grid_constant__ GfView V,
+                              const int* regs, int nreg, int* errflag) {
+  const int M = G.M, T_ = G.T, TT = T_ * T_;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)nreg * 2 * M) return;
+  const int code = regs[idx / (2 * M)];
+  const int k = (int)(idx % (2 * M));
+  const int p = code >> 3, r = code & 7;
+  int i, j;
+  if (r < 4) {
+    const int a = k % 2, b = k / 2;
+    if (r == 0) { i = -2 + a; j = b; }
+    else if (r == 1) { i = M + a; j = b; }
+    else if (r == 2) { i = b; j = -2 + a; }
+    else { i = b; j = M + a; }
+  } else {
+    if (k >= 4) return;
+    const int a = k & 1, b = k >> 1;
+    i = (r == 4 || r == 6) ? -2 + a : M + a;
+    j = (r == 4 || r == 5) ? -2 + b : M + b;
+  }
+  const GfPatch P = V.patch[p];
+  const GfCtl* C = V.ctl + P.scen;
+  if (!C->accepted) return;
+  Geo<T> e(G, V);
+  T* q = e.qp(p, C->cur);
+  const int c = e.tix(i, j);
+  const long long I = (long long)P.px * M + i, J = (long long)P.py * M + j;
+  const double bt = (double)e.bp(p)[c];
+  double out[3];
+  int err = 0;
+  fill_cell(e, P.scen, P.level, I, J, bt, out, &err);
+  if (err && errflag) *errflag = 1;
+  e.store(q, c, out[0], out[1], out[2], bt);
+  // physical-boundary ghosts mirroring this cell (wall: reflected, normal
+  // momentum negated; extrapolation: the edge cell into both layers)
+  const int nxp = G.mi << P.level, nyp = G.mj << P.level;
+  int xm[2], ym[2], nx = 0, ny = 0;
+  T fx = T(1), fy = T(1);
+  if (P.px == 0 && (i == 0 || i == 1)) {
+    if (G.bc[0] == 0) { xm[nx++] = -1 - i; fx = T(-1); }
+    else if (i == 0) { xm[nx++] = -1; xm[nx++] = -2; }
+  } else if (P.px == nxp - 1 && (i == M - 1 || i == M - 2)) {
+    if (G.bc[1] == 0) { xm[nx++] = 2 * M - 1 - i; fx = T(-1); }
+    else if (i == M - 1) { xm[nx++] = M; xm[nx++] = M + 1; }
+  }
+  if (P.py == 0 && (j == 0 || j == 1)) {
+    if (G.bc[2] == 0) { ym[ny++] = -1 - j; fy = T(-1); }
+    else if (j == 0) { ym[ny++] = -1; ym[ny++] = -2; }
+  } else if (P.py == nyp - 1 && (j == M - 1 || j == M - 2)) {
+    if (G.bc[3] == 0) { ym[ny++] = 2 * M - 1 - j; fy = T(-1); }
+    else if (j == M - 1) { ym[ny++] = M; ym[ny++] = M + 1; }
+  }
+  if (nx == 0 && ny == 0) return;
+  const T v0 = q[c], v1 = q[TT + c], v2 = q[2 * TT + c];
+  auto put = [&](int a, int b, T su, T sv) {
+    const int d = e.tix(a, b);
+    q[d] = v0;
+    q[TT + d] = su * v1;
+    q[2 * TT + d] = sv * v2;
+  };
+  for (int a = 0; a < nx; ++a) put(xm[a], j, fx, T(1));
+  for (int b = 0; b < ny; ++b) put(i, ym[b], T(1), fy);
+  for (int a = 0; a < nx; ++a)
+    for (int b = 0; b < ny; ++b) put(xm[a], ym[b], fx, fy);
+}
+
 // ------------------------------------------------------------ topography
 
 __device__ double dem_eval(const GfScenario& S, double x, double y) {
@@ -856,14 +930,14 @@ int launch_ghost_fill(const GfGeom& g, const GfView& v, int only_accepted,
   return ok();
 }
 
-int launch_ghost_rest(const GfGeom& g, const GfView& v, const int* list, int n,
+int launch_ghost_rest(const GfGeom& g, const GfView& v, const int* regs, int nreg,
                       void* stream) {
-  if (n <= 0) return 0;
+  if (nreg <= 0) return 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const int nghost = g.T * g.T - g.M * g.M;
-  const int nt = (nghost + 31) / 32 * 32;
-  if (v.prec) k_ghost_fill<float><<<n, nt, 0, st>>>(g, v, 1, g_errflag, list);
-  else k_ghost_fill<double><<<n, nt, 0, st>>>(g, v, 1, g_errflag, list);
+  const long long total = (long long)nreg * 2 * g.M;
+  const int blocks = (int)((total + 255) / 256);
+  if (v.prec) k_ghost_other<float><<<blocks, 256, 0, st>>>(g, v, regs, nreg, g_errflag);
+  else k_ghost_other<double><<<blocks, 256, 0, st>>>(g, v, regs, nreg, g_errflag);
   return ok();
 }
 

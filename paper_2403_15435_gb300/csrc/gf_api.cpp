@@ -13,6 +13,8 @@
 #include <string>
 #include <tuple>
 #include <vector>
+#include <unordered_map>
+#include <thread>
 
 #include "gf_forest.h"
 #include "gf_internal.h"
@@ -89,7 +91,7 @@ struct geoflood_ctx {
   unsigned* d_pcnt = nullptr;
   int* d_rlist = nullptr;   // regrid: new slots to compute
   int* d_rpairs = nullptr;  // regrid: (new, old) slots to copy
-  int* d_glist[2] = {nullptr, nullptr};  // patches with a coarser/finer neighbour
+  int* d_glist[2] = {nullptr, nullptr};  // ghost regions next to a level change
   int nglist[2] = {0, 0};
   bool own_stream = false;
   // CUDA graphs of chunks of steps, keyed by chunk length
@@ -277,14 +279,12 @@ int upload_tables(geoflood_ctx* ctx, int t,
   }
   CK(cudaMemcpyAsync(ctx->d_nbr[t], nb.data(), sizeof(int) * nb.size(),
                      cudaMemcpyHostToDevice, ctx->st));
-  // patches with a ghost region that no same-level neighbour pushes into (a
-  // finer or coarser neighbour): their ghost fill runs after each step
+  // ghost regions that no same-level neighbour pushes into (a finer or
+  // coarser neighbour), as patch * 8 + region: filled after each step
   std::vector<int> gl;
-  for (size_t k = 0; k < total; ++k) {
-    bool other = false;
-    for (int r = 0; r < 8; ++r) other |= nb[k * 8 + r] == GF_NBR_OTHER;
-    if (other) gl.push_back((int)k);
-  }
+  for (size_t k = 0; k < total; ++k)
+    for (int r = 0; r < 8; ++r)
+      if (nb[k * 8 + r] == GF_NBR_OTHER) gl.push_back((int)k * 8 + r);
   ctx->nglist[t] = (int)gl.size();
   if (!gl.empty())
     CK(cudaMemcpyAsync(ctx->d_glist[t], gl.data(), sizeof(int) * gl.size(),
@@ -568,8 +568,8 @@ int geoflood_init_forest(const geoflood_config* cfg, void* stream,
   okk &= alloc((void**)&ctx->d_pcnt, cap * sizeof(unsigned));
   okk &= alloc((void**)&ctx->d_rlist, cap * sizeof(int));
   okk &= alloc((void**)&ctx->d_rpairs, cap * 2 * sizeof(int));
-  okk &= alloc((void**)&ctx->d_glist[0], cap * sizeof(int));
-  okk &= alloc((void**)&ctx->d_glist[1], cap * sizeof(int));
+  okk &= alloc((void**)&ctx->d_glist[0], cap * 8 * sizeof(int));
+  okk &= alloc((void**)&ctx->d_glist[1], cap * 8 * sizeof(int));
   okk &= alloc((void**)&ctx->d_lut[0], (size_t)ctx->nscen * G.lut_per_scen * sizeof(int));
   okk &= alloc((void**)&ctx->d_lut[1], (size_t)ctx->nscen * G.lut_per_scen * sizeof(int));
   okk &= alloc((void**)&ctx->d_scen, ctx->nscen * sizeof(GfScenario));
@@ -917,8 +917,6 @@ int geoflood_step(geoflood_ctx* ctx, double t_target, int max_steps,
   if (!gr->exec || gr->tsel != ctx->tsel || gr->bsel != ctx->bsel ||
       gr->npatch != ctx->npatch || gr->gauges != ctx->max_gauges_used ||
       gr->prof != prof || gr->variant != ctx->variant) {
-    if (gr->exec) cudaGraphExecDestroy(gr->exec);
-    gr->exec = nullptr;
     gr->ev.clear();
     gr->evg.clear();
     CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
@@ -954,7 +952,19 @@ int geoflood_step(geoflood_ctx* ctx, double t_target, int max_steps,
     if (lrc || ce != cudaSuccess)
       return fail(ctx, GEOFLOOD_ERR_CUDA, std::string("step: graph capture failed: ") +
                                               cudaGetErrorString(ce != cudaSuccess ? ce : cudaGetLastError()));
-    ce = cudaGraphInstantiate(&gr->exec, graph, 0);
+    // after a regrid only the kernels' parameters and grids change: update
+    // the executable graph in place when its shape allows, else instantiate
+    bool updated = false;
+    if (gr->exec) {
+      cudaGraphExecUpdateResultInfo info{};
+      updated = cudaGraphExecUpdate(gr->exec, graph, &info) == cudaSuccess;
+      if (!updated) {
+        cudaGetLastError();
+        cudaGraphExecDestroy(gr->exec);
+        gr->exec = nullptr;
+      }
+    }
+    if (!updated) ce = cudaGraphInstantiate(&gr->exec, graph, 0);
     cudaGraphDestroy(graph);
     if (ce != cudaSuccess)
       return fail(ctx, GEOFLOOD_ERR_CUDA, std::string("step: graph instantiation failed: ") +
@@ -1035,34 +1045,64 @@ int geoflood_regrid(geoflood_ctx* ctx) {
   if ((rc = tag_pass(ctx, ctx->cnn.tagger == GEOFLOOD_TAGGER_LEARNED, nullptr))) return rc;
   CK(cudaMemcpyAsync(flags.data(), ctx->d_flags, ctx->npatch, cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
+  // New forests, scenario by scenario (on several host threads when there
+  // are many scenarios); a leaf present in both forests keeps its data
+  // (copied from its old slot), a new one is computed from the old forest.
   std::vector<std::vector<gf::Leaf>> lv(ctx->nscen);
-  size_t total = 0;
-  // leaves present in both forests keep their data (copied from the old slot)
-  std::map<std::tuple<int, int, int, int>, int> old_index;
-  for (int s = 0; s < ctx->nscen; ++s) {
-    const std::vector<gf::Leaf> old = ctx->forests[s].leaves();
-    for (size_t k = 0; k < old.size(); ++k)
-      old_index[std::make_tuple(s, old[k].level, old[k].px, old[k].py)] =
-          ctx->h_scen[s].poff + (int)k;
+  std::vector<std::vector<int>> fresh_s(ctx->nscen), keep_s(ctx->nscen);
+  std::vector<char> changed(ctx->nscen, 0);
+  auto regrid_one = [&](int s) {
+    const std::vector<gf::Leaf>& old = ctx->forests[s].leaves();
+    std::unordered_map<uint64_t, int> old_index;
+    old_index.reserve(old.size() * 2);
+    auto kk = [](const gf::Leaf& l) {
+      return ((uint64_t)l.level << 58) | ((uint64_t)l.px << 29) | (uint64_t)l.py;
+    };
+    for (size_t k = 0; k < old.size(); ++k) old_index[kk(old[k])] = (int)k;
     lv[s] = ctx->forests[s].regrid(flags.data() + ctx->h_scen[s].poff);
-    total += lv[s].size();
+    bool same = lv[s].size() == old.size();
+    for (size_t k = 0; k < lv[s].size(); ++k) {
+      auto it = old_index.find(kk(lv[s][k]));
+      if (it == old_index.end()) {
+        fresh_s[s].push_back((int)k);
+        same = false;
+      } else {
+        keep_s[s].push_back((int)k);
+        keep_s[s].push_back(ctx->h_scen[s].poff + it->second);
+        same = same && it->second == (int)k;
+      }
+    }
+    changed[s] = same ? 0 : 1;
+  };
+  const int nthreads = std::min(ctx->nscen, std::max(1, std::min(16, (int)std::thread::hardware_concurrency())));
+  if (nthreads <= 1) {
+    for (int s = 0; s < ctx->nscen; ++s) regrid_one(s);
+  } else {
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nthreads; ++t)
+      pool.emplace_back([&, t]() {
+        for (int s = t; s < ctx->nscen; s += nthreads) regrid_one(s);
+      });
+    for (auto& th : pool) th.join();
   }
+  // nothing to do when no forest changed (the tables and graphs stay)
+  bool any_change = false;
+  for (int s = 0; s < ctx->nscen; ++s) any_change |= changed[s] != 0;
+  if (!any_change) {
+    for (int s = 0; s < ctx->nscen; ++s) ctx->forests[s].set_leaves(lv[s]);
+    return 0;
+  }
+  size_t total = 0;
   std::vector<int> fresh;         // new slots computed from the old forest
   std::vector<int> keep;          // (new, old) slot pairs
-  {
-    int off = 0;
-    for (int s = 0; s < ctx->nscen; ++s) {
-      for (size_t k = 0; k < lv[s].size(); ++k) {
-        auto it = old_index.find(std::make_tuple(s, lv[s][k].level, lv[s][k].px, lv[s][k].py));
-        if (it == old_index.end()) {
-          fresh.push_back(off + (int)k);
-        } else {
-          keep.push_back(off + (int)k);
-          keep.push_back(it->second);
-        }
-      }
-      off += (int)lv[s].size();
+  for (int s = 0; s < ctx->nscen; ++s) {
+    const int off = (int)total;
+    for (int k : fresh_s[s]) fresh.push_back(off + k);
+    for (size_t k = 0; k < keep_s[s].size(); k += 2) {
+      keep.push_back(off + keep_s[s][k]);
+      keep.push_back(keep_s[s][k + 1]);
     }
+    total += lv[s].size();
   }
   if ((long long)total > ctx->cap)
     return fail(ctx, GEOFLOOD_ERR_CAPACITY,

@@ -162,9 +162,9 @@ int launch_ctl_begin(GfCtl* ctl, int nscen, double t_target,
 int launch_ghost_fill(const GfGeom& g, const GfView& v, int only_active,
                       void* stream);
 // Ghost cells in regions without a same-level neighbour (which the patch
-// step's push leaves out), then the physical boundaries of the tile, for the
-// patches of list[0..n).
-int launch_ghost_rest(const GfGeom& g, const GfView& v, const int* list, int n,
+// step's push leaves out) with their boundary mirrors: regs[k] = patch * 8 +
+// region, k < nreg.
+int launch_ghost_rest(const GfGeom& g, const GfView& v, const int* regs, int nreg,
                       void* stream);
 // Beds of patches [first, first + count), or of list[0..count) if list.
 int launch_topo(const GfGeom& g, const GfView& v, int first, int count,
