@@ -69,9 +69,14 @@ extern "C" {
  * [xlower, xupper] x [ylower, yupper].  g and drytol (Sec. 5.1 wet/dry
  * threshold tau); CFL control (Sec. 5.1 maximum CFL, Sec. 6.6 initial time
  * step): the next dt is cfl_desired / cmax, a step whose CFL number exceeds
- * cfl_max is retaken.  Tagging thresholds (Sec. 4.1 criteria 1, 3, 4) and
- * the flood-source box [x0, x1, y0, y1] refined to src_level (Sec. 6.4).
- * max_patches bounds the patches of all scenarios together. */
+ * cfl_max is retaken.  Tagging (Sec. 4.1): a wet cell (h > tag_depth) asks
+ * for refinement when its speed exceeds tag_speed or its surface deviates
+ * from eta0 by more than tag_deta (criteria 1, 3) or |hu| exceeds tag_flux
+ * (criterion 2); the flood-source box [x0, x1, y0, y1] is refined to
+ * src_level (criterion 4, Sec. 6.4); a wet cell whose depth (grade kind 0)
+ * or speed (kind 1) exceeds grade_value[k] asks for at least level
+ * grade_level[k] (criterion 5, flow grades).  max_patches bounds the
+ * patches of all scenarios together. */
 typedef struct {
   int mi, mj, mx;
   int minlevel, maxlevel;
@@ -86,7 +91,11 @@ typedef struct {
   double tag_depth, tag_speed, tag_deta;
   double src_box[4];
   int src_level;
-  int reserved;
+  int ngrades;         /* flow grades in use (0..4) */
+  double tag_flux;     /* criterion 2 threshold on |hu| (m^2/s); inf: off */
+  int grade_kind[4];   /* criterion 5: 0 = depth, 1 = speed */
+  double grade_value[4];
+  int grade_level[4];
 } geoflood_config;
 
 typedef struct geoflood_ctx geoflood_ctx;

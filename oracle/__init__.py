@@ -50,6 +50,9 @@ class _Cfg(C.Structure):
         ("tag_depth", C.c_double), ("tag_speed", C.c_double),
         ("tag_deta", C.c_double), ("eta0", C.c_double),
         ("src_box", C.c_double * 4), ("src_level", C.c_int),
+        ("tag_flux", C.c_double), ("ngrades", C.c_int),
+        ("grade_kind", C.c_int * 4), ("grade_value", C.c_double * 4),
+        ("grade_level", C.c_int * 4),
     ]
 
 
@@ -135,6 +138,14 @@ def _cfg_struct(cfg) -> _Cfg:
     for k in range(4):
         c.bc[k] = int(cfg.bc[k])
         c.src_box[k] = float(cfg.src_box[k])
+    c.tag_flux = float(getattr(cfg, "tag_flux", float("inf")))
+    grades = list(getattr(cfg, "grades", ()))
+    assert len(grades) <= 4
+    c.ngrades = len(grades)
+    for k, (kind, value, level) in enumerate(grades):
+        c.grade_kind[k] = int(kind)
+        c.grade_value[k] = float(value)
+        c.grade_level[k] = int(level)
     return c
 
 

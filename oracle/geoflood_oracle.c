@@ -1035,17 +1035,28 @@ int oracle_forest_step(oracle_forest* f, double t_target, int max_steps,
  * for refinement (2) when it is wet and moving or off the reference surface,
  * or lies in the source region below the source level; a source-region cell
  * at or above that level asks to be kept (1). */
-static int cell_flag(const oracle_forest* f, int p, int i, int j) {
+/* What one cell asks of the tagger (Sec. 4.1): *r = 2 refine (criteria 1
+ * to 3: wet and flowing fast, deep-and-moving, or a deviating surface; the
+ * source region below src_level, criterion 4), 1 keep (the source region at
+ * or above src_level), 0 nothing; *gl = the highest level a flow grade asks
+ * for (criterion 5), -1 if none. */
+static void cell_flag(const oracle_forest* f, int p, int i, int j, int* r_out, int* gl_out) {
   size_t TT = (size_t)f->T * f->T, id = TI(f, i, j);
   const double* q = f->tile[p];
   double h = q[id];
   int L = f->lev[p];
-  int r = 0;
+  int r = 0, gl = -1, k;
   if (h > f->c.tag_depth) {
     double u = q[TT + id] / h, v = q[2 * TT + id] / h;
     double sp = sqrt(u * u + v * v);
     double eta = h + q[3 * TT + id];
+    double flux = sqrt(q[TT + id] * q[TT + id] + q[2 * TT + id] * q[2 * TT + id]);
     if (sp > f->c.tag_speed || fabs(eta - f->c.eta0) > f->c.tag_deta) r = 2;
+    if (flux > f->c.tag_flux) r = 2;
+    for (k = 0; k < f->c.ngrades; ++k) {
+      double val = f->c.grade_kind[k] == 0 ? h : sp;
+      if (val > f->c.grade_value[k] && f->c.grade_level[k] > gl) gl = f->c.grade_level[k];
+    }
   }
   double xc = f->c.xlower + ((double)((long)f->px[p] * f->M + i) + 0.5) * DXL(f, L);
   double yc = f->c.ylower + ((double)((long)f->py[p] * f->M + j) + 0.5) * DYL(f, L);
@@ -1054,23 +1065,28 @@ static int cell_flag(const oracle_forest* f, int p, int i, int j) {
     if (L < f->c.src_level) r = 2;
     else if (r < 1) r = 1;
   }
-  return r;
+  *r_out = r;
+  *gl_out = gl;
 }
 
-/* Patch flag: refine when a cell asks for it (below maxlevel), coarsen when
- * no cell asks for anything (above minlevel), keep otherwise. */
+/* Patch flag: refine when a cell asks for it (below maxlevel) or a flow
+ * grade asks for a finer level; keep at the grade's level, or when a cell
+ * asks to be kept; otherwise coarsen (above minlevel). */
 void oracle_forest_tags(const oracle_forest* f, uint8_t* flags) {
   int p, i, j;
   for (p = 0; p < f->np; ++p) {
-    int m = 0;
-    for (j = 0; j < f->M && m < 2; ++j)
-      for (i = 0; i < f->M && m < 2; ++i) {
-        int c = cell_flag(f, p, i, j);
+    int m = 0, g = -1;
+    for (j = 0; j < f->M; ++j)
+      for (i = 0; i < f->M; ++i) {
+        int c, gl;
+        cell_flag(f, p, i, j, &c, &gl);
         if (c > m) m = c;
+        if (gl > g) g = gl;
       }
     int L = f->lev[p];
     if (m == 2) flags[p] = L < f->c.maxlevel ? ORACLE_TAG_REFINE : ORACLE_TAG_KEEP;
-    else if (m == 1) flags[p] = ORACLE_TAG_KEEP;
+    else if (g > L) flags[p] = ORACLE_TAG_REFINE;
+    else if (g == L || m == 1) flags[p] = ORACLE_TAG_KEEP;
     else flags[p] = L > f->c.minlevel ? ORACLE_TAG_COARSEN : ORACLE_TAG_KEEP;
   }
 }

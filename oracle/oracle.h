@@ -24,7 +24,7 @@ extern "C" {
 #define ORACLE_BC_WALL 0
 #define ORACLE_BC_EXTRAP 1
 
-/* Patch flags produced by the tagger (Sec. 4.1 criteria 1, 3, 4). */
+/* Patch flags produced by the tagger (Sec. 4.1 criteria 1 to 5). */
 #define ORACLE_TAG_KEEP 0
 #define ORACLE_TAG_REFINE 1
 #define ORACLE_TAG_COARSEN 2
@@ -40,6 +40,14 @@ typedef struct {
   double tag_depth, tag_speed, tag_deta, eta0;
   double src_box[4]; /* x0, x1, y0, y1 of the flood-source region */
   int src_level;     /* refine the source region up to this level */
+  /* criterion 2: refine where h > tag_depth and |hu| > tag_flux */
+  double tag_flux;
+  /* criterion 5: flow grades -- a wet cell whose depth (kind 0) or speed
+   * (kind 1) exceeds grade_value asks for at least grade_level */
+  int ngrades;
+  int grade_kind[4];
+  double grade_value[4];
+  int grade_level[4];
 } oracle_config;
 
 typedef struct oracle_forest oracle_forest;

@@ -583,6 +583,7 @@ __global__ void k_tags(const __grid_constant__ GfGeom G, const __grid_constant__
                        y1 <= G.src_box[3];
   const int rbox = P.level < G.src_level ? 2 : 1;  // a cell in the box asks this
   int m = box_all ? rbox : 0;
+  int gl = -1;  // the highest level a flow grade asks for (criterion 5)
   if (m < 2) {
     // cells in rounds of blockDim; stop once any cell asks for refinement
     for (int k0 = 0; k0 < M * M; k0 += blockDim.x) {
@@ -601,7 +602,13 @@ __global__ void k_tags(const __grid_constant__ GfGeom G, const __grid_constant__
           const float h = w - b;
           if (h > G.tag_depthf) {
             const float hu = q[TT + c], hv = q[2 * TT + c], st = G.tag_speedf * h;
-            if (hu * hu + hv * hv > st * st || fabsf(w) > G.tag_detaf) r = 2;
+            const float f2 = hu * hu + hv * hv;
+            if (f2 > st * st || fabsf(w) > G.tag_detaf || f2 > G.tag_fluxf * G.tag_fluxf) r = 2;
+            for (int g = 0; g < G.ngrades; ++g) {
+              const float tv = G.grade_valuef[g];
+              const bool over = G.grade_kind[g] == 0 ? h > tv : f2 > (tv * h) * (tv * h);
+              if (over && G.grade_level[g] > gl) gl = G.grade_level[g];
+            }
           }
         } else {
           double v4[4];
@@ -611,7 +618,13 @@ __global__ void k_tags(const __grid_constant__ GfGeom G, const __grid_constant__
             const double u = v4[1] / h, v = v4[2] / h;
             const double sp = sqrt(u * u + v * v);
             const double eta = h + v4[3];
+            const double flux = sqrt(v4[1] * v4[1] + v4[2] * v4[2]);
             if (sp > G.tag_speed || fabs(eta - eref) > G.tag_deta) r = 2;
+            if (flux > G.tag_flux) r = 2;
+            for (int g = 0; g < G.ngrades; ++g) {
+              const double val = G.grade_kind[g] == 0 ? h : sp;
+              if (val > G.grade_value[g] && G.grade_level[g] > gl) gl = G.grade_level[g];
+            }
           }
         }
         if (!box_none && !box_all) {
@@ -630,23 +643,35 @@ __global__ void k_tags(const __grid_constant__ GfGeom G, const __grid_constant__
       }
     }
   }
+  // criterion 5 matters only when no cell asks for full refinement
+  gl = __reduce_max_sync(0xffffffffu, gl);
+  __shared__ int wg[32];
+  if ((threadIdx.x & 31) == 0) wg[threadIdx.x >> 5] = gl;
   m = __reduce_max_sync(0xffffffffu, m);
   __shared__ int wm[32];
   if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
   __syncthreads();
   if (threadIdx.x == 0) {
-    int mm = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mm = wm[w] > mm ? wm[w] : mm;
+    int mm = 0, gmax = -1;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      mm = wm[w] > mm ? wm[w] : mm;
+      gmax = wg[w] > gmax ? wg[w] : gmax;
+    }
+    // a flow grade above the patch's level is a request for refinement
+    const bool grade_up = mm < 2 && gmax > P.level;
     // the plain criterion's own verdict: recorded, turned into training
     // labels, or counted as a miss where the patch could still be refined
-    if (O.raw) O.raw[p] = (uint8_t)mm;
-    if (O.label && mm == 2) O.label[p] = 1.0f;
-    if (O.misses && mm == 2 && P.level < G.maxlevel) atomicAdd(O.misses, 1u);
+    const int raw = grade_up ? 2 : mm;
+    if (O.raw) O.raw[p] = (uint8_t)raw;
+    if (O.label && raw == 2) O.label[p] = 1.0f;
+    if (O.misses && raw == 2 && P.level < G.maxlevel) atomicAdd(O.misses, 1u);
     // learned tags add refinement (or keep a fine patch) on top of it
-    if (O.logit && O.logit[p] > O.logit_thr) mm = 2;
+    const bool learned = O.logit && O.logit[p] > O.logit_thr;
+    if (learned) mm = 2;
     uint8_t f;
     if (mm == 2) f = P.level < G.maxlevel ? 1 : 0;
-    else if (mm == 1) f = 0;
+    else if (gmax > P.level) f = 1;
+    else if (gmax == P.level || mm == 1) f = 0;
     else f = P.level > G.minlevel ? 2 : 0;
     if (O.flags) O.flags[p] = f;
   }

@@ -486,6 +486,11 @@ int geoflood_init_forest(const geoflood_config* cfg, void* stream,
   for (int k = 0; k < 4; ++k)
     if (c.bc[k] != GEOFLOOD_BC_WALL && c.bc[k] != GEOFLOOD_BC_EXTRAP)
       return GEOFLOOD_ERR_ARG;
+  if (c.ngrades < 0 || c.ngrades > 4 || !(c.tag_flux > 0)) return GEOFLOOD_ERR_ARG;
+  for (int k = 0; k < c.ngrades; ++k)
+    if ((c.grade_kind[k] != 0 && c.grade_kind[k] != 1) || c.grade_level[k] < c.minlevel ||
+        c.grade_level[k] > c.maxlevel)
+      return GEOFLOOD_ERR_ARG;
   geoflood_ctx* ctx = new geoflood_ctx();
   ctx->cfg = c;
   ctx->st = static_cast<cudaStream_t>(stream);
@@ -532,6 +537,15 @@ int geoflood_init_forest(const geoflood_config* cfg, void* stream,
   G.tag_depthf = (float)c.tag_depth;
   G.tag_speedf = (float)c.tag_speed;
   G.tag_detaf = (float)c.tag_deta;
+  G.tag_flux = c.tag_flux;
+  G.tag_fluxf = (float)c.tag_flux;
+  G.ngrades = c.ngrades;
+  for (int k = 0; k < 4; ++k) {
+    G.grade_kind[k] = c.grade_kind[k];
+    G.grade_level[k] = c.grade_level[k];
+    G.grade_value[k] = c.grade_value[k];
+    G.grade_valuef[k] = (float)c.grade_value[k];
+  }
 
   const size_t TT = (size_t)G.T * G.T;
   const size_t cap = (size_t)ctx->cap;

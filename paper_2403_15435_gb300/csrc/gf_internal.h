@@ -80,6 +80,13 @@ struct GfGeom {
   float inv_dxf[GF_MAXLEV + 1], inv_dyf[GF_MAXLEV + 1];
   float gf, drytolf, marginf;
   float tag_depthf, tag_speedf, tag_detaf;
+  // criterion 2 (|hu| > tag_flux) and criterion 5 (flow grades)
+  double tag_flux;
+  float tag_fluxf;
+  int ngrades;
+  int grade_kind[4], grade_level[4];
+  double grade_value[4];
+  float grade_valuef[4];
 };
 
 // Everything a kernel needs to find patches and their data.

@@ -50,7 +50,9 @@ class _Cfg(C.Structure):
         ("dt_initial", C.c_double), ("dt_max", C.c_double),
         ("tag_depth", C.c_double), ("tag_speed", C.c_double),
         ("tag_deta", C.c_double), ("src_box", C.c_double * 4),
-        ("src_level", C.c_int), ("reserved", C.c_int),
+        ("src_level", C.c_int), ("ngrades", C.c_int),
+        ("tag_flux", C.c_double), ("grade_kind", C.c_int * 4),
+        ("grade_value", C.c_double * 4), ("grade_level", C.c_int * 4),
     ]
 
 
@@ -156,6 +158,14 @@ def config_struct(cfg: inputs.Config, num_scenarios=1, max_patches=None,
     for k in range(4):
         c.bc[k] = int(cfg.bc[k])
         c.src_box[k] = float(cfg.src_box[k])
+    flux = float(getattr(cfg, "tag_flux", math.inf))
+    c.tag_flux = flux if math.isfinite(flux) else 1e300
+    grades = list(getattr(cfg, "grades", ()))
+    c.ngrades = len(grades)
+    for k, (kind, value, level) in enumerate(grades[:4]):
+        c.grade_kind[k] = int(kind)
+        c.grade_value[k] = float(value)
+        c.grade_level[k] = int(level)
     c.num_scenarios = int(num_scenarios)
     if max_patches is None:
         per = cfg.mi * cfg.mj * (4 ** cfg.maxlevel)

@@ -54,6 +54,11 @@ class Config:
     src_level: int = 0
     regrid_interval: int = 0
     precision: int = 0  # 0 = FP64, 1 = FP32 surface-deviation form
+    # criterion 2 (velocity-depth product) threshold on |hu| in m^2/s
+    tag_flux: float = math.inf
+    # criterion 5 (flow grades): up to 4 (kind, value, level), kind 0 = depth,
+    # 1 = speed; a wet cell above value asks for at least that level
+    grades: Tuple[Tuple[int, float, int], ...] = ()
 
 
 @dataclasses.dataclass

@@ -153,6 +153,51 @@ def test_regrid_and_tags_match_oracle(patch):
     assert np.array_equal(ag, ar)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_criteria_2_and_5_match_oracle(prec):
+    """Refinement criteria 2 (|hu| above tag_flux) and 5 (flow grades by
+    depth and by speed) on the valley breach: FP64 tags bit-exact with the
+    oracle through step/regrid cycles; FP32 (its own single-precision
+    criterion) at most a few tag mismatches."""
+    prob = inputs.v_valley(mi=4, mj=2, patch=16, minlevel=0, maxlevel=3,
+                           dem_spacing=8.0, Lx=1000.0, Ly=500.0, breach_x=300.0,
+                           depth=8.0, n_gauges=6)
+    prob.cfg.src_level = 1
+    prob.cfg.tag_speed = 0.5       # leave room for the other criteria
+    prob.cfg.tag_deta = 0.5
+    prob.cfg.tag_flux = 0.2
+    prob.cfg.grades = ((0, 3.0, 2), (1, 0.1, 1))
+    g, r = pair(prob)
+    if prec:
+        p32 = inputs.Problem(prob.name, inputs.Config(**{**prob.cfg.__dict__, "precision": 1}),
+                             prob.dem, prob.ic, prob.t_end, prob.gauges)
+        g = geoflood.Forest(p32.cfg, p32.dem)
+        g.set_state(prob.ic)
+    mismatch = 0
+    seen = set()
+    for cycle in range(5):
+        tg, tr = g.tags(), r.tags()
+        seen.update(int(x) for x in tr)
+        if prec:
+            mismatch += int(np.count_nonzero(tg != tr))
+        else:
+            assert np.array_equal(tg, tr), "tags differ in cycle %d" % cycle
+        g.regrid()
+        r.regrid()
+        if [list(a) for a in g.patch_info()] != [list(a) for a in r.patch_info()]:
+            assert prec, "patch lists differ"
+            break
+        g.step(1e9, 6)
+        r.step(1e9, 6)
+    assert mismatch <= 3
+    # the depth grade (> 3 m: level 2) refines the still reservoir, which the
+    # source box alone keeps at level 1
+    L, X, Y = r.patch_info()
+    x_lo = X * (1000.0 / (4 * 2 ** L))  # left edge of each patch
+    assert np.any((L == 2) & (x_lo < 250.0))
+    assert oracle.REFINE in seen
+
+
 def test_all_dry_domain_is_a_fixed_point():
     prob = inputs.radial_dambreak(64, 32, dx=8.0, radius=0.0)
     g = geoflood.Forest(prob.cfg, prob.dem)

@@ -193,6 +193,44 @@ def test_tagger_criteria():
     assert list(f.tags()) == [oracle.KEEP, oracle.KEEP]
 
 
+def test_tagger_criteria_2_and_5():
+    """Criterion 2 (velocity-depth product: |hu| above tag_flux refines even
+    when the speed is below tag_speed) and criterion 5 (flow grades: a wet
+    cell deeper than the grade's depth asks for exactly the grade's level:
+    refine below it, keep at it, coarsen above it)."""
+    cfg = inputs.Config(mi=2, mj=1, mx=4, minlevel=0, maxlevel=3, xupper=80.0,
+                        yupper=40.0, tag_depth=1e-3, tag_speed=0.01, tag_deta=10.0,
+                        eta0=0.0, tag_flux=0.05)
+    f = oracle.OracleForest(cfg)
+    h = np.full((2, 4, 4), 10.0)
+    hu = np.zeros_like(h)
+    hu[0, 1, 1] = 0.06   # speed 0.006 < tag_speed, |hu| = 0.06 > tag_flux
+    hu[1, 1, 1] = 0.04   # speed 0.004, |hu| = 0.04 below both
+    f.write(h, hu, np.zeros_like(h))
+    L, X, Y = f.patch_info()
+    k0 = int(np.nonzero(X == 0)[0][0])
+    tags = f.tags()
+    assert tags[k0] == oracle.REFINE and tags[1 - k0] == oracle.KEEP  # level 0: keep
+    # flow grades: depth > 5 m asks for level 2, speed > 0.005 m/s for level 1
+    cfg2 = inputs.Config(**{**cfg.__dict__, "tag_flux": float("inf"), "tag_speed": 1.0,
+                            "grades": ((0, 5.0, 2), (1, 0.005, 1))})
+    f2 = oracle.OracleForest(cfg2)
+    f2.write(h, hu, np.zeros_like(h))
+    assert list(f2.tags()) == [oracle.REFINE, oracle.REFINE]   # level 0 < 2
+    f2.regrid()
+    f2.regrid()                                                # now at level 2
+    L2 = f2.patch_info()[0]
+    assert set(L2) == {2}
+    assert set(f2.tags()) == {oracle.KEEP}                     # the grade's level
+    # shallow water: only the speed grade (level 1) applies -> coarsen from 2
+    n = len(L2)
+    f2.write(np.full((n, 4, 4), 1.0), np.full((n, 4, 4), 0.01), np.zeros((n, 4, 4)))
+    assert set(f2.tags()) == {oracle.COARSEN}
+    # dry cells ask for nothing, whatever the grades
+    f2.write(np.full((n, 4, 4), 1e-4), np.zeros((n, 4, 4)), np.zeros((n, 4, 4)))
+    assert set(f2.tags()) == {oracle.COARSEN}
+
+
 def test_gauges_bilinear_exact_and_arrival():
     """Gauges sample the finest leaf bilinearly, ghosts included: a linear
     field is reproduced exactly anywhere, also next to a coarse/fine edge."""
