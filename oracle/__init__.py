@@ -53,6 +53,7 @@ class _Cfg(C.Structure):
         ("tag_flux", C.c_double), ("ngrades", C.c_int),
         ("grade_kind", C.c_int * 4), ("grade_value", C.c_double * 4),
         ("grade_level", C.c_int * 4),
+        ("first_order", C.c_int), ("no_transverse", C.c_int), ("dim_split", C.c_int),
     ]
 
 
@@ -68,6 +69,9 @@ def lib():
             L.oracle_step_grid.argtypes = ([C.c_int, C.c_int] + [dp] * 4 +
                                            [C.c_double] * 6 + [dp] * 4 +
                                            [C.POINTER(C.c_long), dp])
+            L.oracle_step_grid_ex.argtypes = ([C.c_int, C.c_int] + [dp] * 4 +
+                                              [C.c_double] * 6 + [C.c_int] * 3 +
+                                              [dp] * 4 + [C.POINTER(C.c_long), dp])
             L.oracle_dem_average.restype = C.c_double
             L.oracle_dem_average.argtypes = [dp, C.c_int, C.c_int] + [C.c_double] * 8
             L.oracle_forest_new.restype = vp
@@ -113,17 +117,22 @@ def dem_average(dem, xa, xb, ya, yb):
                                     dem.dy, xa, xb, ya, yb)
 
 
-def step_grid(h, hu, hv, b, dx, dy, dt, g=9.81, drytol=1e-3, manning_n=0.0):
-    """One step on a single [ny+4][nx+4] grid with filled ghosts."""
+def step_grid(h, hu, hv, b, dx, dy, dt, g=9.81, drytol=1e-3, manning_n=0.0,
+              order=2, transverse=True, dim_split=False):
+    """One step on a single [ny+4][nx+4] grid with filled ghosts (Sec. 3.2;
+    order 1 drops the limited corrections, transverse=False the transverse
+    terms, dim_split=True takes an x sweep, then a y sweep on its result).
+    Cells outside the interior are returned as given."""
     H, W = h.shape
     arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (h, hu, hv, b)]
     out = [np.empty_like(arrs[0]) for _ in range(3)]
     cm = C.c_double()
     nc = C.c_long()
     cd = C.c_double()
-    lib().oracle_step_grid(W - 4, H - 4, *[_p(a) for a in arrs], dx, dy, dt, g,
-                           drytol, manning_n, *[_p(a) for a in out],
-                           C.byref(cm), C.byref(nc), C.byref(cd))
+    lib().oracle_step_grid_ex(W - 4, H - 4, *[_p(a) for a in arrs], dx, dy, dt, g,
+                              drytol, manning_n, int(order), int(bool(transverse)),
+                              int(bool(dim_split)), *[_p(a) for a in out],
+                              C.byref(cm), C.byref(nc), C.byref(cd))
     return out[0], out[1], out[2], cm.value, nc.value
 
 
@@ -146,6 +155,9 @@ def _cfg_struct(cfg) -> _Cfg:
         c.grade_kind[k] = int(kind)
         c.grade_value[k] = float(value)
         c.grade_level[k] = int(level)
+    c.first_order = int(cfg.first_order)
+    c.no_transverse = int(cfg.no_transverse)
+    c.dim_split = int(cfg.dim_split)
     return c
 
 

@@ -244,7 +244,8 @@ static void transverse_split(int dir, double h, double hu, double hv,
  * [H][W][3]) for cells along the interior range and updates *smax. */
 static void sweep(int dir, int nx, int ny, const double* h, const double* hu,
                   const double* hv, const double* b, double nu, double g,
-                  double drytol, double* dq, double* smax) {
+                  double drytol, double* dq, double* smax, int order, int c_lo,
+                  int c_hi) {
   int W = nx + 2 * NG;
   int na = dir == 0 ? nx : ny;
   int nc = dir == 0 ? ny : nx;
@@ -258,7 +259,7 @@ static void sweep(int dir, int nx, int ny, const double* h, const double* hu,
   const double* qn = dir == 0 ? hu : hv;
   const double* qt = dir == 0 ? hv : hu;
   int a, c, p, k;
-  for (c = -1; c <= nc; ++c) {
+  for (c = c_lo; c <= c_hi; ++c) {
     for (a = -1; a <= na + 1; ++a) {
       int iL = dir == 0 ? a - 1 : c, jL = dir == 0 ? c : a - 1;
       int iR = dir == 0 ? a : c, jR = dir == 0 ? c : a;
@@ -283,7 +284,7 @@ static void sweep(int dir, int nx, int ny, const double* h, const double* hu,
           cp[p][k] = Z[3 * p + k] * wp;
           cf[p][k] = 0.0;
         }
-        if (S[p] != 0.0 && !wd[a + 1]) {
+        if (order >= 2 && S[p] != 0.0 && !wd[a + 1]) {
           double zz = dot3(Z + 3 * p, Z + 3 * p);
           if (zz != 0.0) {
             int up = S[p] > 0.0 ? a - 1 : a + 1;
@@ -358,11 +359,27 @@ static void transverse(int dir, int nx, int ny, const double* h,
   free(PL); free(MI);
 }
 
-void oracle_step_grid(int nx, int ny, const double* h, const double* hu,
-                      const double* hv, const double* b, double dx, double dy,
-                      double dt, double g, double drytol, double manning_n,
-                      double* hn, double* hun, double* hvn, double* cmax,
-                      long* nclip, double* clipdepth) {
+/* The Manning step of Eq. (manning) on one updated cell r = (h, hu, hv):
+ * semi-implicit, on wet cells, after the hyperbolic update; momenta zeroed
+ * where the cell is dry. */
+static void friction(double* r, double dt, double g, double drytol, double manning_n) {
+  if (manning_n > 0.0 && r[0] > drytol) {
+    double u = r[1] / r[0], v = r[2] / r[0];
+    double sp = sqrt(u * u + v * v);
+    double D = g * manning_n * manning_n * sp / (r[0] * cbrt(r[0]));
+    double den = 1.0 + dt * D;
+    r[1] = r[1] / den;
+    r[2] = r[2] / den;
+  }
+  if (r[0] <= drytol) { r[1] = 0.0; r[2] = 0.0; }
+}
+
+void oracle_step_grid_ex(int nx, int ny, const double* h, const double* hu,
+                         const double* hv, const double* b, double dx, double dy,
+                         double dt, double g, double drytol, double manning_n,
+                         int order, int transv, int dim_split, double* hn,
+                         double* hun, double* hvn, double* cmax, long* nclip,
+                         double* clipdepth) {
   int W = nx + 2 * NG, H = ny + 2 * NG;
   size_t N = (size_t)W * H;
   double clipsum = 0.0;
@@ -372,47 +389,81 @@ void oracle_step_grid(int nx, int ny, const double* h, const double* hu,
   double* ftr = (double*)calloc(3 * N, sizeof(double));
   double nux = dt / dx, nuy = dt / dy;
   double smx = 0.0, smy = 0.0;
+  long clip = 0;
   int i, j, k;
-
-  sweep(0, nx, ny, h, hu, hv, b, nux, g, drytol, dqx, &smx);
-  transverse(0, nx, ny, h, hu, hv, b, dqx, nux, g, drytol, gtr);
-  sweep(1, nx, ny, h, hu, hv, b, nuy, g, drytol, dqy, &smy);
-  transverse(1, nx, ny, h, hu, hv, b, dqy, nuy, g, drytol, ftr);
 
   memcpy(hn, h, sizeof(double) * N);
   memcpy(hun, hu, sizeof(double) * N);
   memcpy(hvn, hv, sizeof(double) * N);
-  long clip = 0;
-  for (j = 0; j < ny; ++j)
-    for (i = 0; i < nx; ++i) {
-      int id = (i + NG) + (j + NG) * W;
-      double q[3] = {h[id], hu[id], hv[id]};
-      double r[3];
-      for (k = 0; k < 3; ++k) {
-        double fl = nux * dqx[3 * id + k] + nuy * dqy[3 * id + k];
-        double tf = nux * (ftr[3 * (id + 1) + k] - ftr[3 * id + k]) +
-                    nuy * (gtr[3 * (id + W) + k] - gtr[3 * id + k]);
-        r[k] = (q[k] - fl) - tf;
+  if (!dim_split) {
+    /* unsplit: both sweeps from Q^n, transverse terms optional */
+    sweep(0, nx, ny, h, hu, hv, b, nux, g, drytol, dqx, &smx, order, -1, ny);
+    if (transv) transverse(0, nx, ny, h, hu, hv, b, dqx, nux, g, drytol, gtr);
+    sweep(1, nx, ny, h, hu, hv, b, nuy, g, drytol, dqy, &smy, order, -1, nx);
+    if (transv) transverse(1, nx, ny, h, hu, hv, b, dqy, nuy, g, drytol, ftr);
+    for (j = 0; j < ny; ++j)
+      for (i = 0; i < nx; ++i) {
+        int id = (i + NG) + (j + NG) * W;
+        double q[3] = {h[id], hu[id], hv[id]};
+        double r[3];
+        for (k = 0; k < 3; ++k) {
+          double fl = nux * dqx[3 * id + k] + nuy * dqy[3 * id + k];
+          double tf = nux * (ftr[3 * (id + 1) + k] - ftr[3 * id + k]) +
+                      nuy * (gtr[3 * (id + W) + k] - gtr[3 * id + k]);
+          r[k] = (q[k] - fl) - tf;
+        }
+        if (r[0] < 0.0) { clipsum -= r[0]; r[0] = 0.0; ++clip; }
+        friction(r, dt, g, drytol, manning_n);
+        hn[id] = r[0]; hun[id] = r[1]; hvn[id] = r[2];
       }
-      if (r[0] < 0.0) { clipsum -= r[0]; r[0] = 0.0; ++clip; }
-      /* Manning friction, Eq. (manning), applied after the hyperbolic update
-       * as a semi-implicit split step on wet cells. */
-      if (manning_n > 0.0 && r[0] > drytol) {
-        double u = r[1] / r[0], v = r[2] / r[0];
-        double sp = sqrt(u * u + v * v);
-        double D = g * manning_n * manning_n * sp / (r[0] * cbrt(r[0]));
-        double den = 1.0 + dt * D;
-        r[1] = r[1] / den;
-        r[2] = r[2] / den;
+  } else {
+    /* dimensional splitting: the x-sweep updates every row of the interior
+     * columns (ghost rows included), the y-sweep runs on that state */
+    double* hs = (double*)malloc(sizeof(double) * N);
+    double* hus = (double*)malloc(sizeof(double) * N);
+    double* hvs = (double*)malloc(sizeof(double) * N);
+    memcpy(hs, h, sizeof(double) * N);
+    memcpy(hus, hu, sizeof(double) * N);
+    memcpy(hvs, hv, sizeof(double) * N);
+    sweep(0, nx, ny, h, hu, hv, b, nux, g, drytol, dqx, &smx, order, -2, ny + 1);
+    for (j = -2; j < ny + 2; ++j)
+      for (i = 0; i < nx; ++i) {
+        int id = (i + NG) + (j + NG) * W;
+        double r[3] = {h[id] - nux * dqx[3 * id], hu[id] - nux * dqx[3 * id + 1],
+                       hv[id] - nux * dqx[3 * id + 2]};
+        if (r[0] < 0.0) {
+          if (j >= 0 && j < ny) { clipsum -= r[0]; ++clip; }
+          r[0] = 0.0;
+        }
+        if (r[0] <= drytol) { r[1] = 0.0; r[2] = 0.0; }
+        hs[id] = r[0]; hus[id] = r[1]; hvs[id] = r[2];
       }
-      if (r[0] <= drytol) { r[1] = 0.0; r[2] = 0.0; }
-      hn[id] = r[0]; hun[id] = r[1]; hvn[id] = r[2];
-    }
+    sweep(1, nx, ny, hs, hus, hvs, b, nuy, g, drytol, dqy, &smy, order, 0, nx - 1);
+    for (j = 0; j < ny; ++j)
+      for (i = 0; i < nx; ++i) {
+        int id = (i + NG) + (j + NG) * W;
+        double r[3] = {hs[id] - nuy * dqy[3 * id], hus[id] - nuy * dqy[3 * id + 1],
+                       hvs[id] - nuy * dqy[3 * id + 2]};
+        if (r[0] < 0.0) { clipsum -= r[0]; r[0] = 0.0; ++clip; }
+        friction(r, dt, g, drytol, manning_n);
+        hn[id] = r[0]; hun[id] = r[1]; hvn[id] = r[2];
+      }
+    free(hs); free(hus); free(hvs);
+  }
   double cx = smx / dx, cy = smy / dy;
   *cmax = cx > cy ? cx : cy;
   *nclip = clip;
   *clipdepth = clipsum;
   free(dqx); free(dqy); free(gtr); free(ftr);
+}
+
+void oracle_step_grid(int nx, int ny, const double* h, const double* hu,
+                      const double* hv, const double* b, double dx, double dy,
+                      double dt, double g, double drytol, double manning_n,
+                      double* hn, double* hun, double* hvn, double* cmax,
+                      long* nclip, double* clipdepth) {
+  oracle_step_grid_ex(nx, ny, h, hu, hv, b, dx, dy, dt, g, drytol, manning_n, 2, 1, 0,
+                      hn, hun, hvn, cmax, nclip, clipdepth);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -994,9 +1045,11 @@ int oracle_forest_step(oracle_forest* f, double t_target, int max_steps,
       double cm;
       double* q = f->tile[p];
       memcpy(nt[p] + 3 * TT, q + 3 * TT, sizeof(double) * TT);
-      oracle_step_grid(f->M, f->M, q, q + TT, q + 2 * TT, q + 3 * TT, DXL(f, L),
-                       DYL(f, L), dt, f->c.g, f->c.drytol, f->c.manning_n,
-                       nt[p], nt[p] + TT, nt[p] + 2 * TT, &cm, &ncl[p], &cdp[p]);
+      oracle_step_grid_ex(f->M, f->M, q, q + TT, q + 2 * TT, q + 3 * TT, DXL(f, L),
+                          DYL(f, L), dt, f->c.g, f->c.drytol, f->c.manning_n,
+                          f->c.first_order ? 1 : 2, !f->c.no_transverse,
+                          f->c.dim_split, nt[p],
+                          nt[p] + TT, nt[p] + 2 * TT, &cm, &ncl[p], &cdp[p]);
       if (cm > cmax) cmax = cm;
     }
     if (dt * cmax > f->c.cfl_max) {
@@ -1030,11 +1083,6 @@ int oracle_forest_step(oracle_forest* f, double t_target, int max_steps,
   return rc;
 }
 
-/* Plain tagger: Sec. 4.1 criteria 1 (depth), 3 (velocity) and 4 (flood
- * source region); Sec. 6.4 (rapid flow and the reservoir box).  A cell asks
- * for refinement (2) when it is wet and moving or off the reference surface,
- * or lies in the source region below the source level; a source-region cell
- * at or above that level asks to be kept (1). */
 /* What one cell asks of the tagger (Sec. 4.1): *r = 2 refine (criteria 1
  * to 3: wet and flowing fast, deep-and-moving, or a deviating surface; the
  * source region below src_level, criterion 4), 1 keep (the source region at

@@ -48,6 +48,11 @@ typedef struct {
   int grade_kind[4];
   double grade_value[4];
   int grade_level[4];
+  /* scheme variants of Sec. 3.2 (all 0: second order, unsplit, with
+   * transverse propagation): first_order drops the limited corrections,
+   * no_transverse the transverse terms, dim_split replaces the unsplit
+   * update by an x sweep followed by a y sweep on its result */
+  int first_order, no_transverse, dim_split;
 } oracle_config;
 
 typedef struct oracle_forest oracle_forest;
@@ -66,6 +71,13 @@ void oracle_riemann(double hL, double nL, double tL, double bL, double hR,
  * in *cmax the largest |s|/dx or |s|/dy over the edges that update interior
  * cells, in *nclip the number of negative depths reset to zero and in
  * *clipdepth the sum of the depths so added. */
+/* The same step with the scheme's options (see oracle_config). */
+void oracle_step_grid_ex(int nx, int ny, const double* h, const double* hu,
+                         const double* hv, const double* b, double dx, double dy,
+                         double dt, double g, double drytol, double manning_n,
+                         int order, int transverse, int dim_split, double* hn,
+                         double* hun, double* hvn, double* cmax, long* nclip,
+                         double* clipdepth);
 void oracle_step_grid(int nx, int ny, const double* h, const double* hu,
                       const double* hv, const double* b, double dx, double dy,
                       double dt, double g, double drytol, double manning_n,

@@ -59,6 +59,11 @@ class Config:
     # criterion 5 (flow grades): up to 4 (kind, value, level), kind 0 = depth,
     # 1 = speed; a wet cell above value asks for at least that level
     grades: Tuple[Tuple[int, float, int], ...] = ()
+    # scheme variants of Sec. 3.2 (all 0: second order, unsplit, with
+    # transverse propagation)
+    first_order: int = 0
+    no_transverse: int = 0
+    dim_split: int = 0
 
 
 @dataclasses.dataclass

@@ -1,0 +1,190 @@
+"""Pins of the scheme variants of Sec. 3.2 in the oracle: the first-order
+method (no limited corrections), the unsplit method without transverse
+propagation, and dimensional splitting (an x sweep, then a y sweep on its
+result).  Each is pinned by what the method fixes independently of the
+oracle's own arithmetic: the width of the stencil, the equality of split and
+unsplit updates on problems that vary along one axis only, the composition
+of one-dimensional steps, first-order convergence on the Stoker dam break,
+and exact symmetries and equivalences on a forest."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2403_15435_gb300 import inputs
+from test_oracle_pins import assemble, run, stoker_exact
+
+NG = 2
+
+
+def wet_state(nx, ny, seed, dry_box=None):
+    """Smooth random wet state on an [ny+4][nx+4] grid (ghosts included) over
+    a bumpy bed; cells in dry_box (j0, j1, i0, i1, grid indices) are dry with
+    zero momenta."""
+    rng = np.random.default_rng(seed)
+    H, W = ny + 2 * NG, nx + 2 * NG
+    y, x = np.mgrid[0:H, 0:W].astype(np.float64)
+    b = 0.3 * np.sin(0.7 * x + rng.uniform(0, 6)) * np.cos(0.5 * y) + 1e-3 * rng.random((H, W))
+    eta = 2.0 + 0.4 * np.sin(0.4 * x + 0.3 * y + rng.uniform(0, 6)) + 1e-3 * rng.random((H, W))
+    h = eta - b
+    hu = h * (0.8 * np.cos(0.3 * y + rng.uniform(0, 6)) + 1e-3 * rng.standard_normal((H, W)))
+    hv = h * (-0.5 * np.sin(0.4 * x + rng.uniform(0, 6)) + 1e-3 * rng.standard_normal((H, W)))
+    if dry_box is not None:
+        j0, j1, i0, i1 = dry_box
+        b[j0:j1, i0:i1] += 3.0
+        h[j0:j1, i0:i1] = 0.0
+        hu[j0:j1, i0:i1] = 0.0
+        hv[j0:j1, i0:i1] = 0.0
+    return h, hu, hv, b
+
+
+DX, DY, DT = 2.0, 2.5, 0.12
+
+
+def step(s, **kw):
+    return oracle.step_grid(*s, DX, DY, DT, **kw)[:3]
+
+
+def test_first_order_and_transverse_stencils():
+    """The first-order update of a cell reads only its four edge neighbours
+    and, through the transverse terms, the four diagonal ones; the
+    second-order corrections reach two cells along each axis; without the
+    transverse terms no diagonal neighbour is read."""
+    nx = ny = 10
+    s = wet_state(nx, ny, 1)
+    i0, j0 = NG + 4, NG + 5  # grid indices of the probed cell
+
+    def changed(pj, pi, **kw):
+        t = [a.copy() for a in s]
+        t[0][pj, pi] += 0.05
+        t[1][pj, pi] += 0.03
+        a, b = step(s, **kw), step(t, **kw)
+        return any(a[k][j0, i0] != b[k][j0, i0] for k in range(3))
+
+    for kw in (dict(order=1), dict(order=2)):
+        assert changed(j0, i0 + 1, **kw) and changed(j0 - 1, i0, **kw)
+    for far in ((j0, i0 + 2), (j0 - 2, i0), (j0, i0 - 2), (j0 + 2, i0)):
+        assert not changed(*far, order=1), far
+        assert changed(*far, order=2), far
+    for diag in ((j0 + 1, i0 + 1), (j0 - 1, i0 + 1), (j0 + 1, i0 - 1), (j0 - 1, i0 - 1)):
+        assert changed(*diag, order=1, transverse=True), diag
+        assert not changed(*diag, order=1, transverse=False), diag
+        assert not changed(*diag, order=2, transverse=False), diag
+    # a diagonal neighbour two cells out reaches the cell through the
+    # corrections and the transverse terms together
+    assert not changed(j0 + 2, i0 + 2, order=1, transverse=True)
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_dim_split_is_row_steps_then_column_steps(order):
+    """Dimensional splitting equals one-dimensional steps: every row of the
+    grid (ghost rows included) stepped alone along x, then every interior
+    column of that result stepped alone along y.  A single row or column is
+    made a grid by repeating it across, so the other direction sees no
+    waves."""
+    nx, ny = 9, 7
+    s = wet_state(nx, ny, 2, dry_box=(NG + 2, NG + 4, NG + 5, NG + 8))
+    split = step(s, order=order, dim_split=True)
+    H, W = ny + 2 * NG, nx + 2 * NG
+    mid = [a.copy() for a in s]
+    for j in range(H):
+        row = [np.repeat(a[j:j + 1, :], 1 + 2 * NG, axis=0) for a in s]
+        out = step(row, order=order, transverse=False)
+        for k in range(3):
+            mid[k][j, NG:NG + nx] = out[k][NG, NG:NG + nx]
+    fin = [a.copy() for a in s]
+    for i in range(NG, NG + nx):
+        col = [np.repeat(a[:, i:i + 1], 1 + 2 * NG, axis=1) for a in mid[:3]] + \
+              [np.repeat(s[3][:, i:i + 1], 1 + 2 * NG, axis=1)]
+        out = step(col, order=order, transverse=False)
+        for k in range(3):
+            fin[k][NG:NG + ny, i] = out[k][NG:NG + ny, NG]
+    for k in range(3):
+        assert np.array_equal(split[k][NG:-NG, NG:-NG], fin[k][NG:-NG, NG:-NG]), k
+    # and it is not the unsplit update
+    uns = step(s, order=order)
+    assert not np.array_equal(split[0][NG:-NG, NG:-NG], uns[0][NG:-NG, NG:-NG])
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+@pytest.mark.parametrize("order", [1, 2])
+def test_dim_split_equals_unsplit_on_one_dimensional_problems(axis, order):
+    """On a state that varies along one axis only, the waves of the other
+    direction, and hence every transverse term, vanish: split and unsplit
+    updates agree exactly."""
+    nx = ny = 12
+    s = wet_state(nx, ny, 3)
+    if axis == 0:  # varies along x only
+        s = tuple(np.repeat(a[5:6, :], ny + 2 * NG, axis=0) for a in s)
+        s = (s[0], s[1], np.zeros_like(s[2]), s[3])
+    else:
+        s = tuple(np.repeat(a[:, 5:6], nx + 2 * NG, axis=1) for a in s)
+        s = (s[0], np.zeros_like(s[1]), s[2], s[3])
+    a = step(s, order=order, dim_split=True)
+    b = step(s, order=order)
+    for k in range(3):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def stoker_l1(n, **flags):
+    prob = inputs.stoker(n)
+    for k, v in flags.items():
+        setattr(prob.cfg, k, v)
+    f = run(prob)
+    h = assemble(f, 0)
+    x = (np.arange(n) + 0.5) * 640.0 / n
+    he, *_ = stoker_exact(x, 20.0)
+    return np.abs(h.mean(axis=0) - he).sum() / np.abs(he).sum(), h
+
+
+def test_first_order_stoker_converges_at_first_order():
+    """Stoker dam break with the first-order method: the L1 error falls at
+    about first order (shock and rarefaction smeared over a number of cells
+    that grows like the square root of the step count) and stays above the
+    second-order error on the same grid."""
+    e1 = []
+    for n in (128, 256):
+        e, h = stoker_l1(n, first_order=1)
+        assert np.all(h == h[0:1, :])
+        e1.append(e)
+    e2, _ = stoker_l1(128)
+    rate = math.log2(e1[0] / e1[1])
+    assert 0.4 <= rate <= 1.1, rate
+    assert e1[0] > 1.3 * e2
+    assert e1[0] <= 0.05
+
+
+def test_dim_split_forest_keeps_mirror_symmetry_and_mass():
+    """Radial dam break with dimensional splitting: the x-then-y order keeps
+    both mirror symmetries exactly (not the diagonal one), walls conserve the
+    volume, and the result is close to the unsplit method's."""
+    prob = inputs.radial_dambreak(64, 32, dx=8.0, radius=100.0, flat=True)
+    prob.cfg.dim_split = 1
+    f = run(prob, t_end=12.0)
+    h = assemble(f, 0)
+    sc = np.abs(h).max()
+    assert np.abs(h - h[:, ::-1]).max() <= 1e-12 * sc
+    assert np.abs(h - h[::-1, :]).max() <= 1e-12 * sc
+    g = run(inputs.radial_dambreak(64, 32, dx=8.0, radius=100.0, flat=True), t_end=12.0)
+    hu = assemble(g, 0)
+    m0 = np.sum(h) * 64.0
+    assert abs(np.sum(hu) * 64.0 - m0) <= 1e-11 * m0
+    assert np.abs(h - hu).max() <= 0.05 * sc
+
+
+@pytest.mark.parametrize("flags", [dict(dim_split=1), dict(first_order=1, no_transverse=1)])
+def test_variants_patches_equal_single_grid_bitwise(flags):
+    """A uniform forest of 4 x 4 patches advances exactly like one grid under
+    the scheme variants too (ghost rows and corners of a patch are copies of
+    its neighbours, walls mirror exactly)."""
+    big = inputs.radial_dambreak(128, 128, dx=4.0, radius=120.0)
+    small = inputs.radial_dambreak(128, 32, dx=4.0, radius=120.0)
+    for p in (big, small):
+        for k, v in flags.items():
+            setattr(p.cfg, k, v)
+    fa = run(big, t_end=6.0)
+    fb = run(small, t_end=6.0)
+    assert fa.time()["steps"] == fb.time()["steps"]
+    for k in range(3):
+        assert np.array_equal(assemble(fa, k), assemble(fb, k))
