@@ -96,6 +96,17 @@ typedef struct {
   int grade_kind[4];   /* criterion 5: 0 = depth, 1 = speed */
   double grade_value[4];
   int grade_level[4];
+  /* scheme variants of Sec. 3.2, each 0 or 1 (all 0: second order, unsplit,
+   * with transverse propagation): first_order drops the limited
+   * corrections; no_transverse drops the transverse terms of the unsplit
+   * update; dim_split replaces the unsplit update by an x sweep over every
+   * row of a patch (ghost rows included), then a y sweep on its result
+   * (negative depths reset and dry momenta zeroed in between), without
+   * transverse terms.  Without transverse terms the unsplit update is
+   * stable only up to a Courant number of 1/2 (set cfl_desired and cfl_max
+   * accordingly); the split update is stable up to 1.  With dim_split the
+   * patch step has a single kernel variant. */
+  int first_order, no_transverse, dim_split;
 } geoflood_config;
 
 typedef struct geoflood_ctx geoflood_ctx;

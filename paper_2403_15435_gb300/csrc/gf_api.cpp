@@ -487,6 +487,7 @@ int geoflood_init_forest(const geoflood_config* cfg, void* stream,
     if (c.bc[k] != GEOFLOOD_BC_WALL && c.bc[k] != GEOFLOOD_BC_EXTRAP)
       return GEOFLOOD_ERR_ARG;
   if (c.ngrades < 0 || c.ngrades > 4 || !(c.tag_flux > 0)) return GEOFLOOD_ERR_ARG;
+  if ((c.first_order | c.no_transverse | c.dim_split) & ~1) return GEOFLOOD_ERR_ARG;
   for (int k = 0; k < c.ngrades; ++k)
     if ((c.grade_kind[k] != 0 && c.grade_kind[k] != 1) || c.grade_level[k] < c.minlevel ||
         c.grade_level[k] > c.maxlevel)
@@ -546,6 +547,9 @@ int geoflood_init_forest(const geoflood_config* cfg, void* stream,
     G.grade_value[k] = c.grade_value[k];
     G.grade_valuef[k] = (float)c.grade_value[k];
   }
+  G.first_order = c.first_order;
+  G.no_transverse = c.no_transverse;
+  G.dim_split = c.dim_split;
 
   const size_t TT = (size_t)G.T * G.T;
   const size_t cap = (size_t)ctx->cap;
@@ -1282,7 +1286,7 @@ int geoflood_autotune(geoflood_ctx* ctx, int reps, int* variant,
   if ((rc = sync_ctl_up(ctx))) return rc;
   GfView v = view(ctx);
   v.done = nullptr;  // no controller: the state does not advance
-  const int nv = gf::patch_step_variants(ctx->G.M, ctx->prec);
+  const int nv = gf::patch_step_variants(ctx->G.M, ctx->prec, ctx->G.dim_split);
   cudaEvent_t a = pool_event(ctx), b = pool_event(ctx);
   int best = 0;
   double best_ms = 1e300;
@@ -1314,7 +1318,8 @@ int geoflood_autotune(geoflood_ctx* ctx, int reps, int* variant,
 }
 
 int geoflood_set_variant(geoflood_ctx* ctx, int variant) {
-  if (!ctx || variant < 0 || variant >= gf::patch_step_variants(ctx->G.M, ctx->prec))
+  if (!ctx || variant < 0 ||
+      variant >= gf::patch_step_variants(ctx->G.M, ctx->prec, ctx->G.dim_split))
     return fail(ctx, GEOFLOOD_ERR_ARG, "set_variant: no such variant");
   ctx->variant = variant;
   // the per-unit volumes of another variant's layout are not reusable

@@ -87,6 +87,8 @@ struct GfGeom {
   int grade_kind[4], grade_level[4];
   double grade_value[4];
   float grade_valuef[4];
+  // scheme variants (Sec. 3.2); all 0: second order, unsplit, transverse
+  int first_order, no_transverse, dim_split;
 };
 
 // Everything a kernel needs to find patches and their data.
@@ -159,7 +161,7 @@ __device__ __forceinline__ double gf_bilinear(double a00, double a10, double a01
 #endif
 
 namespace gf {
-int patch_step_variants(int mx, int prec);
+int patch_step_variants(int mx, int prec, int dim_split);
 int launch_patch_step_f64(const GfGeom& g, const GfView& v, double* pmass,
                           int variant, void* stream);
 int launch_patch_step_f32(const GfGeom& g, const GfView& v, double* pmass,

@@ -45,13 +45,21 @@ namespace gf {
 // patches, 0 = one 512-thread CTA per patch (TMA bulk staging of the whole
 // tile), 1 = four CTAs of 16 x 16 sub-tiles per patch, 2 = as 0 (FP32) or 1
 // (FP64) with the register limit for one CTA per SM; 16 x 16 patches have the
-// single variant 0.
-int patch_step_variants(int mx, int prec) { return mx == 32 ? 4 : 1; }
+// single variant 0.  Dimensionally split stepping has one kernel per patch
+// size (whole-patch CTAs).
+int patch_step_variants(int mx, int prec, int dim_split) {
+  return dim_split ? 1 : (mx == 32 ? 4 : 1);
+}
 
 int launch_patch_step_f64(const GfGeom& g, const GfView& v, double* pmass,
                           int variant, void* stream) {
   if (v.npatch <= 0) return 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (g.dim_split) {
+    if (g.M == 32) return gfs::launch_step<gfs::PrecF64, 32, 32, 512, 1, true>(g, v, pmass, st);
+    if (g.M == 16) return gfs::launch_step<gfs::PrecF64, 16, 16, 256, 1, true>(g, v, pmass, st);
+    return -1;
+  }
   if (g.M == 32 && variant == 1)
     return gfs::launch_step<gfs::PrecF64, 32, 16, 256, 2>(g, v, pmass, st);
   if (g.M == 32 && variant == 2)

@@ -205,22 +205,27 @@ __device__ __forceinline__ void sample_gauges(const GfView& V, int scen, const G
   }
 }
 
-template <class P, int M>
+// Shared-memory layout of one CTA.  DS = dimensional splitting: the x sweep
+// covers every row of the window (two ghost rows each side) and there are no
+// transverse-flux arrays.
+template <class P, int M, bool DS = false>
 struct Layout {
   using R = typename P::R;
   static constexpr int T = M + 2 * GF_NG;
   static constexpr int TT = T * T;
-  static constexpr int NR = M + 2;  // lines swept: one ghost line each side
+  // most lines in one sweep: one ghost line each side (unsplit) or two
+  static constexpr int NR = DS ? M + 4 : M + 2;
   static constexpr int NE = M + 3;  // edges per line, a in [-1, M+1]
   static constexpr int NEDGE = NR * NE;
   static constexpr int NLIM = NR * (M + 1);   // edges a in [0, M] per line
-  static constexpr int NCELL = M * (M + 2);   // cells of the increments
+  static constexpr int NCELL = M * NR;        // cells of the increments
   static constexpr int NF = P::DEV ? 5 : 4;   // tile fields (+ depth)
+  static constexpr size_t TRB = DS ? 0 : sizeof(R) * 3 * M * (M + 1);
   // byte offsets in dynamic shared memory
   static constexpr size_t OFF_W = sizeof(R) * NF * TT;
   static constexpr size_t OFF_F = OFF_W + sizeof(R) * 12 * NEDGE;
-  static constexpr size_t OFF_G = OFF_F + sizeof(R) * 3 * M * (M + 1);
-  static constexpr size_t OFF_RED = align16(OFF_G + sizeof(R) * 3 * M * (M + 1));
+  static constexpr size_t OFF_G = OFF_F + TRB;
+  static constexpr size_t OFF_RED = align16(OFF_G + TRB);
   static constexpr size_t OFF_NB = OFF_RED + sizeof(double) * 64;  // 8 ints
   static constexpr size_t OFF_WET = OFF_NB + 32;
   static constexpr size_t OFF_BAR = align16(OFF_WET + (P::DEV ? TT : 0));
@@ -232,22 +237,22 @@ __device__ __forceinline__ int tix(int i, int j) {
   return (i + GF_NG) + (j + GF_NG) * (M + 2 * GF_NG);
 }
 
-// Increment cell of item k in a sweep: items below M*M are interior cells in
-// the fixed order (i = k % M, j = k / M) used by the final update, so each
-// thread owns the same cells in both sweeps; then the ghost line before and
-// the one after.  a is the position along the sweep, line the one across.
-template <int M>
+// Increment cell of item k in a sweep over NRL lines: items below M*M are
+// interior cells in the fixed order (i = k % M, j = k / M) used by the final
+// update, so each thread owns the same cells in both sweeps; then the ghost
+// lines before the interior (from line L0 on) and those after it.  a is the
+// position along the sweep, line the one across.
+template <int M, int NRL, int L0>
 __device__ __forceinline__ void cell_item(int k, int dir, int& a, int& line) {
   if (k < M * M) {
     const int i = k % M, j = k / M;
     a = dir == 0 ? i : j;
     line = dir == 0 ? j : i;
-  } else if (k < M * M + M) {
-    a = k - M * M;
-    line = -1;
   } else {
-    a = k - M * M - M;
-    line = M;
+    constexpr int HALF = (NRL - M) / 2;
+    const int r = k - M * M, gl = r / M;
+    a = r % M;
+    line = gl < HALF ? L0 + gl : M + (gl - HALF);
   }
 }
 
@@ -257,7 +262,13 @@ __device__ __forceinline__ void cell_item(int k, int dir, int& a, int& line) {
 // whose ghosts are filled) and writing its M x M cells.  Every cell's update
 // depends only on its two-cell neighbourhood, so the result does not depend
 // on M.
-template <class P, int MP, int M, int NT>
+//
+// Scheme variants (Sec. 3.2): G.first_order drops the limited corrections,
+// G.no_transverse the transverse terms; DS (dimensional splitting) takes the
+// x sweep on every row of the window, updates the interior columns of all
+// rows in shared memory (negative depths reset, dry momenta zeroed), and
+// takes the y sweep on that state, without transverse terms.
+template <class P, int MP, int M, int NT, bool DS = false>
 __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
                                           double* __restrict__ pmass,
                                           unsigned char* smraw, const int p,
@@ -265,7 +276,7 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
                                           bool* wrote = nullptr) {
   using R = typename P::R;
   constexpr bool DEV = P::DEV;
-  using Lo = Layout<P, M>;
+  using Lo = Layout<P, M, DS>;
   constexpr int TT = Lo::TT, NE = Lo::NE, NEDGE = Lo::NEDGE;
   constexpr int TGW = MP + 2 * GF_NG, TG = TGW * TGW;  // patch tile
   constexpr int NS1 = MP / M, NSUB = NS1 * NS1;
@@ -484,6 +495,20 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
 
   R X[RC][3];   // nu_x * dQx of owned interior cells
   R Y[RC][3];   // nu_y * dQy
+  // dimensional splitting, deviation form: compensation terms of the
+  // intermediate state of owned interior cells
+  float LO1[DS && DEV ? RC : 1][3];
+  const float* los = nullptr;
+  float* lod = nullptr;
+  if constexpr (DEV) {
+    los = V.lof[cur] + (size_t)p * 3 * MP * MP;
+    lod = V.lof[cur ^ 1] + (size_t)p * 3 * MP * MP;
+  }
+  const bool corr = G.first_order == 0;              // limited corrections
+  const bool trv = !DS && G.no_transverse == 0;      // transverse terms
+  double clipd = 0.0;
+  float clipf = 0.0f;  // deviation form: clipped depth, FP32 per thread
+  unsigned nclip = 0, nwet = 0;
 
   // A tile without a wet cell (ghosts included) has only dry-dry edges: every
   // wave, correction and transverse term is zero and the update reduces to
@@ -493,12 +518,15 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
   // arithmetic of the two sweeps is resolved statically
   auto sweep = [&](auto dirc) {
     constexpr int dir = decltype(dirc)::value;
+    // lines swept: -1..M (unsplit), -2..M+1 (split, x), 0..M-1 (split, y)
+    constexpr int NRL = DS ? (dir == 0 ? M + 4 : M) : M + 2;
+    constexpr int L0 = DS ? (dir == 0 ? -2 : 0) : -1;
     const R* sn = dir == 0 ? shu : shv;  // normal momentum
     const R* st = dir == 0 ? shv : shu;  // transverse momentum
     const R nu = dir == 0 ? nux : nuy;
-    // phase 1: Riemann solves on lines -1..M, edges -1..M+1
-    for (int k = tid; k < Lo::NEDGE; k += NT) {
-      const int line = k / NE - 1, a = k % NE - 1;
+    // phase 1: Riemann solves on the lines, edges -1..M+1
+    for (int k = tid; k < NRL * NE; k += NT) {
+      const int line = k / NE + L0, a = k % NE - 1;
       const int cl = dir == 0 ? tix<M>(a - 1, line) : tix<M>(line, a - 1);
       const int cr = dir == 0 ? tix<M>(a, line) : tix<M>(line, a);
       R Z[9], S[3];
@@ -520,13 +548,13 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
 #pragma unroll
     for (int r = 0; r < RL; ++r) {
       const int k = tid + r * NT;
-      if (k < Lo::NLIM) {
-        const int line = k / (M + 1) - 1, a = k % (M + 1);
-        const int e = (line + 1) * NE + a + 1;
+      if (k < NRL * (M + 1)) {
+        const int line = k / (M + 1) + L0, a = k % (M + 1);
+        const int e = (line - L0) * NE + a + 1;
         const R* w = W + e;
         const int cl = dir == 0 ? tix<M>(a - 1, line) : tix<M>(line, a - 1);
         const int cr = dir == 0 ? tix<M>(a, line) : tix<M>(line, a);
-        const bool wet = wetc(cl) && wetc(cr);
+        const bool wet = corr && wetc(cl) && wetc(cr);
         gfk::edge_fluxes<R, NEDGE>(w, w + 9 * NEDGE, w - 1, w + 1, nu, wet, AMr[r],
                                    APr[r], FFr[r]);
         if (line >= 0 && line < M) {
@@ -546,9 +574,9 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
 #pragma unroll
     for (int r = 0; r < RL; ++r) {
       const int k = tid + r * NT;
-      if (k < Lo::NLIM) {
-        const int line = k / (M + 1) - 1, a = k % (M + 1);
-        R* w = W + ((line + 1) * NE + a + 1);
+      if (k < NRL * (M + 1)) {
+        const int line = k / (M + 1) + L0, a = k % (M + 1);
+        R* w = W + ((line - L0) * NE + a + 1);
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
           w[q * NEDGE] = AMr[r][q];
@@ -558,17 +586,18 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
       }
     }
     __syncthreads();
-    // phase 3: per-cell increments and their transverse split
+    // phase 3: per-cell increments and their transverse split (unsplit),
+    // or the intermediate state of the x sweep (split)
     R* Tr = dir == 0 ? Gtr : Ftr;
     R MIr[RX][3];
 #pragma unroll
     for (int r = 0; r < RX; ++r) {
       const int k = tid + r * NT;
-      if (k < Lo::NCELL) {
+      if (k < M * NRL) {
         int a, line;  // a: position along the sweep, line: across
-        cell_item<M>(k, dir, a, line);
-        const R* wl = W + ((line + 1) * NE + a + 1);  // edge a
-        const R* wr = wl + 1;                          // edge a+1
+        cell_item<M, NRL, L0>(k, dir, a, line);
+        const R* wl = W + ((line - L0) * NE + a + 1);  // edge a
+        const R* wr = wl + 1;                           // edge a+1
         R d[3];  // frame: mass, normal (sweep) momentum, transverse
 #pragma unroll
         for (int q = 0; q < 3; ++q)
@@ -582,6 +611,56 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
             Y[r][0] = nu * d[0]; Y[r][1] = nu * d[2]; Y[r][2] = nu * d[1];
           }
         }
+        if constexpr (DS) {
+          if constexpr (dir == 0) {
+            // intermediate state of cell (a, line) in place: every read of
+            // the window in this sweep is behind the barriers above
+            const int c = tix<M>(a, line);
+            const bool inner = k < M * M;
+            const R xs[3] = {nu * d[0], nu * d[1], nu * d[2]};
+            const R q[3] = {s0[c], shu[c], shv[c]};
+            R o[3];
+            if (inner) nwet += wetc(c) ? 1u : 0u;
+            if constexpr (!DEV) {
+#pragma unroll
+              for (int f = 0; f < 3; ++f) o[f] = q[f] - xs[f];
+              if (o[0] < R(0)) {
+                if (inner) { clipd -= o[0]; ++nclip; }
+                o[0] = R(0);
+              }
+              if (o[0] <= rdry) { o[1] = R(0); o[2] = R(0); }
+            } else {
+              const int kp = pix(a, line);
+              float lo[3];
+#pragma unroll
+              for (int f = 0; f < 3; ++f) {
+                const float x = (inner ? los[f * MP * MP + kp] : 0.0f) - xs[f];
+                const float s = q[f] + x;
+                const float bb = s - q[f];
+                lo[f] = (q[f] - (s - bb)) + (x - bb);
+                o[f] = s;
+              }
+              const float bc = sb[c];
+              if (o[0] < bc) {
+                if (inner) { clipf += bc - o[0]; ++nclip; }
+                o[0] = bc;
+                lo[0] = 0.0f;
+              }
+              const bool wnew = gfk::wet_dev(o[0], bc, drytol, dtf, margin);
+              if (!wnew) { o[1] = 0.0f; o[2] = 0.0f; lo[1] = 0.0f; lo[2] = 0.0f; }
+              sdep[c] = o[0] - bc;
+              swet[c] = wnew ? 1 : 0;
+              if (inner && r < RC) {
+                LO1[r][0] = lo[0]; LO1[r][1] = lo[1]; LO1[r][2] = lo[2];
+              }
+            }
+            s0[c] = o[0];
+            shu[c] = o[1];
+            shv[c] = o[2];
+          }
+          continue;
+        }
+        if (!trv) continue;
         // split along the other direction: in that frame the "along"
         // momentum is this sweep's transverse momentum
         const int ci = dir == 0 ? tix<M>(a, line) : tix<M>(line, a);
@@ -604,13 +683,14 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
       }
     }
     __syncthreads();
+    if (DS || !trv) return;
     const R nut = dir == 0 ? nux : nuy;
 #pragma unroll
     for (int r = 0; r < RX; ++r) {
       const int k = tid + r * NT;
-      if (k < Lo::NCELL) {
+      if (k < M * NRL) {
         int a, line;
-        cell_item<M>(k, dir, a, line);
+        cell_item<M, NRL, L0>(k, dir, a, line);
         if (line >= 0) {
           R* o = Tr + 3 * (a * (M + 1) + line);
 #pragma unroll
@@ -637,17 +717,9 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
 
   // ------------------------------------------------ update, friction, out
   const R mn = rscal[4];
-  double vol = 0.0, clipd = 0.0;
+  double vol = 0.0;
   R volr = R(0);
-  float clipf = 0.0f;  // deviation form: clipped depth, FP32 per thread
-  unsigned nclip = 0, nwet = 0;
   bool bad = false;
-  const float* los = nullptr;
-  float* lod = nullptr;
-  if constexpr (DEV) {
-    los = V.lof[cur] + (size_t)p * 3 * MP * MP;
-    lod = V.lof[cur ^ 1] + (size_t)p * 3 * MP * MP;
-  }
 #pragma unroll
   for (int r = 0; r < RC; ++r) {
     const int k = tid + r * NT;
@@ -671,16 +743,16 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
       else vol += s0[c];
       continue;
     }
-    const R q[3] = {s0[c], shu[c], shv[c]};
-    nwet += wetc(c) ? 1u : 0u;
+    const R q[3] = {s0[c], shu[c], shv[c]};  // split: the intermediate state
+    if (!DS) nwet += wetc(c) ? 1u : 0u;
     R o[3];
     if constexpr (!DEV) {
 #pragma unroll
       for (int f = 0; f < 3; ++f) {
-        const R fl = X[r][f] + Y[r][f];
+        const R fl = DS ? Y[r][f] : X[r][f] + Y[r][f];
         const R* fa = Ftr + 3 * (j * (M + 1) + i);
         const R* ga = Gtr + 3 * (i * (M + 1) + j);
-        const R tf = nux * (fa[3 + f] - fa[f]) + nuy * (ga[3 + f] - ga[f]);
+        const R tf = trv ? nux * (fa[3 + f] - fa[f]) + nuy * (ga[3 + f] - ga[f]) : R(0);
         o[f] = (q[f] - fl) - tf;
       }
       if (o[0] < R(0)) { clipd -= o[0]; o[0] = R(0); ++nclip; }
@@ -699,11 +771,13 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
       float lo[3];
 #pragma unroll
       for (int f = 0; f < 3; ++f) {
-        const float fl = X[r][f] + Y[r][f];
+        const float fl = DS ? Y[r][f] : X[r][f] + Y[r][f];
         const float* fa = Ftr + 3 * (j * (M + 1) + i);
         const float* ga = Gtr + 3 * (i * (M + 1) + j);
-        const float tf = nux * (fa[3 + f] - fa[f]) + nuy * (ga[3 + f] - ga[f]);
-        const float x = (los[f * MP * MP + kp] - fl) - tf;
+        const float tf =
+            trv ? nux * (fa[3 + f] - fa[f]) + nuy * (ga[3 + f] - ga[f]) : 0.0f;
+        const float lin = DS ? LO1[DS && DEV ? r : 0][f] : los[f * MP * MP + kp];
+        const float x = (lin - fl) - tf;
         const float s = q[f] + x;
         const float bb = s - q[f];
         lo[f] = (q[f] - (s - bb)) + (x - bb);
@@ -1104,7 +1178,7 @@ __global__ void __launch_bounds__(NT, MINB)
                     reinterpret_cast<double*>(smraw + Layout<P, M>::OFF_RED), NSUB, MP * MP);
 }
 
-template <class P, int MP, int M, int NT, int MINB>
+template <class P, int MP, int M, int NT, int MINB, bool DS = false>
 __global__ void __launch_bounds__(NT, MINB)
     k_patch_step(const __grid_constant__ GfGeom G,
                  const __grid_constant__ GfView V, double* __restrict__ pmass) {
@@ -1119,7 +1193,8 @@ __global__ void __launch_bounds__(NT, MINB)
   const GfPatch Pt = V.patch[p];
   int wet = 0;
   bool wrote = true;
-  if (V.ctl[Pt.scen].active) wet = patch_body<P, MP, M, NT>(G, V, pmass, smraw, p, sub, nullptr, &wrote);
+  if (V.ctl[Pt.scen].active)
+    wet = patch_body<P, MP, M, NT, DS>(G, V, pmass, smraw, p, sub, nullptr, &wrote);
   else wrote = false;
   if (sched && sub == 0 && threadIdx.x == 0) {
     int* nxt = par ? V.ord0 : V.ord1;
@@ -1128,27 +1203,27 @@ __global__ void __launch_bounds__(NT, MINB)
   }
   if (V.done)
     step_finish<NT>(G, V, pmass,
-                    reinterpret_cast<double*>(smraw + Layout<P, M>::OFF_RED),
+                    reinterpret_cast<double*>(smraw + Layout<P, M, DS>::OFF_RED),
                     NSUB, MP * MP, wrote);
 }
 
 // Launch the patch step on every patch: MP x MP patches, M x M sub-tiles
-// per CTA of NT threads (MINB CTAs per SM).  pmass holds (MP/M)^2 entries
-// per patch.
-template <class P, int MP, int M, int NT, int MINB>
+// per CTA of NT threads (MINB CTAs per SM), DS = dimensional splitting.
+// pmass holds (MP/M)^2 entries per patch.
+template <class P, int MP, int M, int NT, int MINB, bool DS = false>
 int launch_step(const GfGeom& g, const GfView& v, double* pmass,
                 cudaStream_t st) {
-  constexpr size_t bytes = Layout<P, M>::BYTES;
+  constexpr size_t bytes = Layout<P, M, DS>::BYTES;
   static bool attr = false;
   if (!attr) {
-    if (cudaFuncSetAttribute(k_patch_step<P, MP, M, NT, MINB>,
+    if (cudaFuncSetAttribute(k_patch_step<P, MP, M, NT, MINB, DS>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)bytes) != cudaSuccess)
       return -2;
     attr = true;
   }
   constexpr int NSUB = (MP / M) * (MP / M);
-  k_patch_step<P, MP, M, NT, MINB><<<v.npatch * NSUB, NT, bytes, st>>>(g, v, pmass);
+  k_patch_step<P, MP, M, NT, MINB, DS><<<v.npatch * NSUB, NT, bytes, st>>>(g, v, pmass);
   return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 

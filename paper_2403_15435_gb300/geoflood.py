@@ -53,6 +53,7 @@ class _Cfg(C.Structure):
         ("src_level", C.c_int), ("ngrades", C.c_int),
         ("tag_flux", C.c_double), ("grade_kind", C.c_int * 4),
         ("grade_value", C.c_double * 4), ("grade_level", C.c_int * 4),
+        ("first_order", C.c_int), ("no_transverse", C.c_int), ("dim_split", C.c_int),
     ]
 
 
@@ -148,7 +149,8 @@ def _p(a, t=C.c_double):
 def config_struct(cfg: inputs.Config, num_scenarios=1, max_patches=None,
                   max_gauges=64) -> _Cfg:
     c = _Cfg()
-    for name in ("mi", "mj", "mx", "minlevel", "maxlevel", "src_level", "precision"):
+    for name in ("mi", "mj", "mx", "minlevel", "maxlevel", "src_level", "precision",
+                 "first_order", "no_transverse", "dim_split"):
         setattr(c, name, int(getattr(cfg, name)))
     for name in ("xlower", "xupper", "ylower", "yupper", "g", "drytol",
                  "cfl_desired", "cfl_max", "dt_initial", "dt_max", "tag_depth",
