@@ -54,6 +54,9 @@ class _Cfg(C.Structure):
         ("grade_kind", C.c_int * 4), ("grade_value", C.c_double * 4),
         ("grade_level", C.c_int * 4),
         ("first_order", C.c_int), ("no_transverse", C.c_int), ("dim_split", C.c_int),
+        ("n_hydro", C.c_int), ("inflow_side", C.c_int),
+        ("inflow_lo", C.c_double), ("inflow_hi", C.c_double), ("inflow_tau", C.c_double),
+        ("hydro_t", C.c_double * 16), ("hydro_q", C.c_double * 16),
     ]
 
 
@@ -72,6 +75,10 @@ def lib():
             L.oracle_step_grid_ex.argtypes = ([C.c_int, C.c_int] + [dp] * 4 +
                                               [C.c_double] * 6 + [C.c_int] * 3 +
                                               [dp] * 4 + [C.POINTER(C.c_long), dp])
+            L.oracle_hydrograph.restype = C.c_double
+            L.oracle_hydrograph.argtypes = [C.POINTER(_Cfg), C.c_double]
+            L.oracle_inflow_depth.restype = C.c_double
+            L.oracle_inflow_depth.argtypes = [C.c_double] * 5 + [dp, dp]
             L.oracle_dem_average.restype = C.c_double
             L.oracle_dem_average.argtypes = [dp, C.c_int, C.c_int] + [C.c_double] * 8
             L.oracle_forest_new.restype = vp
@@ -108,6 +115,21 @@ def riemann(hL, nL, tL, bL, hR, nR, tR, bR, g=9.81, drytol=1e-3):
     s = np.zeros(3)
     lib().oracle_riemann(hL, nL, tL, bL, hR, nR, tR, bR, g, drytol, _p(Z), _p(s))
     return Z.reshape(3, 3), s
+
+
+def hydrograph(cfg, t):
+    """Discharge Q(t) of the configuration's inflow hydrograph (m^3/s)."""
+    c = _cfg_struct(cfg)
+    return lib().oracle_hydrograph(C.byref(c), float(t))
+
+
+def inflow_depth(q, h_int, qn_int, g=9.81, tau=1e-4):
+    """Ghost depth of the inflow boundary (Sec. 5.1, Eq. riemann / Eq.
+    2-shock) and the interior depth and speed the equations used."""
+    hu = C.c_double()
+    uu = C.c_double()
+    h = lib().oracle_inflow_depth(q, h_int, qn_int, g, tau, C.byref(hu), C.byref(uu))
+    return h, hu.value, uu.value
 
 
 def dem_average(dem, xa, xb, ya, yb):
@@ -158,6 +180,16 @@ def _cfg_struct(cfg) -> _Cfg:
     c.first_order = int(cfg.first_order)
     c.no_transverse = int(cfg.no_transverse)
     c.dim_split = int(cfg.dim_split)
+    hyd = list(cfg.hydrograph)
+    assert len(hyd) <= 16
+    c.n_hydro = len(hyd)
+    for k, (t, q) in enumerate(hyd):
+        c.hydro_t[k] = float(t)
+        c.hydro_q[k] = float(q)
+    c.inflow_side = int(cfg.inflow_side)
+    c.inflow_lo = float(cfg.inflow_lo)
+    c.inflow_hi = float(cfg.inflow_hi)
+    c.inflow_tau = float(cfg.inflow_tau)
     return c
 
 

@@ -717,6 +717,143 @@ static void fill_cell(const oracle_forest* f, int L, long I, long J, double bt,
   out[0] = hf; out[1] = huf; out[2] = hvf;
 }
 
+/* ---------------------------------------------------------------------- */
+/* Inflow hydrograph (Sec. 5.1, Test Case 1 set-up)                         */
+/* ---------------------------------------------------------------------- */
+
+double oracle_hydrograph(const oracle_config* c, double t) {
+  int n = c->n_hydro, k;
+  if (n <= 0) return 0.0;
+  if (t <= c->hydro_t[0]) return c->hydro_q[0];
+  if (t >= c->hydro_t[n - 1]) return c->hydro_q[n - 1];
+  for (k = 0; k + 1 < n; ++k)
+    if (t < c->hydro_t[k + 1]) break;
+  double a = (t - c->hydro_t[k]) / (c->hydro_t[k + 1] - c->hydro_t[k]);
+  return c->hydro_q[k] + (c->hydro_q[k + 1] - c->hydro_q[k]) * a;
+}
+
+/* Eq. riemann as F(h) = q/h - 2 sqrt(g h) - u_i + 2 sqrt(g h_i), and
+ * Eq. 2-shock as F(h) = q/h - u_i - (h - h_i) sqrt(g/2 (1/h + 1/h_i)); both
+ * decrease in h on the range searched.  Returns F, *dF its derivative. */
+static double inflow_eq(int shock, double h, double q, double hi, double ui,
+                        double g, double* dF) {
+  if (!shock) {
+    *dF = -q / (h * h) - sqrt(g / h);
+    return q / h - 2.0 * sqrt(g * h) - ui + 2.0 * sqrt(g * hi);
+  }
+  double S = sqrt(0.5 * g * (1.0 / h + 1.0 / hi));
+  *dF = -q / (h * h) - S + (h - hi) * g / (4.0 * h * h * S);
+  return q / h - ui - (h - hi) * S;
+}
+
+/* Newton's method from h0 for the root of a decreasing F above lo (F > 0
+ * just above lo).  The iterates are kept inside the bracket the signs of F
+ * have established so far; a Newton step that leaves it is replaced by the
+ * bracket's midpoint (or a doubling while no upper end is known). */
+static double inflow_newton(int shock, double h0, double lo, double q,
+                            double hi_, double ui, double g) {
+  double hi = INFINITY, h = h0 > lo ? h0 : 2.0 * lo;
+  int it;
+  for (it = 0; it < 100; ++it) {
+    double dF, F = inflow_eq(shock, h, q, hi_, ui, g, &dF);
+    if (F > 0.0) lo = h;
+    else if (F < 0.0) hi = h;
+    else return h;
+    double hn = h - F / dF;
+    if (!(hn > lo && hn < hi)) hn = isinf(hi) ? 2.0 * h : 0.5 * (lo + hi);
+    if (fabs(hn - h) <= 1e-14 * hn) return hn;
+    h = hn;
+  }
+  return h;
+}
+
+double oracle_inflow_depth(double q, double h_int, double qn_int, double g,
+                           double tau, double* h_used, double* u_used) {
+  double hi, ui;
+  if (h_int < tau) {
+    /* too thin an interior cell (dry included): critical depth of the
+     * inflow, at least tau, at rest */
+    double hc = cbrt(q * q / g);
+    hi = hc > tau ? hc : tau;
+    ui = 0.0;
+  } else {
+    hi = h_int;
+    ui = qn_int / h_int;
+  }
+  if (h_used) *h_used = hi;
+  if (u_used) *u_used = ui;
+  /* first guess [F q / sqrt(g)]^(2/3), F = 0.5 for Eq. riemann */
+  double h = inflow_newton(0, cbrt(0.25 * q * q / g), 0.0, q, hi, ui, g);
+  if (h > hi) h = inflow_newton(1, cbrt(q * q / g), hi, q, hi, ui, g);
+  return h;
+}
+
+/* Inflow ghosts of side `side` of tile p (a tile on that side) after all its
+ * mirrors are set: each
+ * row (or column) of the tile whose centre lies in the inflow segment and
+ * inside the domain gets, in both ghost layers, the depth of Eq. riemann /
+ * Eq. 2-shock from the tile's first cell of that line, the unit discharge
+ * normal to the side into the domain and no tangential momentum.  With no
+ * discharge the side's own rule stays. */
+static void fill_inflow(const oracle_forest* f, int p, int side) {
+  const oracle_config* c = &f->c;
+  double Q = oracle_hydrograph(c, f->t);
+  if (!(Q > 0.0)) return;
+  double q = Q / (c->inflow_hi - c->inflow_lo);
+  int L = f->lev[p], M = f->M, l, g;
+  size_t TT = (size_t)f->T * f->T;
+  double* t = f->tile[p];
+  int xs = side <= 1; /* the side is a left or right one: lines are rows */
+  long N = xs ? NYL(f, L) : NXL(f, L);
+  double d = xs ? DYL(f, L) : DXL(f, L);
+  double o = xs ? c->ylower : c->xlower;
+  long base = xs ? (long)f->py[p] * M : (long)f->px[p] * M;
+  double sg = (side == 0 || side == 2) ? 1.0 : -1.0;
+  for (l = -NG; l < M + NG; ++l) {
+    long J = base + l;
+    if (J < 0 || J >= N) continue;
+    double ctr = o + ((double)J + 0.5) * d;
+    if (!(ctr >= c->inflow_lo && ctr <= c->inflow_hi)) continue;
+    int a0 = (side == 0 || side == 2) ? 0 : M - 1; /* first interior cell */
+    size_t id = xs ? TI(f, a0, l) : TI(f, l, a0);
+    double hin = t[id];
+    double qn = sg * t[(xs ? 1 : 2) * TT + id];
+    double hg = oracle_inflow_depth(q, hin, qn, c->g, c->inflow_tau, NULL, NULL);
+    for (g = 1; g <= NG; ++g) {
+      int ag = (side == 0 || side == 2) ? -g : M - 1 + g;
+      size_t gid = xs ? TI(f, ag, l) : TI(f, l, ag);
+      t[gid] = hg;
+      t[(xs ? 1 : 2) * TT + gid] = sg * q;
+      t[(xs ? 2 : 1) * TT + gid] = 0.0;
+    }
+  }
+  /* where the tile also touches a side across the segment's lines, the
+   * corner ghosts beyond the segment's ghost cells follow that side's rule
+   * applied to them (wall: mirrored, its normal momentum negated;
+   * extrapolation: the nearest one copied), so a segment spanning a whole
+   * side next to walls leaves one-dimensional flow one-dimensional */
+  for (int end = 0; end < 2; ++end) {
+    int pside = xs ? 2 + end : end; /* the side across the lines */
+    int at = end == 0 ? base == 0 : base + M == N;
+    if (!at) continue;
+    int wall = c->bc[pside] == ORACLE_BC_WALL;
+    for (g = 1; g <= NG; ++g) {
+      int ag = (side == 0 || side == 2) ? -g : M - 1 + g;
+      for (int gl = 1; gl <= NG; ++gl) {
+        int lt = end == 0 ? -gl : M - 1 + gl;
+        int ls = wall ? (end == 0 ? gl - 1 : M - gl) : (end == 0 ? 0 : M - 1);
+        size_t dst = xs ? TI(f, ag, lt) : TI(f, lt, ag);
+        size_t src = xs ? TI(f, ag, ls) : TI(f, ls, ag);
+        for (int k = 0; k < 3; ++k) {
+          double v = t[k * TT + src];
+          if (wall && k == (xs ? 2 : 1)) v = -v;
+          t[k * TT + dst] = v;
+        }
+      }
+    }
+  }
+}
+
 /* Physical boundary ghosts of one patch tile (Sec. 5.1 closed walls):
  * bottom/top over columns inside the domain, then left/right over all rows.
  * Walls mirror the cells and negate the normal momentum; extrapolation copies
@@ -761,6 +898,16 @@ static void fill_bc(const oracle_forest* f, int p, int only_b) {
           q[k * TT + TI(f, ig, j)] = v;
         }
       }
+  }
+  /* the inflow segment's ghost cells last: the cells diagonal to the
+   * segment (tile corners) keep the mirrors of the side's own rule */
+  if (!only_b && f->c.n_hydro > 0) {
+    int side = f->c.inflow_side;
+    int at = side == 0   ? f->px[p] == 0
+             : side == 1 ? (long)(f->px[p] + 1) * M == NXL(f, L)
+             : side == 2 ? f->py[p] == 0
+                         : (long)(f->py[p] + 1) * M == NYL(f, L);
+    if (at) fill_inflow(f, p, side);
   }
 }
 

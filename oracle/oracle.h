@@ -53,9 +53,32 @@ typedef struct {
    * no_transverse the transverse terms, dim_split replaces the unsplit
    * update by an x sweep followed by a y sweep on its result */
   int first_order, no_transverse, dim_split;
+  /* inflow hydrograph (Sec. 5.1 set-up, Eq. riemann, Eq. 2-shock): with
+   * n_hydro > 0, the ghost cells of side inflow_side (0 left, 1 right,
+   * 2 bottom, 3 top) whose centre lies in [inflow_lo, inflow_hi] (the
+   * side's coordinate) carry the discharge Q(t) / (inflow_hi - inflow_lo)
+   * per unit width into the domain while Q(t) > 0; Q is piecewise linear
+   * through (hydro_t[k], hydro_q[k]), k < n_hydro <= 16, and constant
+   * beyond the first and last points; inflow_tau is the minimum interior
+   * depth of Sec. 5.1 */
+  int n_hydro, inflow_side;
+  double inflow_lo, inflow_hi, inflow_tau;
+  double hydro_t[16], hydro_q[16];
 } oracle_config;
 
 typedef struct oracle_forest oracle_forest;
+
+/* Discharge Q(t) of the inflow hydrograph (m^3/s). */
+double oracle_hydrograph(const oracle_config* cfg, double t);
+
+/* Ghost depth for the inflow boundary (Sec. 5.1): q > 0 the unit discharge
+ * into the domain, h_int and qn_int the depth and the momentum (into the
+ * domain) of the interior cell next to the ghost cell.  Solves Eq. riemann,
+ * and Eq. 2-shock if that depth exceeds the interior depth, by Newton's
+ * method.  *h_used and *u_used (may be NULL) receive the interior depth and
+ * speed the equations used (after the minimum-depth rule). */
+double oracle_inflow_depth(double q, double h_int, double qn_int, double g,
+                           double tau, double* h_used, double* u_used);
 
 /* One augmented Riemann solve at an edge in the normal frame (Sec. 3.3).
  * Inputs per side: depth h, normal momentum n, transverse momentum t, bed b.

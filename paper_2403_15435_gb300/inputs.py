@@ -64,6 +64,15 @@ class Config:
     first_order: int = 0
     no_transverse: int = 0
     dim_split: int = 0
+    # inflow hydrograph (Sec. 5.1): up to 16 (t, Q) points, Q the discharge
+    # in m^3/s through the segment [inflow_lo, inflow_hi] of side
+    # inflow_side (0 left, 1 right, 2 bottom, 3 top); () = no inflow;
+    # inflow_tau is the minimum interior depth of the boundary rule
+    hydrograph: Tuple[Tuple[float, float], ...] = ()
+    inflow_side: int = 0
+    inflow_lo: float = 0.0
+    inflow_hi: float = 0.0
+    inflow_tau: float = 1e-4
 
 
 @dataclasses.dataclass
@@ -268,6 +277,54 @@ def valley_2km(seed: int = SEED_BASE + 41, depth: float = 12.0,
     prob.cfg.src_level = 1
     prob.cfg.precision = precision
     return prob
+
+
+def inflow_channel(nx: int = 128, patch: int = 32, q: float = 2.0, h0: float = 1.0,
+                   t_end: float = 30.0) -> Problem:
+    """1D-in-2D bore from the inflow boundary (Sec. 5.1): a 640 m x 40 m
+    channel at rest at depth h0 over a flat bed, the whole left side an
+    inflow of unit discharge q (m^2/s), walls elsewhere, n = 0.  The exact
+    solution is a bore of the Eq. 2-shock state moving right."""
+    dx = 640.0 / nx
+    m = patch
+    rows = max(m, int(round(40.0 / dx)) // m * m)
+    cfg = Config(mi=nx // m, mj=rows // m, mx=m, xupper=640.0, yupper=rows * dx,
+                 drytol=1e-4, manning_n=0.0, dt_initial=0.2 * dx / 5.0,
+                 hydrograph=((0.0, q * rows * dx),), inflow_side=0,
+                 inflow_lo=0.0, inflow_hi=rows * dx, inflow_tau=1e-4)
+
+    def ic(x, y, b):
+        h = np.full_like(x, h0)
+        return h, np.zeros_like(h), np.zeros_like(h)
+
+    return Problem("inflow_channel", cfg, flat_dem(cfg), ic, t_end)
+
+
+def flood_speed(patch: int = 32, minlevel: int = 0, maxlevel: int = 3,
+                precision: int = 0, peak: float = 20.0, t_end: float = 21600.0) -> Problem:
+    """Synthetic stand-in for Test Case 1 (Sec. 5.1, flood propagation over
+    an extended floodplain): a flat, dry 1000 m x 2000 m plain, an inflow of
+    Q(t) through 20 m of the left side at its midline (990 <= y <= 1010):
+    Q rises linearly to `peak` m^3/s in 60 min, holds for 180 min and falls
+    to zero in the next 60 min; walls elsewhere, tau = drytol = 1e-4 m,
+    CFL 0.9, Manning n = 0.03, 6 h.  Blocks of 1000 m (1 x 2) with patches
+    of `patch` cells on levels minlevel..maxlevel (level 3 with 32-cell
+    patches: 3.9 m cells, the paper's 5 m being no power-of-two division of
+    the domain); refinement follows the wet region (tag_depth = tau) and the
+    inflow segment (source box, refined to maxlevel)."""
+    cfg = Config(mi=1, mj=2, mx=patch, minlevel=minlevel, maxlevel=maxlevel,
+                 xupper=1000.0, yupper=2000.0, drytol=1e-4, manning_n=0.03,
+                 dt_initial=1.0, tag_depth=1e-4, tag_speed=1e9, tag_deta=1e9,
+                 src_box=(0.0, 40.0, 970.0, 1030.0), src_level=maxlevel,
+                 precision=precision,
+                 hydrograph=((0.0, 0.0), (3600.0, peak), (14400.0, peak), (18000.0, 0.0)),
+                 inflow_side=0, inflow_lo=990.0, inflow_hi=1010.0, inflow_tau=1e-4)
+
+    def ic(x, y, b):
+        z = np.zeros_like(x)
+        return z, z.copy(), z.copy()
+
+    return Problem("flood_speed", cfg, flat_dem(cfg), ic, t_end)
 
 
 def valley_ensemble(n: int, seed: int = SEED_BASE + 4, precision: int = 1):
