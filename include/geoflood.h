@@ -107,6 +107,26 @@ typedef struct {
    * accordingly); the split update is stable up to 1.  With dim_split the
    * patch step has a single kernel variant. */
   int first_order, no_transverse, dim_split;
+  /* Inflow hydrograph (Sec. 5.1, Test Case 1 set-up; Eq. riemann, Eq.
+   * 2-shock).  n_hydro = 0: none.  Otherwise the discharge Q(t) (m^3/s) is
+   * piecewise linear through (hydro_t[k], hydro_q[k]), k < n_hydro <= 16,
+   * hydro_t strictly increasing, hydro_q >= 0, constant before the first
+   * and after the last point; it enters through the segment
+   * [inflow_lo, inflow_hi] of side inflow_side (GEOFLOOD_BC order: 0 left,
+   * 1 right, 2 bottom, 3 top; the coordinate along that side).  While
+   * Q(t) > 0, each ghost line of a tile whose centre lies in the segment
+   * carries, in both ghost layers, the unit discharge Q(t) / (inflow_hi -
+   * inflow_lo) normal to the side into the domain, no tangential momentum,
+   * and the depth that joins it to the tile's first cell of the line by a
+   * single entering wave: Eq. riemann, or Eq. 2-shock where that depth
+   * exceeds the interior's, solved by Newton's method (first guesses
+   * [F Q'/sqrt(g)]^(2/3), F = 0.5 and 1) safeguarded by bisection.  An
+   * interior cell thinner than inflow_tau (> 0) is replaced by the inflow's
+   * critical depth (at least inflow_tau) at rest.  With Q(t) = 0 the side's
+   * own rule applies.  The ghost values use the time of the state. */
+  int n_hydro, inflow_side;
+  double inflow_lo, inflow_hi, inflow_tau;
+  double hydro_t[16], hydro_q[16];
 } geoflood_config;
 
 typedef struct geoflood_ctx geoflood_ctx;

@@ -322,6 +322,148 @@ __global__ void k_ghost_fill(const __grid_constant__ GfGeom G, const __grid_cons
   tile_bc<T>(e, P, q, nullptr, 0);
 }
 
+// ------------------------------------------------------ inflow boundary
+
+// Discharge Q(t) of the inflow hydrograph: piecewise linear through the
+// points, constant before the first and after the last (Sec. 5.1).
+__device__ double hydro_discharge(const GfGeom& G, double t) {
+  const int n = G.n_hydro;
+  if (n <= 0) return 0.0;
+  if (t <= G.hydro_t[0]) return G.hydro_q[0];
+  if (t >= G.hydro_t[n - 1]) return G.hydro_q[n - 1];
+  int k = 0;
+  while (k + 1 < n && !(t < G.hydro_t[k + 1])) ++k;
+  const double a = (t - G.hydro_t[k]) / (G.hydro_t[k + 1] - G.hydro_t[k]);
+  return G.hydro_q[k] + (G.hydro_q[k + 1] - G.hydro_q[k]) * a;
+}
+
+// F(h) and F'(h) of the boundary equation: shock = false is Eq. riemann
+// (the ghost joined to the interior by a rarefaction entering the domain:
+// q/h - 2 sqrt(g h) = u_i - 2 sqrt(g h_i)), shock = true Eq. 2-shock (the
+// Hugoniot locus: q/h = u_i + (h - h_i) sqrt(g/2 (1/h + 1/h_i))).  Both
+// decrease in h where they are solved.
+__device__ double inflow_f(bool shock, double h, double q, double hi, double ui,
+                           double g, double* dF) {
+  if (!shock) {
+    *dF = -q / (h * h) - sqrt(g / h);
+    return q / h - 2.0 * sqrt(g * h) - ui + 2.0 * sqrt(g * hi);
+  }
+  const double S = sqrt(0.5 * g * (1.0 / h + 1.0 / hi));
+  *dF = -q / (h * h) - S + (h - hi) * g / (4.0 * h * h * S);
+  return q / h - ui - (h - hi) * S;
+}
+
+// Newton's method from h0 for the root above lo, safeguarded by the
+// bracket that the signs of F establish: a step leaving it is replaced by
+// the midpoint, or by a doubling while no upper end is known.  At most 100
+// iterations; stops when a step is below 1e-14 relative.
+__device__ double inflow_root(bool shock, double h0, double lo, double q, double hi_,
+                              double ui, double g) {
+  double hi = INFINITY, h = h0 > lo ? h0 : 2.0 * lo;
+  for (int it = 0; it < 100; ++it) {
+    double dF;
+    const double F = inflow_f(shock, h, q, hi_, ui, g, &dF);
+    if (F > 0.0) lo = h;
+    else if (F < 0.0) hi = h;
+    else return h;
+    double hn = h - F / dF;
+    if (!(hn > lo && hn < hi)) hn = isinf(hi) ? 2.0 * h : 0.5 * (lo + hi);
+    if (fabs(hn - h) <= 1e-14 * hn) return hn;
+    h = hn;
+  }
+  return h;
+}
+
+// Ghost depth for unit discharge q > 0 entering next to an interior cell of
+// depth h_int and momentum qn_int into the domain.  An interior thinner than
+// tau is replaced by the inflow's critical depth (at least tau) at rest.
+// Eq. riemann first (first guess [F q / sqrt(g)]^(2/3), F = 0.5); a depth
+// above the interior's is recomputed by Eq. 2-shock (F = 1).
+__device__ double inflow_depth(double q, double h_int, double qn_int, double g,
+                               double tau) {
+  double hi, ui;
+  if (h_int < tau) {
+    const double hc = cbrt(q * q / g);
+    hi = hc > tau ? hc : tau;
+    ui = 0.0;
+  } else {
+    hi = h_int;
+    ui = qn_int / h_int;
+  }
+  double h = inflow_root(false, cbrt(0.25 * q * q / g), 0.0, q, hi, ui, g);
+  if (h > hi) h = inflow_root(true, cbrt(q * q / g), hi, q, hi, ui, g);
+  return h;
+}
+
+// Inflow ghost cells, one CTA per patch on the inflow side, one thread per
+// line of its tile (rows for a left or right side, columns otherwise,
+// -2..M+1).  A line inside the domain whose centre lies in the segment
+// gets, in both ghost layers, the depth of the boundary equations from the
+// tile's first cell of that line, the unit discharge Q(t)/(hi - lo) normal
+// to the side into the domain and no tangential momentum; the tile corners
+// beyond those ghost cells, where the tile touches a side across the lines,
+// follow that side's rule applied to them.  With Q(t) = 0 the side's own
+// rule (written by the step and the other ghost kernels) stays.  Runs after
+// every other ghost cell of the tile is final.
+template <typename T>
+__global__ void k_inflow(const __grid_constant__ GfGeom G, const __grid_constant__ GfView V,
+                         const int* list, int only_accepted) {
+  const int p = list[blockIdx.x];
+  const int M = G.M, TT = G.T * G.T;
+  const int l = (int)threadIdx.x - GF_NG;
+  if (l >= M + GF_NG) return;
+  const GfPatch P = V.patch[p];
+  const GfCtl* C = V.ctl + P.scen;
+  if (only_accepted && !C->accepted) return;
+  const double Q = hydro_discharge(G, C->t);
+  if (!(Q > 0.0)) return;
+  Geo<T> e(G, V);
+  const int side = G.inflow_side;
+  const bool xs = side <= 1;  // left or right side: the lines are rows
+  const long long N = xs ? e.ny(P.level) : e.nx(P.level);
+  const double d = xs ? e.dy(P.level) : e.dx(P.level);
+  const double o = xs ? G.ylower : G.xlower;
+  const long long base = (long long)(xs ? P.py : P.px) * M;
+  const long long J = base + l;
+  if (J < 0 || J >= N) return;
+  const double ctr = o + ((double)J + 0.5) * d;
+  if (!(ctr >= G.inflow_lo && ctr <= G.inflow_hi)) return;
+  const double q = Q / (G.inflow_hi - G.inflow_lo);
+  const bool low = side == 0 || side == 2;
+  const double sg = low ? 1.0 : -1.0;
+  auto cell = [&](int a, int line) { return xs ? e.tix(a, line) : e.tix(line, a); };
+  T* qq = e.qp(p, C->cur);
+  const T* bb = e.bp(p);
+  const int nf = xs ? 1 : 2, tf = xs ? 2 : 1;  // normal, tangential field
+  const int ci = cell(low ? 0 : M - 1, l);
+  const double hin = Geo<T>::DEV ? (double)qq[ci] - (double)bb[ci] : (double)qq[ci];
+  const double qn = sg * (double)qq[nf * TT + ci];
+  const double hg = inflow_depth(q, hin, qn, G.g, G.inflow_tau);
+  const double mom[3] = {0.0, xs ? sg * q : 0.0, xs ? 0.0 : sg * q};
+  for (int g = 1; g <= GF_NG; ++g) {
+    const int c = cell(low ? -g : M - 1 + g, l);
+    e.store(qq, c, hg, mom[1], mom[2], (double)bb[c]);
+  }
+  for (int end = 0; end < 2; ++end) {
+    const int pside = xs ? 2 + end : end;
+    const bool at = end == 0 ? base == 0 : base + M == N;
+    if (!at) continue;
+    const bool wall = G.bc[pside] == 0;
+    for (int gl = 1; gl <= GF_NG; ++gl) {
+      const int ls = wall ? (end == 0 ? gl - 1 : M - gl) : (end == 0 ? 0 : M - 1);
+      if (ls != l) continue;
+      const int lt = end == 0 ? -gl : M - 1 + gl;
+      for (int g = 1; g <= GF_NG; ++g) {
+        const int a = low ? -g : M - 1 + g;
+        const int src = cell(a, l), dst = cell(a, lt);
+        qq[dst] = qq[src];
+        qq[nf * TT + dst] = qq[nf * TT + src];
+        qq[tf * TT + dst] = wall ? -qq[tf * TT + src] : qq[tf * TT + src];
+      }
+    }
+  }
+}
+
 // Ghost cells of one patch region without a same-level neighbour (a finer
 // or coarser leaf covers it), one thread per cell: regs[k] = patch * 8 +
 // region (left, right, bottom, top: 2 x M cells; corners: 2 x 2), filled
@@ -966,6 +1108,16 @@ int launch_ghost_rest(const GfGeom& g, const GfView& v, const int* regs, int nre
   return ok();
 }
 
+
+int launch_inflow(const GfGeom& g, const GfView& v, const int* list, int n,
+                  int only_accepted, void* stream) {
+  if (n <= 0 || g.n_hydro <= 0) return 0;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int nt = (g.T + 31) / 32 * 32;
+  if (v.prec) k_inflow<float><<<n, nt, 0, st>>>(g, v, list, only_accepted);
+  else k_inflow<double><<<n, nt, 0, st>>>(g, v, list, only_accepted);
+  return ok();
+}
 
 int launch_topo(const GfGeom& g, const GfView& v, int first, int count,
                 void* stream, const int* list) {

@@ -93,6 +93,8 @@ struct geoflood_ctx {
   int* d_rpairs = nullptr;  // regrid: (new, old) slots to copy
   int* d_glist[2] = {nullptr, nullptr};  // ghost regions next to a level change
   int nglist[2] = {0, 0};
+  int* d_ilist[2] = {nullptr, nullptr};  // patches on the inflow side
+  int nilist[2] = {0, 0};
   bool own_stream = false;
   // CUDA graphs of chunks of steps, keyed by chunk length
   struct Graph {
@@ -289,6 +291,31 @@ int upload_tables(geoflood_ctx* ctx, int t,
   if (!gl.empty())
     CK(cudaMemcpyAsync(ctx->d_glist[t], gl.data(), sizeof(int) * gl.size(),
                        cudaMemcpyHostToDevice, ctx->st));
+  // patches on the inflow side whose tile lines (ghost lines included) may
+  // reach the inflow segment
+  std::vector<int> il;
+  const GfGeom& G = ctx->G;
+  if (G.n_hydro > 0) {
+    const bool xs = G.inflow_side <= 1;
+    for (size_t k = 0; k < total; ++k) {
+      const GfPatch& P = hp[k];
+      const long long w = (long long)G.mi << P.level, h = (long long)G.mj << P.level;
+      const bool at = G.inflow_side == 0   ? P.px == 0
+                      : G.inflow_side == 1 ? P.px == w - 1
+                      : G.inflow_side == 2 ? P.py == 0
+                                           : P.py == h - 1;
+      if (!at) continue;
+      const double lo = xs ? G.ylower : G.xlower, hi = xs ? G.yupper : G.xupper;
+      const double d = (hi - lo) / (double)((xs ? h : w) * G.M);
+      const double a = lo + ((double)(xs ? P.py : P.px) * G.M - GF_NG) * d;
+      const double b = a + (double)(G.M + 2 * GF_NG) * d;
+      if (b >= G.inflow_lo && a <= G.inflow_hi) il.push_back((int)k);
+    }
+  }
+  ctx->nilist[t] = (int)il.size();
+  if (!il.empty())
+    CK(cudaMemcpyAsync(ctx->d_ilist[t], il.data(), sizeof(int) * il.size(),
+                       cudaMemcpyHostToDevice, ctx->st));
   // a new patch list: launch order back to patch order, no tile known to
   // agree between the buffers
   std::vector<int> iota(total);
@@ -339,8 +366,14 @@ int ghost_fill_all(geoflood_ctx* ctx) {
   ProfRec r;
   prof_begin(ctx, "ghost_fill", &r);
   CKL(gf::launch_ghost_fill(ctx->G, view(ctx), 0, ctx->st), "ghost_fill");
-  prof_end(ctx, "ghost_fill", &r);
   ctx->launches++;
+  if (ctx->nilist[ctx->tsel] > 0) {
+    CKL(gf::launch_inflow(ctx->G, view(ctx), ctx->d_ilist[ctx->tsel],
+                          ctx->nilist[ctx->tsel], 0, ctx->st),
+        "inflow");
+    ctx->launches++;
+  }
+  prof_end(ctx, "ghost_fill", &r);
   return check_errflag(ctx);
 }
 
@@ -488,6 +521,16 @@ int geoflood_init_forest(const geoflood_config* cfg, void* stream,
       return GEOFLOOD_ERR_ARG;
   if (c.ngrades < 0 || c.ngrades > 4 || !(c.tag_flux > 0)) return GEOFLOOD_ERR_ARG;
   if ((c.first_order | c.no_transverse | c.dim_split) & ~1) return GEOFLOOD_ERR_ARG;
+  if (c.n_hydro < 0 || c.n_hydro > 16) return GEOFLOOD_ERR_ARG;
+  if (c.n_hydro > 0) {
+    if (c.inflow_side < 0 || c.inflow_side > 3 || !(c.inflow_hi > c.inflow_lo) ||
+        !(c.inflow_tau > 0))
+      return GEOFLOOD_ERR_ARG;
+    for (int k = 0; k < c.n_hydro; ++k)
+      if (!(c.hydro_q[k] >= 0 && c.hydro_q[k] < 1e300) || !(c.hydro_t[k] > -1e300 && c.hydro_t[k] < 1e300) ||
+          (k > 0 && !(c.hydro_t[k] > c.hydro_t[k - 1])))
+        return GEOFLOOD_ERR_ARG;
+  }
   for (int k = 0; k < c.ngrades; ++k)
     if ((c.grade_kind[k] != 0 && c.grade_kind[k] != 1) || c.grade_level[k] < c.minlevel ||
         c.grade_level[k] > c.maxlevel)
@@ -550,6 +593,15 @@ int geoflood_init_forest(const geoflood_config* cfg, void* stream,
   G.first_order = c.first_order;
   G.no_transverse = c.no_transverse;
   G.dim_split = c.dim_split;
+  G.n_hydro = c.n_hydro;
+  G.inflow_side = c.inflow_side;
+  G.inflow_lo = c.inflow_lo;
+  G.inflow_hi = c.inflow_hi;
+  G.inflow_tau = c.inflow_tau;
+  for (int k = 0; k < 16; ++k) {
+    G.hydro_t[k] = k < c.n_hydro ? c.hydro_t[k] : 0.0;
+    G.hydro_q[k] = k < c.n_hydro ? c.hydro_q[k] : 0.0;
+  }
 
   const size_t TT = (size_t)G.T * G.T;
   const size_t cap = (size_t)ctx->cap;
@@ -588,6 +640,8 @@ int geoflood_init_forest(const geoflood_config* cfg, void* stream,
   okk &= alloc((void**)&ctx->d_rpairs, cap * 2 * sizeof(int));
   okk &= alloc((void**)&ctx->d_glist[0], cap * 8 * sizeof(int));
   okk &= alloc((void**)&ctx->d_glist[1], cap * 8 * sizeof(int));
+  okk &= alloc((void**)&ctx->d_ilist[0], cap * sizeof(int));
+  okk &= alloc((void**)&ctx->d_ilist[1], cap * sizeof(int));
   okk &= alloc((void**)&ctx->d_lut[0], (size_t)ctx->nscen * G.lut_per_scen * sizeof(int));
   okk &= alloc((void**)&ctx->d_lut[1], (size_t)ctx->nscen * G.lut_per_scen * sizeof(int));
   okk &= alloc((void**)&ctx->d_scen, ctx->nscen * sizeof(GfScenario));
@@ -674,6 +728,8 @@ void geoflood_destroy(geoflood_ctx* ctx) {
   cudaFree(ctx->d_rpairs);
   cudaFree(ctx->d_glist[0]);
   cudaFree(ctx->d_glist[1]);
+  cudaFree(ctx->d_ilist[0]);
+  cudaFree(ctx->d_ilist[1]);
   cudaFree(ctx->d_scen);
   cudaFree(ctx->d_ctl);
   cudaFree(ctx->d_pmass);
@@ -960,6 +1016,8 @@ int geoflood_step(geoflood_ctx* ctx, double t_target, int max_steps,
       }
       lrc |= gf::launch_ghost_rest(ctx->G, v, ctx->d_glist[ctx->tsel], ctx->nglist[ctx->tsel],
                                    ctx->st);
+      lrc |= gf::launch_inflow(ctx->G, v, ctx->d_ilist[ctx->tsel], ctx->nilist[ctx->tsel], 1,
+                               ctx->st);
       if (sample) {
         cudaEventRecordWithFlags(rg.b, ctx->st, cudaEventRecordExternal);
         gr->evg.push_back(rg);
@@ -994,7 +1052,8 @@ int geoflood_step(geoflood_ctx* ctx, double t_target, int max_steps,
     gr->prof = prof;
     gr->variant = ctx->variant;
   }
-  const int per_step = 1 + (ctx->nglist[ctx->tsel] > 0 ? 1 : 0);
+  const int per_step = 1 + (ctx->nglist[ctx->tsel] > 0 ? 1 : 0) +
+                       (ctx->nilist[ctx->tsel] > 0 ? 1 : 0);
   long long launched = 0;
   const long long limit = (long long)max_steps * 2 + 64;
   while (max_steps > 0) {

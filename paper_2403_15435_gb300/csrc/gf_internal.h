@@ -89,6 +89,11 @@ struct GfGeom {
   float grade_valuef[4];
   // scheme variants (Sec. 3.2); all 0: second order, unsplit, transverse
   int first_order, no_transverse, dim_split;
+  // inflow hydrograph (Sec. 5.1): n_hydro points (0 = none) of the
+  // discharge through [inflow_lo, inflow_hi] of side inflow_side
+  int n_hydro, inflow_side;
+  double inflow_lo, inflow_hi, inflow_tau;
+  double hydro_t[16], hydro_q[16];
 };
 
 // Everything a kernel needs to find patches and their data.
@@ -175,6 +180,11 @@ int launch_ghost_fill(const GfGeom& g, const GfView& v, int only_active,
 // region, k < nreg.
 int launch_ghost_rest(const GfGeom& g, const GfView& v, const int* regs, int nreg,
                       void* stream);
+// Inflow ghost cells (Sec. 5.1) of the n patches in list (patches on the
+// inflow side), after every other ghost cell is final; only_accepted: skip
+// scenarios whose last step was rejected.
+int launch_inflow(const GfGeom& g, const GfView& v, const int* list, int n,
+                  int only_accepted, void* stream);
 // Beds of patches [first, first + count), or of list[0..count) if list.
 int launch_topo(const GfGeom& g, const GfView& v, int first, int count,
                 void* stream, const int* list = nullptr);

@@ -54,6 +54,9 @@ class _Cfg(C.Structure):
         ("tag_flux", C.c_double), ("grade_kind", C.c_int * 4),
         ("grade_value", C.c_double * 4), ("grade_level", C.c_int * 4),
         ("first_order", C.c_int), ("no_transverse", C.c_int), ("dim_split", C.c_int),
+        ("n_hydro", C.c_int), ("inflow_side", C.c_int),
+        ("inflow_lo", C.c_double), ("inflow_hi", C.c_double), ("inflow_tau", C.c_double),
+        ("hydro_t", C.c_double * 16), ("hydro_q", C.c_double * 16),
     ]
 
 
@@ -168,6 +171,17 @@ def config_struct(cfg: inputs.Config, num_scenarios=1, max_patches=None,
         c.grade_kind[k] = int(kind)
         c.grade_value[k] = float(value)
         c.grade_level[k] = int(level)
+    hyd = list(getattr(cfg, "hydrograph", ()))
+    if len(hyd) > 16:
+        raise ValueError("at most 16 hydrograph points")
+    c.n_hydro = len(hyd)
+    for k, (t, q) in enumerate(hyd):
+        c.hydro_t[k] = float(t)
+        c.hydro_q[k] = float(q)
+    c.inflow_side = int(getattr(cfg, "inflow_side", 0))
+    c.inflow_lo = float(getattr(cfg, "inflow_lo", 0.0))
+    c.inflow_hi = float(getattr(cfg, "inflow_hi", 0.0))
+    c.inflow_tau = float(getattr(cfg, "inflow_tau", 1e-4))
     c.num_scenarios = int(num_scenarios)
     if max_patches is None:
         per = cfg.mi * cfg.mj * (4 ** cfg.maxlevel)

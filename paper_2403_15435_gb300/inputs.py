@@ -315,7 +315,7 @@ def flood_speed(patch: int = 32, minlevel: int = 0, maxlevel: int = 3,
     cfg = Config(mi=1, mj=2, mx=patch, minlevel=minlevel, maxlevel=maxlevel,
                  xupper=1000.0, yupper=2000.0, drytol=1e-4, manning_n=0.03,
                  dt_initial=1.0, tag_depth=1e-4, tag_speed=1e9, tag_deta=1e9,
-                 src_box=(0.0, 40.0, 970.0, 1030.0), src_level=maxlevel,
+                 src_box=(0.0, 100.0, 900.0, 1100.0), src_level=maxlevel,
                  precision=precision,
                  hydrograph=((0.0, 0.0), (3600.0, peak), (14400.0, peak), (18000.0, 0.0)),
                  inflow_side=0, inflow_lo=990.0, inflow_hi=1010.0, inflow_tau=1e-4)

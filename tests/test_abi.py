@@ -37,7 +37,7 @@ def test_config_struct_matches_header():
     hdr = open(os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "geoflood.h")).read()
     body = hdr[hdr.index("typedef struct {"):hdr.index("} geoflood_config;")]
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
-    fields = re.findall(r"\b([a-z_0-9]+)(?:\[\d\])?[,;]", body)
+    fields = re.findall(r"\b([a-z_0-9]+)(?:\[\d+\])?[,;]", body)
     assert [f[0] for f in geoflood._Cfg._fields_] == fields
 
 
