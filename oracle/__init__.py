@@ -79,6 +79,10 @@ def lib():
             L.oracle_hydrograph.argtypes = [C.POINTER(_Cfg), C.c_double]
             L.oracle_inflow_depth.restype = C.c_double
             L.oracle_inflow_depth.argtypes = [C.c_double] * 5 + [dp, dp]
+            L.oracle_dems_average.restype = C.c_double
+            L.oracle_dems_average.argtypes = ([C.c_int, C.POINTER(dp), ip, ip] + [dp] * 4 +
+                                              [C.c_double] * 4)
+            L.oracle_forest_set_topos.argtypes = [vp, C.c_int, C.POINTER(dp), ip, ip] + [dp] * 4
             L.oracle_dem_average.restype = C.c_double
             L.oracle_dem_average.argtypes = [dp, C.c_int, C.c_int] + [C.c_double] * 8
             L.oracle_forest_new.restype = vp
@@ -130,6 +134,23 @@ def inflow_depth(q, h_int, qn_int, g=9.81, tau=1e-4):
     uu = C.c_double()
     h = lib().oracle_inflow_depth(q, h_int, qn_int, g, tau, C.byref(hu), C.byref(uu))
     return h, hu.value, uu.value
+
+
+def _dem_arrays(dems):
+    zs = [np.ascontiguousarray(d.z, dtype=np.float64) for d in dems]
+    n = len(zs)
+    zp = (C.POINTER(C.c_double) * n)(*[_p(z) for z in zs])
+    ints = lambda v: (C.c_int * n)(*v)
+    dbl = lambda v: (C.c_double * n)(*v)
+    return (zs, n, zp, ints([z.shape[1] for z in zs]), ints([z.shape[0] for z in zs]),
+            dbl([d.x0 for d in dems]), dbl([d.y0 for d in dems]),
+            dbl([d.dx for d in dems]), dbl([d.dy for d in dems]))
+
+
+def dems_average(dems, xa, xb, ya, yb):
+    """Cell average of the composite interpolant of several DEMs (Sec. 6.2)."""
+    zs, n, zp, nx, ny, x0, y0, dx, dy = _dem_arrays(dems)
+    return lib().oracle_dems_average(n, zp, nx, ny, x0, y0, dx, dy, xa, xb, ya, yb)
 
 
 def dem_average(dem, xa, xb, ya, yb):
@@ -213,6 +234,11 @@ class OracleForest:
     __del__ = close
 
     def set_topo(self, dem):
+        if isinstance(dem, (list, tuple)):
+            zs, n, zp, nx, ny, x0, y0, dx, dy = _dem_arrays(dem)
+            rc = lib().oracle_forest_set_topos(self._h, n, zp, nx, ny, x0, y0, dx, dy)
+            assert rc == 0
+            return
         z = np.ascontiguousarray(dem.z, dtype=np.float64)
         ny, nx = z.shape
         rc = lib().oracle_forest_set_topo(self._h, _p(z), nx, ny, dem.x0,

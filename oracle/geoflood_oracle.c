@@ -508,16 +508,83 @@ static int dem_breaks(double a, double b, double o, double d, int n,
   return m;
 }
 
-double oracle_dem_average(const double* z, int nx, int ny, double x0,
-                          double y0, double dx, double dy, double xa,
-                          double xb, double ya, double yb) {
-  /* The interpolant is bilinear on every piece of the partition, so its
-   * integral over a piece is the piece area times its midpoint value. */
-  size_t cx = (size_t)((xb - xa) / dx) + 8, cy = (size_t)((yb - ya) / dy) + 8;
-  double* xs = (double*)malloc(sizeof(double) * cx);
-  double* ys = (double*)malloc(sizeof(double) * cy);
-  int mx = dem_breaks(xa, xb, x0, dx, nx, xs);
-  int my = dem_breaks(ya, yb, y0, dy, ny, ys);
+/* Priority order of n DEMs (Sec. 6.2: several overlapping DEMs of different
+ * resolutions): the finer node spacing (smaller dx * dy) first, equal
+ * spacings in the given order. */
+static void dem_order(int n, const double* dx, const double* dy, int* ord) {
+  int i, j;
+  for (i = 0; i < n; ++i) ord[i] = i;
+  for (i = 1; i < n; ++i) /* insertion sort: stable */
+    for (j = i; j > 0 && dx[ord[j]] * dy[ord[j]] < dx[ord[j - 1]] * dy[ord[j - 1]]; --j) {
+      int t = ord[j]; ord[j] = ord[j - 1]; ord[j - 1] = t;
+    }
+}
+
+static int cmp_double(const void* a, const void* b) {
+  double x = *(const double*)a, y = *(const double*)b;
+  return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+/* Sorted distinct break points of [a, b]: its ends and every DEM's node
+ * lines strictly inside it.  Returns the count. */
+static int dems_breaks(int n, const int* ord, const double* o, const double* d,
+                       const int* nn, double a, double b, double** out) {
+  size_t cap = 2;
+  int k, m = 0;
+  for (k = 0; k < n; ++k) cap += (size_t)((b - a) / d[ord[k]]) + 4;
+  double* v = (double*)malloc(sizeof(double) * cap);
+  v[m++] = a;
+  for (k = 0; k < n; ++k) {
+    int q = ord[k];
+    int lo = (int)floor((a - o[q]) / d[q]) - 1, hi = (int)ceil((b - o[q]) / d[q]) + 1;
+    if (lo < 0) lo = 0;
+    if (hi > nn[q] - 1) hi = nn[q] - 1;
+    for (int i = lo; i <= hi; ++i) {
+      double xn = o[q] + (double)i * d[q];
+      if (xn > a && xn < b) v[m++] = xn;
+    }
+  }
+  v[m++] = b;
+  qsort(v, (size_t)m, sizeof(double), cmp_double);
+  int u = 0;
+  for (k = 0; k < m; ++k)
+    if (u == 0 || v[k] != v[u - 1]) v[u++] = v[k];
+  *out = v;
+  return u;
+}
+
+/* Composite interpolant at (x, y): the bilinear interpolant of the first
+ * DEM in priority order whose extent (closed, node to node) holds the
+ * point; outside every extent the last one's, extended as a constant
+ * beyond its edges. */
+static double dems_eval(int n, const int* ord, const double* const* z,
+                        const int* nx, const int* ny, const double* x0,
+                        const double* y0, const double* dx, const double* dy,
+                        double x, double y) {
+  int k;
+  for (k = 0; k < n; ++k) {
+    int q = ord[k];
+    double xe = x0[q] + (double)(nx[q] - 1) * dx[q];
+    double ye = y0[q] + (double)(ny[q] - 1) * dy[q];
+    if (x >= x0[q] && x <= xe && y >= y0[q] && y <= ye) break;
+  }
+  int q = ord[k < n ? k : n - 1];
+  return dem_eval(z[q], nx[q], ny[q], x0[q], y0[q], dx[q], dy[q], x, y);
+}
+
+double oracle_dems_average(int n, const double* const* z, const int* nx,
+                           const int* ny, const double* x0, const double* y0,
+                           const double* dx, const double* dy, double xa,
+                           double xb, double ya, double yb) {
+  /* Every DEM's node lines (and hence every extent edge) are break points,
+   * so the composite interpolant is bilinear on each piece of the partition
+   * and its integral over a piece is the piece area times its midpoint
+   * value (the integral that the AMR keeps under refinement, Sec. 6.2). */
+  int ord[ORACLE_MAXDEM];
+  double *xs, *ys;
+  dem_order(n, dx, dy, ord);
+  int mx = dems_breaks(n, ord, x0, dx, nx, xa, xb, &xs);
+  int my = dems_breaks(n, ord, y0, dy, ny, ya, yb, &ys);
   double sum = 0.0;
   int k, l;
   for (l = 0; l + 1 < my; ++l)
@@ -525,11 +592,18 @@ double oracle_dem_average(const double* z, int nx, int ny, double x0,
       double xm = 0.5 * (xs[k] + xs[k + 1]);
       double ym = 0.5 * (ys[l] + ys[l + 1]);
       double w = (xs[k + 1] - xs[k]) * (ys[l + 1] - ys[l]);
-      sum += w * dem_eval(z, nx, ny, x0, y0, dx, dy, xm, ym);
+      sum += w * dems_eval(n, ord, z, nx, ny, x0, y0, dx, dy, xm, ym);
     }
   free(xs);
   free(ys);
   return sum / ((xb - xa) * (yb - ya));
+}
+
+double oracle_dem_average(const double* z, int nx, int ny, double x0,
+                          double y0, double dx, double dy, double xa,
+                          double xb, double ya, double yb) {
+  const double* zz[1] = {z};
+  return oracle_dems_average(1, zz, &nx, &ny, &x0, &y0, &dx, &dy, xa, xb, ya, yb);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -544,9 +618,10 @@ struct oracle_forest {
   double** tile; /* per patch: h, hu, hv, b, each T*T */
   int* lut[MAXLEV];
   int lutw[MAXLEV], luth[MAXLEV];
-  double* dem;
-  int dnx, dny;
-  double dx0, dy0, ddx, ddy;
+  int ndem; /* DEMs (0: flat bed at 0) */
+  double* dem[ORACLE_MAXDEM];
+  int dnx[ORACLE_MAXDEM], dny[ORACLE_MAXDEM];
+  double dx0[ORACLE_MAXDEM], dy0[ORACLE_MAXDEM], ddx[ORACLE_MAXDEM], ddy[ORACLE_MAXDEM];
   double t, dt_next;
   long steps, rejects, nclip;
   double clipvol; /* volume added by resetting negative depths to zero */
@@ -924,13 +999,13 @@ static void fill_topo(oracle_forest* f, int p) {
       long I = (long)f->px[p] * M + i, J = (long)f->py[p] * M + j;
       double v = 0.0;
       if (I >= 0 && J >= 0 && I < NX && J < NY) {
-        if (f->dem) {
+        if (f->ndem > 0) {
           double xa = f->c.xlower + (double)I * dx;
           double xb = f->c.xlower + (double)(I + 1) * dx;
           double ya = f->c.ylower + (double)J * dy;
           double yb = f->c.ylower + (double)(J + 1) * dy;
-          v = oracle_dem_average(f->dem, f->dnx, f->dny, f->dx0, f->dy0, f->ddx,
-                                 f->ddy, xa, xb, ya, yb);
+          v = oracle_dems_average(f->ndem, (const double* const*)f->dem, f->dnx, f->dny,
+                                  f->dx0, f->dy0, f->ddx, f->ddy, xa, xb, ya, yb);
         }
       }
       f->tile[p][3 * TT + TI(f, i, j)] = v;
@@ -1035,20 +1110,36 @@ void oracle_forest_free(oracle_forest* f) {
   for (k = 0; k < f->np; ++k) free(f->tile[k]);
   free(f->tile); free(f->lev); free(f->px); free(f->py);
   for (k = 0; k < MAXLEV; ++k) free(f->lut[k]);
-  free(f->dem); free(f->gxy); free(f->gout); free(f->garr);
+  for (int k = 0; k < f->ndem; ++k) free(f->dem[k]);
+  free(f->gxy); free(f->gout); free(f->garr);
   free(f);
+}
+
+int oracle_forest_set_topos(oracle_forest* f, int n, const double* const* z,
+                            const int* nx, const int* ny, const double* x0,
+                            const double* y0, const double* dx,
+                            const double* dy) {
+  int k;
+  if (n < 1 || n > ORACLE_MAXDEM) return -1;
+  for (k = 0; k < n; ++k)
+    if (!z[k] || nx[k] < 2 || ny[k] < 2 || !(dx[k] > 0.0) || !(dy[k] > 0.0)) return -1;
+  for (k = 0; k < f->ndem; ++k) free(f->dem[k]);
+  for (k = 0; k < n; ++k) {
+    size_t m = (size_t)nx[k] * ny[k];
+    f->dem[k] = (double*)malloc(sizeof(double) * m);
+    memcpy(f->dem[k], z[k], sizeof(double) * m);
+    f->dnx[k] = nx[k]; f->dny[k] = ny[k];
+    f->dx0[k] = x0[k]; f->dy0[k] = y0[k]; f->ddx[k] = dx[k]; f->ddy[k] = dy[k];
+  }
+  f->ndem = n;
+  for (k = 0; k < f->np; ++k) fill_topo(f, k);
+  return 0;
 }
 
 int oracle_forest_set_topo(oracle_forest* f, const double* z, int nx, int ny,
                            double x0, double y0, double dx, double dy) {
-  int k;
-  if (nx < 2 || ny < 2 || !(dx > 0.0) || !(dy > 0.0)) return -1;
-  free(f->dem);
-  f->dem = (double*)malloc(sizeof(double) * (size_t)nx * ny);
-  memcpy(f->dem, z, sizeof(double) * (size_t)nx * ny);
-  f->dnx = nx; f->dny = ny; f->dx0 = x0; f->dy0 = y0; f->ddx = dx; f->ddy = dy;
-  for (k = 0; k < f->np; ++k) fill_topo(f, k);
-  return 0;
+  const double* zz[1] = {z};
+  return oracle_forest_set_topos(f, 1, zz, &nx, &ny, &x0, &y0, &dx, &dy);
 }
 
 int oracle_forest_npatch(const oracle_forest* f) { return f->np; }

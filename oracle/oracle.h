@@ -21,6 +21,7 @@
 extern "C" {
 #endif
 
+#define ORACLE_MAXDEM 4 /* DEMs per forest */
 #define ORACLE_BC_WALL 0
 #define ORACLE_BC_EXTRAP 1
 
@@ -112,10 +113,25 @@ double oracle_dem_average(const double* z, int nx, int ny, double x0,
                           double y0, double dx, double dy, double xa,
                           double xb, double ya, double yb);
 
+/* Cell average of the composite interpolant of n <= ORACLE_MAXDEM
+ * overlapping DEMs (Sec. 6.2): at each point the bilinear interpolant of the
+ * finest DEM (smallest dx * dy; equal spacings in the given order) whose
+ * node-to-node extent holds it; outside every extent the coarsest one's,
+ * constant beyond its edges. */
+double oracle_dems_average(int n, const double* const* z, const int* nx,
+                           const int* ny, const double* x0, const double* y0,
+                           const double* dx, const double* dy, double xa,
+                           double xb, double ya, double yb);
+
 oracle_forest* oracle_forest_new(const oracle_config* cfg);
 void oracle_forest_free(oracle_forest* f);
 int oracle_forest_set_topo(oracle_forest* f, const double* z, int nx, int ny,
                            double x0, double y0, double dx, double dy);
+/* Several DEMs (arrays per DEM), composed as in oracle_dems_average. */
+int oracle_forest_set_topos(oracle_forest* f, int n, const double* const* z,
+                            const int* nx, const int* ny, const double* x0,
+                            const double* y0, const double* dx,
+                            const double* dy);
 int oracle_forest_npatch(const oracle_forest* f);
 void oracle_forest_patch_info(const oracle_forest* f, int* level, int* px,
                               int* py);

@@ -15,7 +15,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
-from typing import Callable, Optional, Sequence, Tuple
+from typing import Callable, List, Optional, Sequence, Tuple
 
 import numpy as np
 
@@ -160,6 +160,51 @@ def value_noise(X: np.ndarray, Y: np.ndarray, seed: int, octaves: int,
         wl *= 0.5
     peak = np.abs(out).max()
     return out / peak if peak > 0 else out
+
+
+def nested_dems(cfg: Config, seed: int, boxes, spacings,
+                relief: float = 3.0) -> List[Dem]:
+    """Overlapping DEMs of one seeded terrain at several resolutions (Sec.
+    6.2: 2, 5 and 20 m DEMs over parts of the Malpasset domain): DEM k
+    samples, at spacing spacings[k] over boxes[k] (x0, x1, y0, y1; None =
+    the whole domain; widened outward to whole spacings), a valley across y
+    with a slope along x plus octaves of value noise anchored to the domain
+    (wavelengths 256 m, 128 m, ...) down to four node spacings of that DEM.
+    Finer DEMs therefore carry detail the coarser ones leave out."""
+    W = cfg.yupper - cfg.ylower
+    lat = []
+
+    def noise(X, Y, octaves):
+        out = np.zeros_like(X)
+        for o in range(octaves):
+            wl = 256.0 / 2 ** o
+            gx = int(math.ceil((cfg.xupper - cfg.xlower) / wl)) + 3
+            gy = int(math.ceil((cfg.yupper - cfg.ylower) / wl)) + 3
+            while len(lat) <= o:
+                lat.append(np.random.default_rng([seed, len(lat)]).uniform(-1.0, 1.0, (gy, gx)))
+            fx = (X - cfg.xlower) / wl + 1.0
+            fy = (Y - cfg.ylower) / wl + 1.0
+            i = np.clip(np.floor(fx).astype(int), 0, gx - 2)
+            j = np.clip(np.floor(fy).astype(int), 0, gy - 2)
+            ax, ay = fx - i, fy - j
+            L = lat[o]
+            out += 0.5 ** o * ((1 - ay) * ((1 - ax) * L[j, i] + ax * L[j, i + 1]) +
+                               ay * ((1 - ax) * L[j + 1, i] + ax * L[j + 1, i + 1]))
+        return out
+
+    dems = []
+    for box, sp in zip(boxes, spacings):
+        if box is None:
+            box = (cfg.xlower, cfg.xupper, cfg.ylower, cfg.yupper)
+        x0 = math.floor(box[0] / sp) * sp
+        y0 = math.floor(box[2] / sp) * sp
+        nx = int(math.ceil((box[1] - x0) / sp)) + 1
+        ny = int(math.ceil((box[3] - y0) / sp)) + 1
+        X, Y = np.meshgrid(x0 + sp * np.arange(nx), y0 + sp * np.arange(ny))
+        base = 0.02 * (X - cfg.xlower) + relief * ((Y - cfg.ylower - 0.5 * W) / (0.5 * W)) ** 2
+        octaves = max(1, int(math.floor(math.log2(256.0 / (4.0 * sp)))) + 1)
+        dems.append(Dem(base + 0.5 * noise(X, Y, octaves), x0, y0, sp, sp))
+    return dems
 
 
 # --------------------------------------------------------------------------
