@@ -27,10 +27,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 # DRAM bytes (read + write) of one patch_step launch on this workload, from
-# the ncu captures summarised in profiles/ (launch 401 of the run, the second
-# warm-up run; ncu flushes the caches before each pass, so these are
-# cold-cache figures).  None when the kernel has changed since the capture.
-TRAFFIC_PER_LAUNCH_FP64 = None
+# the ncu captures summarised in profiles/ (launch 151 of --profile-case
+# 1024, the same workload at t about 28 s, the middle of the timed run; ncu
+# flushes the caches before each pass, so these are cold-cache figures).
+# None when the kernel has changed since the capture.
+TRAFFIC_PER_LAUNCH_FP64 = 24080128
 N_CELLS = 1024
 PATCH = 32
 T_END = 60.0
@@ -139,7 +140,7 @@ def measured_peaks():
 BYTES_PER_CELL_FP32 = 52
 OPS_PER_WET_CELL_FP32 = 500
 FP32_LANES_PER_SM = 128
-TRAFFIC_PER_LAUNCH_FP32 = None
+TRAFFIC_PER_LAUNCH_FP32 = 13568000
 # Algorithmic work of the FP64 patch step, counted operation by operation
 # from the scheme: a wet cell update takes two edge solves (74 operations
 # each), two limited edge fluxes (81), two increments (9), two transverse
@@ -389,6 +390,129 @@ def measure_ensemble(stream):
             "timing": "wall clock around the whole driver loop (steps, checks, regrids)"}
 
 
+VAR_STEPS = 96
+
+
+def measure_variants(stream):
+    """Scheme variants of Sec. 3.2 on the headline workload (FP32 deviation
+    form and FP64): the state at t = 20 s of the default method, then
+    VAR_STEPS steps of each variant from it (two graph chunks of warm-up
+    first), timed with CUDA events on the library's stream; cell updates per
+    second of the patch step loop.  The no-transverse variant runs at its
+    stability bound (CFL 0.45), which does not change the cost of a step."""
+    import torch
+    from paper_2403_15435_gb300 import geoflood, inputs
+
+    out = {}
+    flags = [("default", {}), ("first_order", dict(first_order=1)),
+             ("no_transverse", dict(no_transverse=1, cfl_desired=0.45, cfl_max=0.5)),
+             ("dim_split", dict(dim_split=1)), ("dim_split_first_order", dict(dim_split=1, first_order=1))]
+    for prec in (1, 0):
+        base = inputs.radial_dambreak(N_CELLS, PATCH, dx=2.0)
+        base.cfg.precision = prec
+        f = geoflood.Forest(base.cfg, base.dem, stream=stream.cuda_stream)
+        f.set_state(base.ic)
+        f.step(20.0)
+        h, hu, hv, _ = f.read()
+        t, dt = f.time()["t"], f.time()["dt_next"]
+        f.close()
+        res = {}
+        for name, fl in flags:
+            cfg = inputs.Config(**{**base.cfg.__dict__, **fl})
+            g = geoflood.Forest(cfg, base.dem, stream=stream.cuda_stream)
+            g.write(h, hu, hv)
+            g.set_time(t, dt)
+            g.step(1e9, 32)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            _, n = g.step(1e9, VAR_STEPS)
+            b.record(stream)
+            torch.cuda.synchronize()
+            sec = a.elapsed_time(b) / 1e3
+            cells = g.npatch * PATCH * PATCH
+            res[name] = {"value": n * cells / sec, "unit": "cell-updates/s",
+                         "us_per_step": 1e6 * sec / max(1, n), "steps": n}
+            g.close()
+        d = res["default"]["value"]
+        for r in res.values():
+            r["vs_default"] = r["value"] / d
+        out["fp32" if prec else "fp64"] = res
+    out["workload"] = WORKLOAD.replace("t 0->60 s", "t 20 s + %d steps" % VAR_STEPS)
+    return out
+
+
+FS_T_END = 3600.0
+
+
+def measure_flood_speed(stream):
+    """Test Case 1 stand-in (Sec. 5.1): flat dry 1000 m x 2000 m plain fed
+    by the inflow hydrograph through 20 m of its left side, 32x32 patches on
+    levels 0-3 (finest dx 3.9 m), plain tagging with a regrid every 4 steps,
+    FP32 deviation form, the first hour (the rising limb); wall clock of the
+    driver loop, and the volume that entered against the integral of Q."""
+    import torch
+    from paper_2403_15435_gb300 import geoflood, inputs
+
+    res = None
+    for rep in range(2):  # the first run instantiates graphs and warms up
+        prob = inputs.flood_speed(patch=32, minlevel=0, maxlevel=3, precision=1,
+                                  t_end=FS_T_END)
+        g = geoflood.Forest(prob.cfg, prob.dem, stream=stream.cuda_stream)
+        g.set_state(prob.ic)
+        v0 = g.mass()
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        st = g.advance(FS_T_END if rep else 120.0, regrid_interval=4, check_interval=4)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - a
+        cells = st["patch_steps"] * PATCH * PATCH
+        vin = 0.5 * FS_T_END * 20.0 * min(FS_T_END, 3600.0) / 3600.0
+        res = {"value": cells / wall, "unit": "cell-updates/s", "wall_s": wall,
+               "steps": st["steps"], "regrids": st["regrids"], "cell_updates": cells,
+               "patches_at_end": g.npatch,
+               "volume_in_m3": g.mass() - v0 - g.time()["clipvol"],
+               "integral_of_Q_m3": vin}
+        g.close()
+    res["workload"] = ("flood speed over a flat dry plain 1000 m x 2000 m, inflow 0->20 m3/s "
+                       "over 20 m of the left side, 32x32 patches, levels 0-3, n 0.03, t 0->%g s"
+                       % FS_T_END)
+    res["timing"] = "wall clock around the whole driver loop (steps, checks, regrids), second run"
+    return res
+
+
+def measure_topo(stream):
+    """Bed evaluation from three nested DEMs (20 m over the whole domain,
+    5 m and 2 m over nested boxes, Sec. 6.2) for a 2 km x 1 km forest of
+    32x32 patches at uniform level 3 (512 patches, 1.95 m cells): seconds
+    per geoflood_set_topos call (every tile cell, ghosts included) against
+    the single 20 m DEM."""
+    import torch
+    from paper_2403_15435_gb300 import geoflood, inputs
+
+    cfg = inputs.Config(mi=4, mj=2, mx=32, minlevel=3, maxlevel=3, xupper=2000.0,
+                        yupper=1000.0, drytol=1e-3)
+    dems = inputs.nested_dems(cfg, 12, [None, (400.0, 1200.0, 200.0, 800.0),
+                                        (600.0, 900.0, 400.0, 600.0)], [20.0, 5.0, 2.0])
+    g = geoflood.Forest(cfg, None, stream=stream.cuda_stream)
+    out = {}
+    for name, d in (("one_dem_20m", dems[:1]), ("nested_20_5_2m", dems)):
+        g.set_topo(d)
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        for _ in range(5):
+            g.set_topo(d)
+        torch.cuda.synchronize()
+        sec = (time.perf_counter() - a) / 5
+        tiles = g.npatch * (PATCH + 4) ** 2
+        out[name] = {"seconds": sec, "tile_cells_per_s": tiles / sec}
+    g.close()
+    out["workload"] = "2 km x 1 km, 512 patches of 32x32 (level 3), every tile cell's bed"
+    out["timing"] = "wall clock per set_topo call (DEM upload, bed kernel, ghost fill), mean of 5"
+    return out
+
+
 def roofline(r, prec, peaks):
     """Roofline of the patch_step kernel from the live per-launch events:
     HBM side from the algorithmic bytes per cell update, ALU side from the
@@ -457,6 +581,9 @@ def run_ours(args):
            "arrival_max_abs_s": float(np.abs(r32["arrival"] - r64["arrival"]).max())}
     amr = measure_amr(stream)
     ens = measure_ensemble(stream)
+    variants = measure_variants(stream)
+    flood = measure_flood_speed(stream)
+    topo = measure_topo(stream)
     cpu = cpu_baseline()
     line = {
         "metric": "cell-updates/s", "value": r32["value"], "unit": "cell-updates/s",
@@ -484,6 +611,9 @@ def run_ours(args):
         "fp32_vs_fp64_error": err,
         "amr_valley": amr,
         "ensemble": ens,
+        "scheme_variants": variants,
+        "flood_speed_inflow": flood,
+        "nested_dem_topography": topo,
     }
     if rank == 0:
         print(json.dumps(line))

@@ -164,6 +164,24 @@ int geoflood_set_scenario(geoflood_ctx* ctx, int scenario, double manning_n,
 int geoflood_set_topo(geoflood_ctx* ctx, int scenario, const double* z, int nx,
                       int ny, double x0, double y0, double dx, double dy);
 
+/* Topography of one scenario from 1..4 overlapping or nested DEMs of
+ * different resolutions (Sec. 6.2, the Malpasset set-up's 2, 5 and 20 m
+ * DEMs): arrays of ndem entries, DEM k being z[k][ny[k]][nx[k]] at
+ * (x0[k] + i dx[k], y0[k] + j dy[k]).  At each point the bed is the bilinear
+ * interpolant of the finest DEM (smallest dx * dy; equal spacings in the
+ * given order) whose node-to-node extent holds the point; outside every
+ * extent the coarsest one's, constant beyond its edges.  Every cell's bed is
+ * the exact cell average of that composite interpolant (its pieces are cut
+ * by every DEM's node lines), so a coarse cell's bed is the mean of its
+ * children's and refinement keeps still water still.  The DEMs are copied to
+ * the device and kept for regrids; geoflood_set_topo is the case ndem = 1.
+ * In the FP32 form the depths are kept.  Errors: ARG (counts, sizes,
+ * spacings), CUDA, OOM. */
+int geoflood_set_topos(geoflood_ctx* ctx, int scenario, int ndem,
+                       const double* const* z, const int* nx, const int* ny,
+                       const double* x0, const double* y0, const double* dx,
+                       const double* dy);
+
 /* Number of patches of a scenario. */
 int geoflood_npatch(geoflood_ctx* ctx, int scenario, int* npatch);
 

@@ -149,6 +149,18 @@ __device__ void fill_cell(const Geo<T>& e, int s, int L, long long I,
     value_at(e, s, L + 1, 2 * I + 1, 2 * J + 1, v[3], err);
     for (int f = 0; f < 3; ++f)
       out[f] = 0.25 * ((v[0][f] + v[1][f]) + (v[2][f] + v[3][f]));
+    if constexpr (Geo<T>::DEV) {
+      // deviation form: over four wet children the mean stored surface is
+      // kept (the FP32 beds of two levels are rounded separately, so the
+      // mean depth over the coarse bed would not keep still water still)
+      const double dt = e.G.drytol;
+      if (v[0][0] > dt && v[1][0] > dt && v[2][0] > dt && v[3][0] > dt) {
+        const double eta = 0.25 * (((v[0][0] + v[0][3]) + (v[1][0] + v[1][3])) +
+                                   ((v[2][0] + v[2][3]) + (v[3][0] + v[3][3])));
+        const double h = eta - bt;
+        out[0] = h > 0.0 ? h : 0.0;
+      }
+    }
     return;
   }
   const long long ic = I >> 1, jc = J >> 1;
@@ -540,9 +552,10 @@ __global__ void k_ghost_other(const __grid_constant__ GfGeom G, const __grid_con
 
 // ------------------------------------------------------------ topography
 
-__device__ double dem_eval(const GfScenario& S, double x, double y) {
-  const int nx = S.dnx, ny = S.dny;
-  double fx = (x - S.dx0) / S.ddx, fy = (y - S.dy0) / S.ddy;
+// Bilinear interpolant of DEM k at (x, y), constant beyond its edges.
+__device__ double dem_eval(const GfScenario& S, int k, double x, double y) {
+  const int nx = S.dnx[k], ny = S.dny[k];
+  double fx = (x - S.dx0[k]) / S.ddx[k], fy = (y - S.dy0[k]) / S.ddy[k];
   if (fx < 0.0) fx = 0.0;
   if (fx > (double)(nx - 1)) fx = (double)(nx - 1);
   if (fy < 0.0) fy = 0.0;
@@ -553,7 +566,7 @@ __device__ double dem_eval(const GfScenario& S, double x, double y) {
   if (i < 0) i = 0;
   if (j < 0) j = 0;
   const double ax = fx - (double)i, ay = fy - (double)j;
-  const double* z = S.dem;
+  const double* z = S.dem[k];
   const double z00 = z[i + (size_t)j * nx], z10 = z[i + 1 + (size_t)j * nx];
   const double z01 = z[i + (size_t)(j + 1) * nx];
   const double z11 = z[i + 1 + (size_t)(j + 1) * nx];
@@ -561,47 +574,59 @@ __device__ double dem_eval(const GfScenario& S, double x, double y) {
          ay * ((1.0 - ax) * z01 + ax * z11);
 }
 
-// Range of DEM node indices that may lie strictly inside (a, b).
-__device__ void node_range(double a, double b, double o, double d, int n,
-                           int* lo, int* hi) {
-  int l = (int)floor((a - o) / d) - 1, h = (int)ceil((b - o) / d) + 1;
-  *lo = l < 0 ? 0 : l;
-  *hi = h > n - 1 ? n - 1 : h;
+// Composite interpolant of the scenario's DEMs (Sec. 6.2): the first DEM in
+// priority order whose node-to-node extent holds the point; outside every
+// extent the last (coarsest) one's, constant beyond its edges.
+__device__ double dems_eval(const GfScenario& S, double x, double y) {
+  int k = 0;
+  for (; k < S.ndem; ++k) {
+    const double xe = S.dx0[k] + (double)(S.dnx[k] - 1) * S.ddx[k];
+    const double ye = S.dy0[k] + (double)(S.dny[k] - 1) * S.ddy[k];
+    if (x >= S.dx0[k] && x <= xe && y >= S.dy0[k] && y <= ye) break;
+  }
+  return dem_eval(S, k < S.ndem ? k : S.ndem - 1, x, y);
 }
 
-// Exact average over [xa,xb]x[ya,yb] of the DEM's bilinear interpolant: the
-// node lines cut the cell into pieces on which the interpolant is bilinear;
-// each piece contributes its area times the value at its midpoint.  The
-// pieces are visited row by row in increasing coordinate order.
+// The smallest break point above v along one axis (xaxis: x), at most b:
+// the node lines of every DEM (node indices 0..n-1).  The extents' edges are
+// node lines, so between consecutive break points every DEM is either
+// bilinear or absent.
+__device__ double next_break(const GfScenario& S, bool xaxis, double v, double b) {
+  double best = b;
+  for (int k = 0; k < S.ndem; ++k) {
+    const double o = xaxis ? S.dx0[k] : S.dy0[k];
+    const double d = xaxis ? S.ddx[k] : S.ddy[k];
+    const int n = xaxis ? S.dnx[k] : S.dny[k];
+    double f = floor((v - o) / d) + 1.0;
+    if (f < 0.0) f = 0.0;
+    if (f > (double)n) f = (double)n;
+    int i = (int)f;
+    while (i > 0 && o + (double)(i - 1) * d > v) --i;
+    while (i <= n - 1 && !(o + (double)i * d > v)) ++i;
+    if (i <= n - 1) {
+      const double xn = o + (double)i * d;
+      if (xn < best) best = xn;
+    }
+  }
+  return best;
+}
+
+// Exact average over [xa,xb]x[ya,yb] of the composite interpolant: the node
+// lines of all DEMs cut the cell into pieces on which it is bilinear; each
+// piece contributes its area times its midpoint value.  Rows of pieces in
+// increasing y, pieces of a row in increasing x.
 __device__ double dem_average(const GfScenario& S, double xa, double xb,
                               double ya, double yb) {
-  int xl, xh, yl, yh;
-  node_range(xa, xb, S.dx0, S.ddx, S.dnx, &xl, &xh);
-  node_range(ya, yb, S.dy0, S.ddy, S.dny, &yl, &yh);
   double sum = 0.0;
   double y0 = ya;
-  for (int jn = yl; jn <= yh + 1; ++jn) {
-    double y1;
-    if (jn <= yh) {
-      const double yn = S.dy0 + (double)jn * S.ddy;
-      if (!(yn > ya && yn < yb)) continue;
-      y1 = yn;
-    } else {
-      y1 = yb;
-    }
+  while (y0 < yb) {
+    const double y1 = next_break(S, false, y0, yb);
     double x0 = xa;
-    for (int in = xl; in <= xh + 1; ++in) {
-      double x1;
-      if (in <= xh) {
-        const double xn = S.dx0 + (double)in * S.ddx;
-        if (!(xn > xa && xn < xb)) continue;
-        x1 = xn;
-      } else {
-        x1 = xb;
-      }
+    while (x0 < xb) {
+      const double x1 = next_break(S, true, x0, xb);
       const double xm = 0.5 * (x0 + x1), ym = 0.5 * (y0 + y1);
       const double w = (x1 - x0) * (y1 - y0);
-      sum += w * dem_eval(S, xm, ym);
+      sum += w * dems_eval(S, xm, ym);
       x0 = x1;
     }
     y0 = y1;
@@ -617,14 +642,14 @@ __global__ void k_topo(const __grid_constant__ GfGeom G, const __grid_constant__
   Geo<T> e(G, V);
   const int M = G.M, T_ = G.T, TT = T_ * T_;
   T* b = e.bp(p);
-  const GfScenario S = V.scen[P.scen];
+  const GfScenario& S = V.scen[P.scen];
   const long long NX = e.nx(P.level), NY = e.ny(P.level);
   const double dx = e.dx(P.level), dy = e.dy(P.level);
   for (int k = threadIdx.x; k < TT; k += blockDim.x) {
     const int i = k % T_ - GF_NG, j = k / T_ - GF_NG;
     const long long I = (long long)P.px * M + i, J = (long long)P.py * M + j;
     double v = 0.0;
-    if (I >= 0 && J >= 0 && I < NX && J < NY && S.dem) {
+    if (I >= 0 && J >= 0 && I < NX && J < NY && S.ndem > 0) {
       const double xa = G.xlower + (double)I * dx;
       const double xb = G.xlower + (double)(I + 1) * dx;
       const double ya = G.ylower + (double)J * dy;

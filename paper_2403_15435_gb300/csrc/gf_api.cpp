@@ -116,7 +116,8 @@ struct geoflood_ctx {
   double* d_stage = nullptr;
   size_t stage_cap = 0;
   std::vector<gf::HostForest> forests;
-  std::vector<double*> d_dem, d_gxy, d_gout, d_garr;
+  std::vector<double*> d_gxy, d_gout, d_garr;
+  std::vector<std::vector<double*>> d_dem;  // per scenario, priority order
   std::vector<GfGaugeRef*> d_gref;
   int max_gauges_used = 0;
   int variant = 0;  // patch-step kernel variant (see geoflood_autotune)
@@ -657,7 +658,7 @@ int geoflood_init_forest(const geoflood_config* cfg, void* stream,
     return GEOFLOOD_ERR_OOM;
   }
   ctx->h_scen.assign(ctx->nscen, GfScenario{});
-  ctx->d_dem.assign(ctx->nscen, nullptr);
+  ctx->d_dem.assign(ctx->nscen, std::vector<double*>());
   ctx->d_gxy.assign(ctx->nscen, nullptr);
   ctx->d_gout.assign(ctx->nscen, nullptr);
   ctx->d_garr.assign(ctx->nscen, nullptr);
@@ -737,7 +738,8 @@ void geoflood_destroy(geoflood_ctx* ctx) {
   cudaFree(ctx->d_flags);
   cudaFree(ctx->d_err);
   cudaFree(ctx->d_stage);
-  for (auto p : ctx->d_dem) cudaFree(p);
+  for (auto& v : ctx->d_dem)
+    for (auto p : v) cudaFree(p);
   for (auto p : ctx->d_gxy) cudaFree(p);
   for (auto p : ctx->d_gout) cudaFree(p);
   for (auto p : ctx->d_garr) cudaFree(p);
@@ -788,28 +790,59 @@ int geoflood_set_scenario(geoflood_ctx* ctx, int s, double manning_n,
   return geoflood_write_patches(ctx, s, h.data(), hu.data(), hv.data());
 }
 
-int geoflood_set_topo(geoflood_ctx* ctx, int s, const double* z, int nx,
-                      int ny, double x0, double y0, double dx, double dy) {
-  if (!valid_scen(ctx, s) || !z || nx < 2 || ny < 2 || !(dx > 0) || !(dy > 0))
+int geoflood_set_topos(geoflood_ctx* ctx, int s, int ndem, const double* const* z,
+                       const int* nx, const int* ny, const double* x0,
+                       const double* y0, const double* dx, const double* dy) {
+  if (!valid_scen(ctx, s) || ndem < 1 || ndem > GF_MAXDEM || !z || !nx || !ny || !x0 ||
+      !y0 || !dx || !dy)
     return fail(ctx, GEOFLOOD_ERR_ARG, "set_topo: bad argument");
+  for (int k = 0; k < ndem; ++k)
+    if (!z[k] || nx[k] < 2 || ny[k] < 2 || !(dx[k] > 0) || !(dy[k] > 0) ||
+        !std::isfinite(x0[k]) || !std::isfinite(y0[k]) || !std::isfinite(dx[k]) ||
+        !std::isfinite(dy[k]))
+      return fail(ctx, GEOFLOOD_ERR_ARG, "set_topo: bad DEM " + std::to_string(k));
+  // priority: finer node spacing (dx * dy) first, equal spacings in the
+  // given order
+  int ord[GF_MAXDEM];
+  for (int k = 0; k < ndem; ++k) ord[k] = k;
+  for (int i = 1; i < ndem; ++i)
+    for (int j = i; j > 0 && dx[ord[j]] * dy[ord[j]] < dx[ord[j - 1]] * dy[ord[j - 1]]; --j)
+      std::swap(ord[j], ord[j - 1]);
   std::vector<double> h, hu, hv;
   int rc = 0;
   if (ctx->prec && (rc = keep_depths(ctx, s, h, hu, hv))) return rc;
-  if (ctx->d_dem[s]) cudaFree(ctx->d_dem[s]);
-  ctx->d_dem[s] = nullptr;
-  const size_t n = (size_t)nx * ny;
-  if (cudaMalloc(&ctx->d_dem[s], n * sizeof(double)) != cudaSuccess)
-    return fail(ctx, GEOFLOOD_ERR_OOM, "set_topo: DEM allocation");
-  CK(cudaMemcpyAsync(ctx->d_dem[s], z, n * sizeof(double),
-                     cudaMemcpyHostToDevice, ctx->st));
+  for (auto p : ctx->d_dem[s]) cudaFree(p);
+  ctx->d_dem[s].clear();
   GfScenario& S = ctx->h_scen[s];
-  S.dem = ctx->d_dem[s];
-  S.dnx = nx; S.dny = ny; S.dx0 = x0; S.dy0 = y0; S.ddx = dx; S.ddy = dy;
+  S.ndem = 0;
+  for (int r = 0; r < ndem; ++r) {
+    const int k = ord[r];
+    const size_t n = (size_t)nx[k] * ny[k];
+    double* d = nullptr;
+    if (cudaMalloc(&d, n * sizeof(double)) != cudaSuccess) {
+      for (auto p : ctx->d_dem[s]) cudaFree(p);
+      ctx->d_dem[s].clear();
+      upload_scen(ctx);
+      return fail(ctx, GEOFLOOD_ERR_OOM, "set_topo: DEM allocation");
+    }
+    ctx->d_dem[s].push_back(d);
+    CK(cudaMemcpyAsync(d, z[k], n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+    S.dem[r] = d;
+    S.dnx[r] = nx[k]; S.dny[r] = ny[k];
+    S.dx0[r] = x0[k]; S.dy0[r] = y0[k]; S.ddx[r] = dx[k]; S.ddy[r] = dy[k];
+  }
+  S.ndem = ndem;
   rc = upload_scen(ctx);
   if (rc) return rc;
   if ((rc = topo_scenario(ctx, s))) return rc;
   if (ctx->prec) return geoflood_write_patches(ctx, s, h.data(), hu.data(), hv.data());
   return ghost_fill_all(ctx);
+}
+
+int geoflood_set_topo(geoflood_ctx* ctx, int s, const double* z, int nx,
+                      int ny, double x0, double y0, double dx, double dy) {
+  const double* zz[1] = {z};
+  return geoflood_set_topos(ctx, s, 1, zz, &nx, &ny, &x0, &y0, &dx, &dy);
 }
 
 int geoflood_npatch(geoflood_ctx* ctx, int s, int* np) {

@@ -18,6 +18,8 @@ struct GfPatch {
 // Where a gauge samples: the finest leaf p holding the point, the tile
 // index c of the lower-left cell of its 2 x 2 bilinear stencil and the
 // weights (ax, ay) of the upper/right cells.  Refreshed after every regrid.
+#define GF_MAXDEM 4  // overlapping DEMs per scenario (Sec. 6.2)
+
 struct GfGaugeRef {
   int p, c;
   double ax, ay;
@@ -27,9 +29,12 @@ struct GfScenario {
   double manning_n, eta0;
   float manning_f;    // FP32 copy of manning_n
   int pad0;
-  const double* dem;  // nodal DEM [dny][dnx] or null (flat bed at 0)
-  int dnx, dny;
-  double dx0, dy0, ddx, ddy;
+  // nodal DEMs [dny][dnx] in priority order (finest node spacing first);
+  // ndem = 0: flat bed at 0
+  int ndem;
+  int dnx[GF_MAXDEM], dny[GF_MAXDEM];
+  const double* dem[GF_MAXDEM];
+  double dx0[GF_MAXDEM], dy0[GF_MAXDEM], ddx[GF_MAXDEM], ddy[GF_MAXDEM];
   int poff, pcount;   // patch range in the table
   long long lut_off;  // offset of this scenario's lookup tables
   int ngauge;

@@ -96,6 +96,8 @@ def lib():
                 "geoflood_init_forest": [C.POINTER(_Cfg), vp, C.POINTER(vp)],
                 "geoflood_set_scenario": [vp, ip, C.c_double, C.c_double],
                 "geoflood_set_topo": [vp, ip, dp, ip, ip] + [C.c_double] * 4,
+                "geoflood_set_topos": [vp, ip, ip, C.POINTER(dp), C.POINTER(ip), C.POINTER(ip)]
+                                      + [dp] * 4,
                 "geoflood_npatch": [vp, ip, pi],
                 "geoflood_patch_info": [vp, ip, pi, pi, pi],
                 "geoflood_write_patches": [vp, ip, dp, dp, dp],
@@ -225,6 +227,18 @@ class Forest:
         self._check(lib().geoflood_set_scenario(self._h, s, manning_n, eta0))
 
     def set_topo(self, dem, s=0):
+        """One DEM, or a list of up to 4 overlapping DEMs (Sec. 6.2)."""
+        if isinstance(dem, (list, tuple)):
+            zs = [np.ascontiguousarray(d.z, dtype=np.float64) for d in dem]
+            n = len(zs)
+            zp = (C.POINTER(C.c_double) * n)(*[_p(z) for z in zs])
+            ints = lambda v: (C.c_int * n)(*v)
+            dbl = lambda v: (C.c_double * n)(*v)
+            self._check(lib().geoflood_set_topos(
+                self._h, s, n, zp, ints([z.shape[1] for z in zs]), ints([z.shape[0] for z in zs]),
+                dbl([d.x0 for d in dem]), dbl([d.y0 for d in dem]),
+                dbl([d.dx for d in dem]), dbl([d.dy for d in dem])))
+            return
         z = np.ascontiguousarray(dem.z, dtype=np.float64)
         ny, nx = z.shape
         self._check(lib().geoflood_set_topo(self._h, s, _p(z), nx, ny, dem.x0,
