@@ -115,8 +115,11 @@ typedef struct {
    * [inflow_lo, inflow_hi] of side inflow_side (GEOFLOOD_BC order: 0 left,
    * 1 right, 2 bottom, 3 top; the coordinate along that side).  While
    * Q(t) > 0, each ghost line of a tile whose centre lies in the segment
-   * carries, in both ghost layers, the unit discharge Q(t) / (inflow_hi -
-   * inflow_lo) normal to the side into the domain, no tangential momentum,
+   * carries, in both ghost layers, the unit discharge Q(t) / W normal to
+   * the side into the domain (W: the number of such lines at the tile's
+   * level times their cell size, so that Q(t) enters at every resolution;
+   * none where no line centre of that level lies in the segment), no
+   * tangential momentum,
    * and the depth that joins it to the tile's first cell of the line by a
    * single entering wave: Eq. riemann, or Eq. 2-shock where that depth
    * exceeds the interior's, solved by Newton's method (first guesses

@@ -54,7 +54,7 @@ class _Cfg(C.Structure):
         ("grade_kind", C.c_int * 4), ("grade_value", C.c_double * 4),
         ("grade_level", C.c_int * 4),
         ("first_order", C.c_int), ("no_transverse", C.c_int), ("dim_split", C.c_int),
-        ("n_hydro", C.c_int), ("inflow_side", C.c_int),
+        ("subcycle", C.c_int), ("n_hydro", C.c_int), ("inflow_side", C.c_int),
         ("inflow_lo", C.c_double), ("inflow_hi", C.c_double), ("inflow_tau", C.c_double),
         ("hydro_t", C.c_double * 16), ("hydro_q", C.c_double * 16),
     ]
@@ -201,6 +201,7 @@ def _cfg_struct(cfg) -> _Cfg:
     c.first_order = int(cfg.first_order)
     c.no_transverse = int(cfg.no_transverse)
     c.dim_split = int(cfg.dim_split)
+    c.subcycle = int(cfg.subcycle)
     hyd = list(cfg.hydrograph)
     assert len(hyd) <= 16
     c.n_hydro = len(hyd)

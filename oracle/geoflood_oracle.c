@@ -623,6 +623,12 @@ struct oracle_forest {
   int dnx[ORACLE_MAXDEM], dny[ORACLE_MAXDEM];
   double dx0[ORACLE_MAXDEM], dy0[ORACLE_MAXDEM], ddx[ORACLE_MAXDEM], ddy[ORACLE_MAXDEM];
   double t, dt_next;
+  /* level subcycling: during a macro step, prev[p] holds patch p's state
+   * before its latest step and sub_k the fine substep; ghost cells are then
+   * filled from states interpolated in time (NULL outside a macro step) */
+  double** prev;
+  long sub_k;
+  double tg; /* time of the ghost values being filled */
   long steps, rejects, nclip;
   double clipvol; /* volume added by resetting negative depths to zero */
   int ngauge;
@@ -682,6 +688,24 @@ static int leaf_at(const oracle_forest* f, int L, long I, long J) {
 /* Composite value of the leaves at cell (I, J) of level L: the leaf's own
  * cell, a coarser leaf's cell (injection) or the mean of the four finer
  * cells.  out = h, hu, hv, b. */
+/* Fields 0..nf-1 of tile cell id of patch p at the time the ghost cells are
+ * being filled: the stored state, or during a subcycled macro step, for a
+ * level between two of its steps, the linear interpolation in time of h, hu
+ * and hv between the states before and after its latest step (the bed does
+ * not change in time). */
+static void cell_read(const oracle_forest* f, int p, size_t id, int nf, double* out) {
+  size_t TT = (size_t)f->T * f->T;
+  int k;
+  for (k = 0; k < nf; ++k) out[k] = f->tile[p][k * TT + id];
+  if (!f->prev) return;
+  long P = 1L << (f->c.maxlevel - f->lev[p]);
+  long r = f->sub_k % P;
+  if (r == 0) return;
+  double a = (double)r / (double)P;
+  for (k = 0; k < nf && k < 3; ++k)
+    out[k] = (1.0 - a) * f->prev[p][k * TT + id] + a * f->tile[p][k * TT + id];
+}
+
 static void value_at(const oracle_forest* f, int L, long I, long J,
                      double* out) {
   int l, k;
@@ -691,8 +715,7 @@ static void value_at(const oracle_forest* f, int L, long I, long J,
     if (p >= 0) {
       int i = (int)(Il - (long)f->px[p] * f->M);
       int j = (int)(Jl - (long)f->py[p] * f->M);
-      size_t id = TI(f, i, j), TT = (size_t)f->T * f->T;
-      for (k = 0; k < 4; ++k) out[k] = f->tile[p][k * TT + id];
+      cell_read(f, p, TI(f, i, j), 4, out);
       return;
     }
   }
@@ -724,8 +747,7 @@ static void fill_cell(const oracle_forest* f, int L, long I, long J, double bt,
   int k, l;
   if (p >= 0) {
     int i = (int)(I - (long)f->px[p] * f->M), j = (int)(J - (long)f->py[p] * f->M);
-    size_t id = TI(f, i, j), TT = (size_t)f->T * f->T;
-    for (k = 0; k < 3; ++k) out[k] = f->tile[p][k * TT + id];
+    cell_read(f, p, TI(f, i, j), 3, out);
     return;
   }
   int coarser = 0;
@@ -870,12 +892,33 @@ double oracle_inflow_depth(double q, double h_int, double qn_int, double g,
  * Eq. 2-shock from the tile's first cell of that line, the unit discharge
  * normal to the side into the domain and no tangential momentum.  With no
  * discharge the side's own rule stays. */
+/* Width of the inflow segment as the grid of level L represents it: the
+ * number of lines (rows or columns of the side) whose centre lies in
+ * [inflow_lo, inflow_hi], times the cell size. */
+static double inflow_width(const oracle_forest* f, int L) {
+  const oracle_config* c = &f->c;
+  int xs = c->inflow_side <= 1;
+  long N = xs ? NYL(f, L) : NXL(f, L), J, n = 0;
+  double d = xs ? DYL(f, L) : DXL(f, L);
+  double o = xs ? c->ylower : c->xlower;
+  long J0 = (long)floor((c->inflow_lo - o) / d) - 1, J1 = (long)ceil((c->inflow_hi - o) / d) + 1;
+  if (J0 < 0) J0 = 0;
+  if (J1 > N - 1) J1 = N - 1;
+  for (J = J0; J <= J1; ++J) {
+    double ctr = o + ((double)J + 0.5) * d;
+    if (ctr >= c->inflow_lo && ctr <= c->inflow_hi) ++n;
+  }
+  return (double)n * d;
+}
+
 static void fill_inflow(const oracle_forest* f, int p, int side) {
   const oracle_config* c = &f->c;
-  double Q = oracle_hydrograph(c, f->t);
+  double Q = oracle_hydrograph(c, f->prev ? f->tg : f->t);
   if (!(Q > 0.0)) return;
-  double q = Q / (c->inflow_hi - c->inflow_lo);
   int L = f->lev[p], M = f->M, l, g;
+  double wd = inflow_width(f, L);
+  if (!(wd > 0.0)) return; /* the segment holds no line centre at this level */
+  double q = Q / wd;
   size_t TT = (size_t)f->T * f->T;
   double* t = f->tile[p];
   int xs = side <= 1; /* the side is a left or right one: lines are rows */
@@ -1263,9 +1306,110 @@ static void sample_gauges(oracle_forest* f) {
 /* Adaptive time stepping with a global dt over all levels (Sec. 5.1: maximum
  * CFL 0.9; Sec. 6.6: initial dt, CFL 0.75): a step whose CFL number exceeds
  * cfl_max is rejected and retaken; the next dt is cfl_desired / cmax. */
+/* Level subcycling (Berger-Oliger local time stepping over the quadtree):
+ * one macro step of DT advances level L by n_L = 2^(L - minlevel) steps of
+ * DT / n_L.  It runs as K = 2^(maxlevel - minlevel) fine substeps of
+ * DT / K; level L steps at the substeps k with k mod 2^(maxlevel - L) = 0,
+ * from the states of all levels at time t + k DT / K: its own, those of the
+ * levels that step with it, and for coarser levels between two of their
+ * steps the linear interpolation in time of their states before and after
+ * that step (used by the ghost cells).  Every level steps at k = 0: the
+ * macro step is retaken with a smaller DT if a level's Courant number
+ * DT / n_L * cmax exceeds cfl_max there; later substeps are not retaken,
+ * their rates cmax / n_L bound the next DT = cfl_desired / max(cmax / n_L).
+ * Ghost cells at level changes are not corrected for the flux mismatch. */
+static int forest_macro_steps(oracle_forest* f, double t_target, int max_steps,
+                              int* steps_out) {
+  int taken = 0, p, inrow = 0, rc = 0;
+  size_t TT = (size_t)f->T * f->T;
+  int np = f->np;
+  long K = 1L << (f->c.maxlevel - f->c.minlevel), k;
+  double** nt = (double**)malloc(sizeof(double*) * np);
+  double** pv = (double**)malloc(sizeof(double*) * np);
+  long* ncl = (long*)malloc(sizeof(long) * np);
+  double* cdp = (double*)malloc(sizeof(double) * np);
+  for (p = 0; p < np; ++p) {
+    nt[p] = (double*)malloc(sizeof(double) * 4 * TT);
+    pv[p] = (double*)malloc(sizeof(double) * 4 * TT);
+  }
+  while (taken < max_steps && f->t < t_target) {
+    double rem = t_target - f->t, DT;
+    int last;
+    if (f->dt_next < rem) { DT = f->dt_next; last = 0; }
+    else { DT = rem; last = 1; }
+    double dtf = DT / (double)K, rmax = 0.0;
+    int rejected = 0;
+    for (k = 0; k < K && !rejected; ++k) {
+      if (k > 0) {
+        /* ghost cells at t + k dtf, coarser levels interpolated in time */
+        f->prev = pv;
+        f->sub_k = k;
+        f->tg = f->t + (double)k * dtf;
+        oracle_forest_ghost_fill(f);
+        f->prev = NULL;
+      }
+      double r0 = 0.0;
+      for (p = 0; p < np; ++p) {
+        int L = f->lev[p];
+        long P = 1L << (f->c.maxlevel - L);
+        if (k % P) continue;
+        double cm, *q = f->tile[p];
+        memcpy(nt[p] + 3 * TT, q + 3 * TT, sizeof(double) * TT);
+        oracle_step_grid_ex(f->M, f->M, q, q + TT, q + 2 * TT, q + 3 * TT, DXL(f, L),
+                            DYL(f, L), dtf * (double)P, f->c.g, f->c.drytol,
+                            f->c.manning_n, f->c.first_order ? 1 : 2,
+                            !f->c.no_transverse, f->c.dim_split, nt[p], nt[p] + TT,
+                            nt[p] + 2 * TT, &cm, &ncl[p], &cdp[p]);
+        double r = cm * (double)P / (double)K; /* cmax / n_L */
+        if (r > r0) r0 = r;
+      }
+      if (k == 0 && DT * r0 > f->c.cfl_max) {
+        f->dt_next = f->c.cfl_desired / r0;
+        f->rejects++;
+        rejected = 1;
+        break;
+      }
+      if (r0 > rmax) rmax = r0;
+      for (p = 0; p < np; ++p) {
+        long P = 1L << (f->c.maxlevel - f->lev[p]);
+        if (k % P) continue;
+        double* tmp = pv[p];
+        pv[p] = f->tile[p];
+        f->tile[p] = nt[p];
+        nt[p] = tmp;
+        f->nclip += ncl[p];
+        f->clipvol += cdp[p] * (DXL(f, f->lev[p]) * DYL(f, f->lev[p]));
+      }
+    }
+    if (rejected) {
+      if (++inrow > 50) { rc = -1; break; }
+      continue;
+    }
+    inrow = 0;
+    f->t = last ? t_target : f->t + DT;
+    f->steps++;
+    taken++;
+    if (rmax > 0.0) {
+      double dn = f->c.cfl_desired / rmax;
+      f->dt_next = dn < f->c.dt_max ? dn : f->c.dt_max;
+    }
+    oracle_forest_ghost_fill(f);
+    sample_gauges(f);
+  }
+  for (p = 0; p < np; ++p) { free(nt[p]); free(pv[p]); }
+  free(nt); free(pv); free(ncl); free(cdp);
+  if (steps_out) *steps_out = taken;
+  return rc;
+}
+
 int oracle_forest_step(oracle_forest* f, double t_target, int max_steps,
                        double* t_out, int* steps_out) {
   int taken = 0, p, inrow = 0;
+  if (f->c.subcycle && f->c.maxlevel > f->c.minlevel) {
+    int rc = forest_macro_steps(f, t_target, max_steps, steps_out);
+    if (t_out) *t_out = f->t;
+    return rc;
+  }
   size_t TT = (size_t)f->T * f->T;
   double** nt = (double**)malloc(sizeof(double*) * f->np);
   long* ncl = (long*)malloc(sizeof(long) * f->np);

@@ -57,11 +57,15 @@ typedef struct {
   /* inflow hydrograph (Sec. 5.1 set-up, Eq. riemann, Eq. 2-shock): with
    * n_hydro > 0, the ghost cells of side inflow_side (0 left, 1 right,
    * 2 bottom, 3 top) whose centre lies in [inflow_lo, inflow_hi] (the
-   * side's coordinate) carry the discharge Q(t) / (inflow_hi - inflow_lo)
-   * per unit width into the domain while Q(t) > 0; Q is piecewise linear
+   * side's coordinate) carry Q(t) divided by the width of those lines at
+   * their level into the domain while Q(t) > 0; Q is piecewise linear
    * through (hydro_t[k], hydro_q[k]), k < n_hydro <= 16, and constant
    * beyond the first and last points; inflow_tau is the minimum interior
    * depth of Sec. 5.1 */
+  /* level subcycling (0: one time step for all levels; 1: level L takes
+   * 2^(L - minlevel) steps per macro step, ghost cells of coarser levels
+   * interpolated in time) */
+  int subcycle;
   int n_hydro, inflow_side;
   double inflow_lo, inflow_hi, inflow_tau;
   double hydro_t[16], hydro_q[16];

@@ -411,8 +411,10 @@ __device__ double inflow_depth(double q, double h_int, double qn_int, double g,
 // line of its tile (rows for a left or right side, columns otherwise,
 // -2..M+1).  A line inside the domain whose centre lies in the segment
 // gets, in both ghost layers, the depth of the boundary equations from the
-// tile's first cell of that line, the unit discharge Q(t)/(hi - lo) normal
-// to the side into the domain and no tangential momentum; the tile corners
+// tile's first cell of that line, the unit discharge Q(t) / W_L normal to
+// the side into the domain (W_L = G.inflow_width[L], the width of the
+// segment's lines at the patch's level, so that Q(t) enters at every
+// resolution) and no tangential momentum; the tile corners
 // beyond those ghost cells, where the tile touches a side across the lines,
 // follow that side's rule applied to them.  With Q(t) = 0 the side's own
 // rule (written by the step and the other ghost kernels) stays.  Runs after
@@ -440,7 +442,9 @@ __global__ void k_inflow(const __grid_constant__ GfGeom G, const __grid_constant
   if (J < 0 || J >= N) return;
   const double ctr = o + ((double)J + 0.5) * d;
   if (!(ctr >= G.inflow_lo && ctr <= G.inflow_hi)) return;
-  const double q = Q / (G.inflow_hi - G.inflow_lo);
+  const double wd = G.inflow_width[P.level];
+  if (!(wd > 0.0)) return;  // no line centre of this level in the segment
+  const double q = Q / wd;
   const bool low = side == 0 || side == 2;
   const double sg = low ? 1.0 : -1.0;
   auto cell = [&](int a, int line) { return xs ? e.tix(a, line) : e.tix(line, a); };

@@ -603,6 +603,25 @@ int geoflood_init_forest(const geoflood_config* cfg, void* stream,
     G.hydro_t[k] = k < c.n_hydro ? c.hydro_t[k] : 0.0;
     G.hydro_q[k] = k < c.n_hydro ? c.hydro_q[k] : 0.0;
   }
+  // the segment's width at each level: its line centres times the cell size
+  for (int L = 0; L <= GF_MAXLEV; ++L) {
+    G.inflow_width[L] = 0.0;
+    if (c.n_hydro <= 0 || L > c.maxlevel) continue;
+    const bool xs = c.inflow_side <= 1;
+    const long long N = (long long)(xs ? c.mj : c.mi) * c.mx << L;
+    const double lo = xs ? c.ylower : c.xlower, hi = xs ? c.yupper : c.xupper;
+    const double d = (hi - lo) / (double)N;
+    long long J0 = (long long)std::floor((c.inflow_lo - lo) / d) - 1;
+    long long J1 = (long long)std::ceil((c.inflow_hi - lo) / d) + 1;
+    if (J0 < 0) J0 = 0;
+    if (J1 > N - 1) J1 = N - 1;
+    long long n = 0;
+    for (long long J = J0; J <= J1; ++J) {
+      const double ctr = lo + ((double)J + 0.5) * d;
+      if (ctr >= c.inflow_lo && ctr <= c.inflow_hi) ++n;
+    }
+    G.inflow_width[L] = (double)n * d;
+  }
 
   const size_t TT = (size_t)G.T * G.T;
   const size_t cap = (size_t)ctx->cap;

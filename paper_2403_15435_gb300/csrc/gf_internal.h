@@ -99,6 +99,9 @@ struct GfGeom {
   int n_hydro, inflow_side;
   double inflow_lo, inflow_hi, inflow_tau;
   double hydro_t[16], hydro_q[16];
+  // per level: lines (rows or columns of the side) whose centre lies in
+  // the segment, times the cell size
+  double inflow_width[GF_MAXLEV + 1];
 };
 
 // Everything a kernel needs to find patches and their data.

@@ -68,6 +68,8 @@ class Config:
     # in m^3/s through the segment [inflow_lo, inflow_hi] of side
     # inflow_side (0 left, 1 right, 2 bottom, 3 top); () = no inflow;
     # inflow_tau is the minimum interior depth of the boundary rule
+    # level subcycling: level L takes 2^(L - minlevel) steps per macro step
+    subcycle: int = 0
     hydrograph: Tuple[Tuple[float, float], ...] = ()
     inflow_side: int = 0
     inflow_lo: float = 0.0
