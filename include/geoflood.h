@@ -130,6 +130,17 @@ typedef struct {
   int n_hydro, inflow_side;
   double inflow_lo, inflow_hi, inflow_tau;
   double hydro_t[16], hydro_q[16];
+  /* Level subcycling (0 or 1; no effect when maxlevel = minlevel): one
+   * step of geoflood_step becomes a macro step of DT in which level L takes
+   * 2^(L - minlevel) steps of DT / 2^(L - minlevel), run as 2^(maxlevel -
+   * minlevel) fine substeps; at each, the levels due step together, and
+   * ghost cells next to a coarser level between two of its steps take that
+   * level's state interpolated linearly in time.  Every level steps at the
+   * first substep, whose Courant numbers are checked (a violation retakes
+   * the macro step with a smaller DT); later substeps are not checked, their
+   * rates bound the next DT = cfl_desired / max_L(cmax_L / n_L).  Steps and
+   * max_steps count macro steps; the patch step has a single variant. */
+  int subcycle;
 } geoflood_config;
 
 typedef struct geoflood_ctx geoflood_ctx;

@@ -43,6 +43,35 @@ struct Geo {
     else base = V.b;
     return base + (size_t)p * G.T * G.T;
   }
+  // Buffer holding patch p's latest state.  With level subcycling, during a
+  // macro step (sub_k > 0) a level with period P = 2^(maxlevel - L) has
+  // taken ceil(sub_k / P) steps, each flipping its buffers.
+  __device__ int cur_of(int p) const {
+    const GfPatch& P = V.patch[p];
+    const GfCtl& C = V.ctl[P.scen];
+    if (!G.subcycle || C.sub_k == 0) return C.cur;
+    const int per = 1 << (G.maxlevel - P.level);
+    const int st = (C.sub_k + per - 1) / per;
+    return C.cur ^ (st & 1);
+  }
+  // (h, hu, hv, b) of cell c of patch p at the time of the substep about to
+  // run: its latest state, or for a level between two of its steps the
+  // linear interpolation in time of h, hu, hv between the states before and
+  // after its latest step
+  __device__ void load_now(int p, int c, double (&o)[4]) const {
+    const int cb = cur_of(p);
+    load(p, cb, c, o);
+    if (!G.subcycle) return;
+    const GfPatch& P = V.patch[p];
+    const int k = V.ctl[P.scen].sub_k;
+    const int per = 1 << (G.maxlevel - P.level);
+    const int r = k % per;
+    if (r == 0) return;
+    double old[4];
+    load(p, cb ^ 1, c, old);
+    const double a = (double)r / (double)per;
+    for (int f = 0; f < 3; ++f) o[f] = (1.0 - a) * old[f] + a * o[f];
+  }
   // (h, hu, hv, b) of cell c of patch p in buffer buf, in FP64; in the
   // deviation form h = w - b exactly and b is the bed minus eta0
   __device__ void load(int p, int buf, int c, double (&o)[4]) const {
@@ -70,7 +99,6 @@ struct Geo {
 template <typename T>
 __device__ void value_at(const Geo<T>& e, int s, int L, long long I,
                          long long J, double (&out)[4], int* err) {
-  const int cur = e.V.ctl[s].cur;
   for (int l = L; l >= 0; --l) {
     const long long Il = I >> (L - l), Jl = J >> (L - l);
     const int p = e.leaf(s, l, Il, Jl);
@@ -78,7 +106,7 @@ __device__ void value_at(const Geo<T>& e, int s, int L, long long I,
       const GfPatch P = e.V.patch[p];
       const int c = e.tix((int)(Il - (long long)P.px * e.G.M),
                           (int)(Jl - (long long)P.py * e.G.M));
-      e.load(p, cur, c, out);
+      e.load_now(p, c, out);
       return;
     }
   }
@@ -90,7 +118,7 @@ __device__ void value_at(const Geo<T>& e, int s, int L, long long I,
       const GfPatch P = e.V.patch[p];
       const int c = e.tix((int)(Ic - (long long)P.px * e.G.M),
                           (int)(Jc - (long long)P.py * e.G.M));
-      e.load(p, cur, c, v[ch]);
+      e.load_now(p, c, v[ch]);
     } else {
       double w[4][4];
       for (int gc = 0; gc < 4; ++gc) {
@@ -104,7 +132,7 @@ __device__ void value_at(const Geo<T>& e, int s, int L, long long I,
         const GfPatch P = e.V.patch[pg];
         const int c = e.tix((int)(Ig - (long long)P.px * e.G.M),
                             (int)(Jg - (long long)P.py * e.G.M));
-        e.load(pg, cur, c, w[gc]);
+        e.load_now(pg, c, w[gc]);
       }
       for (int f = 0; f < 4; ++f)
         v[ch][f] = 0.25 * ((w[0][f] + w[1][f]) + (w[2][f] + w[3][f]));
@@ -132,7 +160,7 @@ __device__ void fill_cell(const Geo<T>& e, int s, int L, long long I,
     const int c = e.tix((int)(I - (long long)P.px * e.G.M),
                         (int)(J - (long long)P.py * e.G.M));
     double o4[4];
-    e.load(p, e.V.ctl[s].cur, c, o4);
+    e.load_now(p, c, o4);
     out[0] = o4[0];
     out[1] = o4[1];
     out[2] = o4[2];
@@ -429,7 +457,10 @@ __global__ void k_inflow(const __grid_constant__ GfGeom G, const __grid_constant
   const GfPatch P = V.patch[p];
   const GfCtl* C = V.ctl + P.scen;
   if (only_accepted && !C->accepted) return;
-  const double Q = hydro_discharge(G, C->t);
+  // time of the ghost values: the macro step's start plus the substep about
+  // to run (level subcycling), else the state's time
+  const double tg = G.subcycle ? C->t + (double)C->sub_k * (C->dt_use / (double)G.sub_K) : C->t;
+  const double Q = hydro_discharge(G, tg);
   if (!(Q > 0.0)) return;
   Geo<T> e(G, V);
   const int side = G.inflow_side;
@@ -448,7 +479,7 @@ __global__ void k_inflow(const __grid_constant__ GfGeom G, const __grid_constant
   const bool low = side == 0 || side == 2;
   const double sg = low ? 1.0 : -1.0;
   auto cell = [&](int a, int line) { return xs ? e.tix(a, line) : e.tix(line, a); };
-  T* qq = e.qp(p, C->cur);
+  T* qq = e.qp(p, e.cur_of(p));
   const T* bb = e.bp(p);
   const int nf = xs ? 1 : 2, tf = xs ? 2 : 1;  // normal, tangential field
   const int ci = cell(low ? 0 : M - 1, l);
@@ -477,6 +508,28 @@ __global__ void k_inflow(const __grid_constant__ GfGeom G, const __grid_constant
         qq[tf * TT + dst] = wall ? -qq[tf * TT + src] : qq[tf * TT + src];
       }
     }
+  }
+}
+
+// End of an accepted subcycled macro step (sub_k back at 0): a patch of
+// level minlevel stepped once, from the current buffer into the other; its
+// new state (tile and, in the deviation form, compensation terms) is
+// copied back into the current buffer, where every finer level already is.
+template <typename T>
+__global__ void k_subcycle_sync(const __grid_constant__ GfGeom G, const __grid_constant__ GfView V) {
+  const int p = blockIdx.x;
+  const GfPatch P = V.patch[p];
+  const GfCtl* C = V.ctl + P.scen;
+  if (P.level != G.minlevel || !C->accepted || C->sub_k != 0) return;
+  Geo<T> e(G, V);
+  const int cur = C->cur, M = G.M, TT = G.T * G.T;
+  const T* s = e.qp(p, cur ^ 1);
+  T* d = e.qp(p, cur);
+  for (int k = threadIdx.x; k < 3 * TT; k += blockDim.x) d[k] = s[k];
+  if constexpr (Geo<T>::DEV) {
+    const float* ls = V.lof[cur ^ 1] + (size_t)p * 3 * M * M;
+    float* ld = V.lof[cur] + (size_t)p * 3 * M * M;
+    for (int k = threadIdx.x; k < 3 * M * M; k += blockDim.x) ld[k] = ls[k];
   }
 }
 
@@ -512,7 +565,7 @@ __global__ void k_ghost_other(const __grid_constant__ GfGeom G, const __grid_con
   const GfCtl* C = V.ctl + P.scen;
   if (!C->accepted) return;
   Geo<T> e(G, V);
-  T* q = e.qp(p, C->cur);
+  T* q = e.qp(p, e.cur_of(p));
   const int c = e.tix(i, j);
   const long long I = (long long)P.px * M + i, J = (long long)P.py * M + j;
   const double bt = (double)e.bp(p)[c];
@@ -1137,6 +1190,14 @@ int launch_ghost_rest(const GfGeom& g, const GfView& v, const int* regs, int nre
   return ok();
 }
 
+
+int launch_subcycle_sync(const GfGeom& g, const GfView& v, void* stream) {
+  if (!g.subcycle || v.npatch <= 0) return 0;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (v.prec) k_subcycle_sync<float><<<v.npatch, 256, 0, st>>>(g, v);
+  else k_subcycle_sync<double><<<v.npatch, 256, 0, st>>>(g, v);
+  return ok();
+}
 
 int launch_inflow(const GfGeom& g, const GfView& v, const int* list, int n,
                   int only_accepted, void* stream) {

@@ -256,6 +256,8 @@ int upload_tables(geoflood_ctx* ctx, int t,
   for (int s = 0; s < ctx->nscen; ++s) {
     ctx->h_scen[s].poff = off;
     ctx->h_scen[s].pcount = (int)lv[s].size();
+    for (int L = 0; L <= GF_MAXLEV; ++L) ctx->h_scen[s].lcount[L] = 0;
+    for (const gf::Leaf& l : lv[s]) ctx->h_scen[s].lcount[l.level]++;
     for (size_t k = 0; k < lv[s].size(); ++k) {
       const gf::Leaf& l = lv[s][k];
       hp[off + k] = GfPatch{l.level, l.px, l.py, s};
@@ -521,7 +523,7 @@ int geoflood_init_forest(const geoflood_config* cfg, void* stream,
     if (c.bc[k] != GEOFLOOD_BC_WALL && c.bc[k] != GEOFLOOD_BC_EXTRAP)
       return GEOFLOOD_ERR_ARG;
   if (c.ngrades < 0 || c.ngrades > 4 || !(c.tag_flux > 0)) return GEOFLOOD_ERR_ARG;
-  if ((c.first_order | c.no_transverse | c.dim_split) & ~1) return GEOFLOOD_ERR_ARG;
+  if ((c.first_order | c.no_transverse | c.dim_split | c.subcycle) & ~1) return GEOFLOOD_ERR_ARG;
   if (c.n_hydro < 0 || c.n_hydro > 16) return GEOFLOOD_ERR_ARG;
   if (c.n_hydro > 0) {
     if (c.inflow_side < 0 || c.inflow_side > 3 || !(c.inflow_hi > c.inflow_lo) ||
@@ -594,6 +596,8 @@ int geoflood_init_forest(const geoflood_config* cfg, void* stream,
   G.first_order = c.first_order;
   G.no_transverse = c.no_transverse;
   G.dim_split = c.dim_split;
+  G.subcycle = c.subcycle && c.maxlevel > c.minlevel ? 1 : 0;
+  G.sub_K = G.subcycle ? 1 << (c.maxlevel - c.minlevel) : 1;
   G.n_hydro = c.n_hydro;
   G.inflow_side = c.inflow_side;
   G.inflow_lo = c.inflow_lo;
@@ -1059,20 +1063,32 @@ int geoflood_step(geoflood_ctx* ctx, double t_target, int max_steps,
         rg.b = pool_event(ctx);
         cudaEventRecordWithFlags(r.a, ctx->st, cudaEventRecordExternal);
       }
-      lrc |= ctx->prec ? gf::launch_patch_step_f32(ctx->G, v, ctx->d_pmass, ctx->variant, ctx->st)
-                       : gf::launch_patch_step_f64(ctx->G, v, ctx->d_pmass, ctx->variant, ctx->st);
-      if (sample) {
-        cudaEventRecordWithFlags(r.b, ctx->st, cudaEventRecordExternal);
-        gr->ev.push_back(r);
-        cudaEventRecordWithFlags(rg.a, ctx->st, cudaEventRecordExternal);
-      }
-      lrc |= gf::launch_ghost_rest(ctx->G, v, ctx->d_glist[ctx->tsel], ctx->nglist[ctx->tsel],
-                                   ctx->st);
-      lrc |= gf::launch_inflow(ctx->G, v, ctx->d_ilist[ctx->tsel], ctx->nilist[ctx->tsel], 1,
-                               ctx->st);
-      if (sample) {
-        cudaEventRecordWithFlags(rg.b, ctx->st, cudaEventRecordExternal);
-        gr->evg.push_back(rg);
+      // one step, or with level subcycling the sub_K substeps of a macro
+      // step (the patches of level minlevel synchronised after the last)
+      for (int sub = 0; sub < ctx->G.sub_K && !lrc; ++sub) {
+        if (sample && sub > 0) {
+          r.a = pool_event(ctx);
+          r.b = pool_event(ctx);
+          rg.a = pool_event(ctx);
+          rg.b = pool_event(ctx);
+          cudaEventRecordWithFlags(r.a, ctx->st, cudaEventRecordExternal);
+        }
+        lrc |= ctx->prec ? gf::launch_patch_step_f32(ctx->G, v, ctx->d_pmass, ctx->variant, ctx->st)
+                         : gf::launch_patch_step_f64(ctx->G, v, ctx->d_pmass, ctx->variant, ctx->st);
+        if (sample) {
+          cudaEventRecordWithFlags(r.b, ctx->st, cudaEventRecordExternal);
+          gr->ev.push_back(r);
+          cudaEventRecordWithFlags(rg.a, ctx->st, cudaEventRecordExternal);
+        }
+        if (sub == ctx->G.sub_K - 1) lrc |= gf::launch_subcycle_sync(ctx->G, v, ctx->st);
+        lrc |= gf::launch_ghost_rest(ctx->G, v, ctx->d_glist[ctx->tsel], ctx->nglist[ctx->tsel],
+                                     ctx->st);
+        lrc |= gf::launch_inflow(ctx->G, v, ctx->d_ilist[ctx->tsel], ctx->nilist[ctx->tsel], 1,
+                                 ctx->st);
+        if (sample) {
+          cudaEventRecordWithFlags(rg.b, ctx->st, cudaEventRecordExternal);
+          gr->evg.push_back(rg);
+        }
       }
     }
     cudaGraph_t graph = nullptr;
@@ -1104,8 +1120,9 @@ int geoflood_step(geoflood_ctx* ctx, double t_target, int max_steps,
     gr->prof = prof;
     gr->variant = ctx->variant;
   }
-  const int per_step = 1 + (ctx->nglist[ctx->tsel] > 0 ? 1 : 0) +
-                       (ctx->nilist[ctx->tsel] > 0 ? 1 : 0);
+  const int per_step = ctx->G.sub_K * (1 + (ctx->nglist[ctx->tsel] > 0 ? 1 : 0) +
+                                       (ctx->nilist[ctx->tsel] > 0 ? 1 : 0)) +
+                       (ctx->G.subcycle ? 1 : 0);
   long long launched = 0;
   const long long limit = (long long)max_steps * 2 + 64;
   while (max_steps > 0) {
@@ -1397,7 +1414,8 @@ int geoflood_autotune(geoflood_ctx* ctx, int reps, int* variant,
   if ((rc = sync_ctl_up(ctx))) return rc;
   GfView v = view(ctx);
   v.done = nullptr;  // no controller: the state does not advance
-  const int nv = gf::patch_step_variants(ctx->G.M, ctx->prec, ctx->G.dim_split);
+  const int nv = gf::patch_step_variants(ctx->G.M, ctx->prec,
+                                        ctx->G.dim_split || ctx->G.subcycle);
   cudaEvent_t a = pool_event(ctx), b = pool_event(ctx);
   int best = 0;
   double best_ms = 1e300;
@@ -1430,7 +1448,8 @@ int geoflood_autotune(geoflood_ctx* ctx, int reps, int* variant,
 
 int geoflood_set_variant(geoflood_ctx* ctx, int variant) {
   if (!ctx || variant < 0 ||
-      variant >= gf::patch_step_variants(ctx->G.M, ctx->prec, ctx->G.dim_split))
+      variant >= gf::patch_step_variants(ctx->G.M, ctx->prec,
+                                         ctx->G.dim_split || ctx->G.subcycle))
     return fail(ctx, GEOFLOOD_ERR_ARG, "set_variant: no such variant");
   ctx->variant = variant;
   // the per-unit volumes of another variant's layout are not reusable

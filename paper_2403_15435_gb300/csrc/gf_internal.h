@@ -36,6 +36,7 @@ struct GfScenario {
   const double* dem[GF_MAXDEM];
   double dx0[GF_MAXDEM], dy0[GF_MAXDEM], ddx[GF_MAXDEM], ddy[GF_MAXDEM];
   int poff, pcount;   // patch range in the table
+  int lcount[GF_MAXLEV + 1];  // patches per level
   long long lut_off;  // offset of this scenario's lookup tables
   int ngauge;
   int pad;
@@ -62,7 +63,13 @@ struct GfCtl {
   int inrow;     // consecutive rejections
   int status;    // GEOFLOOD_* error from the device, 0 if none
   int nonfinite; // a non-finite value was produced
+  // level subcycling: the fine substep about to run (0 .. sub_K - 1; 0 at
+  // macro-step boundaries), whether the macro step in flight was rejected,
+  // and the largest rate cmax / n_L seen in it (bits of a double)
+  int sub_k;
+  int sub_rej;
   int pad;
+  unsigned long long rmax_bits;
 };
 
 // Forest geometry and physics shared by every scenario.
@@ -102,6 +109,9 @@ struct GfGeom {
   // per level: lines (rows or columns of the side) whose centre lies in
   // the segment, times the cell size
   double inflow_width[GF_MAXLEV + 1];
+  // level subcycling (maxlevel > minlevel): level L takes 2^(L - minlevel)
+  // steps per macro step, run as sub_K = 2^(maxlevel - minlevel) substeps
+  int subcycle, sub_K;
 };
 
 // Everything a kernel needs to find patches and their data.
@@ -193,6 +203,11 @@ int launch_ghost_rest(const GfGeom& g, const GfView& v, const int* regs, int nre
 // scenarios whose last step was rejected.
 int launch_inflow(const GfGeom& g, const GfView& v, const int* list, int n,
                   int only_accepted, void* stream);
+// Level subcycling, after the last substep of an accepted macro step: the
+// patches of level minlevel (one step, an odd number) copy their new state
+// (tile and FP32 compensation terms) into the current buffer, which every
+// other level is back in after its even number of steps.
+int launch_subcycle_sync(const GfGeom& g, const GfView& v, void* stream);
 // Beds of patches [first, first + count), or of list[0..count) if list.
 int launch_topo(const GfGeom& g, const GfView& v, int first, int count,
                 void* stream, const int* list = nullptr);

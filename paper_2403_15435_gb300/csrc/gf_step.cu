@@ -24,6 +24,9 @@ __global__ void k_ctl_begin(GfCtl* ctl, int nscen, double t_target,
   C->inrow = 0;
   C->accepted = 0;
   C->cmax_bits = 0ull;
+  C->rmax_bits = 0ull;
+  C->sub_k = 0;
+  C->sub_rej = 0;
   C->step_nclip = 0ull;
   C->step_clipvol = 0.0;
   C->nonfinite = 0;

@@ -307,7 +307,13 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
   uint64_t* bar = reinterpret_cast<uint64_t*>(smraw + Lo::OFF_BAR);
 
   const int tid = threadIdx.x;
-  const int cur = C->cur;
+  // level subcycling: this level's period in fine substeps, its buffer
+  // (ceil(sub_k / per) steps taken in the macro step so far) and its time
+  // step (the macro step's share for the level)
+  const bool subc = G.subcycle != 0;
+  const int per = subc ? 1 << (G.maxlevel - Pt.level) : 1;
+  const int cur = subc ? C->cur ^ ((C->sub_k / per) & 1) : C->cur;
+  const double dtp = subc ? (C->dt_use / (double)G.sub_K) * (double)per : C->dt_use;
   const R* qs;
   R* qd;
   const R* bs;
@@ -380,7 +386,7 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
   if (tid == 0) {
     if constexpr (DEV) {
       // FP32 from the host's per-level tables: one conversion per patch
-      const float dtf32 = (float)C->dt_use;
+      const float dtf32 = (float)dtp;
       rscal[0] = G.gf;
       rscal[1] = G.drytolf;
       rscal[2] = dtf32 * G.inv_dxf[Pt.level];
@@ -396,14 +402,14 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
       const double dy0 = (G.yupper - G.ylower) / (double)NYL;
       scal[0] = dx0;
       scal[1] = dy0;
-      scal[2] = C->dt_use / dx0;
-      scal[3] = C->dt_use / dy0;
+      scal[2] = dtp / dx0;
+      scal[3] = dtp / dy0;
       rscal[0] = (R)G.g;
       rscal[1] = (R)G.drytol;
       rscal[2] = (R)scal[2];
       rscal[3] = (R)scal[3];
       rscal[4] = (R)V.scen[Pt.scen].manning_n;
-      rscal[5] = (R)C->dt_use;
+      rscal[5] = (R)dtp;
     }
   }
   const bool push = V.push != 0 && V.nbr != nullptr;
@@ -475,7 +481,7 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
   // nothing (its update is the identity on the surface, zero momenta)
   const bool skip_writes = same_in && !anywet;
   if (V.same != nullptr && tid == 0) V.same[unit] = anywet ? 0 : 1;
-  if (has_gauge && C->accepted)
+  if (has_gauge && C->accepted && (!subc || C->sub_k == 0))
     sample_gauges<R, DEV, MP, M>(V, Pt.scen, C, p, ox, oy, s0, shu, shv, sb,
                                  M != MP || mom_issued);
   if (skip_writes) {
@@ -846,7 +852,8 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
       vs = warp_sum_tree(vs);
       if (lane == 0) {
         const float cx = mx * G.inv_dxf[Pt.level], cy = my * G.inv_dyf[Pt.level];
-        const double cm = (double)(cx > cy ? cx : cy);
+        double cm = (double)(cx > cy ? cx : cy);
+        if (subc) cm = cm * (double)per / (double)G.sub_K;  // cmax / n_L
         atomicMax(&C->cmax_bits, (unsigned long long)__double_as_longlong(cm));
         pmass[unit] = vs * G.areal[Pt.level];
       }
@@ -872,7 +879,8 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
         vs += red[2 * NW + w];
       }
       const double cx = mx / dx, cy = my / dy;
-      const double cm = cx > cy ? cx : cy;
+      double cm = cx > cy ? cx : cy;
+      if (subc) cm = cm * (double)per / (double)G.sub_K;  // cmax / n_L
       atomicMax(&C->cmax_bits, (unsigned long long)__double_as_longlong(cm));
       pmass[unit] = vs * (dx * dy);
     }
@@ -1013,6 +1021,86 @@ __device__ __forceinline__ int whole_tile(const GfGeom& G, const GfView& V,
 // a fixed order, rejects the step and sets a smaller dt when dt*cmax exceeds
 // cfl_max, else accepts it (swaps the state buffers, advances t) and picks
 // the next dt = cfl_desired / cmax, clipped to land on t_target.
+// Controller of a subcycled macro step (thread 0 of the last CTA of each
+// substep launch, per scenario).  The macro step of DT = dt_use runs as
+// sub_K substeps; the rates cmax / n_L of the levels that stepped arrived in
+// cmax_bits.  Substep 0 (every level steps) is checked against cfl_max: a
+// violation rejects the macro step, whose remaining substeps then do
+// nothing, and it is retaken with DT = cfl_desired / rate.  Later substeps
+// are not checked; their rates bound the next DT.  After the last substep
+// the time advances by DT and the next macro step is set up.
+static __device__ void subcycle_finish(const GfGeom& G, const GfView& V, volatile GfCtl* C,
+                                       int s, double vol, int cells_per_patch) {
+  const int K = G.sub_K, k = C->sub_k;
+  const double rate = __longlong_as_double((long long)C->cmax_bits);
+  C->cmax_bits = 0ull;
+  const double DT = C->dt_use;
+  bool end = k == K - 1, go_on = true;
+  if (C->nonfinite) {
+    C->status = -5;  // GEOFLOOD_ERR_NAN
+    C->active = 0;
+    C->accepted = 0;
+    go_on = false;
+  } else if (C->sub_rej) {
+    C->accepted = 0;
+  } else if (k == 0 && DT * rate > G.cfl_max) {
+    C->dt_next = G.cfl_desired / rate;
+    C->rejects = C->rejects + 1;
+    C->accepted = 0;
+    C->step_nclip = 0ull;
+    C->step_clipvol = 0.0;
+    C->rmax_bits = 0ull;
+    C->inrow = C->inrow + 1;
+    C->sub_rej = 1;
+    if (C->inrow > GF_MAXSTEP_REJECT) {
+      C->status = -4;  // GEOFLOOD_ERR_CFL
+      C->active = 0;
+      go_on = false;
+    }
+  } else {
+    // the substep stands: count the levels that stepped
+    unsigned long long cells = 0ull;
+    for (int L = G.minlevel; L <= G.maxlevel; ++L)
+      if (k % (1 << (G.maxlevel - L)) == 0)
+        cells += (unsigned long long)V.scen[s].lcount[L] * (unsigned long long)cells_per_patch;
+    C->cell_updates = C->cell_updates + cells;
+    const double rm = __longlong_as_double((long long)C->rmax_bits);
+    if (rate > rm) C->rmax_bits = (unsigned long long)__double_as_longlong(rate);
+    C->nclip = C->nclip + (long long)C->step_nclip;
+    C->clipvol = C->clipvol + C->step_clipvol;
+    C->step_nclip = 0ull;
+    C->step_clipvol = 0.0;
+    C->accepted = 1;
+    if (end) {
+      C->inrow = 0;
+      C->t = C->last ? C->t_target : C->t + DT;
+      C->steps = C->steps + 1;
+      C->taken = C->taken + 1;
+      C->mass = vol;
+      const double r = __longlong_as_double((long long)C->rmax_bits);
+      C->rmax_bits = 0ull;
+      if (r > 0.0) {
+        const double dn = G.cfl_desired / r;
+        C->dt_next = dn < G.dt_max ? dn : G.dt_max;
+      }
+    }
+  }
+  if (!go_on) return;
+  if (!end) {
+    C->sub_k = k + 1;
+    return;
+  }
+  C->sub_k = 0;
+  C->sub_rej = 0;
+  if (!(C->t < C->t_target) || C->taken >= C->max_steps) {
+    C->active = 0;
+  } else {
+    const double rem = C->t_target - C->t;
+    if (C->dt_next < rem) { C->dt_use = C->dt_next; C->last = 0; }
+    else { C->dt_use = rem; C->last = 1; }
+  }
+}
+
 template <int NT>
 __device__ void step_finish(const GfGeom& G, const GfView& V,
                             const double* pmass, double* red, int nsub,
@@ -1041,7 +1129,7 @@ __device__ void step_finish(const GfGeom& G, const GfView& V,
       continue;
     }
     const int off = V.scen[s].poff * nsub, n = V.scen[s].pcount * nsub;
-    if (tid == 0)
+    if (tid == 0 && !G.subcycle)
       C->cell_updates = C->cell_updates +
                         (unsigned long long)V.scen[s].pcount * (unsigned long long)cells_per_patch;
     double v = 0.0;
@@ -1049,7 +1137,11 @@ __device__ void step_finish(const GfGeom& G, const GfView& V,
     v = warp_sum_tree(v);
     if (lane == 0) red[wid] = v;
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && G.subcycle) {
+      double vol = 0.0;
+      for (int w = 0; w < NW; ++w) vol += red[w];
+      subcycle_finish(G, V, C, s, vol, cells_per_patch);
+    } else if (tid == 0) {
       double vol = 0.0;
       for (int w = 0; w < NW; ++w) vol += red[w];
       const double cmax = __longlong_as_double((long long)C->cmax_bits);
@@ -1193,7 +1285,13 @@ __global__ void __launch_bounds__(NT, MINB)
   const GfPatch Pt = V.patch[p];
   int wet = 0;
   bool wrote = true;
-  if (V.ctl[Pt.scen].active)
+  bool run = V.ctl[Pt.scen].active != 0;
+  if (run && G.subcycle) {
+    // level subcycling: only the levels due at this substep step
+    const GfCtl& C = V.ctl[Pt.scen];
+    run = !C.sub_rej && C.sub_k % (1 << (G.maxlevel - Pt.level)) == 0;
+  }
+  if (run)
     wet = patch_body<P, MP, M, NT, DS>(G, V, pmass, smraw, p, sub, nullptr, &wrote);
   else wrote = false;
   if (sched && sub == 0 && threadIdx.x == 0) {

@@ -57,6 +57,7 @@ class _Cfg(C.Structure):
         ("n_hydro", C.c_int), ("inflow_side", C.c_int),
         ("inflow_lo", C.c_double), ("inflow_hi", C.c_double), ("inflow_tau", C.c_double),
         ("hydro_t", C.c_double * 16), ("hydro_q", C.c_double * 16),
+        ("subcycle", C.c_int),
     ]
 
 
@@ -184,6 +185,7 @@ def config_struct(cfg: inputs.Config, num_scenarios=1, max_patches=None,
     c.inflow_lo = float(getattr(cfg, "inflow_lo", 0.0))
     c.inflow_hi = float(getattr(cfg, "inflow_hi", 0.0))
     c.inflow_tau = float(getattr(cfg, "inflow_tau", 1e-4))
+    c.subcycle = int(getattr(cfg, "subcycle", 0))
     c.num_scenarios = int(num_scenarios)
     if max_patches is None:
         per = cfg.mi * cfg.mj * (4 ** cfg.maxlevel)
