@@ -307,13 +307,19 @@ def test_kernel_variants_agree_on_the_full_workload(prec):
     prob.cfg.precision = prec
     g = geoflood.Forest(prob.cfg, prob.dem)
     nvar = int(np.count_nonzero(np.isfinite(g.autotune(1)[1])))
+    ang = np.linspace(0.0, 2 * np.pi, 16, endpoint=False)
+    rad = np.linspace(250.0, 900.0, 16)
+    gauges = np.stack([1024.0 + rad * np.cos(ang), 1024.0 + rad * np.sin(ang)], 1)
     ref = None
     for variant in range(nvar):
         g = geoflood.Forest(prob.cfg, prob.dem)
         g.set_state(prob.ic)
+        g.set_gauges(gauges)
         g.set_variant(variant)
+        # several calls: the work list restarts at each
+        g.step(20.0)
         g.step(60.0)
-        st = g.read()
+        st = list(g.read()) + list(g.gauges()) + [np.array([g.time()["steps"]])]
         if ref is None:
             ref = st
             continue
