@@ -233,6 +233,27 @@ int geoflood_get_time(geoflood_ctx* ctx, int scenario, double* t,
                       double* dt_next, long long* steps, long long* rejects,
                       long long* nclip, double* clipvol);
 
+/* Checkpoint (no passage of the paper; the restart facility that GeoClaw
+ * and ForestClaw runs rely on for long simulations): writes everything a
+ * context needs to continue exactly where it stands into the caller's
+ * buffer buf of cap bytes -- per scenario its Manning n and eta0, DEMs,
+ * forest, time-stepping state and counters, gauges and the current state
+ * (whole tiles; in the FP32 form also the compensation terms), and the
+ * network's parameters, Adam state, scales and tagger.  *size receives the
+ * bytes needed; with buf = NULL or cap too small nothing is written and the
+ * call returns CAPACITY (call once to size the buffer).  The record is
+ * plain bytes of this host's byte order.  Errors: ARG, CUDA, CAPACITY. */
+int geoflood_save(geoflood_ctx* ctx, void* buf, size_t cap, size_t* size);
+
+/* Resume from a checkpoint of geoflood_save: ctx must have been created
+ * with the same configuration (compared byte for byte) and precision.
+ * Replaces the context's scenarios, forests, DEMs (beds recomputed), state,
+ * time-stepping state, gauges and network; stepping on continues bit for
+ * bit as the saved context would have.  Errors: ARG (not a checkpoint,
+ * another configuration, corrupt or truncated record), CAPACITY, OOM, CUDA;
+ * after an error the context's state is unspecified. */
+int geoflood_load(geoflood_ctx* ctx, const void* buf, size_t size);
+
 /* Advance every scenario towards t_target by at most max_steps accepted
  * steps of the adaptive scheme (Sec. 3.2, 3.3, Eq. manning; CFL rule of
  * Sec. 5.1): ghost fill, unsplit second-order step with transverse
@@ -263,6 +284,10 @@ int geoflood_mass(geoflood_ctx* ctx, int scenario, double* mass);
  * step. */
 int geoflood_set_gauges(geoflood_ctx* ctx, int scenario, const double* xy,
                         int n);
+
+/* Number of gauges of a scenario (as set by geoflood_set_gauges or
+ * restored by geoflood_load): the rows geoflood_gauges writes. */
+int geoflood_gauge_count(geoflood_ctx* ctx, int scenario, int* n);
 
 /* Latest gauge samples out[n][5] = (t, h, hu, hv, eta) and arrival times
  * arrival[n] (first sample time with h > 0.01 m, -1 if none); either

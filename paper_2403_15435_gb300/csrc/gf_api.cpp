@@ -1341,6 +1341,12 @@ int geoflood_set_gauges(geoflood_ctx* ctx, int s, const double* xy, int n) {
   return 0;
 }
 
+int geoflood_gauge_count(geoflood_ctx* ctx, int s, int* n) {
+  if (!valid_scen(ctx, s) || !n) return fail(ctx, GEOFLOOD_ERR_ARG, "gauge_count: bad argument");
+  *n = ctx->h_scen[s].ngauge;
+  return 0;
+}
+
 int geoflood_gauges(geoflood_ctx* ctx, int s, double* out, double* arrival) {
   if (!valid_scen(ctx, s)) return fail(ctx, GEOFLOOD_ERR_ARG, "gauges: bad scenario");
   const int n = ctx->h_scen[s].ngauge;
@@ -1762,6 +1768,297 @@ int geoflood_set_tagger(geoflood_ctx* ctx, int tagger, float threshold) {
   ctx->cnn.tagger = tagger;
   ctx->cnn.logit_thr = std::log(threshold / (1.f - threshold));
   return 0;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Checkpoint and resume.  The checkpoint is a flat byte record:
+//   "GFCK", version, sizeof(geoflood_config), the configuration bytes,
+//   precision, patch size, scenario count, then per scenario: Manning n and
+//   eta0, the DEMs (count, then per DEM nx, ny, x0, y0, dx, dy, the nodes),
+//   the leaves (count, then level, px, py), the time-stepping state (t,
+//   dt_next, steps, rejects, nclip, clipvol, cell and wet-cell updates),
+//   the gauges (count, positions, latest sample, arrival), the current state
+//   buffer of its patches (whole tiles, ghosts included; in the FP32 form
+//   also the compensation terms); then the network (parameters, Adam
+//   moments and step, input scales, tagger, threshold; or none).
+// Beds are recomputed from the DEMs on load (the same kernel, so the same
+// values).
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Bytes {
+  unsigned char* p;
+  size_t cap, n = 0;
+  void put(const void* src, size_t k) {
+    if (p && n + k <= cap) std::memcpy(p + n, src, k);
+    n += k;
+  }
+  template <typename T> void val(const T& v) { put(&v, sizeof(T)); }
+};
+
+struct Reader {
+  const unsigned char* p;
+  size_t n, at = 0;
+  bool ok = true;
+  void get(void* dst, size_t k) {
+    if (!ok || at + k > n) { ok = false; return; }
+    std::memcpy(dst, p + at, k);
+    at += k;
+  }
+  template <typename T> T val() { T v{}; get(&v, sizeof(T)); return v; }
+};
+
+const char kMagic[4] = {'G', 'F', 'C', 'K'};
+const int kVersion = 1;
+
+}  // namespace
+
+extern "C" {
+
+int geoflood_save(geoflood_ctx* ctx, void* buf, size_t cap, size_t* size) {
+  if (!ctx || !size) return fail(ctx, GEOFLOOD_ERR_ARG, "save: bad argument");
+  int rc = sync_ctl_down(ctx);
+  if (rc) return rc;
+  Bytes w{static_cast<unsigned char*>(buf), buf ? cap : 0};
+  w.put(kMagic, 4);
+  w.val(kVersion);
+  w.val((int)sizeof(geoflood_config));
+  w.put(&ctx->cfg, sizeof(geoflood_config));
+  w.val(ctx->prec);
+  w.val(ctx->G.M);
+  w.val(ctx->nscen);
+  const size_t TT = (size_t)ctx->G.T * ctx->G.T, MM = (size_t)ctx->G.M * ctx->G.M;
+  const size_t esz = ctx->prec ? sizeof(float) : sizeof(double);
+  std::vector<unsigned char> tmp;
+  auto dev = [&](const void* d, size_t bytes) {
+    tmp.resize(bytes);
+    if (bytes) {
+      if (cudaMemcpyAsync(tmp.data(), d, bytes, cudaMemcpyDeviceToHost, ctx->st) != cudaSuccess ||
+          cudaStreamSynchronize(ctx->st) != cudaSuccess)
+        return false;
+    }
+    w.put(tmp.data(), bytes);
+    return true;
+  };
+  for (int s = 0; s < ctx->nscen; ++s) {
+    const GfScenario& S = ctx->h_scen[s];
+    const GfCtl& C = ctx->h_ctl[s];
+    w.val(S.manning_n);
+    w.val(S.eta0);
+    w.val(S.ndem);
+    for (int k = 0; k < S.ndem; ++k) {
+      w.val(S.dnx[k]); w.val(S.dny[k]);
+      w.val(S.dx0[k]); w.val(S.dy0[k]); w.val(S.ddx[k]); w.val(S.ddy[k]);
+      if (!dev(S.dem[k], (size_t)S.dnx[k] * S.dny[k] * sizeof(double)))
+        return fail(ctx, GEOFLOOD_ERR_CUDA, "save: DEM copy");
+    }
+    const auto& lv = ctx->forests[s].leaves();
+    w.val((int)lv.size());
+    for (const gf::Leaf& l : lv) { w.val(l.level); w.val(l.px); w.val(l.py); }
+    w.val(C.t); w.val(C.dt_next); w.val(C.steps); w.val(C.rejects); w.val(C.nclip);
+    w.val(C.clipvol); w.val(C.cell_updates); w.val(C.wet_updates);
+    w.val(S.ngauge);
+    if (S.ngauge > 0) {
+      if (!dev(ctx->d_gxy[s], 2 * S.ngauge * sizeof(double)) ||
+          !dev(ctx->d_gout[s], 5 * S.ngauge * sizeof(double)) ||
+          !dev(ctx->d_garr[s], S.ngauge * sizeof(double)))
+        return fail(ctx, GEOFLOOD_ERR_CUDA, "save: gauge copy");
+    }
+    const size_t np = (size_t)S.pcount, off = (size_t)S.poff;
+    const void* q = ctx->prec ? (const void*)(ctx->qf[C.cur] + off * 3 * TT)
+                              : (const void*)(ctx->q[C.cur] + off * 3 * TT);
+    if (!dev(q, np * 3 * TT * esz)) return fail(ctx, GEOFLOOD_ERR_CUDA, "save: state copy");
+    if (ctx->prec && !dev(ctx->lof[C.cur] + off * 3 * MM, np * 3 * MM * sizeof(float)))
+      return fail(ctx, GEOFLOOD_ERR_CUDA, "save: compensation copy");
+  }
+  const CnnState& c = ctx->cnn;
+  const int nprm = gf::cnn_nparam();
+  w.val((int)(c.ready ? 1 : 0));
+  if (c.ready) {
+    if (!dev(c.prm, (size_t)nprm * 4) || !dev(c.am, (size_t)nprm * 4) ||
+        !dev(c.av, (size_t)nprm * 4))
+      return fail(ctx, GEOFLOOD_ERR_CUDA, "save: network copy");
+    w.val(c.adam_t);
+  }
+  w.put(c.scale, sizeof(c.scale));
+  w.val(c.tagger);
+  w.val(c.logit_thr);
+  *size = w.n;
+  if (!buf || cap < w.n)
+    return fail(ctx, GEOFLOOD_ERR_CAPACITY,
+                "save: the checkpoint needs " + std::to_string(w.n) + " bytes");
+  return 0;
+}
+
+int geoflood_load(geoflood_ctx* ctx, const void* buf, size_t size) {
+  if (!ctx || !buf) return fail(ctx, GEOFLOOD_ERR_ARG, "load: bad argument");
+  Reader r{static_cast<const unsigned char*>(buf), size};
+  char magic[4];
+  r.get(magic, 4);
+  if (!r.ok || std::memcmp(magic, kMagic, 4) || r.val<int>() != kVersion ||
+      r.val<int>() != (int)sizeof(geoflood_config))
+    return fail(ctx, GEOFLOOD_ERR_ARG, "load: not a checkpoint of this library version");
+  geoflood_config cfg{};
+  r.get(&cfg, sizeof(cfg));
+  if (!r.ok || std::memcmp(&cfg, &ctx->cfg, sizeof(cfg)) || r.val<int>() != ctx->prec ||
+      r.val<int>() != ctx->G.M || r.val<int>() != ctx->nscen)
+    return fail(ctx, GEOFLOOD_ERR_ARG, "load: the checkpoint was taken with another configuration");
+  const size_t TT = (size_t)ctx->G.T * ctx->G.T, MM = (size_t)ctx->G.M * ctx->G.M;
+  const size_t esz = ctx->prec ? sizeof(float) : sizeof(double);
+  struct Scen {
+    double manning, eta0;
+    std::vector<std::vector<double>> z;
+    std::vector<int> nx, ny;
+    std::vector<double> x0, y0, dx, dy;
+    std::vector<gf::Leaf> leaves;
+    GfCtl ctl{};
+    int ngauge = 0;
+    std::vector<double> gxy, gout, garr;
+    std::vector<unsigned char> q, lo;
+  };
+  std::vector<Scen> sc(ctx->nscen);
+  size_t total = 0;
+  for (int s = 0; s < ctx->nscen && r.ok; ++s) {
+    Scen& x = sc[s];
+    x.manning = r.val<double>();
+    x.eta0 = r.val<double>();
+    const int ndem = r.val<int>();
+    if (!r.ok || ndem < 0 || ndem > GF_MAXDEM) return fail(ctx, GEOFLOOD_ERR_ARG, "load: corrupt DEM list");
+    for (int k = 0; k < ndem && r.ok; ++k) {
+      x.nx.push_back(r.val<int>()); x.ny.push_back(r.val<int>());
+      x.x0.push_back(r.val<double>()); x.y0.push_back(r.val<double>());
+      x.dx.push_back(r.val<double>()); x.dy.push_back(r.val<double>());
+      if (!r.ok || x.nx.back() < 2 || x.ny.back() < 2 ||
+          (size_t)x.nx.back() * x.ny.back() * 8 > size)
+        return fail(ctx, GEOFLOOD_ERR_ARG, "load: corrupt DEM");
+      x.z.emplace_back((size_t)x.nx.back() * x.ny.back());
+      r.get(x.z.back().data(), x.z.back().size() * 8);
+    }
+    const int nl = r.val<int>();
+    if (!r.ok || nl < 1 || nl > ctx->cap) return fail(ctx, GEOFLOOD_ERR_ARG, "load: corrupt leaf list");
+    for (int k = 0; k < nl && r.ok; ++k) {
+      gf::Leaf l;
+      l.level = r.val<int>(); l.px = r.val<int>(); l.py = r.val<int>();
+      if (l.level < ctx->G.minlevel || l.level > ctx->G.maxlevel || l.px < 0 || l.py < 0 ||
+          l.px >= (ctx->G.mi << l.level) || l.py >= (ctx->G.mj << l.level))
+        return fail(ctx, GEOFLOOD_ERR_ARG, "load: corrupt leaf");
+      x.leaves.push_back(l);
+    }
+    x.ctl.t = r.val<double>(); x.ctl.dt_next = r.val<double>();
+    x.ctl.steps = r.val<long long>(); x.ctl.rejects = r.val<long long>();
+    x.ctl.nclip = r.val<long long>(); x.ctl.clipvol = r.val<double>();
+    x.ctl.cell_updates = r.val<unsigned long long>();
+    x.ctl.wet_updates = r.val<unsigned long long>();
+    x.ngauge = r.val<int>();
+    if (!r.ok || x.ngauge < 0 || x.ngauge > ctx->cfg.max_gauges)
+      return fail(ctx, GEOFLOOD_ERR_ARG, "load: corrupt gauges");
+    x.gxy.resize(2 * x.ngauge); x.gout.resize(5 * x.ngauge); x.garr.resize(x.ngauge);
+    r.get(x.gxy.data(), x.gxy.size() * 8);
+    r.get(x.gout.data(), x.gout.size() * 8);
+    r.get(x.garr.data(), x.garr.size() * 8);
+    x.q.resize((size_t)nl * 3 * TT * esz);
+    r.get(x.q.data(), x.q.size());
+    if (ctx->prec) {
+      x.lo.resize((size_t)nl * 3 * MM * sizeof(float));
+      r.get(x.lo.data(), x.lo.size());
+    }
+    total += (size_t)nl;
+  }
+  const int nprm = gf::cnn_nparam();
+  const int has_net = r.val<int>();
+  std::vector<float> prm, am, av;
+  int adam_t = 0;
+  if (has_net) {
+    prm.resize(nprm); am.resize(nprm); av.resize(nprm);
+    r.get(prm.data(), (size_t)nprm * 4);
+    r.get(am.data(), (size_t)nprm * 4);
+    r.get(av.data(), (size_t)nprm * 4);
+    adam_t = r.val<int>();
+  }
+  float scale[4];
+  r.get(scale, sizeof(scale));
+  const int tagger = r.val<int>();
+  const float thr = r.val<float>();
+  if (!r.ok || r.at != size) return fail(ctx, GEOFLOOD_ERR_ARG, "load: truncated or corrupt checkpoint");
+  if ((long long)total > ctx->cap) return fail(ctx, GEOFLOOD_ERR_CAPACITY, "load: too many patches");
+  int rc = sync_ctl_down(ctx);
+  if (rc) return rc;
+  // forests, tables and scenario parameters
+  std::vector<std::vector<gf::Leaf>> lv(ctx->nscen);
+  for (int s = 0; s < ctx->nscen; ++s) {
+    lv[s] = sc[s].leaves;
+    GfScenario& S = ctx->h_scen[s];
+    S.manning_n = sc[s].manning;
+    S.manning_f = (float)sc[s].manning;
+    S.eta0 = sc[s].eta0;
+  }
+  if ((rc = upload_tables(ctx, ctx->tsel, lv))) return rc;
+  for (int s = 0; s < ctx->nscen; ++s) ctx->forests[s].set_leaves(lv[s]);
+  ctx->npatch = (int)total;
+  ctx->generation++;
+  // DEMs (stored in priority order already) and beds
+  for (int s = 0; s < ctx->nscen; ++s) {
+    for (auto p : ctx->d_dem[s]) cudaFree(p);
+    ctx->d_dem[s].clear();
+    GfScenario& S = ctx->h_scen[s];
+    S.ndem = 0;
+    for (size_t k = 0; k < sc[s].z.size(); ++k) {
+      double* d = nullptr;
+      if (cudaMalloc(&d, sc[s].z[k].size() * 8) != cudaSuccess)
+        return fail(ctx, GEOFLOOD_ERR_OOM, "load: DEM allocation");
+      ctx->d_dem[s].push_back(d);
+      CK(cudaMemcpyAsync(d, sc[s].z[k].data(), sc[s].z[k].size() * 8, cudaMemcpyHostToDevice, ctx->st));
+      S.dem[k] = d;
+      S.dnx[k] = sc[s].nx[k]; S.dny[k] = sc[s].ny[k];
+      S.dx0[k] = sc[s].x0[k]; S.dy0[k] = sc[s].y0[k];
+      S.ddx[k] = sc[s].dx[k]; S.ddy[k] = sc[s].dy[k];
+    }
+    S.ndem = (int)sc[s].z.size();
+  }
+  if ((rc = upload_scen(ctx))) return rc;
+  CKL(gf::launch_topo(ctx->G, view(ctx), 0, ctx->npatch, ctx->st), "topo");
+  ctx->launches++;
+  // states into buffer 0, time-stepping state, gauges
+  for (int s = 0; s < ctx->nscen; ++s) {
+    const GfScenario& S = ctx->h_scen[s];
+    const size_t off = (size_t)S.poff;
+    void* q = ctx->prec ? (void*)(ctx->qf[0] + off * 3 * TT) : (void*)(ctx->q[0] + off * 3 * TT);
+    CK(cudaMemcpyAsync(q, sc[s].q.data(), sc[s].q.size(), cudaMemcpyHostToDevice, ctx->st));
+    if (ctx->prec)
+      CK(cudaMemcpyAsync(ctx->lof[0] + off * 3 * MM, sc[s].lo.data(), sc[s].lo.size(),
+                         cudaMemcpyHostToDevice, ctx->st));
+    GfCtl& C = ctx->h_ctl[s];
+    const GfCtl& X = sc[s].ctl;
+    C.t = X.t; C.dt_next = X.dt_next; C.steps = X.steps; C.rejects = X.rejects;
+    C.nclip = X.nclip; C.clipvol = X.clipvol;
+    C.cell_updates = X.cell_updates; C.wet_updates = X.wet_updates;
+    C.cur = 0; C.accepted = 0; C.status = 0; C.inrow = 0; C.nonfinite = 0;
+    C.sub_k = 0; C.sub_rej = 0; C.rmax_bits = 0ull;
+  }
+  if ((rc = sync_ctl_up(ctx))) return rc;
+  for (int s = 0; s < ctx->nscen; ++s) {
+    if ((rc = geoflood_set_gauges(ctx, s, sc[s].gxy.data(), sc[s].ngauge))) return rc;
+    if (sc[s].ngauge > 0) {
+      CK(cudaMemcpyAsync(ctx->d_gout[s], sc[s].gout.data(), sc[s].gout.size() * 8,
+                         cudaMemcpyHostToDevice, ctx->st));
+      CK(cudaMemcpyAsync(ctx->d_garr[s], sc[s].garr.data(), sc[s].garr.size() * 8,
+                         cudaMemcpyHostToDevice, ctx->st));
+    }
+  }
+  // the network
+  if (has_net) {
+    if ((rc = geoflood_cnn_set_params(ctx, prm.data(), nprm))) return rc;
+    CK(cudaMemcpyAsync(ctx->cnn.am, am.data(), (size_t)nprm * 4, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->cnn.av, av.data(), (size_t)nprm * 4, cudaMemcpyHostToDevice, ctx->st));
+    ctx->cnn.adam_t = adam_t;
+  }
+  std::copy(scale, scale + 4, ctx->cnn.scale);
+  ctx->cnn.tagger = has_net ? tagger : GEOFLOOD_TAGGER_PLAIN;
+  ctx->cnn.logit_thr = thr;
+  CK(cudaStreamSynchronize(ctx->st));
+  return forget_same(ctx);
 }
 
 }  // extern "C"

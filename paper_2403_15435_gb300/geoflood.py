@@ -100,6 +100,9 @@ def lib():
                 "geoflood_set_topos": [vp, ip, ip, C.POINTER(dp), C.POINTER(ip), C.POINTER(ip)]
                                       + [dp] * 4,
                 "geoflood_npatch": [vp, ip, pi],
+                "geoflood_save": [vp, vp, C.c_size_t, C.POINTER(C.c_size_t)],
+                "geoflood_gauge_count": [vp, ip, pi],
+                "geoflood_load": [vp, vp, C.c_size_t],
                 "geoflood_patch_info": [vp, ip, pi, pi, pi],
                 "geoflood_write_patches": [vp, ip, dp, dp, dp],
                 "geoflood_read_patches": [vp, ip, dp, dp, dp, dp],
@@ -228,6 +231,21 @@ class Forest:
     def set_scenario(self, s, manning_n, eta0):
         self._check(lib().geoflood_set_scenario(self._h, s, manning_n, eta0))
 
+    def save(self):
+        """Checkpoint of the whole context (geoflood_save) as bytes."""
+        n = C.c_size_t()
+        rc = lib().geoflood_save(self._h, None, 0, C.byref(n))
+        if rc not in (0, -8):
+            self._check(rc)
+        buf = (C.c_ubyte * n.value)()
+        self._check(lib().geoflood_save(self._h, C.cast(buf, C.c_void_p), n.value, C.byref(n)))
+        return bytes(buf)
+
+    def load(self, data):
+        """Resume from a checkpoint of save() (same configuration)."""
+        buf = (C.c_ubyte * len(data)).from_buffer_copy(data)
+        self._check(lib().geoflood_load(self._h, C.cast(buf, C.c_void_p), len(data)))
+
     def set_topo(self, dem, s=0):
         """One DEM, or a list of up to 4 overlapping DEMs (Sec. 6.2)."""
         if isinstance(dem, (list, tuple)):
@@ -340,7 +358,9 @@ class Forest:
         self._check(lib().geoflood_set_gauges(self._h, s, _p(xy), len(xy)))
 
     def gauges(self, s=0):
-        n = self._ng.get(s, 0)
+        c = C.c_int()
+        self._check(lib().geoflood_gauge_count(self._h, s, C.byref(c)))
+        n = c.value
         out = np.empty((n, 5))
         arr = np.empty(n)
         self._check(lib().geoflood_gauges(self._h, s, _p(out), _p(arr)))
