@@ -374,6 +374,54 @@ def flood_speed(patch: int = 32, minlevel: int = 0, maxlevel: int = 3,
     return Problem("flood_speed", cfg, flat_dem(cfg), ic, t_end)
 
 
+def canyon_plain(patch: int = 32, minlevel: int = 0, maxlevel: int = 4,
+                 seed: int = SEED_BASE + 7, dem_spacing: float = 10.0,
+                 depth: float = 55.0, precision: int = 1) -> Problem:
+    """Large AMR workload (the Malpasset set-up's shape, Sec. 6.2-6.4): a
+    17 km x 9 km domain of 1 km blocks; for x < 10 km a canyon -- fractal
+    terrain 60-120 m high cut 50 m deep by a meandering channel (centre line
+    a seeded sinusoid of 800 m amplitude and 3 km wavelength, width varying
+    between 100 and 300 m) falling 0.004 per metre seawards -- then a
+    coastal plain at slope 0.002 down to the sea at x = 17 km; a reservoir
+    in the channel upstream of x = 2 km filled `depth` m above its bed,
+    instantaneous dam break, dry downstream, n = 0.033.  Levels
+    minlevel..maxlevel (5 levels: 31.25 m to 1.95 m cells with 32-cell
+    patches); refinement to maxlevel where water flows and over the
+    reservoir (source box)."""
+    Lx, Ly = 17000.0, 9000.0
+    cfg = Config(mi=17, mj=9, mx=patch, minlevel=minlevel, maxlevel=maxlevel,
+                 xupper=Lx, yupper=Ly, drytol=1e-3, manning_n=0.033, dt_initial=0.05,
+                 tag_depth=1e-3, tag_speed=0.1, tag_deta=1e9, precision=precision,
+                 src_box=(0.0, 2000.0, 0.0, Ly), src_level=maxlevel)
+    rng = np.random.default_rng(seed)
+    phase = rng.uniform(0.0, 2 * np.pi)
+    wphase = rng.uniform(0.0, 2 * np.pi)
+    X, Y = node_grid(cfg, dem_spacing)
+    centre = 0.5 * Ly + 800.0 * np.sin(2 * np.pi * X / 3000.0 + phase)
+    width = 200.0 + 100.0 * np.sin(2 * np.pi * X / 4100.0 + wphase)
+    noise = value_noise(X, Y, seed, 6, 2000.0)
+    canyon = 90.0 + 30.0 * noise + 0.004 * (10000.0 - X)
+    d = np.abs(Y - centre)
+    cut = np.clip(1.0 - (d - 0.5 * width) / 150.0, 0.0, 1.0)  # channel banks
+    canyon = canyon - 50.0 * cut
+    plain = 0.002 * (Lx - X) + 0.5 * noise
+    blend = np.clip((X - 9500.0) / 1000.0, 0.0, 1.0)  # canyon mouth
+    z = (1.0 - blend) * canyon + blend * plain
+    dem = Dem(z, 0.0, 0.0, dem_spacing, dem_spacing)
+    i_dam = int(round(2000.0 / dem_spacing))
+    j_c = np.argmin(np.abs(Y[:, i_dam] - centre[:, i_dam]))
+    surface = float(z[j_c, i_dam]) + depth
+    cfg.eta0 = 0.0
+
+    def ic(x, y, b):
+        h = np.where(x < 2000.0, np.maximum(surface - b, 0.0), 0.0)
+        return h, np.zeros_like(h), np.zeros_like(h)
+
+    gx = np.linspace(2500.0, 16000.0, 16)
+    gy = 0.5 * Ly + 800.0 * np.sin(2 * np.pi * gx / 3000.0 + phase)
+    return Problem("canyon_plain", cfg, dem, ic, 4000.0, np.stack([gx, gy], 1))
+
+
 def valley_ensemble(n: int, seed: int = SEED_BASE + 4, precision: int = 1):
     """n scenarios of the 2 km x 1 km valley for one batched context:
     breach width U[50, 400] m, reservoir depth U[10, 30] m, Manning n
@@ -389,6 +437,23 @@ def valley_ensemble(n: int, seed: int = SEED_BASE + 4, precision: int = 1):
                         Lx=2000.0, Ly=1000.0,
                         breach_width=float(rng.uniform(50.0, 400.0)))
         prob.cfg.src_level = 1
+        prob.cfg.precision = precision
+        probs.append(prob)
+    return probs
+
+
+def valley_ensemble_full(n: int, seed: int = SEED_BASE + 5, precision: int = 1):
+    """n scenarios of the full 4 km x 2 km valley (16 x 8 blocks of 32 x 32
+    patches, levels 2-4, 2048 patches before any refinement): breach width
+    U[50, 400] m, reservoir depth U[10, 30] m, Manning n U[0.02, 0.05],
+    terrain noise seeded per scenario (DEM nodes every 8 m)."""
+    rng = np.random.default_rng(seed)
+    probs = []
+    for k in range(n):
+        prob = v_valley(seed=seed + 100 + k, dem_spacing=8.0,
+                        depth=float(rng.uniform(10.0, 30.0)),
+                        manning_n=float(rng.uniform(0.02, 0.05)), n_gauges=16,
+                        breach_width=float(rng.uniform(50.0, 400.0)))
         prob.cfg.precision = precision
         probs.append(prob)
     return probs
