@@ -335,6 +335,16 @@ int geoflood_set_variant(geoflood_ctx* ctx, int variant);
 /* Number of kernels this context has launched since it was created. */
 int geoflood_launch_count(geoflood_ctx* ctx, long long* launches);
 
+/* Failure detection check (no counterpart in the paper): every wait of the
+ * library's kernels on an asynchronous copy is bounded; when the bound runs
+ * out the kernel records GEOFLOOD_ERR_TIMEOUT for the host and returns
+ * instead of hanging.  This call confirms that on the GPU in use: a wait on
+ * a transaction that never arrives must give up, and the same wait must
+ * succeed once the transaction is completed.  stream may be NULL.  Returns
+ * 0 when both happen, GEOFLOOD_ERR_STATE otherwise, CUDA or OOM on a failed
+ * call. */
+int geoflood_check_bounded_wait(void* stream);
+
 /* One FP64 patch step on caller-owned device buffers, allocating nothing.
  *
  * The paper has no counterpart: this entry point exists for callers that

@@ -40,6 +40,31 @@ __global__ void k_ctl_begin(GfCtl* ctl, int nscen, double t_target,
   }
 }
 
+// The bounded-wait check: an mbarrier expects 16 bytes that no copy will
+// bring; the CTA's bounded wait must give up (flag 1), then, once the
+// transaction is completed by hand, the same wait must succeed (flag 2).
+__global__ void k_wait_check(int* out, unsigned limit) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    gfs::mbar_init(&bar, 1);
+    gfs::mbar_expect_tx(&bar, 16u);
+  }
+  __syncthreads();
+  const bool first = __syncthreads_and(gfs::mbar_wait(&bar, limit, 0u) ? 1 : 0);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.complete_tx.shared::cta.b64 [%0], %1;" ::"r"(gfs::smem_addr(&bar)),
+                 "r"(16u)
+                 : "memory");
+  }
+  __syncthreads();
+  const bool second = __syncthreads_and(gfs::mbar_wait(&bar, limit, 0u) ? 1 : 0);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(gfs::smem_addr(&bar)) : "memory");
+    out[0] = first ? 0 : 1;
+    out[1] = second ? 2 : 0;
+  }
+}
+
 }  // namespace
 
 namespace gf {
@@ -222,4 +247,22 @@ extern "C" int geoflood_step_tiles_noalloc(const double* q_in, const double* b,
     *cmax = v;
   }
   return 0;
+}
+
+// Confirms, on the GPU in use, that the library's bounded waits end: a wait
+// on a transaction that never arrives gives up after its limit (the patch
+// step then reports GEOFLOOD_ERR_TIMEOUT and returns), and succeeds once the
+// transaction completes.  Runs one CTA; allocates 8 bytes of device memory.
+extern "C" int geoflood_check_bounded_wait(void* stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int* d = nullptr;
+  if (cudaMalloc(&d, 2 * sizeof(int)) != cudaSuccess) return -3;
+  k_wait_check<<<1, 128, 0, st>>>(d, 4096u);
+  int h[2] = {-1, -1};
+  const bool ok = cudaGetLastError() == cudaSuccess &&
+                  cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+                  cudaStreamSynchronize(st) == cudaSuccess;
+  cudaFree(d);
+  if (!ok) return -2;
+  return h[0] == 1 && h[1] == 2 ? 0 : -9;
 }

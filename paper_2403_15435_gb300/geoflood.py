@@ -102,6 +102,7 @@ def lib():
                 "geoflood_npatch": [vp, ip, pi],
                 "geoflood_save": [vp, vp, C.c_size_t, C.POINTER(C.c_size_t)],
                 "geoflood_gauge_count": [vp, ip, pi],
+                "geoflood_check_bounded_wait": [vp],
                 "geoflood_load": [vp, vp, C.c_size_t],
                 "geoflood_patch_info": [vp, ip, pi, pi, pi],
                 "geoflood_write_patches": [vp, ip, dp, dp, dp],
@@ -481,6 +482,12 @@ def cnn_nparam():
 def bf16_to_float(bits):
     """Widen BF16 bit patterns to float32 (exact)."""
     return (np.asarray(bits, np.uint16).astype(np.uint32) << 16).view(np.float32)
+
+
+def check_bounded_wait(stream=None):
+    """geoflood_check_bounded_wait: 0 when a wait on a copy that never
+    arrives gives up after its bound and succeeds once the copy is done."""
+    return lib().geoflood_check_bounded_wait(stream)
 
 
 def exported_symbols():
