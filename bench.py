@@ -590,6 +590,7 @@ def roofline(r, prec, peaks):
            "alu": {"achieved": alu, "peak": alu_peak, "unit": "GOP/s", "frac": alu / alu_peak,
                    "ops_per_launch": ops, "peak_source": "derived: " + alu_src},
            "hbm": {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                   "frac_of_nominal_7900": gbs / 7900.0,
                    "bytes_per_launch": bytes_cell * cells, "peak_source": "measured"}}
     side = "alu" if out["alu"]["frac"] >= out["hbm"]["frac"] else "hbm"
     out.update({"bound": side, "achieved": out[side]["achieved"], "peak": out[side]["peak"],
