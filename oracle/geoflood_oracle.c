@@ -736,13 +736,35 @@ static double minmod(double a, double b) {
   return fabs(a) < fabs(b) ? a : b;
 }
 
-/* Value of (h, hu, hv) for cell (I, J) of level L whose bed is bt: copy from
- * a leaf of the same level, mean of the four cells of finer leaves, or
- * limited interpolation of the coarser level's surface and momenta
- * (ghost-cell exchange, Sec. 4 and the quadtree figure; Sec. 6.2 for the
- * surface-based interpolation that keeps lake at rest). */
-static void fill_cell(const oracle_forest* f, int L, long I, long J, double bt,
-                      double* out) {
+/* Beds of the four cells of a tile that share a parent with tile cell
+ * (i, j): bs[b][a] is the child at x offset a and y offset b.  Patch
+ * origins are even, so siblings have the same tile up to the last bit of
+ * the local index, ghost cells included. */
+static void child_beds(const oracle_forest* f, const double* bed, int i, int j,
+                       double bs[2][2]) {
+  int i0 = i & ~1, j0 = j & ~1, a, b;
+  for (b = 0; b < 2; ++b)
+    for (a = 0; a < 2; ++a) bs[b][a] = bed[TI(f, i0 + a, j0 + b)];
+}
+
+/* Value of (h, hu, hv) for cell (I, J) of level L whose parent's four
+ * children have the beds bs (bs[J & 1][I & 1] is this cell's): copy from a
+ * leaf of the same level, mean of the four cells of finer leaves, or
+ * interpolation of the coarser level (ghost-cell exchange, Sec. 4 and the
+ * quadtree figure; Sec. 6.2 for the surface-based interpolation that keeps
+ * lake at rest).  The interpolation treats the parent's four children
+ * together:
+ *   depth: the interpolated surface (minmod-limited linear when the parent's
+ *     3x3 neighbourhood is wet, the parent's surface otherwise) minus the
+ *     child's bed, clamped at zero;
+ *   momentum: minmod-limited linear interpolation when the neighbourhood is
+ *     wet and no wet child's velocity leaves the range of the
+ *     neighbourhood's velocities; otherwise the parent's momentum split in
+ *     proportion to the children's depths.  Either way the children hold
+ *     the parent's momentum, and a shallow child under a deep parent does
+ *     not take a velocity the coarse flow does not have. */
+static void fill_cell(const oracle_forest* f, int L, long I, long J,
+                      const double bs[2][2], double* out) {
   int p = leaf_at(f, L, I, J);
   int k, l;
   if (p >= 0) {
@@ -768,12 +790,12 @@ static void fill_cell(const oracle_forest* f, int L, long I, long J, double bt,
   long NXc = NXL(f, L - 1), NYc = NYL(f, L - 1);
   double nb[3][3][4];
   int in[3][3];
-  int di, dj;
+  int di, dj, a, b;
   for (dj = -1; dj <= 1; ++dj)
     for (di = -1; di <= 1; ++di) {
-      long a = ic + di, bb = jc + dj;
-      in[dj + 1][di + 1] = a >= 0 && bb >= 0 && a < NXc && bb < NYc;
-      if (in[dj + 1][di + 1]) value_at(f, L - 1, a, bb, nb[dj + 1][di + 1]);
+      long x = ic + di, y = jc + dj;
+      in[dj + 1][di + 1] = x >= 0 && y >= 0 && x < NXc && y < NYc;
+      if (in[dj + 1][di + 1]) value_at(f, L - 1, x, y, nb[dj + 1][di + 1]);
     }
   const double* qc = nb[1][1];
   double drytol = f->c.drytol;
@@ -786,32 +808,58 @@ static void fill_cell(const oracle_forest* f, int L, long I, long J, double bt,
     for (di = 0; di < 3; ++di)
       if (in[dj][di] && !(nb[dj][di][0] > drytol)) allwet = 0;
   double etac = qc[0] + qc[3];
-  double hf, huf, hvf;
+  /* limited slopes per coarse cell of the surface and both momenta */
+  double g[3][2] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
   if (allwet) {
-    double sx = (I & 1) ? 0.25 : -0.25, sy = (J & 1) ? 0.25 : -0.25;
+    int hx = in[1][0] && in[1][2], hy = in[0][1] && in[2][1];
     double e[3][3];
     for (dj = 0; dj < 3; ++dj)
       for (di = 0; di < 3; ++di)
         e[dj][di] = in[dj][di] ? nb[dj][di][0] + nb[dj][di][3] : 0.0;
-    int hx = in[1][0] && in[1][2], hy = in[0][1] && in[2][1];
-    double gx = hx ? minmod(e[1][2] - e[1][1], e[1][1] - e[1][0]) : 0.0;
-    double gy = hy ? minmod(e[2][1] - e[1][1], e[1][1] - e[0][1]) : 0.0;
-    double ux = hx ? minmod(nb[1][2][1] - qc[1], qc[1] - nb[1][0][1]) : 0.0;
-    double uy = hy ? minmod(nb[2][1][1] - qc[1], qc[1] - nb[0][1][1]) : 0.0;
-    double vx = hx ? minmod(nb[1][2][2] - qc[2], qc[2] - nb[1][0][2]) : 0.0;
-    double vy = hy ? minmod(nb[2][1][2] - qc[2], qc[2] - nb[0][1][2]) : 0.0;
-    double etaf = (etac + sx * gx) + sy * gy;
-    huf = (qc[1] + sx * ux) + sy * uy;
-    hvf = (qc[2] + sx * vx) + sy * vy;
-    hf = etaf - bt;
-  } else {
-    hf = etac - bt;
-    huf = qc[1];
-    hvf = qc[2];
+    if (hx) g[0][0] = minmod(e[1][2] - e[1][1], e[1][1] - e[1][0]);
+    if (hy) g[0][1] = minmod(e[2][1] - e[1][1], e[1][1] - e[0][1]);
+    for (k = 1; k < 3; ++k) {
+      if (hx) g[k][0] = minmod(nb[1][2][k] - qc[k], qc[k] - nb[1][0][k]);
+      if (hy) g[k][1] = minmod(nb[2][1][k] - qc[k], qc[k] - nb[0][1][k]);
+    }
   }
-  if (hf < 0.0) hf = 0.0;
-  if (hf <= drytol) { huf = 0.0; hvf = 0.0; }
-  out[0] = hf; out[1] = huf; out[2] = hvf;
+  /* the four children: depth d and linearly interpolated momenta m */
+  double d[2][2], m[2][2][2];
+  for (b = 0; b < 2; ++b)
+    for (a = 0; a < 2; ++a) {
+      double sx = a ? 0.25 : -0.25, sy = b ? 0.25 : -0.25;
+      double eta = allwet ? (etac + sx * g[0][0]) + sy * g[0][1] : etac;
+      double h = eta - bs[b][a];
+      d[b][a] = h > 0.0 ? h : 0.0;
+      for (k = 0; k < 2; ++k)
+        m[b][a][k] = (qc[k + 1] + sx * g[k + 1][0]) + sy * g[k + 1][1];
+    }
+  double S = (d[0][0] + d[0][1]) + (d[1][0] + d[1][1]);
+  int a0 = (int)(I & 1), b0 = (int)(J & 1);
+  double hf = d[b0][a0];
+  out[0] = hf;
+  for (k = 0; k < 2; ++k) {
+    int split = !allwet;
+    if (allwet) {
+      double lo = INFINITY, hi = -INFINITY;
+      for (dj = 0; dj < 3; ++dj)
+        for (di = 0; di < 3; ++di)
+          if (in[dj][di]) {
+            double u = nb[dj][di][k + 1] / nb[dj][di][0];
+            if (u < lo) lo = u;
+            if (u > hi) hi = u;
+          }
+      for (b = 0; b < 2; ++b)
+        for (a = 0; a < 2; ++a)
+          if (d[b][a] > drytol) {
+            double u = m[b][a][k] / d[b][a];
+            if (u < lo || u > hi) split = 1;
+          }
+    }
+    if (!split) out[k + 1] = m[b0][a0][k];
+    else out[k + 1] = S > 0.0 ? (4.0 * qc[k + 1]) * (hf / S) : 0.0;
+  }
+  if (hf <= drytol) { out[1] = 0.0; out[2] = 0.0; }
 }
 
 /* ---------------------------------------------------------------------- */
@@ -1071,7 +1119,9 @@ void oracle_forest_ghost_fill(oracle_forest* f) {
         long I = (long)f->px[p] * M + i, J = (long)f->py[p] * M + j;
         if (I < 0 || J < 0 || I >= NX || J >= NY) continue;
         double out[3];
-        fill_cell(f, L, I, J, f->tile[p][3 * TT + TI(f, i, j)], out);
+        double bs[2][2];
+        child_beds(f, f->tile[p] + 3 * TT, i, j, bs);
+        fill_cell(f, L, I, J, bs, out);
         for (k = 0; k < 3; ++k) buf[k * TT + TI(f, i, j)] = out[k];
       }
     /* stage, then write after the patch is done (reads are interiors only,
@@ -1651,7 +1701,9 @@ int oracle_forest_regrid(oracle_forest* f) {
       for (i = 0; i < f->M; ++i) {
         double out[3];
         long I = (long)f->px[p] * f->M + i, J = (long)f->py[p] * f->M + j;
-        fill_cell(old, L, I, J, f->tile[p][3 * TT + TI(f, i, j)], out);
+        double bs[2][2];
+        child_beds(f, f->tile[p] + 3 * TT, i, j, bs);
+        fill_cell(old, L, I, J, bs, out);
         for (q = 0; q < 3; ++q) f->tile[p][q * TT + TI(f, i, j)] = out[q];
       }
   }

@@ -267,3 +267,113 @@ def test_uniformly_refined_forest_equals_single_level_forest():
     fb.step(5.0)
     for a, b in zip(fa.read(), fb.read()):
         assert np.array_equal(a, b)
+
+
+def _rippled_refinement(dry_column=None, ripple=0.25):
+    """Coarse wet state over a bed rippled at the coarse cell size (a 10 m
+    sine averages to zero over each coarse cell but not over its fine halves)
+    and the forest after one refinement of the lower-left block."""
+    cfg = two_level_cfg(mx=8)
+    xn = np.arange(0.0, 160.0 + 1e-9, 1.25)
+    X, Y = np.meshgrid(xn, xn)
+    dem = inputs.Dem(z=ripple * np.sin(2 * np.pi * X / 10.0) + 0.001 * Y,
+                     x0=0.0, y0=0.0, dx=1.25, dy=1.25)
+    f = oracle.OracleForest(cfg, dem)
+
+    def ic(x, y, b):
+        h = 0.6 + 0.05 * np.sin(x / 17.0) * np.cos(y / 23.0) - b
+        if dry_column is not None:
+            h = np.where(np.floor(x / 10.0) == dry_column, 0.0, h)
+        u = 1.0 + 0.05 * np.cos(y / 13.0)
+        v = -0.5 + 0.05 * np.sin(x / 19.0)
+        return h, h * u, h * v
+
+    f.set_state(ic)
+    L, X0, Y0 = f.patch_info()
+    h, hu, hv, _ = f.read()
+    C = np.zeros((4, 16, 16))
+    for k in range(len(L)):
+        for a, v in enumerate((h, hu, hv)):
+            C[a, Y0[k] * 8:(Y0[k] + 1) * 8, X0[k] * 8:(X0[k] + 1) * 8] = v[k]
+    f.regrid()
+    L, X1, Y1 = f.patch_info()
+    h, hu, hv, _ = f.read()
+    F = np.zeros((3, 16, 16))
+    for k in range(len(L)):
+        if L[k] == 1:
+            for a, v in enumerate((h, hu, hv)):
+                F[a, Y1[k] * 8:(Y1[k] + 1) * 8, X1[k] * 8:(X1[k] + 1) * 8] = v[k]
+    assert (L == 1).sum() == 4
+    return C, F
+
+
+def test_refinement_creates_no_new_velocity_extremes():
+    """A fine cell much shallower than its coarse parent (the bed's ripple)
+    must not inherit the parent's momentum whole: every refined velocity lies
+    in the range of the velocities of the parent's 3x3 neighbourhood (limited
+    interpolation, Sec. 6.2; the velocity bound is the reading that the
+    method's interpolation keeps the flow's speeds)."""
+    C, F = _rippled_refinement()
+    uc, vc = C[1] / C[0], C[2] / C[0]
+    checked = 0
+    for J in range(16):
+        for I in range(16):
+            jc, ic = J >> 1, I >> 1
+            sl = (slice(max(jc - 1, 0), jc + 2), slice(max(ic - 1, 0), ic + 2))
+            uf, vf = F[1, J, I] / F[0, J, I], F[2, J, I] / F[0, J, I]
+            tol = 1e-12
+            assert uc[sl].min() - tol <= uf <= uc[sl].max() + tol
+            assert vc[sl].min() - tol <= vf <= vc[sl].max() + tol
+            checked += 1
+    assert checked == 256
+    # the ripple makes the fine depths differ from the coarse ones by far more
+    # than the surface variation, so the bound is exercised
+    assert np.abs(F[0] - np.kron(C[0, :8, :8], np.ones((2, 2)))).max() > 0.1
+
+
+def test_refinement_next_to_dry_keeps_velocity_and_momentum():
+    """Beside a dry coarse cell the fine surface is the coarse one and each
+    fine cell carries the coarse cell's velocity: the four children hold the
+    parent's volume and momentum (the fine beds average to the coarse bed and
+    no depth is clamped here)."""
+    C, F = _rippled_refinement(dry_column=3)
+    seen = 0
+    for jc in range(8):
+        for ic in (2, 4):
+            ch = F[:, 2 * jc:2 * jc + 2, 2 * ic:2 * ic + 2]
+            assert (ch[0] > 0.1).all()
+            assert np.allclose(ch[1] / ch[0], C[1, jc, ic] / C[0, jc, ic], rtol=1e-13, atol=0)
+            assert np.allclose(ch[2] / ch[0], C[2, jc, ic] / C[0, jc, ic], rtol=1e-13, atol=0)
+            for a in range(3):
+                assert abs(ch[a].sum() - 4 * C[a, jc, ic]) <= 1e-12 * abs(4 * C[a, jc, ic])
+            seen += 1
+    assert seen == 16
+    # the dry column stays dry and still
+    assert (F[:, :, 6:8] == 0).all()
+
+
+@pytest.mark.parametrize("dry_column", [None, 3])
+def test_refinement_with_emerging_children_keeps_momentum_and_speeds(dry_column):
+    """A 1 m ripple lifts some children above the parent's surface (their
+    depth is clamped at zero, so the volume grows, as the surface-based
+    interpolation keeps still water still).  The momentum still is the
+    parent's, split in proportion to the children's depths, and no child is
+    faster than the fastest cell of the parent's neighbourhood."""
+    C, F = _rippled_refinement(dry_column=dry_column, ripple=1.0)
+    clamped = 0
+    for jc in range(8):
+        for ic in range(8):
+            if not C[0, jc, ic] > 1e-3:
+                continue
+            ch = F[:, 2 * jc:2 * jc + 2, 2 * ic:2 * ic + 2]
+            clamped += int((ch[0] == 0).any())
+            if ((ch[0] > 0) & (ch[0] <= 1e-3)).any():
+                continue
+            for a in (1, 2):
+                assert abs(ch[a].sum() - 4 * C[a, jc, ic]) <= 1e-12 * abs(4 * C[a, jc, ic])
+            sl = (slice(max(jc - 1, 0), jc + 2), slice(max(ic - 1, 0), ic + 2))
+            wet = C[0][sl] > 1e-3
+            vmax = np.abs(C[1:3][(slice(None),) + sl][:, wet] / C[0][sl][wet]).max()
+            wf = ch[0] > 0
+            assert (np.abs(ch[1:3][:, wf] / ch[0][wf]) <= vmax * (1 + 1e-12)).all()
+    assert clamped >= 8

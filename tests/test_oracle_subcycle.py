@@ -104,16 +104,37 @@ def test_stoker_with_a_refined_band_matches_closed_form():
     assert errs[1] <= 1.3 * errs[0] + 1e-3
 
 
+def _coarse_depths(f, n0, m):
+    """Depths of a 0..1 forest on the level-0 grid (level-1 patches averaged
+    2x2): n0 x n0 coarse cells in patches of m."""
+    L, X, Y = f.patch_info()
+    h = f.read()[0]
+    out = np.zeros((n0, n0))
+    for k in range(len(L)):
+        c = h[k] if L[k] == 0 else h[k].reshape(m // 2, 2, m // 2, 2).mean(axis=(1, 3))
+        w = m if L[k] == 0 else m // 2
+        out[Y[k] * w:(Y[k] + 1) * w, X[k] * w:(X[k] + 1) * w] = c
+    return out
+
+
 def test_radial_dam_break_close_to_global_stepping():
+    """Two-level radial dam break over terrain onto a dry bed: against the
+    same problem refined everywhere, the subcycled forest's error is of the
+    order of the globally stepped one's (the fronts cross the coarse/fine
+    interface, where the two place a front up to a coarse cell apart)."""
     prob = inputs.radial_dambreak(128, 16, dx=4.0, radius=100.0)
     box = (160.0, 352.0, 160.0, 352.0)
     a = two_level(prob, box)
     b = two_level(prob, box, subcycle=1)
+    c = two_level(prob, (0.0, 1e9, 0.0, 1e9))
     assert set(a.patch_info()[0]) == {0, 1}
-    a.step(12.0)
-    b.step(12.0)
-    ha, hb = a.read()[0], b.read()[0]
-    assert np.abs(ha - hb).max() <= 0.05 * np.abs(ha).max()
-    assert np.abs(ha - hb).mean() <= 0.005 * np.abs(ha).mean()
+    for f in (a, b, c):
+        f.step(12.0)
+    ha, hb, hc = (_coarse_depths(f, 64, 16) for f in (a, b, c))
+    ea, eb = np.abs(ha - hc), np.abs(hb - hc)
+    assert eb.mean() <= 2.0 * ea.mean()
+    assert eb.mean() <= 0.025 * hc.mean()
+    assert eb.max() <= 0.15 * hc.max()
+    assert np.abs(ha - hb).mean() <= 0.015 * hc.mean()
     # fewer coarse updates: the coarse level took half as many steps
     assert b.time()["steps"] < a.time()["steps"]
