@@ -147,13 +147,32 @@ __device__ __forceinline__ double minmod(double a, double b) {
   return fabs(a) < fabs(b) ? a : b;
 }
 
-// Value (h, hu, hv) of cell (I, J) of level L whose bed is bt, from the
-// forest of the view: copy from a same-level leaf, mean of finer cells, or
-// limited interpolation of the coarser level's surface and momenta (Sec. 4
-// ghost cells, Sec. 6.2 surface-preserving interpolation).
+// Beds of the four tile cells that share a parent with tile cell (i, j):
+// bs[b][a] is the child at x offset a and y offset b (patch origins are
+// even, so siblings differ from (i, j) in the last bit only, ghosts included).
+template <typename T, typename B>
+__device__ __forceinline__ void child_beds(const Geo<T>& e, const B* bed, int i, int j,
+                                           double (&bs)[2][2]) {
+  const int i0 = i & ~1, j0 = j & ~1;
+  for (int b = 0; b < 2; ++b)
+    for (int a = 0; a < 2; ++a) bs[b][a] = (double)bed[e.tix(i0 + a, j0 + b)];
+}
+
+// Value (h, hu, hv) of cell (I, J) of level L, whose parent's four children
+// have the beds bs (bs[J & 1][I & 1] is this cell's), from the forest of the
+// view: copy from a same-level leaf, mean of finer cells, or interpolation
+// of the coarser level (Sec. 4 ghost cells, Sec. 6.2 surface-preserving
+// interpolation).  The interpolation treats the four children together:
+// depth = interpolated surface (limited linear over a wet 3x3
+// neighbourhood, the parent's surface otherwise) minus the child's bed,
+// clamped at zero; momentum = limited linear interpolation over a wet
+// neighbourhood unless a wet child's velocity leaves the range of the
+// neighbourhood's velocities, else the parent's momentum split in
+// proportion to the children's depths.
 template <typename T>
 __device__ void fill_cell(const Geo<T>& e, int s, int L, long long I,
-                          long long J, double bt, double (&out)[3], int* err) {
+                          long long J, const double (&bs)[2][2], double (&out)[3], int* err) {
+  const double bt = bs[J & 1][I & 1];
   const int p = e.leaf(s, L, I, J);
   if (p >= 0) {
     const GfPatch P = e.V.patch[p];
@@ -197,9 +216,9 @@ __device__ void fill_cell(const Geo<T>& e, int s, int L, long long I,
   bool in[3][3];
   for (int dj = -1; dj <= 1; ++dj)
     for (int di = -1; di <= 1; ++di) {
-      const long long a = ic + di, b = jc + dj;
-      in[dj + 1][di + 1] = a >= 0 && b >= 0 && a < NXc && b < NYc;
-      if (in[dj + 1][di + 1]) value_at(e, s, L - 1, a, b, nb[dj + 1][di + 1], err);
+      const long long x = ic + di, y = jc + dj;
+      in[dj + 1][di + 1] = x >= 0 && y >= 0 && x < NXc && y < NYc;
+      if (in[dj + 1][di + 1]) value_at(e, s, L - 1, x, y, nb[dj + 1][di + 1], err);
     }
   const double drytol = e.G.drytol;
   const double* qc = nb[1][1];
@@ -214,34 +233,60 @@ __device__ void fill_cell(const Geo<T>& e, int s, int L, long long I,
     for (int di = 0; di < 3; ++di)
       if (in[dj][di] && !(nb[dj][di][0] > drytol)) allwet = false;
   const double etac = qc[0] + qc[3];
-  double hf, huf, hvf;
+  // limited slopes over the coarse cell: surface, then both momenta
+  double g[3][2] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
   if (allwet) {
-    const double sx = (I & 1) ? 0.25 : -0.25, sy = (J & 1) ? 0.25 : -0.25;
+    const bool hx = in[1][0] && in[1][2], hy = in[0][1] && in[2][1];
     double et[3][3];
     for (int dj = 0; dj < 3; ++dj)
       for (int di = 0; di < 3; ++di)
         et[dj][di] = in[dj][di] ? nb[dj][di][0] + nb[dj][di][3] : 0.0;
-    const bool hx = in[1][0] && in[1][2], hy = in[0][1] && in[2][1];
-    const double gx = hx ? minmod(et[1][2] - et[1][1], et[1][1] - et[1][0]) : 0.0;
-    const double gy = hy ? minmod(et[2][1] - et[1][1], et[1][1] - et[0][1]) : 0.0;
-    const double ux = hx ? minmod(nb[1][2][1] - qc[1], qc[1] - nb[1][0][1]) : 0.0;
-    const double uy = hy ? minmod(nb[2][1][1] - qc[1], qc[1] - nb[0][1][1]) : 0.0;
-    const double vx = hx ? minmod(nb[1][2][2] - qc[2], qc[2] - nb[1][0][2]) : 0.0;
-    const double vy = hy ? minmod(nb[2][1][2] - qc[2], qc[2] - nb[0][1][2]) : 0.0;
-    const double etaf = (etac + sx * gx) + sy * gy;
-    huf = (qc[1] + sx * ux) + sy * uy;
-    hvf = (qc[2] + sx * vx) + sy * vy;
-    hf = etaf - bt;
-  } else {
-    hf = etac - bt;
-    huf = qc[1];
-    hvf = qc[2];
+    if (hx) g[0][0] = minmod(et[1][2] - et[1][1], et[1][1] - et[1][0]);
+    if (hy) g[0][1] = minmod(et[2][1] - et[1][1], et[1][1] - et[0][1]);
+    for (int k = 1; k < 3; ++k) {
+      if (hx) g[k][0] = minmod(nb[1][2][k] - qc[k], qc[k] - nb[1][0][k]);
+      if (hy) g[k][1] = minmod(nb[2][1][k] - qc[k], qc[k] - nb[0][1][k]);
+    }
   }
-  if (hf < 0.0) hf = 0.0;
-  if (hf <= drytol) { huf = 0.0; hvf = 0.0; }
+  // the four children: depth d, linearly interpolated momenta m
+  double d[2][2], m[2][2][2];
+  for (int b = 0; b < 2; ++b)
+    for (int a = 0; a < 2; ++a) {
+      const double sx = a ? 0.25 : -0.25, sy = b ? 0.25 : -0.25;
+      const double eta = allwet ? (etac + sx * g[0][0]) + sy * g[0][1] : etac;
+      const double h = eta - bs[b][a];
+      d[b][a] = h > 0.0 ? h : 0.0;
+      for (int k = 0; k < 2; ++k)
+        m[b][a][k] = (qc[k + 1] + sx * g[k + 1][0]) + sy * g[k + 1][1];
+    }
+  const double S = (d[0][0] + d[0][1]) + (d[1][0] + d[1][1]);
+  const int a0 = (int)(I & 1), b0 = (int)(J & 1);
+  const double hf = d[b0][a0];
   out[0] = hf;
-  out[1] = huf;
-  out[2] = hvf;
+  for (int k = 0; k < 2; ++k) {
+    bool split = !allwet;
+    if (allwet) {
+      double lo = INFINITY, hi = -INFINITY;
+      for (int dj = 0; dj < 3; ++dj)
+        for (int di = 0; di < 3; ++di)
+          if (in[dj][di]) {
+            const double u = nb[dj][di][k + 1] / nb[dj][di][0];
+            lo = fmin(lo, u);
+            hi = fmax(hi, u);
+          }
+      for (int b = 0; b < 2; ++b)
+        for (int a = 0; a < 2; ++a)
+          if (d[b][a] > drytol) {
+            const double u = m[b][a][k] / d[b][a];
+            if (u < lo || u > hi) split = true;
+          }
+    }
+    out[k + 1] = !split ? m[b0][a0][k] : (S > 0.0 ? (4.0 * qc[k + 1]) * (hf / S) : 0.0);
+  }
+  if (hf <= drytol) {
+    out[1] = 0.0;
+    out[2] = 0.0;
+  }
 }
 
 // Physical boundaries of one tile held in global memory: bottom/top over the
@@ -351,9 +396,11 @@ __global__ void k_ghost_fill(const __grid_constant__ GfGeom G, const __grid_cons
       q[2 * TT + c] = a2;
       continue;
     }
-    const double bt = (double)bb[c];
+    double bs[2][2];
+    child_beds(e, bb, i, j, bs);
+    const double bt = bs[j & 1][i & 1];
     double out[3];
-    fill_cell(e, P.scen, P.level, I, J, bt, out, &err);
+    fill_cell(e, P.scen, P.level, I, J, bs, out, &err);
     e.store(q, c, out[0], out[1], out[2], bt);
   }
   if (err && errflag) *errflag = 1;
@@ -568,10 +615,12 @@ __global__ void k_ghost_other(const __grid_constant__ GfGeom G, const __grid_con
   T* q = e.qp(p, e.cur_of(p));
   const int c = e.tix(i, j);
   const long long I = (long long)P.px * M + i, J = (long long)P.py * M + j;
-  const double bt = (double)e.bp(p)[c];
+  double bs[2][2];
+  child_beds(e, e.bp(p), i, j, bs);
+  const double bt = bs[j & 1][i & 1];
   double out[3];
   int err = 0;
-  fill_cell(e, P.scen, P.level, I, J, bt, out, &err);
+  fill_cell(e, P.scen, P.level, I, J, bs, out, &err);
   if (err && errflag) *errflag = 1;
   e.store(q, c, out[0], out[1], out[2], bt);
   // physical-boundary ghosts mirroring this cell (wall: reflected, normal
@@ -739,9 +788,11 @@ __global__ void k_regrid_fill(const __grid_constant__ GfGeom G, const __grid_con
     const int i = k % M, j = k / M;
     const long long I = (long long)P.px * M + i, J = (long long)P.py * M + j;
     const int c = (i + GF_NG) + (j + GF_NG) * T_;
-    const double bt = (double)bn[c];
+    double bs[2][2];
+    child_beds(en, bn, i, j, bs);
+    const double bt = bs[j & 1][i & 1];
     double out[3];
-    fill_cell(eo, P.scen, P.level, I, J, bt, out, &err);
+    fill_cell(eo, P.scen, P.level, I, J, bs, out, &err);
     en.store(q, c, out[0], out[1], out[2], bt);
     if constexpr (Geo<T>::DEV) {
       float* lo = N.lof[dst] + (size_t)p * 3 * M * M;
@@ -779,6 +830,30 @@ __global__ void k_regrid_keep(const __grid_constant__ GfGeom G, const __grid_con
     const float* lo = O.lof[src] + (size_t)po * 3 * M * M;
     float* ln = N.lof[dst] + (size_t)pn * 3 * M * M;
     for (int k = threadIdx.x; k < 3 * M * M; k += blockDim.x) ln[k] = lo[k];
+  }
+}
+
+// Bring every patch's latest state into buffer `target`: a patch whose
+// scenario holds it in the other buffer has its tile (ghosts included) and
+// compensation terms copied over.  Patch slots are shared by all scenarios,
+// so a regrid, which writes every new slot into the buffer opposite the
+// latest one, needs that buffer to be the same for every scenario.
+template <typename T>
+__global__ void k_align_buffers(const __grid_constant__ GfGeom G, const __grid_constant__ GfView V,
+                                int target) {
+  const int p = blockIdx.x;
+  const GfPatch P = V.patch[p];
+  const int src = V.ctl[P.scen].cur;
+  if (src == target) return;
+  Geo<T> e(G, V);
+  const int M = G.M, TT = G.T * G.T;
+  const T* qs = e.qp(p, src);
+  T* qd = e.qp(p, target);
+  for (int k = threadIdx.x; k < 3 * TT; k += blockDim.x) qd[k] = qs[k];
+  if constexpr (Geo<T>::DEV) {
+    const float* ls = V.lof[src] + (size_t)p * 3 * M * M;
+    float* ld = V.lof[target] + (size_t)p * 3 * M * M;
+    for (int k = threadIdx.x; k < 3 * M * M; k += blockDim.x) ld[k] = ls[k];
   }
 }
 
@@ -1235,6 +1310,14 @@ int launch_regrid_keep(const GfGeom& g, const GfView& oldv, const GfView& newv,
   const int2* pr = static_cast<const int2*>(pairs);
   if (newv.prec) k_regrid_keep<float><<<count, 256, 0, st>>>(g, oldv, newv, pr);
   else k_regrid_keep<double><<<count, 256, 0, st>>>(g, oldv, newv, pr);
+  return ok();
+}
+
+int launch_align_buffers(const GfGeom& g, const GfView& v, int target, void* stream) {
+  if (v.npatch <= 0) return 0;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (v.prec) k_align_buffers<float><<<v.npatch, 256, 0, st>>>(g, v, target);
+  else k_align_buffers<double><<<v.npatch, 256, 0, st>>>(g, v, target);
   return ok();
 }
 

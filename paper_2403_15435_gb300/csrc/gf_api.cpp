@@ -100,6 +100,10 @@ struct geoflood_ctx {
   struct Graph {
     cudaGraphExec_t exec = nullptr;
     int k = 0, tsel = -1, bsel = -1, npatch = -1, gauges = -1, prof = -1, variant = -1;
+    // the forest the graph was captured for: its launches carry the number
+    // of ghost regions at level changes and of inflow patches, which change
+    // with every regrid even when the patch count does not
+    long long generation = -1;
     std::vector<ProfRec> ev;   // sampled patch-step launches
     std::vector<ProfRec> evg;  // sampled ghost fills
   };
@@ -1044,7 +1048,8 @@ int geoflood_step(geoflood_ctx* ctx, double t_target, int max_steps,
     gr->k = K;
   }
   const int prof = ctx->prof ? ctx->prof_every : 0;
-  if (!gr->exec || gr->tsel != ctx->tsel || gr->bsel != ctx->bsel ||
+  if (!gr->exec || gr->generation != ctx->generation || gr->tsel != ctx->tsel ||
+      gr->bsel != ctx->bsel ||
       gr->npatch != ctx->npatch || gr->gauges != ctx->max_gauges_used ||
       gr->prof != prof || gr->variant != ctx->variant) {
     gr->ev.clear();
@@ -1119,6 +1124,7 @@ int geoflood_step(geoflood_ctx* ctx, double t_target, int max_steps,
     gr->gauges = ctx->max_gauges_used;
     gr->prof = prof;
     gr->variant = ctx->variant;
+    gr->generation = ctx->generation;
   }
   const int per_step = ctx->G.sub_K * (1 + (ctx->nglist[ctx->tsel] > 0 ? 1 : 0) +
                                        (ctx->nilist[ctx->tsel] > 0 ? 1 : 0)) +
@@ -1254,6 +1260,24 @@ int geoflood_regrid(geoflood_ctx* ctx) {
     return fail(ctx, GEOFLOOD_ERR_CAPACITY,
                 "regrid needs " + std::to_string(total) + " patches, capacity is " +
                     std::to_string(ctx->cap));
+  // every scenario's latest state into one buffer, so that the new slots
+  // (written into the other buffer) overwrite no scenario's latest state:
+  // slots are shared, and scenarios that took different numbers of steps
+  // hold their latest state in different buffers
+  {
+    long long ones = 0, zeros = 0;
+    for (int s = 0; s < ctx->nscen; ++s)
+      (ctx->h_ctl[s].cur ? ones : zeros) += ctx->h_scen[s].pcount;
+    const int target = ones > zeros ? 1 : 0;
+    bool mixed = false;
+    for (int s = 0; s < ctx->nscen; ++s) mixed |= ctx->h_ctl[s].cur != target;
+    if (mixed) {
+      CKL(gf::launch_align_buffers(ctx->G, view(ctx), target, ctx->st), "align_buffers");
+      ctx->launches++;
+      for (int s = 0; s < ctx->nscen; ++s) ctx->h_ctl[s].cur = target;
+      if ((rc = sync_ctl_up(ctx))) return rc;
+    }
+  }
   const GfView oldv = view(ctx);
   std::vector<GfScenario> saved = ctx->h_scen;
   const int nt = ctx->tsel ^ 1, nb = ctx->bsel ^ 1;

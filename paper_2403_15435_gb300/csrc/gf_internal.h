@@ -217,6 +217,10 @@ int launch_regrid_fill(const GfGeom& g, const GfView& oldv, const GfView& newv,
 // Copy of the patches present in both forests: pairs (int2: new, old).
 int launch_regrid_keep(const GfGeom& g, const GfView& oldv, const GfView& newv,
                        const void* pairs, int count, void* stream);
+// Latest state of every patch into buffer target (patches whose scenario
+// holds it in the other buffer are copied); the caller then sets every
+// scenario's cur to target.
+int launch_align_buffers(const GfGeom& g, const GfView& v, int target, void* stream);
 int launch_tags(const GfGeom& g, const GfView& v, uint8_t* flags,
                 void* stream);
 // Recompute every scenario's gauge stencils (after a regrid or new gauges).

@@ -325,3 +325,57 @@ def test_kernel_variants_agree_on_the_full_workload(prec):
             continue
         for a, b in zip(st, ref):
             assert np.array_equal(a, b), "variant %d differs" % variant
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_regrid_with_scenarios_at_different_buffer_parities(prec):
+    """Scenarios that took odd and even numbers of steps hold their latest
+    states in different buffers of the shared patch slots; regrids and
+    steps after that leave every scenario as it is when run alone (bit for
+    bit), and equal to the oracle in FP64."""
+    prob = inputs.v_valley(mi=4, mj=2, patch=16, minlevel=0, maxlevel=2,
+                           dem_spacing=8.0, Lx=1000.0, Ly=500.0, breach_x=300.0,
+                           depth=8.0, n_gauges=6)
+    prob.cfg.src_level = 1
+    prob.cfg.precision = prec
+    ns = [0.0, 0.03, 0.1]
+
+    def start(forest, s, n):
+        forest.set_scenario(s, n, prob.cfg.eta0)
+        forest.set_state(prob.ic, s)
+
+    g = geoflood.Forest(prob.cfg, prob.dem, num_scenarios=len(ns))
+    alone = [geoflood.Forest(prob.cfg, prob.dem) for _ in ns]
+    refs = []
+    for s, n in enumerate(ns):
+        start(g, s, n)
+        start(alone[s], 0, n)
+        cfg = inputs.Config(**{**prob.cfg.__dict__, "manning_n": n, "precision": 0})
+        r = oracle.OracleForest(cfg, prob.dem)
+        r.set_state(prob.ic)
+        refs.append(r)
+    for f in [g] + alone + refs:
+        f.regrid()
+    for s in range(len(ns)):
+        g.set_state(prob.ic, s)
+        alone[s].set_state(prob.ic)
+        refs[s].set_state(prob.ic)
+    ops = [("step", 2.0, 1 << 30), ("regrid",), ("step", 1e9, 4), ("regrid",),
+           ("step", 1e9, 3), ("regrid",), ("step", 1e9, 2)]
+    for k, op in enumerate(ops):
+        for f in [g] + alone + refs:
+            f.regrid() if op[0] == "regrid" else f.step(op[1], op[2])
+        if k == 0:
+            parities = {g.time(s)["steps"] % 2 for s in range(len(ns))}
+            assert parities == {0, 1}, "the scenarios must end on both buffer parities"
+        for s in range(len(ns)):
+            assert [list(a) for a in g.patch_info(s)] == [list(a) for a in alone[s].patch_info()]
+            a, b = g.read(s), alone[s].read()
+            for x, y in zip(a, b):
+                assert np.array_equal(x, y), "scenario %d differs from its lone run after %s" % (s, op)
+            assert g.time(s)["steps"] == alone[s].time()["steps"]
+            if prec == 0:
+                assert [list(a) for a in g.patch_info(s)] == [list(a) for a in refs[s].patch_info()]
+                c = refs[s].read()
+                for x, y in zip(a, c):
+                    assert rel(x, y) <= 1e-11
