@@ -49,7 +49,7 @@ struct GfScenario {
 // Per-scenario time-stepping state, owned by the device controller.
 struct GfCtl {
   double t, dt_next, dt_use, t_target;
-  double clipvol, step_clipvol, mass;
+  double clipvol, step_clipvol;
   unsigned long long cmax_bits;     // max CFL rate of the step (bits of a
                                     // non-negative double, atomicMax'ed)
   unsigned long long step_nclip;

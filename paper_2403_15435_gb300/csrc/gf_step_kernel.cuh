@@ -485,8 +485,7 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
     sample_gauges<R, DEV, MP, M>(V, Pt.scen, C, p, ox, oy, s0, shu, shv, sb,
                                  M != MP || mom_issued);
   if (skip_writes) {
-    // nothing changes: no writes, no waves, and the tile's volume from the
-    // previous step (pmass[unit]) still holds
+    // nothing changes: no writes, no waves
     if (wrote) *wrote = false;
     return 0;
   }
@@ -723,8 +722,6 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
 
   // ------------------------------------------------ update, friction, out
   const R mn = rscal[4];
-  double vol = 0.0;
-  R volr = R(0);
   bool bad = false;
 #pragma unroll
   for (int r = 0; r < RC; ++r) {
@@ -745,8 +742,6 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
           lod[2 * MP * MP + kp] = 0.0f;
         }
       }
-      if constexpr (DEV) volr += sdep[c];
-      else vol += s0[c];
       continue;
     }
     const R q[3] = {s0[c], shu[c], shv[c]};  // split: the intermediate state
@@ -771,7 +766,6 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
         o[2] = o[2] / den;
       }
       if (o[0] <= rdry) { o[1] = R(0); o[2] = R(0); }
-      vol += o[0];
     } else {
       // compensated update: (hi + lo) - fl - tf, hi rounded, lo the error
       float lo[3];
@@ -811,7 +805,6 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
       if (!wnew) { o[1] = 0.0f; o[2] = 0.0f; lo[1] = 0.0f; lo[2] = 0.0f; }
 #pragma unroll
       for (int f = 0; f < 3; ++f) lod[f * MP * MP + kp] = lo[f];
-      volr += o[0] - bc;
     }
     bad |= !(isfinite(o[0]) && isfinite(o[1]) && isfinite(o[2]));
     qd[cg] = o[0];
@@ -819,9 +812,8 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
     qd[2 * TG + cg] = o[2];
     push_edge(ox + i, oy + j, o[0], o[1], o[2]);
   }
-  // block reductions: CFL rate (max), volume (fixed-order tree; FP64 in the
-  // plain form, FP32 within a warp and FP64 across warps in the deviation
-  // form)
+  // block reductions: CFL rate (max) and wet-cell count, one atomic of each
+  // per CTA
   const int lane = tid & 31, wid = tid >> 5;
   constexpr int NW = NT / 32;
   static_assert(NW <= 32, "one warp reduces the per-warp partials");
@@ -830,32 +822,27 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
   smx = warp_max(smx);
   smy = warp_max(smy);
   nwet = __reduce_add_sync(0xffffffffu, nwet);
-  if (lane == 0 && nwet) atomicAdd(&C->wet_updates, (unsigned long long)nwet);
   if constexpr (DEV) {
-    // deviation form: FP32 partials; warp 0 converts the NW warp volumes to
-    // FP64 in one instruction and sums them with a shuffle tree
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) volr += __shfl_down_sync(0xffffffffu, volr, o);
     float* redf = reinterpret_cast<float*>(red);
+    unsigned* redu = reinterpret_cast<unsigned*>(redf + 2 * NW);
     if (lane == 0) {
       redf[wid] = smx;
       redf[NW + wid] = smy;
-      redf[2 * NW + wid] = volr;
+      redu[wid] = nwet;
     }
     __syncthreads();
     if (wid == 0) {
       float mx = lane < NW ? redf[lane] : 0.0f;
       float my = lane < NW ? redf[NW + lane] : 0.0f;
+      const unsigned nw = __reduce_add_sync(0xffffffffu, lane < NW ? redu[lane] : 0u);
       mx = warp_max(mx);
       my = warp_max(my);
-      double vs = lane < NW ? (double)redf[2 * NW + lane] : 0.0;
-      vs = warp_sum_tree(vs);
       if (lane == 0) {
         const float cx = mx * G.inv_dxf[Pt.level], cy = my * G.inv_dyf[Pt.level];
         double cm = (double)(cx > cy ? cx : cy);
         if (subc) cm = cm * (double)per / (double)G.sub_K;  // cmax / n_L
         atomicMax(&C->cmax_bits, (unsigned long long)__double_as_longlong(cm));
-        pmass[unit] = vs * G.areal[Pt.level];
+        if (nw) atomicAdd(&C->wet_updates, (unsigned long long)nw);
       }
     }
     if (nclip) {
@@ -864,25 +851,26 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
     }
   } else {
     const double dx = scal[0], dy = scal[1];
-    vol = warp_sum_tree(vol);
+    unsigned* redu = reinterpret_cast<unsigned*>(red + 2 * NW);
     if (lane == 0) {
       red[wid] = (double)smx;
       red[NW + wid] = (double)smy;
-      red[2 * NW + wid] = vol;
+      redu[wid] = nwet;
     }
     __syncthreads();
     if (tid == 0) {
-      double mx = 0.0, my = 0.0, vs = 0.0;
+      double mx = 0.0, my = 0.0;
+      unsigned nw = 0u;
       for (int w = 0; w < NW; ++w) {
         mx = red[w] > mx ? red[w] : mx;
         my = red[NW + w] > my ? red[NW + w] : my;
-        vs += red[2 * NW + w];
+        nw += redu[w];
       }
       const double cx = mx / dx, cy = my / dy;
       double cm = cx > cy ? cx : cy;
       if (subc) cm = cm * (double)per / (double)G.sub_K;  // cmax / n_L
       atomicMax(&C->cmax_bits, (unsigned long long)__double_as_longlong(cm));
-      pmass[unit] = vs * (dx * dy);
+      if (nw) atomicAdd(&C->wet_updates, (unsigned long long)nw);
     }
     if (nclip) {
       atomicAdd(&C->step_nclip, (unsigned long long)nclip);
@@ -909,16 +897,13 @@ __device__ __forceinline__ int whole_tile(const GfGeom& G, const GfView& V,
   using Lo = Layout<P, M>;
   constexpr int TGW = MP + 2 * GF_NG, TG = TGW * TGW;
   constexpr int NS1 = MP / M, NSUB = NS1 * NS1;
-  constexpr int NW = NT / 32;
   static_assert(2 * TG * sizeof(R) <= Lo::OFF_RED, "tile staging fits the sub-tile layout");
-  static_assert(NSUB * NW <= 96, "per-quadrant partials fit the reduction area");
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int tid = threadIdx.x;
   const GfPatch Pt = V.patch[p];
   GfCtl* C = V.ctl + Pt.scen;
   const int cur = C->cur;
   R* s0 = reinterpret_cast<R*>(smraw);
   R* sb = s0 + TG;
-  double* red = reinterpret_cast<double*>(smraw + Lo::OFF_RED);
   int* snb = reinterpret_cast<int*>(smraw + Lo::OFF_NB);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smraw + Lo::OFF_BAR);
   const R* qs;
@@ -970,19 +955,11 @@ __device__ __forceinline__ int whole_tile(const GfGeom& G, const GfView& V,
     los = V.lof[cur] + (size_t)p * 3 * MP * MP;
     lod = V.lof[cur ^ 1] + (size_t)p * 3 * MP * MP;
   }
-  R vq[NSUB];
-#pragma unroll
-  for (int u = 0; u < NSUB; ++u) vq[u] = R(0);
-  for (int k = tid; k < MP * MP; k += NT) {
-    const int i = k % MP, j = k / MP;
-    const int c = (i + GF_NG) + (j + GF_NG) * TGW;
-    const R w = s0[c];
-    const R h = DEV ? w - sb[c] : w;
-    const int u = (i / M) + NS1 * (j / M);
-#pragma unroll
-    for (int q = 0; q < NSUB; ++q)
-      if (q == u) vq[q] += h;
-    if (!same_in) {
+  if (!same_in) {
+    for (int k = tid; k < MP * MP; k += NT) {
+      const int i = k % MP, j = k / MP;
+      const int c = (i + GF_NG) + (j + GF_NG) * TGW;
+      const R w = s0[c];
       qd[c] = w;
       qd[TG + c] = R(0);
       qd[2 * TG + c] = R(0);
@@ -995,32 +972,10 @@ __device__ __forceinline__ int whole_tile(const GfGeom& G, const GfView& V,
                        push, i, j, w, R(0), R(0));
     }
   }
-  // per-quadrant volumes: FP32 (deviation form) or FP64 partials per warp,
-  // summed in FP64 in a fixed order
-#pragma unroll
-  for (int q = 0; q < NSUB; ++q) {
-    R v = vq[q];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    vq[q] = v;
-  }
-  if (lane == 0)
-    for (int q = 0; q < NSUB; ++q) red[q * NW + wid] = (double)vq[q];
-  __syncthreads();
-  if (tid < NSUB) {
-    double vs = 0.0;
-    for (int w = 0; w < NW; ++w) vs += red[tid * NW + w];
-    pmass[p * NSUB + tid] = vs * G.areal[Pt.level];
-    if (V.same != nullptr) V.same[p * NSUB + tid] = 1;
-  }
+  if (tid < NSUB && V.same != nullptr) V.same[p * NSUB + tid] = 1;
   return 0;
 }
 
-// End of a step: the last CTA to finish applies the CFL rule to every active
-// scenario (Sec. 5.1 maximum CFL, Sec. 6.6): it sums the per-patch volumes in
-// a fixed order, rejects the step and sets a smaller dt when dt*cmax exceeds
-// cfl_max, else accepts it (swaps the state buffers, advances t) and picks
-// the next dt = cfl_desired / cmax, clipped to land on t_target.
 // Controller of a subcycled macro step (thread 0 of the last CTA of each
 // substep launch, per scenario).  The macro step of DT = dt_use runs as
 // sub_K substeps; the rates cmax / n_L of the levels that stepped arrived in
@@ -1030,7 +985,7 @@ __device__ __forceinline__ int whole_tile(const GfGeom& G, const GfView& V,
 // are not checked; their rates bound the next DT.  After the last substep
 // the time advances by DT and the next macro step is set up.
 static __device__ void subcycle_finish(const GfGeom& G, const GfView& V, volatile GfCtl* C,
-                                       int s, double vol, int cells_per_patch) {
+                                       int s, int cells_per_patch) {
   const int K = G.sub_K, k = C->sub_k;
   const double rate = __longlong_as_double((long long)C->cmax_bits);
   C->cmax_bits = 0ull;
@@ -1076,7 +1031,6 @@ static __device__ void subcycle_finish(const GfGeom& G, const GfView& V, volatil
       C->t = C->last ? C->t_target : C->t + DT;
       C->steps = C->steps + 1;
       C->taken = C->taken + 1;
-      C->mass = vol;
       const double r = __longlong_as_double((long long)C->rmax_bits);
       C->rmax_bits = 0ull;
       if (r > 0.0) {
@@ -1101,15 +1055,90 @@ static __device__ void subcycle_finish(const GfGeom& G, const GfView& V, volatil
   }
 }
 
+// CFL rule of one scenario at the end of a step (Sec. 5.1 maximum CFL,
+// Sec. 6.6), not subcycled: reject the step and set a smaller dt when
+// dt*cmax exceeds cfl_max, else accept it (swap the state buffers, advance
+// t) and pick the next dt = cfl_desired / cmax, clipped to land on t_target.
+// One thread runs it: every field it needs is read from L2 at once
+// (independent loads, one round trip instead of one per field), the
+// decision is taken on the copies, and only the fields that change are
+// written back.
+static __device__ void ctl_finish(const GfGeom& G, GfCtl* Cp, unsigned long long cells) {
+  const double cmax = __longlong_as_double((long long)__ldcg(&Cp->cmax_bits));
+  const double dt = __ldcg(&Cp->dt_use);
+  const double t = __ldcg(&Cp->t), t_target = __ldcg(&Cp->t_target);
+  const double dt_next0 = __ldcg(&Cp->dt_next);
+  const double clipvol = __ldcg(&Cp->clipvol), step_clipvol = __ldcg(&Cp->step_clipvol);
+  const unsigned long long step_nclip = __ldcg(&Cp->step_nclip);
+  const unsigned long long cell_updates = __ldcg(&Cp->cell_updates);
+  const long long steps = __ldcg(&Cp->steps), rejects = __ldcg(&Cp->rejects);
+  const long long nclip = __ldcg(&Cp->nclip), taken = __ldcg(&Cp->taken);
+  const long long max_steps = __ldcg(&Cp->max_steps);
+  const int cur = __ldcg(&Cp->cur), lastf = __ldcg(&Cp->last);
+  const int inrow = __ldcg(&Cp->inrow), nonfinite = __ldcg(&Cp->nonfinite);
+  Cp->cell_updates = cell_updates + cells;
+  Cp->cmax_bits = 0ull;
+  if (nonfinite) {
+    Cp->status = -5;  // GEOFLOOD_ERR_NAN
+    Cp->active = 0;
+    Cp->accepted = 0;
+    return;
+  }
+  double tn = t, dtn = dt_next0;
+  long long tk = taken;
+  if (dt * cmax > G.cfl_max) {
+    dtn = G.cfl_desired / cmax;
+    Cp->dt_next = dtn;
+    Cp->rejects = rejects + 1;
+    Cp->accepted = 0;
+    Cp->step_nclip = 0ull;
+    Cp->step_clipvol = 0.0;
+    Cp->inrow = inrow + 1;
+    if (inrow + 1 > GF_MAXSTEP_REJECT) {
+      Cp->status = -4;  // GEOFLOOD_ERR_CFL
+      Cp->active = 0;
+      return;
+    }
+  } else {
+    tn = lastf ? t_target : t + dt;
+    tk = taken + 1;
+    Cp->inrow = 0;
+    Cp->cur = cur ^ 1;
+    Cp->t = tn;
+    Cp->steps = steps + 1;
+    Cp->taken = tk;
+    Cp->nclip = nclip + (long long)step_nclip;
+    Cp->clipvol = clipvol + step_clipvol;
+    Cp->step_nclip = 0ull;
+    Cp->step_clipvol = 0.0;
+    Cp->accepted = 1;
+    if (cmax > 0.0) {
+      const double dn = G.cfl_desired / cmax;
+      dtn = dn < G.dt_max ? dn : G.dt_max;
+      Cp->dt_next = dtn;
+    }
+  }
+  if (!(tn < t_target) || tk >= max_steps) {
+    Cp->active = 0;
+  } else {
+    const double rem = t_target - tn;
+    if (dtn < rem) { Cp->dt_use = dtn; Cp->last = 0; }
+    else { Cp->dt_use = rem; Cp->last = 1; }
+  }
+}
+
+// End of a step: the last CTA to finish applies the CFL rule to every active
+// scenario, one thread per scenario (the scenarios' rules are independent).
+// The volume of the state is not part of the step; geoflood_mass computes it
+// on demand.
 template <int NT>
-__device__ void step_finish(const GfGeom& G, const GfView& V,
-                            const double* pmass, double* red, int nsub,
-                            int cells_per_patch, bool wrote = true) {
+__device__ void step_finish(const GfGeom& G, const GfView& V, int cells_per_patch,
+                            bool wrote = true) {
   __shared__ int last;
   __syncthreads();
   if (threadIdx.x == 0) {
-    // a CTA that wrote volumes makes them visible before it counts itself
-    // done; one that wrote nothing the controller reads needs no fence
+    // a CTA that updated the controller's counters (atomics) orders them
+    // before it counts itself done; one that did not needs no fence
     if (wrote) __threadfence();
     const unsigned t = atomicAdd(V.done, 1u);
     last = t == gridDim.x - 1;
@@ -1117,93 +1146,26 @@ __device__ void step_finish(const GfGeom& G, const GfView& V,
   __syncthreads();
   if (!last) return;
   __threadfence();
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  constexpr int NW = NT / 32;
-  const volatile double* pm = pmass;
-  for (int s = 0; s < G.nscen; ++s) {
-    volatile GfCtl* C = V.ctl + s;
-    const int act = C->active;
-    __syncthreads();
-    if (!act) {
-      if (tid == 0) C->accepted = 0;
+  for (int s = threadIdx.x; s < G.nscen; s += NT) {
+    GfCtl* Cp = V.ctl + s;
+    if (!__ldcg(&Cp->active)) {
+      Cp->accepted = 0;
       continue;
     }
-    const int off = V.scen[s].poff * nsub, n = V.scen[s].pcount * nsub;
-    if (tid == 0 && !G.subcycle)
-      C->cell_updates = C->cell_updates +
-                        (unsigned long long)V.scen[s].pcount * (unsigned long long)cells_per_patch;
-    double v = 0.0;
-    for (int k = tid; k < n; k += NT) v += pm[off + k];
-    v = warp_sum_tree(v);
-    if (lane == 0) red[wid] = v;
-    __syncthreads();
-    if (tid == 0 && G.subcycle) {
-      double vol = 0.0;
-      for (int w = 0; w < NW; ++w) vol += red[w];
-      subcycle_finish(G, V, C, s, vol, cells_per_patch);
-    } else if (tid == 0) {
-      double vol = 0.0;
-      for (int w = 0; w < NW; ++w) vol += red[w];
-      const double cmax = __longlong_as_double((long long)C->cmax_bits);
-      C->cmax_bits = 0ull;
-      const double dt = C->dt_use;
-      bool go_on = true;
-      if (C->nonfinite) {
-        C->status = -5;  // GEOFLOOD_ERR_NAN
-        C->active = 0;
-        C->accepted = 0;
-        go_on = false;
-      } else if (dt * cmax > G.cfl_max) {
-        C->dt_next = G.cfl_desired / cmax;
-        C->rejects = C->rejects + 1;
-        C->accepted = 0;
-        C->step_nclip = 0ull;
-        C->step_clipvol = 0.0;
-        C->inrow = C->inrow + 1;
-        if (C->inrow > GF_MAXSTEP_REJECT) {
-          C->status = -4;  // GEOFLOOD_ERR_CFL
-          C->active = 0;
-          go_on = false;
-        }
-      } else {
-        C->inrow = 0;
-        C->cur = C->cur ^ 1;
-        C->t = C->last ? C->t_target : C->t + dt;
-        C->steps = C->steps + 1;
-        C->taken = C->taken + 1;
-        C->nclip = C->nclip + (long long)C->step_nclip;
-        C->clipvol = C->clipvol + C->step_clipvol;
-        C->step_nclip = 0ull;
-        C->step_clipvol = 0.0;
-        C->mass = vol;
-        C->accepted = 1;
-        if (cmax > 0.0) {
-          const double dn = G.cfl_desired / cmax;
-          C->dt_next = dn < G.dt_max ? dn : G.dt_max;
-        }
-      }
-      if (go_on) {
-        if (!(C->t < C->t_target) || C->taken >= C->max_steps) {
-          C->active = 0;
-        } else {
-          const double rem = C->t_target - C->t;
-          if (C->dt_next < rem) { C->dt_use = C->dt_next; C->last = 0; }
-          else { C->dt_use = rem; C->last = 1; }
-        }
-      }
-    }
-    __syncthreads();
+    if (G.subcycle)
+      subcycle_finish(G, V, Cp, s, cells_per_patch);
+    else
+      ctl_finish(G, Cp, (unsigned long long)V.scen[s].pcount * (unsigned long long)cells_per_patch);
   }
-  if (tid == 0) {
-    if (V.sched) {
-      V.sched[0] ^= 1u;
-      V.sched[3] = V.sched[1];  // wet patches at the head of the next order
-      V.sched[1] = 0u;
-      V.sched[2] = 0u;
-    }
-    __threadfence();
-    *V.done = 0u;
+  // the next launch reads the counters and the schedule after this kernel
+  // has ended, which orders these writes before it
+  if (threadIdx.x == 0 && V.sched) {
+    V.sched[0] ^= 1u;
+    V.sched[3] = V.sched[1];  // wet patches at the head of the next order
+    V.sched[1] = 0u;
+    V.sched[2] = 0u;
   }
+  if (threadIdx.x == 0) *V.done = 0u;
 }
 
 // Adaptive variant: the previous launch's wet patches (the head of its
@@ -1266,8 +1228,7 @@ __global__ void __launch_bounds__(NT, MINB)
     else nxt[V.npatch - 1 - (int)atomicAdd(V.sched + 2, 1u)] = p;
   }
   if (V.done)
-    step_finish<NT>(G, V, pmass,
-                    reinterpret_cast<double*>(smraw + Layout<P, M>::OFF_RED), NSUB, MP * MP);
+    step_finish<NT>(G, V, MP * MP);
 }
 
 template <class P, int MP, int M, int NT, int MINB, bool DS = false>
@@ -1300,9 +1261,7 @@ __global__ void __launch_bounds__(NT, MINB)
     else nxt[V.npatch - 1 - (int)atomicAdd(V.sched + 2, 1u)] = p;
   }
   if (V.done)
-    step_finish<NT>(G, V, pmass,
-                    reinterpret_cast<double*>(smraw + Layout<P, M, DS>::OFF_RED),
-                    NSUB, MP * MP, wrote);
+    step_finish<NT>(G, V, MP * MP, wrote);
 }
 
 // Launch the patch step on every patch: MP x MP patches, M x M sub-tiles
