@@ -260,6 +260,11 @@ def measure(prec, args, dev, stream, world, local, gauges):
 AMR_T_END = 90.0
 AMR_WORKLOAD = ("V-valley 2 km x 1 km, 4x2 blocks of 32x32 patches, levels 0-3 (finest dx 1.95 m), "
                 "12 m reservoir, full breach at x = 350 m, n = 0.033, t 0->90 s, 8 gauges")
+AMR4_T_END = 12.0
+AMR4_CAP = 16 * 8 * 4 ** 4  # every patch on the finest level
+AMR4_WORKLOAD = ("V-valley 4 km x 2 km, 16x8 blocks of 32x32 patches, levels 2-4 (finest dx 0.49 m), "
+                 "20 m reservoir, full breach at x = 500 m, n = 0.033, first 12 s of the flood; "
+                 "16 gauges on the thalweg at x = 520, 545, ..., 895 m (within the flood's reach)")
 CNN_SCALE = (4.0, 8.0, 8.0, 4.0)
 
 
@@ -274,39 +279,46 @@ def measure_amr(stream):
     import torch
     from paper_2403_15435_gb300 import geoflood, inputs
 
-    t0 = time.perf_counter()
-    tr = inputs.valley_2km(seed=inputs.SEED_BASE + 40, depth=10.0, breach_x=300.0,
-                           precision=1)
-    f = geoflood.Forest(tr.cfg, tr.dem, stream=stream.cuda_stream)
-    f.set_state(tr.ic)
-    f.cnn_set_scale(CNN_SCALE)
-    f.cnn_dataset(60000)
-    st = f.advance(60.0, regrid_interval=16, check_interval=4, collect=True)
-    _, y = f.cnn_dataset_read(0, st["samples"])
-    npos = int(y.sum())
-    pw = float(np.clip((len(y) - npos) / max(npos, 1), 1.0, 20.0))
-    f.cnn_set_params(inputs.cnn_init(3))
-    loss = f.cnn_train(40, 64, lr=2e-3, pos_weight=pw, seed=7)
-    prm = f.cnn_get_params()
-    f.close()
-    train = {"samples": int(len(y)), "positives": npos, "epochs": 40,
-             "loss_first": float(loss[0]), "loss_last": float(loss[-1]),
-             "seconds": time.perf_counter() - t0}
+    def train_net(tr, t_end, capacity, epochs, cap=None):
+        """Network trained on the plain criterion's flags from a run of tr."""
+        t0 = time.perf_counter()
+        f = geoflood.Forest(tr.cfg, tr.dem, max_patches=cap, stream=stream.cuda_stream)
+        f.set_state(tr.ic)
+        f.cnn_set_scale(CNN_SCALE)
+        f.cnn_dataset(capacity)
+        st = f.advance(t_end, regrid_interval=16, check_interval=4, collect=True)
+        _, y = f.cnn_dataset_read(0, st["samples"])
+        npos = int(y.sum())
+        pw = float(np.clip((len(y) - npos) / max(npos, 1), 1.0, 20.0))
+        f.cnn_set_params(inputs.cnn_init(3))
+        loss = f.cnn_train(epochs, 64, lr=2e-3, pos_weight=pw, seed=7)
+        prm = f.cnn_get_params()
+        f.close()
+        return prm, {"samples": int(len(y)), "positives": npos, "epochs": epochs,
+                     "loss_first": float(loss[0]), "loss_last": float(loss[-1]),
+                     "seconds": time.perf_counter() - t0}
 
-    def run(prec, learned, regrid):
-        prob = inputs.valley_2km(precision=prec)
+    prm, train = train_net(inputs.valley_2km(seed=inputs.SEED_BASE + 40, depth=10.0,
+                                             breach_x=300.0, precision=1), 60.0, 60000, 40)
+
+    def run(prec, learned, regrid, make=None, t_end=AMR_T_END, cap=None, net=None, gauges=None):
+        if make is None:
+            prob = inputs.valley_2km(precision=prec)
+        else:
+            prob = make()
+            prob.cfg.precision = prec
         res = None
         for rep in range(2):  # the first run instantiates graphs and warms up
-            g = geoflood.Forest(prob.cfg, prob.dem, stream=stream.cuda_stream)
+            g = geoflood.Forest(prob.cfg, prob.dem, max_patches=cap, stream=stream.cuda_stream)
             g.set_state(prob.ic)
             g.cnn_set_scale(CNN_SCALE)
             if learned:
-                g.cnn_set_params(prm)
+                g.cnn_set_params(prm if net is None else net)
                 g.set_tagger(geoflood.TAGGER_LEARNED, 0.5)
-            g.set_gauges(prob.gauges)
+            g.set_gauges(prob.gauges if gauges is None else gauges)
             torch.cuda.synchronize()
             a = time.perf_counter()
-            s = g.advance(AMR_T_END, regrid_interval=regrid, check_interval=4,
+            s = g.advance(t_end, regrid_interval=regrid, check_interval=4,
                           regrid_on_miss=learned)
             torch.cuda.synchronize()
             wall = time.perf_counter() - a
@@ -315,24 +327,49 @@ def measure_amr(stream):
             res = {"value": cells / wall, "unit": "cell-updates/s", "wall_s": wall,
                    "steps": s["steps"], "regrids": s["regrids"],
                    "regrids_on_miss": s["miss_regrids"], "criterion_misses": s["misses"],
-                   "cell_updates": cells, "gauge_h": out[:, 1].copy(), "arrival": arr.copy()}
+                   "cell_updates": cells, "patches_at_end": g.npatch,
+                   "gauge_h": out[:, 1].copy(), "arrival": arr.copy()}
             g.close()
         return res
 
+    def compare(plain, learned):
+        both = (plain["arrival"] >= 0) & (learned["arrival"] >= 0)
+        err = {"gauge_depth_max_abs_m": float(np.abs(learned["gauge_h"] - plain["gauge_h"]).max()),
+               "arrival_max_abs_s": float(np.abs(learned["arrival"] - plain["arrival"])[both].max())
+               if both.any() else None,
+               "gauges_reached": [int((plain["arrival"] >= 0).sum()),
+                                  int((learned["arrival"] >= 0).sum())]}
+        for r in (plain, learned):
+            r.pop("gauge_h")
+            r.pop("arrival")
+        return err
+
     plain = run(0, False, 4)
     learned = run(1, True, 16)
-    both = (plain["arrival"] >= 0) & (learned["arrival"] >= 0)
-    err = {"gauge_depth_max_abs_m": float(np.abs(learned["gauge_h"] - plain["gauge_h"]).max()),
-           "arrival_max_abs_s": float(np.abs(learned["arrival"] - plain["arrival"])[both].max())
-           if both.any() else None,
-           "gauges_reached": [int((plain["arrival"] >= 0).sum()), int((learned["arrival"] >= 0).sum())]}
-    for r in (plain, learned):
-        r.pop("gauge_h")
-        r.pop("arrival")
+    err = compare(plain, learned)
+    # the full-size valley on three levels, over the first seconds of the
+    # flood, with a network trained on the plain criterion's flags from
+    # another seed of the same valley
+    tr4 = inputs.v_valley(seed=inputs.SEED_BASE + 50)
+    tr4.cfg.precision = 1
+    prm4, train4 = train_net(tr4, AMR4_T_END, 120000, 10, cap=AMR4_CAP)
+    thalweg = np.stack([520.0 + 25.0 * np.arange(16), np.full(16, 1000.0)], axis=1)
+    plain4 = run(0, False, 4, make=inputs.v_valley, t_end=AMR4_T_END, cap=AMR4_CAP,
+                 gauges=thalweg)
+    learned4 = run(1, True, 16, make=inputs.v_valley, t_end=AMR4_T_END, cap=AMR4_CAP,
+                   net=prm4, gauges=thalweg)
+    err4 = compare(plain4, learned4)
+    full = {"workload": AMR4_WORKLOAD, "plain_fp64_regrid4": plain4,
+            "fp32_learned_regrid16": learned4,
+            "speedup": learned4["value"] / plain4["value"],
+            "wall_clock_ratio": plain4["wall_s"] / learned4["wall_s"],
+            "error_vs_plain_fp64": err4, "training": train4,
+            "timing": "wall clock around the whole driver loop, second of two runs"}
     return {"workload": AMR_WORKLOAD, "plain_fp64_regrid4": plain,
             "fp32_learned_regrid16": learned, "speedup": learned["value"] / plain["value"],
             "error_vs_plain_fp64": err, "training": train,
-            "timing": "wall clock around the whole driver loop, second of two runs"}
+            "timing": "wall clock around the whole driver loop, second of two runs",
+            "valley_4km_three_levels": full}
 
 
 ENS_N = 64
