@@ -294,14 +294,19 @@ def measure_amr(stream):
         loss = f.cnn_train(epochs, 64, lr=2e-3, pos_weight=pw, seed=7)
         prm = f.cnn_get_params()
         f.close()
-        return prm, {"samples": int(len(y)), "positives": npos, "epochs": epochs,
-                     "loss_first": float(loss[0]), "loss_last": float(loss[-1]),
-                     "seconds": time.perf_counter() - t0}
+        # the positives' weight pw shifts the trained logit by log(pw): the
+        # decision threshold pw / (1 + pw) undoes it
+        thr = pw / (1.0 + pw)
+        return prm, thr, {"samples": int(len(y)), "positives": npos, "epochs": epochs,
+                          "pos_weight": pw, "threshold": thr,
+                          "loss_first": float(loss[0]), "loss_last": float(loss[-1]),
+                          "seconds": time.perf_counter() - t0}
 
-    prm, train = train_net(inputs.valley_2km(seed=inputs.SEED_BASE + 40, depth=10.0,
+    prm, thr, train = train_net(inputs.valley_2km(seed=inputs.SEED_BASE + 40, depth=10.0,
                                              breach_x=300.0, precision=1), 60.0, 60000, 40)
 
-    def run(prec, learned, regrid, make=None, t_end=AMR_T_END, cap=None, net=None, gauges=None):
+    def run(prec, learned, regrid, make=None, t_end=AMR_T_END, cap=None, net=None, gauges=None,
+            threshold=None):
         if make is None:
             prob = inputs.valley_2km(precision=prec)
         else:
@@ -314,7 +319,7 @@ def measure_amr(stream):
             g.cnn_set_scale(CNN_SCALE)
             if learned:
                 g.cnn_set_params(prm if net is None else net)
-                g.set_tagger(geoflood.TAGGER_LEARNED, 0.5)
+                g.set_tagger(geoflood.TAGGER_LEARNED, thr if threshold is None else threshold)
             g.set_gauges(prob.gauges if gauges is None else gauges)
             torch.cuda.synchronize()
             a = time.perf_counter()
@@ -352,12 +357,12 @@ def measure_amr(stream):
     # another seed of the same valley
     tr4 = inputs.v_valley(seed=inputs.SEED_BASE + 50)
     tr4.cfg.precision = 1
-    prm4, train4 = train_net(tr4, AMR4_T_END, 120000, 10, cap=AMR4_CAP)
+    prm4, thr4, train4 = train_net(tr4, AMR4_T_END, 120000, 10, cap=AMR4_CAP)
     thalweg = np.stack([520.0 + 25.0 * np.arange(16), np.full(16, 1000.0)], axis=1)
     plain4 = run(0, False, 4, make=inputs.v_valley, t_end=AMR4_T_END, cap=AMR4_CAP,
                  gauges=thalweg)
     learned4 = run(1, True, 16, make=inputs.v_valley, t_end=AMR4_T_END, cap=AMR4_CAP,
-                   net=prm4, gauges=thalweg)
+                   net=prm4, gauges=thalweg, threshold=thr4)
     err4 = compare(plain4, learned4)
     full = {"workload": AMR4_WORKLOAD, "plain_fp64_regrid4": plain4,
             "fp32_learned_regrid16": learned4,
