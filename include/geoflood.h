@@ -368,8 +368,8 @@ int geoflood_check_bounded_wait(void* stream);
  *          synchronises the stream;
  *   stream cudaStream_t or NULL.
  *
- * The scratch it needs (patch table, per-patch volumes, the CFL reduction
- * cell) lives in one static device array of about 384 KiB that every GPU
+ * The scratch it needs (patch table and the CFL reduction cell) lives in
+ * one static device array of about 260 KiB that every GPU
  * loading the library keeps until the process exits; hence npatch is limited
  * to 16384 and a larger npatch returns GEOFLOOD_ERR_CAPACITY.  The first call
  * on a device looks up that array's device address (once per device), so

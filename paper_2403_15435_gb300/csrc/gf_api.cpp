@@ -674,7 +674,7 @@ int geoflood_init_forest(const geoflood_config* cfg, void* stream,
   okk &= alloc((void**)&ctx->d_lut[1], (size_t)ctx->nscen * G.lut_per_scen * sizeof(int));
   okk &= alloc((void**)&ctx->d_scen, ctx->nscen * sizeof(GfScenario));
   okk &= alloc((void**)&ctx->d_ctl, ctx->nscen * sizeof(GfCtl));
-  okk &= alloc((void**)&ctx->d_pmass, cap * 4 * sizeof(double));  // per sub-tile
+  okk &= alloc((void**)&ctx->d_pmass, cap * sizeof(double));  // per patch (geoflood_mass)
   okk &= alloc((void**)&ctx->d_smass, ctx->nscen * sizeof(double));
   okk &= alloc((void**)&ctx->d_flags, cap);
   okk &= alloc((void**)&ctx->d_err, sizeof(int));
@@ -1078,8 +1078,8 @@ int geoflood_step(geoflood_ctx* ctx, double t_target, int max_steps,
           rg.b = pool_event(ctx);
           cudaEventRecordWithFlags(r.a, ctx->st, cudaEventRecordExternal);
         }
-        lrc |= ctx->prec ? gf::launch_patch_step_f32(ctx->G, v, ctx->d_pmass, ctx->variant, ctx->st)
-                         : gf::launch_patch_step_f64(ctx->G, v, ctx->d_pmass, ctx->variant, ctx->st);
+        lrc |= ctx->prec ? gf::launch_patch_step_f32(ctx->G, v, ctx->variant, ctx->st)
+                         : gf::launch_patch_step_f64(ctx->G, v, ctx->variant, ctx->st);
         if (sample) {
           cudaEventRecordWithFlags(r.b, ctx->st, cudaEventRecordExternal);
           gr->ev.push_back(r);
@@ -1451,13 +1451,13 @@ int geoflood_autotune(geoflood_ctx* ctx, int reps, int* variant,
   double best_ms = 1e300;
   for (int k = 0; k < nv; ++k) {
     for (int w = 0; w < 2; ++w)  // warm-up
-      CKL(ctx->prec ? gf::launch_patch_step_f32(ctx->G, v, ctx->d_pmass, k, ctx->st)
-                    : gf::launch_patch_step_f64(ctx->G, v, ctx->d_pmass, k, ctx->st),
+      CKL(ctx->prec ? gf::launch_patch_step_f32(ctx->G, v, k, ctx->st)
+                    : gf::launch_patch_step_f64(ctx->G, v, k, ctx->st),
           "autotune");
     CK(cudaEventRecord(a, ctx->st));
     for (int r = 0; r < reps; ++r)
-      CKL(ctx->prec ? gf::launch_patch_step_f32(ctx->G, v, ctx->d_pmass, k, ctx->st)
-                    : gf::launch_patch_step_f64(ctx->G, v, ctx->d_pmass, k, ctx->st),
+      CKL(ctx->prec ? gf::launch_patch_step_f32(ctx->G, v, k, ctx->st)
+                    : gf::launch_patch_step_f64(ctx->G, v, k, ctx->st),
           "autotune");
     CK(cudaEventRecord(b, ctx->st));
     CK(cudaEventSynchronize(b));

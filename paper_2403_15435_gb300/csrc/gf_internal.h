@@ -185,10 +185,8 @@ __device__ __forceinline__ double gf_bilinear(double a00, double a10, double a01
 
 namespace gf {
 int patch_step_variants(int mx, int prec, int dim_split);
-int launch_patch_step_f64(const GfGeom& g, const GfView& v, double* pmass,
-                          int variant, void* stream);
-int launch_patch_step_f32(const GfGeom& g, const GfView& v, double* pmass,
-                          int variant, void* stream);
+int launch_patch_step_f64(const GfGeom& g, const GfView& v, int variant, void* stream);
+int launch_patch_step_f32(const GfGeom& g, const GfView& v, int variant, void* stream);
 int launch_ctl_begin(GfCtl* ctl, int nscen, double t_target,
                      long long max_steps, const int* scen_mask, void* stream);
 int launch_ghost_fill(const GfGeom& g, const GfView& v, int only_active,

@@ -79,23 +79,23 @@ int patch_step_variants(int mx, int prec, int dim_split) {
   return dim_split ? 1 : (mx == 32 ? 4 : 1);
 }
 
-int launch_patch_step_f64(const GfGeom& g, const GfView& v, double* pmass,
-                          int variant, void* stream) {
+int launch_patch_step_f64(const GfGeom& g, const GfView& v, int variant,
+                          void* stream) {
   if (v.npatch <= 0) return 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (g.dim_split) {
-    if (g.M == 32) return gfs::launch_step<gfs::PrecF64, 32, 32, 512, 1, true>(g, v, pmass, st);
-    if (g.M == 16) return gfs::launch_step<gfs::PrecF64, 16, 16, 256, 1, true>(g, v, pmass, st);
+    if (g.M == 32) return gfs::launch_step<gfs::PrecF64, 32, 32, 512, 1, true>(g, v, st);
+    if (g.M == 16) return gfs::launch_step<gfs::PrecF64, 16, 16, 256, 1, true>(g, v, st);
     return -1;
   }
   if (g.M == 32 && variant == 1)
-    return gfs::launch_step<gfs::PrecF64, 32, 16, 256, 2>(g, v, pmass, st);
+    return gfs::launch_step<gfs::PrecF64, 32, 16, 256, 2>(g, v, st);
   if (g.M == 32 && variant == 2)
-    return gfs::launch_step<gfs::PrecF64, 32, 16, 256, 1>(g, v, pmass, st);
+    return gfs::launch_step<gfs::PrecF64, 32, 16, 256, 1>(g, v, st);
   if (g.M == 32 && variant == 3)
-    return gfs::launch_step_adaptive<gfs::PrecF64, 32, 16, 352, 1>(g, v, pmass, st);
-  if (g.M == 32) return gfs::launch_step<gfs::PrecF64, 32, 32, 512, 1>(g, v, pmass, st);
-  if (g.M == 16) return gfs::launch_step<gfs::PrecF64, 16, 16, 256, 1>(g, v, pmass, st);
+    return gfs::launch_step_adaptive<gfs::PrecF64, 32, 16, 352, 1>(g, v, st);
+  if (g.M == 32) return gfs::launch_step<gfs::PrecF64, 32, 32, 512, 1>(g, v, st);
+  if (g.M == 16) return gfs::launch_step<gfs::PrecF64, 16, 16, 256, 1>(g, v, st);
   return -1;
 }
 
@@ -119,12 +119,12 @@ int launch_ctl_begin(GfCtl* ctl, int nscen, double t_target,
 // They cannot create a geoflood context, because a context allocates its
 // state.  geoflood_step_tiles_noalloc runs the same FP64 patch-step kernel on
 // tiles the caller provides, and keeps the small scratch it needs (patch
-// table, per-patch volume, the reduction cell of the CFL rate) in the static
+// table and the reduction cell of the CFL rate) in the static
 // device array below, so the call allocates nothing.
 //
 // Limits and behaviour:
 //   - at most GF_NOALLOC_MAX_PATCHES patches per call (the array holds
-//     GF_NOALLOC_MAX_PATCHES * 24 bytes + 512 bytes, about 384 KiB, on every
+//     GF_NOALLOC_MAX_PATCHES * 16 bytes + 512 bytes, about 260 KiB, on every
 //     GPU that loads the library, until the process exits);
 //   - the first call on a device looks up the array's device address with
 //     cudaGetSymbolAddress (once per device); make that first call before any
@@ -142,7 +142,6 @@ struct NoallocScratch {
   GfCtl ctl;
   GfScenario scen;
   GfPatch patch[GF_NOALLOC_MAX_PATCHES];
-  double pmass[GF_NOALLOC_MAX_PATCHES];
 };
 
 static __device__ __align__(256) unsigned char
@@ -233,8 +232,8 @@ extern "C" int geoflood_step_tiles_noalloc(const double* q_in, const double* b,
   if (cudaGetLastError() != cudaSuccess)
     return noalloc_fail(-2, "step_tiles_noalloc: init launch failed");
   const int lr = mx == 32
-                     ? gfs::launch_step<gfs::PrecF64, 32, 32, 512, 1>(G, V, S->pmass, st)
-                     : gfs::launch_step<gfs::PrecF64, 16, 16, 256, 1>(G, V, S->pmass, st);
+                     ? gfs::launch_step<gfs::PrecF64, 32, 32, 512, 1>(G, V, st)
+                     : gfs::launch_step<gfs::PrecF64, 16, 16, 256, 1>(G, V, st);
   if (lr) return noalloc_fail(-2, "step_tiles_noalloc: step launch failed");
   if (cmax) {
     unsigned long long bits = 0;

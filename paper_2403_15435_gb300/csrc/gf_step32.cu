@@ -8,23 +8,23 @@
 
 namespace gf {
 
-int launch_patch_step_f32(const GfGeom& g, const GfView& v, double* pmass,
-                          int variant, void* stream) {
+int launch_patch_step_f32(const GfGeom& g, const GfView& v, int variant,
+                          void* stream) {
   if (v.npatch <= 0) return 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (g.dim_split) {
-    if (g.M == 32) return gfs::launch_step<gfs::PrecF32, 32, 32, 512, 2, true>(g, v, pmass, st);
-    if (g.M == 16) return gfs::launch_step<gfs::PrecF32, 16, 16, 352, 2, true>(g, v, pmass, st);
+    if (g.M == 32) return gfs::launch_step<gfs::PrecF32, 32, 32, 512, 2, true>(g, v, st);
+    if (g.M == 16) return gfs::launch_step<gfs::PrecF32, 16, 16, 352, 2, true>(g, v, st);
     return -1;
   }
   if (g.M == 32 && variant == 1)
-    return gfs::launch_step<gfs::PrecF32, 32, 16, 352, 2>(g, v, pmass, st);
+    return gfs::launch_step<gfs::PrecF32, 32, 16, 352, 2>(g, v, st);
   if (g.M == 32 && variant == 2)
-    return gfs::launch_step<gfs::PrecF32, 32, 32, 512, 1>(g, v, pmass, st);
+    return gfs::launch_step<gfs::PrecF32, 32, 32, 512, 1>(g, v, st);
   if (g.M == 32 && variant == 3)
-    return gfs::launch_step<gfs::PrecF32, 32, 32, 1024, 1>(g, v, pmass, st);
-  if (g.M == 32) return gfs::launch_step<gfs::PrecF32, 32, 32, 512, 2>(g, v, pmass, st);
-  if (g.M == 16) return gfs::launch_step<gfs::PrecF32, 16, 16, 352, 2>(g, v, pmass, st);
+    return gfs::launch_step<gfs::PrecF32, 32, 32, 1024, 1>(g, v, st);
+  if (g.M == 32) return gfs::launch_step<gfs::PrecF32, 32, 32, 512, 2>(g, v, st);
+  if (g.M == 16) return gfs::launch_step<gfs::PrecF32, 16, 16, 352, 2>(g, v, st);
   return -1;
 }
 

@@ -270,7 +270,6 @@ __device__ __forceinline__ void cell_item(int k, int dir, int& a, int& line) {
 // takes the y sweep on that state, without transverse terms.
 template <class P, int MP, int M, int NT, bool DS = false>
 __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
-                                          double* __restrict__ pmass,
                                           unsigned char* smraw, const int p,
                                           const int sub, TmaPhase* tp = nullptr,
                                           bool* wrote = nullptr) {
@@ -890,7 +889,6 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
 // split).
 template <class P, int MP, int M, int NT>
 __device__ __forceinline__ int whole_tile(const GfGeom& G, const GfView& V,
-                                          double* __restrict__ pmass,
                                           unsigned char* smraw, const int p) {
   using R = typename P::R;
   constexpr bool DEV = P::DEV;
@@ -1176,8 +1174,7 @@ __device__ void step_finish(const GfGeom& G, const GfView& V, int cells_per_patc
 template <class P, int MP, int M, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
     k_patch_step_adaptive(const __grid_constant__ GfGeom G,
-                          const __grid_constant__ GfView V,
-                          double* __restrict__ pmass) {
+                          const __grid_constant__ GfView V) {
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int NSUB = (MP / M) * (MP / M);
   const bool sched = V.sched != nullptr && V.done != nullptr;
@@ -1197,7 +1194,7 @@ __global__ void __launch_bounds__(NT, MINB)
     whole = true;
   }
   if (p >= 0) active = V.ctl[V.patch[p].scen].active != 0;
-  if (whole && active && whole_tile<P, MP, M, NT>(G, V, pmass, smraw, p)) {
+  if (whole && active && whole_tile<P, MP, M, NT>(G, V, smraw, p)) {
     wet = 1;
     s_lo = 0;
     s_hi = NSUB;
@@ -1205,7 +1202,7 @@ __global__ void __launch_bounds__(NT, MINB)
   if (!active) s_hi = s_lo;
   // one call site of the sub-tile body
   for (int sub = s_lo; sub < s_hi; ++sub) {
-    wet |= patch_body<P, MP, M, NT>(G, V, pmass, smraw, p, sub);
+    wet |= patch_body<P, MP, M, NT>(G, V, smraw, p, sub);
     __syncthreads();
   }
   bool report = whole && threadIdx.x == 0;
@@ -1234,7 +1231,7 @@ __global__ void __launch_bounds__(NT, MINB)
 template <class P, int MP, int M, int NT, int MINB, bool DS = false>
 __global__ void __launch_bounds__(NT, MINB)
     k_patch_step(const __grid_constant__ GfGeom G,
-                 const __grid_constant__ GfView V, double* __restrict__ pmass) {
+                 const __grid_constant__ GfView V) {
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int NSUB = (MP / M) * (MP / M);
   const int slot = blockIdx.x / NSUB, sub = blockIdx.x % NSUB;
@@ -1253,7 +1250,7 @@ __global__ void __launch_bounds__(NT, MINB)
     run = !C.sub_rej && C.sub_k % (1 << (G.maxlevel - Pt.level)) == 0;
   }
   if (run)
-    wet = patch_body<P, MP, M, NT, DS>(G, V, pmass, smraw, p, sub, nullptr, &wrote);
+    wet = patch_body<P, MP, M, NT, DS>(G, V, smraw, p, sub, nullptr, &wrote);
   else wrote = false;
   if (sched && sub == 0 && threadIdx.x == 0) {
     int* nxt = par ? V.ord0 : V.ord1;
@@ -1266,10 +1263,8 @@ __global__ void __launch_bounds__(NT, MINB)
 
 // Launch the patch step on every patch: MP x MP patches, M x M sub-tiles
 // per CTA of NT threads (MINB CTAs per SM), DS = dimensional splitting.
-// pmass holds (MP/M)^2 entries per patch.
 template <class P, int MP, int M, int NT, int MINB, bool DS = false>
-int launch_step(const GfGeom& g, const GfView& v, double* pmass,
-                cudaStream_t st) {
+int launch_step(const GfGeom& g, const GfView& v, cudaStream_t st) {
   constexpr size_t bytes = Layout<P, M, DS>::BYTES;
   static bool attr = false;
   if (!attr) {
@@ -1280,15 +1275,14 @@ int launch_step(const GfGeom& g, const GfView& v, double* pmass,
     attr = true;
   }
   constexpr int NSUB = (MP / M) * (MP / M);
-  k_patch_step<P, MP, M, NT, MINB, DS><<<v.npatch * NSUB, NT, bytes, st>>>(g, v, pmass);
+  k_patch_step<P, MP, M, NT, MINB, DS><<<v.npatch * NSUB, NT, bytes, st>>>(g, v);
   return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
 // Launch the adaptive variant (NSUB CTAs per patch, see
-// k_patch_step_adaptive); pmass holds (MP/M)^2 entries per patch.
+// k_patch_step_adaptive).
 template <class P, int MP, int M, int NT, int MINB>
-int launch_step_adaptive(const GfGeom& g, const GfView& v, double* pmass,
-                         cudaStream_t st) {
+int launch_step_adaptive(const GfGeom& g, const GfView& v, cudaStream_t st) {
   constexpr size_t bytes = Layout<P, M>::BYTES;
   static bool attr = false;
   if (!attr) {
@@ -1299,7 +1293,7 @@ int launch_step_adaptive(const GfGeom& g, const GfView& v, double* pmass,
     attr = true;
   }
   constexpr int NSUB = (MP / M) * (MP / M);
-  k_patch_step_adaptive<P, MP, M, NT, MINB><<<v.npatch * NSUB, NT, bytes, st>>>(g, v, pmass);
+  k_patch_step_adaptive<P, MP, M, NT, MINB><<<v.npatch * NSUB, NT, bytes, st>>>(g, v);
   return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
