@@ -377,3 +377,52 @@ def test_refinement_with_emerging_children_keeps_momentum_and_speeds(dry_column)
             wf = ch[0] > 0
             assert (np.abs(ch[1:3][:, wf] / ch[0][wf]) <= vmax * (1 + 1e-12)).all()
     assert clamped >= 8
+
+
+def test_valley_floods_keep_physical_speeds_through_regrids():
+    """Eight valleys of the 64-scenario ensemble as one context runs them
+    (the first valley's configuration, each with its own Manning n, surface
+    and terrain; a regrid whenever 4 steps have passed in some scenario)
+    advanced 2 s, then two regrid + 4-step cycles: no cell deeper than
+    drytol moves faster than 60 m/s.  The interpolation of momentum into new
+    fine cells (Sec. 6.2) must not hand a shallow child its deep parent's
+    momentum: copying it gave 200-1300 m/s in these valleys."""
+    probs = inputs.valley_ensemble(64, precision=0)
+    cfg = probs[0].cfg
+    fs = []
+    for p in probs[:8]:
+        c = inputs.Config(**{**cfg.__dict__, "manning_n": p.cfg.manning_n, "eta0": p.cfg.eta0})
+        f = oracle.OracleForest(c, p.dem)
+        f.set_state(p.ic)
+        fs.append(f)
+
+    def fastest():
+        out = []
+        for f in fs:
+            h, hu, hv, _ = f.read()
+            wet = h > 1e-3
+            sp = np.sqrt(hu[wet] ** 2 + hv[wet] ** 2) / h[wet]
+            assert np.isfinite(sp).all()
+            out.append(float(sp.max()) if sp.size else 0.0)
+        return max(out)
+
+    since = 0
+    while True:
+        before = [f.time()["steps"] for f in fs]
+        for f in fs:
+            f.step(2.0, 4 - since)
+        since += max(f.time()["steps"] - b for f, b in zip(fs, before))
+        if all(f.time()["t"] >= 2.0 for f in fs):
+            break
+        if since >= 4:
+            for f in fs:
+                f.regrid()
+            since = 0
+    assert fastest() < 60.0
+    for _ in range(2):
+        for f in fs:
+            f.regrid()
+        assert fastest() < 60.0
+        for f in fs:
+            f.step(1e9, 4)
+        assert fastest() < 60.0
