@@ -974,41 +974,58 @@ __device__ __forceinline__ int whole_tile(const GfGeom& G, const GfView& V,
   return 0;
 }
 
-// Controller of a subcycled macro step (thread 0 of the last CTA of each
-// substep launch, per scenario).  The macro step of DT = dt_use runs as
+// Controller of a subcycled macro step (one thread of the last CTA of each
+// substep launch per scenario).  The macro step of DT = dt_use runs as
 // sub_K substeps; the rates cmax / n_L of the levels that stepped arrived in
 // cmax_bits.  Substep 0 (every level steps) is checked against cfl_max: a
 // violation rejects the macro step, whose remaining substeps then do
 // nothing, and it is retaken with DT = cfl_desired / rate.  Later substeps
 // are not checked; their rates bound the next DT.  After the last substep
 // the time advances by DT and the next macro step is set up.
-static __device__ void subcycle_finish(const GfGeom& G, const GfView& V, volatile GfCtl* C,
+static __device__ void subcycle_finish(const GfGeom& G, const GfView& V, GfCtl* Cp,
                                        int s, int cells_per_patch) {
-  const int K = G.sub_K, k = C->sub_k;
-  const double rate = __longlong_as_double((long long)C->cmax_bits);
-  C->cmax_bits = 0ull;
-  const double DT = C->dt_use;
-  bool end = k == K - 1, go_on = true;
-  if (C->nonfinite) {
-    C->status = -5;  // GEOFLOOD_ERR_NAN
-    C->active = 0;
-    C->accepted = 0;
-    go_on = false;
-  } else if (C->sub_rej) {
-    C->accepted = 0;
+  // every field the rule needs, read from L2 at once
+  const int K = G.sub_K;
+  const int k = __ldcg(&Cp->sub_k), sub_rej = __ldcg(&Cp->sub_rej);
+  const double rate = __longlong_as_double((long long)__ldcg(&Cp->cmax_bits));
+  const double DT = __ldcg(&Cp->dt_use);
+  const double t = __ldcg(&Cp->t), t_target = __ldcg(&Cp->t_target);
+  const double dt_next0 = __ldcg(&Cp->dt_next);
+  const double clipvol = __ldcg(&Cp->clipvol), step_clipvol = __ldcg(&Cp->step_clipvol);
+  const unsigned long long step_nclip = __ldcg(&Cp->step_nclip);
+  const unsigned long long cell_updates = __ldcg(&Cp->cell_updates);
+  const unsigned long long rmax_bits = __ldcg(&Cp->rmax_bits);
+  const long long steps = __ldcg(&Cp->steps), rejects = __ldcg(&Cp->rejects);
+  const long long nclip = __ldcg(&Cp->nclip), taken = __ldcg(&Cp->taken);
+  const long long max_steps = __ldcg(&Cp->max_steps);
+  const int inrow = __ldcg(&Cp->inrow), lastf = __ldcg(&Cp->last);
+  const int nonfinite = __ldcg(&Cp->nonfinite);
+  Cp->cmax_bits = 0ull;
+  const bool end = k == K - 1;
+  double tn = t, dtn = dt_next0;
+  long long tk = taken;
+  if (nonfinite) {
+    Cp->status = -5;  // GEOFLOOD_ERR_NAN
+    Cp->active = 0;
+    Cp->accepted = 0;
+    return;
+  }
+  if (sub_rej) {
+    Cp->accepted = 0;
   } else if (k == 0 && DT * rate > G.cfl_max) {
-    C->dt_next = G.cfl_desired / rate;
-    C->rejects = C->rejects + 1;
-    C->accepted = 0;
-    C->step_nclip = 0ull;
-    C->step_clipvol = 0.0;
-    C->rmax_bits = 0ull;
-    C->inrow = C->inrow + 1;
-    C->sub_rej = 1;
-    if (C->inrow > GF_MAXSTEP_REJECT) {
-      C->status = -4;  // GEOFLOOD_ERR_CFL
-      C->active = 0;
-      go_on = false;
+    dtn = G.cfl_desired / rate;
+    Cp->dt_next = dtn;
+    Cp->rejects = rejects + 1;
+    Cp->accepted = 0;
+    Cp->step_nclip = 0ull;
+    Cp->step_clipvol = 0.0;
+    Cp->rmax_bits = 0ull;
+    Cp->inrow = inrow + 1;
+    Cp->sub_rej = 1;
+    if (inrow + 1 > GF_MAXSTEP_REJECT) {
+      Cp->status = -4;  // GEOFLOOD_ERR_CFL
+      Cp->active = 0;
+      return;
     }
   } else {
     // the substep stands: count the levels that stepped
@@ -1016,40 +1033,44 @@ static __device__ void subcycle_finish(const GfGeom& G, const GfView& V, volatil
     for (int L = G.minlevel; L <= G.maxlevel; ++L)
       if (k % (1 << (G.maxlevel - L)) == 0)
         cells += (unsigned long long)V.scen[s].lcount[L] * (unsigned long long)cells_per_patch;
-    C->cell_updates = C->cell_updates + cells;
-    const double rm = __longlong_as_double((long long)C->rmax_bits);
-    if (rate > rm) C->rmax_bits = (unsigned long long)__double_as_longlong(rate);
-    C->nclip = C->nclip + (long long)C->step_nclip;
-    C->clipvol = C->clipvol + C->step_clipvol;
-    C->step_nclip = 0ull;
-    C->step_clipvol = 0.0;
-    C->accepted = 1;
+    Cp->cell_updates = cell_updates + cells;
+    unsigned long long rb = rmax_bits;
+    if (rate > __longlong_as_double((long long)rmax_bits))
+      rb = (unsigned long long)__double_as_longlong(rate);
+    Cp->nclip = nclip + (long long)step_nclip;
+    Cp->clipvol = clipvol + step_clipvol;
+    Cp->step_nclip = 0ull;
+    Cp->step_clipvol = 0.0;
+    Cp->accepted = 1;
     if (end) {
-      C->inrow = 0;
-      C->t = C->last ? C->t_target : C->t + DT;
-      C->steps = C->steps + 1;
-      C->taken = C->taken + 1;
-      const double r = __longlong_as_double((long long)C->rmax_bits);
-      C->rmax_bits = 0ull;
+      tn = lastf ? t_target : t + DT;
+      tk = taken + 1;
+      Cp->inrow = 0;
+      Cp->t = tn;
+      Cp->steps = steps + 1;
+      Cp->taken = tk;
+      const double r = __longlong_as_double((long long)rb);
+      rb = 0ull;
       if (r > 0.0) {
         const double dn = G.cfl_desired / r;
-        C->dt_next = dn < G.dt_max ? dn : G.dt_max;
+        dtn = dn < G.dt_max ? dn : G.dt_max;
+        Cp->dt_next = dtn;
       }
     }
+    Cp->rmax_bits = rb;
   }
-  if (!go_on) return;
   if (!end) {
-    C->sub_k = k + 1;
+    Cp->sub_k = k + 1;
     return;
   }
-  C->sub_k = 0;
-  C->sub_rej = 0;
-  if (!(C->t < C->t_target) || C->taken >= C->max_steps) {
-    C->active = 0;
+  Cp->sub_k = 0;
+  Cp->sub_rej = 0;
+  if (!(tn < t_target) || tk >= max_steps) {
+    Cp->active = 0;
   } else {
-    const double rem = C->t_target - C->t;
-    if (C->dt_next < rem) { C->dt_use = C->dt_next; C->last = 0; }
-    else { C->dt_use = rem; C->last = 1; }
+    const double rem = t_target - tn;
+    if (dtn < rem) { Cp->dt_use = dtn; Cp->last = 0; }
+    else { Cp->dt_use = rem; Cp->last = 1; }
   }
 }
 
