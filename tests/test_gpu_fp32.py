@@ -1,7 +1,7 @@
 """FP32 surface-deviation path (GEOFLOOD_FP32_DEV) against the FP64 oracle.
 
 Per step from identical inputs: |dh| <= 1e-4 m and |dhu|, |dhv| <= 1e-4 m^2/s
-(spec bound).  Whole runs: the errors (depth, momentum, volume drift,
+(the FP32 per-step bound).  Whole runs: the errors (depth, momentum, volume drift,
 gauge arrival times, wet-mask and tag mismatches) are measured and bounded
 loosely, since limiter switches amplify rounding differences over many
 steps.  Lake at rest stays exactly at rest in FP32 (the deviation form)."""

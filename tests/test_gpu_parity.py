@@ -1,7 +1,7 @@
 """GPU (sm_103a) vs the FP64 oracle through the C ABI.
 
 Tolerance (FP64): max-norm difference per field <= 1e-12 relative to the
-field's largest magnitude (spec bound); wet masks (h > drytol), tags and
+field's largest magnitude (the FP64 bound); wet masks (h > drytol), tags and
 patch lists bit-exact.  Both sides run without fused multiply-add, so most
 results agree to the last bit; the bound leaves room for the one libm
 difference (cbrt in the friction term)."""
