@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 # 1024, the same workload at t about 28 s, the middle of the timed run; ncu
 # flushes the caches before each pass, so these are cold-cache figures).
 # None when the kernel has changed since the capture.
-TRAFFIC_PER_LAUNCH_FP64 = 24070144
+TRAFFIC_PER_LAUNCH_FP64 = 24068864
 N_CELLS = 1024
 PATCH = 32
 T_END = 60.0
@@ -153,7 +153,7 @@ def measured_peaks():
 BYTES_PER_CELL_FP32 = 52
 OPS_PER_WET_CELL_FP32 = 500
 FP32_LANES_PER_SM = 128
-TRAFFIC_PER_LAUNCH_FP32 = 13560320
+TRAFFIC_PER_LAUNCH_FP32 = 13558528
 # Algorithmic work of the FP64 patch step, counted operation by operation
 # from the scheme: a wet cell update takes two edge solves (74 operations
 # each), two limited edge fluxes (81), two increments (9), two transverse
