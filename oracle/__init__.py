@@ -100,6 +100,7 @@ def lib():
             L.oracle_forest_step.argtypes = [vp, C.c_double, C.c_int, dp, ip]
             L.oracle_forest_tags.argtypes = [vp, C.POINTER(C.c_uint8)]
             L.oracle_forest_regrid.argtypes = [vp]
+            L.oracle_forest_regrid_flags.argtypes = [vp, C.POINTER(C.c_uint8)]
             L.oracle_forest_mass.restype = C.c_double
             L.oracle_forest_mass.argtypes = [vp]
             L.oracle_forest_set_gauges.argtypes = [vp, dp, C.c_int]
@@ -313,6 +314,12 @@ class OracleForest:
 
     def regrid(self):
         return lib().oracle_forest_regrid(self._h)
+
+    def regrid_flags(self, flags):
+        """Regrid from given per-leaf flags (0 keep, 1 refine, 2 coarsen)."""
+        f = np.ascontiguousarray(flags, dtype=np.uint8)
+        assert f.shape == (self.npatch,)
+        return lib().oracle_forest_regrid_flags(self._h, _p(f, C.c_uint8))
 
     def mass(self):
         return lib().oracle_forest_mass(self._h)

@@ -1603,10 +1603,10 @@ static int lm_ring_max(const lvlmap* lm, int L, int px, int py) {
  * 2:1 balance across faces and corners (no level skipping), coarsen sibling
  * quartets that all ask for it when the balance allows, then move the data
  * with the ghost-cell operators (copy, average, interpolate). */
-int oracle_forest_regrid(oracle_forest* f) {
+int oracle_forest_regrid_flags(oracle_forest* f, const uint8_t* given) {
   int n0 = f->np, k, c;
   uint8_t* flags = (uint8_t*)malloc(n0 ? n0 : 1);
-  oracle_forest_tags(f, flags);
+  if (n0) memcpy(flags, given, (size_t)n0);
   int cap = 4 * n0 + 16;
   int* lev = (int*)malloc(sizeof(int) * cap);
   int* px = (int*)malloc(sizeof(int) * cap);
@@ -1716,6 +1716,14 @@ int oracle_forest_regrid(oracle_forest* f) {
   free(keep); free(pos); free(addL); free(addX); free(addY);
   free(NL); free(NX_); free(NY_);
   return f->np;
+}
+
+int oracle_forest_regrid(oracle_forest* f) {
+  uint8_t* flags = (uint8_t*)malloc(f->np ? f->np : 1);
+  oracle_forest_tags(f, flags);
+  int n = oracle_forest_regrid_flags(f, flags);
+  free(flags);
+  return n;
 }
 
 /* Volume sum_cells h dx dy with Kahan compensation. */

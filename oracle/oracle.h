@@ -154,6 +154,9 @@ int oracle_forest_step(oracle_forest* f, double t_target, int max_steps,
                        double* t_out, int* steps_out);
 void oracle_forest_tags(const oracle_forest* f, uint8_t* flags);
 int oracle_forest_regrid(oracle_forest* f);
+/* The same regrid from given per-leaf flags (ORACLE_TAG_*, one per current
+ * leaf, in patch order) instead of the tagger's. */
+int oracle_forest_regrid_flags(oracle_forest* f, const uint8_t* flags);
 double oracle_forest_mass(const oracle_forest* f);
 int oracle_forest_set_gauges(oracle_forest* f, const double* xy, int n);
 void oracle_forest_gauges(const oracle_forest* f, double* out,
