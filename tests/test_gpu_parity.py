@@ -379,3 +379,22 @@ def test_regrid_with_scenarios_at_different_buffer_parities(prec):
                 c = refs[s].read()
                 for x, y in zip(a, c):
                     assert rel(x, y) <= 1e-11
+
+
+def test_regrid_beyond_capacity_fails_and_leaves_the_forest_usable():
+    """A regrid that needs more patches than the context holds returns
+    GEOFLOOD_ERR_CAPACITY and changes nothing: the context keeps its forest
+    and then steps exactly as the oracle does on the unrefined forest."""
+    base = inputs.radial_dambreak(64, 16, dx=8.0, radius=120.0)
+    prob = two_level(base, (0.0, 1e9, 0.0, 1e9))  # every patch asks to refine
+    g, r = pair(prob, max_patches=4)
+    before = [list(a) for a in g.patch_info()]
+    assert len(before[0]) == 4
+    with pytest.raises(geoflood.GeoFloodError) as e:
+        g.regrid()
+    assert e.value.code == -8
+    assert [list(a) for a in g.patch_info()] == before
+    g.step(1e9, 6)
+    r.step(1e9, 6)
+    assert g.time()["steps"] == r.time()["steps"]
+    assert_same_state(g, r, tol=1e-11)
