@@ -398,3 +398,32 @@ def test_regrid_beyond_capacity_fails_and_leaves_the_forest_usable():
     r.step(1e9, 6)
     assert g.time()["steps"] == r.time()["steps"]
     assert_same_state(g, r, tol=1e-11)
+
+
+@pytest.mark.parametrize("bad", [{"mx": 24}, {"minlevel": 2, "maxlevel": 1}, {"drytol": 0.0},
+                                 {"cfl_desired": 0.9, "cfl_max": 0.5}, {"precision": 7}])
+def test_invalid_configuration_is_refused(bad):
+    """Patch sizes other than 16 and 32, an inverted level range, a
+    non-positive dry tolerance, cfl_max below cfl_desired and unknown
+    precisions are refused at creation with GEOFLOOD_ERR_ARG."""
+    prob = inputs.radial_dambreak(64, 16, dx=8.0, radius=120.0)
+    cfg = inputs.Config(**{**prob.cfg.__dict__, **bad})
+    with pytest.raises(geoflood.GeoFloodError) as e:
+        geoflood.Forest(cfg, prob.dem)
+    assert e.value.code == -1
+
+
+def test_bad_call_arguments_are_refused_and_the_context_still_steps():
+    """A scenario index out of range and a negative Manning coefficient are
+    refused with GEOFLOOD_ERR_ARG; the context then steps as the oracle."""
+    prob = inputs.radial_dambreak(64, 16, dx=8.0, radius=120.0)
+    g, r = pair(prob)
+    for call in (lambda: g.read(1), lambda: g.set_scenario(1, 0.03, 0.0),
+                 lambda: g.set_scenario(0, -0.01, 0.0)):
+        with pytest.raises(geoflood.GeoFloodError) as e:
+            call()
+        assert e.value.code == -1
+    g.step(1e9, 4)
+    r.step(1e9, 4)
+    assert g.time()["steps"] == r.time()["steps"]
+    assert_same_state(g, r)
