@@ -427,3 +427,22 @@ def test_bad_call_arguments_are_refused_and_the_context_still_steps():
     r.step(1e9, 4)
     assert g.time()["steps"] == r.time()["steps"]
     assert_same_state(g, r)
+
+
+def test_single_patch_forest_and_a_target_already_reached():
+    """Degenerate sizes: a forest of one 32 x 32 patch (all four sides
+    physical boundaries) steps as the oracle; a call whose target time is
+    already reached takes no step and leaves the state as it was."""
+    prob = inputs.radial_dambreak(32, 32, dx=4.0, radius=40.0)
+    g, r = pair(prob)
+    assert g.npatch == 1
+    g.step(1e9, 10)
+    r.step(1e9, 10)
+    assert g.time()["steps"] == r.time()["steps"] == 10
+    assert_same_state(g, r)
+    t = g.time()["t"]
+    before = g.read()
+    _, n = g.step(t, 5)
+    assert n == 0 and g.time()["t"] == t and g.time()["steps"] == 10
+    for a, b in zip(g.read(), before):
+        assert np.array_equal(a, b)
