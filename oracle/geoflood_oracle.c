@@ -4,10 +4,11 @@
  * Plain double-precision loops, written from the method as the GeoFlood paper
  * (arXiv 2403.15435) states it and from the published methods it names.
  * Each function cites the passage it follows.  Where the paper only cites a
- * method (the augmented solver, the limiter, the 2D extension, the ghost-cell
- * operators, the tagging thresholds) the code follows the written readings of
- * the repository's design notes; the same readings bind the CUDA library,
- * which shares no code with this file.
+ * method (the augmented solver of Sec. 3.3, the TVD limiter and the 2D
+ * extension of Sec. 3.2, the ghost-cell operators of Sec. 4, the tagging
+ * thresholds of Sec. 4.1) the comment beside the code states the reading
+ * taken; the same readings bind the CUDA library, which shares no code with
+ * this file.
  *
  * Parity pins for every function live in tests/test_oracle_*.py.
  */
