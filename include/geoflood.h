@@ -18,8 +18,10 @@
  *     the call; device state is owned by the context and freed by
  *     geoflood_destroy();
  *   - calls on one context are not thread safe; all device work is issued on
- *     the stream given to geoflood_init_forest() (NULL = the legacy default
- *     stream); calls that return host data synchronise that stream;
+ *     the stream given to geoflood_init_forest() (NULL = a blocking stream
+ *     the context creates for itself, since CUDA graphs cannot be captured
+ *     on the legacy default stream); calls that return host data
+ *     synchronise that stream;
  *   - arrays of patch data are [npatch][mx][mx] row-major (row index j along
  *     y, column index i along x) in the scenario's patch order, which is the
  *     Morton order of the patches on the finest patch grid;
@@ -358,14 +360,24 @@ int geoflood_check_bounded_wait(void* stream);
  *   q_in   device, [npatch][3][mx+4][mx+4] h, hu, hv with the two ghost
  *          layers already filled (e.g. by geoflood_read_tiles);
  *   b      device, [npatch][mx+4][mx+4] bed, ghosts included;
- *   q_out  device, same shape as q_in and distinct from it: the interior of
- *          every tile is written, the ghost entries are left untouched;
+ *   q_out  device, same shape as q_in, not overlapping q_in or b: the
+ *          interior of every tile is written; each tile is stepped as a lone
+ *          patch with walls on all four sides, so the two ghost layers of
+ *          q_out receive the wall mirrors of the new edge cells (normal
+ *          momentum negated), not neighbour data: refill them before using
+ *          q_out as the next call's q_in;
+ *   q_in, b and q_out must be 16-byte aligned (the tiles are staged with
+ *   bulk copies); a misaligned or overlapping buffer returns ARG before any
+ *   work is issued;
  *   mx     16 or 32; dx, dy the cell sizes; dt the step; g, drytol,
  *          manning_n as in the context API;
  *   cmax   host, may be NULL: receives max over the patches of
  *          max(|s|/dx, |s|/dy) over the edges that update interior cells
  *          (the CFL number of the step is dt * cmax); when non-NULL the call
- *          synchronises the stream;
+ *          synchronises the stream and also reads the kernel's status:
+ *          TIMEOUT if a bounded wait gave up (some tiles unwritten), NAN if
+ *          a non-finite value appeared.  With cmax NULL nothing is read back
+ *          and these two errors are not reported;
  *   stream cudaStream_t or NULL.
  *
  * The scratch it needs (patch table and the CFL reduction cell) lives in
@@ -376,8 +388,10 @@ int geoflood_check_bounded_wait(void* stream);
  * make the first call before any stream capture.  All calls share the array
  * and each call overwrites the previous call's contents (the reduction cell
  * is cleared at the start of every call): calls whose work overlaps on the
- * GPU race, so keep them on one stream.  Errors: ARG, CAPACITY, CUDA; the
- * message is returned by geoflood_noalloc_last_error(). */
+ * GPU race, so keep them on one stream.  Only the device-address lookup is
+ * safe to make from several host threads at once; calls made concurrently
+ * share the array and race as above.  Errors: ARG, CAPACITY, CUDA, TIMEOUT,
+ * NAN; the message is returned by geoflood_noalloc_last_error(). */
 int geoflood_step_tiles_noalloc(const double* q_in, const double* b,
                                 double* q_out, int npatch, int mx, double dx,
                                 double dy, double dt, double g, double drytol,

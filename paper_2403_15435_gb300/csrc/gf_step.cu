@@ -6,6 +6,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <atomic>
 #include <cstring>
 
 #include "gf_internal.h"
@@ -114,8 +115,8 @@ int launch_ctl_begin(GfCtl* ctl, int nscen, double t_target,
 //
 // Some callers own every byte of device memory themselves: a solver embedded
 // in a host code with its own memory pool, or code that runs where
-// cudaMalloc is not allowed (inside a captured region that must not grow the
-// pool, or under an allocator that hands out only pre-registered buffers).
+// cudaMalloc is not allowed (a section that must not grow the device pool,
+// or an allocator that hands out only pre-registered buffers).
 // They cannot create a geoflood context, because a context allocates its
 // state.  geoflood_step_tiles_noalloc runs the same FP64 patch-step kernel on
 // tiles the caller provides, and keeps the small scratch it needs (patch
@@ -164,23 +165,35 @@ __global__ void k_noalloc_init(NoallocScratch* S, int n, double dt,
   if (k < n) S->patch[k] = GfPatch{0, 0, 0, 0};
 }
 
+// Device address of the scratch array on the current device, looked up once
+// per device.  Two host threads may look it up at the same time; both store
+// the same address, and the atomics make that well defined.
 NoallocScratch* noalloc_scratch(int* rc) {
-  static NoallocScratch* addr[64] = {nullptr};
+  static std::atomic<NoallocScratch*> addr[64];
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
     *rc = -2;
     return nullptr;
   }
-  if (!addr[dev]) {
+  NoallocScratch* a = addr[dev].load(std::memory_order_acquire);
+  if (!a) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, gf_noalloc_scratch) != cudaSuccess || !p) {
       *rc = -2;
       return nullptr;
     }
-    addr[dev] = static_cast<NoallocScratch*>(p);
+    a = static_cast<NoallocScratch*>(p);
+    addr[dev].store(a, std::memory_order_release);
   }
   *rc = 0;
-  return addr[dev];
+  return a;
+}
+
+// Whether the byte ranges [a, a + na) and [b, b + nb) intersect.
+bool ranges_overlap(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t pa = reinterpret_cast<uintptr_t>(a);
+  const uintptr_t pb = reinterpret_cast<uintptr_t>(b);
+  return pa < pb + nb && pb < pa + na;
 }
 
 thread_local char noalloc_err[256] = "";
@@ -206,6 +219,19 @@ extern "C" int geoflood_step_tiles_noalloc(const double* q_in, const double* b,
     return noalloc_fail(-1, "step_tiles_noalloc: bad argument");
   if (npatch < 1 || npatch > GF_NOALLOC_MAX_PATCHES)
     return noalloc_fail(-8, "step_tiles_noalloc: npatch must be in [1, 16384]");
+  // the kernel stages whole tiles with bulk copies, which need 16-byte
+  // aligned addresses (a tile plane is a multiple of 16 bytes for mx = 16
+  // and 32, so every tile of an aligned buffer is aligned)
+  if ((reinterpret_cast<uintptr_t>(q_in) | reinterpret_cast<uintptr_t>(b) |
+       reinterpret_cast<uintptr_t>(q_out)) & 15u)
+    return noalloc_fail(-1, "step_tiles_noalloc: q_in, b and q_out must be 16-byte aligned");
+  {
+    const size_t T = (size_t)mx + 2 * GF_NG;
+    const size_t qbytes = 3 * (size_t)npatch * T * T * sizeof(double);
+    const size_t bbytes = (size_t)npatch * T * T * sizeof(double);
+    if (ranges_overlap(q_out, qbytes, q_in, qbytes) || ranges_overlap(q_out, qbytes, b, bbytes))
+      return noalloc_fail(-1, "step_tiles_noalloc: q_out overlaps q_in or b");
+  }
   int rc = 0;
   NoallocScratch* S = noalloc_scratch(&rc);
   if (!S) return noalloc_fail(rc, "step_tiles_noalloc: cudaGetSymbolAddress failed");
@@ -236,14 +262,21 @@ extern "C" int geoflood_step_tiles_noalloc(const double* q_in, const double* b,
                      : gfs::launch_step<gfs::PrecF64, 16, 16, 256, 1>(G, V, st);
   if (lr) return noalloc_fail(-2, "step_tiles_noalloc: step launch failed");
   if (cmax) {
-    unsigned long long bits = 0;
-    if (cudaMemcpyAsync(&bits, &S->ctl.cmax_bits, sizeof(bits),
-                        cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+    // the reduction cell and the kernel's status in one copy: a bounded
+    // wait that gave up leaves its tile unwritten, and a non-finite value
+    // makes the result unusable; both are reported instead of success
+    GfCtl c{};
+    if (cudaMemcpyAsync(&c, &S->ctl, sizeof(c), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
       return noalloc_fail(-2, "step_tiles_noalloc: reading the CFL rate failed");
     double v;
-    std::memcpy(&v, &bits, sizeof(v));
+    std::memcpy(&v, &c.cmax_bits, sizeof(v));
     *cmax = v;
+    if (c.status == -7)
+      return noalloc_fail(-7, "step_tiles_noalloc: a bounded device wait expired; "
+                              "some tiles were not written");
+    if (c.nonfinite || c.status == -5)
+      return noalloc_fail(-5, "step_tiles_noalloc: non-finite value in the result");
   }
   return 0;
 }
