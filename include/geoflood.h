@@ -309,6 +309,13 @@ int geoflood_profile(geoflood_ctx* ctx, int enable);
 int geoflood_profile_read(geoflood_ctx* ctx, const char* kernel,
                           double* total_ms, long long* launches);
 
+/* Interior cells covered by the recorded launches of one kernel family
+ * since geoflood_profile(ctx, 1): for "patch_step", the patch count times
+ * mx^2 of each recorded launch (all patches of the launch, dry or wet), so
+ * that a roofline can use the cells of the launches actually timed while
+ * the forest changes.  0 for kernels without a count.  Synchronises. */
+int geoflood_profile_cells(geoflood_ctx* ctx, const char* kernel, long long* cells);
+
 /* Work counters of a scenario since the context was created: interior cell
  * updates computed by the patch step (rejected steps included) and how many
  * of them were wet (h > drytol) at the start of the step. */
@@ -508,6 +515,10 @@ typedef struct {
   long long regrids;      /* regrids done */
   long long miss_regrids; /* of which triggered by a miss */
   long long samples;      /* dataset size after the run (COLLECT) */
+  /* host wall-clock seconds, each including the waits for the device work
+   * it issued: in geoflood_step, in the criterion checks, in the regrids,
+   * and, of the regrids' time, in the host quadtree (new leaf lists) */
+  double step_s, check_s, regrid_s, regrid_host_s;
 } geoflood_advance_stats;
 int geoflood_advance(geoflood_ctx* ctx, double t_target, int regrid_interval,
                      int check_interval, int mode, geoflood_advance_stats* out);

@@ -1165,6 +1165,56 @@ struct FeatScale {
   float s[4];
 };
 
+// Composite value at cell (I, J) of level L next to a patch of that level.
+// In a 2:1 balanced forest the leaf holding such a cell is almost always of
+// level L, L - 1 or L + 1, so those are looked up first (one or two lookups
+// instead of value_at's walk down to level 0 before it tries finer leaves);
+// anything else goes to value_at.  The leaf holding a cell is unique, so the
+// result is value_at's, computed with the same operations.
+template <typename T>
+__device__ void value_near(const Geo<T>& e, int s, int L, long long I, long long J,
+                           double (&out)[4], int* err) {
+  for (int l = L; l >= L - 1 && l >= 0; --l) {
+    const long long Il = I >> (L - l), Jl = J >> (L - l);
+    const int p = e.leaf(s, l, Il, Jl);
+    if (p >= 0) {
+      const GfPatch P = e.V.patch[p];
+      const int c = e.tix((int)(Il - (long long)P.px * e.G.M),
+                          (int)(Jl - (long long)P.py * e.G.M));
+      e.load_now(p, c, out);
+      return;
+    }
+  }
+  if (L + 1 <= e.G.maxlevel) {
+    int pc[4];
+    bool all = true;
+    for (int ch = 0; ch < 4; ++ch) {
+      pc[ch] = e.leaf(s, L + 1, 2 * I + (ch & 1), 2 * J + (ch >> 1));
+      all = all && pc[ch] >= 0;
+    }
+    if (all) {
+      double v[4][4];
+      for (int ch = 0; ch < 4; ++ch) {
+        const long long Ic = 2 * I + (ch & 1), Jc = 2 * J + (ch >> 1);
+        const GfPatch P = e.V.patch[pc[ch]];
+        const int c = e.tix((int)(Ic - (long long)P.px * e.G.M),
+                            (int)(Jc - (long long)P.py * e.G.M));
+        e.load_now(pc[ch], c, v[ch]);
+      }
+      for (int f = 0; f < 4; ++f)
+        out[f] = 0.25 * ((v[0][f] + v[1][f]) + (v[2][f] + v[3][f]));
+      return;
+    }
+  }
+  value_at(e, s, L, I, J, out, err);
+}
+
+__device__ __forceinline__ double warp_sum_f64(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 template <typename T>
 __global__ void k_cnn_features(const __grid_constant__ GfGeom G,
                                const __grid_constant__ GfView V, int first,
@@ -1194,32 +1244,7 @@ __global__ void k_cnn_features(const __grid_constant__ GfGeom G,
   const long long NX = e.nx(P.level), NY = e.ny(P.level);
   const long long I0 = (long long)P.px * M, J0 = (long long)P.py * M;
   int err = 0;
-  for (int px = threadIdx.x; px < 324; px += blockDim.x) {
-    const int Y = px / 18, X = px % 18;
-    // cell range [i0, i1) x [j0, j1) of the pixel, patch-relative
-    const int i0 = X == 0 ? -W : X == 17 ? M : (X - 1) * f;
-    const int i1 = X == 0 ? 0 : X == 17 ? M + W : X * f;
-    const int j0 = Y == 0 ? -W : Y == 17 ? M : (Y - 1) * f;
-    const int j1 = Y == 0 ? 0 : Y == 17 ? M + W : Y * f;
-    const bool inner = X >= 1 && X <= 16 && Y >= 1 && Y <= 16;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    int cnt = 0;
-    for (int j = j0; j < j1; ++j)
-      for (int i = i0; i < i1; ++i) {
-        double c4[4];
-        if (inner) {
-          e.load(p, cur, e.tix(i, j), c4);
-        } else {
-          const long long I = I0 + i, J = J0 + j;
-          if (I < 0 || J < 0 || I >= NX || J >= NY) continue;
-          value_at(e, P.scen, P.level, I, J, c4, &err);
-        }
-        acc[0] += c4[0];
-        acc[1] += c4[1];
-        acc[2] += c4[2];
-        acc[3] += c4[3];
-        ++cnt;
-      }
+  auto emit = [&](int X, int Y, const double (&acc)[4], int cnt) {
     float v[4] = {0.f, 0.f, 0.f, 0.f};
     if (cnt > 0) {
       const double inv = 1.0 / (double)cnt;
@@ -1228,10 +1253,51 @@ __global__ void k_cnn_features(const __grid_constant__ GfGeom G,
       v[2] = (float)(acc[2] * inv / (double)sc.s[2]);
       v[3] = (float)((acc[3] * inv - bmean) / (double)sc.s[3]);
     }
-    __nv_bfloat16* op = o + px * 16;
+    __nv_bfloat16* op = o + (Y * 18 + X) * 16;
     for (int c = 0; c < 4; ++c) op[c] = __float2bfloat16_rn(v[c]);
     op[4] = __float2bfloat16_rn(0.25f * (float)P.level);
     for (int c = 5; c < 16; ++c) op[c] = __float2bfloat16_rn(0.f);
+  };
+  // inner pixels: one thread each, f x f cells of the patch's own tile
+  for (int q = threadIdx.x; q < 256; q += blockDim.x) {
+    const int X = q % 16 + 1, Y = q / 16 + 1;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int j = (Y - 1) * f; j < Y * f; ++j)
+      for (int i = (X - 1) * f; i < X * f; ++i) {
+        double c4[4];
+        e.load(p, cur, e.tix(i, j), c4);
+        for (int c = 0; c < 4; ++c) acc[c] += c4[c];
+      }
+    emit(X, Y, acc, f * f);
+  }
+  // ring pixels: one warp each; the lanes share the band's cells (f x M/2
+  // beside an edge, M/2 x M/2 at a corner), read from whichever leaves
+  // cover them, and sum them with a warp reduction
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int r = warp; r < 68; r += nwarp) {
+    int X, Y;
+    if (r < 18) { X = r; Y = 0; }
+    else if (r < 36) { X = r - 18; Y = 17; }
+    else if (r < 52) { X = 0; Y = r - 36 + 1; }
+    else { X = 17; Y = r - 52 + 1; }
+    const int i0 = X == 0 ? -W : X == 17 ? M : (X - 1) * f;
+    const int i1 = X == 0 ? 0 : X == 17 ? M + W : X * f;
+    const int j0 = Y == 0 ? -W : Y == 17 ? M : (Y - 1) * f;
+    const int j1 = Y == 0 ? 0 : Y == 17 ? M + W : Y * f;
+    const int wi = i1 - i0, ncell = wi * (j1 - j0);
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    int cnt = 0;
+    for (int k = lane; k < ncell; k += 32) {
+      const long long I = I0 + i0 + k % wi, J = J0 + j0 + k / wi;
+      if (I < 0 || J < 0 || I >= NX || J >= NY) continue;
+      double c4[4];
+      value_near(e, P.scen, P.level, I, J, c4, &err);
+      for (int c = 0; c < 4; ++c) acc[c] += c4[c];
+      ++cnt;
+    }
+    for (int c = 0; c < 4; ++c) acc[c] = warp_sum_f64(acc[c]);
+    cnt = __reduce_add_sync(0xffffffffu, cnt);
+    if (lane == 0) emit(X, Y, acc, cnt);
   }
 }
 

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -23,6 +24,7 @@ namespace {
 
 struct ProfRec {
   cudaEvent_t a, b;
+  long long cells = 0;  // interior cells of the launch (patch step)
 };
 
 // Device state of the learned refinement predictor.
@@ -131,10 +133,20 @@ struct geoflood_ctx {
   std::map<std::string, std::vector<ProfRec>> prof_recs;
   std::map<std::string, double> prof_ms;
   std::map<std::string, long long> prof_n;
+  std::map<std::string, long long> prof_cells;
   std::vector<cudaEvent_t> pool;
   size_t pool_used = 0;
   long long launches = 0;
   long long generation = 0;  // bumped by every regrid
+  double regrid_host_s = 0;  // host wall time of the quadtree regrids so far
+  // pinned staging of host-built tables: uploads read it asynchronously; the
+  // event marks when the last upload from it has been consumed
+  unsigned char* h_up = nullptr;
+  size_t h_up_cap = 0, h_up_used = 0;
+  cudaEvent_t up_ev = nullptr;
+  bool up_pending = false;
+  uint8_t* h_flags = nullptr;  // pinned copy of the tags for the host quadtree
+  size_t h_flags_cap = 0;
   CnnState cnn;
 };
 
@@ -244,10 +256,72 @@ int ensure_stage(geoflood_ctx* ctx, size_t doubles) {
   return 0;
 }
 
+// Start a batch of uploads of at most `bytes` through the pinned staging
+// buffer: waits until the previous batch has been consumed, grows the buffer
+// if needed.
+int upload_begin(geoflood_ctx* ctx, size_t bytes) {
+  if (ctx->up_pending) {
+    CK(cudaEventSynchronize(ctx->up_ev));
+    ctx->up_pending = false;
+  }
+  if (!ctx->up_ev) CK(cudaEventCreateWithFlags(&ctx->up_ev, cudaEventDisableTiming));
+  if (bytes > ctx->h_up_cap) {
+    if (ctx->h_up) cudaFreeHost(ctx->h_up);
+    ctx->h_up = nullptr;
+    ctx->h_up_cap = 0;
+    const size_t cap = bytes + bytes / 2 + 4096;
+    if (cudaMallocHost((void**)&ctx->h_up, cap) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->h_up = nullptr;
+      return fail(ctx, GEOFLOOD_ERR_OOM, "pinned staging buffer");
+    }
+    ctx->h_up_cap = cap;
+  }
+  ctx->h_up_used = 0;
+  return 0;
+}
+
+// Copy `bytes` from host memory into the staging buffer and enqueue their
+// transfer to the device address dst on the context's stream.
+int upload_put(geoflood_ctx* ctx, void* dst, const void* src, size_t bytes) {
+  if (!bytes) return 0;
+  const size_t at = (ctx->h_up_used + 255) & ~size_t(255);
+  if (at + bytes > ctx->h_up_cap) return fail(ctx, GEOFLOOD_ERR_STATE, "staging overflow");
+  std::memcpy(ctx->h_up + at, src, bytes);
+  CK(cudaMemcpyAsync(dst, ctx->h_up + at, bytes, cudaMemcpyHostToDevice, ctx->st));
+  ctx->h_up_used = at + bytes;
+  return 0;
+}
+
+// Close the batch: the buffer may be reused once the stream has passed here.
+int upload_end(geoflood_ctx* ctx) {
+  CK(cudaEventRecord(ctx->up_ev, ctx->st));
+  ctx->up_pending = true;
+  return 0;
+}
+
+// Room a batch of uploads needs: the bytes plus the alignment of each piece.
+size_t upload_room(std::initializer_list<size_t> sizes) {
+  size_t t = 0;
+  for (size_t b : sizes) t += b + 256;
+  return t;
+}
+
+// Staging room that upload_tables needs for `total` patches (an upper bound:
+// neighbour table, ghost regions, inflow list, launch order, patch table,
+// lookup tables, scenarios).
+size_t tables_room(const geoflood_ctx* ctx, size_t total) {
+  return upload_room({sizeof(int) * 8 * total, sizeof(int) * 8 * total, sizeof(int) * total,
+                      sizeof(int) * total, sizeof(GfPatch) * total,
+                      sizeof(int) * (size_t)ctx->nscen * ctx->G.lut_per_scen,
+                      sizeof(GfScenario) * ctx->nscen});
+}
+
 // Upload the patch table and lookup tables of the current forests into
-// table slot t; updates poff/pcount of every scenario.
+// table slot t; updates poff/pcount of every scenario.  The uploads are
+// asynchronous (staged in pinned memory).
 int upload_tables(geoflood_ctx* ctx, int t,
-                  const std::vector<std::vector<gf::Leaf>>& lv) {
+                  const std::vector<std::vector<gf::Leaf>>& lv, bool batch_open = false) {
   size_t total = 0;
   for (auto& v : lv) total += v.size();
   if ((long long)total > ctx->cap)
@@ -286,8 +360,6 @@ int upload_tables(geoflood_ctx* ctx, int t,
       nb[k * 8 + r] = q >= 0 ? q : GF_NBR_OTHER;
     }
   }
-  CK(cudaMemcpyAsync(ctx->d_nbr[t], nb.data(), sizeof(int) * nb.size(),
-                     cudaMemcpyHostToDevice, ctx->st));
   // ghost regions that no same-level neighbour pushes into (a finer or
   // coarser neighbour), as patch * 8 + region: filled after each step
   std::vector<int> gl;
@@ -295,9 +367,6 @@ int upload_tables(geoflood_ctx* ctx, int t,
     for (int r = 0; r < 8; ++r)
       if (nb[k * 8 + r] == GF_NBR_OTHER) gl.push_back((int)k * 8 + r);
   ctx->nglist[t] = (int)gl.size();
-  if (!gl.empty())
-    CK(cudaMemcpyAsync(ctx->d_glist[t], gl.data(), sizeof(int) * gl.size(),
-                       cudaMemcpyHostToDevice, ctx->st));
   // patches on the inflow side whose tile lines (ghost lines included) may
   // reach the inflow segment
   std::vector<int> il;
@@ -320,31 +389,29 @@ int upload_tables(geoflood_ctx* ctx, int t,
     }
   }
   ctx->nilist[t] = (int)il.size();
-  if (!il.empty())
-    CK(cudaMemcpyAsync(ctx->d_ilist[t], il.data(), sizeof(int) * il.size(),
-                       cudaMemcpyHostToDevice, ctx->st));
   // a new patch list: launch order back to patch order, no tile known to
   // agree between the buffers
   std::vector<int> iota(total);
   for (size_t k = 0; k < total; ++k) iota[k] = (int)k;
-  CK(cudaMemcpyAsync(ctx->d_ord[0], iota.data(), sizeof(int) * total,
-                     cudaMemcpyHostToDevice, ctx->st));
-  CK(cudaMemcpyAsync(ctx->d_ord[1], iota.data(), sizeof(int) * total,
-                     cudaMemcpyHostToDevice, ctx->st));
+  int rc = batch_open ? 0
+                      : upload_begin(ctx, tables_room(ctx, total));
+  if (rc) return rc;
+  rc |= upload_put(ctx, ctx->d_nbr[t], nb.data(), sizeof(int) * nb.size());
+  rc |= upload_put(ctx, ctx->d_glist[t], gl.data(), sizeof(int) * gl.size());
+  rc |= upload_put(ctx, ctx->d_ilist[t], il.data(), sizeof(int) * il.size());
+  rc |= upload_put(ctx, ctx->d_ord[0], iota.data(), sizeof(int) * total);
+  CK(cudaMemcpyAsync(ctx->d_ord[1], ctx->d_ord[0], sizeof(int) * total,
+                     cudaMemcpyDeviceToDevice, ctx->st));
   CK(cudaMemsetAsync(ctx->d_sched, 0, 8 * sizeof(unsigned), ctx->st));
   CK(cudaMemsetAsync(ctx->d_same, 0, (size_t)ctx->cap * 4, ctx->st));
   CK(cudaMemsetAsync(ctx->d_pwet, 0, (size_t)ctx->cap * sizeof(unsigned), ctx->st));
   CK(cudaMemsetAsync(ctx->d_gflag, 0, (size_t)ctx->cap, ctx->st));
   CK(cudaMemsetAsync(ctx->d_pcnt, 0, (size_t)ctx->cap * sizeof(unsigned), ctx->st));
-  CK(cudaMemcpyAsync(ctx->d_patch[t], hp.data(), sizeof(GfPatch) * total,
-                     cudaMemcpyHostToDevice, ctx->st));
-  CK(cudaMemcpyAsync(ctx->d_lut[t], lut.data(), sizeof(int) * lut.size(),
-                     cudaMemcpyHostToDevice, ctx->st));
-  CK(cudaMemcpyAsync(ctx->d_scen, ctx->h_scen.data(),
-                     sizeof(GfScenario) * ctx->nscen, cudaMemcpyHostToDevice,
-                     ctx->st));
-  CK(cudaStreamSynchronize(ctx->st));  // host vectors die at return
-  return 0;
+  rc |= upload_put(ctx, ctx->d_patch[t], hp.data(), sizeof(GfPatch) * total);
+  rc |= upload_put(ctx, ctx->d_lut[t], lut.data(), sizeof(int) * lut.size());
+  rc |= upload_put(ctx, ctx->d_scen, ctx->h_scen.data(), sizeof(GfScenario) * ctx->nscen);
+  if (rc) return rc;
+  return batch_open ? 0 : upload_end(ctx);
 }
 
 int upload_scen(geoflood_ctx* ctx) {
@@ -772,6 +839,10 @@ void geoflood_destroy(geoflood_ctx* ctx) {
   for (auto p : ctx->d_garr) cudaFree(p);
   for (auto p : ctx->d_gref) cudaFree(p);
   if (ctx->h_ctl) cudaFreeHost(ctx->h_ctl);
+  if (ctx->up_pending) cudaEventSynchronize(ctx->up_ev);
+  if (ctx->h_up) cudaFreeHost(ctx->h_up);
+  if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
+  if (ctx->up_ev) cudaEventDestroy(ctx->up_ev);
   if (ctx->own_stream) cudaStreamDestroy(ctx->st);
   for (auto e : ctx->pool) cudaEventDestroy(e);
   CnnState& n = ctx->cnn;
@@ -1082,6 +1153,7 @@ int geoflood_step(geoflood_ctx* ctx, double t_target, int max_steps,
                          : gf::launch_patch_step_f64(ctx->G, v, ctx->variant, ctx->st);
         if (sample) {
           cudaEventRecordWithFlags(r.b, ctx->st, cudaEventRecordExternal);
+          r.cells = (long long)ctx->npatch * ctx->G.M * ctx->G.M;
           gr->ev.push_back(r);
           cudaEventRecordWithFlags(rg.a, ctx->st, cudaEventRecordExternal);
         }
@@ -1143,6 +1215,7 @@ int geoflood_step(geoflood_ctx* ctx, double t_target, int max_steps,
         CK(cudaEventElapsedTime(&ms, r.a, r.b));
         ctx->prof_ms["patch_step"] += ms;
         ctx->prof_n["patch_step"] += 1;
+        ctx->prof_cells["patch_step"] += r.cells;
       }
       for (auto& r : gr->evg) {
         float ms = 0.f;
@@ -1193,9 +1266,20 @@ int geoflood_regrid(geoflood_ctx* ctx) {
   if (!ctx) return GEOFLOOD_ERR_ARG;
   int rc = sync_ctl_down(ctx);
   if (rc) return rc;
-  std::vector<uint8_t> flags(ctx->npatch);
+  if ((size_t)ctx->npatch > ctx->h_flags_cap) {
+    if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
+    ctx->h_flags = nullptr;
+    ctx->h_flags_cap = 0;
+    if (cudaMallocHost((void**)&ctx->h_flags, (size_t)ctx->cap) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->h_flags = nullptr;
+      return fail(ctx, GEOFLOOD_ERR_OOM, "pinned tag buffer");
+    }
+    ctx->h_flags_cap = (size_t)ctx->cap;
+  }
+  const uint8_t* flags_h = ctx->h_flags;
   if ((rc = tag_pass(ctx, ctx->cnn.tagger == GEOFLOOD_TAGGER_LEARNED, nullptr))) return rc;
-  CK(cudaMemcpyAsync(flags.data(), ctx->d_flags, ctx->npatch, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, ctx->npatch, cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
   // New forests, scenario by scenario (on several host threads when there
   // are many scenarios); a leaf present in both forests keeps its data
@@ -1204,28 +1288,34 @@ int geoflood_regrid(geoflood_ctx* ctx) {
   std::vector<std::vector<int>> fresh_s(ctx->nscen), keep_s(ctx->nscen);
   std::vector<char> changed(ctx->nscen, 0);
   auto regrid_one = [&](int s) {
-    const std::vector<gf::Leaf>& old = ctx->forests[s].leaves();
-    std::unordered_map<uint64_t, int> old_index;
-    old_index.reserve(old.size() * 2);
-    auto kk = [](const gf::Leaf& l) {
-      return ((uint64_t)l.level << 58) | ((uint64_t)l.px << 29) | (uint64_t)l.py;
-    };
-    for (size_t k = 0; k < old.size(); ++k) old_index[kk(old[k])] = (int)k;
-    lv[s] = ctx->forests[s].regrid(flags.data() + ctx->h_scen[s].poff);
+    const gf::HostForest& F = ctx->forests[s];
+    const std::vector<gf::Leaf>& old = F.leaves();
+    lv[s] = F.regrid(flags_h + ctx->h_scen[s].poff);
+    // Both leaf lists are in Morton order of their lower-left corners, and
+    // the leaves of one forest have distinct corners, so one merge pass
+    // finds the leaves present in both (same corner and level).
     bool same = lv[s].size() == old.size();
+    size_t o = 0;
+    uint64_t ko = o < old.size() ? F.morton(old[o]) : ~0ull;
     for (size_t k = 0; k < lv[s].size(); ++k) {
-      auto it = old_index.find(kk(lv[s][k]));
-      if (it == old_index.end()) {
+      const gf::Leaf& l = lv[s][k];
+      const uint64_t kn = F.morton(l);
+      while (ko < kn) {
+        ++o;
+        ko = o < old.size() ? F.morton(old[o]) : ~0ull;
+      }
+      if (ko == kn && old[o].level == l.level) {
+        keep_s[s].push_back((int)k);
+        keep_s[s].push_back(ctx->h_scen[s].poff + (int)o);
+        same = same && o == k;
+      } else {
         fresh_s[s].push_back((int)k);
         same = false;
-      } else {
-        keep_s[s].push_back((int)k);
-        keep_s[s].push_back(ctx->h_scen[s].poff + it->second);
-        same = same && it->second == (int)k;
       }
     }
     changed[s] = same ? 0 : 1;
   };
+  const auto t_host = std::chrono::steady_clock::now();
   const int nthreads = std::min(ctx->nscen, std::max(1, std::min(16, (int)std::thread::hardware_concurrency())));
   if (nthreads <= 1) {
     for (int s = 0; s < ctx->nscen; ++s) regrid_one(s);
@@ -1237,6 +1327,8 @@ int geoflood_regrid(geoflood_ctx* ctx) {
       });
     for (auto& th : pool) th.join();
   }
+  ctx->regrid_host_s +=
+      std::chrono::duration<double>(std::chrono::steady_clock::now() - t_host).count();
   // nothing to do when no forest changed (the tables and graphs stay)
   bool any_change = false;
   for (int s = 0; s < ctx->nscen; ++s) any_change |= changed[s] != 0;
@@ -1281,7 +1373,14 @@ int geoflood_regrid(geoflood_ctx* ctx) {
   const GfView oldv = view(ctx);
   std::vector<GfScenario> saved = ctx->h_scen;
   const int nt = ctx->tsel ^ 1, nb = ctx->bsel ^ 1;
-  if ((rc = upload_tables(ctx, nt, lv))) {
+  // one staging batch for the tables, the regrid lists and the controllers
+  if ((rc = upload_begin(ctx, tables_room(ctx, total) +
+                                  upload_room({sizeof(int) * fresh.size(),
+                                               sizeof(int) * keep.size(),
+                                               sizeof(GfCtl) * ctx->nscen}))))
+    return rc;
+  if ((rc = upload_tables(ctx, nt, lv, true))) {
+    upload_end(ctx);
     ctx->h_scen = saved;
     upload_scen(ctx);
     return rc;
@@ -1289,23 +1388,23 @@ int geoflood_regrid(geoflood_ctx* ctx) {
   GfView newv = view(ctx, nt, nb);
   newv.npatch = (int)total;
   const int nfresh = (int)fresh.size(), nkeep = (int)keep.size() / 2;
-  if (nfresh)
-    CK(cudaMemcpyAsync(ctx->d_rlist, fresh.data(), sizeof(int) * fresh.size(),
-                       cudaMemcpyHostToDevice, ctx->st));
-  if (nkeep)
-    CK(cudaMemcpyAsync(ctx->d_rpairs, keep.data(), sizeof(int) * keep.size(),
-                       cudaMemcpyHostToDevice, ctx->st));
+  rc |= upload_put(ctx, ctx->d_rlist, fresh.data(), sizeof(int) * fresh.size());
+  rc |= upload_put(ctx, ctx->d_rpairs, keep.data(), sizeof(int) * keep.size());
+  if (rc) return rc;
   CKL(gf::launch_topo(ctx->G, newv, 0, nfresh, ctx->st, ctx->d_rlist), "topo");
   gf::set_errflag(ctx->d_err);
   CKL(gf::launch_regrid_fill(ctx->G, oldv, newv, ctx->st, ctx->d_rlist, nfresh), "regrid_fill");
   CKL(gf::launch_regrid_keep(ctx->G, oldv, newv, ctx->d_rpairs, nkeep, ctx->st), "regrid_keep");
   ctx->launches += 3;
-  CK(cudaStreamSynchronize(ctx->st));
+  // the controllers after the regrid (stream-ordered behind the fills,
+  // which read the old current buffer)
   for (int s = 0; s < ctx->nscen; ++s) {
     ctx->h_ctl[s].cur ^= 1;
     ctx->h_ctl[s].accepted = 0;  // gauges sample step results only
     ctx->forests[s].set_leaves(lv[s]);
   }
+  if ((rc = upload_put(ctx, ctx->d_ctl, ctx->h_ctl, sizeof(GfCtl) * ctx->nscen))) return rc;
+  if ((rc = upload_end(ctx))) return rc;
   ctx->tsel = nt;
   ctx->bsel = nb;
   ctx->npatch = (int)total;
@@ -1314,8 +1413,8 @@ int geoflood_regrid(geoflood_ctx* ctx) {
     CKL(gf::launch_gauge_refs(ctx->G, view(ctx), ctx->max_gauges_used, ctx->st), "gauge_refs");
     ctx->launches++;
   }
-  if ((rc = sync_ctl_up(ctx))) return rc;
-  if ((rc = check_errflag(ctx))) return rc;
+  // one wait for the whole regrid: the ghost fill ends by reading the
+  // lookup-error flag, which the fills above also set
   return ghost_fill_all(ctx);
 }
 
@@ -1388,6 +1487,7 @@ int geoflood_profile(geoflood_ctx* ctx, int enable) {
   ctx->prof_recs.clear();
   ctx->prof_ms.clear();
   ctx->prof_n.clear();
+  ctx->prof_cells.clear();
   for (auto& gr : ctx->graphs) {  // their events come from the pool
     if (gr.exec) cudaGraphExecDestroy(gr.exec);
     gr.exec = nullptr;
@@ -1416,6 +1516,13 @@ int geoflood_profile_read(geoflood_ctx* ctx, const char* kernel,
     }
   if (total_ms) *total_ms = tot;
   if (launches) *launches = n;
+  return 0;
+}
+
+int geoflood_profile_cells(geoflood_ctx* ctx, const char* kernel, long long* cells) {
+  if (!ctx || !kernel || !cells) return GEOFLOOD_ERR_ARG;
+  CK(cudaStreamSynchronize(ctx->st));
+  *cells = ctx->prof_cells.count(kernel) ? ctx->prof_cells[kernel] : 0;
   return 0;
 }
 
@@ -1744,10 +1851,18 @@ int geoflood_advance(geoflood_ctx* ctx, double t_target, int regrid_interval,
   std::vector<double> t(ctx->nscen);
   std::vector<int> n(ctx->nscen);
   int since = 0;
+  using clock = std::chrono::steady_clock;
+  auto secs = [](clock::time_point a) {
+    return std::chrono::duration<double>(clock::now() - a).count();
+  };
+  const double host0 = ctx->regrid_host_s;
   for (;;) {
     const int want = std::min(check_interval, regrid_interval - since);
     const int np = ctx->npatch;
-    if ((rc = geoflood_step(ctx, t_target, want, t.data(), n.data()))) return rc;
+    auto t0 = clock::now();
+    rc = geoflood_step(ctx, t_target, want, t.data(), n.data());
+    st.step_s += secs(t0);
+    if (rc) return rc;
     int taken = 0;
     bool done = true;
     for (int s = 0; s < ctx->nscen; ++s) {
@@ -1761,7 +1876,10 @@ int geoflood_advance(geoflood_ctx* ctx, double t_target, int regrid_interval,
     if (taken == 0) return fail(ctx, GEOFLOOD_ERR_STATE, "advance: no progress");
     // the plain criterion judges at every check
     int misses = 0;
-    if ((rc = geoflood_check_tags(ctx, collect ? 1 : 0, &misses))) return rc;
+    t0 = clock::now();
+    rc = geoflood_check_tags(ctx, collect ? 1 : 0, &misses);
+    st.check_s += secs(t0);
+    if (rc) return rc;
     st.checks++;
     st.misses += misses;
     const bool due = since >= regrid_interval;
@@ -1771,7 +1889,10 @@ int geoflood_advance(geoflood_ctx* ctx, double t_target, int regrid_interval,
         if ((rc = geoflood_cnn_commit(ctx, &total, nullptr))) return rc;
         st.samples = total;
       }
-      if ((rc = geoflood_regrid(ctx))) return rc;
+      t0 = clock::now();
+      rc = geoflood_regrid(ctx);
+      st.regrid_s += secs(t0);
+      if (rc) return rc;
       st.regrids++;
       if (!due) st.miss_regrids++;
       since = 0;
@@ -1779,6 +1900,7 @@ int geoflood_advance(geoflood_ctx* ctx, double t_target, int regrid_interval,
     }
   }
   if (collect) ctx->cnn.pend_n = -1;
+  st.regrid_host_s = ctx->regrid_host_s - host0;
   if (out) *out = st;
   return 0;
 }

@@ -15,17 +15,38 @@ inline uint64_t key(int L, long long x, long long y) {
   return ((uint64_t)L << 58) | ((uint64_t)x << 29) | (uint64_t)y;
 }
 
+// The set of tree nodes (leaves and their ancestors).  A dense bit map per
+// level when the levels' patch grids are small enough (every lookup is one
+// load), else a hash set.
 class NodeSet {
  public:
-  NodeSet(int mi, int mj) : mi_(mi), mj_(mj) {}
+  NodeSet(int mi, int mj, int maxl) : mi_(mi), mj_(mj) {
+    size_t total = 0;
+    for (int l = 0; l <= maxl; ++l) total += ((size_t)mi << l) * ((size_t)mj << l);
+    dense_ = total <= kDenseLimit;
+    if (dense_) {
+      off_.resize(maxl + 2, 0);
+      for (int l = 0; l <= maxl; ++l)
+        off_[l + 1] = off_[l] + ((size_t)mi << l) * ((size_t)mj << l);
+      bits_.assign(total, 0);
+    }
+  }
   void add_leaf(int L, int x, int y) {
     for (int l = L; l >= 0; --l) {
-      if (!s_.insert(key(l, x >> (L - l), y >> (L - l))).second) break;
+      const long long xl = x >> (L - l), yl = y >> (L - l);
+      if (dense_) {
+        uint8_t& b = bits_[index(l, xl, yl)];
+        if (b) break;
+        b = 1;
+      } else if (!s_.insert(key(l, xl, yl)).second) {
+        break;
+      }
     }
   }
   bool has(int L, long long x, long long y) const {
     if (x < 0 || y < 0 || x >= ((long long)mi_ << L) || y >= ((long long)mj_ << L))
       return false;
+    if (dense_) return bits_[index(L, x, y)] != 0;
     return s_.count(key(L, x, y)) != 0;
   }
   // any node of level Lr in the one-position ring around the square
@@ -41,27 +62,49 @@ class NodeSet {
   }
 
  private:
+  static constexpr size_t kDenseLimit = size_t(1) << 26;  // 64 MB of flags
+  size_t index(int L, long long x, long long y) const {
+    return off_[L] + (size_t)y * ((size_t)mi_ << L) + (size_t)x;
+  }
   int mi_, mj_;
+  bool dense_ = false;
+  std::vector<size_t> off_;
+  std::vector<uint8_t> bits_;
   std::unordered_set<uint64_t> s_;
 };
+
+}  // namespace
+
+namespace {
+
+// Spread the low 32 bits of v to the even bit positions (bit b -> 2b).
+inline uint64_t spread_bits(uint64_t v) {
+  v &= 0xffffffffull;
+  v = (v | (v << 16)) & 0x0000ffff0000ffffull;
+  v = (v | (v << 8)) & 0x00ff00ff00ff00ffull;
+  v = (v | (v << 4)) & 0x0f0f0f0f0f0f0f0full;
+  v = (v | (v << 2)) & 0x3333333333333333ull;
+  v = (v | (v << 1)) & 0x5555555555555555ull;
+  return v;
+}
 
 }  // namespace
 
 uint64_t HostForest::morton(const Leaf& l) const {
   const uint64_t X = (uint64_t)l.px << (maxl_ - l.level);
   const uint64_t Y = (uint64_t)l.py << (maxl_ - l.level);
-  uint64_t k = 0;
-  for (int b = 0; b < 31; ++b) {
-    k |= ((X >> b) & 1ull) << (2 * b);
-    k |= ((Y >> b) & 1ull) << (2 * b + 1);
-  }
-  return k;
+  return spread_bits(X) | (spread_bits(Y) << 1);
 }
 
 void HostForest::sort(std::vector<Leaf>& v) const {
-  std::sort(v.begin(), v.end(), [this](const Leaf& a, const Leaf& b) {
-    return morton(a) < morton(b);
+  // keys computed once per leaf, then sorted with their leaves
+  std::vector<std::pair<uint64_t, Leaf>> kv(v.size());
+  for (size_t k = 0; k < v.size(); ++k) kv[k] = {morton(v[k]), v[k]};
+  std::sort(kv.begin(), kv.end(), [](const std::pair<uint64_t, Leaf>& a,
+                                     const std::pair<uint64_t, Leaf>& b) {
+    return a.first < b.first;
   });
+  for (size_t k = 0; k < v.size(); ++k) v[k] = kv[k].second;
 }
 
 void HostForest::uniform(int level) {
@@ -91,7 +134,7 @@ std::vector<Leaf> HostForest::regrid(const uint8_t* flags) const {
     }
   }
   // 2. balance: refine leaves that touch a leaf two or more levels finer
-  NodeSet nodes(mi_, mj_);
+  NodeSet nodes(mi_, mj_, maxl_);
   for (const Leaf& l : cur) nodes.add_leaf(l.level, l.px, l.py);
   for (bool changed = true; changed;) {
     changed = false;

@@ -63,7 +63,8 @@ class _Cfg(C.Structure):
 
 class AdvanceStats(C.Structure):
     _fields_ = [(n, C.c_longlong) for n in ("steps", "patch_steps", "checks", "misses",
-                                             "regrids", "miss_regrids", "samples")]
+                                             "regrids", "miss_regrids", "samples")] + \
+        [(n, C.c_double) for n in ("step_s", "check_s", "regrid_s", "regrid_host_s")]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -119,6 +120,7 @@ def lib():
                 "geoflood_gauges": [vp, ip, dp, dp],
                 "geoflood_profile": [vp, ip],
                 "geoflood_profile_read": [vp, C.c_char_p, dp, ll],
+                "geoflood_profile_cells": [vp, C.c_char_p, ll],
                 "geoflood_launch_count": [vp, ll],
                 "geoflood_counters": [vp, ip, ll, ll],
                 "geoflood_autotune": [vp, ip, pi, dp],
@@ -375,6 +377,12 @@ class Forest:
         n = C.c_longlong()
         self._check(lib().geoflood_profile_read(self._h, kernel.encode(), C.byref(ms), C.byref(n)))
         return ms.value, n.value
+
+    def profile_cells(self, kernel):
+        """Interior cells covered by the recorded launches of a kernel."""
+        n = C.c_longlong()
+        self._check(lib().geoflood_profile_cells(self._h, kernel.encode(), C.byref(n)))
+        return n.value
 
     def counters(self, s=0):
         a, b = C.c_longlong(), C.c_longlong()

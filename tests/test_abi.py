@@ -46,3 +46,20 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(geoflood, "_lib", None)
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         geoflood.lib()
+
+
+def test_advance_stats_struct_matches_header():
+    """The binding's advance statistics have the header's fields, in order
+    and with the header's types (counts as long long, times as double)."""
+    import re
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "geoflood.h")).read()
+    end = hdr.index("} geoflood_advance_stats;")
+    body = hdr[hdr.rindex("typedef struct {", 0, end):end]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = []
+    for decl in body.split(";"):
+        m = re.match(r"\s*(long long|double)\s+(.*)", decl.replace("typedef struct {", ""))
+        if m:
+            fields += [(n.strip(), m.group(1)) for n in m.group(2).split(",")]
+    ctype = {"long long": ctypes.c_longlong, "double": ctypes.c_double}
+    assert [(n, ctype[t]) for n, t in fields] == list(geoflood.AdvanceStats._fields_)

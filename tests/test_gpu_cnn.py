@@ -66,10 +66,12 @@ def test_features_match_oracle(patch):
     c = prob.cfg
     ref = ocnn.bf16_round(ocnn.features(L, X, Y, *g.read(), c.mi, c.mj, c.mx, SCALE))
     d = np.abs(gpu - ref)
-    assert np.all(d <= ulp_bf16(ref) + 1e-5), d.max()
+    # every feature within one BF16 unit in the last place of the larger of
+    # the two (both round the same FP64 means; only summation order differs)
+    assert np.all(d <= ulp_bf16(np.maximum(np.abs(ref), np.abs(gpu)))), d.max()
     exact = np.mean(d == 0)
     print("features: %d patches, %.4f%% bit-exact" % (len(L), 100 * exact))
-    assert exact >= 0.995
+    assert exact >= 0.999
 
 
 def test_forward_backward_match_oracle():
@@ -90,7 +92,8 @@ def test_forward_backward_match_oracle():
     dz = np.abs(z - f["z"]).max()
     print("logits: max |dz| %.2e vs the BF16-point oracle, %.2e vs exact FP64"
           % (dz, np.abs(z - f_ex["z"]).max()))
-    assert dz <= 1e-3 * max(1.0, np.abs(f["z"]).max())
+    # measured 3.7e-7: FP32 summation order only
+    assert dz <= 1e-5 * max(1.0, np.abs(f["z"]).max())
     assert abs(loss - l_ref) <= 1e-4 * max(1.0, l_ref)
     # per parameter block: relative L2 error of the gradient
     blocks = {"W1": (0, 2304), "b1": (2304, 2320), "W2": (2320, 4624), "b2": (4624, 4640),
@@ -100,7 +103,7 @@ def test_forward_backward_match_oracle():
         err = np.linalg.norm(grad[a:b] - ref) / max(np.linalg.norm(ref), 1e-30)
         err_ex = np.linalg.norm(grad[a:b] - g_ex[a:b]) / max(np.linalg.norm(g_ex[a:b]), 1e-30)
         print("grad %s: rel L2 %.2e (BF16-point oracle), %.2e (exact FP64)" % (name, err, err_ex))
-        assert err <= 1e-2, name
+        assert err <= 1e-4, name  # measured at most 1.4e-6
 
 
 def collect_dataset(prob, t_end, capacity=20000, regrid=16, check=4):
