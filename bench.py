@@ -332,12 +332,16 @@ class ValleyArm:
                 flush.fill_(1.0)
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
+        c0 = f.counters()
         torch.cuda.synchronize()
         a.record(self.stream)
         st = f.advance(self.t_end if t_end is None else t_end, regrid_interval=self.regrid,
                        check_interval=4, regrid_on_miss=self.learned)
         b.record(self.stream)
         torch.cuda.synchronize()
+        c1 = f.counters()
+        st["cell_updates_counted"] = c1[0] - c0[0]
+        st["wet_updates_counted"] = c1[1] - c0[1]
         return st, a.elapsed_time(b) / 1e3
 
     def summary(self, runs):
@@ -411,13 +415,12 @@ def measure_valley(args, dev, stream, world, local, peaks):
     # the patch step's per-launch time: a separate run with every 4th launch
     # of each captured chunk bracketed by events
     head.f.profile(True, every=4)
-    cu0, wet0 = head.f.counters()
-    head.run(flush)
-    cu1, wet1 = head.f.counters()
+    pst, _ = head.run(flush)
     k_ms, k_n = head.f.profile_read("patch_step")
     k_cells = head.f.profile_cells("patch_step")
     head.f.profile(False)
-    prof = {"k_ms": k_ms, "k_n": k_n, "cells": k_cells, "wet": wet1 - wet0, "updates": cu1 - cu0}
+    prof = {"k_ms": k_ms, "k_n": k_n, "cells": k_cells, "wet": pst["wet_updates_counted"],
+            "updates": pst["cell_updates_counted"]}
     traffic = None
     if TRAFFIC_PER_CELL_VALLEY_FP32 is not None and k_n:
         traffic = TRAFFIC_PER_CELL_VALLEY_FP32 * k_cells / k_n
@@ -468,7 +471,8 @@ def measure_valley(args, dev, stream, world, local, peaks):
     for r in (learned, plain64, plain32):
         r.pop("_gauge_h")
         r.pop("_arrival")
-    return dict(value=value, sec=sec_max, runs=len(runs), launches=launches,
+    return dict(net=(net_prm, net_thr), value=value, sec=sec_max, runs=len(runs),
+                launches=launches,
                 clocks=clk.summary(), learned=learned, fp64=plain64, fp32_plain=plain32,
                 err=err, train=train, roofline=roof, e2e=e2e,
                 cells_per_run=cells / max(1, len(runs)))
@@ -567,36 +571,23 @@ def measure_uniform_pair(args, dev, stream, peaks):
 CANYON_T = 20.0
 
 
-def measure_canyon(stream):
+def measure_canyon(stream, net):
     """The 17 km x 9 km canyon-to-plain dam break (55 m reservoir, five
     levels, 32 x 32 patches on levels 0-4), first CANYON_T seconds: FP32 with
-    learned tags (regrid every 16; the network trained on the plain
-    criterion's flags from this workload's own first seconds) against FP32
-    and FP64 with plain tags (regrid every 4).  Wall clock of the driver
-    loop, second of two runs."""
+    learned tags (regrid every 16; the network is the one trained on the
+    plain criterion's flags from valley runs) against FP32 and FP64 with
+    plain tags (regrid every 4).  Wall clock of the driver loop, second of
+    two runs."""
     import numpy as np
     import torch
     from paper_2403_15435_gb300 import geoflood, inputs
 
     cap = 40000
-    scale = (10.0, 20.0, 20.0, 10.0)
-    tr = inputs.canyon_plain(precision=1, seed=inputs.SEED_BASE + 57)
-    f = geoflood.Forest(tr.cfg, tr.dem, max_patches=cap, stream=stream.cuda_stream)
-    f.set_state(tr.ic)
-    f.cnn_set_scale(scale)
-    f.cnn_dataset(100000)
-    st = f.advance(CANYON_T, regrid_interval=16, check_interval=4, collect=True)
-    _, y = f.cnn_dataset_read(0, st["samples"])
-    npos = int(y.sum())
-    pw = float(np.clip((len(y) - npos) / max(npos, 1), 1.0, 20.0))
-    f.cnn_set_params(inputs.cnn_init(3))
-    f.cnn_train(10, 64, lr=2e-3, pos_weight=pw, seed=7)
-    prm = f.cnn_get_params()
-    f.close()
-    thr = pw / (1.0 + pw)
+    scale = CNN_SCALE
+    prm, thr = net
 
     def run(prec, learned, regrid):
-        prob = inputs.canyon_plain(precision=prec)
+        prob = inputs.canyon_plain(precision=prec, near_gauges=16)
         res = None
         for rep in range(2):
             g = geoflood.Forest(prob.cfg, prob.dem, max_patches=cap, stream=stream.cuda_stream)
@@ -637,13 +628,14 @@ def measure_canyon(stream):
         r.pop("_h")
         r.pop("_a")
     return {"workload": "canyon-to-plain 17 km x 9 km, 55 m reservoir, 32x32 patches, levels "
-                        "0-4 (finest dx 1.95 m), 16 gauges on the channel, t 0->%g s" % CANYON_T,
+                        "0-4 (finest dx 1.95 m), 32 gauges on the channel (16 within 2.05-2.8 km "
+                        "of the upstream end), t 0->%g s" % CANYON_T,
             "fp32_learned_regrid16": learned, "fp32_plain_regrid4": plain32,
             "fp64_plain_regrid4": plain64, "error_vs_plain_fp64": err,
             "wall_clock_ratio_vs_fp64": plain64["wall_s"] / learned["wall_s"],
             "network_gain_wall": plain32["wall_s"] / learned["wall_s"],
-            "training": {"samples": int(len(y)), "positives": npos, "threshold": thr,
-                         "data": "plain-criterion flags of another seed of the canyon"},
+            "training": {"threshold": thr,
+                         "data": "the headline's network: plain-criterion flags of valley runs"},
             "timing": "wall clock around the whole driver loop, second of two runs"}
 
 
@@ -889,7 +881,7 @@ def measure_topo(stream):
 # CPU baselines: the oracle as it stands
 # ----------------------------------------------------------------------------
 
-CPU_STEPS = 12
+CPU_STEPS = 20
 
 
 def _oracle_valley(steps):
@@ -923,7 +915,7 @@ def cpu_baseline():
                       "4 (2048 -> ~6000 patches of 32x32), FP64, %.1f s" % (CPU_STEPS, sec)}
 
 
-def cpu_baseline_all_cores(steps=8):
+def cpu_baseline_all_cores(steps=12):
     """The same oracle, unchanged, on every host core at once: one spawned
     process per core, each stepping its own copy of the sample; the sum of
     their rates."""
@@ -998,7 +990,7 @@ def run_ours(args):
     # replicas on several GPUs the headline is what scales)
     single = world == 1 and not args.headline_only
     uniform = measure_uniform_pair(args, dev, stream, peaks) if single else None
-    canyon = measure_canyon(stream) if single else None
+    canyon = measure_canyon(stream, v["net"]) if single else None
     ens = measure_ensemble_full(stream) if single else None
     variants = measure_variants(stream) if single else None
     flood = measure_flood_speed(stream) if single else None

@@ -23,10 +23,19 @@ struct Geo {
   __device__ double dx(int L) const { return (G.xupper - G.xlower) / (double)nx(L); }
   __device__ double dy(int L) const { return (G.yupper - G.ylower) / (double)ny(L); }
   __device__ int tix(int i, int j) const { return (i + GF_NG) + (j + GF_NG) * G.T; }
+  // tile index of cell (I, J) of a level inside the leaf that the level's
+  // lookup table returned for it: that leaf is the patch at (I / M, J / M)
+  // of the level, so the local cell is (I mod M, J mod M) (M = 16 or 32)
+  __device__ int local(long long I, long long J) const {
+    return tix((int)(I & (G.M - 1)), (int)(J & (G.M - 1)));
+  }
   // leaf of level L holding cell (I, J) of that level, or -1
   __device__ int leaf(int s, int L, long long I, long long J) const {
     if (L < 0 || L > G.maxlevel) return -1;
-    const long long P = I >= 0 ? I / G.M : -1, Q = J >= 0 ? J / G.M : -1;
+    // patch sizes are 16 or 32, so the patch index of a non-negative cell
+    // index is a shift (a 64-bit division would be emulated in software)
+    const int sh = G.M == 32 ? 5 : 4;
+    const long long P = I >= 0 ? I >> sh : -1, Q = J >= 0 ? J >> sh : -1;
     const long long w = (long long)G.mi << L, h = (long long)G.mj << L;
     if (P < 0 || Q < 0 || P >= w || Q >= h) return -1;
     return V.lut[V.scen[s].lut_off + G.lut_lev_off[L] + P + Q * w];
@@ -58,6 +67,15 @@ struct Geo {
   // run: its latest state, or for a level between two of its steps the
   // linear interpolation in time of h, hu, hv between the states before and
   // after its latest step
+  // load_now for a patch p of scenario s: without subcycling the latest
+  // buffer is the scenario's current one, read without the patch record
+  __device__ void load_now_s(int p, int s, int c, double (&o)[4]) const {
+    if (!G.subcycle) {
+      load(p, V.ctl[s].cur, c, o);
+      return;
+    }
+    load_now(p, c, o);
+  }
   __device__ void load_now(int p, int c, double (&o)[4]) const {
     const int cb = cur_of(p);
     load(p, cb, c, o);
@@ -103,10 +121,8 @@ __device__ void value_at(const Geo<T>& e, int s, int L, long long I,
     const long long Il = I >> (L - l), Jl = J >> (L - l);
     const int p = e.leaf(s, l, Il, Jl);
     if (p >= 0) {
-      const GfPatch P = e.V.patch[p];
-      const int c = e.tix((int)(Il - (long long)P.px * e.G.M),
-                          (int)(Jl - (long long)P.py * e.G.M));
-      e.load_now(p, c, out);
+      const int c = e.local(Il, Jl);
+      e.load_now_s(p, s, c, out);
       return;
     }
   }
@@ -115,10 +131,8 @@ __device__ void value_at(const Geo<T>& e, int s, int L, long long I,
     const long long Ic = 2 * I + (ch & 1), Jc = 2 * J + (ch >> 1);
     const int p = e.leaf(s, L + 1, Ic, Jc);
     if (p >= 0) {
-      const GfPatch P = e.V.patch[p];
-      const int c = e.tix((int)(Ic - (long long)P.px * e.G.M),
-                          (int)(Jc - (long long)P.py * e.G.M));
-      e.load_now(p, c, v[ch]);
+      const int c = e.local(Ic, Jc);
+      e.load_now_s(p, s, c, v[ch]);
     } else {
       double w[4][4];
       for (int gc = 0; gc < 4; ++gc) {
@@ -129,10 +143,8 @@ __device__ void value_at(const Geo<T>& e, int s, int L, long long I,
           w[gc][0] = w[gc][1] = w[gc][2] = w[gc][3] = 0.0;
           continue;
         }
-        const GfPatch P = e.V.patch[pg];
-        const int c = e.tix((int)(Ig - (long long)P.px * e.G.M),
-                            (int)(Jg - (long long)P.py * e.G.M));
-        e.load_now(pg, c, w[gc]);
+        const int c = e.local(Ig, Jg);
+        e.load_now_s(pg, s, c, w[gc]);
       }
       for (int f = 0; f < 4; ++f)
         v[ch][f] = 0.25 * ((w[0][f] + w[1][f]) + (w[2][f] + w[3][f]));
@@ -175,11 +187,9 @@ __device__ void fill_cell(const Geo<T>& e, int s, int L, long long I,
   const double bt = bs[J & 1][I & 1];
   const int p = e.leaf(s, L, I, J);
   if (p >= 0) {
-    const GfPatch P = e.V.patch[p];
-    const int c = e.tix((int)(I - (long long)P.px * e.G.M),
-                        (int)(J - (long long)P.py * e.G.M));
+    const int c = e.local(I, J);
     double o4[4];
-    e.load_now(p, c, o4);
+    e.load_now_s(p, s, c, o4);
     out[0] = o4[0];
     out[1] = o4[1];
     out[2] = o4[2];
@@ -749,6 +759,15 @@ __global__ void k_topo(const __grid_constant__ GfGeom G, const __grid_constant__
   const int M = G.M, T_ = G.T, TT = T_ * T_;
   T* b = e.bp(p);
   const GfScenario& S = V.scen[P.scen];
+  // a tile already computed for this position (the same DEMs and eta0):
+  // copied, bit for bit what the computation below gives
+  const size_t slot = (size_t)S.lut_off + G.lut_lev_off[P.level] + P.px +
+                      (size_t)P.py * ((size_t)G.mi << P.level);
+  T* cache = V.bcache ? static_cast<T*>(V.bcache) + slot * TT : nullptr;
+  if (cache && V.bvalid[slot]) {
+    for (int k = threadIdx.x; k < TT; k += blockDim.x) b[k] = cache[k];
+    return;
+  }
   const long long NX = e.nx(P.level), NY = e.ny(P.level);
   const double dx = e.dx(P.level), dy = e.dy(P.level);
   for (int k = threadIdx.x; k < TT; k += blockDim.x) {
@@ -767,6 +786,13 @@ __global__ void k_topo(const __grid_constant__ GfGeom G, const __grid_constant__
   }
   __syncthreads();
   tile_bc<T>(e, P, nullptr, b, 1);
+  if (cache) {
+    // no other CTA of this launch has this position; later launches see the
+    // tile and the flag after this kernel ends
+    __syncthreads();
+    for (int k = threadIdx.x; k < TT; k += blockDim.x) cache[k] = b[k];
+    if (threadIdx.x == 0) V.bvalid[slot] = 1;
+  }
 }
 
 // Regrid transfer: every interior cell of every new patch from the old
@@ -1178,10 +1204,8 @@ __device__ void value_near(const Geo<T>& e, int s, int L, long long I, long long
     const long long Il = I >> (L - l), Jl = J >> (L - l);
     const int p = e.leaf(s, l, Il, Jl);
     if (p >= 0) {
-      const GfPatch P = e.V.patch[p];
-      const int c = e.tix((int)(Il - (long long)P.px * e.G.M),
-                          (int)(Jl - (long long)P.py * e.G.M));
-      e.load_now(p, c, out);
+      const int c = e.local(Il, Jl);
+      e.load_now_s(p, s, c, out);
       return;
     }
   }
@@ -1196,10 +1220,7 @@ __device__ void value_near(const Geo<T>& e, int s, int L, long long I, long long
       double v[4][4];
       for (int ch = 0; ch < 4; ++ch) {
         const long long Ic = 2 * I + (ch & 1), Jc = 2 * J + (ch >> 1);
-        const GfPatch P = e.V.patch[pc[ch]];
-        const int c = e.tix((int)(Ic - (long long)P.px * e.G.M),
-                            (int)(Jc - (long long)P.py * e.G.M));
-        e.load_now(pc[ch], c, v[ch]);
+        e.load_now_s(pc[ch], s, e.local(Ic, Jc), v[ch]);
       }
       for (int f = 0; f < 4; ++f)
         out[f] = 0.25 * ((v[0][f] + v[1][f]) + (v[2][f] + v[3][f]));
@@ -1296,6 +1317,147 @@ __global__ void k_cnn_features(const __grid_constant__ GfGeom G,
       ++cnt;
     }
     for (int c = 0; c < 4; ++c) acc[c] = warp_sum_f64(acc[c]);
+    cnt = __reduce_add_sync(0xffffffffu, cnt);
+    if (lane == 0) emit(X, Y, acc, cnt);
+  }
+}
+
+// The same features for the FP32 deviation form, in single precision: the
+// depth of a cell is w - b of its stored FP32 values, the block and band
+// means are FP32 sums (the features are rounded to BF16, whose unit is 2^15
+// times FP32's, so the precision of the sums changes a feature only when it
+// lies within a few FP32 units of a BF16 rounding boundary), and the
+// lookups are value_near's.  Register use is capped so that three CTAs
+// share an SM: the kernel waits on chains of dependent loads.
+__device__ __forceinline__ void load_f32(const GfGeom& G, const GfView& V, int p, int cur, int c,
+                                         float (&o)[4]) {
+  const int TT = G.T * G.T;
+  const float* q = V.qf[cur] + (size_t)p * 3 * TT;
+  const float b = V.bf[(size_t)p * TT + c];
+  o[0] = q[c] - b;
+  o[1] = q[TT + c];
+  o[2] = q[2 * TT + c];
+  o[3] = b;
+}
+
+// value_at for the FP32 feature kernel, kept out of line: it is the rare
+// case, and inlined its FP64 arrays would crowd the kernel's registers.
+__device__ __noinline__ void value_at_f32(const Geo<float>& e, int s, int L, long long I,
+                                          long long J, float (&out)[4], int* err) {
+  double d[4];
+  value_at(e, s, L, I, J, d, err);
+  for (int f = 0; f < 4; ++f) out[f] = (float)d[f];
+}
+
+// value_near in FP32 (deviation form, no subcycling): the leaf of level L or
+// L - 1, the mean of four leaves of level L + 1, else value_at's composite.
+__device__ void value_near_f32(const Geo<float>& e, int s, int cur, int L, long long I,
+                               long long J, float (&out)[4], int* err) {
+  for (int l = L; l >= L - 1 && l >= 0; --l) {
+    const long long Il = I >> (L - l), Jl = J >> (L - l);
+    const int p = e.leaf(s, l, Il, Jl);
+    if (p >= 0) {
+      load_f32(e.G, e.V, p, cur, e.local(Il, Jl), out);
+      return;
+    }
+  }
+  if (L + 1 <= e.G.maxlevel) {
+    int pc[4];
+    bool all = true;
+    for (int ch = 0; ch < 4; ++ch) {
+      pc[ch] = e.leaf(s, L + 1, 2 * I + (ch & 1), 2 * J + (ch >> 1));
+      all = all && pc[ch] >= 0;
+    }
+    if (all) {
+      float v[4][4];
+      for (int ch = 0; ch < 4; ++ch)
+        load_f32(e.G, e.V, pc[ch], cur, e.local(2 * I + (ch & 1), 2 * J + (ch >> 1)), v[ch]);
+      for (int f = 0; f < 4; ++f)
+        out[f] = 0.25f * ((v[0][f] + v[1][f]) + (v[2][f] + v[3][f]));
+      return;
+    }
+  }
+  value_at_f32(e, s, L, I, J, out, err);
+}
+
+__global__ void __launch_bounds__(256, 3)
+    k_cnn_features_f32(const __grid_constant__ GfGeom G, const __grid_constant__ GfView V,
+                       int first, FeatScale sc, __nv_bfloat16* out) {
+  const int p = first + blockIdx.x;
+  const GfPatch P = V.patch[p];
+  Geo<float> e(G, V);
+  const int M = G.M, f = M / 16, W = M / 2, TT = G.T * G.T;
+  const int cur = V.ctl[P.scen].cur;
+  __shared__ float part[8];
+  __shared__ float bmean;
+  const float* bp = V.bf + (size_t)p * TT;
+  float bs = 0.0f;
+  for (int k = threadIdx.x; k < M * M; k += blockDim.x) bs += bp[e.tix(k % M, k / M)];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) bs += __shfl_xor_sync(0xffffffffu, bs, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = bs;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.0f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+    bmean = t / (float)(M * M);
+  }
+  __syncthreads();
+  __nv_bfloat16* o = out + (size_t)blockIdx.x * 324 * 16;
+  const long long NX = e.nx(P.level), NY = e.ny(P.level);
+  const long long I0 = (long long)P.px * M, J0 = (long long)P.py * M;
+  int err = 0;
+  const float lev = 0.25f * (float)P.level;
+  auto emit = [&](int X, int Y, const float (&acc)[4], int cnt) {
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    if (cnt > 0) {
+      const float inv = 1.0f / (float)cnt;
+      v[0] = acc[0] * inv / sc.s[0];
+      v[1] = acc[1] * inv / sc.s[1];
+      v[2] = acc[2] * inv / sc.s[2];
+      v[3] = (acc[3] * inv - bmean) / sc.s[3];
+    }
+    __nv_bfloat16* op = o + (Y * 18 + X) * 16;
+    for (int c = 0; c < 4; ++c) op[c] = __float2bfloat16_rn(v[c]);
+    op[4] = __float2bfloat16_rn(lev);
+    for (int c = 5; c < 16; ++c) op[c] = __float2bfloat16_rn(0.f);
+  };
+  for (int q = threadIdx.x; q < 256; q += blockDim.x) {
+    const int X = q % 16 + 1, Y = q / 16 + 1;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int j = (Y - 1) * f; j < Y * f; ++j)
+      for (int i = (X - 1) * f; i < X * f; ++i) {
+        float c4[4];
+        load_f32(G, V, p, cur, e.tix(i, j), c4);
+        for (int c = 0; c < 4; ++c) acc[c] += c4[c];
+      }
+    emit(X, Y, acc, f * f);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int r = warp; r < 68; r += nwarp) {
+    int X, Y;
+    if (r < 18) { X = r; Y = 0; }
+    else if (r < 36) { X = r - 18; Y = 17; }
+    else if (r < 52) { X = 0; Y = r - 36 + 1; }
+    else { X = 17; Y = r - 52 + 1; }
+    const int i0 = X == 0 ? -W : X == 17 ? M : (X - 1) * f;
+    const int i1 = X == 0 ? 0 : X == 17 ? M + W : X * f;
+    const int j0 = Y == 0 ? -W : Y == 17 ? M : (Y - 1) * f;
+    const int j1 = Y == 0 ? 0 : Y == 17 ? M + W : Y * f;
+    const int wi = i1 - i0, ncell = wi * (j1 - j0);
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    int cnt = 0;
+    for (int k = lane; k < ncell; k += 32) {
+      const long long I = I0 + i0 + k % wi, J = J0 + j0 + k / wi;
+      if (I < 0 || J < 0 || I >= NX || J >= NY) continue;
+      float c4[4];
+      value_near_f32(e, P.scen, cur, P.level, I, J, c4, &err);
+      for (int c = 0; c < 4; ++c) acc[c] += c4[c];
+      ++cnt;
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      for (int d = 16; d > 0; d >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], d);
     cnt = __reduce_add_sync(0xffffffffu, cnt);
     if (lane == 0) emit(X, Y, acc, cnt);
   }
@@ -1408,7 +1570,9 @@ int launch_cnn_features(const GfGeom& g, const GfView& v, int first, int count,
   if (count <= 0) return 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   FeatScale sc{{scale[0], scale[1], scale[2], scale[3]}};
-  if (v.prec)
+  if (v.prec && !g.subcycle)
+    k_cnn_features_f32<<<count, 256, 0, st>>>(g, v, first, sc, static_cast<__nv_bfloat16*>(out));
+  else if (v.prec)
     k_cnn_features<float><<<count, 256, 0, st>>>(g, v, first, sc, static_cast<__nv_bfloat16*>(out));
   else
     k_cnn_features<double><<<count, 256, 0, st>>>(g, v, first, sc, static_cast<__nv_bfloat16*>(out));

@@ -139,6 +139,10 @@ struct geoflood_ctx {
   long long launches = 0;
   long long generation = 0;  // bumped by every regrid
   double regrid_host_s = 0;  // host wall time of the quadtree regrids so far
+  // bed tiles by position (see GfView::bcache), allocated when they fit
+  // kBedCacheBudget bytes
+  void* d_bcache = nullptr;
+  unsigned char* d_bvalid = nullptr;
   // pinned staging of host-built tables: uploads read it asynchronously; the
   // event marks when the last upload from it has been consumed
   unsigned char* h_up = nullptr;
@@ -151,6 +155,9 @@ struct geoflood_ctx {
 };
 
 namespace {
+
+// Device memory the bed cache may take (all scenarios, all levels).
+constexpr size_t kBedCacheBudget = size_t(4) << 30;
 
 int fail(geoflood_ctx* c, int code, const std::string& msg) {
   if (c) c->err = msg;
@@ -199,6 +206,8 @@ GfView view(geoflood_ctx* c, int t, int bb) {
   v.pwet = c->d_pwet;
   v.gflag = c->d_gflag;
   v.pcnt = c->d_pcnt;
+  v.bcache = c->d_bcache;
+  v.bvalid = c->d_bvalid;
   v.npatch = c->npatch;
   v.prec = c->prec;
   return v;
@@ -458,9 +467,19 @@ int forget_same(geoflood_ctx* ctx) {
   return 0;
 }
 
+// The bed tiles cached for a scenario no longer match after its DEMs or its
+// reference surface change.
+int forget_beds(geoflood_ctx* ctx, int s) {
+  if (ctx->d_bvalid)
+    CK(cudaMemsetAsync(ctx->d_bvalid + (size_t)s * ctx->G.lut_per_scen, 0,
+                       (size_t)ctx->G.lut_per_scen, ctx->st));
+  return 0;
+}
+
 int topo_scenario(geoflood_ctx* ctx, int s) {
   int rc = forget_same(ctx);
   if (rc) return rc;
+  if ((rc = forget_beds(ctx, s))) return rc;
   CKL(gf::launch_topo(ctx->G, view(ctx), ctx->h_scen[s].poff,
                       ctx->h_scen[s].pcount, ctx->st),
       "topo");
@@ -746,6 +765,23 @@ int geoflood_init_forest(const geoflood_config* cfg, void* stream,
   okk &= alloc((void**)&ctx->d_flags, cap);
   okk &= alloc((void**)&ctx->d_err, sizeof(int));
   okk &= cudaMallocHost((void**)&ctx->h_ctl, ctx->nscen * sizeof(GfCtl)) == cudaSuccess;
+  {
+    // bed tiles by position: every patch position of every level, when that
+    // fits the budget (else beds are always recomputed from the DEMs)
+    const size_t slots = (size_t)ctx->nscen * G.lut_per_scen;
+    const size_t bytes = slots * TT * (ctx->prec ? sizeof(float) : sizeof(double));
+    if (okk && bytes <= kBedCacheBudget) {
+      if (cudaMalloc(&ctx->d_bcache, bytes) != cudaSuccess ||
+          cudaMalloc((void**)&ctx->d_bvalid, slots) != cudaSuccess ||
+          cudaMemsetAsync(ctx->d_bvalid, 0, slots, ctx->st) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(ctx->d_bcache);
+        cudaFree(ctx->d_bvalid);
+        ctx->d_bcache = nullptr;
+        ctx->d_bvalid = nullptr;
+      }
+    }
+  }
   if (!okk) {
     cudaGetLastError();
     geoflood_destroy(ctx);
@@ -832,6 +868,8 @@ void geoflood_destroy(geoflood_ctx* ctx) {
   cudaFree(ctx->d_flags);
   cudaFree(ctx->d_err);
   cudaFree(ctx->d_stage);
+  cudaFree(ctx->d_bcache);
+  cudaFree(ctx->d_bvalid);
   for (auto& v : ctx->d_dem)
     for (auto p : v) cudaFree(p);
   for (auto p : ctx->d_gxy) cudaFree(p);
@@ -2164,6 +2202,8 @@ int geoflood_load(geoflood_ctx* ctx, const void* buf, size_t size) {
     S.ndem = (int)sc[s].z.size();
   }
   if ((rc = upload_scen(ctx))) return rc;
+  for (int s = 0; s < ctx->nscen; ++s)
+    if ((rc = forget_beds(ctx, s))) return rc;
   CKL(gf::launch_topo(ctx->G, view(ctx), 0, ctx->npatch, ctx->st), "topo");
   ctx->launches++;
   // states into buffer 0, time-stepping state, gauges

@@ -149,6 +149,13 @@ struct GfView {
   unsigned* pcnt;
   // per patch: 1 if a gauge samples in it (or null)
   unsigned char* gflag;
+  // Bed tiles by position (or null): slot = the lookup-table index of
+  // (scenario, level, px, py); bcache holds [slots][T][T] of the state's
+  // type (double in FP64, float minus eta0 in the deviation form) and
+  // bvalid[slot] says whether that slot holds the tile for the current
+  // DEMs and eta0.
+  void* bcache;
+  unsigned char* bvalid;
   int npatch;
   int prec;               // 0 = FP64, 1 = FP32 surface deviation
 };

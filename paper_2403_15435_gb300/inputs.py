@@ -376,7 +376,7 @@ def flood_speed(patch: int = 32, minlevel: int = 0, maxlevel: int = 3,
 
 def canyon_plain(patch: int = 32, minlevel: int = 0, maxlevel: int = 4,
                  seed: int = SEED_BASE + 7, dem_spacing: float = 10.0,
-                 depth: float = 55.0, precision: int = 1) -> Problem:
+                 depth: float = 55.0, precision: int = 1, near_gauges: int = 0) -> Problem:
     """Large AMR workload (the Malpasset set-up's shape, Sec. 6.2-6.4): a
     17 km x 9 km domain of 1 km blocks; for x < 10 km a canyon -- fractal
     terrain 60-120 m high cut 50 m deep by a meandering channel (centre line
@@ -387,7 +387,9 @@ def canyon_plain(patch: int = 32, minlevel: int = 0, maxlevel: int = 4,
     instantaneous dam break, dry downstream, n = 0.033.  Levels
     minlevel..maxlevel (5 levels: 31.25 m to 1.95 m cells with 32-cell
     patches); refinement to maxlevel where water flows and over the
-    reservoir (source box)."""
+    reservoir (source box).  Gauges: 16 on the channel's centre line from
+    x = 2.5 km to 16 km, then near_gauges more on it from x = 2050 m to
+    2800 m (reached in the flood's first seconds)."""
     Lx, Ly = 17000.0, 9000.0
     cfg = Config(mi=17, mj=9, mx=patch, minlevel=minlevel, maxlevel=maxlevel,
                  xupper=Lx, yupper=Ly, drytol=1e-3, manning_n=0.033, dt_initial=0.05,
@@ -418,6 +420,8 @@ def canyon_plain(patch: int = 32, minlevel: int = 0, maxlevel: int = 4,
         return h, np.zeros_like(h), np.zeros_like(h)
 
     gx = np.linspace(2500.0, 16000.0, 16)
+    if near_gauges:
+        gx = np.concatenate([gx, np.linspace(2050.0, 2800.0, near_gauges)])
     gy = 0.5 * Ly + 800.0 * np.sin(2 * np.pi * gx / 3000.0 + phase)
     return Problem("canyon_plain", cfg, dem, ic, 4000.0, np.stack([gx, gy], 1))
 

@@ -53,9 +53,11 @@ def ulp_bf16(x):
     return 2.0 ** (e - 7)
 
 
-@pytest.mark.parametrize("patch", [16, 32])
-def test_features_match_oracle(patch):
-    prob = small_valley(patch)
+@pytest.mark.parametrize("patch,precision", [(16, 0), (32, 0), (16, 1), (32, 1)])
+def test_features_match_oracle(patch, precision):
+    """FP64 forests: FP64 sums, as the oracle.  FP32 forests: FP32 sums of
+    the stored values; the oracle takes the same state read out in FP64."""
+    prob = small_valley(patch, precision=precision)
     g = forest(prob)
     for _ in range(3):
         g.regrid()
