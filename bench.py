@@ -344,6 +344,18 @@ class ValleyArm:
         st["wet_updates_counted"] = c1[1] - c0[1]
         return st, a.elapsed_time(b) / 1e3
 
+    def autotune(self, t_mid):
+        """The patch-step kernel shape for this arm: every variant timed on
+        the state at t_mid (the middle of the window), the fastest kept for
+        the runs that follow (a checkpoint load keeps it)."""
+        self.f.load(self.ckpt)
+        self.f.advance(t_mid, regrid_interval=self.regrid, check_interval=4,
+                       regrid_on_miss=self.learned)
+        variant, ms = self.f.autotune(5)
+        self.variant = {"chosen": int(variant), "ms_per_launch": [float(x) for x in ms if x == x],
+                        "at_t_s": t_mid, "patches": self.f.npatch}
+        return self.variant
+
     def summary(self, runs):
         """Rates of a list of (stats, seconds) runs and the last run's state."""
         cells = sum(st["patch_steps"] for st, _ in runs) * PATCH * PATCH
@@ -352,6 +364,7 @@ class ValleyArm:
         out, arr = self.f.gauges()
         return {"value": cells / sec, "unit": "cell-updates/s",
                 "wall_s": sec / len(runs), "runs": len(runs),
+                "kernel_variant": getattr(self, "variant", None),
                 "steps": st["steps"], "regrids": st["regrids"],
                 "regrids_on_miss": st["miss_regrids"], "checks": st["checks"],
                 "criterion_misses": st["misses"],
@@ -395,6 +408,8 @@ def measure_valley(args, dev, stream, world, local, peaks):
     net_prm, net_thr, train = train_network(stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     head = ValleyArm(stream, 1, True, 16, net=(net_prm, net_thr), t_end=args.t_end)
+    head.run(flush)
+    head.autotune(0.5 * args.t_end)
     for _ in range(args.warmup):
         head.run(flush)
     launches0 = head.f.launch_count()
@@ -459,10 +474,12 @@ def measure_valley(args, dev, stream, world, local, peaks):
     # the pair's other side and the control, each warmed up on a short run
     fp64 = ValleyArm(stream, 0, False, 4, t_end=args.t_end)
     fp64.run(flush, t_end=2.0)
+    fp64.autotune(0.25 * args.t_end)
     plain64 = fp64.summary([fp64.run(flush)])
     fp64.close()
     fp32p = ValleyArm(stream, 1, False, 4, t_end=args.t_end)
     fp32p.run(flush, t_end=2.0)
+    fp32p.autotune(0.5 * args.t_end)
     plain32 = fp32p.summary([fp32p.run(flush) for _ in range(2)])
     fp32p.close()
 

@@ -326,15 +326,18 @@ int geoflood_counters(geoflood_ctx* ctx, int scenario, long long* cell_updates,
  * halo staging): times every available variant reps times on the current
  * state (without advancing it), selects the fastest for this context and
  * returns its number in *variant and the times (ms per launch) in
- * ms_per_variant (one entry per variant, at most 16: four for 32 x 32
- * patches, one for 16 x 16; either pointer may be NULL).  Variants of
+ * ms_per_variant (one entry per variant, at most 16: six for 32 x 32
+ * patches in FP32, four in FP64, one for 16 x 16; either pointer may be
+ * NULL).  Variants of
  * 32 x 32 patches: 0 = one 512-thread CTA per patch staging the whole tile
  * by TMA bulk copies, 1 = four CTAs per patch, each staging a 16 x 16
  * sub-tile with its two-cell halo, 2 = the FP32 shape of 0 or the FP64 shape
  * of 1 with the register budget of one CTA per SM, 3 = FP32: one 1024-thread
  * CTA per patch; FP64: adaptive (four sub-tile CTAs for each patch that held
  * water in the previous step, one CTA that checks the whole tile for every
- * other patch).  Results do not depend on the variant. */
+ * other patch); FP32 only: 4 = the sub-tiles of 1 with three 352-thread CTAs
+ * per SM, 5 = with four 320-thread CTAs per SM.  Results do not depend on
+ * the variant. */
 int geoflood_autotune(geoflood_ctx* ctx, int reps, int* variant,
                       double* ms_per_variant);
 

@@ -509,6 +509,9 @@ __global__ void k_inflow(const __grid_constant__ GfGeom G, const __grid_constant
                          const int* list, int only_accepted) {
   const int p = list[blockIdx.x];
   const int M = G.M, TT = G.T * G.T;
+  // a patch on the inflow side runs in every launch
+  if (threadIdx.x == 0 && V.runf != nullptr && V.sched != nullptr)
+    V.runf[(size_t)(V.sched[0] & 1u) * V.runf_stride + p] = 1;
   const int l = (int)threadIdx.x - GF_NG;
   if (l >= M + GF_NG) return;
   const GfPatch P = V.patch[p];
@@ -633,6 +636,10 @@ __global__ void k_ghost_other(const __grid_constant__ GfGeom G, const __grid_con
   fill_cell(e, P.scen, P.level, I, J, bs, out, &err);
   if (err && errflag) *errflag = 1;
   e.store(q, c, out[0], out[1], out[2], bt);
+  // water written into this patch's ghost cells: it runs in the next launch
+  // (the patch step has flipped the parity, so sched[0] selects it)
+  if (out[0] > 0.0 && V.runf != nullptr && V.sched != nullptr)
+    V.runf[(size_t)(V.sched[0] & 1u) * V.runf_stride + p] = 1;
   // physical-boundary ghosts mirroring this cell (wall: reflected, normal
   // momentum negated; extrapolation: the edge cell into both layers)
   const int nxp = G.mi << P.level, nyp = G.mj << P.level;

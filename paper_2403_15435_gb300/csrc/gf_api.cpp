@@ -88,6 +88,7 @@ struct geoflood_ctx {
   unsigned* d_sched = nullptr;        // launch-order parity and counters
   int* d_ord[2] = {nullptr, nullptr}; // launch orders of the patch step
   unsigned char* d_same = nullptr;    // per work unit: buffers agree
+  unsigned char* d_runf = nullptr;    // [2][cap] run flags (see GfView::runf)
   unsigned char* d_gflag = nullptr;   // per patch: holds a gauge
   unsigned* d_pwet = nullptr;         // adaptive variant: per-patch flags
   unsigned* d_pcnt = nullptr;
@@ -208,6 +209,8 @@ GfView view(geoflood_ctx* c, int t, int bb) {
   v.pcnt = c->d_pcnt;
   v.bcache = c->d_bcache;
   v.bvalid = c->d_bvalid;
+  v.runf = c->d_runf;
+  v.runf_stride = c->cap;
   v.npatch = c->npatch;
   v.prec = c->prec;
   return v;
@@ -413,6 +416,7 @@ int upload_tables(geoflood_ctx* ctx, int t,
                      cudaMemcpyDeviceToDevice, ctx->st));
   CK(cudaMemsetAsync(ctx->d_sched, 0, 8 * sizeof(unsigned), ctx->st));
   CK(cudaMemsetAsync(ctx->d_same, 0, (size_t)ctx->cap * 4, ctx->st));
+  CK(cudaMemsetAsync(ctx->d_runf, 1, (size_t)ctx->cap * 2, ctx->st));
   CK(cudaMemsetAsync(ctx->d_pwet, 0, (size_t)ctx->cap * sizeof(unsigned), ctx->st));
   CK(cudaMemsetAsync(ctx->d_gflag, 0, (size_t)ctx->cap, ctx->st));
   CK(cudaMemsetAsync(ctx->d_pcnt, 0, (size_t)ctx->cap * sizeof(unsigned), ctx->st));
@@ -446,6 +450,8 @@ int check_errflag(geoflood_ctx* ctx) {
 
 int ghost_fill_all(geoflood_ctx* ctx) {
   gf::set_errflag(ctx->d_err);
+  // ghost cells rewritten from scratch: every patch runs next
+  CK(cudaMemsetAsync(ctx->d_runf, 1, (size_t)ctx->cap * 2, ctx->st));
   ProfRec r;
   prof_begin(ctx, "ghost_fill", &r);
   CKL(gf::launch_ghost_fill(ctx->G, view(ctx), 0, ctx->st), "ghost_fill");
@@ -464,6 +470,8 @@ int ghost_fill_all(geoflood_ctx* ctx) {
 // the two state buffers.
 int forget_same(geoflood_ctx* ctx) {
   CK(cudaMemsetAsync(ctx->d_same, 0, (size_t)ctx->cap * 4, ctx->st));
+  // every patch runs until the marks of two launches have built up again
+  CK(cudaMemsetAsync(ctx->d_runf, 1, (size_t)ctx->cap * 2, ctx->st));
   return 0;
 }
 
@@ -747,6 +755,7 @@ int geoflood_init_forest(const geoflood_config* cfg, void* stream,
   okk &= alloc((void**)&ctx->d_ord[0], cap * sizeof(int));
   okk &= alloc((void**)&ctx->d_ord[1], cap * sizeof(int));
   okk &= alloc((void**)&ctx->d_same, cap * 4);
+  okk &= alloc((void**)&ctx->d_runf, cap * 2);
   okk &= alloc((void**)&ctx->d_pwet, cap * sizeof(unsigned));
   okk &= alloc((void**)&ctx->d_gflag, cap);
   okk &= alloc((void**)&ctx->d_pcnt, cap * sizeof(unsigned));
@@ -852,6 +861,7 @@ void geoflood_destroy(geoflood_ctx* ctx) {
   cudaFree(ctx->d_ord[0]);
   cudaFree(ctx->d_ord[1]);
   cudaFree(ctx->d_same);
+  cudaFree(ctx->d_runf);
   cudaFree(ctx->d_pwet);
   cudaFree(ctx->d_gflag);
   cudaFree(ctx->d_pcnt);

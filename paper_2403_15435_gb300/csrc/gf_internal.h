@@ -156,6 +156,17 @@ struct GfView {
   // DEMs and eta0.
   void* bcache;
   unsigned char* bvalid;
+  // Per patch, two arrays selected by the launch-order parity sched[0] (or
+  // null: every patch runs): 1 if the patch must run in the launch that
+  // reads that parity.  A launch clears the flags it reads and sets, in the
+  // other array, those of every patch whose tile held water and of its
+  // same-level neighbours; the cross-level ghost fill and the inflow set
+  // those of the patches whose ghost cells they write.  An unmarked patch
+  // whose tile is dry and unchanged in both buffers and that holds no gauge
+  // returns before staging: its ghost ring is dry, so the full path would
+  // write nothing either.  Whole-tile CTAs only; not with subcycling.
+  unsigned char* runf;
+  int runf_stride;
   int npatch;
   int prec;               // 0 = FP64, 1 = FP32 surface deviation
 };

@@ -23,6 +23,12 @@ int launch_patch_step_f32(const GfGeom& g, const GfView& v, int variant,
     return gfs::launch_step<gfs::PrecF32, 32, 32, 512, 1>(g, v, st);
   if (g.M == 32 && variant == 3)
     return gfs::launch_step<gfs::PrecF32, 32, 32, 1024, 1>(g, v, st);
+  // 16 x 16 sub-tiles with more CTAs per SM: 352 threads, three CTAs (one
+  // round per sweep phase, 56 registers); 320 threads, four CTAs
+  if (g.M == 32 && variant == 4)
+    return gfs::launch_step<gfs::PrecF32, 32, 16, 352, 3>(g, v, st);
+  if (g.M == 32 && variant == 5)
+    return gfs::launch_step<gfs::PrecF32, 32, 16, 320, 4>(g, v, st);
   if (g.M == 32) return gfs::launch_step<gfs::PrecF32, 32, 32, 512, 2>(g, v, st);
   if (g.M == 16) return gfs::launch_step<gfs::PrecF32, 16, 16, 352, 2>(g, v, st);
   return -1;

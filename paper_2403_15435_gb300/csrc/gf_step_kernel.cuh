@@ -1261,18 +1261,45 @@ __global__ void __launch_bounds__(NT, MINB)
   const bool sched = V.sched != nullptr && V.done != nullptr;
   const unsigned par = sched ? V.sched[0] : 0u;
   const int p = sched ? (par ? V.ord1 : V.ord0)[slot] : slot;
-  const GfPatch Pt = V.patch[p];
+  // run flags (GfView::runf): read by every thread beside the patch record,
+  // so that a running tile waits for nothing more
+  constexpr bool FLAGS = NSUB == 1 && !DS;
+  const bool use_flags = FLAGS && sched && V.runf != nullptr && !G.subcycle;
+  unsigned char* rcur = use_flags ? V.runf + (size_t)(par & 1u) * V.runf_stride : nullptr;
+  unsigned char* rnxt = use_flags ? V.runf + (size_t)((par ^ 1u) & 1u) * V.runf_stride : nullptr;
+  const bool marked = use_flags && rcur[p] != 0;
+  // an unmarked dry, unchanged tile without a gauge takes no step (the full
+  // path would find its ghost ring dry and write nothing)
+  const bool skip = use_flags && !marked && V.same != nullptr && V.same[p] != 0 &&
+                    !(V.gflag != nullptr && V.gflag[p] != 0);
   int wet = 0;
-  bool wrote = true;
-  bool run = V.ctl[Pt.scen].active != 0;
-  if (run && G.subcycle) {
-    // level subcycling: only the levels due at this substep step
-    const GfCtl& C = V.ctl[Pt.scen];
-    run = !C.sub_rej && C.sub_k % (1 << (G.maxlevel - Pt.level)) == 0;
+  bool wrote = false;
+  if (!skip) {
+    const GfPatch Pt = V.patch[p];
+    bool run = V.ctl[Pt.scen].active != 0;
+    if (run && G.subcycle) {
+      // level subcycling: only the levels due at this substep step
+      const GfCtl& C = V.ctl[Pt.scen];
+      run = !C.sub_rej && C.sub_k % (1 << (G.maxlevel - Pt.level)) == 0;
+    }
+    wrote = true;
+    if (run)
+      wet = patch_body<P, MP, M, NT, DS>(G, V, smraw, p, sub, nullptr, &wrote);
+    else wrote = false;
+    if (use_flags && threadIdx.x == 0) {
+      // the mark is consumed; a patch that did not run carries it forward
+      rcur[p] = 0;
+      if (!run) rnxt[p] = 1;
+    }
+    if (use_flags && wet && threadIdx.x < 9) {
+      // water in this tile: it and its same-level neighbours run next launch
+      // (their indices were staged in shared memory by the patch body)
+      using Lo = Layout<P, M, DS>;
+      const int* snb = reinterpret_cast<const int*>(smraw + Lo::OFF_NB);
+      const int q = threadIdx.x == 8 ? p : snb[threadIdx.x];
+      if (q >= 0) rnxt[q] = 1;
+    }
   }
-  if (run)
-    wet = patch_body<P, MP, M, NT, DS>(G, V, smraw, p, sub, nullptr, &wrote);
-  else wrote = false;
   if (sched && sub == 0 && threadIdx.x == 0) {
     int* nxt = par ? V.ord0 : V.ord1;
     if (wet) nxt[atomicAdd(V.sched + 1, 1u)] = p;
