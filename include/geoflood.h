@@ -501,7 +501,8 @@ int geoflood_cnn_train(geoflood_ctx* ctx, int epochs, int batch, float lr,
 /* Time stepping with periodic regridding (Sec. 3.3 regrids every few
  * steps; Sec. 6.4 every 4).  Advances every scenario to t_target in chunks
  * of check_interval steps; after each chunk the plain criterion is
- * evaluated (geoflood_check_tags) and the forest regrids when
+ * evaluated (geoflood_check_tags; when a regrid is due, the regrid's own tag
+ * pass counts the criterion's misses instead) and the forest regrids when
  * regrid_interval steps have passed since the last regrid or, with
  * GEOFLOOD_ADVANCE_REGRID_ON_MISS, as soon as the criterion reports a
  * miss.  With GEOFLOOD_ADVANCE_COLLECT it records training samples instead

@@ -170,6 +170,98 @@ __device__ __forceinline__ void child_beds(const Geo<T>& e, const B* bed, int i,
     for (int a = 0; a < 2; ++a) bs[b][a] = (double)bed[e.tix(i0 + a, j0 + b)];
 }
 
+// The four children (a, b) of cell (ic, jc) of level L - 1, whose beds are
+// bs[b][a], interpolated from level L - 1 (the rule fill_cell states):
+// out[b][a] = (h, hu, hv) of child (2 ic + a, 2 jc + b) of level L.
+template <typename T>
+__device__ void interp_children(const Geo<T>& e, int s, int L, long long ic, long long jc,
+                                const double (&bs)[2][2], double (&out)[2][2][3], int* err) {
+  const long long NXc = e.nx(L - 1), NYc = e.ny(L - 1);
+  double nb[3][3][4];
+  bool in[3][3];
+  for (int dj = -1; dj <= 1; ++dj)
+    for (int di = -1; di <= 1; ++di) {
+      const long long x = ic + di, y = jc + dj;
+      in[dj + 1][di + 1] = x >= 0 && y >= 0 && x < NXc && y < NYc;
+      if (in[dj + 1][di + 1]) value_at(e, s, L - 1, x, y, nb[dj + 1][di + 1], err);
+    }
+  const double drytol = e.G.drytol;
+  const double* qc = nb[1][1];
+  if (qc[0] <= drytol) {
+    for (int b = 0; b < 2; ++b)
+      for (int a = 0; a < 2; ++a) {
+        out[b][a][0] = qc[0];
+        out[b][a][1] = qc[1];
+        out[b][a][2] = qc[2];
+      }
+    return;
+  }
+  bool allwet = true;
+  for (int dj = 0; dj < 3; ++dj)
+    for (int di = 0; di < 3; ++di)
+      if (in[dj][di] && !(nb[dj][di][0] > drytol)) allwet = false;
+  const double etac = qc[0] + qc[3];
+  // limited slopes over the coarse cell: surface, then both momenta
+  double g[3][2] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
+  if (allwet) {
+    const bool hx = in[1][0] && in[1][2], hy = in[0][1] && in[2][1];
+    double et[3][3];
+    for (int dj = 0; dj < 3; ++dj)
+      for (int di = 0; di < 3; ++di)
+        et[dj][di] = in[dj][di] ? nb[dj][di][0] + nb[dj][di][3] : 0.0;
+    if (hx) g[0][0] = minmod(et[1][2] - et[1][1], et[1][1] - et[1][0]);
+    if (hy) g[0][1] = minmod(et[2][1] - et[1][1], et[1][1] - et[0][1]);
+    for (int k = 1; k < 3; ++k) {
+      if (hx) g[k][0] = minmod(nb[1][2][k] - qc[k], qc[k] - nb[1][0][k]);
+      if (hy) g[k][1] = minmod(nb[2][1][k] - qc[k], qc[k] - nb[0][1][k]);
+    }
+  }
+  // the four children: depth d, linearly interpolated momenta m
+  double d[2][2], m[2][2][2];
+  for (int b = 0; b < 2; ++b)
+    for (int a = 0; a < 2; ++a) {
+      const double sx = a ? 0.25 : -0.25, sy = b ? 0.25 : -0.25;
+      const double eta = allwet ? (etac + sx * g[0][0]) + sy * g[0][1] : etac;
+      const double h = eta - bs[b][a];
+      d[b][a] = h > 0.0 ? h : 0.0;
+      for (int k = 0; k < 2; ++k)
+        m[b][a][k] = (qc[k + 1] + sx * g[k + 1][0]) + sy * g[k + 1][1];
+    }
+  const double S = (d[0][0] + d[0][1]) + (d[1][0] + d[1][1]);
+  bool split[2];
+  for (int k = 0; k < 2; ++k) {
+    split[k] = !allwet;
+    if (allwet) {
+      double lo = INFINITY, hi = -INFINITY;
+      for (int dj = 0; dj < 3; ++dj)
+        for (int di = 0; di < 3; ++di)
+          if (in[dj][di]) {
+            const double u = nb[dj][di][k + 1] / nb[dj][di][0];
+            lo = fmin(lo, u);
+            hi = fmax(hi, u);
+          }
+      for (int b = 0; b < 2; ++b)
+        for (int a = 0; a < 2; ++a)
+          if (d[b][a] > drytol) {
+            const double u = m[b][a][k] / d[b][a];
+            if (u < lo || u > hi) split[k] = true;
+          }
+    }
+  }
+  for (int b0 = 0; b0 < 2; ++b0)
+    for (int a0 = 0; a0 < 2; ++a0) {
+      const double hf = d[b0][a0];
+      out[b0][a0][0] = hf;
+      for (int k = 0; k < 2; ++k)
+        out[b0][a0][k + 1] = !split[k] ? m[b0][a0][k]
+                                       : (S > 0.0 ? (4.0 * qc[k + 1]) * (hf / S) : 0.0);
+      if (hf <= drytol) {
+        out[b0][a0][1] = 0.0;
+        out[b0][a0][2] = 0.0;
+      }
+    }
+}
+
 // Value (h, hu, hv) of cell (I, J) of level L, whose parent's four children
 // have the beds bs (bs[J & 1][I & 1] is this cell's), from the forest of the
 // view: copy from a same-level leaf, mean of finer cells, or interpolation
@@ -220,83 +312,9 @@ __device__ void fill_cell(const Geo<T>& e, int s, int L, long long I,
     }
     return;
   }
-  const long long ic = I >> 1, jc = J >> 1;
-  const long long NXc = e.nx(L - 1), NYc = e.ny(L - 1);
-  double nb[3][3][4];
-  bool in[3][3];
-  for (int dj = -1; dj <= 1; ++dj)
-    for (int di = -1; di <= 1; ++di) {
-      const long long x = ic + di, y = jc + dj;
-      in[dj + 1][di + 1] = x >= 0 && y >= 0 && x < NXc && y < NYc;
-      if (in[dj + 1][di + 1]) value_at(e, s, L - 1, x, y, nb[dj + 1][di + 1], err);
-    }
-  const double drytol = e.G.drytol;
-  const double* qc = nb[1][1];
-  if (qc[0] <= drytol) {
-    out[0] = qc[0];
-    out[1] = qc[1];
-    out[2] = qc[2];
-    return;
-  }
-  bool allwet = true;
-  for (int dj = 0; dj < 3; ++dj)
-    for (int di = 0; di < 3; ++di)
-      if (in[dj][di] && !(nb[dj][di][0] > drytol)) allwet = false;
-  const double etac = qc[0] + qc[3];
-  // limited slopes over the coarse cell: surface, then both momenta
-  double g[3][2] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
-  if (allwet) {
-    const bool hx = in[1][0] && in[1][2], hy = in[0][1] && in[2][1];
-    double et[3][3];
-    for (int dj = 0; dj < 3; ++dj)
-      for (int di = 0; di < 3; ++di)
-        et[dj][di] = in[dj][di] ? nb[dj][di][0] + nb[dj][di][3] : 0.0;
-    if (hx) g[0][0] = minmod(et[1][2] - et[1][1], et[1][1] - et[1][0]);
-    if (hy) g[0][1] = minmod(et[2][1] - et[1][1], et[1][1] - et[0][1]);
-    for (int k = 1; k < 3; ++k) {
-      if (hx) g[k][0] = minmod(nb[1][2][k] - qc[k], qc[k] - nb[1][0][k]);
-      if (hy) g[k][1] = minmod(nb[2][1][k] - qc[k], qc[k] - nb[0][1][k]);
-    }
-  }
-  // the four children: depth d, linearly interpolated momenta m
-  double d[2][2], m[2][2][2];
-  for (int b = 0; b < 2; ++b)
-    for (int a = 0; a < 2; ++a) {
-      const double sx = a ? 0.25 : -0.25, sy = b ? 0.25 : -0.25;
-      const double eta = allwet ? (etac + sx * g[0][0]) + sy * g[0][1] : etac;
-      const double h = eta - bs[b][a];
-      d[b][a] = h > 0.0 ? h : 0.0;
-      for (int k = 0; k < 2; ++k)
-        m[b][a][k] = (qc[k + 1] + sx * g[k + 1][0]) + sy * g[k + 1][1];
-    }
-  const double S = (d[0][0] + d[0][1]) + (d[1][0] + d[1][1]);
-  const int a0 = (int)(I & 1), b0 = (int)(J & 1);
-  const double hf = d[b0][a0];
-  out[0] = hf;
-  for (int k = 0; k < 2; ++k) {
-    bool split = !allwet;
-    if (allwet) {
-      double lo = INFINITY, hi = -INFINITY;
-      for (int dj = 0; dj < 3; ++dj)
-        for (int di = 0; di < 3; ++di)
-          if (in[dj][di]) {
-            const double u = nb[dj][di][k + 1] / nb[dj][di][0];
-            lo = fmin(lo, u);
-            hi = fmax(hi, u);
-          }
-      for (int b = 0; b < 2; ++b)
-        for (int a = 0; a < 2; ++a)
-          if (d[b][a] > drytol) {
-            const double u = m[b][a][k] / d[b][a];
-            if (u < lo || u > hi) split = true;
-          }
-    }
-    out[k + 1] = !split ? m[b0][a0][k] : (S > 0.0 ? (4.0 * qc[k + 1]) * (hf / S) : 0.0);
-  }
-  if (hf <= drytol) {
-    out[1] = 0.0;
-    out[2] = 0.0;
-  }
+  double quad[2][2][3];
+  interp_children(e, s, L, I >> 1, J >> 1, bs, quad, err);
+  for (int f = 0; f < 3; ++f) out[f] = quad[J & 1][I & 1][f];
 }
 
 // Physical boundaries of one tile held in global memory: bottom/top over the
@@ -599,49 +617,21 @@ __global__ void k_subcycle_sync(const __grid_constant__ GfGeom G, const __grid_c
 // from the leaves by the ghost operators, then copied to the physical-boundary
 // ghost cells that mirror it.  Runs after each accepted step; the same-level
 // regions and the other boundary ghosts are written by the patch step.
+// Store (h, hu, hv) into ghost cell (i, j) of patch P's tile q (bed bt),
+// mark the patch to run in the next launch if the cell holds water, and
+// write the physical-boundary ghosts that mirror it (wall: reflected,
+// normal momentum negated; extrapolation: the edge cell into both layers).
 template <typename T>
-__global__ void k_ghost_other(const __grid_constant__ GfGeom G, const __grid_constant__ GfView V,
-                              const int* regs, int nreg, int* errflag) {
-  const int M = G.M, T_ = G.T, TT = T_ * T_;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long long)nreg * 2 * M) return;
-  const int code = regs[idx / (2 * M)];
-  const int k = (int)(idx % (2 * M));
-  const int p = code >> 3, r = code & 7;
-  int i, j;
-  if (r < 4) {
-    const int a = k % 2, b = k / 2;
-    if (r == 0) { i = -2 + a; j = b; }
-    else if (r == 1) { i = M + a; j = b; }
-    else if (r == 2) { i = b; j = -2 + a; }
-    else { i = b; j = M + a; }
-  } else {
-    if (k >= 4) return;
-    const int a = k & 1, b = k >> 1;
-    i = (r == 4 || r == 6) ? -2 + a : M + a;
-    j = (r == 4 || r == 5) ? -2 + b : M + b;
-  }
-  const GfPatch P = V.patch[p];
-  const GfCtl* C = V.ctl + P.scen;
-  if (!C->accepted) return;
-  Geo<T> e(G, V);
-  T* q = e.qp(p, e.cur_of(p));
+__device__ void store_ghost(const Geo<T>& e, const GfView& V, T* q, const GfPatch& P, int p,
+                            int i, int j, const double (&out)[3], double bt) {
+  const GfGeom& G = e.G;
+  const int M = G.M, TT = G.T * G.T;
   const int c = e.tix(i, j);
-  const long long I = (long long)P.px * M + i, J = (long long)P.py * M + j;
-  double bs[2][2];
-  child_beds(e, e.bp(p), i, j, bs);
-  const double bt = bs[j & 1][i & 1];
-  double out[3];
-  int err = 0;
-  fill_cell(e, P.scen, P.level, I, J, bs, out, &err);
-  if (err && errflag) *errflag = 1;
   e.store(q, c, out[0], out[1], out[2], bt);
   // water written into this patch's ghost cells: it runs in the next launch
   // (the patch step has flipped the parity, so sched[0] selects it)
   if (out[0] > 0.0 && V.runf != nullptr && V.sched != nullptr)
     V.runf[(size_t)(V.sched[0] & 1u) * V.runf_stride + p] = 1;
-  // physical-boundary ghosts mirroring this cell (wall: reflected, normal
-  // momentum negated; extrapolation: the edge cell into both layers)
   const int nxp = G.mi << P.level, nyp = G.mj << P.level;
   int xm[2], ym[2], nx = 0, ny = 0;
   T fx = T(1), fy = T(1);
@@ -671,6 +661,79 @@ __global__ void k_ghost_other(const __grid_constant__ GfGeom G, const __grid_con
   for (int b = 0; b < ny; ++b) put(i, ym[b], T(1), fy);
   for (int a = 0; a < nx; ++a)
     for (int b = 0; b < ny; ++b) put(xm[a], ym[b], fx, fy);
+}
+
+// Ghost cells of regions without a same-level neighbour, after each step.
+// regs[0, nquad) are regions next to a coarser leaf: one thread per 2 x 2
+// block of ghost cells (the children of one coarser cell, interpolated
+// together: the same values as cell by cell, a quarter of the work);
+// regs[nquad, nreg) are regions next to finer leaves: one thread per ghost
+// cell (the mean of its four finer cells).  Region r of patch p: 0 left,
+// 1 right, 2 bottom, 3 top (2 x M cells each), 4-7 the corners (2 x 2).
+template <typename T>
+__global__ void k_ghost_other(const __grid_constant__ GfGeom G, const __grid_constant__ GfView V,
+                              const int* regs, int nquad, int nreg, int* errflag) {
+  const int M = G.M;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nq_items = (long long)nquad * (M / 2);
+  const bool quad = idx < nq_items;
+  int code, k;
+  if (quad) {
+    code = regs[idx / (M / 2)];
+    k = (int)(idx % (M / 2));
+  } else {
+    const long long r2 = idx - nq_items;
+    if (r2 >= (long long)(nreg - nquad) * 2 * M) return;
+    code = regs[nquad + r2 / (2 * M)];
+    k = (int)(r2 % (2 * M));
+  }
+  const int p = code >> 3, r = code & 7;
+  int i, j;
+  if (quad) {
+    // lower-left cell of the block (even, like the coarser cell's children)
+    if (r >= 4 && k > 0) return;
+    if (r == 0) { i = -2; j = 2 * k; }
+    else if (r == 1) { i = M; j = 2 * k; }
+    else if (r == 2) { i = 2 * k; j = -2; }
+    else if (r == 3) { i = 2 * k; j = M; }
+    else {
+      i = (r == 4 || r == 6) ? -2 : M;
+      j = (r == 4 || r == 5) ? -2 : M;
+    }
+  } else if (r < 4) {
+    const int a = k % 2, b = k / 2;
+    if (r == 0) { i = -2 + a; j = b; }
+    else if (r == 1) { i = M + a; j = b; }
+    else if (r == 2) { i = b; j = -2 + a; }
+    else { i = b; j = M + a; }
+  } else {
+    if (k >= 4) return;
+    const int a = k & 1, b = k >> 1;
+    i = (r == 4 || r == 6) ? -2 + a : M + a;
+    j = (r == 4 || r == 5) ? -2 + b : M + b;
+  }
+  const GfPatch P = V.patch[p];
+  const GfCtl* C = V.ctl + P.scen;
+  if (!C->accepted) return;
+  Geo<T> e(G, V);
+  T* q = e.qp(p, e.cur_of(p));
+  const long long I = (long long)P.px * M + i, J = (long long)P.py * M + j;
+  double bs[2][2];
+  child_beds(e, e.bp(p), i, j, bs);
+  int err = 0;
+  if (quad) {
+    double out4[2][2][3];
+    interp_children(e, P.scen, P.level, I >> 1, J >> 1, bs, out4, &err);
+    if (err && errflag) *errflag = 1;
+    for (int b = 0; b < 2; ++b)
+      for (int a = 0; a < 2; ++a)
+        store_ghost(e, V, q, P, p, i + a, j + b, out4[b][a], bs[b][a]);
+    return;
+  }
+  double out[3];
+  fill_cell(e, P.scen, P.level, I, J, bs, out, &err);
+  if (err && errflag) *errflag = 1;
+  store_ghost(e, V, q, P, p, i, j, out, bs[j & 1][i & 1]);
 }
 
 // ------------------------------------------------------------ topography
@@ -817,22 +880,42 @@ __global__ void k_regrid_fill(const __grid_constant__ GfGeom G, const __grid_con
   T* q = en.qp(p, dst);
   const T* bn = en.bp(p);
   int err = 0;
-  for (int k = threadIdx.x; k < M * M; k += blockDim.x) {
-    const int i = k % M, j = k / M;
-    const long long I = (long long)P.px * M + i, J = (long long)P.py * M + j;
-    const int c = (i + GF_NG) + (j + GF_NG) * T_;
+  // by blocks of 2 x 2 cells (the children of one cell of level L - 1, all
+  // in this patch): a block that the old forest covers with a coarser leaf
+  // is interpolated in one go, any other cell by cell, with the same values
+  const int H = M / 2;
+  for (int k = threadIdx.x; k < H * H; k += blockDim.x) {
+    const int i0 = 2 * (k % H), j0 = 2 * (k / H);
+    const long long I0 = (long long)P.px * M + i0, J0 = (long long)P.py * M + j0;
     double bs[2][2];
-    child_beds(en, bn, i, j, bs);
-    const double bt = bs[j & 1][i & 1];
-    double out[3];
-    fill_cell(eo, P.scen, P.level, I, J, bs, out, &err);
-    en.store(q, c, out[0], out[1], out[2], bt);
-    if constexpr (Geo<T>::DEV) {
-      float* lo = N.lof[dst] + (size_t)p * 3 * M * M;
-      lo[k] = 0.0f;
-      lo[M * M + k] = 0.0f;
-      lo[2 * M * M + k] = 0.0f;
+    child_beds(en, bn, i0, j0, bs);
+    double out4[2][2][3];
+    bool coarse = P.level > 0 && eo.leaf(P.scen, P.level, I0, J0) < 0;
+    if (coarse) {
+      coarse = false;
+      for (int l = P.level - 1; l >= 0 && !coarse; --l)
+        coarse = eo.leaf(P.scen, l, I0 >> (P.level - l), J0 >> (P.level - l)) >= 0;
     }
+    if (coarse) {
+      interp_children(eo, P.scen, P.level, I0 >> 1, J0 >> 1, bs, out4, &err);
+    } else {
+      for (int b = 0; b < 2; ++b)
+        for (int a = 0; a < 2; ++a)
+          fill_cell(eo, P.scen, P.level, I0 + a, J0 + b, bs, out4[b][a], &err);
+    }
+    for (int b = 0; b < 2; ++b)
+      for (int a = 0; a < 2; ++a) {
+        const int i = i0 + a, j = j0 + b;
+        const int c = (i + GF_NG) + (j + GF_NG) * T_;
+        en.store(q, c, out4[b][a][0], out4[b][a][1], out4[b][a][2], bs[b][a]);
+        if constexpr (Geo<T>::DEV) {
+          const int kc = i + j * M;
+          float* lo = N.lof[dst] + (size_t)p * 3 * M * M;
+          lo[kc] = 0.0f;
+          lo[M * M + kc] = 0.0f;
+          lo[2 * M * M + kc] = 0.0f;
+        }
+      }
   }
   if (err && errflag) *errflag = 1;
 }
@@ -899,20 +982,31 @@ __global__ void k_tags(const __grid_constant__ GfGeom G, const __grid_constant__
   Geo<T> e(G, V);
   const int M = G.M;
   const int cur = V.ctl[P.scen].cur;
-  const GfScenario S = V.scen[P.scen];
-  const double dx = e.dx(P.level), dy = e.dy(P.level);
-  // surfaces are compared with eta0; the deviation form stores them relative
-  const double eref = Geo<T>::DEV ? 0.0 : S.eta0;
-  // the source box against the patch's first and last cell centres (the
-  // centres grow with the index, so the per-cell test is needed only for a
-  // patch that the box edge crosses)
-  auto xcen = [&](int i) { return G.xlower + ((double)((long long)P.px * M + i) + 0.5) * dx; };
-  auto ycen = [&](int j) { return G.ylower + ((double)((long long)P.py * M + j) + 0.5) * dy; };
-  const double x0 = xcen(0), x1 = xcen(M - 1), y0 = ycen(0), y1 = ycen(M - 1);
-  const bool box_none = x1 < G.src_box[0] || x0 > G.src_box[1] || y1 < G.src_box[2] ||
-                        y0 > G.src_box[3];
-  const bool box_all = x0 >= G.src_box[0] && x1 <= G.src_box[1] && y0 >= G.src_box[2] &&
-                       y1 <= G.src_box[3];
+  // per-patch FP64 scalars, computed once by thread 0 (an FP64 division in
+  // every thread would dominate the kernel on this part) and shared
+  __shared__ double sdx, sdy, seref;
+  __shared__ int sbox;  // bit 0: the box misses the patch, bit 1: covers it
+  auto xcen = [&](int i) { return G.xlower + ((double)((long long)P.px * M + i) + 0.5) * sdx; };
+  auto ycen = [&](int j) { return G.ylower + ((double)((long long)P.py * M + j) + 0.5) * sdy; };
+  if (threadIdx.x == 0) {
+    sdx = e.dx(P.level);
+    sdy = e.dy(P.level);
+    // surfaces are compared with eta0; the deviation form stores them
+    // relative to it
+    seref = Geo<T>::DEV ? 0.0 : V.scen[P.scen].eta0;
+    // the source box against the patch's first and last cell centres (the
+    // centres grow with the index, so the per-cell test is needed only for
+    // a patch that the box edge crosses)
+    const double x0 = xcen(0), x1 = xcen(M - 1), y0 = ycen(0), y1 = ycen(M - 1);
+    const bool none = x1 < G.src_box[0] || x0 > G.src_box[1] || y1 < G.src_box[2] ||
+                      y0 > G.src_box[3];
+    const bool all = x0 >= G.src_box[0] && x1 <= G.src_box[1] && y0 >= G.src_box[2] &&
+                     y1 <= G.src_box[3];
+    sbox = (none ? 1 : 0) | (all ? 2 : 0);
+  }
+  __syncthreads();
+  const double eref = seref;
+  const bool box_none = (sbox & 1) != 0, box_all = (sbox & 2) != 0;
   const int rbox = P.level < G.src_level ? 2 : 1;  // a cell in the box asks this
   int m = box_all ? rbox : 0;
   int gl = -1;  // the highest level a flow grade asks for (criterion 5)
@@ -1489,14 +1583,14 @@ int launch_ghost_fill(const GfGeom& g, const GfView& v, int only_accepted,
   return ok();
 }
 
-int launch_ghost_rest(const GfGeom& g, const GfView& v, const int* regs, int nreg,
-                      void* stream) {
+int launch_ghost_rest(const GfGeom& g, const GfView& v, const int* regs, int nquad,
+                      int nreg, void* stream) {
   if (nreg <= 0) return 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const long long total = (long long)nreg * 2 * g.M;
+  const long long total = (long long)nquad * (g.M / 2) + (long long)(nreg - nquad) * 2 * g.M;
   const int blocks = (int)((total + 255) / 256);
-  if (v.prec) k_ghost_other<float><<<blocks, 256, 0, st>>>(g, v, regs, nreg, g_errflag);
-  else k_ghost_other<double><<<blocks, 256, 0, st>>>(g, v, regs, nreg, g_errflag);
+  if (v.prec) k_ghost_other<float><<<blocks, 256, 0, st>>>(g, v, regs, nquad, nreg, g_errflag);
+  else k_ghost_other<double><<<blocks, 256, 0, st>>>(g, v, regs, nquad, nreg, g_errflag);
   return ok();
 }
 

@@ -96,6 +96,7 @@ struct geoflood_ctx {
   int* d_rpairs = nullptr;  // regrid: (new, old) slots to copy
   int* d_glist[2] = {nullptr, nullptr};  // ghost regions next to a level change
   int nglist[2] = {0, 0};
+  int nglist_c[2] = {0, 0};  // of which the first ones border a coarser leaf
   int* d_ilist[2] = {nullptr, nullptr};  // patches on the inflow side
   int nilist[2] = {0, 0};
   bool own_stream = false;
@@ -374,10 +375,24 @@ int upload_tables(geoflood_ctx* ctx, int t,
   }
   // ghost regions that no same-level neighbour pushes into (a finer or
   // coarser neighbour), as patch * 8 + region: filled after each step
-  std::vector<int> gl;
-  for (size_t k = 0; k < total; ++k)
-    for (int r = 0; r < 8; ++r)
-      if (nb[k * 8 + r] == GF_NBR_OTHER) gl.push_back((int)k * 8 + r);
+  // first those next to a coarser leaf, then those next to finer leaves
+  std::vector<int> gl, glf;
+  for (size_t k = 0; k < total; ++k) {
+    const GfPatch& P = hp[k];
+    for (int r = 0; r < 8; ++r) {
+      if (nb[k * 8 + r] != GF_NBR_OTHER) continue;
+      bool coarser = false;
+      if (P.level > 0) {
+        const long long X = (P.px + DX[r]) >> 1, Y = (P.py + DY[r]) >> 1;
+        const long long w = (long long)ctx->G.mi << (P.level - 1);
+        coarser = lut[(size_t)ctx->h_scen[P.scen].lut_off + ctx->G.lut_lev_off[P.level - 1] + X +
+                      Y * w] >= 0;
+      }
+      (coarser ? gl : glf).push_back((int)k * 8 + r);
+    }
+  }
+  ctx->nglist_c[t] = (int)gl.size();
+  gl.insert(gl.end(), glf.begin(), glf.end());
   ctx->nglist[t] = (int)gl.size();
   // patches on the inflow side whose tile lines (ghost lines included) may
   // reach the inflow segment
@@ -1206,7 +1221,8 @@ int geoflood_step(geoflood_ctx* ctx, double t_target, int max_steps,
           cudaEventRecordWithFlags(rg.a, ctx->st, cudaEventRecordExternal);
         }
         if (sub == ctx->G.sub_K - 1) lrc |= gf::launch_subcycle_sync(ctx->G, v, ctx->st);
-        lrc |= gf::launch_ghost_rest(ctx->G, v, ctx->d_glist[ctx->tsel], ctx->nglist[ctx->tsel],
+        lrc |= gf::launch_ghost_rest(ctx->G, v, ctx->d_glist[ctx->tsel],
+                                     ctx->nglist_c[ctx->tsel], ctx->nglist[ctx->tsel],
                                      ctx->st);
         lrc |= gf::launch_inflow(ctx->G, v, ctx->d_ilist[ctx->tsel], ctx->nilist[ctx->tsel], 1,
                                  ctx->st);
@@ -1310,15 +1326,21 @@ int geoflood_tags(geoflood_ctx* ctx, int s, uint8_t* flags) {
   return 0;
 }
 
-int geoflood_regrid(geoflood_ctx* ctx) {
+}  // extern "C"
+
+namespace {
+
+// A regrid; with misses non-null its tag pass also counts what the plain
+// criterion wants refined below the finest level (geoflood_check_tags's
+// count), so that a check due together with a regrid needs no pass of its
+// own.
+int regrid_impl(geoflood_ctx* ctx, int* misses) {
   if (!ctx) return GEOFLOOD_ERR_ARG;
   int rc = sync_ctl_down(ctx);
   if (rc) return rc;
-  if ((size_t)ctx->npatch > ctx->h_flags_cap) {
-    if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
-    ctx->h_flags = nullptr;
-    ctx->h_flags_cap = 0;
-    if (cudaMallocHost((void**)&ctx->h_flags, (size_t)ctx->cap) != cudaSuccess) {
+  if (!ctx->h_flags) {
+    // the tags of every patch, then the miss count
+    if (cudaMallocHost((void**)&ctx->h_flags, (size_t)ctx->cap + 16) != cudaSuccess) {
       cudaGetLastError();
       ctx->h_flags = nullptr;
       return fail(ctx, GEOFLOOD_ERR_OOM, "pinned tag buffer");
@@ -1326,9 +1348,19 @@ int geoflood_regrid(geoflood_ctx* ctx) {
     ctx->h_flags_cap = (size_t)ctx->cap;
   }
   const uint8_t* flags_h = ctx->h_flags;
-  if ((rc = tag_pass(ctx, ctx->cnn.tagger == GEOFLOOD_TAGGER_LEARNED, nullptr))) return rc;
+  unsigned* miss_h = reinterpret_cast<unsigned*>(ctx->h_flags + ((ctx->h_flags_cap + 3) & ~size_t(3)));
+  unsigned* miss_d = nullptr;
+  if (misses) {
+    if ((rc = cnn_alloc(ctx, (void**)&ctx->cnn.misses, sizeof(unsigned)))) return rc;
+    miss_d = ctx->cnn.misses;
+    CK(cudaMemsetAsync(miss_d, 0, sizeof(unsigned), ctx->st));
+  }
+  if ((rc = tag_pass(ctx, ctx->cnn.tagger == GEOFLOOD_TAGGER_LEARNED, miss_d))) return rc;
   CK(cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, ctx->npatch, cudaMemcpyDeviceToHost, ctx->st));
+  if (misses)
+    CK(cudaMemcpyAsync(miss_h, miss_d, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
+  if (misses) *misses = (int)*miss_h;
   // New forests, scenario by scenario (on several host threads when there
   // are many scenarios); a leaf present in both forests keeps its data
   // (copied from its old slot), a new one is computed from the old forest.
@@ -1465,6 +1497,12 @@ int geoflood_regrid(geoflood_ctx* ctx) {
   // lookup-error flag, which the fills above also set
   return ghost_fill_all(ctx);
 }
+
+}  // namespace
+
+extern "C" {
+
+int geoflood_regrid(geoflood_ctx* ctx) { return regrid_impl(ctx, nullptr); }
 
 int geoflood_mass(geoflood_ctx* ctx, int s, double* mass) {
   if (!valid_scen(ctx, s) || !mass) return fail(ctx, GEOFLOOD_ERR_ARG, "mass: bad argument");
@@ -1922,15 +1960,27 @@ int geoflood_advance(geoflood_ctx* ctx, double t_target, int regrid_interval,
     since += taken;
     if (done) break;
     if (taken == 0) return fail(ctx, GEOFLOOD_ERR_STATE, "advance: no progress");
-    // the plain criterion judges at every check
+    // the plain criterion judges at every check; a check that falls on a
+    // regrid is counted by the regrid's own tag pass
     int misses = 0;
+    const bool due = since >= regrid_interval;
+    if (due && !collect) {
+      t0 = clock::now();
+      rc = regrid_impl(ctx, &misses);
+      st.regrid_s += secs(t0);
+      if (rc) return rc;
+      st.checks++;
+      st.misses += misses;
+      st.regrids++;
+      since = 0;
+      continue;
+    }
     t0 = clock::now();
     rc = geoflood_check_tags(ctx, collect ? 1 : 0, &misses);
     st.check_s += secs(t0);
     if (rc) return rc;
     st.checks++;
     st.misses += misses;
-    const bool due = since >= regrid_interval;
     if (due || (on_miss && misses > 0)) {
       if (collect) {
         int total = 0;

@@ -211,9 +211,10 @@ int launch_ghost_fill(const GfGeom& g, const GfView& v, int only_active,
                       void* stream);
 // Ghost cells in regions without a same-level neighbour (which the patch
 // step's push leaves out) with their boundary mirrors: regs[k] = patch * 8 +
-// region, k < nreg.
-int launch_ghost_rest(const GfGeom& g, const GfView& v, const int* regs, int nreg,
-                      void* stream);
+// region, k < nreg; the first nquad regions border a coarser leaf (filled
+// by blocks of 2 x 2 children), the others finer leaves.
+int launch_ghost_rest(const GfGeom& g, const GfView& v, const int* regs, int nquad,
+                      int nreg, void* stream);
 // Inflow ghost cells (Sec. 5.1) of the n patches in list (patches on the
 // inflow side), after every other ghost cell is final; only_accepted: skip
 // scenarios whose last step was rejected.
