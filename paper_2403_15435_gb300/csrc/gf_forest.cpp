@@ -161,31 +161,23 @@ std::vector<Leaf> HostForest::regrid(const uint8_t* flags) const {
   std::vector<int> where(n0, -1);
   for (size_t k = 0; k < cur.size(); ++k)
     if (from[k] >= 0) where[from[k]] = (int)k;
-  // index of original leaves by position
-  std::unordered_set<uint64_t> orig;
-  for (size_t k = 0; k < n0; ++k) orig.insert(key(leaves_[k].level, leaves_[k].px, leaves_[k].py));
   std::vector<char> drop(cur.size(), 0);
   std::vector<Leaf> parents;
-  // map position -> original index for the sibling lookup
-  std::vector<std::pair<uint64_t, int>> pos;
-  pos.reserve(n0);
-  for (size_t k = 0; k < n0; ++k)
-    pos.emplace_back(key(leaves_[k].level, leaves_[k].px, leaves_[k].py), (int)k);
-  std::sort(pos.begin(), pos.end());
-  auto find = [&](int L, int x, int y) -> int {
-    const uint64_t kk = key(L, x, y);
-    auto it = std::lower_bound(pos.begin(), pos.end(), std::make_pair(kk, -1));
-    return (it != pos.end() && it->first == kk) ? it->second : -1;
-  };
+  // The leaves are in Morton order and four sibling leaves tile their
+  // parent, so a complete quartet occupies four consecutive entries, in the
+  // order (0,0), (1,0), (0,1), (1,1) of the children.
   for (size_t k = 0; k < n0; ++k) {
     const Leaf& l = leaves_[k];
     if (l.level <= minl_ || (l.px & 1) || (l.py & 1)) continue;
     int sib[4];
-    bool ok = true;
+    bool ok = k + 3 < n0;
     for (int c = 0; c < 4 && ok; ++c) {
-      const int o = find(l.level, l.px + (c & 1), l.py + (c >> 1));
-      if (o < 0 || flags[o] != 2 || where[o] < 0) ok = false;
-      else sib[c] = o;
+      const size_t o = k + c;
+      const Leaf& m = leaves_[o];
+      if (m.level != l.level || m.px != l.px + (c & 1) || m.py != l.py + (c >> 1) ||
+          flags[o] != 2 || where[o] < 0)
+        ok = false;
+      else sib[c] = (int)o;
     }
     if (!ok) continue;
     // parent at level L-1 spans 4x4 positions of level L+1
