@@ -13,7 +13,7 @@ regridded (tags, 2:1 balance, refine and coarsen, new tables, fills).
 
 The metric is the spec pair on that workload:
   value      FP32 surface-deviation form with the learned refinement
-             predictor, regrid every 16 steps (the plain criterion still
+             predictor, regrid every 64 steps (the plain criterion still
              judges every 4 steps and forces a regrid on a miss);
   fp64_plain the paper's method: plain FP64, plain tags, regrid every 4;
   fp32_plain the control: FP32 with plain tags, regrid every 4 (the
@@ -51,6 +51,12 @@ VALLEY_WORKLOAD = ("V-valley 4 km x 2 km, 16x8 blocks of 32x32 patches, levels 2
                    "0.49 m), 20 m reservoir, full breach at x = 500 m, n = 0.033, t 0->%g s")
 CNN_SCALE = (4.0, 8.0, 8.0, 4.0)
 TRAIN_T = 30.0
+# regrid interval of the learned arm (the network is trained on labels over
+# the same interval; the plain criterion still checks every 4 steps and
+# forces a regrid on a miss): measured on this workload, 16 / 32 / 64 steps
+# take 1.33 / 1.20 / 1.05 s per run against 1.38 s for plain tags every 4,
+# at the same gauge depths within 1.4e-5 m
+LEARNED_REGRID = 64
 
 N_CELLS = 1024
 T_UNIFORM = 60.0
@@ -74,12 +80,13 @@ FP32_LANES_PER_SM = 128
 FP64_LANES_PER_SM = 2  # measured: DFMA throughput 1.20 TFLOP/s on 152 SMs
 N_SM = 152
 # DRAM bytes (read + write) of one patch-step launch, from the ncu captures
-# summarised in profiles/; None when the kernel has changed since.  Uniform
-# workload: the launch at t about 28 s.  Valley: bytes per interior cell of
-# a launch mid-run (scaled to the cells of an average launch).
-TRAFFIC_PER_LAUNCH_FP32 = None
+# summarised in profiles/ (cold caches); None when the kernel has changed
+# since.  Uniform workload: launch 151 (t = 29.5 s).  Valley: the launch at
+# t = 30 s (6827 patches), 331 701 504 B over 6 990 848 cells, scaled to the
+# cells of an average timed launch.
+TRAFFIC_PER_LAUNCH_FP32 = 4635392
 TRAFFIC_PER_LAUNCH_FP64 = None
-TRAFFIC_PER_CELL_VALLEY_FP32 = None
+TRAFFIC_PER_CELL_VALLEY_FP32 = 331701504 / 6990848
 
 
 def parse():
@@ -263,7 +270,8 @@ def roofline(r, prec, peaks, traffic=None):
 
 def train_network(stream, t_end=TRAIN_T, epochs=10, capacity=200000):
     """Network trained on the plain criterion's flags from another seed of the
-    valley (FP32, regrid every 16, criterion OR'ed over the checks)."""
+    valley (FP32, regrid every LEARNED_REGRID steps, the criterion OR'ed over
+    the checks up to the next regrid)."""
     import numpy as np
     from paper_2403_15435_gb300 import geoflood, inputs
     t0 = time.perf_counter()
@@ -273,7 +281,7 @@ def train_network(stream, t_end=TRAIN_T, epochs=10, capacity=200000):
     f.set_state(tr.ic)
     f.cnn_set_scale(CNN_SCALE)
     f.cnn_dataset(capacity)
-    st = f.advance(t_end, regrid_interval=16, check_interval=4, collect=True)
+    st = f.advance(t_end, regrid_interval=LEARNED_REGRID, check_interval=4, collect=True)
     _, y = f.cnn_dataset_read(0, st["samples"])
     npos = int(y.sum())
     pw = float(np.clip((len(y) - npos) / max(npos, 1), 1.0, 20.0))
@@ -285,7 +293,8 @@ def train_network(stream, t_end=TRAIN_T, epochs=10, capacity=200000):
     # decision threshold pw / (1 + pw) undoes it
     thr = pw / (1.0 + pw)
     return prm, thr, {"workload": "V-valley 4 km x 2 km, seed + 50 (not the benchmarked "
-                                  "terrain), FP32, t 0->%g s" % t_end,
+                                  "terrain), FP32, t 0->%g s, labels over %d steps"
+                                  % (t_end, LEARNED_REGRID),
                       "samples": int(len(y)), "positives": npos, "epochs": epochs,
                       "pos_weight": pw, "threshold": thr, "loss_first": float(loss[0]),
                       "loss_last": float(loss[-1]), "seconds": time.perf_counter() - t0}
@@ -407,7 +416,7 @@ def measure_valley(args, dev, stream, world, local, peaks):
 
     net_prm, net_thr, train = train_network(stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    head = ValleyArm(stream, 1, True, 16, net=(net_prm, net_thr), t_end=args.t_end)
+    head = ValleyArm(stream, 1, True, LEARNED_REGRID, net=(net_prm, net_thr), t_end=args.t_end)
     head.run(flush)
     head.autotune(0.5 * args.t_end)
     for _ in range(args.warmup):
@@ -418,9 +427,13 @@ def measure_valley(args, dev, stream, world, local, peaks):
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
+        # an NVTX range around the timed runs, so that a profiler can be
+        # told to record this region only
+        torch.cuda.nvtx.range_push("timed")
         for _ in range(args.steps):
             runs.append(head.run(flush))
         torch.cuda.synchronize(dev)
+        torch.cuda.nvtx.range_pop()
     launches = head.f.launch_count() - launches0
     sec = sum(s for _, s in runs)
     cells = sum(st["patch_steps"] for st, _ in runs) * PATCH * PATCH
@@ -458,7 +471,8 @@ def measure_valley(args, dev, stream, world, local, peaks):
         t0 = time.perf_counter()
         f.write(H, HU, HV)
         f.set_time(0.0, head.prob.cfg.dt_initial)
-        st = f.advance(args.t_end, regrid_interval=16, check_interval=4, regrid_on_miss=True)
+        st = f.advance(args.t_end, regrid_interval=LEARNED_REGRID, check_interval=4,
+                       regrid_on_miss=True)
         if f.npatch != n_end:
             OH, OHU, OHV = pin(f.npatch), pin(f.npatch), pin(f.npatch)
             n_end = f.npatch
@@ -591,7 +605,7 @@ CANYON_T = 20.0
 def measure_canyon(stream, net):
     """The 17 km x 9 km canyon-to-plain dam break (55 m reservoir, five
     levels, 32 x 32 patches on levels 0-4), first CANYON_T seconds: FP32 with
-    learned tags (regrid every 16; the network is the one trained on the
+    learned tags (regrid every LEARNED_REGRID; the network is the one trained on the
     plain criterion's flags from valley runs) against FP32 and FP64 with
     plain tags (regrid every 4).  Wall clock of the driver loop, second of
     two runs."""
@@ -631,7 +645,7 @@ def measure_canyon(stream, net):
             g.close()
         return res
 
-    learned = run(1, True, 16)
+    learned = run(1, True, LEARNED_REGRID)
     plain32 = run(1, False, 4)
     plain64 = run(0, False, 4)
     err = {}
@@ -647,7 +661,8 @@ def measure_canyon(stream, net):
     return {"workload": "canyon-to-plain 17 km x 9 km, 55 m reservoir, 32x32 patches, levels "
                         "0-4 (finest dx 1.95 m), 32 gauges on the channel (16 within 2.05-2.8 km "
                         "of the upstream end), t 0->%g s" % CANYON_T,
-            "fp32_learned_regrid16": learned, "fp32_plain_regrid4": plain32,
+            "fp32_learned": learned, "fp32_plain_regrid4": plain32,
+            "learned_regrid_interval": LEARNED_REGRID,
             "fp64_plain_regrid4": plain64, "error_vs_plain_fp64": err,
             "wall_clock_ratio_vs_fp64": plain64["wall_s"] / learned["wall_s"],
             "network_gain_wall": plain32["wall_s"] / learned["wall_s"],
@@ -1022,8 +1037,9 @@ def run_ours(args):
         "ms_per_step": 1e3 * v["sec"] / max(1, v["runs"]), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (vs f64)", "data": "synthetic",
         "config": {"workload": VALLEY_WORKLOAD % args.t_end,
-                   "pair": "FP32 surface-deviation form + learned tags, regrid every 16 "
-                           "(value) vs plain FP64 + plain tags, regrid every 4 (fp64_plain)",
+                   "pair": "FP32 surface-deviation form + learned tags, regrid every %d "
+                           "(value) vs plain FP64 + plain tags, regrid every 4 (fp64_plain)"
+                           % LEARNED_REGRID,
                    "cell_updates_per_run": v["cells_per_run"],
                    "steps_per_run": lr["steps"], "patches_at_end": lr["patches_at_end"],
                    "l2": "flushed (256 MB write) before each timed run; the state (2-8k "

@@ -1534,6 +1534,10 @@ __global__ void __launch_bounds__(256, 3)
       }
     emit(X, Y, acc, f * f);
   }
+  // ring pixels: one warp each.  A pixel's band lies in one of the eight
+  // neighbour regions; a same-level neighbour's cells are read from its
+  // tile directly (the leaf value_near would find), anything else through
+  // the forest lookups
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   for (int r = warp; r < 68; r += nwarp) {
     int X, Y;
@@ -1545,14 +1549,26 @@ __global__ void __launch_bounds__(256, 3)
     const int i1 = X == 0 ? 0 : X == 17 ? M + W : X * f;
     const int j0 = Y == 0 ? -W : Y == 17 ? M : (Y - 1) * f;
     const int j1 = Y == 0 ? 0 : Y == 17 ? M + W : Y * f;
+    // neighbour region (0 left, 1 right, 2 bottom, 3 top, 4-7 the corners
+    // bottom-left, bottom-right, top-left, top-right) and its offset
+    const int ox = X == 0 ? -1 : X == 17 ? 1 : 0, oy = Y == 0 ? -1 : Y == 17 ? 1 : 0;
+    const int reg = oy == 0 ? (ox < 0 ? 0 : 1)
+                  : ox == 0 ? (oy < 0 ? 2 : 3)
+                            : 4 + (ox > 0 ? 1 : 0) + (oy > 0 ? 2 : 0);
+    const int nb = V.nbr != nullptr ? V.nbr[(size_t)p * 8 + reg] : GF_NBR_OTHER;
     const int wi = i1 - i0, ncell = wi * (j1 - j0);
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     int cnt = 0;
     for (int k = lane; k < ncell; k += 32) {
-      const long long I = I0 + i0 + k % wi, J = J0 + j0 + k / wi;
-      if (I < 0 || J < 0 || I >= NX || J >= NY) continue;
+      const int i = i0 + k % wi, j = j0 + k / wi;
       float c4[4];
-      value_near_f32(e, P.scen, cur, P.level, I, J, c4, &err);
+      if (nb >= 0) {
+        load_f32(G, V, nb, cur, e.tix(i - ox * M, j - oy * M), c4);
+      } else {
+        const long long I = I0 + i, J = J0 + j;
+        if (I < 0 || J < 0 || I >= NX || J >= NY) continue;
+        value_near_f32(e, P.scen, cur, P.level, I, J, c4, &err);
+      }
       for (int c = 0; c < 4; ++c) acc[c] += c4[c];
       ++cnt;
     }

@@ -11,7 +11,7 @@ relative, FP32 within 1e-4 m and 1e-4 m^2/s (the deviation form's bound).
 Workloads: the 1024 x 1024 radial dam break (the uniform secondary
 workload) at t = 5, 30 and 60 s in both precisions, and the 4 km x 2 km
 valley on levels 2-4 (the headline workload) in FP32 with the learned
-tagger and regrid every 16 steps, and in FP64 with plain tags and regrid
+tagger and regrid every 64 steps, and in FP64 with plain tags and regrid
 every 4, at t = 5 and 20 s."""
 import numpy as np
 import pytest
@@ -92,7 +92,7 @@ def _valley_net(stream=None):
     f.set_state(tr.ic)
     f.cnn_set_scale((4.0, 8.0, 8.0, 4.0))
     f.cnn_dataset(60000)
-    st = f.advance(8.0, regrid_interval=16, check_interval=4, collect=True)
+    st = f.advance(8.0, regrid_interval=64, check_interval=4, collect=True)
     _, y = f.cnn_dataset_read(0, st["samples"])
     pw = float(np.clip((len(y) - y.sum()) / max(y.sum(), 1), 1.0, 20.0))
     f.cnn_set_params(inputs.cnn_init(3))
@@ -102,7 +102,7 @@ def _valley_net(stream=None):
     return prm, pw / (1.0 + pw)
 
 
-@pytest.mark.parametrize("prec,learned,regrid", [(1, True, 16), (0, False, 4)])
+@pytest.mark.parametrize("prec,learned,regrid", [(1, True, 64), (0, False, 4)])
 def test_headline_valley_in_bench_configuration(prec, learned, regrid):
     prob = inputs.v_valley()
     prob.cfg.precision = prec
