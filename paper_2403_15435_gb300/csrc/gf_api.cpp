@@ -159,7 +159,7 @@ struct geoflood_ctx {
 namespace {
 
 // Device memory the bed cache may take (all scenarios, all levels).
-constexpr size_t kBedCacheBudget = size_t(4) << 30;
+constexpr size_t kBedCacheBudget = size_t(16) << 30;
 
 int fail(geoflood_ctx* c, int code, const std::string& msg) {
   if (c) c->err = msg;

@@ -29,6 +29,10 @@ int launch_patch_step_f32(const GfGeom& g, const GfView& v, int variant,
     return gfs::launch_step<gfs::PrecF32, 32, 16, 352, 3>(g, v, st);
   if (g.M == 32 && variant == 5)
     return gfs::launch_step<gfs::PrecF32, 32, 16, 320, 4>(g, v, st);
+  // adaptive: four 16 x 16 sub-tile CTAs for each patch wet in the previous
+  // launch, one whole-tile check (and dry update) for every other patch
+  if (g.M == 32 && variant == 6)
+    return gfs::launch_step_adaptive<gfs::PrecF32, 32, 16, 352, 1>(g, v, st);
   if (g.M == 32) return gfs::launch_step<gfs::PrecF32, 32, 32, 512, 2>(g, v, st);
   if (g.M == 16) return gfs::launch_step<gfs::PrecF32, 16, 16, 352, 2>(g, v, st);
   return -1;

@@ -528,9 +528,14 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
     const R* sn = dir == 0 ? shu : shv;  // normal momentum
     const R* st = dir == 0 ? shv : shu;  // transverse momentum
     const R nu = dir == 0 ? nux : nuy;
-    // phase 1: Riemann solves on the lines, edges -1..M+1
+    // phase 1: Riemann solves on the lines, edges -1..M+1.  Consecutive
+    // threads take consecutive cells of a row: along the row in the x sweep,
+    // across the lines in the y sweep (a column walk would make every tile
+    // load a 4-way shared-memory bank conflict); each edge's wave planes
+    // keep their place, so the work is the same whichever thread does it
     for (int k = tid; k < NRL * NE; k += NT) {
-      const int line = k / NE + L0, a = k % NE - 1;
+      const int line = (dir == 0 ? k / NE : k % NRL) + L0;
+      const int a = (dir == 0 ? k % NE : k / NRL) - 1;
       const int cl = dir == 0 ? tix<M>(a - 1, line) : tix<M>(line, a - 1);
       const int cr = dir == 0 ? tix<M>(a, line) : tix<M>(line, a);
       R Z[9], S[3];
@@ -538,8 +543,9 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
           gfk::Side<R>{sdep[cl], sn[cl], st[cl], sb[cl], s0[cl], wetc(cl)},
           gfk::Side<R>{sdep[cr], sn[cr], st[cr], sb[cr], s0[cr], wetc(cr)}, g,
           rdry, Z, S);
-      // waves in planes: component q of edge k at W[q * NEDGE + k]
-      R* w = W + k;
+      // waves in planes: component q of edge e at W[q * NEDGE + e], e the
+      // edge's place (line, a) in the sweep
+      R* w = W + ((line - L0) * NE + a + 1);
 #pragma unroll
       for (int q = 0; q < 9; ++q) w[q * NEDGE] = Z[q];
       w[9 * NEDGE] = S[0];
@@ -722,6 +728,19 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
   // ------------------------------------------------ update, friction, out
   const R mn = rscal[4];
   bool bad = false;
+  // the compensation terms of every owned cell requested at once, so that
+  // their global loads overlap instead of one wait per cell
+  float lpre[DEV && !DS ? RC : 1][3];
+  if constexpr (DEV && !DS) {
+#pragma unroll
+    for (int r = 0; r < RC; ++r) {
+      const int k = tid + r * NT;
+      const int kp = k < M * M ? pix(k % M, k / M) : 0;
+#pragma unroll
+      for (int f = 0; f < 3; ++f)
+        lpre[r][f] = (anywet && k < M * M) ? los[f * MP * MP + kp] : 0.0f;
+    }
+  }
 #pragma unroll
   for (int r = 0; r < RC; ++r) {
     const int k = tid + r * NT;
@@ -775,7 +794,7 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
         const float* ga = Gtr + 3 * (i * (M + 1) + j);
         const float tf =
             trv ? nux * (fa[3 + f] - fa[f]) + nuy * (ga[3 + f] - ga[f]) : 0.0f;
-        const float lin = DS ? LO1[DS && DEV ? r : 0][f] : los[f * MP * MP + kp];
+        const float lin = DS ? LO1[DS && DEV ? r : 0][f] : lpre[DS ? 0 : r][f];
         const float x = (lin - fl) - tf;
         const float s = q[f] + x;
         const float bb = s - q[f];
