@@ -330,7 +330,7 @@ int geoflood_counters(geoflood_ctx* ctx, int scenario, long long* cell_updates,
  * halo staging): times every available variant reps times on the current
  * state (without advancing it), selects the fastest for this context and
  * returns its number in *variant and the times (ms per launch) in
- * ms_per_variant (one entry per variant, at most 16: seven for 32 x 32
+ * ms_per_variant (one entry per variant, at most 16: eight for 32 x 32
  * patches in FP32, four in FP64, one for 16 x 16; either pointer may be
  * NULL).  Variants of
  * 32 x 32 patches: 0 = one 512-thread CTA per patch staging the whole tile
@@ -340,8 +340,9 @@ int geoflood_counters(geoflood_ctx* ctx, int scenario, long long* cell_updates,
  * CTA per patch; FP64: adaptive (four sub-tile CTAs for each patch that held
  * water in the previous step, one CTA that checks the whole tile for every
  * other patch); FP32 only: 4 = the sub-tiles of 1 with three 352-thread CTAs
- * per SM, 5 = with four 320-thread CTAs per SM, 6 = adaptive as FP64's 3.
- * Results do not depend on the variant. */
+ * per SM, 5 = with four 320-thread CTAs per SM, 6 = adaptive as FP64's 3,
+ * 7 = one 608-thread CTA per patch, two per SM.  Results do not depend on
+ * the variant. */
 int geoflood_autotune(geoflood_ctx* ctx, int reps, int* variant,
                       double* ms_per_variant);
 

@@ -77,7 +77,7 @@ namespace gf {
 // single variant 0.  Dimensionally split stepping has one kernel per patch
 // size (whole-patch CTAs).
 int patch_step_variants(int mx, int prec, int dim_split) {
-  return dim_split ? 1 : (mx == 32 ? (prec ? 7 : 4) : 1);
+  return dim_split ? 1 : (mx == 32 ? (prec ? 8 : 4) : 1);
 }
 
 int launch_patch_step_f64(const GfGeom& g, const GfView& v, int variant,

@@ -33,6 +33,10 @@ int launch_patch_step_f32(const GfGeom& g, const GfView& v, int variant,
   // launch, one whole-tile check (and dry update) for every other patch
   if (g.M == 32 && variant == 6)
     return gfs::launch_step_adaptive<gfs::PrecF32, 32, 16, 352, 1>(g, v, st);
+  // 608 threads, two CTAs per SM: every sweep phase in two rounds instead of
+  // three (48 registers, a few bytes spilled)
+  if (g.M == 32 && variant == 7)
+    return gfs::launch_step<gfs::PrecF32, 32, 32, 608, 2>(g, v, st);
   if (g.M == 32) return gfs::launch_step<gfs::PrecF32, 32, 32, 512, 2>(g, v, st);
   if (g.M == 16) return gfs::launch_step<gfs::PrecF32, 16, 16, 352, 2>(g, v, st);
   return -1;
