@@ -9,6 +9,7 @@
 #include <cstdint>
 
 #include "gf_internal.h"
+#include "gf_solver.cuh"
 
 namespace {
 
@@ -363,6 +364,11 @@ __device__ void tile_bc(const G2& e, const GfPatch& P, T* q, T* bfield,
   }
 }
 
+// FP32 ghost operator (defined with the level-change ghosts below).
+__device__ void fill_cell_f32(const Geo<float>& e, int s, int cur, int L, long long I,
+                              long long J, const float (&bs)[2][2], float (&out)[3],
+                              int* err);
+
 // Ghost fill: one CTA per patch, one thread per ghost cell.  Interior-domain
 // ghosts from the leaves (reads only leaf interiors, so patches are
 // independent), then the physical boundaries.  A ghost cell in a region
@@ -423,6 +429,18 @@ __global__ void k_ghost_fill(const __grid_constant__ GfGeom G, const __grid_cons
       q[TT + c] = a1;
       q[2 * TT + c] = a2;
       continue;
+    }
+    if constexpr (Geo<T>::DEV) {
+      if (!G.subcycle) {
+        float bs[2][2], out[3];
+        for (int b = 0; b < 2; ++b)
+          for (int a = 0; a < 2; ++a) bs[b][a] = bb[e.tix((i & ~1) + a, (j & ~1) + b)];
+        fill_cell_f32(e, P.scen, cur, P.level, I, J, bs, out, &err);
+        q[c] = out[0];
+        q[TT + c] = out[1];
+        q[2 * TT + c] = out[2];
+        continue;
+      }
     }
     double bs[2][2];
     child_beds(e, bb, i, j, bs);
@@ -622,15 +640,26 @@ __global__ void k_subcycle_sync(const __grid_constant__ GfGeom G, const __grid_c
 // write the physical-boundary ghosts that mirror it (wall: reflected,
 // normal momentum negated; extrapolation: the edge cell into both layers).
 template <typename T>
+__device__ void mark_and_mirror(const Geo<T>& e, const GfView& V, T* q, const GfPatch& P,
+                                int p, int i, int j, bool water);
+
+template <typename T>
 __device__ void store_ghost(const Geo<T>& e, const GfView& V, T* q, const GfPatch& P, int p,
                             int i, int j, const double (&out)[3], double bt) {
+  e.store(q, e.tix(i, j), out[0], out[1], out[2], bt);
+  mark_and_mirror(e, V, q, P, p, i, j, out[0] > 0.0);
+}
+
+// The second half of store_ghost, once ghost cell (i, j) holds its value.
+template <typename T>
+__device__ void mark_and_mirror(const Geo<T>& e, const GfView& V, T* q, const GfPatch& P,
+                                int p, int i, int j, bool water) {
   const GfGeom& G = e.G;
   const int M = G.M, TT = G.T * G.T;
   const int c = e.tix(i, j);
-  e.store(q, c, out[0], out[1], out[2], bt);
   // water written into this patch's ghost cells: it runs in the next launch
   // (the patch step has flipped the parity, so sched[0] selects it)
-  if (out[0] > 0.0 && V.runf != nullptr && V.sched != nullptr)
+  if (water && V.runf != nullptr && V.sched != nullptr)
     V.runf[(size_t)(V.sched[0] & 1u) * V.runf_stride + p] = 1;
   const int nxp = G.mi << P.level, nyp = G.mj << P.level;
   int xm[2], ym[2], nx = 0, ny = 0;
@@ -663,6 +692,225 @@ __device__ void store_ghost(const Geo<T>& e, const GfView& V, T* q, const GfPatc
     for (int b = 0; b < ny; ++b) put(xm[a], ym[b], fx, fy);
 }
 
+// ------------------------------------------- level-change ghosts in FP32
+//
+// The FP32 deviation form's ghost operators, for forests without level
+// subcycling: the same rules as value_at / interp_children / fill_cell, in
+// FP32 arithmetic (FP64 runs at a small fraction of the FP32 rate on this
+// part).  They carry the stored surface w = h + b - eta0 instead of the
+// depth, so that the means and limited slopes of still water are exactly
+// zero and a wet child's stored surface is the interpolated surface itself;
+// the wet tests are the patch step's exact ones (wet_dev), so every wet/dry
+// decision is the one the FP64 operators take on the same stored values.
+
+// (w, hu, hv, b) of cell c of patch p in buffer cur
+__device__ __forceinline__ void load_surf(const Geo<float>& e, int p, int cur, int c,
+                                          float (&o)[4]) {
+  const int TT = e.G.T * e.G.T;
+  const float* q = e.V.qf[cur] + (size_t)p * 3 * TT;
+  o[0] = q[c];
+  o[1] = q[TT + c];
+  o[2] = q[2 * TT + c];
+  o[3] = e.V.bf[(size_t)p * TT + c];
+}
+
+// value_at's composite in FP64 with the surface in place of the depth: the
+// rare lookups (a leaf two levels coarser, cells two levels finer), kept out
+// of line so that its FP64 arrays stay out of the callers' registers.
+__device__ __noinline__ void surf_at_f64(const Geo<float>& e, int s, int L, long long I,
+                                         long long J, float (&o)[4], int* err) {
+  double d[4];
+  value_at(e, s, L, I, J, d, err);
+  o[0] = (float)(d[0] + d[3]);
+  o[1] = (float)d[1];
+  o[2] = (float)d[2];
+  o[3] = (float)d[3];
+}
+
+// (w, hu, hv, b) of cell (I, J) of level L: the leaf of level L or L - 1,
+// the mean of four leaves of level L + 1, else the FP64 composite.
+__device__ void surf_near_f32(const Geo<float>& e, int s, int cur, int L, long long I,
+                              long long J, float (&o)[4], int* err) {
+  for (int l = L; l >= L - 1 && l >= 0; --l) {
+    const long long Il = I >> (L - l), Jl = J >> (L - l);
+    const int p = e.leaf(s, l, Il, Jl);
+    if (p >= 0) {
+      load_surf(e, p, cur, e.local(Il, Jl), o);
+      return;
+    }
+  }
+  if (L + 1 <= e.G.maxlevel) {
+    int pc[4];
+    bool all = true;
+    for (int ch = 0; ch < 4; ++ch) {
+      pc[ch] = e.leaf(s, L + 1, 2 * I + (ch & 1), 2 * J + (ch >> 1));
+      all = all && pc[ch] >= 0;
+    }
+    if (all) {
+      float v[4][4];
+      for (int ch = 0; ch < 4; ++ch)
+        load_surf(e, pc[ch], cur, e.local(2 * I + (ch & 1), 2 * J + (ch >> 1)), v[ch]);
+      for (int f = 0; f < 4; ++f)
+        o[f] = 0.25f * ((v[0][f] + v[1][f]) + (v[2][f] + v[3][f]));
+      return;
+    }
+  }
+  surf_at_f64(e, s, L, I, J, o, err);
+}
+
+__device__ __forceinline__ float minmodf(float a, float b) {
+  if (a * b <= 0.0f) return 0.0f;
+  return fabsf(a) < fabsf(b) ? a : b;
+}
+
+__device__ __forceinline__ bool wet_f32(const GfGeom& G, float w, float b) {
+  return gfk::wet_dev(w, b, G.drytol, G.drytolf, G.marginf);
+}
+
+// interp_children in FP32: out[b][a] = (w, hu, hv) of child (2 ic + a,
+// 2 jc + b) of level L, whose bed is bs[b][a].
+__device__ void interp_children_f32(const Geo<float>& e, int s, int cur, int L, long long ic,
+                                    long long jc, const float (&bs)[2][2],
+                                    float (&out)[2][2][3], int* err) {
+  const GfGeom& G = e.G;
+  const long long NXc = e.nx(L - 1), NYc = e.ny(L - 1);
+  float nb[3][3][4];
+  bool in[3][3], wt[3][3];
+  for (int dj = -1; dj <= 1; ++dj)
+    for (int di = -1; di <= 1; ++di) {
+      const long long x = ic + di, y = jc + dj;
+      const bool ok = x >= 0 && y >= 0 && x < NXc && y < NYc;
+      in[dj + 1][di + 1] = ok;
+      wt[dj + 1][di + 1] = false;
+      if (ok) {
+        surf_near_f32(e, s, cur, L - 1, x, y, nb[dj + 1][di + 1], err);
+        wt[dj + 1][di + 1] = wet_f32(G, nb[dj + 1][di + 1][0], nb[dj + 1][di + 1][3]);
+      }
+    }
+  const float* qc = nb[1][1];
+  if (!wt[1][1]) {
+    // a dry coarse cell: its depth and momenta in every child
+    const float hc = qc[0] - qc[3];
+    for (int b = 0; b < 2; ++b)
+      for (int a = 0; a < 2; ++a) {
+        out[b][a][0] = hc + bs[b][a];
+        out[b][a][1] = qc[1];
+        out[b][a][2] = qc[2];
+      }
+    return;
+  }
+  bool allwet = true;
+  for (int dj = 0; dj < 3; ++dj)
+    for (int di = 0; di < 3; ++di)
+      if (in[dj][di] && !wt[dj][di]) allwet = false;
+  // limited slopes over the coarse cell: surface, then both momenta
+  float g[3][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+  if (allwet) {
+    const bool hx = in[1][0] && in[1][2], hy = in[0][1] && in[2][1];
+    for (int k = 0; k < 3; ++k) {
+      if (hx) g[k][0] = minmodf(nb[1][2][k] - qc[k], qc[k] - nb[1][0][k]);
+      if (hy) g[k][1] = minmodf(nb[2][1][k] - qc[k], qc[k] - nb[0][1][k]);
+    }
+  }
+  // the four children: surface eta, depth d, linearly interpolated momenta m
+  float eta[2][2], d[2][2], m[2][2][2];
+  bool cw[2][2];
+  for (int b = 0; b < 2; ++b)
+    for (int a = 0; a < 2; ++a) {
+      const float sx = a ? 0.25f : -0.25f, sy = b ? 0.25f : -0.25f;
+      eta[b][a] = allwet ? (qc[0] + sx * g[0][0]) + sy * g[0][1] : qc[0];
+      const float h = eta[b][a] - bs[b][a];
+      d[b][a] = h > 0.0f ? h : 0.0f;
+      cw[b][a] = wet_f32(G, eta[b][a], bs[b][a]);
+      for (int k = 0; k < 2; ++k)
+        m[b][a][k] = (qc[k + 1] + sx * g[k + 1][0]) + sy * g[k + 1][1];
+    }
+  const float S = (d[0][0] + d[0][1]) + (d[1][0] + d[1][1]);
+  bool split[2];
+  for (int k = 0; k < 2; ++k) {
+    split[k] = !allwet;
+    if (allwet) {
+      float lo = INFINITY, hi = -INFINITY;
+      for (int dj = 0; dj < 3; ++dj)
+        for (int di = 0; di < 3; ++di)
+          if (in[dj][di]) {
+            const float u = nb[dj][di][k + 1] / (nb[dj][di][0] - nb[dj][di][3]);
+            lo = fminf(lo, u);
+            hi = fmaxf(hi, u);
+          }
+      for (int b = 0; b < 2; ++b)
+        for (int a = 0; a < 2; ++a)
+          if (cw[b][a]) {
+            const float u = m[b][a][k] / d[b][a];
+            if (u < lo || u > hi) split[k] = true;
+          }
+    }
+  }
+  for (int b = 0; b < 2; ++b)
+    for (int a = 0; a < 2; ++a) {
+      // a child with water stores the interpolated surface itself
+      out[b][a][0] = eta[b][a] > bs[b][a] ? eta[b][a] : bs[b][a];
+      for (int k = 0; k < 2; ++k)
+        out[b][a][k + 1] = !cw[b][a] ? 0.0f
+                           : !split[k] ? m[b][a][k]
+                                       : (S > 0.0f ? (4.0f * qc[k + 1]) * (d[b][a] / S) : 0.0f);
+    }
+}
+
+// fill_cell in FP32: (w, hu, hv) of cell (I, J) of level L, whose parent's
+// four children have the beds bs (bs[J & 1][I & 1] is this cell's).
+__device__ void fill_cell_f32(const Geo<float>& e, int s, int cur, int L, long long I,
+                              long long J, const float (&bs)[2][2], float (&out)[3],
+                              int* err) {
+  const float bt = bs[J & 1][I & 1];
+  const int p = e.leaf(s, L, I, J);
+  if (p >= 0) {
+    float o4[4];
+    load_surf(e, p, cur, e.local(I, J), o4);
+    out[0] = o4[0];
+    out[1] = o4[1];
+    out[2] = o4[2];
+    return;
+  }
+  bool coarser = false;
+  for (int l = L - 1; l >= 0 && !coarser; --l)
+    coarser = e.leaf(s, l, I >> (L - l), J >> (L - l)) >= 0;
+  if (coarser) {
+    float quad[2][2][3];
+    interp_children_f32(e, s, cur, L, I >> 1, J >> 1, bs, quad, err);
+    for (int f = 0; f < 3; ++f) out[f] = quad[J & 1][I & 1][f];
+    return;
+  }
+  float v[4][4];
+  bool all = true;
+  for (int ch = 0; ch < 4; ++ch) {
+    surf_near_f32(e, s, cur, L + 1, 2 * I + (ch & 1), 2 * J + (ch >> 1), v[ch], err);
+    all = all && wet_f32(e.G, v[ch][0], v[ch][3]);
+  }
+  for (int f = 1; f < 3; ++f) out[f] = 0.25f * ((v[0][f] + v[1][f]) + (v[2][f] + v[3][f]));
+  if (all) {
+    // four wet children: their mean stored surface
+    const float w = 0.25f * ((v[0][0] + v[1][0]) + (v[2][0] + v[3][0]));
+    out[0] = w > bt ? w : bt;
+  } else {
+    float h[4];
+    for (int ch = 0; ch < 4; ++ch) h[ch] = v[ch][0] - v[ch][3];
+    out[0] = 0.25f * ((h[0] + h[1]) + (h[2] + h[3])) + bt;
+  }
+}
+
+// Store (w, hu, hv) into ghost cell (i, j) of patch P's tile q (bed bt),
+// then mark and mirror as store_ghost does.
+__device__ void store_ghost_f32(const Geo<float>& e, const GfView& V, float* q,
+                                const GfPatch& P, int p, int i, int j,
+                                const float (&out)[3], float bt) {
+  const int TT = e.G.T * e.G.T, c = e.tix(i, j);
+  q[c] = out[0];
+  q[TT + c] = out[1];
+  q[2 * TT + c] = out[2];
+  mark_and_mirror(e, V, q, P, p, i, j, out[0] > bt);
+}
+
 // Ghost cells of regions without a same-level neighbour, after each step.
 // regs[0, nquad) are regions next to a coarser leaf: one thread per 2 x 2
 // block of ghost cells (the children of one coarser cell, interpolated
@@ -670,8 +918,9 @@ __device__ void store_ghost(const Geo<T>& e, const GfView& V, T* q, const GfPatc
 // regs[nquad, nreg) are regions next to finer leaves: one thread per ghost
 // cell (the mean of its four finer cells).  Region r of patch p: 0 left,
 // 1 right, 2 bottom, 3 top (2 x M cells each), 4-7 the corners (2 x 2).
-template <typename T>
-__global__ void k_ghost_other(const __grid_constant__ GfGeom G, const __grid_constant__ GfView V,
+// F32: the FP32 operators above (FP32 forests without subcycling).
+template <typename T, bool F32>
+__global__ void __launch_bounds__(256, 2) k_ghost_other(const __grid_constant__ GfGeom G, const __grid_constant__ GfView V,
                               const int* regs, int nquad, int nreg, int* errflag) {
   const int M = G.M;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -718,6 +967,28 @@ __global__ void k_ghost_other(const __grid_constant__ GfGeom G, const __grid_con
   Geo<T> e(G, V);
   T* q = e.qp(p, e.cur_of(p));
   const long long I = (long long)P.px * M + i, J = (long long)P.py * M + j;
+  if constexpr (F32) {
+    const int cur = C->cur;
+    const float* bb = e.bp(p);
+    float bs[2][2];
+    for (int b = 0; b < 2; ++b)
+      for (int a = 0; a < 2; ++a) bs[b][a] = bb[e.tix((i & ~1) + a, (j & ~1) + b)];
+    int err = 0;
+    if (quad) {
+      float out4[2][2][3];
+      interp_children_f32(e, P.scen, cur, P.level, I >> 1, J >> 1, bs, out4, &err);
+      if (err && errflag) *errflag = 1;
+      for (int b = 0; b < 2; ++b)
+        for (int a = 0; a < 2; ++a)
+          store_ghost_f32(e, V, q, P, p, i + a, j + b, out4[b][a], bs[b][a]);
+      return;
+    }
+    float out[3];
+    fill_cell_f32(e, P.scen, cur, P.level, I, J, bs, out, &err);
+    if (err && errflag) *errflag = 1;
+    store_ghost_f32(e, V, q, P, p, i, j, out, bs[j & 1][i & 1]);
+    return;
+  }
   double bs[2][2];
   child_beds(e, e.bp(p), i, j, bs);
   int err = 0;
@@ -1605,8 +1876,11 @@ int launch_ghost_rest(const GfGeom& g, const GfView& v, const int* regs, int nqu
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const long long total = (long long)nquad * (g.M / 2) + (long long)(nreg - nquad) * 2 * g.M;
   const int blocks = (int)((total + 255) / 256);
-  if (v.prec) k_ghost_other<float><<<blocks, 256, 0, st>>>(g, v, regs, nquad, nreg, g_errflag);
-  else k_ghost_other<double><<<blocks, 256, 0, st>>>(g, v, regs, nquad, nreg, g_errflag);
+  if (v.prec && !g.subcycle)
+    k_ghost_other<float, true><<<blocks, 256, 0, st>>>(g, v, regs, nquad, nreg, g_errflag);
+  else if (v.prec)
+    k_ghost_other<float, false><<<blocks, 256, 0, st>>>(g, v, regs, nquad, nreg, g_errflag);
+  else k_ghost_other<double, false><<<blocks, 256, 0, st>>>(g, v, regs, nquad, nreg, g_errflag);
   return ok();
 }
 

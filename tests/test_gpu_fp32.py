@@ -123,3 +123,76 @@ def test_fp32_amr_valley_runs_and_tags_agree_mostly():
     og, ag = g.gauges()
     orr, ar = r.gauges()
     assert np.abs(og[:, 1] - orr[:, 1]).max() <= 0.05
+
+
+def _two_level(prob, box, precision):
+    """The problem on a two-level forest: level 1 inside box, level 0 elsewhere."""
+    cfg = inputs.Config(**{**prob.cfg.__dict__, "mi": prob.cfg.mi // 2,
+                           "mj": prob.cfg.mj // 2, "minlevel": 0, "maxlevel": 1,
+                           "src_box": box, "src_level": 1, "tag_depth": 1e9,
+                           "precision": precision})
+    return inputs.Problem(prob.name, cfg, prob.dem, prob.ic, prob.t_end)
+
+
+RING = np.ones((36, 36), bool)  # the ghost ring of a 32 x 32 patch's tile
+RING[2:-2, 2:-2] = False
+
+
+def _ghost_gap(tg, tr):
+    """Largest |difference| of (h, hu, hv) over the tiles, and over their ghost rings."""
+    d = np.abs(tg[:, :3] - tr[:, :3])
+    return float(d.max()), float(d[..., RING].max())
+
+
+def test_fp32_ghost_cells_across_levels_match_oracle():
+    """The FP32 ghost operators (copy, 2x2 mean and limited interpolation of
+    the stored surface, in FP32) against the FP64 oracle's on the same
+    stored state: after the full ghost fill that follows a host write, and
+    after one step, whose level-change ghosts the per-step ghost kernel
+    writes.  Smooth, partly dry state; within the FP32 per-step bound."""
+    base = inputs.radial_dambreak(128, 32, dx=4.0, radius=150.0)
+    box = (0.0, 200.0, 0.0, 300.0)
+    p32, p64 = _two_level(base, box, 1), _two_level(base, box, 0)
+
+    def ic(x, y, b):
+        # the bed spans 4.5-19 m: a surface near 13 m leaves wet and dry
+        # cells on both sides of the level interface
+        h = np.maximum(0.0, 13.0 + 1.5 * np.sin(x / 40.0) * np.cos(y / 55.0) - b)
+        return h, 0.2 * h * np.cos(y / 30.0), -0.1 * h
+    g = geoflood.Forest(p32.cfg, p32.dem)
+    r = oracle.OracleForest(p64.cfg, p64.dem)
+    g.regrid()
+    r.regrid()
+    assert [list(a) for a in g.patch_info()] == [list(a) for a in r.patch_info()]
+    assert len(set(int(x) for x in g.patch_info()[0])) == 2
+    g.set_state(ic)
+    for stage in ("host write", "one step"):
+        if stage == "one step":
+            g.step(1e9, 1)
+        h, hu, hv, _ = g.read()
+        r.write(h, hu, hv)
+        r.ghost_fill()
+        tr = r.read_tiles()
+        wet = tr[:, 0][:, RING] > p64.cfg.drytol
+        assert 0.2 <= wet.mean() <= 0.8, "the ghost rings must hold wet and dry cells"
+        whole, ring = _ghost_gap(g.read_tiles(), tr)
+        print("%s: max |d| %.2e over the tiles, %.2e over the ghost rings" % (stage, whole, ring))
+        assert whole <= ABS
+
+
+def test_fp32_lake_at_rest_across_levels_is_exact():
+    """Still water over a submerged bump on a two-level forest (the level
+    interface crosses the bump) stays exactly still in FP32 without
+    subcycling: the level-change ghosts carry the stored surface, whose
+    means and limited slopes are exactly zero."""
+    prob = _two_level(inputs.lake_at_rest(128, patch=32, eta=1.0), (0.0, 300.0, 0.0, 300.0), 1)
+    prob.cfg.eta0 = 1.0
+    g = geoflood.Forest(prob.cfg, prob.dem)
+    g.regrid()
+    assert len(set(int(x) for x in g.patch_info()[0])) == 2
+    g.set_state(prob.ic)
+    h0 = g.read()[0]
+    g.step(1e9, 200)
+    h, hu, hv, _ = g.read()
+    assert np.abs(h - h0).max() <= 1e-6
+    assert np.all(hu == 0.0) and np.all(hv == 0.0)

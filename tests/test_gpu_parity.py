@@ -114,7 +114,9 @@ def test_ghost_fill_across_levels_matches_oracle():
     prob = two_level(base, (0.0, 200.0, 0.0, 300.0))
 
     def ic(x, y, b):
-        h = np.maximum(0.0, 1.2 + 0.3 * np.sin(x / 40.0) * np.cos(y / 55.0) - 0.4 * b)
+        # the bed spans 4.5-19 m: a surface near 13 m leaves wet and dry
+        # cells on both sides of the level interface
+        h = np.maximum(0.0, 13.0 + 1.5 * np.sin(x / 40.0) * np.cos(y / 55.0) - b)
         return h, 0.2 * h * np.cos(y / 30.0), -0.1 * h
     prob.ic = ic
     g = geoflood.Forest(prob.cfg, prob.dem)
@@ -125,6 +127,10 @@ def test_ghost_fill_across_levels_matches_oracle():
     g.set_state(ic)
     r.set_state(ic)
     tg, tr = g.read_tiles(), r.read_tiles()
+    ring = np.ones(tr.shape[-2:], bool)
+    ring[2:-2, 2:-2] = False
+    wet = tr[:, 0][:, ring] > prob.cfg.drytol
+    assert 0.2 <= wet.mean() <= 0.8, "the ghost rings must hold wet and dry cells"
     assert rel(tg, tr) <= 1e-14
 
 
