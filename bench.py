@@ -133,6 +133,7 @@ def run_profile_valley(args):
     prob.cfg.precision = args.profile_precision
     f = geoflood.Forest(prob.cfg, prob.dem, max_patches=VALLEY_CAP)
     f.set_state(prob.ic)
+    f.set_variant(args.profile_variant)
     f.advance(args.profile_valley, regrid_interval=4, check_interval=4)
     _, steps = f.step(1e9, args.profile_steps)
     print("profile valley: %d patches, %d steps, t = %.3f s" % (f.npatch, steps, f.time()["t"]))
