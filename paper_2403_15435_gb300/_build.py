@@ -22,8 +22,8 @@ SOURCES = [
     ("gf_step.cu", ["-fmad=false"]),
     # FP32 kernels: approximate single-precision division and square root
     # (a few ulp; the FP32 path is held to absolute tolerances, and a lake at
-    # rest still gives exactly zero waves)
-    ("gf_step32.cu", ["-prec-div=false", "-prec-sqrt=false"]),
+    # rest still gives exactly zero waves), denormals flushed to zero
+    ("gf_step32.cu", ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]),
     ("gf_amr.cu", ["-fmad=false"]),
     ("gf_cnn.cu", []),
     ("gf_forest.cpp", []),
