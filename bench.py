@@ -380,7 +380,7 @@ class ValleyArm:
                 "criterion_misses": st["misses"],
                 "cell_updates": st["patch_steps"] * PATCH * PATCH,
                 "patches_at_end": self.f.npatch,
-                "time_split_s": {"steps": st["step_s"], "criterion_checks": st["check_s"],
+                "time_split_s": {"steps_and_checks": st["step_s"], "separate_checks": st["check_s"],
                                  "regrids": st["regrid_s"],
                                  "of_which_host_quadtree": st["regrid_host_s"]},
                 "_gauge_h": out[:, 1].copy(), "_arrival": arr.copy()}
@@ -639,7 +639,7 @@ def measure_canyon(stream, net):
             res = {"value": s["patch_steps"] * PATCH * PATCH / wall, "unit": "cell-updates/s",
                    "wall_s": wall, "steps": s["steps"], "regrids": s["regrids"],
                    "patches_at_end": g.npatch, "levels": sorted(set(int(x) for x in g.patch_info()[0])),
-                   "time_split_s": {"steps": s["step_s"], "criterion_checks": s["check_s"],
+                   "time_split_s": {"steps_and_checks": s["step_s"], "separate_checks": s["check_s"],
                                     "regrids": s["regrid_s"],
                                     "of_which_host_quadtree": s["regrid_host_s"]},
                    "_h": out[:, 1].copy(), "_a": arr.copy()}
@@ -733,7 +733,7 @@ def measure_ensemble_full(stream):
                                "max": int(max(patches))},
             "steps_per_scenario": {"min": min(steps), "max": max(steps)},
             "regrids": st["regrids"],
-            "time_split_s": {"steps": st["step_s"], "criterion_checks": st["check_s"],
+            "time_split_s": {"steps_and_checks": st["step_s"], "separate_checks": st["check_s"],
                              "regrids": st["regrid_s"],
                              "of_which_host_quadtree": st["regrid_host_s"]},
             "time_to_t_end_s": {"all_scenarios_in_one_context": wall,
@@ -823,7 +823,7 @@ def measure_flood_speed(stream):
         res = {"value": cells / wall, "unit": "cell-updates/s", "wall_s": wall,
                "steps": st["steps"], "regrids": st["regrids"], "cell_updates": cells,
                "patches_at_end": g.npatch,
-               "time_split_s": {"steps": st["step_s"], "criterion_checks": st["check_s"],
+               "time_split_s": {"steps_and_checks": st["step_s"], "separate_checks": st["check_s"],
                                 "regrids": st["regrid_s"],
                                 "of_which_host_quadtree": st["regrid_host_s"]},
                "volume_in_m3": g.mass() - v0 - g.time()["clipvol"],

@@ -506,8 +506,10 @@ int geoflood_cnn_train(geoflood_ctx* ctx, int epochs, int batch, float lr,
 /* Time stepping with periodic regridding (Sec. 3.3 regrids every few
  * steps; Sec. 6.4 every 4).  Advances every scenario to t_target in chunks
  * of check_interval steps; after each chunk the plain criterion is
- * evaluated (geoflood_check_tags; when a regrid is due, the regrid's own tag
- * pass counts the criterion's misses instead) and the forest regrids when
+ * evaluated (geoflood_check_tags's count, taken on the device right after
+ * the chunk's steps and read back with them; when a regrid is due, the
+ * regrid's own tag pass counts the criterion's misses instead) and the
+ * forest regrids when
  * regrid_interval steps have passed since the last regrid or, with
  * GEOFLOOD_ADVANCE_REGRID_ON_MISS, as soon as the criterion reports a
  * miss.  With GEOFLOOD_ADVANCE_COLLECT it records training samples instead
@@ -525,8 +527,9 @@ typedef struct {
   long long miss_regrids; /* of which triggered by a miss */
   long long samples;      /* dataset size after the run (COLLECT) */
   /* host wall-clock seconds, each including the waits for the device work
-   * it issued: in geoflood_step, in the criterion checks, in the regrids,
-   * and, of the regrids' time, in the host quadtree (new leaf lists) */
+   * it issued: in the steps (with the checks taken inside their readback),
+   * in separate criterion checks (COLLECT mode), in the regrids, and, of the
+   * regrids' time, in the host quadtree (new leaf lists) */
   double step_s, check_s, regrid_s, regrid_host_s;
 } geoflood_advance_stats;
 int geoflood_advance(geoflood_ctx* ctx, double t_target, int regrid_interval,

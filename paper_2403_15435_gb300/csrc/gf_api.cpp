@@ -117,6 +117,7 @@ struct geoflood_ctx {
   std::vector<GfScenario> h_scen;
   GfCtl* d_ctl = nullptr;
   GfCtl* h_ctl = nullptr;  // pinned mirror
+  int* h_rb = nullptr;     // pinned: [0] device error flag, [1] criterion misses
   double* d_pmass = nullptr;
   double* d_smass = nullptr;
   uint8_t* d_flags = nullptr;
@@ -789,6 +790,7 @@ int geoflood_init_forest(const geoflood_config* cfg, void* stream,
   okk &= alloc((void**)&ctx->d_flags, cap);
   okk &= alloc((void**)&ctx->d_err, sizeof(int));
   okk &= cudaMallocHost((void**)&ctx->h_ctl, ctx->nscen * sizeof(GfCtl)) == cudaSuccess;
+  okk &= cudaMallocHost((void**)&ctx->h_rb, 2 * sizeof(int)) == cudaSuccess;
   {
     // bed tiles by position: every patch position of every level, when that
     // fits the budget (else beds are always recomputed from the DEMs)
@@ -902,6 +904,7 @@ void geoflood_destroy(geoflood_ctx* ctx) {
   for (auto p : ctx->d_garr) cudaFree(p);
   for (auto p : ctx->d_gref) cudaFree(p);
   if (ctx->h_ctl) cudaFreeHost(ctx->h_ctl);
+  if (ctx->h_rb) cudaFreeHost(ctx->h_rb);
   if (ctx->up_pending) cudaEventSynchronize(ctx->up_ev);
   if (ctx->h_up) cudaFreeHost(ctx->h_up);
   if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
@@ -1158,8 +1161,14 @@ int geoflood_get_time(geoflood_ctx* ctx, int s, double* t, double* dt_next,
   return 0;
 }
 
-int geoflood_step(geoflood_ctx* ctx, double t_target, int max_steps,
-                  double* t_out, int* steps_out) {
+// The steps of geoflood_step; with misses non-null the plain criterion's
+// check (geoflood_check_tags's count) also runs on the final state, inside
+// the same readback.  Each graph launch is followed by the gauges' sample of
+// its final state and one readback of the controllers, the device error flag
+// and the check's count (one host wait per launch).  A sample taken before a
+// retake is one the next step takes again at its start.
+static int step_core(geoflood_ctx* ctx, double t_target, int max_steps, double* t_out,
+                     int* steps_out, int* misses) {
   if (!ctx || max_steps < 0) return fail(ctx, GEOFLOOD_ERR_ARG, "step: bad argument");
   CKL(gf::launch_ctl_begin(ctx->d_ctl, ctx->nscen, t_target, max_steps,
                            nullptr, ctx->st),
@@ -1267,12 +1276,44 @@ int geoflood_step(geoflood_ctx* ctx, double t_target, int max_steps,
                        (ctx->G.subcycle ? 1 : 0);
   long long launched = 0;
   const long long limit = (long long)max_steps * 2 + 64;
+  unsigned* d_misses = nullptr;
+  if (misses) {
+    int rc = cnn_alloc(ctx, (void**)&ctx->cnn.misses, sizeof(unsigned));
+    if (rc) return rc;
+    d_misses = ctx->cnn.misses;
+  }
+  // the final-state work after a graph launch, then one host wait
+  auto finish = [&]() -> int {
+    if (ctx->max_gauges_used > 0) {
+      CKL(gf::launch_gauges(ctx->G, v, 0, ctx->max_gauges_used, ctx->st), "gauges");
+      ctx->launches++;
+    }
+    if (d_misses) {
+      CK(cudaMemsetAsync(d_misses, 0, sizeof(unsigned), ctx->st));
+      int rc = tag_pass(ctx, false, d_misses);
+      if (rc) return rc;
+      CK(cudaMemcpyAsync(ctx->h_rb + 1, d_misses, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                         ctx->st));
+    }
+    CK(cudaMemcpyAsync(ctx->h_ctl, ctx->d_ctl, sizeof(GfCtl) * ctx->nscen,
+                       cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(ctx->h_rb, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    if (ctx->h_rb[0]) {
+      CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->st));
+      return fail(ctx, GEOFLOOD_ERR_STATE,
+                  "forest lookup failed (unbalanced or uncovered forest)");
+    }
+    return 0;
+  };
+  bool finished = false;
   while (max_steps > 0) {
     CK(cudaGraphLaunch(gr->exec, ctx->st));
     ctx->launches += (long long)K * per_step;
     launched += K;
-    int rc = sync_ctl_down(ctx);
+    int rc = finish();
     if (rc) return rc;
+    finished = true;
     if (prof) {
       for (auto& r : gr->ev) {
         float ms = 0.f;
@@ -1293,15 +1334,11 @@ int geoflood_step(geoflood_ctx* ctx, double t_target, int max_steps,
     if (!any) break;
     if (launched > limit) return fail(ctx, GEOFLOOD_ERR_CFL, "step: too many retakes");
   }
-  // the steps sample the gauges at the start of the next step; sample the
-  // final state here
-  if (ctx->max_gauges_used > 0) {
-    CKL(gf::launch_gauges(ctx->G, v, 0, ctx->max_gauges_used, ctx->st), "gauges");
-    ctx->launches++;
+  if (!finished) {
+    int rc = finish();
+    if (rc) return rc;
   }
-  int rc = sync_ctl_down(ctx);
-  if (rc) return rc;
-  if ((rc = check_errflag(ctx))) return rc;
+  if (misses) *misses = ctx->h_rb[1];
   int status = 0;
   for (int s = 0; s < ctx->nscen; ++s) {
     const GfCtl& C = ctx->h_ctl[s];
@@ -1314,6 +1351,11 @@ int geoflood_step(geoflood_ctx* ctx, double t_target, int max_steps,
   if (status == GEOFLOOD_ERR_TIMEOUT) return fail(ctx, status, "bounded device wait expired");
   if (status) return fail(ctx, status, "device error");
   return 0;
+}
+
+int geoflood_step(geoflood_ctx* ctx, double t_target, int max_steps,
+                  double* t_out, int* steps_out) {
+  return step_core(ctx, t_target, max_steps, t_out, steps_out, nullptr);
 }
 
 int geoflood_tags(geoflood_ctx* ctx, int s, uint8_t* flags) {
@@ -1945,8 +1987,12 @@ int geoflood_advance(geoflood_ctx* ctx, double t_target, int regrid_interval,
   for (;;) {
     const int want = std::min(check_interval, regrid_interval - since);
     const int np = ctx->npatch;
+    // a chunk that cannot end in a regrid takes its check inside the step's
+    // readback (a regrid's own tag pass counts the misses)
+    const bool fused = !collect && since + want < regrid_interval;
+    int fmisses = 0;
     auto t0 = clock::now();
-    rc = geoflood_step(ctx, t_target, want, t.data(), n.data());
+    rc = step_core(ctx, t_target, want, t.data(), n.data(), fused ? &fmisses : nullptr);
     st.step_s += secs(t0);
     if (rc) return rc;
     int taken = 0;
@@ -1975,10 +2021,14 @@ int geoflood_advance(geoflood_ctx* ctx, double t_target, int regrid_interval,
       since = 0;
       continue;
     }
-    t0 = clock::now();
-    rc = geoflood_check_tags(ctx, collect ? 1 : 0, &misses);
-    st.check_s += secs(t0);
-    if (rc) return rc;
+    if (fused) {
+      misses = fmisses;
+    } else {
+      t0 = clock::now();
+      rc = geoflood_check_tags(ctx, collect ? 1 : 0, &misses);
+      st.check_s += secs(t0);
+      if (rc) return rc;
+    }
     st.checks++;
     st.misses += misses;
     if (due || (on_miss && misses > 0)) {
