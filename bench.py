@@ -447,7 +447,9 @@ def measure_valley(args, dev, stream, world, local, peaks):
     pst, _ = head.run(flush)
     k_ms, k_n = head.f.profile_read("patch_step")
     k_cells = head.f.profile_cells("patch_step")
+    g_ms, g_n = head.f.profile_read("ghost_fill")
     head.f.profile(False)
+    learned["level_change_ghost_fill_ms_per_launch"] = g_ms / g_n if g_n else None
     prof = {"k_ms": k_ms, "k_n": k_n, "cells": k_cells, "wet": pst["wet_updates_counted"],
             "updates": pst["cell_updates_counted"]}
     traffic = None

@@ -375,8 +375,10 @@ __device__ void fill_cell_f32(const Geo<float>& e, int s, int cur, int L, long l
 // whose same-level neighbour exists is a plain copy of that neighbour's
 // stored values; its position in the neighbour follows from the region's
 // offset, so only the neighbour's index is looked up (in shared memory).
+// (At most 288 threads: one per ghost cell of a 32 x 32 patch's tile.)
 template <typename T>
-__global__ void k_ghost_fill(const __grid_constant__ GfGeom G, const __grid_constant__ GfView V, int only_accepted,
+__global__ void __launch_bounds__(288, 1)
+    k_ghost_fill(const __grid_constant__ GfGeom G, const __grid_constant__ GfView V, int only_accepted,
                              int* errflag, const int* list) {
   // with a list: only the listed patches, and only the regions without a
   // same-level neighbour (the patch step pushed those)
@@ -714,17 +716,28 @@ __device__ __forceinline__ void load_surf(const Geo<float>& e, int p, int cur, i
   o[3] = e.V.bf[(size_t)p * TT + c];
 }
 
+// Four values of a cell and a lookup-error flag, returned by value from the
+// out-of-line lookups below, so that no caller array has its address taken
+// (which would put it in local memory).
+struct Cell4 {
+  float v[4];
+  int err;
+};
+
 // value_at's composite in FP64 with the surface in place of the depth: the
 // rare lookups (a leaf two levels coarser, cells two levels finer), kept out
 // of line so that its FP64 arrays stay out of the callers' registers.
-__device__ __noinline__ void surf_at_f64(const Geo<float>& e, int s, int L, long long I,
-                                         long long J, float (&o)[4], int* err) {
+__device__ __noinline__ Cell4 surf_at_f64(const GfGeom* G, const GfView* V, int s, int L,
+                                          long long I, long long J) {
+  const Geo<float> e(*G, *V);
   double d[4];
-  value_at(e, s, L, I, J, d, err);
-  o[0] = (float)(d[0] + d[3]);
-  o[1] = (float)d[1];
-  o[2] = (float)d[2];
-  o[3] = (float)d[3];
+  Cell4 r{};
+  value_at(e, s, L, I, J, d, &r.err);
+  r.v[0] = (float)(d[0] + d[3]);
+  r.v[1] = (float)d[1];
+  r.v[2] = (float)d[2];
+  r.v[3] = (float)d[3];
+  return r;
 }
 
 // (w, hu, hv, b) of cell (I, J) of level L: the leaf of level L or L - 1,
@@ -755,7 +768,9 @@ __device__ void surf_near_f32(const Geo<float>& e, int s, int cur, int L, long l
       return;
     }
   }
-  surf_at_f64(e, s, L, I, J, o, err);
+  const Cell4 r = surf_at_f64(&e.G, &e.V, s, L, I, J);
+  for (int f = 0; f < 4; ++f) o[f] = r.v[f];
+  if (r.err) *err = 1;
 }
 
 __device__ __forceinline__ float minmodf(float a, float b) {
@@ -776,16 +791,30 @@ __device__ void interp_children_f32(const Geo<float>& e, int s, int cur, int L, 
   const long long NXc = e.nx(L - 1), NYc = e.ny(L - 1);
   float nb[3][3][4];
   bool in[3][3], wt[3][3];
-  for (int dj = -1; dj <= 1; ++dj)
-    for (int di = -1; di <= 1; ++di) {
-      const long long x = ic + di, y = jc + dj;
-      const bool ok = x >= 0 && y >= 0 && x < NXc && y < NYc;
-      in[dj + 1][di + 1] = ok;
-      wt[dj + 1][di + 1] = false;
-      if (ok) {
-        surf_near_f32(e, s, cur, L - 1, x, y, nb[dj + 1][di + 1], err);
-        wt[dj + 1][di + 1] = wet_f32(G, nb[dj + 1][di + 1][0], nb[dj + 1][di + 1][3]);
-      }
+  // the neighbourhood in three straight-line passes, so that the loads of
+  // the nine cells overlap: the leaves of level L - 1 holding them, the
+  // values of those found, then the others (surf_near_f32's rarer cases)
+  int pl[3][3];
+#pragma unroll
+  for (int dj = 0; dj < 3; ++dj)
+#pragma unroll
+    for (int di = 0; di < 3; ++di) {
+      const long long x = ic + di - 1, y = jc + dj - 1;
+      in[dj][di] = x >= 0 && y >= 0 && x < NXc && y < NYc;
+      pl[dj][di] = in[dj][di] ? e.leaf(s, L - 1, x, y) : -1;
+    }
+#pragma unroll
+  for (int dj = 0; dj < 3; ++dj)
+#pragma unroll
+    for (int di = 0; di < 3; ++di)
+      if (pl[dj][di] >= 0) load_surf(e, pl[dj][di], cur, e.local(ic + di - 1, jc + dj - 1), nb[dj][di]);
+#pragma unroll
+  for (int dj = 0; dj < 3; ++dj)
+#pragma unroll
+    for (int di = 0; di < 3; ++di) {
+      if (in[dj][di] && pl[dj][di] < 0)
+        surf_near_f32(e, s, cur, L - 1, ic + di - 1, jc + dj - 1, nb[dj][di], err);
+      wt[dj][di] = in[dj][di] && wet_f32(G, nb[dj][di][0], nb[dj][di][3]);
     }
   const float* qc = nb[1][1];
   if (!wt[1][1]) {
@@ -834,18 +863,21 @@ __device__ void interp_children_f32(const Geo<float>& e, int s, int cur, int L, 
       for (int dj = 0; dj < 3; ++dj)
         for (int di = 0; di < 3; ++di)
           if (in[dj][di]) {
-            const float u = nb[dj][di][k + 1] / (nb[dj][di][0] - nb[dj][di][3]);
+            // velocities by the fast division (a few ulp): they only bound
+            // the children's velocities
+            const float u = __fdividef(nb[dj][di][k + 1], nb[dj][di][0] - nb[dj][di][3]);
             lo = fminf(lo, u);
             hi = fmaxf(hi, u);
           }
       for (int b = 0; b < 2; ++b)
         for (int a = 0; a < 2; ++a)
           if (cw[b][a]) {
-            const float u = m[b][a][k] / d[b][a];
+            const float u = __fdividef(m[b][a][k], d[b][a]);
             if (u < lo || u > hi) split[k] = true;
           }
     }
   }
+  const float rS = S > 0.0f ? __fdividef(1.0f, S) : 0.0f;
   for (int b = 0; b < 2; ++b)
     for (int a = 0; a < 2; ++a) {
       // a child with water stores the interpolated surface itself
@@ -853,7 +885,7 @@ __device__ void interp_children_f32(const Geo<float>& e, int s, int cur, int L, 
       for (int k = 0; k < 2; ++k)
         out[b][a][k + 1] = !cw[b][a] ? 0.0f
                            : !split[k] ? m[b][a][k]
-                                       : (S > 0.0f ? (4.0f * qc[k + 1]) * (d[b][a] / S) : 0.0f);
+                                       : (4.0f * qc[k + 1]) * (d[b][a] * rS);
     }
 }
 
@@ -881,10 +913,19 @@ __device__ void fill_cell_f32(const Geo<float>& e, int s, int cur, int L, long l
     for (int f = 0; f < 3; ++f) out[f] = quad[J & 1][I & 1][f];
     return;
   }
+  // the four finer cells: their leaves, their values, then the rarer cases
   float v[4][4];
+  int pc[4];
+#pragma unroll
+  for (int ch = 0; ch < 4; ++ch) pc[ch] = e.leaf(s, L + 1, 2 * I + (ch & 1), 2 * J + (ch >> 1));
+#pragma unroll
+  for (int ch = 0; ch < 4; ++ch)
+    if (pc[ch] >= 0) load_surf(e, pc[ch], cur, e.local(2 * I + (ch & 1), 2 * J + (ch >> 1)), v[ch]);
   bool all = true;
+#pragma unroll
   for (int ch = 0; ch < 4; ++ch) {
-    surf_near_f32(e, s, cur, L + 1, 2 * I + (ch & 1), 2 * J + (ch >> 1), v[ch], err);
+    if (pc[ch] < 0)
+      surf_near_f32(e, s, cur, L + 1, 2 * I + (ch & 1), 2 * J + (ch >> 1), v[ch], err);
     all = all && wet_f32(e.G, v[ch][0], v[ch][3]);
   }
   for (int f = 1; f < 3; ++f) out[f] = 0.25f * ((v[0][f] + v[1][f]) + (v[2][f] + v[3][f]));
@@ -920,7 +961,7 @@ __device__ void store_ghost_f32(const Geo<float>& e, const GfView& V, float* q,
 // 1 right, 2 bottom, 3 top (2 x M cells each), 4-7 the corners (2 x 2).
 // F32: the FP32 operators above (FP32 forests without subcycling).
 template <typename T, bool F32>
-__global__ void __launch_bounds__(256, 2) k_ghost_other(const __grid_constant__ GfGeom G, const __grid_constant__ GfView V,
+__global__ void __launch_bounds__(256, 1) k_ghost_other(const __grid_constant__ GfGeom G, const __grid_constant__ GfView V,
                               const int* regs, int nquad, int nreg, int* errflag) {
   const int M = G.M;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1714,11 +1755,14 @@ __device__ __forceinline__ void load_f32(const GfGeom& G, const GfView& V, int p
 
 // value_at for the FP32 feature kernel, kept out of line: it is the rare
 // case, and inlined its FP64 arrays would crowd the kernel's registers.
-__device__ __noinline__ void value_at_f32(const Geo<float>& e, int s, int L, long long I,
-                                          long long J, float (&out)[4], int* err) {
+__device__ __noinline__ Cell4 value_at_f32(const GfGeom* G, const GfView* V, int s, int L,
+                                           long long I, long long J) {
+  const Geo<float> e(*G, *V);
   double d[4];
-  value_at(e, s, L, I, J, d, err);
-  for (int f = 0; f < 4; ++f) out[f] = (float)d[f];
+  Cell4 r{};
+  value_at(e, s, L, I, J, d, &r.err);
+  for (int f = 0; f < 4; ++f) r.v[f] = (float)d[f];
+  return r;
 }
 
 // value_near in FP32 (deviation form, no subcycling): the leaf of level L or
@@ -1749,7 +1793,9 @@ __device__ void value_near_f32(const Geo<float>& e, int s, int cur, int L, long 
       return;
     }
   }
-  value_at_f32(e, s, L, I, J, out, err);
+  const Cell4 r = value_at_f32(&e.G, &e.V, s, L, I, J);
+  for (int f = 0; f < 4; ++f) out[f] = r.v[f];
+  if (r.err) *err = 1;
 }
 
 __global__ void __launch_bounds__(256, 3)
