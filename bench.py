@@ -82,11 +82,12 @@ N_SM = 152
 # DRAM bytes (read + write) of one patch-step launch, from the ncu captures
 # summarised in profiles/ (cold caches); None when the kernel has changed
 # since.  Uniform workload: launch 151 (t = 29.5 s).  Valley: the launch at
-# t = 30 s (6827 patches), 331 701 504 B over 6 990 848 cells, scaled to the
-# cells of an average timed launch.
-TRAFFIC_PER_LAUNCH_FP32 = 4635392
+# t = 30 s (6827 patches) of the 608-thread variant that the autotuner
+# picks there, 340 639 232 B over 6 990 848 cells, scaled to the cells of an
+# average timed launch.
+TRAFFIC_PER_LAUNCH_FP32 = 4630784
 TRAFFIC_PER_LAUNCH_FP64 = None
-TRAFFIC_PER_CELL_VALLEY_FP32 = 331701504 / 6990848
+TRAFFIC_PER_CELL_VALLEY_FP32 = 340639232 / 6990848
 
 
 def parse():
