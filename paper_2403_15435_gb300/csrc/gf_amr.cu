@@ -1322,7 +1322,66 @@ __global__ void k_tags(const __grid_constant__ GfGeom G, const __grid_constant__
   const int rbox = P.level < G.src_level ? 2 : 1;  // a cell in the box asks this
   int m = box_all ? rbox : 0;
   int gl = -1;  // the highest level a flow grade asks for (criterion 5)
-  if (m < 2) {
+  if constexpr (Geo<T>::DEV) {
+    // FP32 deviation form: up to four cells per thread at once, so that a
+    // block waits for two rounds of loads (surfaces and beds, then the
+    // momenta of the cells deep enough to be tested) instead of one per
+    // cell; stop once any cell asks for refinement
+    constexpr int U = 4;
+    const float* q = e.qp(p, cur);
+    const float* bq = e.bp(p);
+    const int TT = G.T * G.T;
+    for (int k0 = 0; m < 2 && k0 < M * M; k0 += U * (int)blockDim.x) {
+      float w[U], b[U], hu[U], hv[U];
+      int c[U];
+      bool ok[U], deep[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int k = k0 + u * (int)blockDim.x + (int)threadIdx.x;
+        ok[u] = k < M * M;
+        c[u] = ok[u] ? e.tix(k % M, k / M) : 0;
+        w[u] = ok[u] ? q[c[u]] : 0.0f;
+        b[u] = ok[u] ? bq[c[u]] : 0.0f;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        deep[u] = ok[u] && w[u] - b[u] > G.tag_depthf;
+        hu[u] = deep[u] ? q[TT + c[u]] : 0.0f;
+        hv[u] = deep[u] ? q[2 * TT + c[u]] : 0.0f;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (!ok[u]) continue;
+        const int k = k0 + u * (int)blockDim.x + (int)threadIdx.x;
+        const int i = k % M, j = k / M;
+        int r = 0;
+        if (deep[u]) {
+          // depth w - b, speed test without a division, surface deviation
+          // |w| (one mismatch with the FP64 criterion is possible at a
+          // threshold tie; counted in the tests)
+          const float h = w[u] - b[u];
+          const float st = G.tag_speedf * h;
+          const float f2 = hu[u] * hu[u] + hv[u] * hv[u];
+          if (f2 > st * st || fabsf(w[u]) > G.tag_detaf || f2 > G.tag_fluxf * G.tag_fluxf) r = 2;
+          for (int g = 0; g < G.ngrades; ++g) {
+            const float tv = G.grade_valuef[g];
+            const bool over = G.grade_kind[g] == 0 ? h > tv : f2 > (tv * h) * (tv * h);
+            if (over && G.grade_level[g] > gl) gl = G.grade_level[g];
+          }
+        }
+        if (!box_none && !box_all) {
+          const double xc = xcen(i), yc = ycen(j);
+          if (xc >= G.src_box[0] && xc <= G.src_box[1] && yc >= G.src_box[2] &&
+              yc <= G.src_box[3]) {
+            if (rbox == 2) r = 2;
+            else if (r < 1) r = 1;
+          }
+        }
+        m = r > m ? r : m;
+      }
+      if (__syncthreads_or(m == 2)) m = 2;
+    }
+  } else if (m < 2) {
     // cells in rounds of blockDim; stop once any cell asks for refinement
     for (int k0 = 0; k0 < M * M; k0 += blockDim.x) {
       const int k = k0 + threadIdx.x;
@@ -1740,8 +1799,8 @@ __global__ void k_cnn_features(const __grid_constant__ GfGeom G,
 // means are FP32 sums (the features are rounded to BF16, whose unit is 2^15
 // times FP32's, so the precision of the sums changes a feature only when it
 // lies within a few FP32 units of a BF16 rounding boundary), and the
-// lookups are value_near's.  Register use is capped so that three CTAs
-// share an SM: the kernel waits on chains of dependent loads.
+// lookups are value_near's.  Register use is capped so that two CTAs
+// share an SM; each lane keeps its partial sums of all its ring pixels.
 __device__ __forceinline__ void load_f32(const GfGeom& G, const GfView& V, int p, int cur, int c,
                                          float (&o)[4]) {
   const int TT = G.T * G.T;
@@ -1798,7 +1857,7 @@ __device__ void value_near_f32(const Geo<float>& e, int s, int cur, int L, long 
   if (r.err) *err = 1;
 }
 
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256, 2)
     k_cnn_features_f32(const __grid_constant__ GfGeom G, const __grid_constant__ GfView V,
                        int first, FeatScale sc, __nv_bfloat16* out) {
   const int p = first + blockIdx.x;
@@ -1808,6 +1867,9 @@ __global__ void __launch_bounds__(256, 3)
   const int cur = V.ctl[P.scen].cur;
   __shared__ float part[8];
   __shared__ float bmean;
+  __shared__ int snb8[8];  // same-level neighbours by region (GfView::nbr)
+  if (threadIdx.x < 8)
+    snb8[threadIdx.x] = V.nbr != nullptr ? V.nbr[(size_t)p * 8 + threadIdx.x] : GF_NBR_OTHER;
   const float* bp = V.bf + (size_t)p * TT;
   float bs = 0.0f;
   for (int k = threadIdx.x; k < M * M; k += blockDim.x) bs += bp[e.tix(k % M, k / M)];
@@ -1854,14 +1916,27 @@ __global__ void __launch_bounds__(256, 3)
   // ring pixels: one warp each.  A pixel's band lies in one of the eight
   // neighbour regions; a same-level neighbour's cells are read from its
   // tile directly (the leaf value_near would find), anything else through
-  // the forest lookups
+  // the forest lookups.  Every lane first gathers its cells of all of its
+  // warp's pixels (pixels warp, warp + 8, ...; their loads overlap), then
+  // the warp sums each pixel.
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  for (int r = warp; r < 68; r += nwarp) {
-    int X, Y;
+  constexpr int RP = 9;  // pixels per warp: ceil(68 / 8) with 256 threads
+  auto ring = [&](int r, int& X, int& Y) {
     if (r < 18) { X = r; Y = 0; }
     else if (r < 36) { X = r - 18; Y = 17; }
     else if (r < 52) { X = 0; Y = r - 36 + 1; }
     else { X = 17; Y = r - 52 + 1; }
+  };
+  float racc[RP][4];
+  int rcnt[RP];
+#pragma unroll
+  for (int t = 0; t < RP; ++t) {
+    racc[t][0] = racc[t][1] = racc[t][2] = racc[t][3] = 0.f;
+    rcnt[t] = 0;
+    const int r = warp + t * nwarp;
+    if (r >= 68) continue;
+    int X, Y;
+    ring(r, X, Y);
     const int i0 = X == 0 ? -W : X == 17 ? M : (X - 1) * f;
     const int i1 = X == 0 ? 0 : X == 17 ? M + W : X * f;
     const int j0 = Y == 0 ? -W : Y == 17 ? M : (Y - 1) * f;
@@ -1872,10 +1947,8 @@ __global__ void __launch_bounds__(256, 3)
     const int reg = oy == 0 ? (ox < 0 ? 0 : 1)
                   : ox == 0 ? (oy < 0 ? 2 : 3)
                             : 4 + (ox > 0 ? 1 : 0) + (oy > 0 ? 2 : 0);
-    const int nb = V.nbr != nullptr ? V.nbr[(size_t)p * 8 + reg] : GF_NBR_OTHER;
+    const int nb = snb8[reg];
     const int wi = i1 - i0, ncell = wi * (j1 - j0);
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    int cnt = 0;
     for (int k = lane; k < ncell; k += 32) {
       const int i = i0 + k % wi, j = j0 + k / wi;
       float c4[4];
@@ -1886,14 +1959,21 @@ __global__ void __launch_bounds__(256, 3)
         if (I < 0 || J < 0 || I >= NX || J >= NY) continue;
         value_near_f32(e, P.scen, cur, P.level, I, J, c4, &err);
       }
-      for (int c = 0; c < 4; ++c) acc[c] += c4[c];
-      ++cnt;
+      for (int c = 0; c < 4; ++c) racc[t][c] += c4[c];
+      ++rcnt[t];
     }
+  }
+#pragma unroll
+  for (int t = 0; t < RP; ++t) {
+    const int r = warp + t * nwarp;
+    if (r >= 68) continue;
 #pragma unroll
     for (int c = 0; c < 4; ++c)
-      for (int d = 16; d > 0; d >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], d);
-    cnt = __reduce_add_sync(0xffffffffu, cnt);
-    if (lane == 0) emit(X, Y, acc, cnt);
+      for (int d = 16; d > 0; d >>= 1) racc[t][c] += __shfl_xor_sync(0xffffffffu, racc[t][c], d);
+    const int cnt = __reduce_add_sync(0xffffffffu, rcnt[t]);
+    int X, Y;
+    ring(r, X, Y);
+    if (lane == 0) emit(X, Y, racc[t], cnt);
   }
 }
 
