@@ -27,7 +27,9 @@ SOURCES = [
     ("gf_amr.cu", ["-fmad=false"]),
     ("gf_cnn.cu", []),
     ("gf_forest.cpp", []),
-    ("gf_api.cpp", []),
+    # host FP64 that must round as the device does (the tag kernel's box
+    # test): no contraction into fused multiply-adds
+    ("gf_api.cpp", ["-Xcompiler", "-ffp-contract=off"]),
 ]
 HEADERS = ["gf_internal.h", "gf_solver.cuh", "gf_forest.h", "gf_step_kernel.cuh"]
 

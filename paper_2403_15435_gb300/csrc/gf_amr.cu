@@ -1294,31 +1294,34 @@ __global__ void k_tags(const __grid_constant__ GfGeom G, const __grid_constant__
   Geo<T> e(G, V);
   const int M = G.M;
   const int cur = V.ctl[P.scen].cur;
-  // per-patch FP64 scalars, computed once by thread 0 (an FP64 division in
-  // every thread would dominate the kernel on this part) and shared
-  __shared__ double sdx, sdy, seref;
-  __shared__ int sbox;  // bit 0: the box misses the patch, bit 1: covers it
+  // per-level cell sizes from the host's table (the same division as
+  // Geo::dx); surfaces are compared with eta0, relative to which the
+  // deviation form stores them
+  const double sdx = G.dxl[P.level], sdy = G.dyl[P.level];
+  const double eref = Geo<T>::DEV ? 0.0 : V.scen[P.scen].eta0;
   auto xcen = [&](int i) { return G.xlower + ((double)((long long)P.px * M + i) + 0.5) * sdx; };
   auto ycen = [&](int j) { return G.ylower + ((double)((long long)P.py * M + j) + 0.5) * sdy; };
-  if (threadIdx.x == 0) {
-    sdx = e.dx(P.level);
-    sdy = e.dy(P.level);
-    // surfaces are compared with eta0; the deviation form stores them
-    // relative to it
-    seref = Geo<T>::DEV ? 0.0 : V.scen[P.scen].eta0;
-    // the source box against the patch's first and last cell centres (the
-    // centres grow with the index, so the per-cell test is needed only for
-    // a patch that the box edge crosses)
-    const double x0 = xcen(0), x1 = xcen(M - 1), y0 = ycen(0), y1 = ycen(M - 1);
-    const bool none = x1 < G.src_box[0] || x0 > G.src_box[1] || y1 < G.src_box[2] ||
-                      y0 > G.src_box[3];
-    const bool all = x0 >= G.src_box[0] && x1 <= G.src_box[1] && y0 >= G.src_box[2] &&
-                     y1 <= G.src_box[3];
-    sbox = (none ? 1 : 0) | (all ? 2 : 0);
+  // the source box against the patch's first and last cell centres (the
+  // centres grow with the index, so the per-cell test is needed only for a
+  // patch that the box edge crosses): from the host's per-patch table, or
+  // computed once by thread 0 (FP64 is slow on this part) and shared
+  int box;  // bit 0: the box misses the patch, bit 1: covers it
+  if (V.pbox != nullptr) {
+    box = V.pbox[p];
+  } else {
+    __shared__ int sbox;
+    if (threadIdx.x == 0) {
+      const double x0 = xcen(0), x1 = xcen(M - 1), y0 = ycen(0), y1 = ycen(M - 1);
+      const bool none = x1 < G.src_box[0] || x0 > G.src_box[1] || y1 < G.src_box[2] ||
+                        y0 > G.src_box[3];
+      const bool all = x0 >= G.src_box[0] && x1 <= G.src_box[1] && y0 >= G.src_box[2] &&
+                       y1 <= G.src_box[3];
+      sbox = (none ? 1 : 0) | (all ? 2 : 0);
+    }
+    __syncthreads();
+    box = sbox;
   }
-  __syncthreads();
-  const double eref = seref;
-  const bool box_none = (sbox & 1) != 0, box_all = (sbox & 2) != 0;
+  const bool box_none = (box & 1) != 0, box_all = (box & 2) != 0;
   const int rbox = P.level < G.src_level ? 2 : 1;  // a cell in the box asks this
   int m = box_all ? rbox : 0;
   int gl = -1;  // the highest level a flow grade asks for (criterion 5)

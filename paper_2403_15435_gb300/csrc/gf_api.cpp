@@ -84,6 +84,7 @@ struct geoflood_ctx {
   GfPatch* d_patch[2] = {nullptr, nullptr};
   int* d_lut[2] = {nullptr, nullptr};
   int* d_nbr[2] = {nullptr, nullptr};
+  unsigned char* d_pbox[2] = {nullptr, nullptr};
   unsigned* d_done = nullptr;
   unsigned* d_sched = nullptr;        // launch-order parity and counters
   int* d_ord[2] = {nullptr, nullptr}; // launch orders of the patch step
@@ -200,6 +201,7 @@ GfView view(geoflood_ctx* c, int t, int bb) {
   v.lof[0] = c->lof[0];
   v.lof[1] = c->lof[1];
   v.nbr = c->d_nbr[t];
+  v.pbox = c->d_pbox[t];
   v.done = c->d_done;
   v.sched = c->d_sched;
   v.ord0 = c->d_ord[0];
@@ -326,7 +328,7 @@ size_t upload_room(std::initializer_list<size_t> sizes) {
 // lookup tables, scenarios).
 size_t tables_room(const geoflood_ctx* ctx, size_t total) {
   return upload_room({sizeof(int) * 8 * total, sizeof(int) * 8 * total, sizeof(int) * total,
-                      sizeof(int) * total, sizeof(GfPatch) * total,
+                      sizeof(int) * total, sizeof(GfPatch) * total, total,
                       sizeof(int) * (size_t)ctx->nscen * ctx->G.lut_per_scen,
                       sizeof(GfScenario) * ctx->nscen});
 }
@@ -394,6 +396,27 @@ int upload_tables(geoflood_ctx* ctx, int t,
   }
   ctx->nglist_c[t] = (int)gl.size();
   gl.insert(gl.end(), glf.begin(), glf.end());
+  // the source box against each patch's first and last cell centres, in
+  // the tag kernel's FP64 arithmetic (this file is compiled without
+  // contraction, like the device code)
+  std::vector<unsigned char> pbox(total);
+  {
+    const GfGeom& G = ctx->G;
+    const int M = G.M;
+    for (size_t k = 0; k < total; ++k) {
+      const GfPatch& P = hp[k];
+      const double dx = G.dxl[P.level], dy = G.dyl[P.level];
+      const double x0 = G.xlower + ((double)((long long)P.px * M) + 0.5) * dx;
+      const double x1 = G.xlower + ((double)((long long)P.px * M + M - 1) + 0.5) * dx;
+      const double y0 = G.ylower + ((double)((long long)P.py * M) + 0.5) * dy;
+      const double y1 = G.ylower + ((double)((long long)P.py * M + M - 1) + 0.5) * dy;
+      const bool none = x1 < G.src_box[0] || x0 > G.src_box[1] || y1 < G.src_box[2] ||
+                        y0 > G.src_box[3];
+      const bool all = x0 >= G.src_box[0] && x1 <= G.src_box[1] && y0 >= G.src_box[2] &&
+                       y1 <= G.src_box[3];
+      pbox[k] = (unsigned char)((none ? 1 : 0) | (all ? 2 : 0));
+    }
+  }
   ctx->nglist[t] = (int)gl.size();
   // patches on the inflow side whose tile lines (ghost lines included) may
   // reach the inflow segment
@@ -425,6 +448,7 @@ int upload_tables(geoflood_ctx* ctx, int t,
                       : upload_begin(ctx, tables_room(ctx, total));
   if (rc) return rc;
   rc |= upload_put(ctx, ctx->d_nbr[t], nb.data(), sizeof(int) * nb.size());
+  rc |= upload_put(ctx, ctx->d_pbox[t], pbox.data(), total);
   rc |= upload_put(ctx, ctx->d_glist[t], gl.data(), sizeof(int) * gl.size());
   rc |= upload_put(ctx, ctx->d_ilist[t], il.data(), sizeof(int) * il.size());
   rc |= upload_put(ctx, ctx->d_ord[0], iota.data(), sizeof(int) * total);
@@ -766,6 +790,8 @@ int geoflood_init_forest(const geoflood_config* cfg, void* stream,
   okk &= alloc((void**)&ctx->d_patch[1], cap * sizeof(GfPatch));
   okk &= alloc((void**)&ctx->d_nbr[0], cap * 8 * sizeof(int));
   okk &= alloc((void**)&ctx->d_nbr[1], cap * 8 * sizeof(int));
+  okk &= alloc((void**)&ctx->d_pbox[0], cap);
+  okk &= alloc((void**)&ctx->d_pbox[1], cap);
   okk &= alloc((void**)&ctx->d_done, sizeof(unsigned));
   okk &= alloc((void**)&ctx->d_sched, 8 * sizeof(unsigned));
   okk &= alloc((void**)&ctx->d_ord[0], cap * sizeof(int));
@@ -870,6 +896,7 @@ void geoflood_destroy(geoflood_ctx* ctx) {
     cudaFree(ctx->d_patch[k]);
     cudaFree(ctx->d_lut[k]);
     cudaFree(ctx->d_nbr[k]);
+    cudaFree(ctx->d_pbox[k]);
   }
   for (auto& gr : ctx->graphs)
     if (gr.exec) cudaGraphExecDestroy(gr.exec);

@@ -126,6 +126,10 @@ struct GfView {
   float* bf;              // FP32 beds minus eta0 [cap][T][T]
   float* lof[2];          // FP32 compensation terms [cap][3][M][M]
   const int* nbr;         // [npatch][8] same-level neighbours (see below)
+  // [npatch] the refinement source box against the patch's cell centres
+  // (the first and last in each direction, in FP64): 1 it misses the
+  // patch, 2 it covers it, 0 it crosses it; or null (then per patch)
+  const unsigned char* pbox;
   unsigned* done;         // CTA completion counter of the step (or null)
   // Launch order of the patch step (or null: patch order).  sched[0] selects
   // which of ord0/ord1 this launch reads; the launch writes the other one
