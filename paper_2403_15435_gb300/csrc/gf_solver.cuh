@@ -7,6 +7,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 namespace gfk {
 
 template <typename R>
@@ -15,6 +17,26 @@ struct Side {
   R w;           // surface-deviation form only: stored surface h + b - eta0
   bool wet;      // surface-deviation form only: exact wet test of the cell
 };
+
+// Quotient a / b.  FP64: the correctly rounded division, so that the FP64
+// path rounds as written.  FP32: the approximate reciprocal times a (within
+// 2 ulp for |b| below 2^126, far above any depth, momentum or speed here);
+// the product is rounded on its own (never fused into a neighbouring
+// addition), so that every kernel variant that inlines this code rounds it
+// alike.  Zero numerators still give exact zeros, so a lake at rest keeps
+// exactly zero waves.
+template <typename R>
+__device__ __forceinline__ R qdiv(R a, R b) { return a / b; }
+template <>
+__device__ __forceinline__ float qdiv<float>(float a, float b) {
+  return __fmul_rn(a, __fdividef(1.0f, b));
+}
+
+// Product rounded on its own (FP32: never fused into a neighbouring addition).
+template <typename R>
+__device__ __forceinline__ R rmul(R a, R b) { return a * b; }
+template <>
+__device__ __forceinline__ float rmul<float>(float a, float b) { return __fmul_rn(a, b); }
 
 template <typename R>
 __device__ __forceinline__ R rmin(R a, R b) { return a < b ? a : b; }
@@ -52,10 +74,10 @@ __device__ __forceinline__ void riemann(Side<R> l, Side<R> r, R g, R drytol,
 
   int wall = 0;  // +1: right side is a wall, -1: left side is a wall
   if (!wetr && (DEV ? r.b > l.w : r.b > l.h + l.b)) {
-    const R u = l.n / l.h;
+    const R u = qdiv(l.n, l.h);
     const R c = sqrt(g * l.h);
     const R sw = rmax(c - u, c);       // fastest wave of the mirrored problem
-    const R hm = l.h + l.n / sw;       // its HLL middle depth
+    const R hm = l.h + qdiv(l.n, sw);  // its HLL middle depth
     if (r.b >= l.b + hm) {
       wall = 1;
       r.h = l.h; r.n = -l.n; r.t = l.t; r.b = l.b; er = l.h; r.w = l.w;
@@ -66,10 +88,10 @@ __device__ __forceinline__ void riemann(Side<R> l, Side<R> r, R g, R drytol,
       r.b = l.h + l.b;
     }
   } else if (!wetl && (DEV ? l.b > r.w : l.b > r.h + r.b)) {
-    const R u = r.n / r.h;
+    const R u = qdiv(r.n, r.h);
     const R c = sqrt(g * r.h);
     const R sw = rmax(u + c, c);
-    const R hm = r.h - r.n / sw;
+    const R hm = r.h - qdiv(r.n, sw);
     if (l.b >= r.b + hm) {
       wall = -1;
       l.h = r.h; l.n = -r.n; l.t = r.t; l.b = r.b; el = r.h; l.w = r.w;
@@ -81,16 +103,22 @@ __device__ __forceinline__ void riemann(Side<R> l, Side<R> r, R g, R drytol,
     }
   }
 
-  const R ul = l.h > R(0) ? l.n / l.h : R(0);
-  const R ur = r.h > R(0) ? r.n / r.h : R(0);
-  const R vl = l.h > R(0) ? l.t / l.h : R(0);
-  const R vr = r.h > R(0) ? r.t / r.h : R(0);
-  const R cl = sqrt(g * l.h);
-  const R cr = sqrt(g * r.h);
+  const R ul = l.h > R(0) ? qdiv(l.n, l.h) : R(0);
+  const R ur = r.h > R(0) ? qdiv(r.n, r.h) : R(0);
+  const R vl = l.h > R(0) ? qdiv(l.t, l.h) : R(0);
+  const R vr = r.h > R(0) ? qdiv(r.t, r.h) : R(0);
+  // FP32: the celerities from the square roots of the depths, which the
+  // Roe average needs anyway (two square roots fewer per edge), each product
+  // rounded on its own (not fused, so every inlining rounds it alike); FP64:
+  // as written, sqrt(g h)
+  constexpr bool F32 = std::is_same<R, float>::value;
+  const R ql = F32 ? sqrt(l.h) : R(0), qr = F32 ? sqrt(r.h) : R(0);
+  const R cl = F32 ? rmul(sqrt(g), ql) : sqrt(g * l.h);
+  const R cr = F32 ? rmul(sqrt(g), qr) : sqrt(g * r.h);
   R s1, s3;
   if (l.h > R(0) && r.h > R(0)) {
-    const R ql = sqrt(l.h), qr = sqrt(r.h);
-    const R uhat = (ql * ul + qr * ur) / (ql + qr);
+    const R qlw = F32 ? ql : sqrt(l.h), qrw = F32 ? qr : sqrt(r.h);
+    const R uhat = qdiv(qlw * ul + qrw * ur, qlw + qrw);
     const R chat = sqrt(g * (R(0.5) * (l.h + r.h)));
     s1 = rmin(ul - cl, uhat - chat);
     s3 = rmax(ur + cr, uhat + chat);
@@ -108,30 +136,30 @@ __device__ __forceinline__ void riemann(Side<R> l, Side<R> r, R g, R drytol,
   const R deta = DEV ? r.w - l.w : (er + r.b) - (el + l.b);
   const R den = s3 - s1;
   const R dn = r.n - l.n;
-  const R hhll = (s3 * r.h - s1 * l.h - dn) / den;
+  const R hhll = qdiv(s3 * r.h - s1 * l.h - dn, den);
 
   // depth jump of the stationary wave, bounded for non-negative depths
   R dhs = -db;
   bool clamped = false;
   if (s1 < R(0) && s3 > R(0)) {
-    const R lo = hhll * den / s1;
-    const R hi = hhll * den / s3;
+    const R lo = qdiv(hhll * den, s1);
+    const R hi = qdiv(hhll * den, s3);
     if (dhs < lo) { dhs = lo; clamped = true; }
     if (dhs > hi) { dhs = hi; clamped = true; }
   } else if (s1 >= R(0)) {
-    const R hi = s1 > R(0) ? hhll * den / s1 : dhs;
+    const R hi = s1 > R(0) ? qdiv(hhll * den, s1) : dhs;
     if (dhs > hi) { dhs = hi; clamped = true; }
     if (dhs < -l.h) { dhs = -l.h; clamped = true; }
   } else {
-    const R lo = s3 < R(0) ? hhll * den / s3 : dhs;
+    const R lo = s3 < R(0) ? qdiv(hhll * den, s3) : dhs;
     if (dhs < lo) { dhs = lo; clamped = true; }
     if (dhs > r.h) { dhs = r.h; clamped = true; }
   }
   const R d1 = clamped ? (r.h - l.h) - dhs : deta;
   const R d3 = (r.n * ur - l.n * ul) + g * hbar * deta;
 
-  const R b1 = (s3 * d1 - dn) / den;
-  const R b3 = (dn - s1 * d1) / den;
+  const R b1 = qdiv(s3 * d1 - dn, den);
+  const R b3 = qdiv(dn - s1 * d1, den);
   const R b2 = d3 - (s1 * s1 * b1 + s3 * s3 * b3);
 
   Z[0] = s1 * b1;
@@ -175,7 +203,10 @@ __device__ __forceinline__ R dot3(const R* a, const R* b) {
 // edge before, Zp at the edge after).  Component c of a wave array is at
 // [c * ST] (ST = 1: packed; larger: one plane per component).  nodry = false
 // switches the correction off (an edge touching a dry cell).
-template <typename R, int ST = 1>
+// Z3Z = true: the middle wave's mass component (Z[3], zero by construction
+// of the solver) is neither read nor added, and A+dQ is formed as the wave
+// minus its A-dQ part; both give the same values up to the sign of zeros.
+template <typename R, int ST = 1, bool Z3Z = false>
 __device__ __forceinline__ void edge_fluxes(const R* Z, const R* S,
                                             const R* Zm, const R* Zp, R nu,
                                             bool nodry, R (&am)[3],
@@ -183,7 +214,7 @@ __device__ __forceinline__ void edge_fluxes(const R* Z, const R* S,
   R cm[3][3], cp[3][3], cf[3][3];
   R z[9];
 #pragma unroll
-  for (int c = 0; c < 9; ++c) z[c] = Z[c * ST];
+  for (int c = 0; c < 9; ++c) z[c] = (Z3Z && c == 3) ? R(0) : Z[c * ST];
 #pragma unroll
   for (int p = 0; p < 3; ++p) {
     const R sp = S[p * ST];
@@ -192,15 +223,18 @@ __device__ __forceinline__ void edge_fluxes(const R* Z, const R* S,
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       cm[p][k] = z[3 * p + k] * wm;
-      cp[p][k] = z[3 * p + k] * wp;
+      cp[p][k] = Z3Z ? z[3 * p + k] - cm[p][k] : z[3 * p + k] * wp;
       cf[p][k] = R(0);
     }
     if (sp != R(0) && nodry) {
-      const R zz = dot3(z + 3 * p, z + 3 * p);
+      const bool m0 = Z3Z && p == 1;  // mass component known zero
+      const R zz = m0 ? z[4] * z[4] + z[5] * z[5] : dot3(z + 3 * p, z + 3 * p);
       if (zz != R(0)) {
         const R* up = sp > R(0) ? Zm : Zp;
-        const R u3[3] = {up[(3 * p) * ST], up[(3 * p + 1) * ST], up[(3 * p + 2) * ST]};
-        const R th = dot3(u3, z + 3 * p) / zz;
+        const R u3[3] = {m0 ? R(0) : up[(3 * p) * ST], up[(3 * p + 1) * ST],
+                         up[(3 * p + 2) * ST]};
+        const R num = m0 ? u3[1] * z[4] + u3[2] * z[5] : dot3(u3, z + 3 * p);
+        const R th = qdiv(num, zz);
         const R phi = mc(th);
         const R sg = sp > R(0) ? R(1) : R(-1);
         const R as = sp > R(0) ? sp : -sp;
@@ -212,9 +246,15 @@ __device__ __forceinline__ void edge_fluxes(const R* Z, const R* S,
   }
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    am[k] = (cm[0][k] + cm[2][k]) + cm[1][k];
-    ap[k] = (cp[0][k] + cp[2][k]) + cp[1][k];
-    ff[k] = (cf[0][k] + cf[2][k]) + cf[1][k];
+    if (Z3Z && k == 0) {
+      am[0] = cm[0][0] + cm[2][0];
+      ap[0] = cp[0][0] + cp[2][0];
+      ff[0] = cf[0][0] + cf[2][0];
+    } else {
+      am[k] = (cm[0][k] + cm[2][k]) + cm[1][k];
+      ap[k] = (cp[0][k] + cp[2][k]) + cp[1][k];
+      ff[k] = (cf[0][k] + cf[2][k]) + cf[1][k];
+    }
   }
 }
 
@@ -234,11 +274,11 @@ __device__ __forceinline__ void tsplit(R h, R ma, R mo, R eta, bool wet,
   plus[0] = plus[1] = plus[2] = R(0);
   minus[0] = minus[1] = minus[2] = R(0);
   if (!wet) return;
-  const R w = ma / h;
-  const R z = mo / h;
+  const R w = qdiv(ma, h);
+  const R z = qdiv(mo, h);
   const R c = sqrt(g * h);
-  const R a1 = ((w + c) * d[0] - d[1]) / (R(2) * c);
-  const R a3 = (d[1] - (w - c) * d[0]) / (R(2) * c);
+  const R a1 = qdiv((w + c) * d[0] - d[1], R(2) * c);
+  const R a3 = qdiv(d[1] - (w - c) * d[0], R(2) * c);
   const R a2 = d[2] - z * d[0];
   const R l1 = w - c, l2 = w, l3 = w + c;
   const R c1 = l1 * a1, c3 = l3 * a3, c2 = l2 * a2;

@@ -547,7 +547,8 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
       // edge's place (line, a) in the sweep
       R* w = W + ((line - L0) * NE + a + 1);
 #pragma unroll
-      for (int q = 0; q < 9; ++q) w[q * NEDGE] = Z[q];
+      for (int q = 0; q < 9; ++q)
+        if (!(DEV && q == 3)) w[q * NEDGE] = Z[q];  // FP32: Z[3] is zero, not read
       w[9 * NEDGE] = S[0];
       w[10 * NEDGE] = S[1];
       w[11 * NEDGE] = S[2];
@@ -565,8 +566,8 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
         const int cl = dir == 0 ? tix<M>(a - 1, line) : tix<M>(line, a - 1);
         const int cr = dir == 0 ? tix<M>(a, line) : tix<M>(line, a);
         const bool wet = corr && wetc(cl) && wetc(cr);
-        gfk::edge_fluxes<R, NEDGE>(w, w + 9 * NEDGE, w - 1, w + 1, nu, wet, AMr[r],
-                                   APr[r], FFr[r]);
+        gfk::edge_fluxes<R, NEDGE, DEV>(w, w + 9 * NEDGE, w - 1, w + 1, nu, wet,
+                                        AMr[r], APr[r], FFr[r]);
         if (line >= 0 && line < M) {
           R m = R(0);
 #pragma unroll
@@ -810,15 +811,19 @@ __device__ __forceinline__ int patch_body(const GfGeom& G, const GfView& V,
       }
       const bool wnew = gfk::wet_dev(o[0], bc, drytol, dtf, margin);
       if (mn > 0.0f && wnew) {
+        // approximate reciprocals and h^(-4/3) by the fast power (relative
+        // error about 1e-6, far inside the FP32 path's tolerance); products
+        // rounded on their own, so every kernel variant rounds them alike
         const float h = o[0] - bc;
-        const float u = o[1] / h, v = o[2] / h;
+        const float rh = __fdividef(1.0f, h);
+        const float u = __fmul_rn(o[1], rh), v = __fmul_rn(o[2], rh);
         const float sp = sqrtf(u * u + v * v);
-        const float D = g * mn * mn * sp / (h * cbrtf(h));
-        const float den = 1.0f + dtr * D;
-        o[1] = o[1] / den;
-        o[2] = o[2] / den;
-        lo[1] = lo[1] / den;
-        lo[2] = lo[2] / den;
+        const float D = g * mn * mn * sp * __powf(h, -4.0f / 3.0f);
+        const float rden = __fdividef(1.0f, 1.0f + dtr * D);
+        o[1] = __fmul_rn(o[1], rden);
+        o[2] = __fmul_rn(o[2], rden);
+        lo[1] = __fmul_rn(lo[1], rden);
+        lo[2] = __fmul_rn(lo[2], rden);
       }
       if (!wnew) { o[1] = 0.0f; o[2] = 0.0f; lo[1] = 0.0f; lo[2] = 0.0f; }
 #pragma unroll
