@@ -57,6 +57,11 @@ class _Cfg(C.Structure):
         ("subcycle", C.c_int), ("n_hydro", C.c_int), ("inflow_side", C.c_int),
         ("inflow_lo", C.c_double), ("inflow_hi", C.c_double), ("inflow_tau", C.c_double),
         ("hydro_t", C.c_double * 16), ("hydro_q", C.c_double * 16),
+        ("nregions", C.c_int), ("region_minlevel", C.c_int * 8),
+        ("region_maxlevel", C.c_int * 8),
+        ("region_x0", C.c_double * 8), ("region_x1", C.c_double * 8),
+        ("region_y0", C.c_double * 8), ("region_y1", C.c_double * 8),
+        ("region_t0", C.c_double * 8), ("region_t1", C.c_double * 8),
     ]
 
 
@@ -213,6 +218,14 @@ def _cfg_struct(cfg) -> _Cfg:
     c.inflow_lo = float(cfg.inflow_lo)
     c.inflow_hi = float(cfg.inflow_hi)
     c.inflow_tau = float(cfg.inflow_tau)
+    regions = list(getattr(cfg, "regions", ()))
+    assert len(regions) <= 8
+    c.nregions = len(regions)
+    for k, (x0, x1, y0, y1, t0, t1, lmin, lmax) in enumerate(regions):
+        c.region_x0[k], c.region_x1[k] = float(x0), float(x1)
+        c.region_y0[k], c.region_y1[k] = float(y0), float(y1)
+        c.region_t0[k], c.region_t1[k] = float(t0), float(t1)
+        c.region_minlevel[k], c.region_maxlevel[k] = int(lmin), int(lmax)
     return c
 
 
@@ -220,6 +233,7 @@ class OracleForest:
     """Quadtree forest of patches advanced by the oracle."""
 
     def __init__(self, cfg, dem=None):
+        self._h = None
         self.cfg = cfg
         self._c = _cfg_struct(cfg)
         self._h = lib().oracle_forest_new(C.byref(self._c))

@@ -1183,7 +1183,7 @@ static void set_leaves(oracle_forest* f, int n, const int* lev, const int* px,
 
 oracle_forest* oracle_forest_new(const oracle_config* cfg) {
   if (cfg->mx < 4 || cfg->minlevel < 0 || cfg->maxlevel < cfg->minlevel ||
-      cfg->maxlevel >= MAXLEV)
+      cfg->maxlevel >= MAXLEV || cfg->nregions < 0 || cfg->nregions > ORACLE_MAXREGION)
     return NULL;
   oracle_forest* f = forest_alloc(cfg);
   int L = cfg->minlevel;
@@ -1520,7 +1520,12 @@ int oracle_forest_step(oracle_forest* f, double t_target, int max_steps,
  * to 3: wet and flowing fast, deep-and-moving, or a deviating surface; the
  * source region below src_level, criterion 4), 1 keep (the source region at
  * or above src_level), 0 nothing; *gl = the highest level a flow grade asks
- * for (criterion 5), -1 if none. */
+ * for (criterion 5), -1 if none.  Then the refinement regions active at the
+ * state's time (criterion 4's regions between a minimum and a maximum
+ * level): a cell whose centre lies in one or more of them wants the level
+ * the rest asks for (L + 1 to refine, L to keep, L - 1 otherwise, or a
+ * grade's level if higher) moved into [largest minimum, largest maximum],
+ * and that level becomes its request (*gl then -1). */
 static void cell_flag(const oracle_forest* f, int p, int i, int j, int* r_out, int* gl_out) {
   size_t TT = (size_t)f->T * f->T, id = TI(f, i, j);
   const double* q = f->tile[p];
@@ -1545,6 +1550,26 @@ static void cell_flag(const oracle_forest* f, int p, int i, int j, int* r_out, i
       yc >= f->c.src_box[2] && yc <= f->c.src_box[3]) {
     if (L < f->c.src_level) r = 2;
     else if (r < 1) r = 1;
+  }
+  {
+    int in = 0, rmin = -1, rmax = -1;
+    for (k = 0; k < f->c.nregions; ++k) {
+      if (!(f->t >= f->c.region_t0[k] && f->t <= f->c.region_t1[k])) continue;
+      if (!(xc >= f->c.region_x0[k] && xc <= f->c.region_x1[k] &&
+            yc >= f->c.region_y0[k] && yc <= f->c.region_y1[k]))
+        continue;
+      in = 1;
+      if (f->c.region_minlevel[k] > rmin) rmin = f->c.region_minlevel[k];
+      if (f->c.region_maxlevel[k] > rmax) rmax = f->c.region_maxlevel[k];
+    }
+    if (in) {
+      int want = r == 2 ? L + 1 : (r == 1 ? L : L - 1);
+      if (gl > want) want = gl;
+      if (want < rmin) want = rmin;
+      if (want > rmax) want = rmax;
+      r = want > L ? 2 : (want == L ? 1 : 0);
+      gl = -1;
+    }
   }
   *r_out = r;
   *gl_out = gl;

@@ -22,6 +22,7 @@ extern "C" {
 #endif
 
 #define ORACLE_MAXDEM 4 /* DEMs per forest */
+#define ORACLE_MAXREGION 8 /* refinement regions per forest */
 #define ORACLE_BC_WALL 0
 #define ORACLE_BC_EXTRAP 1
 
@@ -69,6 +70,18 @@ typedef struct {
   int n_hydro, inflow_side;
   double inflow_lo, inflow_hi, inflow_tau;
   double hydro_t[16], hydro_q[16];
+  /* refinement regions (Sec. 4.1 criterion 4: regions refined to a desired
+   * resolution between user-given minimum and maximum levels; Sec. 6.4:
+   * particular locations or times): while region_t0[k] <= t <= region_t1[k]
+   * (t the time of the state), a cell whose centre lies in
+   * [region_x0[k], region_x1[k]] x [region_y0[k], region_y1[k]] asks for a
+   * level of at least region_minlevel[k] and at most region_maxlevel[k];
+   * where several active regions hold the centre, the largest minimum and
+   * the largest maximum apply.  nregions <= ORACLE_MAXREGION. */
+  int nregions;
+  int region_minlevel[8], region_maxlevel[8];
+  double region_x0[8], region_x1[8], region_y0[8], region_y1[8];
+  double region_t0[8], region_t1[8];
 } oracle_config;
 
 typedef struct oracle_forest oracle_forest;

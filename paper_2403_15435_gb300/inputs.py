@@ -75,6 +75,11 @@ class Config:
     inflow_lo: float = 0.0
     inflow_hi: float = 0.0
     inflow_tau: float = 1e-4
+    # refinement regions (Sec. 4.1 criterion 4, Sec. 6.4): up to 8
+    # (x0, x1, y0, y1, t0, t1, minlevel, maxlevel); while t0 <= t <= t1 a
+    # cell whose centre lies in the box asks for a level in
+    # [minlevel, maxlevel] (overlaps: the largest of each)
+    regions: Tuple[Tuple[float, float, float, float, float, float, int, int], ...] = ()
 
 
 @dataclasses.dataclass
