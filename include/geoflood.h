@@ -143,6 +143,23 @@ typedef struct {
    * rates bound the next DT = cfl_desired / max_L(cmax_L / n_L).  Steps and
    * max_steps count macro steps; the patch step has a single variant. */
   int subcycle;
+  /* Refinement regions (Sec. 4.1 criterion 4: regions refined to a desired
+   * resolution between user-given minimum and maximum levels; Sec. 6.4:
+   * particular locations or times).  nregions = 0..8.  While
+   * region_t0[k] <= t <= region_t1[k] (t the time of the scenario's state),
+   * a cell whose centre lies in [region_x0[k], region_x1[k]] x
+   * [region_y0[k], region_y1[k]] asks for a level of at least
+   * region_minlevel[k] and at most region_maxlevel[k] (minlevel <= these <=
+   * maxlevel): the level the other criteria ask for (L + 1 to refine, L to
+   * keep, L - 1 otherwise, or a flow grade's level if higher) is moved into
+   * [the largest minimum, the largest maximum] of the active regions that
+   * hold the centre, dry cells included.  The learned tagger's requests are
+   * bounded the same way.  The 2:1 balance of a regrid may still refine
+   * past a region's maximum next to finer patches. */
+  int nregions;
+  int region_minlevel[8], region_maxlevel[8];
+  double region_x0[8], region_x1[8], region_y0[8], region_y1[8];
+  double region_t0[8], region_t1[8];
 } geoflood_config;
 
 typedef struct geoflood_ctx geoflood_ctx;

@@ -1285,7 +1285,33 @@ __global__ void k_align_buffers(const __grid_constant__ GfGeom G, const __grid_c
   }
 }
 
-// Plain tagger (Sec. 4.1 criteria 1, 3, 4; Sec. 6.4).
+// Bound what one cell asks for by the refinement regions holding its centre
+// (Sec. 4.1 criterion 4, Sec. 6.4): rmin, rmax the largest minimum and the
+// largest maximum (rmax < 0: none holds it).  The level the cell asks for
+// (L + 1 for r = 2, L for r = 1, L - 1 otherwise, or the grade's level cgl
+// if higher) is moved into [rmin, rmax] and becomes r (cgl then -1); netw
+// collects the bounded level of a refinement request at this cell (the
+// learned tagger's request), L + 1 where no region holds it.
+__device__ __forceinline__ void cov_region_bound(int L, int& r, int& cgl, int& netw,
+                                                 int rmin, int rmax) {
+  if (rmax < 0) {
+    netw = L + 1 > netw ? L + 1 : netw;
+    return;
+  }
+  int want = r == 2 ? L + 1 : (r == 1 ? L : L - 1);
+  if (cgl > want) want = cgl;
+  if (want < rmin) want = rmin;
+  if (want > rmax) want = rmax;
+  r = want > L ? 2 : (want == L ? 1 : 0);
+  cgl = -1;
+  int nw = L + 1;
+  if (nw < rmin) nw = rmin;
+  if (nw > rmax) nw = rmax;
+  netw = nw > netw ? nw : netw;
+}
+
+// Plain tagger (Sec. 4.1 criteria 1 to 5; Sec. 6.4), with the refinement
+// regions active at the scenario's time bounding what each cell asks for.
 template <typename T>
 __global__ void k_tags(const __grid_constant__ GfGeom G, const __grid_constant__ GfView V,
                        const GfTagOut O) {
@@ -1293,38 +1319,90 @@ __global__ void k_tags(const __grid_constant__ GfGeom G, const __grid_constant__
   const GfPatch P = V.patch[p];
   Geo<T> e(G, V);
   const int M = G.M;
+  const int L = P.level;
   const int cur = V.ctl[P.scen].cur;
   // per-level cell sizes from the host's table (the same division as
   // Geo::dx); surfaces are compared with eta0, relative to which the
   // deviation form stores them
-  const double sdx = G.dxl[P.level], sdy = G.dyl[P.level];
+  const double sdx = G.dxl[L], sdy = G.dyl[L];
   const double eref = Geo<T>::DEV ? 0.0 : V.scen[P.scen].eta0;
   auto xcen = [&](int i) { return G.xlower + ((double)((long long)P.px * M + i) + 0.5) * sdx; };
   auto ycen = [&](int j) { return G.ylower + ((double)((long long)P.py * M + j) + 0.5) * sdy; };
-  // the source box against the patch's first and last cell centres (the
-  // centres grow with the index, so the per-cell test is needed only for a
-  // patch that the box edge crosses): from the host's per-patch table, or
-  // computed once by thread 0 (FP64 is slow on this part) and shared
-  int box;  // bit 0: the box misses the patch, bit 1: covers it
+  // the source box and the regions against the patch's first and last cell
+  // centres (the centres grow with the index, so the per-cell test is needed
+  // only where an edge crosses the patch): from the host's per-patch table,
+  // or computed once by thread 0 (FP64 is slow on this part) and shared;
+  // without the table every region is tested per cell
+  unsigned box;  // bits 0-1: 1 the box misses the patch, 2 covers it
   if (V.pbox != nullptr) {
     box = V.pbox[p];
   } else {
-    __shared__ int sbox;
+    __shared__ unsigned sbox;
     if (threadIdx.x == 0) {
       const double x0 = xcen(0), x1 = xcen(M - 1), y0 = ycen(0), y1 = ycen(M - 1);
       const bool none = x1 < G.src_box[0] || x0 > G.src_box[1] || y1 < G.src_box[2] ||
                         y0 > G.src_box[3];
       const bool all = x0 >= G.src_box[0] && x1 <= G.src_box[1] && y0 >= G.src_box[2] &&
                        y1 <= G.src_box[3];
-      sbox = (none ? 1 : 0) | (all ? 2 : 0);
+      sbox = (none ? 1u : 0u) | (all ? 2u : 0u);
     }
     __syncthreads();
     box = sbox;
   }
-  const bool box_none = (box & 1) != 0, box_all = (box & 2) != 0;
-  const int rbox = P.level < G.src_level ? 2 : 1;  // a cell in the box asks this
-  int m = box_all ? rbox : 0;
-  int gl = -1;  // the highest level a flow grade asks for (criterion 5)
+  const bool box_none = (box & 1u) != 0u, box_all = (box & 2u) != 0u;
+  const int rbox = L < G.src_level ? 2 : 1;  // a cell in the box asks this
+  // refinement regions active now: those covering the patch bound every
+  // cell alike (cov_min, cov_max), those crossing it are tested per cell
+  const double tnow = V.ctl[P.scen].t;
+  int cov_min = -1, cov_max = -1;
+  unsigned cross = 0u;
+  for (int r = 0; r < G.nregions; ++r) {
+    if (!(tnow >= G.rt0[r] && tnow <= G.rt1[r])) continue;
+    const unsigned cl = V.pbox != nullptr ? (box >> (2 + 2 * r)) & 3u : 0u;
+    if (cl == 1u) continue;
+    if (cl == 2u) {
+      cov_min = G.rminl[r] > cov_min ? G.rminl[r] : cov_min;
+      cov_max = G.rmaxl[r] > cov_max ? G.rmaxl[r] : cov_max;
+    } else {
+      cross |= 1u << r;
+    }
+  }
+  const bool regs = cov_max >= 0 || cross != 0u;
+  int m = box_all && !regs ? rbox : 0;
+  int gl = -1;    // the highest level a flow grade asks for (criterion 5)
+  int netw = -1;  // with regions: the highest level the learned tagger may ask for
+  // Cell (i, j) asks r (2 refine, 1 keep, 0 nothing) and grade level cgl
+  // from the criteria; then the source box, then the regions holding its
+  // centre move the level it asks for into their bounds.
+  auto finish_cell = [&](int i, int j, int r, int cgl) {
+    const bool box_cell = !box_none && !box_all;
+    double xc = 0.0, yc = 0.0;
+    if (box_cell || cross != 0u) {
+      xc = xcen(i);
+      yc = ycen(j);
+    }
+    // (without regions a box covering the patch is already in m)
+    const bool in_box = box_cell ? (xc >= G.src_box[0] && xc <= G.src_box[1] &&
+                                    yc >= G.src_box[2] && yc <= G.src_box[3])
+                                 : box_all && regs;
+    if (in_box) {
+      if (rbox == 2) r = 2;
+      else if (r < 1) r = 1;
+    }
+    if (regs) {
+      int rmin = cov_min, rmax = cov_max;
+      for (unsigned bits = cross; bits != 0u; bits &= bits - 1u) {
+        const int k = __ffs(bits) - 1;
+        if (xc >= G.rx0[k] && xc <= G.rx1[k] && yc >= G.ry0[k] && yc <= G.ry1[k]) {
+          rmin = G.rminl[k] > rmin ? G.rminl[k] : rmin;
+          rmax = G.rmaxl[k] > rmax ? G.rmaxl[k] : rmax;
+        }
+      }
+      cov_region_bound(L, r, cgl, netw, rmin, rmax);
+    }
+    m = r > m ? r : m;
+    gl = cgl > gl ? cgl : gl;
+  };
   if constexpr (Geo<T>::DEV) {
     // FP32 deviation form: up to four cells per thread at once, so that a
     // block waits for two rounds of loads (surfaces and beds, then the
@@ -1356,8 +1434,7 @@ __global__ void k_tags(const __grid_constant__ GfGeom G, const __grid_constant__
       for (int u = 0; u < U; ++u) {
         if (!ok[u]) continue;
         const int k = k0 + u * (int)blockDim.x + (int)threadIdx.x;
-        const int i = k % M, j = k / M;
-        int r = 0;
+        int r = 0, cgl = -1;
         if (deep[u]) {
           // depth w - b, speed test without a division, surface deviation
           // |w| (one mismatch with the FP64 criterion is possible at a
@@ -1369,18 +1446,10 @@ __global__ void k_tags(const __grid_constant__ GfGeom G, const __grid_constant__
           for (int g = 0; g < G.ngrades; ++g) {
             const float tv = G.grade_valuef[g];
             const bool over = G.grade_kind[g] == 0 ? h > tv : f2 > (tv * h) * (tv * h);
-            if (over && G.grade_level[g] > gl) gl = G.grade_level[g];
+            if (over && G.grade_level[g] > cgl) cgl = G.grade_level[g];
           }
         }
-        if (!box_none && !box_all) {
-          const double xc = xcen(i), yc = ycen(j);
-          if (xc >= G.src_box[0] && xc <= G.src_box[1] && yc >= G.src_box[2] &&
-              yc <= G.src_box[3]) {
-            if (rbox == 2) r = 2;
-            else if (r < 1) r = 1;
-          }
-        }
-        m = r > m ? r : m;
+        finish_cell(k % M, k / M, r, cgl);
       }
       if (__syncthreads_or(m == 2)) m = 2;
     }
@@ -1391,51 +1460,23 @@ __global__ void k_tags(const __grid_constant__ GfGeom G, const __grid_constant__
       if (k < M * M) {
         const int i = k % M, j = k / M;
         const int c = e.tix(i, j);
-        int r = 0;
-        if constexpr (Geo<T>::DEV) {
-          // deviation form in FP32: depth w - b, speed test without a
-          // division, surface deviation |w| (one mismatch with the FP64
-          // criterion is possible at a threshold tie; counted in the tests)
-          const float* q = e.qp(p, cur);
-          const int TT = G.T * G.T;
-          const float w = q[c], b = e.bp(p)[c];
-          const float h = w - b;
-          if (h > G.tag_depthf) {
-            const float hu = q[TT + c], hv = q[2 * TT + c], st = G.tag_speedf * h;
-            const float f2 = hu * hu + hv * hv;
-            if (f2 > st * st || fabsf(w) > G.tag_detaf || f2 > G.tag_fluxf * G.tag_fluxf) r = 2;
-            for (int g = 0; g < G.ngrades; ++g) {
-              const float tv = G.grade_valuef[g];
-              const bool over = G.grade_kind[g] == 0 ? h > tv : f2 > (tv * h) * (tv * h);
-              if (over && G.grade_level[g] > gl) gl = G.grade_level[g];
-            }
-          }
-        } else {
-          double v4[4];
-          e.load(p, cur, c, v4);
-          const double h = v4[0];
-          if (h > G.tag_depth) {
-            const double u = v4[1] / h, v = v4[2] / h;
-            const double sp = sqrt(u * u + v * v);
-            const double eta = h + v4[3];
-            const double flux = sqrt(v4[1] * v4[1] + v4[2] * v4[2]);
-            if (sp > G.tag_speed || fabs(eta - eref) > G.tag_deta) r = 2;
-            if (flux > G.tag_flux) r = 2;
-            for (int g = 0; g < G.ngrades; ++g) {
-              const double val = G.grade_kind[g] == 0 ? h : sp;
-              if (val > G.grade_value[g] && G.grade_level[g] > gl) gl = G.grade_level[g];
-            }
+        int r = 0, cgl = -1;
+        double v4[4];
+        e.load(p, cur, c, v4);
+        const double h = v4[0];
+        if (h > G.tag_depth) {
+          const double u = v4[1] / h, v = v4[2] / h;
+          const double sp = sqrt(u * u + v * v);
+          const double eta = h + v4[3];
+          const double flux = sqrt(v4[1] * v4[1] + v4[2] * v4[2]);
+          if (sp > G.tag_speed || fabs(eta - eref) > G.tag_deta) r = 2;
+          if (flux > G.tag_flux) r = 2;
+          for (int g = 0; g < G.ngrades; ++g) {
+            const double val = G.grade_kind[g] == 0 ? h : sp;
+            if (val > G.grade_value[g] && G.grade_level[g] > cgl) cgl = G.grade_level[g];
           }
         }
-        if (!box_none && !box_all) {
-          const double xc = xcen(i), yc = ycen(j);
-          if (xc >= G.src_box[0] && xc <= G.src_box[1] && yc >= G.src_box[2] &&
-              yc <= G.src_box[3]) {
-            if (rbox == 2) r = 2;
-            else if (r < 1) r = 1;
-          }
-        }
-        m = r > m ? r : m;
+        finish_cell(i, j, r, cgl);
       }
       if (__syncthreads_or(m == 2)) {
         m = 2;
@@ -1445,34 +1486,45 @@ __global__ void k_tags(const __grid_constant__ GfGeom G, const __grid_constant__
   }
   // criterion 5 matters only when no cell asks for full refinement
   gl = __reduce_max_sync(0xffffffffu, gl);
-  __shared__ int wg[32];
-  if ((threadIdx.x & 31) == 0) wg[threadIdx.x >> 5] = gl;
+  netw = __reduce_max_sync(0xffffffffu, netw);
+  __shared__ int wg[32], wn[32];
+  if ((threadIdx.x & 31) == 0) {
+    wg[threadIdx.x >> 5] = gl;
+    wn[threadIdx.x >> 5] = netw;
+  }
   m = __reduce_max_sync(0xffffffffu, m);
   __shared__ int wm[32];
   if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
   __syncthreads();
   if (threadIdx.x == 0) {
-    int mm = 0, gmax = -1;
+    int mm = 0, gmax = -1, nmax = -1;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
       mm = wm[w] > mm ? wm[w] : mm;
       gmax = wg[w] > gmax ? wg[w] : gmax;
+      nmax = wn[w] > nmax ? wn[w] : nmax;
     }
     // a flow grade above the patch's level is a request for refinement
-    const bool grade_up = mm < 2 && gmax > P.level;
+    const bool grade_up = mm < 2 && gmax > L;
     // the plain criterion's own verdict: recorded, turned into training
     // labels, or counted as a miss where the patch could still be refined
     const int raw = grade_up ? 2 : mm;
     if (O.raw) O.raw[p] = (uint8_t)raw;
     if (O.label && raw == 2) O.label[p] = 1.0f;
-    if (O.misses && raw == 2 && P.level < G.maxlevel) atomicAdd(O.misses, 1u);
-    // learned tags add refinement (or keep a fine patch) on top of it
+    if (O.misses && raw == 2 && L < G.maxlevel) atomicAdd(O.misses, 1u);
+    // learned tags add refinement (or keep a fine patch) on top of it: a
+    // request for level L + 1 at every cell, bounded by the regions like
+    // the criterion's own (nmax: the highest bounded level; every cell was
+    // visited unless a cell already asked for refinement)
     const bool learned = O.logit && O.logit[p] > O.logit_thr;
-    if (learned) mm = 2;
+    if (learned) {
+      if (!regs || nmax > L) mm = 2;
+      else if (nmax == L && mm < 1) mm = 1;
+    }
     uint8_t f;
-    if (mm == 2) f = P.level < G.maxlevel ? 1 : 0;
-    else if (gmax > P.level) f = 1;
-    else if (gmax == P.level || mm == 1) f = 0;
-    else f = P.level > G.minlevel ? 2 : 0;
+    if (mm == 2) f = L < G.maxlevel ? 1 : 0;
+    else if (gmax > L) f = 1;
+    else if (gmax == L || mm == 1) f = 0;
+    else f = L > G.minlevel ? 2 : 0;
     if (O.flags) O.flags[p] = f;
   }
 }

@@ -84,7 +84,7 @@ struct geoflood_ctx {
   GfPatch* d_patch[2] = {nullptr, nullptr};
   int* d_lut[2] = {nullptr, nullptr};
   int* d_nbr[2] = {nullptr, nullptr};
-  unsigned char* d_pbox[2] = {nullptr, nullptr};
+  unsigned* d_pbox[2] = {nullptr, nullptr};
   unsigned* d_done = nullptr;
   unsigned* d_sched = nullptr;        // launch-order parity and counters
   int* d_ord[2] = {nullptr, nullptr}; // launch orders of the patch step
@@ -325,10 +325,10 @@ size_t upload_room(std::initializer_list<size_t> sizes) {
 
 // Staging room that upload_tables needs for `total` patches (an upper bound:
 // neighbour table, ghost regions, inflow list, launch order, patch table,
-// lookup tables, scenarios).
+// box and region classes, lookup tables, scenarios).
 size_t tables_room(const geoflood_ctx* ctx, size_t total) {
   return upload_room({sizeof(int) * 8 * total, sizeof(int) * 8 * total, sizeof(int) * total,
-                      sizeof(int) * total, sizeof(GfPatch) * total, total,
+                      sizeof(int) * total, sizeof(GfPatch) * total, sizeof(unsigned) * total,
                       sizeof(int) * (size_t)ctx->nscen * ctx->G.lut_per_scen,
                       sizeof(GfScenario) * ctx->nscen});
 }
@@ -396,10 +396,11 @@ int upload_tables(geoflood_ctx* ctx, int t,
   }
   ctx->nglist_c[t] = (int)gl.size();
   gl.insert(gl.end(), glf.begin(), glf.end());
-  // the source box against each patch's first and last cell centres, in
-  // the tag kernel's FP64 arithmetic (this file is compiled without
-  // contraction, like the device code)
-  std::vector<unsigned char> pbox(total);
+  // the source box and the refinement regions against each patch's first
+  // and last cell centres, in the tag kernel's FP64 arithmetic (this file is
+  // compiled without contraction, like the device code): two bits each,
+  // 1 misses the patch, 2 covers it, 0 crosses it
+  std::vector<unsigned> pbox(total);
   {
     const GfGeom& G = ctx->G;
     const int M = G.M;
@@ -410,11 +411,15 @@ int upload_tables(geoflood_ctx* ctx, int t,
       const double x1 = G.xlower + ((double)((long long)P.px * M + M - 1) + 0.5) * dx;
       const double y0 = G.ylower + ((double)((long long)P.py * M) + 0.5) * dy;
       const double y1 = G.ylower + ((double)((long long)P.py * M + M - 1) + 0.5) * dy;
-      const bool none = x1 < G.src_box[0] || x0 > G.src_box[1] || y1 < G.src_box[2] ||
-                        y0 > G.src_box[3];
-      const bool all = x0 >= G.src_box[0] && x1 <= G.src_box[1] && y0 >= G.src_box[2] &&
-                       y1 <= G.src_box[3];
-      pbox[k] = (unsigned char)((none ? 1 : 0) | (all ? 2 : 0));
+      auto cls = [&](double bx0, double bx1, double by0, double by1) -> unsigned {
+        const bool none = x1 < bx0 || x0 > bx1 || y1 < by0 || y0 > by1;
+        const bool all = x0 >= bx0 && x1 <= bx1 && y0 >= by0 && y1 <= by1;
+        return (none ? 1u : 0u) | (all ? 2u : 0u);
+      };
+      unsigned bits = cls(G.src_box[0], G.src_box[1], G.src_box[2], G.src_box[3]);
+      for (int r = 0; r < G.nregions; ++r)
+        bits |= cls(G.rx0[r], G.rx1[r], G.ry0[r], G.ry1[r]) << (2 + 2 * r);
+      pbox[k] = bits;
     }
   }
   ctx->nglist[t] = (int)gl.size();
@@ -448,7 +453,7 @@ int upload_tables(geoflood_ctx* ctx, int t,
                       : upload_begin(ctx, tables_room(ctx, total));
   if (rc) return rc;
   rc |= upload_put(ctx, ctx->d_nbr[t], nb.data(), sizeof(int) * nb.size());
-  rc |= upload_put(ctx, ctx->d_pbox[t], pbox.data(), total);
+  rc |= upload_put(ctx, ctx->d_pbox[t], pbox.data(), sizeof(unsigned) * total);
   rc |= upload_put(ctx, ctx->d_glist[t], gl.data(), sizeof(int) * gl.size());
   rc |= upload_put(ctx, ctx->d_ilist[t], il.data(), sizeof(int) * il.size());
   rc |= upload_put(ctx, ctx->d_ord[0], iota.data(), sizeof(int) * total);
@@ -676,6 +681,12 @@ int geoflood_init_forest(const geoflood_config* cfg, void* stream,
     if ((c.grade_kind[k] != 0 && c.grade_kind[k] != 1) || c.grade_level[k] < c.minlevel ||
         c.grade_level[k] > c.maxlevel)
       return GEOFLOOD_ERR_ARG;
+  if (c.nregions < 0 || c.nregions > GF_MAXREGION) return GEOFLOOD_ERR_ARG;
+  for (int k = 0; k < c.nregions; ++k)
+    if (c.region_minlevel[k] < c.minlevel || c.region_maxlevel[k] > c.maxlevel ||
+        c.region_minlevel[k] > c.region_maxlevel[k] || !(c.region_x1[k] >= c.region_x0[k]) ||
+        !(c.region_y1[k] >= c.region_y0[k]) || !(c.region_t1[k] >= c.region_t0[k]))
+      return GEOFLOOD_ERR_ARG;
   geoflood_ctx* ctx = new geoflood_ctx();
   ctx->cfg = c;
   ctx->st = static_cast<cudaStream_t>(stream);
@@ -736,6 +747,18 @@ int geoflood_init_forest(const geoflood_config* cfg, void* stream,
   G.dim_split = c.dim_split;
   G.subcycle = c.subcycle && c.maxlevel > c.minlevel ? 1 : 0;
   G.sub_K = G.subcycle ? 1 << (c.maxlevel - c.minlevel) : 1;
+  G.nregions = c.nregions;
+  for (int k = 0; k < GF_MAXREGION; ++k) {
+    const bool on = k < c.nregions;
+    G.rminl[k] = on ? c.region_minlevel[k] : 0;
+    G.rmaxl[k] = on ? c.region_maxlevel[k] : 0;
+    G.rx0[k] = on ? c.region_x0[k] : 0.0;
+    G.rx1[k] = on ? c.region_x1[k] : 0.0;
+    G.ry0[k] = on ? c.region_y0[k] : 0.0;
+    G.ry1[k] = on ? c.region_y1[k] : 0.0;
+    G.rt0[k] = on ? c.region_t0[k] : 0.0;
+    G.rt1[k] = on ? c.region_t1[k] : 0.0;
+  }
   G.n_hydro = c.n_hydro;
   G.inflow_side = c.inflow_side;
   G.inflow_lo = c.inflow_lo;
@@ -790,8 +813,8 @@ int geoflood_init_forest(const geoflood_config* cfg, void* stream,
   okk &= alloc((void**)&ctx->d_patch[1], cap * sizeof(GfPatch));
   okk &= alloc((void**)&ctx->d_nbr[0], cap * 8 * sizeof(int));
   okk &= alloc((void**)&ctx->d_nbr[1], cap * 8 * sizeof(int));
-  okk &= alloc((void**)&ctx->d_pbox[0], cap);
-  okk &= alloc((void**)&ctx->d_pbox[1], cap);
+  okk &= alloc((void**)&ctx->d_pbox[0], cap * sizeof(unsigned));
+  okk &= alloc((void**)&ctx->d_pbox[1], cap * sizeof(unsigned));
   okk &= alloc((void**)&ctx->d_done, sizeof(unsigned));
   okk &= alloc((void**)&ctx->d_sched, 8 * sizeof(unsigned));
   okk &= alloc((void**)&ctx->d_ord[0], cap * sizeof(int));

@@ -6,6 +6,7 @@
 
 #define GF_NG 2          // ghost layers
 #define GF_MAXLEV 16     // deepest level a forest may use
+#define GF_MAXREGION 8   // refinement regions per context
 #define GF_MAXSTEP_REJECT 50
 #define GF_SPIN_LIMIT (1u << 22)  // bounded waits on TMA mbarriers
 
@@ -112,6 +113,13 @@ struct GfGeom {
   // level subcycling (maxlevel > minlevel): level L takes 2^(L - minlevel)
   // steps per macro step, run as sub_K = 2^(maxlevel - minlevel) substeps
   int subcycle, sub_K;
+  // refinement regions (Sec. 4.1 criterion 4, Sec. 6.4): active while
+  // rt0 <= t <= rt1, they bound the level a cell whose centre lies in
+  // [rx0, rx1] x [ry0, ry1] asks for to [rminl, rmaxl]
+  int nregions;
+  int rminl[GF_MAXREGION], rmaxl[GF_MAXREGION];
+  double rx0[GF_MAXREGION], rx1[GF_MAXREGION], ry0[GF_MAXREGION], ry1[GF_MAXREGION];
+  double rt0[GF_MAXREGION], rt1[GF_MAXREGION];
 };
 
 // Everything a kernel needs to find patches and their data.
@@ -127,9 +135,11 @@ struct GfView {
   float* lof[2];          // FP32 compensation terms [cap][3][M][M]
   const int* nbr;         // [npatch][8] same-level neighbours (see below)
   // [npatch] the refinement source box against the patch's cell centres
-  // (the first and last in each direction, in FP64): 1 it misses the
-  // patch, 2 it covers it, 0 it crosses it; or null (then per patch)
-  const unsigned char* pbox;
+  // (the first and last in each direction, in FP64): bits 0-1 = 1 it misses
+  // the patch, 2 it covers it, 0 it crosses it; bits 2k + 2, 2k + 3 the same
+  // for refinement region k; or null (then every box and region is tested
+  // per cell)
+  const unsigned* pbox;
   unsigned* done;         // CTA completion counter of the step (or null)
   // Launch order of the patch step (or null: patch order).  sched[0] selects
   // which of ord0/ord1 this launch reads; the launch writes the other one

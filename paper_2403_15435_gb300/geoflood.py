@@ -58,6 +58,11 @@ class _Cfg(C.Structure):
         ("inflow_lo", C.c_double), ("inflow_hi", C.c_double), ("inflow_tau", C.c_double),
         ("hydro_t", C.c_double * 16), ("hydro_q", C.c_double * 16),
         ("subcycle", C.c_int),
+        ("nregions", C.c_int), ("region_minlevel", C.c_int * 8),
+        ("region_maxlevel", C.c_int * 8),
+        ("region_x0", C.c_double * 8), ("region_x1", C.c_double * 8),
+        ("region_y0", C.c_double * 8), ("region_y1", C.c_double * 8),
+        ("region_t0", C.c_double * 8), ("region_t1", C.c_double * 8),
     ]
 
 
@@ -192,6 +197,15 @@ def config_struct(cfg: inputs.Config, num_scenarios=1, max_patches=None,
     c.inflow_hi = float(getattr(cfg, "inflow_hi", 0.0))
     c.inflow_tau = float(getattr(cfg, "inflow_tau", 1e-4))
     c.subcycle = int(getattr(cfg, "subcycle", 0))
+    regions = list(getattr(cfg, "regions", ()))
+    if len(regions) > 8:
+        raise ValueError("at most 8 refinement regions")
+    c.nregions = len(regions)
+    for k, (x0, x1, y0, y1, t0, t1, lmin, lmax) in enumerate(regions):
+        c.region_x0[k], c.region_x1[k] = float(x0), float(x1)
+        c.region_y0[k], c.region_y1[k] = float(y0), float(y1)
+        c.region_t0[k], c.region_t1[k] = float(t0), float(t1)
+        c.region_minlevel[k], c.region_maxlevel[k] = int(lmin), int(lmax)
     c.num_scenarios = int(num_scenarios)
     if max_patches is None:
         per = cfg.mi * cfg.mj * (4 ** cfg.maxlevel)
