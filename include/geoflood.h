@@ -145,7 +145,7 @@ typedef struct {
   int subcycle;
   /* Refinement regions (Sec. 4.1 criterion 4: regions refined to a desired
    * resolution between user-given minimum and maximum levels; Sec. 6.4:
-   * particular locations or times).  nregions = 0..8.  While
+   * places and times of interest).  nregions = 0..8.  While
    * region_t0[k] <= t <= region_t1[k] (t the time of the scenario's state),
    * a cell whose centre lies in [region_x0[k], region_x1[k]] x
    * [region_y0[k], region_y1[k]] asks for a level of at least

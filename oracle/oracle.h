@@ -72,7 +72,7 @@ typedef struct {
   double hydro_t[16], hydro_q[16];
   /* refinement regions (Sec. 4.1 criterion 4: regions refined to a desired
    * resolution between user-given minimum and maximum levels; Sec. 6.4:
-   * particular locations or times): while region_t0[k] <= t <= region_t1[k]
+   * places and times of interest): while region_t0[k] <= t <= region_t1[k]
    * (t the time of the state), a cell whose centre lies in
    * [region_x0[k], region_x1[k]] x [region_y0[k], region_y1[k]] asks for a
    * level of at least region_minlevel[k] and at most region_maxlevel[k];

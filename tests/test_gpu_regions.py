@@ -1,6 +1,6 @@
 """Refinement regions (Sec. 4.1 criterion 4: regions refined between
-user-given minimum and maximum levels; Sec. 6.4: particular locations or
-times) on the GPU against the FP64 oracle through the C ABI.
+user-given minimum and maximum levels; Sec. 6.4: places and times of
+interest) on the GPU against the FP64 oracle through the C ABI.
 
 Tolerances: FP64 tags and patch lists bit-exact, states within 1e-11 of the
 field's largest magnitude after steps and regrids (the FP64 bound, as in the

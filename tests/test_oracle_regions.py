@@ -1,6 +1,6 @@
 """Pins of the oracle's refinement regions (Sec. 4.1 criterion 4: regions
 refined to a desired resolution between user-given minimum and maximum
-levels; Sec. 6.4: particular locations or times).  Each case is built so that
+levels; Sec. 6.4: places and times of interest).  Each case is built so that
 the expected levels or flags follow by hand from that statement: a region's
 minimum forces refinement even of dry water, its maximum caps what the other
 criteria ask for, overlapping regions take the largest minimum and the
