@@ -951,6 +951,28 @@ def cpu_baseline():
                       "4 (2048 -> ~6000 patches of 32x32), FP64, %.1f s" % (CPU_STEPS, sec)}
 
 
+CPU_STEPS_UNIFORM = 40
+
+
+def cpu_baseline_uniform(steps=CPU_STEPS_UNIFORM):
+    """The oracle on one host core on the 1024 x 1024 radial dam break (the
+    uniform workload) from t = 0: its first `steps` accepted steps of the
+    299 that reach t = 60 s."""
+    import oracle
+    from paper_2403_15435_gb300 import inputs
+    prob = inputs.radial_dambreak(N_CELLS, PATCH, dx=2.0, radius=200.0)
+    f = oracle.OracleForest(prob.cfg, prob.dem)
+    f.set_state(prob.ic)
+    t0 = time.perf_counter()
+    _, n = f.step(1e9, steps)
+    sec = time.perf_counter() - t0
+    cells = n * N_CELLS * N_CELLS
+    f.close()
+    return {"value": cells / sec, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+            "sample": "the 1024 x 1024 radial dam break from t = 0, its first %d steps "
+                      "(of 299 to t = 60 s), FP64, %.1f s" % (n, sec)}
+
+
 def cpu_baseline_all_cores(steps=12):
     """The same oracle, unchanged, on every host core at once: one spawned
     process per core, each stepping its own copy of the sample; the sum of
@@ -1034,6 +1056,7 @@ def run_ours(args):
     subcyc = measure_subcycle(stream) if single else None
     cpu = cpu_baseline() if (world == 1 and rank == 0) else None
     cpu_all = cpu_baseline_all_cores() if single else None
+    cpu_uniform = cpu_baseline_uniform() if single else None
     lr, f64 = v["learned"], v["fp64"]
     line = {
         "metric": "cell-updates/s", "value": v["value"], "unit": "cell-updates/s",
@@ -1057,6 +1080,7 @@ def run_ours(args):
         "error_vs_plain_fp64": v["err"],
         "training": v["train"],
         "roofline": v["roofline"], "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all,
+        "cpu_baseline_uniform_1024": cpu_uniform,
         "e2e": v["e2e"], "gpu_launches": v["launches"], "clocks": v["clocks"],
         "uniform_1024": uniform,
         "canyon_plain": canyon,
