@@ -100,6 +100,10 @@ def parse():
                     help="end of the headline window in simulated seconds")
     ap.add_argument("--headline-only", action="store_true",
                     help="skip the secondary workloads and CPU baselines")
+    ap.add_argument("--pair-only", action="store_true",
+                    help="only the valley pair and its control over --t-end, one run each "
+                         "after a short warm-up (no profiled or e2e runs); prints its own "
+                         "JSON line, not the benchmark line")
     ap.add_argument("--profile-case", type=int, default=0,
                     help="run N x N cells of the uniform workload for --profile-steps "
                          "steps and exit (for ncu captures; prints no JSON)")
@@ -511,6 +515,45 @@ def measure_valley(args, dev, stream, world, local, peaks):
                 clocks=clk.summary(), learned=learned, fp64=plain64, fp32_plain=plain32,
                 err=err, train=train, roofline=roof, e2e=e2e,
                 cells_per_run=cells / max(1, len(runs)))
+
+
+def run_pair_only(args):
+    """The metric's pair over a longer window: FP32 + learned tags (regrid
+    every LEARNED_REGRID), plain FP64 and FP32 + plain tags (regrid every 4),
+    each warmed up on the first 2 s and then run once over t = 0 -> t_end,
+    timed with CUDA events around the run; gauge errors against plain FP64."""
+    import torch
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    net_prm, net_thr, train = train_network(stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    out = {}
+    for key, prec, learned, regrid in (("fp32_learned", 1, True, LEARNED_REGRID),
+                                       ("fp64_plain", 0, False, 4),
+                                       ("fp32_plain", 1, False, 4)):
+        arm = ValleyArm(stream, prec, learned, regrid,
+                        net=(net_prm, net_thr) if learned else None, t_end=args.t_end)
+        arm.run(flush, t_end=2.0)
+        out[key] = arm.summary([arm.run(flush)])
+        arm.close()
+    err = {"fp32_learned": compare_gauges(out["fp64_plain"], out["fp32_learned"]),
+           "fp32_plain": compare_gauges(out["fp64_plain"], out["fp32_plain"])}
+    for r in out.values():
+        r.pop("_gauge_h")
+        r.pop("_arrival")
+    lr, f64 = out["fp32_learned"], out["fp64_plain"]
+    print(json.dumps({
+        "mode": "pair-only", "metric": "cell-updates/s", "unit": "cell-updates/s",
+        "value": lr["value"], "dtype": "f32 (vs f64)", "data": "synthetic",
+        "config": {"workload": VALLEY_WORKLOAD % args.t_end,
+                   "timing": "one run per arm after a 2 s warm-up, CUDA events on the "
+                             "library's stream, L2 flushed before each run"},
+        "fp32_learned": lr, "fp64_plain": f64, "fp32_plain": out["fp32_plain"],
+        "wall_clock_ratio_vs_fp64": f64["wall_s"] / lr["wall_s"],
+        "network_gain_wall": out["fp32_plain"]["wall_s"] / lr["wall_s"],
+        "error_vs_plain_fp64": err, "training": train}))
 
 
 # ----------------------------------------------------------------------------
@@ -1104,6 +1147,8 @@ def main():
         run_profile_valley(args)
     elif args.impl == "reference":
         run_reference(args)
+    elif args.pair_only:
+        run_pair_only(args)
     else:
         run_ours(args)
 
