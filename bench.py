@@ -82,12 +82,12 @@ N_SM = 152
 # DRAM bytes (read + write) of one patch-step launch, from the ncu captures
 # summarised in profiles/ (cold caches); None when the kernel has changed
 # since.  Valley: the launch at t = 30 s (6827 patches) of the 608-thread
-# variant that the autotuner picks there, 341 414 656 B over 6 990 848
+# variant that the autotuner picks there, 341 667 840 B over 6 990 848
 # cells, scaled to the cells of an average timed launch.  Uniform workload:
-# not recaptured since the FP32 quotient change.
-TRAFFIC_PER_LAUNCH_FP32 = None
+# launch 151 (t = 29.5 s), 4 629 504 B.
+TRAFFIC_PER_LAUNCH_FP32 = 4629504
 TRAFFIC_PER_LAUNCH_FP64 = None
-TRAFFIC_PER_CELL_VALLEY_FP32 = 341414656 / 6990848
+TRAFFIC_PER_CELL_VALLEY_FP32 = 341667840 / 6990848
 
 
 def parse():
