@@ -11,7 +11,7 @@ terms, update, Manning friction and the CFL control on every patch; the
 plain refinement criterion is checked every 4 steps and the forest is
 regridded (tags, 2:1 balance, refine and coarsen, new tables, fills).
 
-The metric is the spec pair on that workload:
+The metric is a pair of runs on that workload:
   value      FP32 surface-deviation form with the learned refinement
              predictor, regrid every 64 steps (the plain criterion still
              judges every 4 steps and forces a regrid on a miss);
