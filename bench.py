@@ -649,23 +649,26 @@ def measure_uniform_pair(args, dev, stream, peaks):
 CANYON_T = 20.0
 
 
-def measure_canyon(stream, net):
+def measure_canyon(stream, net, patch=32):
     """The 17 km x 9 km canyon-to-plain dam break (55 m reservoir, five
-    levels, 32 x 32 patches on levels 0-4), first CANYON_T seconds: FP32 with
-    learned tags (regrid every LEARNED_REGRID; the network is the one trained on the
-    plain criterion's flags from valley runs) against FP32 and FP64 with
-    plain tags (regrid every 4).  Wall clock of the driver loop, second of
-    two runs."""
+    levels: 32 x 32 patches on levels 0-4, or 16 x 16 patches on levels 1-5,
+    the same cell sizes), first CANYON_T seconds: FP32 with learned tags
+    (regrid every LEARNED_REGRID; the network is the one trained on the plain
+    criterion's flags from valley runs of 32 x 32 patches) against FP32 and
+    FP64 with plain tags (regrid every 4).  Wall clock of the driver loop,
+    second of two runs."""
     import numpy as np
     import torch
     from paper_2403_15435_gb300 import geoflood, inputs
 
-    cap = 40000
+    cap = 40000 if patch == 32 else 160000
+    lmin, lmax = (0, 4) if patch == 32 else (1, 5)
     scale = CNN_SCALE
     prm, thr = net
 
     def run(prec, learned, regrid):
-        prob = inputs.canyon_plain(precision=prec, near_gauges=16)
+        prob = inputs.canyon_plain(patch=patch, minlevel=lmin, maxlevel=lmax, precision=prec,
+                                   near_gauges=16)
         res = None
         for rep in range(2):
             g = geoflood.Forest(prob.cfg, prob.dem, max_patches=cap, stream=stream.cuda_stream)
@@ -682,7 +685,7 @@ def measure_canyon(stream, net):
             torch.cuda.synchronize()
             wall = time.perf_counter() - a
             out, arr = g.gauges()
-            res = {"value": s["patch_steps"] * PATCH * PATCH / wall, "unit": "cell-updates/s",
+            res = {"value": s["patch_steps"] * patch * patch / wall, "unit": "cell-updates/s",
                    "wall_s": wall, "steps": s["steps"], "regrids": s["regrids"],
                    "patches_at_end": g.npatch, "levels": sorted(set(int(x) for x in g.patch_info()[0])),
                    "time_split_s": {"steps_and_checks": s["step_s"], "separate_checks": s["check_s"],
@@ -705,9 +708,9 @@ def measure_canyon(stream, net):
     for r in (learned, plain32, plain64):
         r.pop("_h")
         r.pop("_a")
-    return {"workload": "canyon-to-plain 17 km x 9 km, 55 m reservoir, 32x32 patches, levels "
-                        "0-4 (finest dx 1.95 m), 32 gauges on the channel (16 within 2.05-2.8 km "
-                        "of the upstream end), t 0->%g s" % CANYON_T,
+    return {"workload": "canyon-to-plain 17 km x 9 km, 55 m reservoir, %dx%d patches, levels "
+                        "%d-%d (finest dx 1.95 m), 32 gauges on the channel (16 within 2.05-2.8 km "
+                        "of the upstream end), t 0->%g s" % (patch, patch, lmin, lmax, CANYON_T),
             "fp32_learned": learned, "fp32_plain_regrid4": plain32,
             "learned_regrid_interval": LEARNED_REGRID,
             "fp64_plain_regrid4": plain64, "error_vs_plain_fp64": err,
@@ -1092,6 +1095,7 @@ def run_ours(args):
     single = world == 1 and not args.headline_only
     uniform = measure_uniform_pair(args, dev, stream, peaks) if single else None
     canyon = measure_canyon(stream, v["net"]) if single else None
+    canyon16 = measure_canyon(stream, v["net"], patch=16) if single else None
     ens = measure_ensemble_full(stream) if single else None
     variants = measure_variants(stream) if single else None
     flood = measure_flood_speed(stream) if single else None
@@ -1127,6 +1131,7 @@ def run_ours(args):
         "e2e": v["e2e"], "gpu_launches": v["launches"], "clocks": v["clocks"],
         "uniform_1024": uniform,
         "canyon_plain": canyon,
+        "canyon_plain_16": canyon16,
         "ensemble_full": ens,
         "scheme_variants": variants,
         "flood_speed_inflow": flood,
