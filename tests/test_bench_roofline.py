@@ -61,3 +61,12 @@ def test_alu_side_counts_wet_cell_updates_and_binding_side_is_the_larger():
     assert abs(out["alu"]["peak"] - peak) <= 1e-12 * peak
     assert out["bound"] == ("alu" if out["alu"]["frac"] >= out["hbm"]["frac"] else "hbm")
     assert out["frac"] == max(out["alu"]["frac"], out["hbm"]["frac"])
+
+
+def test_uniform_cpu_sample_is_a_bounded_oracle_run():
+    """The uniform workload's CPU sample: the oracle on one core over the
+    first steps of the 1024 x 1024 radial dam break, every cell counted."""
+    out = bench.cpu_baseline_uniform(steps=1)
+    assert out["kind"] == "oracle" and out["cores"] == 1
+    assert out["unit"] == "cell-updates/s" and out["value"] > 0
+    assert "1024 x 1024 radial dam break" in out["sample"] and "first 1 steps" in out["sample"]
