@@ -1763,6 +1763,24 @@ __device__ __forceinline__ double warp_sum_f64(double v) {
   return v;
 }
 
+// One pixel of the network input: 16 BF16 channels (the four fields, the
+// level channel, zeros), written as two 16-byte stores (the pixel's 32
+// bytes are 32-byte aligned); each channel rounded to nearest as one
+// conversion would.
+__device__ __forceinline__ void store_pixel(__nv_bfloat16* op, const float (&v)[4], float lev) {
+  const __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]);
+  const __nv_bfloat162 b = __floats2bfloat162_rn(v[2], v[3]);
+  const __nv_bfloat162 c = __floats2bfloat162_rn(lev, 0.0f);
+  uint4 lo;
+  lo.x = *reinterpret_cast<const unsigned*>(&a);
+  lo.y = *reinterpret_cast<const unsigned*>(&b);
+  lo.z = *reinterpret_cast<const unsigned*>(&c);
+  lo.w = 0u;
+  uint4* o4 = reinterpret_cast<uint4*>(op);
+  o4[0] = lo;
+  o4[1] = make_uint4(0u, 0u, 0u, 0u);
+}
+
 template <typename T>
 __global__ void k_cnn_features(const __grid_constant__ GfGeom G,
                                const __grid_constant__ GfView V, int first,
@@ -1801,10 +1819,7 @@ __global__ void k_cnn_features(const __grid_constant__ GfGeom G,
       v[2] = (float)(acc[2] * inv / (double)sc.s[2]);
       v[3] = (float)((acc[3] * inv - bmean) / (double)sc.s[3]);
     }
-    __nv_bfloat16* op = o + (Y * 18 + X) * 16;
-    for (int c = 0; c < 4; ++c) op[c] = __float2bfloat16_rn(v[c]);
-    op[4] = __float2bfloat16_rn(0.25f * (float)P.level);
-    for (int c = 5; c < 16; ++c) op[c] = __float2bfloat16_rn(0.f);
+    store_pixel(o + (Y * 18 + X) * 16, v, 0.25f * (float)P.level);
   };
   // inner pixels: one thread each, f x f cells of the patch's own tile
   for (int q = threadIdx.x; q < 256; q += blockDim.x) {
@@ -1952,10 +1967,7 @@ __global__ void __launch_bounds__(256, 2)
       v[2] = acc[2] * inv / sc.s[2];
       v[3] = (acc[3] * inv - bmean) / sc.s[3];
     }
-    __nv_bfloat16* op = o + (Y * 18 + X) * 16;
-    for (int c = 0; c < 4; ++c) op[c] = __float2bfloat16_rn(v[c]);
-    op[4] = __float2bfloat16_rn(lev);
-    for (int c = 5; c < 16; ++c) op[c] = __float2bfloat16_rn(0.f);
+    store_pixel(o + (Y * 18 + X) * 16, v, lev);
   };
   for (int q = threadIdx.x; q < 256; q += blockDim.x) {
     const int X = q % 16 + 1, Y = q / 16 + 1;
